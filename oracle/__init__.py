@@ -1,0 +1,183 @@
+"""FP64 CPU oracle of the soliton relaxation method -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline /
+reference leg may import this package. The CUDA product path never calls it and
+shares no code with it (``soliton_oracle.cpp`` includes nothing of the product).
+
+Every function follows the paper step by step (equation numbers in order of
+appearance, see ``soliton_oracle.cpp``):
+
+* ``derivatives``          -- Eq. 1, Eq. 2 and the composed mixed derivative (Sec. 3.1)
+* ``energy`` / ``energy_density`` -- E_h of Table 1 (Abelian Higgs) and Eq. 5 (chiral magnet)
+* ``force``                -- Euler-Lagrange residual G driving Eq. 3
+* ``energy_grad_exact``    -- exact dE_h/dphi, only for pinning ``force``
+* ``anf_step`` / ``minimise`` -- arrested Newton flow, RK4 + Eq. 4 (Sec. 3.2)
+* ``observables``          -- energy, topological charge, flux, residual, |n|-1
+* ``ansatz``               -- vortex / skyrmion initial data (Sec. 3.4; standard forms)
+
+All functions are pinned by the ``-m "not gpu"`` tests in ``tests/test_oracle_pins.py``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+ABELIAN_HIGGS = 1
+CHIRAL_MAGNET = 2
+HARMONIC_TEST = 99
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "soliton_oracle.cpp")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_D = ctypes.POINTER(ctypes.c_double)
+
+
+def build(force: bool = False) -> str:
+    """Compile ``liboracle.so`` in-tree with g++ (OpenMP when available)."""
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
+        return _LIB_PATH
+    base = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-shared", "-fPIC", _SRC, "-o", _LIB_PATH + ".tmp"]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True)
+    os.replace(_LIB_PATH + ".tmp", _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            i, d, ll = ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+            lib.or_ncomp.argtypes = [i]
+            lib.or_ncomp.restype = i
+            lib.or_time_step.argtypes = [d, d]
+            lib.or_time_step.restype = d
+            lib.or_derivatives.argtypes = [_D, i, i, d, d, _D, _D, _D, _D, _D]
+            lib.or_derivatives.restype = None
+            lib.or_energy_density.argtypes = [i, _D, _D, i, i, d, d, _D]
+            lib.or_energy_density.restype = None
+            lib.or_energy.argtypes = [i, _D, _D, i, i, d, d]
+            lib.or_energy.restype = d
+            lib.or_force.argtypes = [i, _D, _D, i, i, d, d, _D]
+            lib.or_force.restype = None
+            lib.or_energy_grad_exact.argtypes = [i, _D, _D, i, i, d, d, _D]
+            lib.or_energy_grad_exact.restype = None
+            lib.or_anf_step.argtypes = [i, _D, _D, _D, i, i, d, d, d, _D]
+            lib.or_anf_step.restype = i
+            lib.or_minimise.argtypes = [i, _D, _D, _D, i, i, d, d, d, d, ll, _D]
+            lib.or_minimise.restype = i
+            lib.or_observables.argtypes = [i, _D, _D, i, i, d, d, _D]
+            lib.or_observables.restype = None
+            lib.or_ansatz.argtypes = [i, _D, i, _D, i, i, d, d]
+            lib.or_ansatz.restype = None
+            _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(_D)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _params(params) -> np.ndarray:
+    return _f64(np.asarray(params, dtype=np.float64).reshape(-1))
+
+
+def ncomp(theory: int) -> int:
+    return _load().or_ncomp(theory)
+
+
+def time_step(dx: float, dy: float) -> float:
+    """dt = C min(dx, dy), C = 0.5 (Sec. 3.1)."""
+    return _load().or_time_step(dx, dy)
+
+
+def derivatives(plane, dx: float, dy: float) -> dict:
+    p = _f64(plane)
+    ny, nx = p.shape
+    outs = {k: np.zeros_like(p) for k in ("fx", "fy", "fxx", "fyy", "fxy")}
+    _load().or_derivatives(_p(p), nx, ny, dx, dy, *(_p(outs[k]) for k in ("fx", "fy", "fxx", "fyy", "fxy")))
+    return outs
+
+
+def energy(theory: int, params, f, dx: float, dy: float) -> float:
+    f = _f64(f)
+    _, ny, nx = f.shape
+    return _load().or_energy(theory, _p(_params(params)), _p(f), nx, ny, dx, dy)
+
+
+def energy_density(theory: int, params, f, dx: float, dy: float) -> np.ndarray:
+    f = _f64(f)
+    _, ny, nx = f.shape
+    e = np.zeros((ny, nx))
+    _load().or_energy_density(theory, _p(_params(params)), _p(f), nx, ny, dx, dy, _p(e))
+    return e
+
+
+def force(theory: int, params, f, dx: float, dy: float) -> np.ndarray:
+    f = _f64(f)
+    _, ny, nx = f.shape
+    G = np.zeros_like(f)
+    _load().or_force(theory, _p(_params(params)), _p(f), nx, ny, dx, dy, _p(G))
+    return G
+
+
+def energy_grad_exact(theory: int, params, f, dx: float, dy: float) -> np.ndarray:
+    f = _f64(f)
+    _, ny, nx = f.shape
+    g = np.zeros_like(f)
+    _load().or_energy_grad_exact(theory, _p(_params(params)), _p(f), nx, ny, dx, dy, _p(g))
+    return g
+
+
+def anf_step(theory: int, params, f, v, dx: float, dy: float, dt: float, E: float):
+    """One arrested-Newton-flow RK4 step. Returns (f_new, v_new, E_new, arrested)."""
+    f = _f64(f).copy()
+    v = _f64(v).copy()
+    _, ny, nx = f.shape
+    e = np.array([E], dtype=np.float64)
+    arrested = _load().or_anf_step(theory, _p(_params(params)), _p(f), _p(v), nx, ny, dx, dy, dt, _p(e))
+    return f, v, float(e[0]), bool(arrested)
+
+
+def minimise(theory: int, params, f, dx: float, dy: float, tol: float, max_steps: int, v=None, dt=None) -> dict:
+    """Arrested Newton flow from rest (unless ``v`` is given) until dx dy max|G| < tol."""
+    f = _f64(f).copy()
+    v = np.zeros_like(f) if v is None else _f64(v).copy()
+    _, ny, nx = f.shape
+    dt = time_step(dx, dy) if dt is None else dt
+    out = np.zeros(4)
+    conv = _load().or_minimise(theory, _p(_params(params)), _p(f), _p(v), nx, ny, dx, dy, dt, tol, int(max_steps),
+                               _p(out))
+    return {"f": f, "v": v, "energy": out[0], "grad_max": out[1], "steps": int(out[2]), "arrests": int(out[3]),
+            "converged": bool(conv)}
+
+
+def observables(theory: int, params, f, dx: float, dy: float) -> dict:
+    f = _f64(f)
+    _, ny, nx = f.shape
+    out = np.zeros(6)
+    _load().or_observables(theory, _p(_params(params)), _p(f), nx, ny, dx, dy, _p(out))
+    return {"energy": out[0], "charge": out[1], "flux": out[2], "grad_max": out[3], "grad_max_raw": out[4],
+            "norm_dev": out[5]}
+
+
+def ansatz(theory: int, solitons, nx: int, ny: int, dx: float, dy: float) -> np.ndarray:
+    """``solitons``: rows (x, y, charge, size, phase)."""
+    s = _f64(np.asarray(solitons, dtype=np.float64).reshape(-1, 5))
+    f = np.zeros((ncomp(theory), ny, nx))
+    _load().or_ansatz(theory, _p(s), s.shape[0], _p(f), nx, ny, dx, dy)
+    return f

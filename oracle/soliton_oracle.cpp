@@ -1,0 +1,606 @@
+// soliton_oracle.cpp -- plain FP64 CPU restatement of the soliton relaxation method.
+//
+// TEST INFRASTRUCTURE ONLY. Only tests/, __graft_entry__.smoke() and bench.py's
+// cpu_baseline / reference leg load this library. The product (the CUDA library
+// under paper_2603_24370_gb300/csrc) never includes, links or calls it, and the
+// two share no code: no header, no helper, no constant table.
+//
+// Equation numbering follows the order of appearance in the paper (its equations
+// are unnumbered in print):
+//   Eq. 1  4th-order first-derivative stencil            (Sec. 3.1)
+//   Eq. 2  4th-order second-derivative stencil           (Sec. 3.1)
+//   Eq. 3  arrested Newton flow  phi'' = -grad E_h       (Sec. 3.2)
+//   Eq. 4  arrest test  E_h[phi^{n+1}] > E_h[phi^n]      (Sec. 3.2)
+//   Eq. 5  chiral-magnet energy functional               (Sec. 4.2)
+//   Table 1  energy functionals (Abelian Higgs row)      (Sec. 2.3)
+//
+// Readings of points the paper leaves open (each is listed with its reason in the
+// design notes of the repository):
+//   * The array is nx x ny sites including a halo of width 2 (Sec. 3.1). The halo
+//     keeps the initial values for ever (Dirichlet); only interior sites
+//     I = [2, nx-3] x [2, ny-3] are updated.
+//   * Coordinates x_i = (i - (nx-1)/2) dx, y_j = (j - (ny-1)/2) dy; i runs along x
+//     and is the fastest index; planes are stored [C][ny][nx].
+//   * E_h = dx dy sum_I e, with e evaluated with Eq. 1 only.
+//   * The force G that drives Eq. 3 is the continuum Euler-Lagrange expression with
+//     Eq. 1 / Eq. 2 derivatives (and Eq. 1 in x composed with Eq. 1 in y for the
+//     mixed derivative); it is the density-form residual, so the flow has unit wave
+//     speed and dt = C min(dx, dy) with C = 0.5 (Sec. 3.1).
+//   * The exact gradient of E_h (adjoint of Eq. 1) is provided separately, only for
+//     the tests that pin G.
+//   * Chiral magnet: interfacial DMI vectors d_1 = e_3 x e_1, d_2 = e_3 x e_2 by
+//     default, no demagnetising term; the unit-length constraint is enforced by
+//     normalising every RK stage input and the new field, tangent-projecting the
+//     force and the new velocity (Sec. 3.2, projection paragraph).
+//   * Arrest compares potential energies with a strict '>' (Eq. 4).
+//   * Convergence measure: max over I and components of |dx dy G|.
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+namespace {
+
+const double PI = 3.14159265358979323846;
+
+enum { TH_ABELIAN_HIGGS = 1, TH_CHIRAL_MAGNET = 2, TH_HARMONIC_TEST = 99 };
+
+struct Grid {
+  int nx, ny;
+  double dx, dy;
+  size_t plane() const { return (size_t)nx * ny; }
+  bool interior(int i, int j) const { return i >= 2 && i <= nx - 3 && j >= 2 && j <= ny - 3; }
+};
+
+int ncomp(int theory) {
+  switch (theory) {
+    case TH_ABELIAN_HIGGS: return 4;   // psi_1, psi_2, A_1, A_2 (Table 1)
+    case TH_CHIRAL_MAGNET: return 3;   // n_1, n_2, n_3 (Eq. 5)
+    case TH_HARMONIC_TEST: return 1;   // scalar test field
+    default: return 0;
+  }
+}
+
+// Neumaier compensated sum, fixed (row-major) order.
+struct Neumaier {
+  double s = 0.0, c = 0.0;
+  void add(double x) {
+    double t = s + x;
+    if (std::fabs(s) >= std::fabs(x)) c += (s - t) + x; else c += (x - t) + s;
+    s = t;
+  }
+  double value() const { return s + c; }
+};
+
+// ---------------------------------------------------------------- stencils
+// Eq. 1 (Sec. 3.1): d_x phi_{i,j} ~ (-phi_{i+2} + 8 phi_{i+1} - 8 phi_{i-1} + phi_{i-2}) / (12 dx)
+double d1x(const double* p, const Grid& g, int i, int j) {
+  const double* r = p + (size_t)j * g.nx;
+  return (-r[i + 2] + 8.0 * r[i + 1] - 8.0 * r[i - 1] + r[i - 2]) / (12.0 * g.dx);
+}
+// Eq. 1, "analogous expression in the y direction".
+double d1y(const double* p, const Grid& g, int i, int j) {
+  const size_t n = g.nx;
+  return (-p[(j + 2) * n + i] + 8.0 * p[(j + 1) * n + i] - 8.0 * p[(j - 1) * n + i] + p[(j - 2) * n + i]) /
+         (12.0 * g.dy);
+}
+// Eq. 2 (Sec. 3.1): d_x^2 phi ~ (-phi_{i+2} + 16 phi_{i+1} - 30 phi_i + 16 phi_{i-1} - phi_{i-2}) / (12 dx^2)
+double d2x(const double* p, const Grid& g, int i, int j) {
+  const double* r = p + (size_t)j * g.nx;
+  return (-r[i + 2] + 16.0 * r[i + 1] - 30.0 * r[i] + 16.0 * r[i - 1] - r[i - 2]) / (12.0 * g.dx * g.dx);
+}
+double d2y(const double* p, const Grid& g, int i, int j) {
+  const size_t n = g.nx;
+  return (-p[(j + 2) * n + i] + 16.0 * p[(j + 1) * n + i] - 30.0 * p[j * n + i] + 16.0 * p[(j - 1) * n + i] -
+          p[(j - 2) * n + i]) /
+         (12.0 * g.dy * g.dy);
+}
+// Mixed derivative d_x d_y: Eq. 1 along y applied to Eq. 1 along x (the paper is
+// silent on mixed derivatives; this is the composition of its two stencils).
+double d12(const double* p, const Grid& g, int i, int j) {
+  return (-d1x(p, g, i, j + 2) + 8.0 * d1x(p, g, i, j + 1) - 8.0 * d1x(p, g, i, j - 1) + d1x(p, g, i, j - 2)) /
+         (12.0 * g.dy);
+}
+
+// All derivatives of every component at one interior site.
+struct Site {
+  double v[4], fx[4], fy[4], fxx[4], fyy[4], fxy[4];
+};
+
+Site gather(const double* f, int C, const Grid& g, int i, int j, bool second) {
+  Site s;
+  for (int c = 0; c < C; ++c) {
+    const double* p = f + c * g.plane();
+    s.v[c] = p[(size_t)j * g.nx + i];
+    s.fx[c] = d1x(p, g, i, j);
+    s.fy[c] = d1y(p, g, i, j);
+    if (second) {
+      s.fxx[c] = d2x(p, g, i, j);
+      s.fyy[c] = d2y(p, g, i, j);
+      s.fxy[c] = d12(p, g, i, j);
+    } else {
+      s.fxx[c] = s.fyy[c] = s.fxy[c] = 0.0;
+    }
+  }
+  return s;
+}
+
+// DMI vectors d_1, d_2 (Eq. 5). type 0: interfacial d_i = e_3 x e_i (Neel);
+// type 1: bulk d_i = e_i (Bloch); type 2: d_1 = e_1, d_2 = -e_2 (D_2d, "Heusler",
+// anti-skyrmions; Sec. 4.2).
+void dmi_vectors(int type, double d1[3], double d2[3]) {
+  for (int k = 0; k < 3; ++k) d1[k] = d2[k] = 0.0;
+  if (type == 1) { d1[0] = 1.0; d2[1] = 1.0; }
+  else if (type == 2) { d1[0] = 1.0; d2[1] = -1.0; }
+  else { d1[1] = 1.0; d2[0] = -1.0; }  // e3 x e1 = e2, e3 x e2 = -e1
+}
+
+void cross(const double a[3], const double b[3], double out[3]) {
+  out[0] = a[1] * b[2] - a[2] * b[1];
+  out[1] = a[2] * b[0] - a[0] * b[2];
+  out[2] = a[0] * b[1] - a[1] * b[0];
+}
+double dot3(const double a[3], const double b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+// ---------------------------------------------------------------- energy densities
+// Abelian Higgs (Table 1): e = 1/2 |D psi|^2 + 1/2 |curl A|^2 + lambda/8 (u^2 - |psi|^2)^2,
+// with D_i psi = d_i psi - i A_i psi (unit charge). params = {lambda, u}.
+double density_ah(const double* prm, const Site& s) {
+  const double lam = prm[0], u = prm[1];
+  const double p1 = s.v[0], p2 = s.v[1], A1 = s.v[2], A2 = s.v[3];
+  // D_i psi = (d_i psi_1 + A_i psi_2) + i (d_i psi_2 - A_i psi_1)
+  const double re1 = s.fx[0] + A1 * p2, im1 = s.fx[1] - A1 * p1;
+  const double re2 = s.fy[0] + A2 * p2, im2 = s.fy[1] - A2 * p1;
+  const double B = s.fx[3] - s.fy[2];  // d_1 A_2 - d_2 A_1
+  const double w = u * u - (p1 * p1 + p2 * p2);
+  return 0.5 * (re1 * re1 + im1 * im1 + re2 * re2 + im2 * im2) + 0.5 * B * B + lam / 8.0 * w * w;
+}
+
+// Chiral magnet (Eq. 5 without the demagnetising term, dimensionless):
+// e = J/2 |d n|^2 + D sum_i d_i . (n x d_i n) + K (1 - n_3^2) + h (1 - n_3).
+// params = {J, D, K, h, dmi_type}.
+double density_cm(const double* prm, const Site& s) {
+  const double J = prm[0], D = prm[1], K = prm[2], h = prm[3];
+  double dv1[3], dv2[3];
+  dmi_vectors((int)prm[4], dv1, dv2);
+  const double n[3] = {s.v[0], s.v[1], s.v[2]};
+  const double nx_[3] = {s.fx[0], s.fx[1], s.fx[2]};
+  const double ny_[3] = {s.fy[0], s.fy[1], s.fy[2]};
+  double c1[3], c2[3];
+  cross(n, nx_, c1);
+  cross(n, ny_, c2);
+  const double ex = 0.5 * J * (dot3(nx_, nx_) + dot3(ny_, ny_));
+  const double dmi = D * (dot3(dv1, c1) + dot3(dv2, c2));
+  return ex + dmi + K * (1.0 - n[2] * n[2]) + h * (1.0 - n[2]);
+}
+
+// Harmonic test theory (oracle only, pins the time integrator): e = k/2 phi^2.
+double density_harm(const double* prm, const Site& s) { return 0.5 * prm[0] * s.v[0] * s.v[0]; }
+
+double density(int theory, const double* prm, const Site& s) {
+  switch (theory) {
+    case TH_ABELIAN_HIGGS: return density_ah(prm, s);
+    case TH_CHIRAL_MAGNET: return density_cm(prm, s);
+    default: return density_harm(prm, s);
+  }
+}
+
+// ---------------------------------------------------------------- Euler-Lagrange forces
+// Abelian Higgs: G = delta E / delta phi written out from Table 1:
+//   G_psi = -D_i D_i psi - lambda/2 (u^2 - |psi|^2) psi
+//         = -lap psi + i (div A) psi + 2 i A_i d_i psi + |A|^2 psi - lambda/2 (u^2-|psi|^2) psi
+//   G_A1  =  d_2 B - Im(conj(psi) D_1 psi),   G_A2 = -d_1 B - Im(conj(psi) D_2 psi),
+//   with B = d_1 A_2 - d_2 A_1 and -Im(conj(psi) D_i psi) = psi_2 d_i psi_1 - psi_1 d_i psi_2 + A_i |psi|^2.
+void force_ah(const double* prm, const Site& s, double G[4]) {
+  const double lam = prm[0], u = prm[1];
+  const double p1 = s.v[0], p2 = s.v[1], A1 = s.v[2], A2 = s.v[3];
+  const double lap1 = s.fxx[0] + s.fyy[0], lap2 = s.fxx[1] + s.fyy[1];
+  const double divA = s.fx[2] + s.fy[3];
+  const double AA = A1 * A1 + A2 * A2, mod2 = p1 * p1 + p2 * p2;
+  const double pot = 0.5 * lam * (u * u - mod2);
+  // Re and Im of 2 i A_i d_i psi:  2 i A_i (d_i psi_1 + i d_i psi_2) = -2 A_i d_i psi_2 + 2 i A_i d_i psi_1
+  G[0] = -lap1 - 2.0 * (A1 * s.fx[1] + A2 * s.fy[1]) - divA * p2 + AA * p1 - pot * p1;
+  G[1] = -lap2 + 2.0 * (A1 * s.fx[0] + A2 * s.fy[0]) + divA * p1 + AA * p2 - pot * p2;
+  const double d2B = s.fxy[3] - s.fyy[2];  // d_2 (d_1 A_2 - d_2 A_1)
+  const double d1B = s.fxx[3] - s.fxy[2];  // d_1 (d_1 A_2 - d_2 A_1)
+  G[2] = d2B + (p2 * s.fx[0] - p1 * s.fx[1]) + A1 * mod2;
+  G[3] = -d1B + (p2 * s.fy[0] - p1 * s.fy[1]) + A2 * mod2;
+}
+
+// Chiral magnet: delta E / delta n = -J lap n - 2 D sum_i d_i x d_i n - 2 K n_3 e_3 - h e_3,
+// then the tangent projection G <- G - (G . n) n that keeps |n| = 1 (Sec. 3.2).
+void force_cm(const double* prm, const Site& s, double G[3]) {
+  const double J = prm[0], D = prm[1], K = prm[2], h = prm[3];
+  double dv1[3], dv2[3];
+  dmi_vectors((int)prm[4], dv1, dv2);
+  const double nx_[3] = {s.fx[0], s.fx[1], s.fx[2]};
+  const double ny_[3] = {s.fy[0], s.fy[1], s.fy[2]};
+  double c1[3], c2[3];
+  cross(dv1, nx_, c1);
+  cross(dv2, ny_, c2);
+  for (int a = 0; a < 3; ++a) G[a] = -J * (s.fxx[a] + s.fyy[a]) - 2.0 * D * (c1[a] + c2[a]);
+  G[2] += -2.0 * K * s.v[2] - h;
+  const double n[3] = {s.v[0], s.v[1], s.v[2]};
+  const double gn = dot3(G, n);
+  for (int a = 0; a < 3; ++a) G[a] -= gn * n[a];
+}
+
+void force_site(int theory, const double* prm, const Site& s, double* G) {
+  switch (theory) {
+    case TH_ABELIAN_HIGGS: force_ah(prm, s, G); break;
+    case TH_CHIRAL_MAGNET: force_cm(prm, s, G); break;
+    default: G[0] = prm[0] * s.v[0]; break;
+  }
+}
+
+// ---------------------------------------------------------------- partial derivatives of e
+// d e / d phi_c and d e / d(d_i phi_c), used only by the exact gradient of E_h.
+void partials(int theory, const double* prm, const Site& s, double dv[4], double dgx[4], double dgy[4]) {
+  for (int c = 0; c < 4; ++c) dv[c] = dgx[c] = dgy[c] = 0.0;
+  if (theory == TH_ABELIAN_HIGGS) {
+    const double lam = prm[0], u = prm[1];
+    const double p1 = s.v[0], p2 = s.v[1], A1 = s.v[2], A2 = s.v[3];
+    const double X1 = s.fx[0] + A1 * p2, Y1 = s.fx[1] - A1 * p1;  // Re, Im of D_1 psi
+    const double X2 = s.fy[0] + A2 * p2, Y2 = s.fy[1] - A2 * p1;  // Re, Im of D_2 psi
+    const double B = s.fx[3] - s.fy[2];
+    const double w = u * u - (p1 * p1 + p2 * p2);
+    dgx[0] = X1; dgy[0] = X2;
+    dgx[1] = Y1; dgy[1] = Y2;
+    dgx[3] = B;  dgy[2] = -B;
+    dv[0] = -A1 * Y1 - A2 * Y2 - 0.5 * lam * w * p1;
+    dv[1] = A1 * X1 + A2 * X2 - 0.5 * lam * w * p2;
+    dv[2] = X1 * p2 - Y1 * p1;
+    dv[3] = X2 * p2 - Y2 * p1;
+  } else if (theory == TH_CHIRAL_MAGNET) {
+    const double J = prm[0], D = prm[1], K = prm[2], h = prm[3];
+    double dv1[3], dv2[3];
+    dmi_vectors((int)prm[4], dv1, dv2);
+    const double n[3] = {s.v[0], s.v[1], s.v[2]};
+    const double nx_[3] = {s.fx[0], s.fx[1], s.fx[2]};
+    const double ny_[3] = {s.fy[0], s.fy[1], s.fy[2]};
+    // d_i . (n x d_i n) = n . (d_i n x d_i)  = d_i n . (d_i x n)
+    double a1[3], a2[3], b1[3], b2[3];
+    cross(dv1, n, a1);    // d/d(d_1 n) of the DMI term
+    cross(dv2, n, a2);
+    cross(nx_, dv1, b1);  // d/dn of the DMI term
+    cross(ny_, dv2, b2);
+    for (int a = 0; a < 3; ++a) {
+      dgx[a] = J * nx_[a] + D * a1[a];
+      dgy[a] = J * ny_[a] + D * a2[a];
+      dv[a] = D * (b1[a] + b2[a]);
+    }
+    dv[2] += -2.0 * K * n[2] - h;
+  } else {
+    dv[0] = prm[0] * s.v[0];
+  }
+}
+
+// ---------------------------------------------------------------- lattice sums
+double energy(int theory, const double* prm, const double* f, const Grid& g) {
+  const int C = ncomp(theory);
+  std::vector<double> e(g.plane(), 0.0);
+#pragma omp parallel for schedule(static)
+  for (int j = 2; j <= g.ny - 3; ++j)
+    for (int i = 2; i <= g.nx - 3; ++i) e[(size_t)j * g.nx + i] = density(theory, prm, gather(f, C, g, i, j, false));
+  Neumaier acc;
+  for (int j = 2; j <= g.ny - 3; ++j)
+    for (int i = 2; i <= g.nx - 3; ++i) acc.add(e[(size_t)j * g.nx + i]);
+  return g.dx * g.dy * acc.value();
+}
+
+// G on I, zero on the halo.
+void force(int theory, const double* prm, const double* f, const Grid& g, double* G) {
+  const int C = ncomp(theory);
+  std::memset(G, 0, sizeof(double) * C * g.plane());
+#pragma omp parallel for schedule(static)
+  for (int j = 2; j <= g.ny - 3; ++j)
+    for (int i = 2; i <= g.nx - 3; ++i) {
+      double Gs[4];
+      force_site(theory, prm, gather(f, C, g, i, j, true), Gs);
+      for (int c = 0; c < C; ++c) G[c * g.plane() + (size_t)j * g.nx + i] = Gs[c];
+    }
+}
+
+double max_abs(const double* a, size_t n) {
+  double m = 0.0;
+  for (size_t k = 0; k < n; ++k) m = std::fmax(m, std::fabs(a[k]));
+  return m;
+}
+
+// Unit-length projection of the chiral magnet (Sec. 3.2): n <- n / |n| on every
+// interior site (the halo is fixed and already unit length).
+void normalise(double* f, const Grid& g) {
+  const size_t P = g.plane();
+  for (int j = 2; j <= g.ny - 3; ++j)
+    for (int i = 2; i <= g.nx - 3; ++i) {
+      const size_t k = (size_t)j * g.nx + i;
+      const double r = std::sqrt(f[k] * f[k] + f[P + k] * f[P + k] + f[2 * P + k] * f[2 * P + k]);
+      f[k] /= r; f[P + k] /= r; f[2 * P + k] /= r;
+    }
+}
+// Tangent projection of a velocity: v <- v - (v . n) n.
+void tangent(double* v, const double* n, const Grid& g) {
+  const size_t P = g.plane();
+  for (size_t k = 0; k < P; ++k) {
+    const double vn = v[k] * n[k] + v[P + k] * n[P + k] + v[2 * P + k] * n[2 * P + k];
+    v[k] -= vn * n[k]; v[P + k] -= vn * n[P + k]; v[2 * P + k] -= vn * n[2 * P + k];
+  }
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+int or_ncomp(int theory) { return ncomp(theory); }
+
+// Sec. 3.1: dt = C * dx with the default Courant-like number C = 0.5; with
+// unequal spacings the smaller one is used.
+double or_time_step(double dx, double dy) { return 0.5 * (dx < dy ? dx : dy); }
+
+// Eq. 1, Eq. 2 and the mixed derivative of one plane on I (zero on the halo).
+void or_derivatives(const double* p, int nx, int ny, double dx, double dy, double* fx, double* fy, double* fxx,
+                    double* fyy, double* fxy) {
+  const Grid g{nx, ny, dx, dy};
+  const size_t P = g.plane();
+  std::memset(fx, 0, P * 8); std::memset(fy, 0, P * 8); std::memset(fxx, 0, P * 8);
+  std::memset(fyy, 0, P * 8); std::memset(fxy, 0, P * 8);
+  for (int j = 2; j <= ny - 3; ++j)
+    for (int i = 2; i <= nx - 3; ++i) {
+      const size_t k = (size_t)j * nx + i;
+      fx[k] = d1x(p, g, i, j); fy[k] = d1y(p, g, i, j);
+      fxx[k] = d2x(p, g, i, j); fyy[k] = d2y(p, g, i, j); fxy[k] = d12(p, g, i, j);
+    }
+}
+
+// Energy density e on I (zero on the halo).
+void or_energy_density(int theory, const double* prm, const double* f, int nx, int ny, double dx, double dy,
+                       double* e) {
+  const Grid g{nx, ny, dx, dy};
+  const int C = ncomp(theory);
+  std::memset(e, 0, sizeof(double) * g.plane());
+  for (int j = 2; j <= ny - 3; ++j)
+    for (int i = 2; i <= nx - 3; ++i) e[(size_t)j * nx + i] = density(theory, prm, gather(f, C, g, i, j, false));
+}
+
+// E_h = dx dy sum_I e  (Sec. 3.2, discretised energy functional).
+double or_energy(int theory, const double* prm, const double* f, int nx, int ny, double dx, double dy) {
+  return energy(theory, prm, f, Grid{nx, ny, dx, dy});
+}
+
+// Euler-Lagrange force G on I (zero on the halo); chiral magnet tangent-projected.
+void or_force(int theory, const double* prm, const double* f, int nx, int ny, double dx, double dy, double* G) {
+  force(theory, prm, f, Grid{nx, ny, dx, dy}, G);
+}
+
+// Exact gradient dE_h/dphi of the lattice energy (adjoint of Eq. 1), no projection.
+// Used only to pin G; footprint 9x9 instead of G's 5x5.
+void or_energy_grad_exact(int theory, const double* prm, const double* f, int nx, int ny, double dx, double dy,
+                          double* grad) {
+  const Grid g{nx, ny, dx, dy};
+  const int C = ncomp(theory);
+  const size_t P = g.plane();
+  std::memset(grad, 0, sizeof(double) * C * P);
+  const double w[5] = {1.0, -8.0, 0.0, 8.0, -1.0};  // Eq. 1 weights at offsets -2..2
+  const double A = dx * dy;
+  for (int j = 2; j <= ny - 3; ++j)
+    for (int i = 2; i <= nx - 3; ++i) {
+      double dv[4], dgx[4], dgy[4];
+      partials(theory, prm, gather(f, C, g, i, j, false), dv, dgx, dgy);
+      for (int c = 0; c < C; ++c) {
+        double* gc = grad + c * P;
+        gc[(size_t)j * nx + i] += A * dv[c];
+        for (int m = -2; m <= 2; ++m) {
+          gc[(size_t)j * nx + (i + m)] += A * dgx[c] * w[m + 2] / (12.0 * dx);
+          gc[(size_t)(j + m) * nx + i] += A * dgy[c] * w[m + 2] / (12.0 * dy);
+        }
+      }
+    }
+}
+
+// One arrested-Newton-flow step (Eq. 3, Eq. 4) by classic RK4 on the first-order
+// system (phi, v = phi-dot) (Sec. 3.2):
+//   k1 = (v,            -G(phi))
+//   k2 = (v + dt/2 k1v, -G(phi + dt/2 k1phi))
+//   k3 = (v + dt/2 k2v, -G(phi + dt/2 k2phi))
+//   k4 = (v + dt   k3v, -G(phi + dt   k3phi))
+//   (phi, v) += dt/6 (k1 + 2 k2 + 2 k3 + k4)
+// then, if E_h(phi^{n+1}) > E_h(phi^n), v^{n+1} <- 0 (Eq. 4).
+// Chiral magnet: every stage input and phi^{n+1} are normalised; v^{n+1} is
+// tangent-projected at phi^{n+1}. Halo sites stay fixed (v = 0 there).
+// *E_io holds E_h(phi^n) on entry and E_h(phi^{n+1}) on exit. Returns 1 if arrested.
+int or_anf_step(int theory, const double* prm, double* f, double* v, int nx, int ny, double dx, double dy, double dt,
+                double* E_io) {
+  const Grid g{nx, ny, dx, dy};
+  const int C = ncomp(theory);
+  const size_t N = (size_t)C * g.plane();
+  const bool cm = (theory == TH_CHIRAL_MAGNET);
+  // v and every G vanish on the halo, so every k_phi and k_v does too and the halo
+  // stays fixed without special cases.
+  std::vector<double> k1p(N), k1v(N), k2p(N), k2v(N), k3p(N), k3v(N), k4p(N), k4v(N), y(N);
+  auto kv_at = [&](std::vector<double>& kv) {  // k_v = -G(y)
+    if (cm) normalise(y.data(), g);
+    force(theory, prm, y.data(), g, kv.data());
+    for (size_t k = 0; k < N; ++k) kv[k] = -kv[k];
+  };
+  // k1
+  for (size_t k = 0; k < N; ++k) { y[k] = f[k]; k1p[k] = v[k]; }
+  kv_at(k1v);
+  // k2
+  for (size_t k = 0; k < N; ++k) { y[k] = f[k] + 0.5 * dt * k1p[k]; k2p[k] = v[k] + 0.5 * dt * k1v[k]; }
+  kv_at(k2v);
+  // k3
+  for (size_t k = 0; k < N; ++k) { y[k] = f[k] + 0.5 * dt * k2p[k]; k3p[k] = v[k] + 0.5 * dt * k2v[k]; }
+  kv_at(k3v);
+  // k4
+  for (size_t k = 0; k < N; ++k) { y[k] = f[k] + dt * k3p[k]; k4p[k] = v[k] + dt * k3v[k]; }
+  kv_at(k4v);
+  // combine
+  for (size_t k = 0; k < N; ++k) {
+    f[k] += dt / 6.0 * (k1p[k] + 2.0 * k2p[k] + 2.0 * k3p[k] + k4p[k]);
+    v[k] += dt / 6.0 * (k1v[k] + 2.0 * k2v[k] + 2.0 * k3v[k] + k4v[k]);
+  }
+  if (cm) {
+    normalise(f, g);
+    tangent(v, f, g);
+  }
+  const double E_new = energy(theory, prm, f, g);
+  int arrested = 0;
+  if (E_new > *E_io) {  // Eq. 4, strict
+    std::memset(v, 0, sizeof(double) * N);
+    arrested = 1;
+  }
+  *E_io = E_new;
+  return arrested;
+}
+
+// Arrested Newton flow from the given (phi, v) until max_I |dx dy G(phi)| < tol or
+// max_steps steps have been taken. out = {E, norm (dx dy max|G|), steps, arrests}.
+// Returns 1 if converged, 0 otherwise.
+int or_minimise(int theory, const double* prm, double* f, double* v, int nx, int ny, double dx, double dy, double dt,
+                double tol, long long max_steps, double* out) {
+  const Grid g{nx, ny, dx, dy};
+  const int C = ncomp(theory);
+  const size_t N = (size_t)C * g.plane();
+  std::vector<double> G(N);
+  double E = energy(theory, prm, f, g);
+  long long steps = 0, arrests = 0;
+  double norm = 0.0;
+  int converged = 0;
+  for (;;) {
+    force(theory, prm, f, g, G.data());
+    norm = dx * dy * max_abs(G.data(), N);
+    if (norm < tol) { converged = 1; break; }
+    if (steps >= max_steps) break;
+    arrests += or_anf_step(theory, prm, f, v, nx, ny, dx, dy, dt, &E);
+    ++steps;
+  }
+  out[0] = E; out[1] = norm; out[2] = (double)steps; out[3] = (double)arrests;
+  return converged;
+}
+
+// Signed solid angle of the spherical triangle (a, b, c):
+// tan(Omega/2) = a.(b x c) / (1 + a.b + b.c + c.a)   (Berg and Luescher, 1981).
+static double solid_angle(const double a[3], const double b[3], const double c[3]) {
+  double bc[3];
+  cross(b, c, bc);
+  return 2.0 * std::atan2(dot3(a, bc), 1.0 + dot3(a, b) + dot3(b, c) + dot3(c, a));
+}
+
+// Observables (Sec. 2 "GPU-resident evaluation of observables"; Sec. 3.3):
+// out[0] = E_h
+// out[1] = topological charge: chiral magnet Berg-Luescher lattice charge over all
+//          plaquettes, two triangles each, oriented like n.(d_1 n x d_2 n), divided by
+//          4 pi; Abelian Higgs winding of arg psi around the boundary of I
+//          (counter-clockwise), divided by 2 pi.
+// out[2] = magnetic flux dx dy sum_I (d_1 A_2 - d_2 A_1) (Abelian Higgs), 0 otherwise
+// out[3] = dx dy max_I |G|, out[4] = max_I |G|
+// out[5] = max over all sites of ||n| - 1| (chiral magnet), 0 otherwise
+void or_observables(int theory, const double* prm, const double* f, int nx, int ny, double dx, double dy,
+                    double* out) {
+  const Grid g{nx, ny, dx, dy};
+  const int C = ncomp(theory);
+  const size_t P = g.plane(), N = (size_t)C * P;
+  std::vector<double> G(N);
+  force(theory, prm, f, g, G.data());
+  const double gmax = max_abs(G.data(), N);
+  out[0] = energy(theory, prm, f, g);
+  out[1] = 0.0; out[2] = 0.0; out[3] = dx * dy * gmax; out[4] = gmax; out[5] = 0.0;
+  if (theory == TH_CHIRAL_MAGNET) {
+    auto unit = [&](int i, int j, double n[3]) {
+      const size_t k = (size_t)j * nx + i;
+      const double r = std::sqrt(f[k] * f[k] + f[P + k] * f[P + k] + f[2 * P + k] * f[2 * P + k]);
+      n[0] = f[k] / r; n[1] = f[P + k] / r; n[2] = f[2 * P + k] / r;
+    };
+    Neumaier q;
+    for (int j = 0; j + 1 < ny; ++j)
+      for (int i = 0; i + 1 < nx; ++i) {
+        double n00[3], n10[3], n11[3], n01[3];
+        unit(i, j, n00); unit(i + 1, j, n10); unit(i + 1, j + 1, n11); unit(i, j + 1, n01);
+        q.add(solid_angle(n00, n10, n11));
+        q.add(solid_angle(n00, n11, n01));
+      }
+    out[1] = q.value() / (4.0 * PI);
+    double dev = 0.0;
+    for (size_t k = 0; k < P; ++k)
+      dev = std::fmax(dev, std::fabs(std::sqrt(f[k] * f[k] + f[P + k] * f[P + k] + f[2 * P + k] * f[2 * P + k]) - 1.0));
+    out[5] = dev;
+  } else if (theory == TH_ABELIAN_HIGGS) {
+    // loop of boundary sites of I, counter-clockwise
+    std::vector<int> li, lj;
+    for (int i = 2; i < nx - 3; ++i) { li.push_back(i); lj.push_back(2); }
+    for (int j = 2; j < ny - 3; ++j) { li.push_back(nx - 3); lj.push_back(j); }
+    for (int i = nx - 3; i > 2; --i) { li.push_back(i); lj.push_back(ny - 3); }
+    for (int j = ny - 3; j > 2; --j) { li.push_back(2); lj.push_back(j); }
+    Neumaier w;
+    const size_t L = li.size();
+    for (size_t k = 0; k < L; ++k) {
+      const size_t a = (size_t)lj[k] * nx + li[k], b = (size_t)lj[(k + 1) % L] * nx + li[(k + 1) % L];
+      double d = std::atan2(f[P + b], f[b]) - std::atan2(f[P + a], f[a]);
+      while (d > PI) d -= 2.0 * PI;
+      while (d <= -PI) d += 2.0 * PI;
+      w.add(d);
+    }
+    out[1] = w.value() / (2.0 * PI);
+    Neumaier flux;
+    const double* A1 = f + 2 * P;
+    const double* A2 = f + 3 * P;
+    for (int j = 2; j <= ny - 3; ++j)
+      for (int i = 2; i <= nx - 3; ++i) flux.add(d1x(A2, g, i, j) - d1y(A1, g, i, j));
+    out[2] = dx * dy * flux.value();
+  }
+}
+
+// Initial configurations ("model-specific ansatz", Sec. 3.4 / Sec. 4.1). The paper
+// gives no formula; these are the standard forms.
+// Abelian Higgs, product of unit-size radial vortices of winding n_k at (x_k, y_k):
+//   psi = prod_k tanh(r_k/s_k)^{|n_k|} exp(i (n_k theta_k + chi_k)),
+//   A   = sum_k n_k tanh^2(r_k/s_k) (-(y-y_k), x-x_k) / r_k^2   (A = 0 at r_k = 0).
+// Chiral magnet, compact skyrmions of radius R_k = s_k, vorticity m_k, helicity gamma_k:
+//   n = (sin f cos(m theta + gamma), sin f sin(m theta + gamma), cos f),
+//   f = pi (1 - r/R) for r < R, else 0 (n = e_3); the first disc containing a site wins.
+// sol[k*5 + 0..4] = {x, y, charge, size, phase}.
+void or_ansatz(int theory, const double* sol, int nsol, double* f, int nx, int ny, double dx, double dy) {
+  const size_t P = (size_t)nx * ny;
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      const double x = (i - 0.5 * (nx - 1)) * dx, y = (j - 0.5 * (ny - 1)) * dy;
+      const size_t k = (size_t)j * nx + i;
+      if (theory == TH_ABELIAN_HIGGS) {
+        double mod = 1.0, ph = 0.0, A1 = 0.0, A2 = 0.0;
+        for (int s = 0; s < nsol; ++s) {
+          const double X = x - sol[5 * s], Y = y - sol[5 * s + 1];
+          const double n = sol[5 * s + 2], sz = sol[5 * s + 3], chi = sol[5 * s + 4];
+          const double r2 = X * X + Y * Y, r = std::sqrt(r2);
+          const double t = std::tanh(r / sz);
+          mod *= std::pow(t, std::fabs(n));
+          ph += n * std::atan2(Y, X) + chi;
+          if (r2 > 0.0) {
+            A1 += n * t * t * (-Y) / r2;
+            A2 += n * t * t * X / r2;
+          }
+        }
+        f[k] = mod * std::cos(ph);
+        f[P + k] = mod * std::sin(ph);
+        f[2 * P + k] = A1;
+        f[3 * P + k] = A2;
+      } else if (theory == TH_CHIRAL_MAGNET) {
+        double n1 = 0.0, n2 = 0.0, n3 = 1.0;
+        for (int s = 0; s < nsol; ++s) {
+          const double X = x - sol[5 * s], Y = y - sol[5 * s + 1];
+          const double m = sol[5 * s + 2], R = sol[5 * s + 3], gam = sol[5 * s + 4];
+          const double r = std::sqrt(X * X + Y * Y);
+          if (r < R) {
+            const double fr = PI * (1.0 - r / R), th = m * std::atan2(Y, X) + gam;
+            n1 = std::sin(fr) * std::cos(th);
+            n2 = std::sin(fr) * std::sin(th);
+            n3 = std::cos(fr);
+            break;
+          }
+        }
+        f[k] = n1; f[P + k] = n2; f[2 * P + k] = n3;
+      }
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,433 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test pins one part of ``oracle/`` to something other than the oracle itself:
+values printed in the paper (``tests/golden/paper_constants.json``), closed forms,
+textbook radial reductions of the energies, symmetries that hold exactly on the
+lattice, brute-force finite differences, and the Bogomolny bound. A plausible slip
+in the oracle (a dropped term, a wrong sign, a swapped dx/dy, a wrong RK4 weight)
+fails at least one of them. Unequal spacings are used where a test allows it.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2603_24370_gb300 import inputs as I
+
+AH, CM, HARM = O.ABELIAN_HIGGS, O.CHIRAL_MAGNET, O.HARMONIC_TEST
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_constants.json")
+AH_PRM = (1.0, 1.0)
+CM_PRM = (1.0, 1.0, 0.1, 0.6, 0.0)
+
+
+def golden():
+    with open(GOLDEN) as fh:
+        return json.load(fh)
+
+
+def grid(nx, ny, dx, dy):
+    x = (np.arange(nx) - 0.5 * (nx - 1)) * dx
+    y = (np.arange(ny) - 0.5 * (ny - 1)) * dy
+    return np.meshgrid(x, y)
+
+
+# ---------------------------------------------------------------- stencils (Eq. 1, Eq. 2)
+def test_stencil_weights_are_the_papers():
+    g = golden()
+    nx, ny, dx, dy = 11, 11, 0.3, 0.7
+    p = np.zeros((ny, nx))
+    i0, j0 = 5, 5
+    p[j0, i0] = 1.0
+    d = O.derivatives(p, dx, dy)
+    w1 = g["eq1_first_derivative"]
+    w2 = g["eq2_second_derivative"]
+    for off, w in zip(w1["offsets"], w1["weights"]):
+        # d1x(i) = sum_m w_m p(i+m) / (12 dx)  ->  at i = i0 - m it equals w_m / (12 dx)
+        assert d["fx"][j0, i0 - off] == pytest.approx(w / (w1["denominator"] * dx), abs=1e-15)
+        assert d["fy"][j0 - off, i0] == pytest.approx(w / (w1["denominator"] * dy), abs=1e-15)
+    for off, w in zip(w2["offsets"], w2["weights"]):
+        assert d["fxx"][j0, i0 - off] == pytest.approx(w / (w2["denominator"] * dx * dx), abs=1e-13)
+        assert d["fyy"][j0 - off, i0] == pytest.approx(w / (w2["denominator"] * dy * dy), abs=1e-13)
+    # mixed derivative = product of the Eq. 1 weights in x and y
+    for ox, wx in zip(w1["offsets"], w1["weights"]):
+        for oy, wy in zip(w1["offsets"], w1["weights"]):
+            exp = wx * wy / (144.0 * dx * dy)
+            assert d["fxy"][j0 - oy, i0 - ox] == pytest.approx(exp, abs=1e-13)
+
+
+def test_courant_number_is_the_papers():
+    c = golden()["courant_number"]["value"]
+    assert O.time_step(0.1, 0.1) == pytest.approx(c * 0.1, rel=1e-15)
+    assert O.time_step(0.3, 0.2) == pytest.approx(c * 0.2, rel=1e-15)
+
+
+def test_stencils_exact_on_polynomials():
+    nx, ny, dx, dy = 13, 11, 0.37, 0.23
+    X, Y = grid(nx, ny, dx, dy)
+    f = 0.3 * X**4 - 1.1 * X**3 + 0.7 * X * X + 2.0 * X + 1.5 * Y**4 - 0.4 * Y**3 + 0.9 * X**3 * Y**2 + 0.2 * X * Y**4
+    fx = 1.2 * X**3 - 3.3 * X * X + 1.4 * X + 2.0 + 2.7 * X * X * Y * Y + 0.2 * Y**4
+    fy = 6.0 * Y**3 - 1.2 * Y * Y + 1.8 * X**3 * Y + 0.8 * X * Y**3
+    fxx = 3.6 * X * X - 6.6 * X + 1.4 + 5.4 * X * Y * Y
+    fyy = 18.0 * Y * Y - 2.4 * Y + 1.8 * X**3 + 2.4 * X * Y * Y
+    fxy = 5.4 * X * X * Y + 0.8 * Y**3
+    d = O.derivatives(f, dx, dy)
+    sl = (slice(2, ny - 2), slice(2, nx - 2))
+    for key, ref in (("fx", fx), ("fy", fy), ("fxx", fxx), ("fyy", fyy), ("fxy", fxy)):
+        np.testing.assert_allclose(d[key][sl], ref[sl], rtol=0, atol=1e-9 * np.abs(ref).max(), err_msg=key)
+
+
+def test_stencils_fourth_order():
+    errs = []
+    for n in (33, 65):
+        L = 4.0
+        dx = L / (n - 1)
+        dy = 0.8 * dx
+        X, Y = grid(n, n, dx, dy)
+        f = np.sin(1.3 * X + 0.4) * np.cos(0.9 * Y - 0.2)
+        ex = {
+            "fx": 1.3 * np.cos(1.3 * X + 0.4) * np.cos(0.9 * Y - 0.2),
+            "fy": -0.9 * np.sin(1.3 * X + 0.4) * np.sin(0.9 * Y - 0.2),
+            "fxx": -1.69 * f,
+            "fyy": -0.81 * f,
+            "fxy": -1.17 * np.cos(1.3 * X + 0.4) * np.sin(0.9 * Y - 0.2),
+        }
+        d = O.derivatives(f, dx, dy)
+        errs.append({k: np.abs(d[k] - ex[k])[2:-2, 2:-2].max() for k in ex})
+    for k in errs[0]:
+        ratio = errs[0][k] / errs[1][k]
+        assert 12.0 < ratio < 20.0, (k, ratio)
+
+
+# ---------------------------------------------------------------- energy (Table 1, Eq. 5)
+def _ah_radial_energy(lam):
+    from scipy.integrate import quad
+
+    def integrand(r):
+        t = math.tanh(r)
+        s2 = 1.0 - t * t
+        g, gp, a, ap = t, s2, t * t, 2.0 * t * s2
+        return (0.5 * (gp * gp + g * g * (1 - a) ** 2 / (r * r)) + 0.5 * (ap / r) ** 2
+                + lam / 8.0 * (1 - g * g) ** 2) * r
+
+    val, _ = quad(integrand, 0.0, 40.0, epsabs=1e-13, epsrel=1e-13, limit=400)
+    return 2 * math.pi * val
+
+
+@pytest.mark.parametrize("lam", [1.0, 1.7])
+def test_ah_energy_matches_radial_reduction(lam):
+    """E_h of the radial vortex psi = tanh(r) e^{i theta}, A = tanh(r)^2 dtheta converges
+    at fourth order to the textbook radial integral of Table 1's functional."""
+    Econt = _ah_radial_energy(lam)
+    errs = []
+    for n in (81, 161):
+        L = 20.0
+        dx = L / (n - 1)
+        f = O.ansatz(AH, [[0.0, 0.0, 1.0, 1.0, 0.0]], n, n, dx, dx)
+        errs.append(abs(O.energy(AH, (lam, 1.0), f, dx, dx) - Econt))
+    # a wrong term would make E_h converge to another value and the ratio collapse to ~1
+    assert errs[1] < 1e-4 * Econt
+    assert 12.0 < errs[0] / errs[1] < 20.0
+
+
+def _cm_radial_energy(prm, w, helicity):
+    from scipy.integrate import quad
+    J, D, K, h = prm[:4]
+
+    def integrand(r):
+        f = math.pi * (1 - math.tanh(r / w))
+        fp = -math.pi / w / math.cosh(r / w) ** 2
+        ex = 0.5 * J * (fp * fp + math.sin(f) ** 2 / (r * r))
+        dmi = D * math.cos(helicity) * (fp + math.sin(f) * math.cos(f) / r)
+        return (ex + dmi + K * math.sin(f) ** 2 + h * (1 - math.cos(f))) * r
+
+    val, _ = quad(integrand, 0.0, 60.0, epsabs=1e-13, epsrel=1e-13, limit=400)
+    return 2 * math.pi * val
+
+
+@pytest.mark.parametrize("helicity", [0.0, math.pi, 0.5 * math.pi])
+def test_cm_energy_matches_radial_reduction(helicity):
+    """Interfacial-DMI chiral magnet energy of a smooth skyrmion profile converges at
+    fourth order to the radial reduction (Neel helicity: DMI = D cos(gamma)(f' + sin f cos f / r))."""
+    w = 2.0
+    Econt = _cm_radial_energy(CM_PRM, w, helicity)
+    errs = []
+    for n in (161, 321):
+        L = 32.0
+        dx = L / (n - 1)
+        X, Y = grid(n, n, dx, dx)
+        r = np.hypot(X, Y)
+        th = np.arctan2(Y, X) + helicity
+        f = np.pi * (1 - np.tanh(r / w))
+        field = np.stack([np.sin(f) * np.cos(th), np.sin(f) * np.sin(th), np.cos(f)])
+        errs.append(abs(O.energy(CM, CM_PRM, field, dx, dx) - Econt))
+    assert errs[1] < 5e-5 * max(10.0, abs(Econt))
+    assert 12.0 < errs[0] / errs[1] < 20.0
+
+
+def test_dmi_sign_of_neel_skyrmion():
+    """With D > 0 and interfacial DMI the Neel helicity 0 lowers the energy and helicity pi raises it."""
+    n, dx = 64, 0.2
+    for gam, sign in ((0.0, -1.0), (math.pi, 1.0)):
+        f = O.ansatz(CM, [[0.0, 0.0, 1.0, 2.0, gam]], n, n, dx, dx)
+        e_d = O.energy(CM, (1.0, 1.0, 0.1, 0.6, 0.0), f, dx, dx) - O.energy(CM, (1.0, 0.0, 0.1, 0.6, 0.0), f, dx, dx)
+        assert sign * e_d > 0.5
+
+
+def test_vacua_have_zero_energy_and_force():
+    n, dx, dy = 16, 0.3, 0.2
+    ah = np.zeros((4, n, n))
+    ah[0] = math.cos(0.7)
+    ah[1] = math.sin(0.7)
+    assert abs(O.energy(AH, AH_PRM, ah, dx, dy)) < 1e-28  # |psi|^2 = 1 up to rounding
+    assert np.abs(O.force(AH, AH_PRM, ah, dx, dy)).max() < 1e-13
+    cm = np.zeros((3, n, n))
+    cm[2] = 1.0
+    assert O.energy(CM, CM_PRM, cm, dx, dy) == 0.0
+    assert np.abs(O.force(CM, CM_PRM, cm, dx, dy)).max() == 0.0
+
+
+def test_uniform_fields_closed_form():
+    """Uniform fields: only the potential survives; E_h = area(I) * potential."""
+    nx, ny, dx, dy = 14, 10, 0.3, 0.2
+    area = (nx - 4) * (ny - 4) * dx * dy
+    ah = np.zeros((4, ny, nx))
+    ah[0] = 0.6
+    ah[2] = 0.4  # a constant A is a pure gauge field: no energy of its own, but |D psi|^2 = A^2 |psi|^2
+    lam, u = 1.3, 1.1
+    exp = area * (0.5 * 0.4**2 * 0.36 + lam / 8 * (u * u - 0.36) ** 2)
+    assert O.energy(AH, (lam, u), ah, dx, dy) == pytest.approx(exp, rel=1e-13)
+    cm = np.zeros((3, ny, nx))
+    cm[2] = -1.0
+    K, h = 0.1, 0.6
+    assert O.energy(CM, (1.0, 1.0, K, h, 0.0), cm, dx, dy) == pytest.approx(area * 2 * h, rel=1e-13)
+
+
+def _rot90_scalar(a):
+    # (x, y) -> (-y, x) about the array centre: new[j, i] = old[n-1-i, j]
+    return a[::-1, :].T.copy()
+
+
+def test_exact_90_degree_symmetry_ah():
+    """Rotating space and A by 90 degrees maps the lattice onto itself: E_h is invariant
+    and G is equivariant to rounding (Table 1's functional is rotation invariant)."""
+    n, dx = 24, 0.25
+    f = I.smooth_field(AH, n, n, dx, dx, seed=11)
+    g = np.stack([_rot90_scalar(f[0]), _rot90_scalar(f[1]), -_rot90_scalar(f[3]), _rot90_scalar(f[2])])
+    assert O.energy(AH, AH_PRM, g, dx, dx) == pytest.approx(O.energy(AH, AH_PRM, f, dx, dx), rel=1e-13)
+    Gf, Gg = O.force(AH, AH_PRM, f, dx, dx), O.force(AH, AH_PRM, g, dx, dx)
+    Grot = np.stack([_rot90_scalar(Gf[0]), _rot90_scalar(Gf[1]), -_rot90_scalar(Gf[3]), _rot90_scalar(Gf[2])])
+    np.testing.assert_allclose(Gg, Grot, rtol=0, atol=1e-11 * np.abs(Gf).max())
+
+
+def test_exact_90_degree_symmetry_cm_interfacial():
+    """Interfacial DMI is invariant under a joint rotation of space and spin about e_3."""
+    n, dx = 24, 0.25
+    f = I.smooth_field(CM, n, n, dx, dx, seed=12)
+    g = np.stack([-_rot90_scalar(f[1]), _rot90_scalar(f[0]), _rot90_scalar(f[2])])
+    assert O.energy(CM, CM_PRM, g, dx, dx) == pytest.approx(O.energy(CM, CM_PRM, f, dx, dx), rel=1e-13)
+    Gf, Gg = O.force(CM, CM_PRM, f, dx, dx), O.force(CM, CM_PRM, g, dx, dx)
+    Grot = np.stack([-_rot90_scalar(Gf[1]), _rot90_scalar(Gf[0]), _rot90_scalar(Gf[2])])
+    np.testing.assert_allclose(Gg, Grot, rtol=0, atol=1e-11 * np.abs(Gf).max())
+
+
+def test_gauge_invariance_fourth_order():
+    """psi -> psi e^{i chi}, A -> A + grad chi leaves Table 1's functional invariant; on
+    the lattice E_h changes at O(h^4) and G_psi rotates with psi while G_A is unchanged."""
+    errs_e, errs_g = [], []
+    for n in (41, 81):
+        L = 8.0
+        dx = L / (n - 1)
+        dy = 0.9 * dx
+        X, Y = grid(n, n, dx, dy)
+        f = I.smooth_field(AH, n, n, dx, dy, seed=5)
+        chi = 0.8 * np.sin(0.6 * X + 0.3) * np.cos(0.5 * Y) + 0.1 * X * Y
+        cx = 0.48 * np.cos(0.6 * X + 0.3) * np.cos(0.5 * Y) + 0.1 * Y
+        cy = -0.4 * np.sin(0.6 * X + 0.3) * np.sin(0.5 * Y) + 0.1 * X
+        c, s = np.cos(chi), np.sin(chi)
+        g = np.stack([c * f[0] - s * f[1], s * f[0] + c * f[1], f[2] + cx, f[3] + cy])
+        errs_e.append(abs(O.energy(AH, AH_PRM, g, dx, dy) - O.energy(AH, AH_PRM, f, dx, dy)))
+        Gf, Gg = O.force(AH, AH_PRM, f, dx, dy), O.force(AH, AH_PRM, g, dx, dy)
+        rot = np.stack([c * Gf[0] - s * Gf[1], s * Gf[0] + c * Gf[1], Gf[2], Gf[3]])
+        errs_g.append(np.abs(Gg - rot)[:, 2:-2, 2:-2].max())
+    assert errs_e[0] / errs_e[1] > 12.0 and errs_e[1] < 2e-4
+    assert errs_g[0] / errs_g[1] > 12.0 and errs_g[1] < 1e-2
+
+
+# ---------------------------------------------------------------- force (Eq. 3's right-hand side)
+@pytest.mark.parametrize("theory", [AH, CM])
+def test_exact_gradient_matches_brute_force(theory):
+    nx, ny, dx, dy = 12, 11, 0.3, 0.25
+    prm = AH_PRM if theory == AH else (1.0, 0.8, 0.15, 0.5, 0.0)
+    f = I.smooth_field(theory, nx, ny, dx, dy, seed=21, amplitude=0.5)
+    grad = O.energy_grad_exact(theory, prm, f, dx, dy)
+    eps = 1e-6
+    fd = np.zeros_like(f)
+    for idx in np.ndindex(f.shape):
+        fp, fm = f.copy(), f.copy()
+        fp[idx] += eps
+        fm[idx] -= eps
+        fd[idx] = (O.energy(theory, prm, fp, dx, dy) - O.energy(theory, prm, fm, dx, dy)) / (2 * eps)
+    np.testing.assert_allclose(grad, fd, rtol=0, atol=1e-7 * np.abs(grad).max())
+
+
+@pytest.mark.parametrize("theory", [AH, CM])
+def test_force_is_energy_gradient_to_fourth_order(theory):
+    """dx dy G and dE_h/dphi (tangent part for the chiral magnet) are two O(h^4)
+    discretisations of the same Euler-Lagrange expression: their gap shrinks ~16x per halving."""
+    prm = AH_PRM if theory == AH else (1.0, 0.8, 0.15, 0.5, 0.0)
+    errs = []
+    for n in (41, 81):
+        L = 8.0
+        dx = L / (n - 1)
+        dy = 0.9 * dx
+        f = I.smooth_field(theory, n, n, dx, dy, seed=7)
+        G = O.force(theory, prm, f, dx, dy)
+        gr = O.energy_grad_exact(theory, prm, f, dx, dy) / (dx * dy)
+        if theory == CM:
+            gr = gr - (gr * f).sum(axis=0, keepdims=True) * f
+        k = 4 if n == 41 else 8  # same physical margin on both grids
+        errs.append(np.abs(G - gr)[:, k:-k, k:-k].max() / np.abs(G).max())
+    assert errs[0] / errs[1] > 12.0, errs
+    assert errs[1] < 5e-3
+
+
+# ---------------------------------------------------------------- time integrator (Eq. 3, Eq. 4)
+def _rk4_matrix(omega2, dt):
+    """Classic RK4 on y' = M y is the degree-4 Taylor polynomial of exp(dt M)."""
+    M = np.array([[0.0, 1.0], [-omega2, 0.0]])
+    Z = dt * M
+    return np.eye(2) + Z + Z @ Z / 2 + Z @ Z @ Z / 6 + Z @ Z @ Z @ Z / 24
+
+
+def test_rk4_and_arrest_on_harmonic_oscillator():
+    """Harmonic test field (e = k phi^2 / 2 on the single interior site of a 5x5 grid):
+    every step must equal the closed-form RK4 propagator, and the velocity must be
+    zeroed exactly on the steps where the energy rises (Eq. 4)."""
+    k, dt = 4.0, 0.3
+    T = _rk4_matrix(k, dt)
+    f = np.zeros((1, 5, 5))
+    v = np.zeros((1, 5, 5))
+    f[0, 2, 2] = 1.0
+    E = 0.5 * k
+    y = np.array([1.0, 0.0])
+    Eref = 0.5 * k
+    n_arrest = 0
+    for _ in range(120):
+        f, v, E, arrested = O.anf_step(HARM, (k,), f, v, 1.0, 1.0, dt, E)
+        y = T @ y
+        Enew = 0.5 * k * y[0] ** 2
+        exp_arrest = Enew > Eref
+        if exp_arrest:
+            y[1] = 0.0
+        Eref = Enew
+        assert arrested == exp_arrest
+        n_arrest += arrested
+        assert f[0, 2, 2] == pytest.approx(y[0], abs=1e-13)
+        assert v[0, 2, 2] == pytest.approx(y[1], abs=1e-13)
+        assert E == pytest.approx(Enew, abs=1e-13)
+        # halo untouched
+        assert np.count_nonzero(f) <= 1 and np.count_nonzero(v) <= 1
+    assert n_arrest >= 1
+    assert abs(f[0, 2, 2]) < 1e-2  # arrested flow has relaxed the oscillator
+
+
+def test_minimise_stops_at_tolerance():
+    k, dt = 4.0, 0.3
+    f = np.zeros((1, 5, 5))
+    f[0, 2, 2] = 1.0
+    r = O.minimise(HARM, (k,), f, 1.0, 1.0, tol=1e-9, max_steps=10_000, dt=dt)
+    assert r["converged"] and abs(k * r["f"][0, 2, 2]) < 1e-9
+    r2 = O.minimise(HARM, (k,), f, 1.0, 1.0, tol=1e-9, max_steps=3, dt=dt)
+    assert not r2["converged"] and r2["steps"] == 3
+
+
+def test_cm_flow_keeps_unit_length():
+    p = I.cm_skyrmions(n=96, count=2, seed=3, min_sep=8.0, margin=4.0)
+    f = O.ansatz(CM, p.soliton_array(), p.nx, p.ny, p.dx, p.dy)
+    v = np.zeros_like(f)
+    E = O.energy(CM, p.params, f, p.dx, p.dy)
+    dt = O.time_step(p.dx, p.dy)
+    for _ in range(20):
+        f, v, E, _ = O.anf_step(CM, p.params, f, v, p.dx, p.dy, dt, E)
+    assert np.abs(np.sqrt((f * f).sum(axis=0)) - 1.0).max() < 1e-14
+    assert np.abs((f * v).sum(axis=0)).max() < 1e-14  # velocity stays tangent
+    assert O.observables(CM, p.params, f, p.dx, p.dy)["charge"] == pytest.approx(-2.0, abs=1e-10)
+
+
+# ---------------------------------------------------------------- observables and physics
+def test_berg_luescher_charge_is_exact_integer():
+    n, dx = 96, 0.2
+    sol = [[-5.0, -4.0, 1.0, 2.0, 0.0], [4.0, 3.0, 1.0, 2.5, 1.0], [-3.0, 5.0, -1.0, 2.0, 0.0]]
+    f = O.ansatz(CM, sol, n, n, dx, dx)
+    assert O.observables(CM, CM_PRM, f, dx, dx)["charge"] == pytest.approx(-1.0 - 1.0 + 1.0, abs=1e-12)
+    f1 = O.ansatz(CM, sol[:1], n, n, dx, dx)
+    assert O.observables(CM, CM_PRM, f1, dx, dx)["charge"] == pytest.approx(-1.0, abs=1e-12)
+
+
+def test_ah_winding_and_flux_of_ansatz():
+    n, dx = 128, 0.125
+    g = golden()["flux_per_unit_winding"]["value_over_pi"]
+    for sol in ([[0.0, 0.0, 1.0, 1.0, 0.0]],
+                [[-1.0, 0.5, 1.0, 1.0, 0.0], [1.2, -0.7, 1.0, 1.0, 0.3]],
+                [[-1.0, 0.0, 1.0, 1.0, 0.0], [1.0, 1.0, 1.0, 1.0, 0.0], [0.2, -1.3, 1.0, 1.0, 0.0]]):
+        N = len(sol)
+        o = O.observables(AH, AH_PRM, O.ansatz(AH, sol, n, n, dx, dx), dx, dx)
+        assert o["charge"] == pytest.approx(N, abs=1e-12)
+        assert o["flux"] == pytest.approx(g * math.pi * N, rel=2e-3)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("N", [1, 2])
+def test_ah_relaxes_to_bogomolny_bound(N):
+    """At lambda = 1 the relaxed N-vortex energy sits at pi N (Bogomolny bound of Table 1's
+    functional), the flux at 2 pi N and the winding at N."""
+    g = golden()
+    n, dx = 64, 0.2
+    f = O.ansatz(AH, [[0.0, 0.0, float(N), 1.0, 0.0]], n, n, dx, dx)
+    r = O.minimise(AH, AH_PRM, f, dx, dx, tol=1e-6, max_steps=5000)
+    assert r["converged"]
+    o = O.observables(AH, AH_PRM, r["f"], dx, dx)
+    bound = g["bogomolny_energy_per_unit_winding"]["value_over_pi"] * math.pi * N
+    assert abs(o["energy"] - bound) < 3e-4 * bound  # lattice error at dx = 0.2
+    assert o["flux"] == pytest.approx(g["flux_per_unit_winding"]["value_over_pi"] * math.pi * N, rel=5e-3)
+    assert o["charge"] == pytest.approx(N, abs=1e-12)
+
+
+@pytest.mark.slow
+def test_ah_energy_ordering_with_coupling():
+    """Away from critical coupling a single vortex lies below pi for lambda < 1 and above for lambda > 1."""
+    n, dx = 64, 0.2
+    f = O.ansatz(AH, [[0.0, 0.0, 1.0, 1.0, 0.0]], n, n, dx, dx)
+    e = {}
+    for lam in (0.5, 2.0):
+        r = O.minimise(AH, (lam, 1.0), f, dx, dx, tol=1e-6, max_steps=8000)
+        assert r["converged"]
+        e[lam] = r["energy"]
+    assert e[0.5] < math.pi - 0.05 < math.pi + 0.05 < e[2.0]
+
+
+# ---------------------------------------------------------------- input generator
+def test_splitmix64_reference_value():
+    # first output of SplitMix64 seeded with 0 (published reference sequence)
+    assert I.SplitMix64(0).next_u64() == 0xE220A8397B1DCDAF
+
+
+def test_workload_generators_are_deterministic_and_valid():
+    a = I.cm_skyrmions(n=1024, count=8)
+    b = I.cm_skyrmions(n=1024, count=8)
+    assert a.solitons == b.solitons
+    pts = np.array([(s[0], s[1]) for s in a.solitons])
+    d = np.hypot(pts[:, None, 0] - pts[None, :, 0], pts[:, None, 1] - pts[None, :, 1])
+    assert (d[np.triu_indices(8, 1)] >= 8.0).all()
+    half = 0.5 * 1023 * 0.2
+    assert (np.abs(pts) <= half - 8.0).all()
+    batch = I.ah_batch()
+    assert len(batch) == 256
+    assert {p.nx for p in batch} == {64, 128, 256, 512}
+    for p in batch:
+        L = p.nx * p.dx
+        assert 0.5 <= p.params[0] < 2.0 and 1 <= len(p.solitons) <= 4
+        assert all(abs(s[0]) <= L / 4 and abs(s[1]) <= L / 4 for s in p.solitons)
