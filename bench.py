@@ -1,0 +1,321 @@
+"""Throughput of the arrested-Newton-flow hot path on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+Workload: chiral magnet (J = D = 1, h = 0.6, K = 0.1, interfacial DMI) on a
+4096 x 4096 grid (dx = 0.2, halo included), FP32 fields with FP64 reductions,
+400 compact skyrmions at seeded positions (minimum separation 8). Its arrays
+(7 x 201 MB) are far larger than the 129 MB L2, so every timed step streams HBM.
+
+One bench step = one call ss_step(ctx, 32): 32 flow steps (each four RK stage
+kernels; stage 1 fuses the energy / residual reductions and the arrest decision),
+enqueued as one CUDA graph. value = interior site-updates per second.
+e2e: the same calls with the field copied in from pinned host memory and out
+again every bench step (ss_set_fields / ss_step / ss_get_fields on host buffers).
+--impl reference: the FP64 CPU oracle on the host cores, same metric, each step one
+oracle flow step on a 512 x 512 crop of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2603_24370_gb300 import dist as D  # noqa: E402  (no CUDA import)
+
+INNER = 32          # flow steps per bench step (one captured graph)
+N = 4096
+DX = 0.2
+COUNT = 400
+SEED = 20264
+CROP = 512          # oracle sample (CPU baseline / reference arm)
+C = 3
+WORKLOAD = ("chiral magnet 4096x4096 (halo incl.), dx=0.2, J=D=1, h=0.6, K=0.1, interfacial DMI, "
+            "400 skyrmions min-sep 8, FP32 fields + FP64 reductions, ANF-RK4 (4 stage kernels/step)")
+
+
+def interior(n: int) -> int:
+    return (n - 4) * (n - 4)
+
+
+# algorithmic bytes per interior site of each RK stage kernel (FP32, C components):
+# stage 1 reads phi, writes k_v1; 2 reads phi, v, writes k_v2; 3 reads phi, v, k_v1,
+# writes k_v3; 4 reads phi, v, k_v1..3, writes phi', v'.
+STAGE_BYTES = {1: 4 * 2 * C, 2: 4 * 3 * C, 3: 4 * 4 * C, 4: 4 * 7 * C}
+
+
+def measured_peaks() -> tuple[dict, str]:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for fn in ("ss_flow.cu", "ss_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2603_24370_gb300", "csrc", fn), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "stage_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        d = json.load(fh)
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    return d.get("bytes_per_launch", {}).get(kernel)
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: str):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+        self.t0 = self.t1 = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.index, f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        self.t0 = time.time()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def stop(self) -> dict:
+        self.t1 = time.time()
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ts, line in self.lines:
+            if ts < self.t0 or ts > self.t1 + 0.1:
+                continue
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_sample(steps_budget_s: float = 12.0, max_steps: int = 40, min_steps: int = 3):
+    """Oracle (FP64, as it stands) flow steps on a 512^2 crop of the workload."""
+    import numpy as np
+    import oracle as O
+    from paper_2603_24370_gb300 import inputs as I
+    p = I.cm_skyrmions(n=N, count=COUNT, seed=SEED)
+    # crop: the workload's skyrmions that fall in the central 512^2 window
+    sol = [s for s in p.solitons if abs(s[0]) < 0.5 * CROP * DX - 4 and abs(s[1]) < 0.5 * CROP * DX - 4]
+    f = O.ansatz(O.CHIRAL_MAGNET, sol if sol else [(0.0, 0.0, 1.0, 2.0, 0.0)], CROP, CROP, DX, DX)
+    v = np.zeros_like(f)
+    E = O.energy(O.CHIRAL_MAGNET, p.params, f, DX, DX)
+    dt = O.time_step(DX, DX)
+    t0 = time.perf_counter()
+    n = 0
+    while n < min_steps or (time.perf_counter() - t0 < steps_budget_s and n < max_steps):
+        f, v, E, _ = O.anf_step(O.CHIRAL_MAGNET, p.params, f, v, DX, DX, dt, E)
+        n += 1
+    dt_s = time.perf_counter() - t0
+    return {"value": interior(CROP) * n / dt_s, "unit": "site-updates/s", "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"{n} oracle FP64 flow steps on a {CROP}x{CROP} crop of the workload ({len(sol)} skyrmions), "
+                      f"{dt_s:.1f} s"}
+
+
+def run_reference(args) -> int:
+    rank, _, world = D.env_rank()
+    if rank != 0:
+        return 0
+    import numpy as np
+    import oracle as O
+    from paper_2603_24370_gb300 import inputs as I
+    O.build()
+    p = I.cm_skyrmions(n=N, count=COUNT, seed=SEED)
+    sol = [s for s in p.solitons if abs(s[0]) < 0.5 * CROP * DX - 4 and abs(s[1]) < 0.5 * CROP * DX - 4]
+    f = O.ansatz(O.CHIRAL_MAGNET, sol if sol else [(0.0, 0.0, 1.0, 2.0, 0.0)], CROP, CROP, DX, DX)
+    v = np.zeros_like(f)
+    E = O.energy(O.CHIRAL_MAGNET, p.params, f, DX, DX)
+    dt = O.time_step(DX, DX)
+    for _ in range(args.warmup):
+        f, v, E, _ = O.anf_step(O.CHIRAL_MAGNET, p.params, f, v, DX, DX, dt, E)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f, v, E, _ = O.anf_step(O.CHIRAL_MAGNET, p.params, f, v, DX, DX, dt, E)
+    sec = time.perf_counter() - t0
+    value = interior(CROP) * args.steps / sec
+    line = {
+        "impl": "reference", "metric": "site-updates/s", "value": value, "unit": "site-updates/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "reference_sample": f"one oracle flow step per bench step on a {CROP}x{CROP} crop"},
+        "cpu_baseline": {"value": value, "unit": "site-updates/s", "cores": O.num_threads(), "kind": "oracle",
+                         "sample": f"{args.steps} oracle FP64 flow steps on a {CROP}x{CROP} crop"},
+        "e2e": {"value": value, "unit": "site-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_native(args) -> int:
+    rank, local_rank, world = D.env_rank()
+    D.pin_visible_device(local_rank, world)
+    import numpy as np
+    import torch
+    import torch.distributed as tdist
+
+    if world > 1:
+        torch.cuda.set_device(0)
+        tdist.init_process_group("nccl")
+    from paper_2603_24370_gb300 import build as B
+    from paper_2603_24370_gb300 import inputs as I
+    from paper_2603_24370_gb300 import soliton as S
+    B.build()
+    S.load_library()
+
+    p = I.cm_skyrmions(n=N, count=COUNT, seed=SEED)
+    stream = torch.cuda.Stream()
+    s = S.Solver(S.SS_CHIRAL_MAGNET, p.params, N, N, DX, DX, S.SS_FP32, stream=stream)
+    s.init_ansatz(p.soliton_array())
+    f_init = s.fields()
+    launches_per_call = 2 + ((INNER + 31) // 32) * 32 * 4  # set_run + head + graph chunk(s)
+
+    for _ in range(args.warmup):
+        s.step(INNER)
+
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    smi_index = vis.split(",")[0].strip() if vis and vis.split(",")[0].strip().isdigit() else str(local_rank)
+    clocks = ClockSampler(smi_index)
+    clocks.start()
+    D.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        st = s.step(INNER)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    D.barrier()
+    clk = clocks.stop()
+    sec = ev0.elapsed_time(ev1) / 1e3
+    units, job_sec = D.aggregate(interior(N) * INNER * args.steps, sec)
+    value = units / job_sec
+
+    # per-kernel durations (CUDA events around each stage launch on the context stream)
+    stage_ms = S.ss_profile_stages(s.ctx, 8)
+    dominant = max(range(4), key=lambda i: stage_ms[i] * 1.0) + 1
+    peaks, src = measured_peaks()
+    kname = f"k_stage<CM, float, {dominant}>"
+    alg = STAGE_BYTES[dominant] * interior(N)
+    achieved = alg / (stage_ms[dominant - 1] * 1e-3) / 1e9
+    traffic = ncu_traffic(f"stage{dominant}")
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "kernel": kname,
+                "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else "fallback 6.8 TB/s",
+                "algorithmic_bytes_per_launch": alg,
+                "stage_ms": stage_ms,
+                "step_bytes_per_site_update": sum(STAGE_BYTES.values()),
+                "step_frac": (sum(STAGE_BYTES.values()) * interior(N) / (sum(stage_ms) * 1e-3) / 1e9) / peaks["hbm_gbs"]}
+
+    # end to end through the C-ABI with host buffers: field in from pinned memory,
+    # 32 flow steps, field out to pinned memory, every bench step
+    host_in = torch.from_numpy(np.ascontiguousarray(f_init)).pin_memory()
+    host_out = torch.empty(host_in.shape, dtype=torch.float32).pin_memory()
+    e2e_steps = max(3, args.steps // 4)
+    s.set_fields(host_in)
+    s.step(INNER)
+    D.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        s.set_fields(host_in)
+        s.step(INNER)
+        S.ss_get_fields(s.ctx, host_out)
+    torch.cuda.synchronize()
+    e2e_sec = time.perf_counter() - t0
+    e_units, e_sec = D.aggregate(interior(N) * INNER * e2e_steps, e2e_sec)
+    nbytes = C * N * N * 4
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_sample()
+
+    s.close()
+    if rank == 0:
+        line = {
+            "metric": "site-updates/s", "value": value, "unit": "site-updates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * job_sec / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "flow_steps_per_bench_step": INNER, "grid": [N, N],
+                       "interior_sites": interior(N), "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "working set 1.4 GB >> 129 MB L2 (no flush needed)"},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e_units / e_sec, "unit": "site-updates/s", "h2d_bytes_per_step": nbytes,
+                    "d2h_bytes_per_step": nbytes},
+            "gpu_launches": launches_per_call * args.steps,
+            "clocks": clk,
+            "final_energy": st["energy"], "final_grad_max": st["grad_max"],
+        }
+        print(json.dumps(line))
+    if world > 1:
+        tdist.destroy_process_group()
+    return 0
+
+
+def main() -> int:
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("native", "reference"), default="native")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_native(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,182 @@
+/*
+ * soliton.h -- C-ABI of the GB300 (sm_103a) soliton relaxation library.
+ *
+ * The library relaxes topological solitons of 2D field theories by arrested
+ * Newton flow (arxiv 2603.24370, Sec. 3): 4th-order finite-difference stencils
+ * with a halo of width two (Sec. 3.1, Eq. 1 and Eq. 2), the flow
+ * phi'' = -grad E_h integrated by classic RK4 from rest (Sec. 3.2, Eq. 3), and the
+ * arrest v <- 0 whenever E_h rises (Sec. 3.2, Eq. 4), with the unit-length
+ * projection of magnetisation models in every RK stage (Sec. 3.2) and GPU-resident
+ * reductions of the energy and convergence norm (Sec. 3.3). Theories: Abelian
+ * Higgs (Table 1) and the chiral magnet without demagnetisation (Sec. 4.2, Eq. 5).
+ *
+ * Conventions shared by every call:
+ *  - Every call returns SS_OK (0) or a negative SS_ERR_* code; ss_last_error()
+ *    returns a message for the calling thread's last failure.
+ *  - A grid is nx x ny sites INCLUDING the width-2 halo. The halo keeps the values
+ *    it was given (ss_init_ansatz / ss_set_fields) for ever; interior sites
+ *    [2, nx-3] x [2, ny-3] are updated. Site (i, j) sits at
+ *    x = (i - (nx-1)/2) dx, y = (j - (ny-1)/2) dy.
+ *  - Field arrays are component planes [C][ny][nx], x fastest, in the context's
+ *    precision (float for SS_FP32, double for SS_FP64). C = 4 for the Abelian
+ *    Higgs model (Re psi, Im psi, A_1, A_2), C = 3 for the chiral magnet
+ *    (n_1, n_2, n_3).
+ *  - Pointers passed in are borrowed for the duration of the call only; the
+ *    library copies what it keeps. "is_device" = 1 means a device pointer of the
+ *    current CUDA device, 0 a host pointer (pinned host memory gives the fastest
+ *    copies). The library owns every device buffer it allocates and frees them in
+ *    ss_destroy.
+ *  - All GPU work of a context runs on the stream given to ss_create_grid; with
+ *    NULL the context creates its own blocking stream (ordered with the legacy
+ *    default stream; CUDA graphs cannot be captured on the legacy stream itself).
+ *    Calls return after their GPU work has completed.
+ *  - The library is built for sm_103a only; it has no CPU fallback.
+ */
+#ifndef SOLITON_H
+#define SOLITON_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define SS_OK 0
+#define SS_ERR_ARG (-1)           /* invalid argument (sizes, spacings, theory, params) */
+#define SS_ERR_STATE (-2)         /* call out of order (e.g. step before theory/fields) */
+#define SS_ERR_CUDA (-3)          /* a CUDA runtime call failed; see ss_last_error()   */
+#define SS_ERR_TIMEOUT (-4)       /* a bounded device-side wait ran out               */
+#define SS_ERR_NONFINITE (-5)     /* energy or force became NaN/Inf; the flow stopped  */
+#define SS_ERR_NOT_CONVERGED (-6) /* ss_minimise hit max_steps before the tolerance    */
+#define SS_ERR_NOMEM (-7)         /* device or host allocation failed                 */
+
+/* ---- precisions ---- */
+#define SS_FP32 1 /* FP32 fields and stencils, FP64 compensated reductions */
+#define SS_FP64 2 /* all-FP64 reference form                              */
+
+/* ---- theories ---- */
+#define SS_ABELIAN_HIGGS 1 /* Table 1, params {lambda, u}                                */
+#define SS_CHIRAL_MAGNET 2 /* Eq. 5 without demag, params {J, D, K, h, dmi_type}:       */
+                           /* dmi_type 0 interfacial (d_i = e_3 x e_i), 1 bulk (d_i = e_i),*/
+                           /* 2 D_2d "Heusler" (d_1 = e_1, d_2 = -e_2)                     */
+
+typedef struct ss_ctx ss_ctx;
+
+/* One soliton of an initial configuration (Sec. 3.4 "model-specific ansatz"; the
+ * paper gives no formula, the standard forms are used):
+ *  Abelian Higgs: psi = prod_k tanh(r_k/size_k)^|charge_k| exp(i (charge_k theta_k + phase_k)),
+ *                 A = sum_k charge_k tanh(r_k/size_k)^2 (-(y-y_k), x-x_k) / r_k^2.
+ *  Chiral magnet: compact skyrmion of radius R = size, vorticity m = charge,
+ *                 helicity gamma = phase: n = (sin f cos(m theta + gamma),
+ *                 sin f sin(m theta + gamma), cos f), f = pi (1 - r/R) for r < R,
+ *                 n = e_3 outside every disc; the first disc containing a site wins.
+ *                 Its lattice charge is -m. */
+typedef struct {
+  double x, y;
+  int charge;
+  double size, phase;
+} ss_soliton;
+
+/* Flow status after ss_step / ss_minimise. */
+typedef struct {
+  double energy;      /* E_h of the current field (FP64 accumulation)                  */
+  double grad_max;    /* dx dy max_I |G| of the current field: the convergence measure */
+  long long steps;    /* steps taken since the fields were last set                    */
+  long long arrests;  /* arrests (Eq. 4) since the fields were last set                */
+  int converged;      /* grad_max < tol (ss_minimise only)                             */
+  int arrested;       /* the current velocity is zeroed by a pending arrest            */
+} ss_status;
+
+/* Observables of the current field, evaluated in FP64 arithmetic. */
+typedef struct {
+  double energy;       /* E_h = dx dy sum_I e                                           */
+  double charge;       /* chiral magnet: Berg-Luescher lattice charge; Abelian Higgs:   */
+                       /* winding of arg psi around the boundary of I                   */
+  double flux;         /* Abelian Higgs: dx dy sum_I (d_1 A_2 - d_2 A_1); else 0        */
+  double grad_max;     /* dx dy max_I |G|                                               */
+  double grad_max_raw; /* max_I |G|                                                     */
+  double norm_dev;     /* chiral magnet: max over sites of ||n| - 1|; else 0            */
+  long long steps;     /* steps taken since the fields were last set                    */
+} ss_obs;
+
+/* Message for the calling thread's last failed call ("" if none). Owned by the
+ * library; valid until the thread's next failing call. */
+const char* ss_last_error(void);
+
+/* Library ABI version (increments on incompatible changes). */
+int ss_version(void);
+
+/* Create a context for an nx x ny grid (halo included; nx, ny >= 5) with spacings
+ * dx, dy > 0 (Sec. 3.1 lattice). precision: SS_FP32 or SS_FP64. cuda_stream: a
+ * cudaStream_t borrowed for the context's lifetime, or NULL (see above). The
+ * context uses the calling thread's current CUDA device. The time step is
+ * dt = 0.5 min(dx, dy) (Sec. 3.1, Courant number C = 0.5). Device buffers are
+ * allocated by ss_set_theory. Errors: SS_ERR_ARG, SS_ERR_CUDA, SS_ERR_NOMEM. */
+int ss_create_grid(ss_ctx** out, int nx, int ny, double dx, double dy, int precision, void* cuda_stream);
+
+/* Select the theory and its couplings (Sec. 3.1 "theory-specific parameters packed
+ * into device arrays"; Table 1; Eq. 5). params is a host array of n_params
+ * doubles: Abelian Higgs {lambda, u} (u defaults to 1 if n_params == 1); chiral
+ * magnet {J, D, K, h, dmi_type} (dmi_type defaults to 0 if n_params == 4).
+ * Allocates the device buffers; previous fields are discarded.
+ * Errors: SS_ERR_ARG (unknown theory, bad n_params, J <= 0), SS_ERR_NOMEM, SS_ERR_CUDA. */
+int ss_set_theory(ss_ctx* ctx, int theory, const double* params, int n_params);
+
+/* Set the fields to the ansatz of n >= 1 solitons (host array, copied), evaluated
+ * in FP64 on the device and rounded to the context precision; the halo receives the
+ * same formula and is then frozen. Velocity v = 0 (flow from rest, Sec. 3.2).
+ * Errors: SS_ERR_STATE (no theory), SS_ERR_ARG (n < 1, size <= 0), SS_ERR_CUDA. */
+int ss_init_ansatz(ss_ctx* ctx, const ss_soliton* solitons, int n);
+
+/* Copy a caller field array [C][ny][nx] (context precision) into the context,
+ * halo included, and restart the flow from rest (v = 0, no pending arrest): the
+ * resume step of a checkpoint. Errors: SS_ERR_STATE, SS_ERR_ARG (NULL), SS_ERR_CUDA. */
+int ss_set_fields(ss_ctx* ctx, const void* fields, int is_device);
+
+/* Copy the current field [C][ny][nx] (context precision) out to the caller.
+ * Errors: SS_ERR_STATE, SS_ERR_ARG, SS_ERR_CUDA. */
+int ss_get_fields(ss_ctx* ctx, void* fields, int is_device);
+
+/* Copy the current velocity phi-dot [C][ny][nx] out, with a pending arrest (Eq. 4)
+ * applied (zeros if the last step raised the energy). Errors as ss_get_fields. */
+int ss_get_velocity(ss_ctx* ctx, void* velocity, int is_device);
+
+/* Euler-Lagrange force G of the current field (the right-hand side of Eq. 3 up to
+ * sign; chiral magnet tangent-projected), [C][ny][nx], zero on the halo, in the
+ * context precision. Optionally returns E_h and dx dy max|G| (may be NULL).
+ * Errors: SS_ERR_STATE, SS_ERR_ARG, SS_ERR_CUDA. */
+int ss_force(ss_ctx* ctx, void* force, int is_device, double* energy, double* grad_max);
+
+/* Take n_steps >= 0 arrested-Newton-flow RK4 steps (Sec. 3.2, Eq. 3, Eq. 4). The
+ * energy of each new field is reduced on the device and compared with the previous
+ * one there; the host is not involved between steps. out (may be NULL) receives
+ * the status of the resulting field. Errors: SS_ERR_STATE, SS_ERR_ARG,
+ * SS_ERR_NONFINITE (flow stopped at the first non-finite energy/force), SS_ERR_CUDA. */
+int ss_step(ss_ctx* ctx, int n_steps, ss_status* out);
+
+/* Run the flow until dx dy max_I |G| < tol (checked before every step) or
+ * max_steps steps have been taken in this call. Steps run in CUDA-graph chunks;
+ * the host polls one small status record per chunk. Returns SS_OK if converged,
+ * SS_ERR_NOT_CONVERGED if max_steps was reached, SS_ERR_NONFINITE, or another error.
+ * out (may be NULL) receives the final status in every case. */
+int ss_minimise(ss_ctx* ctx, double tol, long long max_steps, ss_status* out);
+
+/* Observables of the current field (Sec. 2: "GPU-resident evaluation of
+ * observables"; Sec. 3.3 reductions), in FP64 arithmetic with compensated sums.
+ * Errors: SS_ERR_STATE, SS_ERR_ARG (NULL), SS_ERR_CUDA. */
+int ss_observables(ss_ctx* ctx, ss_obs* out);
+
+/* Tracing: take n_steps (1..4096) flow steps exactly as ss_step does, but with
+ * direct launches bracketed by CUDA events on the context stream, and return in
+ * ms_out[0..3] the mean device duration in milliseconds of RK stage kernels 1..4
+ * (stage 1 includes the energy/residual reduction and the arrest decision of
+ * Eq. 4). The steps advance the flow. Errors: SS_ERR_STATE, SS_ERR_ARG, SS_ERR_CUDA,
+ * SS_ERR_NONFINITE. */
+int ss_profile_stages(ss_ctx* ctx, int n_steps, float* ms_out);
+
+/* Release every device and host resource of the context (NULL is a no-op). */
+int ss_destroy(ss_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SOLITON_H */

@@ -21,6 +21,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import platform
 import subprocess
 import threading
 
@@ -33,6 +34,7 @@ HARMONIC_TEST = 99
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "soliton_oracle.cpp")
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_STAMP = _LIB_PATH + ".arch"
 _lock = threading.Lock()
 _lib = None
 
@@ -41,7 +43,9 @@ _D = ctypes.POINTER(ctypes.c_double)
 
 def build(force: bool = False) -> str:
     """Compile ``liboracle.so`` in-tree with g++ (OpenMP when available)."""
-    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
+    if (not force and os.path.exists(_LIB_PATH) and os.path.exists(_STAMP)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)
+            and open(_STAMP).read().strip() == platform.machine()):
         return _LIB_PATH
     base = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-shared", "-fPIC", _SRC, "-o", _LIB_PATH + ".tmp"]
     try:
@@ -49,6 +53,8 @@ def build(force: bool = False) -> str:
     except subprocess.CalledProcessError:
         subprocess.run(base, check=True)
     os.replace(_LIB_PATH + ".tmp", _LIB_PATH)
+    with open(_STAMP, "w") as fh:
+        fh.write(platform.machine())
     return _LIB_PATH
 
 
@@ -58,6 +64,8 @@ def _load():
         if _lib is None:
             lib = ctypes.CDLL(build())
             i, d, ll = ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+            lib.or_num_threads.argtypes = []
+            lib.or_num_threads.restype = i
             lib.or_ncomp.argtypes = [i]
             lib.or_ncomp.restype = i
             lib.or_time_step.argtypes = [d, d]
@@ -94,6 +102,11 @@ def _f64(a) -> np.ndarray:
 
 def _params(params) -> np.ndarray:
     return _f64(np.asarray(params, dtype=np.float64).reshape(-1))
+
+
+def num_threads() -> int:
+    """Threads used by the oracle's parallel loops."""
+    return _load().or_num_threads()
 
 
 def ncomp(theory: int) -> int:

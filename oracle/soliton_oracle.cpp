@@ -36,6 +36,9 @@
 //   * Convergence measure: max over I and components of |dx dy G|.
 #include <cmath>
 #include <cstdint>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <cstring>
 #include <vector>
 
@@ -333,6 +336,15 @@ void tangent(double* v, const double* n, const Grid& g) {
 extern "C" {
 
 int or_ncomp(int theory) { return ncomp(theory); }
+
+// Threads the oracle's parallel loops use (1 without OpenMP).
+int or_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
 
 // Sec. 3.1: dt = C * dx with the default Courant-like number C = 0.5; with
 // unequal spacings the smaller one is used.

@@ -1,0 +1,254 @@
+// ss_device.cuh -- device-side building blocks of the soliton relaxation kernels:
+// the flow's device status record, compensated FP64 reductions, the 4th-order
+// stencils and the Euler-Lagrange forces / energy densities of the two theories.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+namespace ss {
+
+// ------------------------------------------------------------------ tiling
+// A tile is TX x TY output sites; a block of BX x BY threads covers it with each
+// thread owning TY/BY sites of one column. The shared tile carries the width-2
+// halo of the 5-point stencils (Sec. 3.1).
+constexpr int TX = 32, TY = 16, BX = 32, BY = 8, NT = BX * BY;
+constexpr int HALO = 2;
+constexpr int SX = TX + 2 * HALO, SY = TY + 2 * HALO;
+constexpr int ROWS_PER_THREAD = TY / BY;
+
+enum { TH_AH = 1, TH_CM = 2 };
+
+template <int TH> struct NComp;
+template <> struct NComp<TH_AH> { static constexpr int C = 4; };
+template <> struct NComp<TH_CM> { static constexpr int C = 3; };
+
+// ------------------------------------------------------------------ flow state
+// One per context, in device memory. Written only by the single last-arriving
+// block of a reduction kernel (or by 1-thread control kernels), read by the
+// following launches in stream order.
+struct DevState {
+  double E_last;   // E_h of the previous head field (Eq. 4 compares against it)
+  double E_cur;    // E_h of the current head field
+  double gmax;     // dx dy max_I |G| of the current head field
+  double tol;      // convergence threshold on gmax (< 0 disables)
+  long long steps;       // steps taken since the fields were set
+  long long arrests;     // arrests since the fields were set
+  long long head_step;   // value of `steps` when stage 1 last evaluated the field (-1: never)
+  long long step_limit;  // stages 2-4 do nothing once steps >= step_limit
+  int arrest;      // 1: the current velocity counts as zero (pending arrest)
+  int converged;   // 1: gmax < tol; stage kernels become no-ops
+  int nonfinite;   // 1: E or G not finite; stage kernels become no-ops
+  int pad0;
+  unsigned int ticket;      // arrival counter of the flow reduction
+  unsigned int obs_ticket;  // arrival counter of the observables reduction
+  // observables (FP64 evaluation)
+  double obs_energy, obs_charge, obs_flux, obs_gmax_raw, obs_normdev;
+};
+
+struct FlowPartial {  // per-block part of the flow reduction (32 B)
+  double s, c, m, pad;
+};
+struct ObsPartial {  // per-block part of the observables reduction (64 B)
+  double es, ec, fs, fc, qs, qc, gm, nd;
+};
+
+// ------------------------------------------------------------------ compensated sums
+struct DD {
+  double s, c;
+};
+__device__ __forceinline__ void two_sum(double a, double b, double& s, double& e) {
+  s = a + b;
+  const double bp = s - a;
+  e = (a - (s - bp)) + (b - bp);
+}
+__device__ __forceinline__ DD dd_add(DD x, DD y) {
+  double s, e;
+  two_sum(x.s, y.s, s, e);
+  return DD{s, x.c + y.c + e};
+}
+// Neumaier's compensated addition of one term.
+__device__ __forceinline__ void neumaier(DD& a, double x) {
+  const double t = a.s + x;
+  if (fabs(a.s) >= fabs(x)) a.c += (a.s - t) + x; else a.c += (x - t) + a.s;
+  a.s = t;
+}
+__device__ __forceinline__ DD shfl_down_dd(DD v, int off) {
+  return DD{__shfl_down_sync(0xffffffffu, v.s, off), __shfl_down_sync(0xffffffffu, v.c, off)};
+}
+// Fixed-shape warp tree: lane 0 ends with the warp's value; the order never depends
+// on timing, so results are bitwise reproducible.
+__device__ __forceinline__ DD warp_sum(DD v) {
+  for (int off = 16; off > 0; off >>= 1) v = dd_add(v, shfl_down_dd(v, off));
+  return v;
+}
+// Maximum that propagates NaN (fmax would drop it and hide a blown-up force).
+__device__ __forceinline__ double nanmax(double a, double b) { return (b > a || b != b) ? b : a; }
+__device__ __forceinline__ double warp_max(double m) {
+  for (int off = 16; off > 0; off >>= 1) m = nanmax(m, __shfl_down_sync(0xffffffffu, m, off));
+  return m;
+}
+
+// Block reduction of K compensated sums and L maxima over NT threads; thread 0
+// returns the block result. sm must hold (NT/32) * (2K + L) doubles.
+template <int K, int L>
+__device__ __forceinline__ void block_reduce(DD (&s)[K], double (&m)[L], double* sm) {
+  constexpr int W = NT / 32;
+  const int lane = threadIdx.x & 31, wid = (threadIdx.y * BX + threadIdx.x) >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) s[k] = warp_sum(s[k]);
+#pragma unroll
+  for (int l = 0; l < L; ++l) m[l] = warp_max(m[l]);
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) { sm[(2 * k) * W + wid] = s[k].s; sm[(2 * k + 1) * W + wid] = s[k].c; }
+#pragma unroll
+    for (int l = 0; l < L; ++l) sm[(2 * K + l) * W + wid] = m[l];
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+      s[k] = lane < W ? DD{sm[(2 * k) * W + lane], sm[(2 * k + 1) * W + lane]} : DD{0.0, 0.0};
+#pragma unroll
+    for (int l = 0; l < L; ++l) m[l] = lane < W ? sm[(2 * K + l) * W + lane] : 0.0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) s[k] = warp_sum(s[k]);
+#pragma unroll
+    for (int l = 0; l < L; ++l) m[l] = warp_max(m[l]);
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------------------------ stencils
+// Spacing factors of Eq. 1 / Eq. 2, precomputed per context in the working type.
+template <typename R>
+struct Spacing {
+  R i12dx, i12dy;      // 1 / (12 dx), 1 / (12 dy)
+  R i12dx2, i12dy2;    // 1 / (12 dx^2), 1 / (12 dy^2)
+  R i144dxdy;          // 1 / (144 dx dy)
+};
+
+// Derivatives of one component at shared-tile position (sx, sy). Differences are
+// formed first so that FP32 keeps the small differences of neighbouring values.
+template <typename R>
+struct Deriv {
+  R v, fx, fy, fxx, fyy, fxy;
+};
+
+// Eq. 1 / Eq. 2 in x and y at tile position (sx, sy) of plane P (row stride SX).
+template <typename R, bool SECOND, bool MIXED>
+__device__ __forceinline__ Deriv<R> stencil(const R* P, int sx, int sy, const Spacing<R>& h) {
+  Deriv<R> d;
+  const R* r = P + sy * SX + sx;
+  const R c = r[0];
+  const R xm2 = r[-2], xm1 = r[-1], xp1 = r[1], xp2 = r[2];
+  const R ym2 = r[-2 * SX], ym1 = r[-SX], yp1 = r[SX], yp2 = r[2 * SX];
+  d.v = c;
+  // Eq. 1: (-f_{+2} + 8 f_{+1} - 8 f_{-1} + f_{-2}) / (12 h) = (8 (f_{+1} - f_{-1}) - (f_{+2} - f_{-2})) / (12 h)
+  d.fx = (R(8) * (xp1 - xm1) - (xp2 - xm2)) * h.i12dx;
+  d.fy = (R(8) * (yp1 - ym1) - (yp2 - ym2)) * h.i12dy;
+  if (SECOND) {
+    // Eq. 2: (16 ((f_{+1} - f_0) + (f_{-1} - f_0)) - ((f_{+2} - f_0) + (f_{-2} - f_0))) / (12 h^2)
+    d.fxx = (R(16) * ((xp1 - c) + (xm1 - c)) - ((xp2 - c) + (xm2 - c))) * h.i12dx2;
+    d.fyy = (R(16) * ((yp1 - c) + (ym1 - c)) - ((yp2 - c) + (ym2 - c))) * h.i12dy2;
+  } else {
+    d.fxx = d.fyy = R(0);
+  }
+  if (MIXED) {
+    // d_x d_y: Eq. 1 along y of the (unscaled) Eq. 1 along x.
+    auto gx = [&](int dy) {
+      const R* q = r + dy * SX;
+      return R(8) * (q[1] - q[-1]) - (q[2] - q[-2]);
+    };
+    d.fxy = (R(8) * (gx(1) - gx(-1)) - (gx(2) - gx(-2))) * h.i144dxdy;
+  } else {
+    d.fxy = R(0);
+  }
+  return d;
+}
+
+// ------------------------------------------------------------------ theories
+// Couplings in the working type. Abelian Higgs: c[0] = lambda, c[1] = u^2.
+// Chiral magnet: c[0] = J, c[1] = D, c[2] = K, c[3] = h, c[4..6] = d_1, c[7..9] = d_2.
+template <typename R>
+struct Couplings {
+  R c[10];
+};
+
+// Abelian Higgs (Table 1): e = 1/2 |D psi|^2 + 1/2 B^2 + lambda/8 (u^2 - |psi|^2)^2,
+// D_i = d_i - i A_i, B = d_1 A_2 - d_2 A_1. Components: 0 Re psi, 1 Im psi, 2 A_1, 3 A_2.
+template <typename R>
+__device__ __forceinline__ R density_ah(const Couplings<R>& k, const R* v, const R* fx, const R* fy) {
+  const R p1 = v[0], p2 = v[1], A1 = v[2], A2 = v[3];
+  const R re1 = fx[0] + A1 * p2, im1 = fx[1] - A1 * p1;
+  const R re2 = fy[0] + A2 * p2, im2 = fy[1] - A2 * p1;
+  const R B = fx[3] - fy[2];
+  const R w = k.c[1] - (p1 * p1 + p2 * p2);
+  return R(0.5) * (re1 * re1 + im1 * im1 + re2 * re2 + im2 * im2) + R(0.5) * B * B + k.c[0] * R(0.125) * w * w;
+}
+
+// Euler-Lagrange force of the Abelian Higgs energy:
+//   G_psi = -lap psi + i (div A) psi + 2 i A_i d_i psi + |A|^2 psi - lambda/2 (u^2 - |psi|^2) psi
+//   G_A1 = d_2 B + psi_2 d_1 psi_1 - psi_1 d_1 psi_2 + A_1 |psi|^2
+//   G_A2 = -d_1 B + psi_2 d_2 psi_1 - psi_1 d_2 psi_2 + A_2 |psi|^2
+template <typename R>
+__device__ __forceinline__ void force_ah(const Couplings<R>& k, const R* v, const R* fx, const R* fy, const R* fxx,
+                                         const R* fyy, const R* fxy, R* G) {
+  const R p1 = v[0], p2 = v[1], A1 = v[2], A2 = v[3];
+  const R divA = fx[2] + fy[3];
+  const R AA = A1 * A1 + A2 * A2, mod2 = p1 * p1 + p2 * p2;
+  const R pot = R(0.5) * k.c[0] * (k.c[1] - mod2);
+  G[0] = -(fxx[0] + fyy[0]) - R(2) * (A1 * fx[1] + A2 * fy[1]) - divA * p2 + (AA - pot) * p1;
+  G[1] = -(fxx[1] + fyy[1]) + R(2) * (A1 * fx[0] + A2 * fy[0]) + divA * p1 + (AA - pot) * p2;
+  G[2] = (fxy[3] - fyy[2]) + (p2 * fx[0] - p1 * fx[1]) + A1 * mod2;
+  G[3] = (fxy[2] - fxx[3]) + (p2 * fy[0] - p1 * fy[1]) + A2 * mod2;
+}
+
+template <typename R>
+__device__ __forceinline__ void cross3(const R* a, const R* b, R* o) {
+  o[0] = a[1] * b[2] - a[2] * b[1];
+  o[1] = a[2] * b[0] - a[0] * b[2];
+  o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// Chiral magnet (Eq. 5, no demag): e = J/2 |d n|^2 + D sum_i d_i . (n x d_i n)
+//   + K (1 - n_3^2) + h (1 - n_3).
+template <typename R>
+__device__ __forceinline__ R density_cm(const Couplings<R>& k, const R* n, const R* fx, const R* fy) {
+  R c1[3], c2[3];
+  cross3(n, fx, c1);
+  cross3(n, fy, c2);
+  const R ex = R(0.5) * k.c[0] * (fx[0] * fx[0] + fx[1] * fx[1] + fx[2] * fx[2] + fy[0] * fy[0] + fy[1] * fy[1] +
+                                  fy[2] * fy[2]);
+  const R dmi = k.c[1] * (k.c[4] * c1[0] + k.c[5] * c1[1] + k.c[6] * c1[2] + k.c[7] * c2[0] + k.c[8] * c2[1] +
+                          k.c[9] * c2[2]);
+  const R one_m = R(1) - n[2];
+  return ex + dmi + k.c[2] * one_m * (R(1) + n[2]) + k.c[3] * one_m;
+}
+
+// G = -J lap n - 2 D sum_i d_i x d_i n - 2 K n_3 e_3 - h e_3, then G <- G - (G.n) n.
+template <typename R>
+__device__ __forceinline__ void force_cm(const Couplings<R>& k, const R* n, const R* fx, const R* fy, const R* fxx,
+                                         const R* fyy, R* G) {
+  R c1[3], c2[3];
+  const R d1[3] = {k.c[4], k.c[5], k.c[6]}, d2[3] = {k.c[7], k.c[8], k.c[9]};
+  cross3(d1, fx, c1);
+  cross3(d2, fy, c2);
+  const R twoD = R(2) * k.c[1];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) G[a] = -k.c[0] * (fxx[a] + fyy[a]) - twoD * (c1[a] + c2[a]);
+  G[2] += -R(2) * k.c[2] * n[2] - k.c[3];
+  const R gn = G[0] * n[0] + G[1] * n[1] + G[2] * n[2];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) G[a] -= gn * n[a];
+}
+
+template <typename R>
+__device__ __forceinline__ R rsqrt_t(R x);
+template <>
+__device__ __forceinline__ float rsqrt_t<float>(float x) { return 1.0f / sqrtf(x); }
+template <>
+__device__ __forceinline__ double rsqrt_t<double>(double x) { return 1.0 / sqrt(x); }
+
+}  // namespace ss

@@ -1,0 +1,292 @@
+// ss_observe.cu -- GPU-resident observables and initial data (arxiv 2603.24370,
+// Sec. 2 "GPU-resident evaluation of observables", Sec. 3.3 reductions, Sec. 3.4
+// initialisation).
+//
+// Observables are evaluated in FP64 arithmetic from the stored field (FP32 or
+// FP64), with compensated sums and a fixed reduction order:
+//   E_h  = dx dy sum_I e                              (Table 1 / Eq. 5 densities)
+//   flux = dx dy sum_I (d_1 A_2 - d_2 A_1)            (Abelian Higgs)
+//   Q    = (1/4pi) sum over plaquettes of the Berg-Luescher solid angles of the
+//          two triangles (n00, n10, n11), (n00, n11, n01)   (chiral magnet)
+//   Q    = (1/2pi) sum of wrapped arg-psi steps around the boundary of I (Abelian Higgs)
+//   max_I |G|, max ||n| - 1|
+#include "ss_internal.h"
+
+namespace ss {
+
+template <typename R>
+struct ObsArgs {
+  const R* __restrict__ phi;
+  int nx, ny;
+  size_t plane;
+  int ntx, ntiles;
+  Spacing<double> h;
+  Couplings<double> k;
+  double area;
+  DevState* st;
+  ObsPartial* part;
+};
+
+__device__ __forceinline__ double dot3d(const double* a, const double* b) {
+  return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+// Signed solid angle of the spherical triangle (a, b, c):
+// tan(Omega / 2) = a.(b x c) / (1 + a.b + b.c + c.a)   (Berg and Luescher 1981).
+__device__ __forceinline__ double solid_angle(const double* a, const double* b, const double* c) {
+  double bc[3];
+  cross3<double>(b, c, bc);
+  return 2.0 * atan2(dot3d(a, bc), 1.0 + dot3d(a, b) + dot3d(b, c) + dot3d(c, a));
+}
+
+template <int TH, typename R>
+__global__ void __launch_bounds__(NT) k_observables(ObsArgs<R> a) {
+  constexpr int C = NComp<TH>::C;
+  __shared__ double sY[C][SY * SX];
+  __shared__ double sred[(NT / 32) * 8];
+  __shared__ int s_last;
+  const int tid = threadIdx.y * BX + threadIdx.x;
+  const size_t P = a.plane;
+  DD se{0.0, 0.0}, sf{0.0, 0.0}, sq{0.0, 0.0};
+  double gm = 0.0, nd = 0.0;
+
+  for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+    const int x0 = (t % a.ntx) * TX, y0 = (t / a.ntx) * TY;
+    __syncthreads();
+    for (int idx = tid; idx < SX * SY; idx += NT) {
+      const int lx = idx % SX, ly = idx / SX;
+      const int gx = x0 + lx - HALO, gy = y0 + ly - HALO;
+      const bool in = gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny;
+      const size_t s = (size_t)gy * a.nx + gx;
+#pragma unroll
+      for (int c = 0; c < C; ++c) sY[c][idx] = in ? (double)a.phi[c * P + s] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < ROWS_PER_THREAD; ++r) {
+      const int lx = threadIdx.x, ly = threadIdx.y + r * BY;
+      const int gx = x0 + lx, gy = y0 + ly;
+      if (gx >= a.nx || gy >= a.ny) continue;
+      const int sx = lx + HALO, sy = ly + HALO;
+      if (TH == TH_CM) {
+        const int o = sy * SX + sx;
+        const double n00[3] = {sY[0][o], sY[1][o], sY[2][o]};
+        nd = nanmax(nd, fabs(sqrt(dot3d(n00, n00)) - 1.0));
+        if (gx + 1 < a.nx && gy + 1 < a.ny) {
+          double q[4][3];
+          const int off[4] = {o, o + 1, o + 1 + SX, o + SX};  // (i,j) (i+1,j) (i+1,j+1) (i,j+1)
+#pragma unroll
+          for (int m = 0; m < 4; ++m) {
+            const double x = sY[0][off[m]], y = sY[1][off[m]], z = sY[2][off[m]];
+            const double inv = 1.0 / sqrt(x * x + y * y + z * z);
+            q[m][0] = x * inv; q[m][1] = y * inv; q[m][2] = z * inv;
+          }
+          neumaier(sq, solid_angle(q[0], q[1], q[2]));
+          neumaier(sq, solid_angle(q[0], q[2], q[3]));
+        }
+      }
+      if (gx < HALO || gx >= a.nx - HALO || gy < HALO || gy >= a.ny - HALO) continue;
+      double v[C], fx[C], fy[C], fxx[C], fyy[C], fxy[C];
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        const Deriv<double> d = (TH == TH_AH && c >= 2) ? stencil<double, true, true>(sY[c], sx, sy, a.h)
+                                                        : stencil<double, true, false>(sY[c], sx, sy, a.h);
+        v[c] = d.v; fx[c] = d.fx; fy[c] = d.fy; fxx[c] = d.fxx; fyy[c] = d.fyy; fxy[c] = d.fxy;
+      }
+      double G[C];
+      if (TH == TH_AH) {
+        force_ah<double>(a.k, v, fx, fy, fxx, fyy, fxy, G);
+        neumaier(se, density_ah<double>(a.k, v, fx, fy));
+        neumaier(sf, fx[3] - fy[2]);
+      } else {
+        force_cm<double>(a.k, v, fx, fy, fxx, fyy, G);
+        neumaier(se, density_cm<double>(a.k, v, fx, fy));
+      }
+#pragma unroll
+      for (int c = 0; c < C; ++c) gm = nanmax(gm, fabs(G[c]));
+    }
+  }
+
+  DD sv[3] = {se, sf, sq};
+  double mv[2] = {gm, nd};
+  block_reduce<3, 2>(sv, mv, sred);
+  if (tid == 0) {
+    a.part[blockIdx.x] = ObsPartial{sv[0].s, sv[0].c, sv[1].s, sv[1].c, sv[2].s, sv[2].c, mv[0], mv[1]};
+    __threadfence();
+    const unsigned prev = atomicAdd(&a.st->obs_ticket, 1u);
+    s_last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  DD ae{0.0, 0.0}, af{0.0, 0.0}, aq{0.0, 0.0};
+  double am = 0.0, an = 0.0;
+  for (int i = tid; i < (int)gridDim.x; i += NT) {
+    const ObsPartial* p = a.part + i;
+    ae = dd_add(ae, DD{__ldcg(&p->es), __ldcg(&p->ec)});
+    af = dd_add(af, DD{__ldcg(&p->fs), __ldcg(&p->fc)});
+    aq = dd_add(aq, DD{__ldcg(&p->qs), __ldcg(&p->qc)});
+    am = nanmax(am, __ldcg(&p->gm));
+    an = nanmax(an, __ldcg(&p->nd));
+  }
+  DD sv2[3] = {ae, af, aq};
+  double mv2[2] = {am, an};
+  block_reduce<3, 2>(sv2, mv2, sred);
+  if (tid == 0) {
+    DevState* st = a.st;
+    st->obs_energy = a.area * (sv2[0].s + sv2[0].c);
+    st->obs_flux = a.area * (sv2[1].s + sv2[1].c);
+    if (TH == TH_CM) st->obs_charge = (sv2[2].s + sv2[2].c) / (4.0 * 3.14159265358979323846);
+    st->obs_gmax_raw = mv2[0];
+    st->obs_normdev = mv2[1];
+    st->obs_ticket = 0;
+  }
+}
+
+// Winding of arg psi around the boundary loop of I, counter-clockwise, one block.
+template <typename R>
+__global__ void __launch_bounds__(NT) k_winding(const R* __restrict__ phi, int nx, int ny, size_t plane,
+                                                DevState* st) {
+  __shared__ double sred[(NT / 32) * 2];
+  const int tid = threadIdx.y * BX + threadIdx.x;
+  const int a = nx - 5, b = ny - 5, L = 2 * a + 2 * b;
+  auto site = [&](int k, int& i, int& j) {
+    if (k < a) { i = 2 + k; j = 2; }
+    else if (k < a + b) { i = nx - 3; j = 2 + (k - a); }
+    else if (k < 2 * a + b) { i = nx - 3 - (k - a - b); j = ny - 3; }
+    else { i = 2; j = ny - 3 - (k - 2 * a - b); }
+  };
+  const double PI = 3.14159265358979323846;
+  DD acc{0.0, 0.0};
+  for (int k = tid; k < L; k += NT) {
+    int i0, j0, i1, j1;
+    site(k, i0, j0);
+    site((k + 1) % L, i1, j1);
+    const size_t s0 = (size_t)j0 * nx + i0, s1 = (size_t)j1 * nx + i1;
+    double d = atan2((double)phi[plane + s1], (double)phi[s1]) - atan2((double)phi[plane + s0], (double)phi[s0]);
+    if (d > PI) d -= 2.0 * PI;
+    if (d <= -PI) d += 2.0 * PI;
+    neumaier(acc, d);
+  }
+  DD sv[1] = {acc};
+  double mv[1] = {0.0};
+  block_reduce<1, 1>(sv, mv, sred);
+  if (tid == 0) st->obs_charge = (sv[0].s + sv[0].c) / (2.0 * PI);
+}
+
+// Initial data (Sec. 3.4 "model-specific ansatz"; standard forms, see soliton.h),
+// evaluated in FP64 and rounded once to the storage type, into both field buffers.
+template <int TH, typename R>
+__global__ void k_ansatz(R* __restrict__ f0, R* __restrict__ f1, int nx, int ny, size_t plane, double dx, double dy,
+                         const double* __restrict__ sol, int ns) {
+  const double PI = 3.14159265358979323846;
+  for (size_t s = (size_t)blockIdx.x * blockDim.x + threadIdx.x; s < plane; s += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(s % nx), j = (int)(s / nx);
+    const double x = (i - 0.5 * (nx - 1)) * dx, y = (j - 0.5 * (ny - 1)) * dy;
+    if (TH == TH_AH) {
+      double mod = 1.0, ph = 0.0, A1 = 0.0, A2 = 0.0;
+      for (int k = 0; k < ns; ++k) {
+        const double X = x - sol[5 * k], Y = y - sol[5 * k + 1];
+        const double n = sol[5 * k + 2], sz = sol[5 * k + 3], chi = sol[5 * k + 4];
+        const double r2 = X * X + Y * Y;
+        const double t = tanh(sqrt(r2) / sz);
+        mod *= pow(t, fabs(n));
+        ph += n * atan2(Y, X) + chi;
+        if (r2 > 0.0) {
+          A1 += n * t * t * (-Y) / r2;
+          A2 += n * t * t * X / r2;
+        }
+      }
+      double sn, cs;
+      sincos(ph, &sn, &cs);
+      const R v[4] = {(R)(mod * cs), (R)(mod * sn), (R)A1, (R)A2};
+#pragma unroll
+      for (int c = 0; c < 4; ++c) { f0[c * plane + s] = v[c]; f1[c * plane + s] = v[c]; }
+    } else {
+      double n1 = 0.0, n2 = 0.0, n3 = 1.0;
+      for (int k = 0; k < ns; ++k) {
+        const double X = x - sol[5 * k], Y = y - sol[5 * k + 1];
+        const double R0 = sol[5 * k + 3];
+        const double r2 = X * X + Y * Y;
+        if (r2 < R0 * R0) {
+          const double r = sqrt(r2);
+          const double fr = PI * (1.0 - r / R0), th = sol[5 * k + 2] * atan2(Y, X) + sol[5 * k + 4];
+          n1 = sin(fr) * cos(th);
+          n2 = sin(fr) * sin(th);
+          n3 = cos(fr);
+          break;
+        }
+      }
+      const R v[3] = {(R)n1, (R)n2, (R)n3};
+#pragma unroll
+      for (int c = 0; c < 3; ++c) { f0[c * plane + s] = v[c]; f1[c * plane + s] = v[c]; }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+template <int TH, typename R>
+static cudaError_t obs_t(const LaunchCtx& c, int cur, cudaStream_t s) {
+  ObsArgs<R> a{};
+  a.phi = static_cast<const R*>(c.phi[cur]);
+  a.nx = c.nx;
+  a.ny = c.ny;
+  a.plane = c.plane;
+  a.ntx = c.ntiles_x;
+  a.ntiles = c.ntiles_x * c.ntiles_y;
+  a.h.i12dx = 1.0 / (12.0 * c.dx);
+  a.h.i12dy = 1.0 / (12.0 * c.dy);
+  a.h.i12dx2 = 1.0 / (12.0 * c.dx * c.dx);
+  a.h.i12dy2 = 1.0 / (12.0 * c.dy * c.dy);
+  a.h.i144dxdy = 1.0 / (144.0 * c.dx * c.dy);
+  for (int i = 0; i < 10; ++i) a.k.c[i] = c.coup[i];
+  a.area = c.dx * c.dy;
+  a.st = c.st;
+  a.part = c.opart;
+  k_observables<TH, R><<<c.obs_blocks, dim3(BX, BY), 0, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (TH == TH_AH) {
+    k_winding<R><<<1, dim3(BX, BY), 0, s>>>(a.phi, c.nx, c.ny, c.plane, c.st);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+cudaError_t launch_observables(const LaunchCtx& c, int cur, cudaStream_t s) {
+  if (c.theory == TH_AH) return c.prec == 1 ? obs_t<TH_AH, float>(c, cur, s) : obs_t<TH_AH, double>(c, cur, s);
+  return c.prec == 1 ? obs_t<TH_CM, float>(c, cur, s) : obs_t<TH_CM, double>(c, cur, s);
+}
+
+template <int TH, typename R>
+static cudaError_t ansatz_t(const LaunchCtx& c, const double* sol, int n, cudaStream_t s) {
+  const int blocks = (int)((c.plane + 255) / 256 < 4096 ? (c.plane + 255) / 256 : 4096);
+  k_ansatz<TH, R><<<blocks, 256, 0, s>>>(static_cast<R*>(c.phi[0]), static_cast<R*>(c.phi[1]), c.nx, c.ny, c.plane,
+                                         c.dx, c.dy, sol, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ansatz(const LaunchCtx& c, const double* d_sol, int n, cudaStream_t s) {
+  if (c.theory == TH_AH) return c.prec == 1 ? ansatz_t<TH_AH, float>(c, d_sol, n, s) : ansatz_t<TH_AH, double>(c, d_sol, n, s);
+  return c.prec == 1 ? ansatz_t<TH_CM, float>(c, d_sol, n, s) : ansatz_t<TH_CM, double>(c, d_sol, n, s);
+}
+
+template <int TH, typename R>
+static int obs_occ() {
+  int b = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_observables<TH, R>, NT, 0);
+  return b < 1 ? 1 : b;
+}
+
+int obs_grid(int theory, int prec, int ntiles) {
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  int occ;
+  if (theory == TH_AH) occ = prec == 1 ? obs_occ<TH_AH, float>() : obs_occ<TH_AH, double>();
+  else occ = prec == 1 ? obs_occ<TH_CM, float>() : obs_occ<TH_CM, double>();
+  const int g = nsm * occ;
+  return ntiles < g ? ntiles : g;
+}
+
+}  // namespace ss

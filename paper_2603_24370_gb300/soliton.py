@@ -1,0 +1,292 @@
+"""Thin Python binding of the C-ABI in ``include/soliton.h`` (argument marshalling only).
+
+Every step of the relaxation runs in the CUDA kernels of ``libsoliton.so``; this
+module converts arguments (numpy arrays / torch tensors / pointers), checks the
+return codes and raises ``SolitonError`` with the library's message. There is no
+CPU fallback: without the compiled library every call raises.
+
+The functions keep the C names: ``ss_create_grid``, ``ss_set_theory``,
+``ss_init_ansatz``, ``ss_set_fields``, ``ss_get_fields``, ``ss_get_velocity``,
+``ss_force``, ``ss_step``, ``ss_minimise``, ``ss_observables``, ``ss_destroy``.
+``Solver`` bundles them for convenience.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+SS_OK = 0
+SS_ERR_ARG = -1
+SS_ERR_STATE = -2
+SS_ERR_CUDA = -3
+SS_ERR_TIMEOUT = -4
+SS_ERR_NONFINITE = -5
+SS_ERR_NOT_CONVERGED = -6
+SS_ERR_NOMEM = -7
+
+SS_FP32 = 1
+SS_FP64 = 2
+SS_ABELIAN_HIGGS = 1
+SS_CHIRAL_MAGNET = 2
+
+_ERR_NAMES = {
+    SS_ERR_ARG: "SS_ERR_ARG", SS_ERR_STATE: "SS_ERR_STATE", SS_ERR_CUDA: "SS_ERR_CUDA",
+    SS_ERR_TIMEOUT: "SS_ERR_TIMEOUT", SS_ERR_NONFINITE: "SS_ERR_NONFINITE",
+    SS_ERR_NOT_CONVERGED: "SS_ERR_NOT_CONVERGED", SS_ERR_NOMEM: "SS_ERR_NOMEM",
+}
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libsoliton.so")
+
+
+class SolitonError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_ERR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class ss_soliton(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_double), ("y", ctypes.c_double), ("charge", ctypes.c_int),
+                ("size", ctypes.c_double), ("phase", ctypes.c_double)]
+
+
+class ss_status(ctypes.Structure):
+    _fields_ = [("energy", ctypes.c_double), ("grad_max", ctypes.c_double), ("steps", ctypes.c_longlong),
+                ("arrests", ctypes.c_longlong), ("converged", ctypes.c_int), ("arrested", ctypes.c_int)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ss_obs(ctypes.Structure):
+    _fields_ = [("energy", ctypes.c_double), ("charge", ctypes.c_double), ("flux", ctypes.c_double),
+                ("grad_max", ctypes.c_double), ("grad_max_raw", ctypes.c_double), ("norm_dev", ctypes.c_double),
+                ("steps", ctypes.c_longlong)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load_library(path: str | None = None):
+    """Load ``libsoliton.so`` (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"{p} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+        lib = ctypes.CDLL(p)
+        vp, i, d, ll = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+        pd = ctypes.POINTER(ctypes.c_double)
+        sig = {
+            "ss_last_error": ([], ctypes.c_char_p),
+            "ss_version": ([], i),
+            "ss_create_grid": ([ctypes.POINTER(vp), i, i, d, d, i, vp], i),
+            "ss_set_theory": ([vp, i, pd, i], i),
+            "ss_init_ansatz": ([vp, ctypes.POINTER(ss_soliton), i], i),
+            "ss_set_fields": ([vp, vp, i], i),
+            "ss_get_fields": ([vp, vp, i], i),
+            "ss_get_velocity": ([vp, vp, i], i),
+            "ss_force": ([vp, vp, i, pd, pd], i),
+            "ss_step": ([vp, i, ctypes.POINTER(ss_status)], i),
+            "ss_minimise": ([vp, d, ll, ctypes.POINTER(ss_status)], i),
+            "ss_observables": ([vp, ctypes.POINTER(ss_obs)], i),
+            "ss_profile_stages": ([vp, i, ctypes.POINTER(ctypes.c_float)], i),
+            "ss_destroy": ([vp], i),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def last_error() -> str:
+    return load_library().ss_last_error().decode(errors="replace")
+
+
+def _check(rc: int, allow=()):
+    if rc != SS_OK and rc not in allow:
+        raise SolitonError(rc, last_error())
+    return rc
+
+
+def _ptr(arr, dtype):
+    """(pointer, is_device) of a contiguous numpy array or torch tensor of ``dtype``."""
+    if hasattr(arr, "data_ptr"):  # torch tensor
+        import torch
+        want = torch.float32 if dtype == np.float32 else torch.float64
+        if arr.dtype != want or not arr.is_contiguous():
+            raise ValueError(f"tensor must be contiguous {want}")
+        return ctypes.c_void_p(arr.data_ptr()), 1 if arr.is_cuda else 0
+    if not isinstance(arr, np.ndarray) or arr.dtype != dtype or not arr.flags["C_CONTIGUOUS"]:
+        raise ValueError(f"array must be a C-contiguous numpy {np.dtype(dtype).name} array")
+    return ctypes.c_void_p(arr.ctypes.data), 0
+
+
+# ---------------------------------------------------------------- C names
+def ss_create_grid(nx: int, ny: int, dx: float, dy: float, precision: int = SS_FP32, stream=None):
+    lib = load_library()
+    ctx = ctypes.c_void_p()
+    s = None
+    if stream is not None:
+        s = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    _check(lib.ss_create_grid(ctypes.byref(ctx), nx, ny, dx, dy, precision, s))
+    return ctx
+
+
+def ss_set_theory(ctx, theory: int, params) -> None:
+    p = np.ascontiguousarray(np.asarray(params, dtype=np.float64).reshape(-1))
+    _check(load_library().ss_set_theory(ctx, theory, p.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), p.size))
+
+
+def ss_init_ansatz(ctx, solitons) -> None:
+    rows = np.asarray(solitons, dtype=np.float64).reshape(-1, 5)
+    arr = (ss_soliton * max(len(rows), 1))()
+    for k, (x, y, q, size, ph) in enumerate(rows):
+        if q != int(q):
+            raise ValueError("soliton charges must be integers")
+        arr[k] = ss_soliton(x, y, int(q), size, ph)
+    _check(load_library().ss_init_ansatz(ctx, arr, len(rows)))
+
+
+def ss_set_fields(ctx, fields, dtype) -> None:
+    p, dev = _ptr(fields, dtype)
+    _check(load_library().ss_set_fields(ctx, p, dev))
+
+
+def ss_get_fields(ctx, out) -> None:
+    p, dev = _ptr(out, np.float32 if _dtype_of(out) == np.float32 else np.float64)
+    _check(load_library().ss_get_fields(ctx, p, dev))
+
+
+def ss_get_velocity(ctx, out) -> None:
+    p, dev = _ptr(out, np.float32 if _dtype_of(out) == np.float32 else np.float64)
+    _check(load_library().ss_get_velocity(ctx, p, dev))
+
+
+def ss_force(ctx, out):
+    p, dev = _ptr(out, np.float32 if _dtype_of(out) == np.float32 else np.float64)
+    e, g = ctypes.c_double(), ctypes.c_double()
+    _check(load_library().ss_force(ctx, p, dev, ctypes.byref(e), ctypes.byref(g)))
+    return e.value, g.value
+
+
+def ss_step(ctx, n_steps: int, allow=()) -> dict:
+    st = ss_status()
+    rc = _check(load_library().ss_step(ctx, int(n_steps), ctypes.byref(st)), allow)
+    d = st.as_dict()
+    d["rc"] = rc
+    return d
+
+
+def ss_minimise(ctx, tol: float, max_steps: int, allow=(SS_ERR_NOT_CONVERGED,)) -> dict:
+    st = ss_status()
+    rc = _check(load_library().ss_minimise(ctx, float(tol), int(max_steps), ctypes.byref(st)), allow)
+    d = st.as_dict()
+    d["rc"] = rc
+    return d
+
+
+def ss_observables(ctx) -> dict:
+    o = ss_obs()
+    _check(load_library().ss_observables(ctx, ctypes.byref(o)))
+    return o.as_dict()
+
+
+def ss_profile_stages(ctx, n_steps: int) -> list[float]:
+    """Mean device milliseconds of RK stages 1..4 over n_steps real flow steps."""
+    ms = (ctypes.c_float * 4)()
+    _check(load_library().ss_profile_stages(ctx, int(n_steps), ms))
+    return [float(x) for x in ms]
+
+
+def ss_destroy(ctx) -> None:
+    if ctx is not None:
+        _check(load_library().ss_destroy(ctx))
+
+
+def _dtype_of(a):
+    if hasattr(a, "data_ptr"):
+        import torch
+        return np.float32 if a.dtype == torch.float32 else np.float64
+    return a.dtype.type
+
+
+# ---------------------------------------------------------------- convenience
+class Solver:
+    """One relaxation problem on the GPU: a context plus its shape and dtype."""
+
+    def __init__(self, theory: int, params, nx: int, ny: int, dx: float, dy: float, precision: int = SS_FP32,
+                 stream=None):
+        self.theory, self.nx, self.ny, self.dx, self.dy = theory, nx, ny, dx, dy
+        self.precision = precision
+        self.C = 4 if theory == SS_ABELIAN_HIGGS else 3
+        self.dtype = np.float32 if precision == SS_FP32 else np.float64
+        self.ctx = ss_create_grid(nx, ny, dx, dy, precision, stream)
+        try:
+            ss_set_theory(self.ctx, theory, params)
+        except Exception:
+            ss_destroy(self.ctx)
+            raise
+
+    @property
+    def shape(self):
+        return (self.C, self.ny, self.nx)
+
+    def init_ansatz(self, solitons):
+        ss_init_ansatz(self.ctx, solitons)
+
+    def set_fields(self, f):
+        if isinstance(f, np.ndarray):
+            f = np.ascontiguousarray(f, dtype=self.dtype)
+        ss_set_fields(self.ctx, f, self.dtype)
+
+    def fields(self, out=None):
+        out = np.empty(self.shape, dtype=self.dtype) if out is None else out
+        ss_get_fields(self.ctx, out)
+        return out
+
+    def velocity(self):
+        out = np.empty(self.shape, dtype=self.dtype)
+        ss_get_velocity(self.ctx, out)
+        return out
+
+    def force(self):
+        out = np.empty(self.shape, dtype=self.dtype)
+        e, g = ss_force(self.ctx, out)
+        return out, e, g
+
+    def step(self, n: int, allow=()):
+        return ss_step(self.ctx, n, allow)
+
+    def minimise(self, tol: float, max_steps: int):
+        return ss_minimise(self.ctx, tol, max_steps)
+
+    def observables(self):
+        return ss_observables(self.ctx)
+
+    def close(self):
+        if self.ctx is not None:
+            ss_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
