@@ -7,9 +7,10 @@ Workload: chiral magnet (J = D = 1, h = 0.6, K = 0.1, interfacial DMI) on a
 400 compact skyrmions at seeded positions (minimum separation 8). Its arrays
 (7 x 201 MB) are far larger than the 129 MB L2, so every timed step streams HBM.
 
-One bench step = one call ss_step(ctx, 32): 32 flow steps (each four RK stage
-kernels; stage 1 fuses the energy / residual reductions and the arrest decision),
-enqueued as one CUDA graph. value = interior site-updates per second.
+One bench step = one call ss_step(ctx, 32): 32 flow steps, each two fused kernels
+(pass 1: RK stages 1-2 with the energy / residual / energy-change reductions and
+the arrest decision; pass 2: RK stages 3-4 and the RK4 combination), enqueued as
+one CUDA graph. value = interior site-updates per second.
 e2e: the same calls with the field copied in from pinned host memory and out
 again every bench step (ss_set_fields / ss_step / ss_get_fields on host buffers).
 --impl reference: the FP64 CPU oracle on the host cores, same metric, each step one
@@ -40,17 +41,17 @@ SEED = 20264
 CROP = 512          # oracle sample (CPU baseline / reference arm)
 C = 3
 WORKLOAD = ("chiral magnet 4096x4096 (halo incl.), dx=0.2, J=D=1, h=0.6, K=0.1, interfacial DMI, "
-            "400 skyrmions min-sep 8, FP32 fields + FP64 reductions, ANF-RK4 (4 stage kernels/step)")
+            "400 skyrmions min-sep 8, FP32 fields + FP64 reductions, ANF-RK4 (2 fused kernels/step)")
 
 
 def interior(n: int) -> int:
     return (n - 4) * (n - 4)
 
 
-# algorithmic bytes per interior site of each RK stage kernel (FP32, C components):
-# stage 1 reads phi, writes k_v1; 2 reads phi, v, writes k_v2; 3 reads phi, v, k_v1,
-# writes k_v3; 4 reads phi, v, k_v1..3, writes phi', v'.
-STAGE_BYTES = {1: 4 * 2 * C, 2: 4 * 3 * C, 3: 4 * 4 * C, 4: 4 * 7 * C}
+# algorithmic bytes per interior site of each kernel of a step (FP32, C components):
+# pass 1 reads phi, v, phi^{n-1} and writes k_v1, k_v2; pass 2 reads phi, v, k_v1,
+# k_v2 and writes phi', v'.
+PASS_BYTES = {1: 4 * 5 * C, 2: 4 * 6 * C}
 
 
 def measured_peaks() -> tuple[dict, str]:
@@ -212,12 +213,13 @@ def run_native(args) -> int:
     B.build()
     S.load_library()
 
-    p = I.cm_skyrmions(n=N, count=COUNT, seed=SEED)
+    n = args.grid
+    p = I.cm_skyrmions(n=n, count=COUNT if n >= 2048 else max(1, COUNT * n * n // (N * N)), seed=SEED)
     stream = torch.cuda.Stream()
-    s = S.Solver(S.SS_CHIRAL_MAGNET, p.params, N, N, DX, DX, S.SS_FP32, stream=stream)
+    s = S.Solver(S.SS_CHIRAL_MAGNET, p.params, n, n, DX, DX, S.SS_FP32, stream=stream)
     s.init_ansatz(p.soliton_array())
     f_init = s.fields()
-    launches_per_call = 2 + ((INNER + 31) // 32) * 32 * 4  # set_run + head + graph chunk(s)
+    launches_per_call = 2 + ((INNER + 31) // 32) * 32 * 2  # set_run + head + graph chunk(s)
 
     for _ in range(args.warmup):
         s.step(INNER)
@@ -237,24 +239,24 @@ def run_native(args) -> int:
     D.barrier()
     clk = clocks.stop()
     sec = ev0.elapsed_time(ev1) / 1e3
-    units, job_sec = D.aggregate(interior(N) * INNER * args.steps, sec)
+    units, job_sec = D.aggregate(interior(n) * INNER * args.steps, sec)
     value = units / job_sec
 
-    # per-kernel durations (CUDA events around each stage launch on the context stream)
+    # per-kernel durations (CUDA events around each launch on the context stream)
     stage_ms = S.ss_profile_stages(s.ctx, 8)
-    dominant = max(range(4), key=lambda i: stage_ms[i] * 1.0) + 1
+    dominant = max(range(2), key=lambda i: stage_ms[i]) + 1
     peaks, src = measured_peaks()
-    kname = f"k_stage<CM, float, {dominant}>"
-    alg = STAGE_BYTES[dominant] * interior(N)
+    kname = f"k_pass<CM, float, {dominant}>"
+    alg = PASS_BYTES[dominant] * interior(n)
     achieved = alg / (stage_ms[dominant - 1] * 1e-3) / 1e9
-    traffic = ncu_traffic(f"stage{dominant}")
+    traffic = ncu_traffic(f"pass{dominant}")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "kernel": kname,
                 "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else "fallback 6.8 TB/s",
                 "algorithmic_bytes_per_launch": alg,
-                "stage_ms": stage_ms,
-                "step_bytes_per_site_update": sum(STAGE_BYTES.values()),
-                "step_frac": (sum(STAGE_BYTES.values()) * interior(N) / (sum(stage_ms) * 1e-3) / 1e9) / peaks["hbm_gbs"]}
+                "pass_ms": stage_ms,
+                "step_bytes_per_site_update": sum(PASS_BYTES.values()),
+                "step_frac": (sum(PASS_BYTES.values()) * interior(n) / (sum(stage_ms) * 1e-3) / 1e9) / peaks["hbm_gbs"]}
 
     # end to end through the C-ABI with host buffers: field in from pinned memory,
     # 32 flow steps, field out to pinned memory, every bench step
@@ -272,8 +274,8 @@ def run_native(args) -> int:
         S.ss_get_fields(s.ctx, host_out)
     torch.cuda.synchronize()
     e2e_sec = time.perf_counter() - t0
-    e_units, e_sec = D.aggregate(interior(N) * INNER * e2e_steps, e2e_sec)
-    nbytes = C * N * N * 4
+    e_units, e_sec = D.aggregate(interior(n) * INNER * e2e_steps, e2e_sec)
+    nbytes = C * n * n * 4
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -285,9 +287,10 @@ def run_native(args) -> int:
             "metric": "site-updates/s", "value": value, "unit": "site-updates/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * job_sec / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "flow_steps_per_bench_step": INNER, "grid": [N, N],
-                       "interior_sites": interior(N), "parallelism": "replicas" if world > 1 else "single",
-                       "l2": "working set 1.4 GB >> 129 MB L2 (no flush needed)"},
+            "config": {"workload": WORKLOAD if n == N else WORKLOAD.replace("4096x4096", f"{n}x{n}"),
+                       "flow_steps_per_bench_step": INNER, "grid": [n, n],
+                       "interior_sites": interior(n), "parallelism": "replicas" if world > 1 else "single",
+                       "l2": f"working set {7 * C * n * n * 4 / 1e9:.2f} GB vs 129 MB L2"},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": e_units / e_sec, "unit": "site-updates/s", "h2d_bytes_per_step": nbytes,
@@ -309,6 +312,7 @@ def main() -> int:
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("native", "reference"), default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--grid", type=int, default=N, help="grid side (default: the 4096 workload; smaller for ncu)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -84,6 +84,8 @@ typedef struct {
   long long arrests;  /* arrests (Eq. 4) since the fields were last set                */
   int converged;      /* grad_max < tol (ss_minimise only)                             */
   int arrested;       /* the current velocity is zeroed by a pending arrest            */
+  double energy_change; /* E_h(current) - E_h(previous field) as used by the arrest     */
+                        /* test, summed per site in cancellation-free form (0 if none)  */
 } ss_status;
 
 /* Observables of the current field, evaluated in FP64 arithmetic. */
@@ -166,11 +168,12 @@ int ss_minimise(ss_ctx* ctx, double tol, long long max_steps, ss_status* out);
 int ss_observables(ss_ctx* ctx, ss_obs* out);
 
 /* Tracing: take n_steps (1..4096) flow steps exactly as ss_step does, but with
- * direct launches bracketed by CUDA events on the context stream, and return in
- * ms_out[0..3] the mean device duration in milliseconds of RK stage kernels 1..4
- * (stage 1 includes the energy/residual reduction and the arrest decision of
- * Eq. 4). The steps advance the flow. Errors: SS_ERR_STATE, SS_ERR_ARG, SS_ERR_CUDA,
- * SS_ERR_NONFINITE. */
+ * direct launches bracketed by CUDA events on the context stream, and return the
+ * mean device duration in milliseconds of the two kernels of a step:
+ * ms_out[0] = pass 1 (RK stages 1-2 with the energy / residual / energy-change
+ * reductions and the on-device arrest decision of Eq. 4), ms_out[1] = pass 2 (RK
+ * stages 3-4 and the RK4 combination). The steps advance the flow.
+ * Errors: SS_ERR_STATE, SS_ERR_ARG, SS_ERR_CUDA, SS_ERR_NONFINITE. */
 int ss_profile_stages(ss_ctx* ctx, int n_steps, float* ms_out);
 
 /* Release every device and host resource of the context (NULL is a no-op). */

@@ -6,8 +6,8 @@
 // then minimise. The buffer set is reduced to what the fused stage kernels need
 // (Sec. 3.1 lists fields, velocity, gradient, derivative work arrays and RK stages):
 //   phi[2], v[2]   ping-pong field and velocity (RK4 reads phi^n around each site
-//                  while writing phi^{n+1}),
-//   kv[3]          stage accelerations k_v1..k_v3,
+//                  while writing phi^{n+1}; phi^{n-1} feeds the arrest test),
+//   kv[2]          stage accelerations k_v1, k_v2 (k_v3, k_v4 stay in registers),
 // plus one device status record and per-block reduction partials. Derivatives never
 // touch memory. Steps are enqueued as CUDA graphs of K_CHUNK steps; convergence,
 // arrest and the step budget are decided on the device, so the host only polls a
@@ -28,6 +28,7 @@ using namespace ss;
 namespace {
 
 constexpr int K_CHUNK = 32;  // steps per captured graph (even: parity returns)
+constexpr int NBUF = 6;      // phi[2], v[2], kv[2]
 
 thread_local std::string g_err;
 
@@ -90,12 +91,11 @@ int read_state(ss_ctx* c, DevState* out) {
   return SS_OK;
 }
 
-// One step from parity p: stages 2-4, then stage 1 (the head) of the new field.
+// One step from parity p: pass 2 (stages 3-4, new field), then pass 1 (stages 1-2,
+// reductions, arrest decision) of the new field, which is the next step's head.
 int enqueue_step(ss_ctx* c, int p) {
-  SS_CK(launch_stage(c->L, 2, p, c->stream));
-  SS_CK(launch_stage(c->L, 3, p, c->stream));
-  SS_CK(launch_stage(c->L, 4, p, c->stream));
-  SS_CK(launch_stage(c->L, 1, p ^ 1, c->stream));
+  SS_CK(launch_pass(c->L, 2, p, c->stream));
+  SS_CK(launch_pass(c->L, 1, p ^ 1, c->stream));
   return SS_OK;
 }
 
@@ -139,6 +139,7 @@ void fill_status(const DevState& h, ss_status* out) {
   out->arrests = h.arrests;
   out->converged = h.converged;
   out->arrested = h.arrest;
+  out->energy_change = h.dE;
 }
 
 // Run up to max_steps steps with threshold tol (< 0: none). Chunk i is enqueued
@@ -148,7 +149,7 @@ void fill_status(const DevState& h, ss_status* out) {
 int run(ss_ctx* c, double tol, long long max_steps, DevState* fin) {
   const int p0 = c->cur;
   SS_CK(launch_set_run(c->L, tol, max_steps, c->stream));
-  SS_CK(launch_stage(c->L, 1, p0, c->stream));  // head of the current field (no-op if done)
+  SS_CK(launch_pass(c->L, 1, p0, c->stream));  // head of the current field (no-op if done)
   const long long nchunks = (max_steps + K_CHUNK - 1) / K_CHUNK;
   if (nchunks > 0) {
     int rc = ensure_chunk(c, p0);
@@ -176,7 +177,7 @@ extern "C" {
 
 const char* ss_last_error(void) { return g_err.c_str(); }
 
-int ss_version(void) { return 1; }
+int ss_version(void) { return 3; }
 
 int ss_create_grid(ss_ctx** out, int nx, int ny, double dx, double dy, int precision, void* cuda_stream) {
   if (!out) return fail(SS_ERR_ARG, "out is NULL");
@@ -261,12 +262,12 @@ int ss_set_theory(ss_ctx* c, int theory, const double* params, int n_params) {
     free_buffers(c);
     const size_t pb = align256((size_t)C * c->L.plane * c->elem);
     const int ntiles = c->L.ntiles_x * c->L.ntiles_y;
-    const int fb = flow_grid(theory, c->prec, ntiles);
-    const int ob = obs_grid(theory, c->prec, ntiles);
+    const int fb = flow_grid(theory == SS_ABELIAN_HIGGS ? TH_AH : TH_CM, c->prec, c->nx, c->ny);
+    const int ob = obs_grid(theory == SS_ABELIAN_HIGGS ? TH_AH : TH_CM, c->prec, ntiles);
     const size_t stb = align256(sizeof(DevState));
     const size_t fpb = align256(sizeof(FlowPartial) * (size_t)fb);
     const size_t opb = align256(sizeof(ObsPartial) * (size_t)ob);
-    const size_t total = 7 * pb + stb + fpb + opb;
+    const size_t total = NBUF * pb + stb + fpb + opb;
     cudaError_t e = cudaMalloc(&c->base, total);
     if (e != cudaSuccess) {
       c->base = nullptr;
@@ -279,7 +280,7 @@ int ss_set_theory(ss_ctx* c, int theory, const double* params, int n_params) {
     c->L.phi[1] = p; p += pb;
     c->L.v[0] = p; p += pb;
     c->L.v[1] = p; p += pb;
-    for (int i = 0; i < 3; ++i) { c->L.kv[i] = p; p += pb; }
+    for (int i = 0; i < 2; ++i) { c->L.kv[i] = p; p += pb; }
     c->L.st = reinterpret_cast<DevState*>(p); p += stb;
     c->L.fpart = reinterpret_cast<FlowPartial*>(p); p += fpb;
     c->L.opart = reinterpret_cast<ObsPartial*>(p);
@@ -362,7 +363,7 @@ int ss_get_velocity(ss_ctx* c, void* out, int is_device) {
   int rc = check_ready(c);
   if (rc != SS_OK) return rc;
   if (!out) return fail(SS_ERR_ARG, "velocity is NULL");
-  SS_CK(launch_stage(c->L, 1, c->cur, c->stream));  // resolves a pending arrest (no-op if known)
+  SS_CK(launch_pass(c->L, 1, c->cur, c->stream));  // resolves a pending arrest (no-op if known)
   DevState h;
   rc = read_state(c, &h);
   if (rc != SS_OK) return rc;
@@ -382,13 +383,15 @@ int ss_force(ss_ctx* c, void* out, int is_device, double* energy, double* grad_m
   int rc = check_ready(c);
   if (rc != SS_OK) return rc;
   if (!out) return fail(SS_ERR_ARG, "force is NULL");
-  SS_CK(launch_stage(c->L, 1, c->cur, c->stream));  // k_v1 = -G of the current field
+  SS_CK(launch_pass(c->L, 1, c->cur, c->stream));  // k_v1 = -G of the current field
   const size_t bytes = (size_t)c->C * c->L.plane * c->elem;
   if (is_device) {
     SS_CK(launch_scaled_copy(c->L, out, c->L.kv[0], -1.0, c->stream));
   } else {
-    SS_CK(launch_scaled_copy(c->L, c->L.kv[2], c->L.kv[0], -1.0, c->stream));  // k_v3 is free between steps
-    SS_CK(cudaMemcpyAsync(out, c->L.kv[2], bytes, cudaMemcpyDeviceToHost, c->stream));
+    // v[cur ^ 1] is the next step's output buffer: free scratch, and -G keeps its halo zero
+    void* scratch = c->L.v[c->cur ^ 1];
+    SS_CK(launch_scaled_copy(c->L, scratch, c->L.kv[0], -1.0, c->stream));
+    SS_CK(cudaMemcpyAsync(out, scratch, bytes, cudaMemcpyDeviceToHost, c->stream));
   }
   DevState h;
   rc = read_state(c, &h);
@@ -447,33 +450,33 @@ int ss_profile_stages(ss_ctx* c, int n_steps, float* ms_out) {
   if (rc != SS_OK) return rc;
   if (n_steps < 1 || n_steps > 4096 || !ms_out) return fail(SS_ERR_ARG, "n_steps must be in 1..4096 and ms_out non-NULL");
   SS_CK(launch_set_run(c->L, -1.0, n_steps, c->stream));
-  SS_CK(launch_stage(c->L, 1, c->cur, c->stream));  // head of the current field, untimed
-  cudaEvent_t ev[5];
-  for (int i = 0; i < 5; ++i) SS_CK(cudaEventCreate(&ev[i]));
-  double acc[4] = {0, 0, 0, 0};
+  SS_CK(launch_pass(c->L, 1, c->cur, c->stream));  // head of the current field, untimed
+  cudaEvent_t ev[3];
+  for (int i = 0; i < 3; ++i) SS_CK(cudaEventCreate(&ev[i]));
+  double acc[2] = {0, 0};
   int p = c->cur;
   cudaError_t e = cudaSuccess;
   for (int k = 0; k < n_steps && e == cudaSuccess; ++k) {
-    const int order[4] = {2, 3, 4, 1};  // stage 1 runs on the new field
     e = cudaEventRecord(ev[0], c->stream);
-    for (int q = 0; q < 4 && e == cudaSuccess; ++q) {
-      e = launch_stage(c->L, order[q], order[q] == 1 ? (p ^ 1) : p, c->stream);
-      if (e == cudaSuccess) e = cudaEventRecord(ev[q + 1], c->stream);
-    }
-    if (e == cudaSuccess) e = cudaEventSynchronize(ev[4]);
-    for (int q = 0; q < 4 && e == cudaSuccess; ++q) {
-      float ms = 0.f;
-      e = cudaEventElapsedTime(&ms, ev[q], ev[q + 1]);
-      acc[order[q] - 1] += ms;
-    }
+    if (e == cudaSuccess) e = launch_pass(c->L, 2, p, c->stream);      // stages 3-4 -> new field
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1], c->stream);
+    if (e == cudaSuccess) e = launch_pass(c->L, 1, p ^ 1, c->stream);  // stages 1-2 of the new field
+    if (e == cudaSuccess) e = cudaEventRecord(ev[2], c->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[2]);
+    float m1 = 0.f, m2 = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&m2, ev[0], ev[1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&m1, ev[1], ev[2]);
+    acc[0] += m1;
+    acc[1] += m2;
     p ^= 1;
   }
-  for (int i = 0; i < 5; ++i) cudaEventDestroy(ev[i]);
+  for (int i = 0; i < 3; ++i) cudaEventDestroy(ev[i]);
   if (e != cudaSuccess) return fail(SS_ERR_CUDA, std::string("ss_profile_stages: ") + cudaGetErrorString(e));
   DevState h;
   rc = read_state(c, &h);
   if (rc != SS_OK) return rc;
-  for (int i = 0; i < 4; ++i) ms_out[i] = (float)(acc[i] / n_steps);
+  ms_out[0] = (float)(acc[0] / n_steps);
+  ms_out[1] = (float)(acc[1] / n_steps);
   if (h.nonfinite) return fail(SS_ERR_NONFINITE, "energy or force became non-finite; the flow stopped");
   return SS_OK;
 }

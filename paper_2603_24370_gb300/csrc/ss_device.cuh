@@ -6,6 +6,11 @@
 #include <math.h>
 #include <stdint.h>
 
+// The per-site physics (densities, forces, energy differences, stencil arithmetic)
+// is plain arithmetic, compiled for host and device so that host-only checks can
+// exercise exactly the code the kernels run.
+#define SS_HD __host__ __device__ __forceinline__
+
 namespace ss {
 
 // ------------------------------------------------------------------ tiling
@@ -30,6 +35,7 @@ template <> struct NComp<TH_CM> { static constexpr int C = 3; };
 struct DevState {
   double E_last;   // E_h of the previous head field (Eq. 4 compares against it)
   double E_cur;    // E_h of the current head field
+  double dE;       // E_h(current) - E_h(previous field), cancellation-free (0 if none)
   double gmax;     // dx dy max_I |G| of the current head field
   double tol;      // convergence threshold on gmax (< 0 disables)
   long long steps;       // steps taken since the fields were set
@@ -46,8 +52,11 @@ struct DevState {
   double obs_energy, obs_charge, obs_flux, obs_gmax_raw, obs_normdev;
 };
 
-struct FlowPartial {  // per-block part of the flow reduction (32 B)
-  double s, c, m, pad;
+struct FlowPartial {  // per-block part of the flow reduction (64 B)
+  double es, ec;  // sum of e
+  double ds, dc;  // sum of e(new) - e(previous)
+  double m;       // max |G|
+  double pad[3];
 };
 struct ObsPartial {  // per-block part of the observables reduction (64 B)
   double es, ec, fs, fc, qs, qc, gm, nd;
@@ -89,8 +98,15 @@ __device__ __forceinline__ double warp_max(double m) {
   return m;
 }
 
+// Shared doubles that block_reduce<K, L> needs; every caller sizes its buffer
+// with this so the two can never disagree.
+template <int K, int L>
+struct RedSmem {
+  static constexpr int n = (NT / 32) * (2 * K + L);
+};
+
 // Block reduction of K compensated sums and L maxima over NT threads; thread 0
-// returns the block result. sm must hold (NT/32) * (2K + L) doubles.
+// returns the block result. sm must hold RedSmem<K, L>::n doubles.
 template <int K, int L>
 __device__ __forceinline__ void block_reduce(DD (&s)[K], double (&m)[L], double* sm) {
   constexpr int W = NT / 32;
@@ -138,7 +154,7 @@ struct Deriv {
 
 // Eq. 1 / Eq. 2 in x and y at tile position (sx, sy) of plane P (row stride SX).
 template <typename R, bool SECOND, bool MIXED>
-__device__ __forceinline__ Deriv<R> stencil(const R* P, int sx, int sy, const Spacing<R>& h) {
+SS_HD Deriv<R> stencil(const R* P, int sx, int sy, const Spacing<R>& h) {
   Deriv<R> d;
   const R* r = P + sy * SX + sx;
   const R c = r[0];
@@ -179,7 +195,7 @@ struct Couplings {
 // Abelian Higgs (Table 1): e = 1/2 |D psi|^2 + 1/2 B^2 + lambda/8 (u^2 - |psi|^2)^2,
 // D_i = d_i - i A_i, B = d_1 A_2 - d_2 A_1. Components: 0 Re psi, 1 Im psi, 2 A_1, 3 A_2.
 template <typename R>
-__device__ __forceinline__ R density_ah(const Couplings<R>& k, const R* v, const R* fx, const R* fy) {
+SS_HD R density_ah(const Couplings<R>& k, const R* v, const R* fx, const R* fy) {
   const R p1 = v[0], p2 = v[1], A1 = v[2], A2 = v[3];
   const R re1 = fx[0] + A1 * p2, im1 = fx[1] - A1 * p1;
   const R re2 = fy[0] + A2 * p2, im2 = fy[1] - A2 * p1;
@@ -193,7 +209,7 @@ __device__ __forceinline__ R density_ah(const Couplings<R>& k, const R* v, const
 //   G_A1 = d_2 B + psi_2 d_1 psi_1 - psi_1 d_1 psi_2 + A_1 |psi|^2
 //   G_A2 = -d_1 B + psi_2 d_2 psi_1 - psi_1 d_2 psi_2 + A_2 |psi|^2
 template <typename R>
-__device__ __forceinline__ void force_ah(const Couplings<R>& k, const R* v, const R* fx, const R* fy, const R* fxx,
+SS_HD void force_ah(const Couplings<R>& k, const R* v, const R* fx, const R* fy, const R* fxx,
                                          const R* fyy, const R* fxy, R* G) {
   const R p1 = v[0], p2 = v[1], A1 = v[2], A2 = v[3];
   const R divA = fx[2] + fy[3];
@@ -206,7 +222,7 @@ __device__ __forceinline__ void force_ah(const Couplings<R>& k, const R* v, cons
 }
 
 template <typename R>
-__device__ __forceinline__ void cross3(const R* a, const R* b, R* o) {
+SS_HD void cross3(const R* a, const R* b, R* o) {
   o[0] = a[1] * b[2] - a[2] * b[1];
   o[1] = a[2] * b[0] - a[0] * b[2];
   o[2] = a[0] * b[1] - a[1] * b[0];
@@ -215,7 +231,7 @@ __device__ __forceinline__ void cross3(const R* a, const R* b, R* o) {
 // Chiral magnet (Eq. 5, no demag): e = J/2 |d n|^2 + D sum_i d_i . (n x d_i n)
 //   + K (1 - n_3^2) + h (1 - n_3).
 template <typename R>
-__device__ __forceinline__ R density_cm(const Couplings<R>& k, const R* n, const R* fx, const R* fy) {
+SS_HD R density_cm(const Couplings<R>& k, const R* n, const R* fx, const R* fy) {
   R c1[3], c2[3];
   cross3(n, fx, c1);
   cross3(n, fy, c2);
@@ -229,7 +245,7 @@ __device__ __forceinline__ R density_cm(const Couplings<R>& k, const R* n, const
 
 // G = -J lap n - 2 D sum_i d_i x d_i n - 2 K n_3 e_3 - h e_3, then G <- G - (G.n) n.
 template <typename R>
-__device__ __forceinline__ void force_cm(const Couplings<R>& k, const R* n, const R* fx, const R* fy, const R* fxx,
+SS_HD void force_cm(const Couplings<R>& k, const R* n, const R* fx, const R* fy, const R* fxx,
                                          const R* fyy, R* G) {
   R c1[3], c2[3];
   const R d1[3] = {k.c[4], k.c[5], k.c[6]}, d2[3] = {k.c[7], k.c[8], k.c[9]};
@@ -242,6 +258,64 @@ __device__ __forceinline__ void force_cm(const Couplings<R>& k, const R* n, cons
   const R gn = G[0] * n[0] + G[1] * n[1] + G[2] * n[2];
 #pragma unroll
   for (int a = 0; a < 3; ++a) G[a] -= gn * n[a];
+}
+
+// ------------------------------------------------------------------ energy differences
+// Eq. 4 compares E_h(phi^{n+1}) with E_h(phi^n). Both energy densities are
+// polynomials in (phi, d phi), so with a = phi^{n+1} and delta = phi^{n+1} - phi^n
+// (exact in floating point: neighbouring values) the per-site difference
+// e(a) - e(a - delta) expands exactly in delta and its derivatives. Evaluated in
+// this form its rounding error is relative to the difference itself, not to e, so
+// the arrest decision stays meaningful when the energy changes by far less than
+// the rounding of e (FP32 near convergence). Identities used: for any Z that is a
+// polynomial of the fields, Z(a)^2 - Z(a - delta)^2 = (2 Z(a) - dZ) dZ with
+// dZ = Z(a) - Z(a - delta) written out exactly.
+
+// Abelian Higgs: X_i = d_i psi_1 + A_i psi_2, Y_i = d_i psi_2 - A_i psi_1,
+// B = d_1 A_2 - d_2 A_1, w = u^2 - |psi|^2; e = (X^2 + Y^2 + B^2)/2 + lambda/8 w^2.
+template <typename R>
+SS_HD R delta_density_ah(const Couplings<R>& k, const R* a, const R* ax, const R* ay,
+                                              const R* d, const R* dx, const R* dy) {
+  const R p1 = a[0], p2 = a[1], A1 = a[2], A2 = a[3];
+  const R q1 = d[0], q2 = d[1], B1 = d[2], B2 = d[3];
+  // new values
+  const R X1 = ax[0] + A1 * p2, Y1 = ax[1] - A1 * p1;
+  const R X2 = ay[0] + A2 * p2, Y2 = ay[1] - A2 * p1;
+  const R B = ax[3] - ay[2];
+  const R w = k.c[1] - (p1 * p1 + p2 * p2);
+  // exact differences: A_i psi_c - (A_i - B_i)(psi_c - q_c) = A_i q_c + B_i psi_c - B_i q_c
+  const R dX1 = dx[0] + (A1 * q2 + B1 * (p2 - q2));
+  const R dY1 = dx[1] - (A1 * q1 + B1 * (p1 - q1));
+  const R dX2 = dy[0] + (A2 * q2 + B2 * (p2 - q2));
+  const R dY2 = dy[1] - (A2 * q1 + B2 * (p1 - q1));
+  const R dB = dx[3] - dy[2];
+  const R dw = -(q1 * (R(2) * p1 - q1) + q2 * (R(2) * p2 - q2));
+  return R(0.5) * ((R(2) * X1 - dX1) * dX1 + (R(2) * Y1 - dY1) * dY1 + (R(2) * X2 - dX2) * dX2 +
+                   (R(2) * Y2 - dY2) * dY2 + (R(2) * B - dB) * dB) +
+         k.c[0] * R(0.125) * (R(2) * w - dw) * dw;
+}
+
+// Chiral magnet: every term is at most quadratic in (n, d n):
+//   exchange  J sum_i d_i delta . (d_i a - d_i delta / 2)
+//   DMI       D sum_i d_i . (a x d_i delta + delta x d_i a - delta x d_i delta)
+//   anisotropy -K delta_3 (2 a_3 - delta_3),  Zeeman -h delta_3.
+template <typename R>
+SS_HD R delta_density_cm(const Couplings<R>& k, const R* a, const R* ax, const R* ay,
+                                              const R* d, const R* dx, const R* dy) {
+  R ex = R(0);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) ex += dx[c] * (ax[c] - R(0.5) * dx[c]) + dy[c] * (ay[c] - R(0.5) * dy[c]);
+  R u1[3], u2[3], u3[3], w1[3], w2[3], w3[3];
+  cross3(a, dx, u1);
+  cross3(d, ax, u2);
+  cross3(d, dx, u3);
+  cross3(a, dy, w1);
+  cross3(d, ay, w2);
+  cross3(d, dy, w3);
+  R dmi = R(0);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) dmi += k.c[4 + c] * (u1[c] + u2[c] - u3[c]) + k.c[7 + c] * (w1[c] + w2[c] - w3[c]);
+  return k.c[0] * ex + k.c[1] * dmi - k.c[2] * d[2] * (R(2) * a[2] - d[2]) - k.c[3] * d[2];
 }
 
 template <typename R>

@@ -1,44 +1,59 @@
-// ss_flow.cu -- the arrested-Newton-flow step (arxiv 2603.24370, Sec. 3.2).
+// ss_flow.cu -- the arrested-Newton-flow step (arxiv 2603.24370, Sec. 3.2) as two
+// fused passes over the grid.
 //
-// One RK4 step of phi'' = -G(phi) (Eq. 3) on the first-order system (phi, v) is
-// four stage kernels. Writing k_vi = -G(Y_i) for the stage inputs Y_i, classic RK4
-// reads
-//   Y_1 = phi,  Y_2 = phi + dt/2 v,  Y_3 = phi + dt/2 v + dt^2/4 k_v1,
-//   Y_4 = phi + dt v + dt^2/2 k_v2,
+// One RK4 step of phi'' = -G(phi) (Eq. 3) on the first-order system (phi, v), with
+// k_vi = -G(Y_i) at the stage inputs
+//   Y_1 = phi,                       Y_2 = phi + dt/2 v,
+//   Y_3 = phi + dt/2 v + dt^2/4 k_v1, Y_4 = phi + dt v + dt^2/2 k_v2,
 //   phi' = phi + dt v + dt^2/6 (k_v1 + k_v2 + k_v3),
 //   v'   = v + dt/6 (k_v1 + 2 k_v2 + 2 k_v3 + k_v4),
-// which is the textbook (k_phi, k_v) form with every k_phi eliminated, so no k_phi
-// array is ever stored. Chiral magnet: every Y_i and phi' are normalised and v'
-// is tangent-projected (Sec. 3.2, constraint projection).
+// is the textbook (k_phi, k_v) form with every k_phi eliminated. Y_1 and Y_2 need
+// only (phi, v); Y_3 and Y_4 need only (phi, v, k_v1, k_v2). So a step is two passes
+// with the ordinary width-2 halo and no recomputation:
+//   pass A  (stages 1, 2): reads phi, v (and phi^{n-1}), writes k_v1, k_v2;
+//   pass B  (stages 3, 4): reads phi, v, k_v1, k_v2, writes phi', v'
+// (k_v3, k_v4 live in registers). Chiral magnet: every Y_i and phi' are normalised
+// and v' tangent-projected (Sec. 3.2, constraint projection).
 //
-// Stage 1 also reduces E_h(phi) (a compensated pair per thread, FP64 TwoSum warp
+// Pass A also reduces E_h(phi) (a compensated pair per thread, FP64 TwoSum warp
 // trees, one partial per block, the last-arriving block sums the partials in a
-// fixed order) and dx dy max|G|, and then decides on the device, with no host
-// round trip:
-//   arrest    = E_h(phi^n) > E_h(phi^{n-1})   (Eq. 4; stages 2-4 then use v = 0)
-//   converged = dx dy max|G| < tol            (stages of later steps become no-ops)
-// Because the arrest of step n-1 -> n is only needed by stage 2 of step n, zeroing
-// v is lazy: no extra pass over memory.
+// fixed order), dx dy max|G|, and the energy change since the previous field,
+// dE = sum_I [e(phi^n) - e(phi^{n-1})] in the cancellation-free form of
+// ss_device.cuh (phi^{n-1} is still intact in the other ping-pong buffer). Its last
+// block then decides on the device, with no host round trip:
+//   arrest    = dE > 0, i.e. E_h(phi^n) > E_h(phi^{n-1})   (Eq. 4)
+//   converged = dx dy max|G| < tol
+// Pass A computes k_v2 with v before the arrest is known. That is exact either way:
+// when the step is arrested v counts as zero, so Y_2 = Y_1 and k_v2 = k_v1, and
+// pass B simply reads k_v1 in place of k_v2 (and zero in place of v).
 //
-// Each stage loads its input Y over a (TX+4) x (TY+4) shared tile (the width-2 halo
-// of Eq. 1 / Eq. 2), evaluates Eq. 1, Eq. 2 and the mixed derivative from shared
-// memory and writes C values per interior site. Blocks stride over tiles, so the
-// grid is a multiple of the SM count and the reduction has one partial per block.
+// Per block a tile of TX x TY sites is staged in shared memory with its halo, the
+// stage inputs formed while loading. Each thread then walks RY rows of one column
+// with a 5-row register window per component, so a component costs 5 shared loads
+// per site (centre + 4 x-neighbours) for Eq. 1, Eq. 2 and the mixed derivative.
+// Blocks stride over tiles; the grid is occupancy x SM count.
 #include "ss_internal.h"
 
 namespace ss {
 
 template <typename R>
-struct StageArgs {
-  const R* __restrict__ phi;   // phi^n (current field)
-  const R* __restrict__ v;     // v^n
-  const R* __restrict__ kvin;  // stage 3: k_v1, stage 4: k_v2 (part of Y)
-  const R* __restrict__ kv1;   // stage 4 combine
-  const R* __restrict__ kv2;
-  const R* __restrict__ kv3;
-  R* __restrict__ kv_out;      // stages 1-3: k_vs
-  R* __restrict__ phi_out;     // stage 4: phi^{n+1}
-  R* __restrict__ v_out;       // stage 4: v^{n+1}
+struct FlowTile {
+  static constexpr int RY = sizeof(R) == 4 ? 4 : 2;  // rows per thread
+  static constexpr int TX = 32, TY = BY * RY;
+  static constexpr int SX = TX + 4, SY = TY + 4, SXY = SX * SY;
+};
+
+template <typename R>
+struct PassArgs {
+  const R* __restrict__ phi;       // phi^n (current field)
+  const R* __restrict__ phi_prev;  // pass A: phi^{n-1} (other ping-pong buffer)
+  const R* __restrict__ v;         // v^n
+  const R* __restrict__ kv1;       // pass B
+  const R* __restrict__ kv2;       // pass B
+  R* __restrict__ kv1_out;         // pass A
+  R* __restrict__ kv2_out;         // pass A
+  R* __restrict__ phi_out;         // pass B: phi^{n+1}
+  R* __restrict__ v_out;           // pass B: v^{n+1}
   int nx, ny;
   size_t plane;
   int ntx, ntiles;
@@ -50,141 +65,376 @@ struct StageArgs {
   FlowPartial* part;
 };
 
-template <typename R>
-__device__ __forceinline__ R ldcg(const R* p) {
-  return __ldcg(p);
+// 1 / |n| for the unit-length projection: FP32 uses the hardware reciprocal square
+// root refined by one Newton-Raphson step (y <- y (3 - x y^2) / 2), FP64 divides.
+__device__ __forceinline__ float inv_norm(float x) {
+  float y = rsqrtf(x);
+  return y * (1.5f - 0.5f * x * y * y);
+}
+__device__ __forceinline__ double inv_norm(double x) { return 1.0 / sqrt(x); }
+
+template <int C, typename R>
+__device__ __forceinline__ void normalise(R* y) {
+  const R s = inv_norm(y[0] * y[0] + y[1] * y[1] + y[2] * y[2]);
+#pragma unroll
+  for (int c = 0; c < C; ++c) y[c] *= s;
 }
 
-template <int TH, typename R, int STAGE>
-__global__ void __launch_bounds__(NT) k_stage(StageArgs<R> a) {
+// Sliding 5-row window over one component plane of the shared tile, for one
+// column. MIX keeps the x-stencil of all five rows for the mixed derivative.
+template <typename R, bool MIX>
+struct Win {
+  R c[5];   // centre values of rows y-2 .. y+2
+  R g[5];   // MIX: unscaled Eq. 1 along x of rows y-2 .. y+2
+  R xx[5];  // MIX: unscaled Eq. 2 along x of rows y-2 .. y+2
+
+  __device__ __forceinline__ void enter(const R* P, int slot) {  // P points at the row's centre
+    const R ce = P[0];
+    c[slot] = ce;
+    if (MIX) {
+      const R m2 = P[-2], m1 = P[-1], p1 = P[1], p2 = P[2];
+      g[slot] = R(8) * (p1 - m1) - (p2 - m2);
+      xx[slot] = R(16) * ((p1 - ce) + (m1 - ce)) - ((p2 - ce) + (m2 - ce));
+    }
+  }
+  __device__ __forceinline__ void shift() {
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      c[s] = c[s + 1];
+      if (MIX) { g[s] = g[s + 1]; xx[s] = xx[s + 1]; }
+    }
+  }
+  // Derivatives at the window's centre row; Pc points at that row's centre.
+  template <bool SECOND>
+  __device__ __forceinline__ void derivs(const R* Pc, const Spacing<R>& h, R& v, R& fx, R& fy, R& fxx, R& fyy,
+                                         R& fxy) const {
+    const R ce = c[2];
+    v = ce;
+    R gx, gxx;
+    if (MIX) {
+      gx = g[2];
+      gxx = xx[2];
+    } else {
+      const R m2 = Pc[-2], m1 = Pc[-1], p1 = Pc[1], p2 = Pc[2];
+      gx = R(8) * (p1 - m1) - (p2 - m2);
+      gxx = R(16) * ((p1 - ce) + (m1 - ce)) - ((p2 - ce) + (m2 - ce));
+    }
+    fx = gx * h.i12dx;                                       // Eq. 1, x
+    fy = (R(8) * (c[3] - c[1]) - (c[4] - c[0])) * h.i12dy;  // Eq. 1, y
+    if (SECOND) {
+      fxx = gxx * h.i12dx2;                                                                  // Eq. 2, x
+      fyy = (R(16) * ((c[3] - ce) + (c[1] - ce)) - ((c[4] - ce) + (c[0] - ce))) * h.i12dy2;  // Eq. 2, y
+    } else {
+      fxx = fyy = R(0);
+    }
+    fxy = MIX ? (R(8) * (g[3] - g[1]) - (g[4] - g[0])) * h.i144dxdy : R(0);  // Eq. 1 in y of Eq. 1 in x
+  }
+};
+
+// Window set of one stage input: all C components, mixed derivatives for the gauge
+// field of the Abelian Higgs model (components 2, 3).
+template <int TH, typename R>
+struct StageWin {
+  static constexpr int C = NComp<TH>::C;
+  static constexpr int SXY = FlowTile<R>::SXY;
+  Win<R, false> w0, w1;
+  Win<R, TH == TH_AH> w2;
+  Win<R, TH == TH_AH> w3;  // unused for the chiral magnet
+
+  __device__ __forceinline__ void enter(const R* tiles, int off, int slot) {
+    w0.enter(tiles + off, slot);
+    w1.enter(tiles + SXY + off, slot);
+    w2.enter(tiles + 2 * SXY + off, slot);
+    if (C == 4) w3.enter(tiles + 3 * SXY + off, slot);
+  }
+  __device__ __forceinline__ void shift() {
+    w0.shift();
+    w1.shift();
+    w2.shift();
+    if (C == 4) w3.shift();
+  }
+  __device__ __forceinline__ void derivs(const R* tiles, int off, const Spacing<R>& h, R* v, R* fx, R* fy, R* fxx,
+                                         R* fyy, R* fxy) const {
+    w0.template derivs<true>(tiles + off, h, v[0], fx[0], fy[0], fxx[0], fyy[0], fxy[0]);
+    w1.template derivs<true>(tiles + SXY + off, h, v[1], fx[1], fy[1], fxx[1], fyy[1], fxy[1]);
+    w2.template derivs<true>(tiles + 2 * SXY + off, h, v[2], fx[2], fy[2], fxx[2], fyy[2], fxy[2]);
+    if (C == 4) w3.template derivs<true>(tiles + 3 * SXY + off, h, v[3], fx[3], fy[3], fxx[3], fyy[3], fxy[3]);
+  }
+};
+
+// First derivatives only (the field difference of the arrest test).
+template <int TH, typename R>
+struct DiffWin {
+  static constexpr int C = NComp<TH>::C;
+  static constexpr int SXY = FlowTile<R>::SXY;
+  Win<R, false> w[C];
+  __device__ __forceinline__ void enter(const R* tiles, int off, int slot) {
+#pragma unroll
+    for (int c = 0; c < C; ++c) w[c].enter(tiles + c * SXY + off, slot);
+  }
+  __device__ __forceinline__ void shift() {
+#pragma unroll
+    for (int c = 0; c < C; ++c) w[c].shift();
+  }
+  __device__ __forceinline__ void derivs(const R* tiles, int off, const Spacing<R>& h, R* v, R* fx, R* fy) const {
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      R unused0, unused1, unused2;
+      w[c].template derivs<false>(tiles + c * SXY + off, h, v[c], fx[c], fy[c], unused0, unused1, unused2);
+    }
+  }
+};
+
+template <int TH, typename R>
+__device__ __forceinline__ void force_at(const Couplings<R>& k, const R* v, const R* fx, const R* fy, const R* fxx,
+                                         const R* fyy, const R* fxy, R* G) {
+  if (TH == TH_AH) force_ah<R>(k, v, fx, fy, fxx, fyy, fxy, G);
+  else force_cm<R>(k, v, fx, fy, fxx, fyy, G);
+}
+
+template <int TH, typename R, int PASS>
+__global__ void __launch_bounds__(NT) k_pass(PassArgs<R> a) {
+  using T = FlowTile<R>;
   constexpr int C = NComp<TH>::C;
-  __shared__ R sY[C][SY * SX];
-  __shared__ double sred[(NT / 32) * 3];
+  constexpr int RY = T::RY;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  R* sm = reinterpret_cast<R*>(smraw);  // pass A: [Y1 | Y2 | delta][C][SXY]; pass B: [Y3 | Y4][C][SXY]
+  __shared__ double sred[RedSmem<2, 1>::n];
   __shared__ int s_last;
 
   DevState* st = a.st;
-  // Uniform over the grid (the record only changes between launches). Stage 1 runs
-  // once per field; stages 2-4 stop at convergence, at a non-finite value and at
-  // the step limit of the current call.
+  // Uniform over the grid (the record only changes between launches). Pass A runs
+  // once per field; pass B stops at convergence, at a non-finite value and at the
+  // step limit of the current call.
   if (st->converged | st->nonfinite) return;
-  if (STAGE == 1 ? (st->head_step == st->steps) : (st->steps >= st->step_limit)) return;
+  if (PASS == 1 ? (st->head_step == st->steps) : (st->steps >= st->step_limit)) return;
   const int tid = threadIdx.y * BX + threadIdx.x;
-  const bool arrest = (STAGE > 1) && (st->arrest != 0);
-  const R cv = arrest ? R(0) : (STAGE == 4 ? a.dt : R(0.5) * a.dt);
-  const R ck = STAGE == 3 ? R(0.25) * a.dt * a.dt : R(0.5) * a.dt * a.dt;
+  const bool arrest = (PASS == 2) && (st->arrest != 0);
+  const bool has_prev = (PASS == 1) && (st->steps > 0);
   const size_t P = a.plane;
+  const R dt = a.dt, hdt = R(0.5) * a.dt;
+  const R c3 = R(0.25) * dt * dt, c4 = R(0.5) * dt * dt;
+  R* const set0 = sm;
+  R* const set1 = sm + C * T::SXY;
+  R* const set2 = sm + 2 * C * T::SXY;
 
-  // Per-thread compensated pair in the working type; widened to FP64 once per
-  // thread (the pair keeps the sum to O(n eps^2), so FP32 loses nothing material
-  // over the few dozen sites a thread owns).
-  R es = R(0), ec = R(0), gmr = R(0);
+  R es = R(0), ec = R(0), ds = R(0), dc = R(0), gmr = R(0);
 
   for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
-    const int x0 = (t % a.ntx) * TX, y0 = (t / a.ntx) * TY;
+    const int x0 = (t % a.ntx) * T::TX, y0 = (t / a.ntx) * T::TY;
     __syncthreads();  // the previous tile's shared reads are finished
-    for (int idx = tid; idx < SX * SY; idx += NT) {
-      const int lx = idx % SX, ly = idx / SX;
-      const int gx = x0 + lx - HALO, gy = y0 + ly - HALO;
-      R y[C];
+    // ---- stage inputs over the tile and its halo
+    int ly = tid / T::SX, lx = tid - ly * T::SX;
+    for (int idx = tid; idx < T::SXY; idx += NT) {
+      const int gx = x0 + lx - 2, gy = y0 + ly - 2;
+      R y0v[C], y1v[C], y2v[C];
       if (gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny) {
         const size_t s = (size_t)gy * a.nx + gx;
+        const bool inside = gx >= 2 && gx < a.nx - 2 && gy >= 2 && gy < a.ny - 2;
+        R p[C];
 #pragma unroll
-        for (int c = 0; c < C; ++c) y[c] = a.phi[c * P + s];
-        // Halo sites have v = k_v = 0: their stage input is phi itself.
-        if (STAGE > 1 && gx >= HALO && gx < a.nx - HALO && gy >= HALO && gy < a.ny - HALO) {
+        for (int c = 0; c < C; ++c) p[c] = a.phi[c * P + s];
+        if (PASS == 1) {
 #pragma unroll
           for (int c = 0; c < C; ++c) {
-            R u = y[c];
-            if (!arrest) u += cv * a.v[c * P + s];
-            if (STAGE > 2) u += ck * a.kvin[c * P + s];
-            y[c] = u;
+            y0v[c] = p[c];
+            y2v[c] = has_prev ? p[c] - a.phi_prev[c * P + s] : R(0);
+            y1v[c] = inside ? p[c] + hdt * a.v[c * P + s] : p[c];  // halo: v = 0
           }
-          if (TH == TH_CM) {
-            const R inv = rsqrt_t<R>(y[0] * y[0] + y[1] * y[1] + y[2] * y[2]);
+          if (TH == TH_CM && inside) normalise<C>(y1v);
+        } else {
+          if (inside) {
 #pragma unroll
-            for (int c = 0; c < C; ++c) y[c] *= inv;
+            for (int c = 0; c < C; ++c) {
+              const R vv = arrest ? R(0) : a.v[c * P + s];
+              const R k1 = a.kv1[c * P + s];
+              const R k2 = arrest ? k1 : a.kv2[c * P + s];
+              y0v[c] = p[c] + hdt * vv + c3 * k1;
+              y1v[c] = p[c] + dt * vv + c4 * k2;
+            }
+            if (TH == TH_CM) {
+              normalise<C>(y0v);
+              normalise<C>(y1v);
+            }
+          } else {
+#pragma unroll
+            for (int c = 0; c < C; ++c) y0v[c] = y1v[c] = p[c];
           }
         }
       } else {
 #pragma unroll
-        for (int c = 0; c < C; ++c) y[c] = R(0);
+        for (int c = 0; c < C; ++c) y0v[c] = y1v[c] = y2v[c] = R(0);
       }
 #pragma unroll
-      for (int c = 0; c < C; ++c) sY[c][idx] = y[c];
+      for (int c = 0; c < C; ++c) {
+        set0[c * T::SXY + idx] = y0v[c];
+        set1[c * T::SXY + idx] = y1v[c];
+        if (PASS == 1) set2[c * T::SXY + idx] = y2v[c];
+      }
+      lx += NT % T::SX;
+      ly += NT / T::SX;
+      if (lx >= T::SX) { lx -= T::SX; ++ly; }
     }
     __syncthreads();
 
+    // ---- column walk: RY rows of column threadIdx.x
+    const int sx = threadIdx.x + 2, sy0 = threadIdx.y * RY + 2;
+    const int gx = x0 + threadIdx.x, gyb = y0 + threadIdx.y * RY;
+    const bool colok = gx >= 2 && gx < a.nx - 2;
+
+    if (PASS == 1) {
+      // stage 1 at Y_1 = phi: k_v1, e, max|G|, and e(phi^n) - e(phi^{n-1})
+      {
+        StageWin<TH, R> W;
+        DiffWin<TH, R> D;
 #pragma unroll
-    for (int r = 0; r < ROWS_PER_THREAD; ++r) {
-      const int lx = threadIdx.x, ly = threadIdx.y + r * BY;
-      const int gx = x0 + lx, gy = y0 + ly;
-      if (gx < HALO || gx >= a.nx - HALO || gy < HALO || gy >= a.ny - HALO) continue;
-      const int sx = lx + HALO, sy = ly + HALO;
-      R v[C], fx[C], fy[C], fxx[C], fyy[C], fxy[C];
+        for (int s = 0; s < 5; ++s) {
+          const int off = (sy0 - 2 + s) * T::SX + sx;
+          W.enter(set0, off, s);
+          if (has_prev) D.enter(set2, off, s);
+        }
 #pragma unroll
-      for (int c = 0; c < C; ++c) {
-        const Deriv<R> d = (TH == TH_AH && c >= 2) ? stencil<R, true, true>(sY[c], sx, sy, a.h)
-                                                   : stencil<R, true, false>(sY[c], sx, sy, a.h);
-        v[c] = d.v; fx[c] = d.fx; fy[c] = d.fy; fxx[c] = d.fxx; fyy[c] = d.fyy; fxy[c] = d.fxy;
-      }
-      R G[C];
-      if (TH == TH_AH) force_ah<R>(a.k, v, fx, fy, fxx, fyy, fxy, G);
-      else force_cm<R>(a.k, v, fx, fy, fxx, fyy, G);
-      const size_t s = (size_t)gy * a.nx + gx;
-      if (STAGE == 1) {
-        const R e = (TH == TH_AH) ? density_ah<R>(a.k, v, fx, fy) : density_cm<R>(a.k, v, fx, fy);
-        const R t = es + e;
-        ec += (fabs(es) >= fabs(e)) ? (es - t) + e : (e - t) + es;
-        es = t;
+        for (int r = 0; r < RY; ++r) {
+          const int off = (sy0 + r) * T::SX + sx;
+          const bool ok = colok && gyb + r >= 2 && gyb + r < a.ny - 2;
+          R v[C], fx[C], fy[C], fxx[C], fyy[C], fxy[C], G[C];
+          W.derivs(set0, off, a.h, v, fx, fy, fxx, fyy, fxy);
+          force_at<TH, R>(a.k, v, fx, fy, fxx, fyy, fxy, G);
+          if (ok) {
+            const size_t s = (size_t)(gyb + r) * a.nx + gx;
 #pragma unroll
-        for (int c = 0; c < C; ++c) {
-          const R ag = fabs(G[c]);
-          gmr = (ag > gmr || ag != ag) ? ag : gmr;
+            for (int c = 0; c < C; ++c) {
+              a.kv1_out[c * P + s] = -G[c];
+              const R ag = fabs(G[c]);
+              gmr = (ag > gmr || ag != ag) ? ag : gmr;
+            }
+            const R e = (TH == TH_AH) ? density_ah<R>(a.k, v, fx, fy) : density_cm<R>(a.k, v, fx, fy);
+            const R t1 = es + e;
+            ec += (fabs(es) >= fabs(e)) ? (es - t1) + e : (e - t1) + es;
+            es = t1;
+          }
+          if (has_prev) {
+            R d[C], dxv[C], dyv[C];
+            D.derivs(set2, off, a.h, d, dxv, dyv);
+            if (ok) {
+              const R de = (TH == TH_AH) ? delta_density_ah<R>(a.k, v, fx, fy, d, dxv, dyv)
+                                         : delta_density_cm<R>(a.k, v, fx, fy, d, dxv, dyv);
+              const R t2 = ds + de;
+              dc += (fabs(ds) >= fabs(de)) ? (ds - t2) + de : (de - t2) + ds;
+              ds = t2;
+            }
+          }
+          if (r + 1 < RY) {
+            const int noff = (sy0 + r + 3) * T::SX + sx;
+            W.shift();
+            W.enter(set0, noff, 4);
+            if (has_prev) {
+              D.shift();
+              D.enter(set2, noff, 4);
+            }
+          }
         }
       }
-      if (STAGE < 4) {
+      // stage 2 at Y_2 = phi + dt/2 v: k_v2
+      {
+        StageWin<TH, R> W;
 #pragma unroll
-        for (int c = 0; c < C; ++c) a.kv_out[c * P + s] = -G[c];
-      } else {
-        const R dt = a.dt, w = dt * dt / R(6), u = dt / R(6);
-        R pn[C], vn[C];
+        for (int s = 0; s < 5; ++s) W.enter(set1, (sy0 - 2 + s) * T::SX + sx, s);
 #pragma unroll
-        for (int c = 0; c < C; ++c) {
-          const R p0 = a.phi[c * P + s];
-          const R v0 = arrest ? R(0) : a.v[c * P + s];
-          const R k1 = a.kv1[c * P + s], k2 = a.kv2[c * P + s], k3 = a.kv3[c * P + s], k4 = -G[c];
-          pn[c] = p0 + dt * v0 + w * (k1 + k2 + k3);
-          vn[c] = v0 + u * (k1 + R(2) * (k2 + k3) + k4);
+        for (int r = 0; r < RY; ++r) {
+          const int off = (sy0 + r) * T::SX + sx;
+          R v[C], fx[C], fy[C], fxx[C], fyy[C], fxy[C], G[C];
+          W.derivs(set1, off, a.h, v, fx, fy, fxx, fyy, fxy);
+          force_at<TH, R>(a.k, v, fx, fy, fxx, fyy, fxy, G);
+          if (colok && gyb + r >= 2 && gyb + r < a.ny - 2) {
+            const size_t s = (size_t)(gyb + r) * a.nx + gx;
+#pragma unroll
+            for (int c = 0; c < C; ++c) a.kv2_out[c * P + s] = -G[c];
+          }
+          if (r + 1 < RY) {
+            W.shift();
+            W.enter(set1, (sy0 + r + 3) * T::SX + sx, 4);
+          }
         }
-        if (TH == TH_CM) {
-          const R inv = rsqrt_t<R>(pn[0] * pn[0] + pn[1] * pn[1] + pn[2] * pn[2]);
+      }
+    } else {
+      // stage 3 at Y_3: k_v3 kept in registers
+      R k3[RY][C];
+      {
+        StageWin<TH, R> W;
 #pragma unroll
-          for (int c = 0; c < C; ++c) pn[c] *= inv;
-          const R vp = vn[0] * pn[0] + vn[1] * pn[1] + vn[2] * pn[2];
+        for (int s = 0; s < 5; ++s) W.enter(set0, (sy0 - 2 + s) * T::SX + sx, s);
 #pragma unroll
-          for (int c = 0; c < C; ++c) vn[c] -= vp * pn[c];
+        for (int r = 0; r < RY; ++r) {
+          const int off = (sy0 + r) * T::SX + sx;
+          R v[C], fx[C], fy[C], fxx[C], fyy[C], fxy[C], G[C];
+          W.derivs(set0, off, a.h, v, fx, fy, fxx, fyy, fxy);
+          force_at<TH, R>(a.k, v, fx, fy, fxx, fyy, fxy, G);
+#pragma unroll
+          for (int c = 0; c < C; ++c) k3[r][c] = -G[c];
+          if (r + 1 < RY) {
+            W.shift();
+            W.enter(set0, (sy0 + r + 3) * T::SX + sx, 4);
+          }
         }
+      }
+      // stage 4 at Y_4, then the RK4 combination
+      {
+        StageWin<TH, R> W;
 #pragma unroll
-        for (int c = 0; c < C; ++c) {
-          a.phi_out[c * P + s] = pn[c];
-          a.v_out[c * P + s] = vn[c];
+        for (int s = 0; s < 5; ++s) W.enter(set1, (sy0 - 2 + s) * T::SX + sx, s);
+        const R w6 = dt * dt / R(6), u6 = dt / R(6);
+#pragma unroll
+        for (int r = 0; r < RY; ++r) {
+          const int off = (sy0 + r) * T::SX + sx;
+          R v[C], fx[C], fy[C], fxx[C], fyy[C], fxy[C], G[C];
+          W.derivs(set1, off, a.h, v, fx, fy, fxx, fyy, fxy);
+          force_at<TH, R>(a.k, v, fx, fy, fxx, fyy, fxy, G);
+          if (colok && gyb + r >= 2 && gyb + r < a.ny - 2) {
+            const size_t s = (size_t)(gyb + r) * a.nx + gx;
+            R pn[C], vn[C];
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+              const R p0 = a.phi[c * P + s];
+              const R v0 = arrest ? R(0) : a.v[c * P + s];
+              const R k1 = a.kv1[c * P + s];
+              const R k2 = arrest ? k1 : a.kv2[c * P + s];
+              const R k4 = -G[c];
+              pn[c] = p0 + dt * v0 + w6 * (k1 + k2 + k3[r][c]);
+              vn[c] = v0 + u6 * (k1 + R(2) * (k2 + k3[r][c]) + k4);
+            }
+            if (TH == TH_CM) {
+              normalise<C>(pn);
+              const R vp = vn[0] * pn[0] + vn[1] * pn[1] + vn[2] * pn[2];
+#pragma unroll
+              for (int c = 0; c < C; ++c) vn[c] -= vp * pn[c];
+            }
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+              a.phi_out[c * P + s] = pn[c];
+              a.v_out[c * P + s] = vn[c];
+            }
+          }
+          if (r + 1 < RY) {
+            W.shift();
+            W.enter(set1, (sy0 + r + 3) * T::SX + sx, 4);
+          }
         }
       }
     }
   }
 
-  if (STAGE == 4) {
+  if (PASS == 2) {
     if (blockIdx.x == 0 && tid == 0) st->steps += 1;  // single writer; read after this launch
     return;
   }
-  if (STAGE != 1) return;
 
   // ---- energy / residual reduction and the on-device arrest + convergence decision
-  DD sv[1] = {DD{(double)es, (double)ec}};
+  DD sv[2] = {DD{(double)es, (double)ec}, DD{(double)ds, (double)dc}};
   double mv[1] = {(double)gmr};
-  block_reduce<1, 1>(sv, mv, sred);
+  block_reduce<2, 1>(sv, mv, sred);
   if (tid == 0) {
-    a.part[blockIdx.x] = FlowPartial{sv[0].s, sv[0].c, mv[0], 0.0};
+    a.part[blockIdx.x] = FlowPartial{sv[0].s, sv[0].c, sv[1].s, sv[1].c, mv[0], {0.0, 0.0, 0.0}};
     __threadfence();
     const unsigned prev = atomicAdd(&st->ticket, 1u);
     s_last = (prev == gridDim.x - 1);
@@ -192,27 +442,31 @@ __global__ void __launch_bounds__(NT) k_stage(StageArgs<R> a) {
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  DD acc{0.0, 0.0};
+  DD acc{0.0, 0.0}, dacc{0.0, 0.0};
   double mm = 0.0;
   for (int i = tid; i < (int)gridDim.x; i += NT) {
-    const double ps = ldcg(&a.part[i].s), pc = ldcg(&a.part[i].c), pm = ldcg(&a.part[i].m);
-    acc = dd_add(acc, DD{ps, pc});
-    mm = nanmax(mm, pm);
+    const FlowPartial* q = a.part + i;
+    acc = dd_add(acc, DD{__ldcg(&q->es), __ldcg(&q->ec)});
+    dacc = dd_add(dacc, DD{__ldcg(&q->ds), __ldcg(&q->dc)});
+    mm = nanmax(mm, __ldcg(&q->m));
   }
-  DD sv2[1] = {acc};
+  DD sv2[2] = {acc, dacc};
   double mv2[1] = {mm};
-  block_reduce<1, 1>(sv2, mv2, sred);
+  block_reduce<2, 1>(sv2, mv2, sred);
   if (tid == 0) {
     const double E = a.area * (sv2[0].s + sv2[0].c);
+    const double dE = a.area * (sv2[1].s + sv2[1].c);
     const double g = a.area * mv2[0];
-    const int arr = (E > st->E_last) ? 1 : 0;  // Eq. 4, strict
+    // Eq. 4, strict: E_h(phi^n) > E_h(phi^{n-1}); no previous field (E_last = +inf): no arrest
+    const int arr = has_prev ? (dE > 0.0 ? 1 : 0) : (E > st->E_last ? 1 : 0);
     st->E_cur = E;
+    st->dE = has_prev ? dE : 0.0;
     st->gmax = g;
     st->arrest = arr;
     st->arrests += arr;
     st->E_last = E;
     st->converged = (g < st->tol) ? 1 : 0;
-    st->nonfinite = (isfinite(E) && isfinite(g)) ? 0 : 1;
+    st->nonfinite = (isfinite(E) && isfinite(g) && isfinite(dE)) ? 0 : 1;
     st->head_step = st->steps;
     st->ticket = 0;
   }
@@ -222,6 +476,7 @@ __global__ void __launch_bounds__(NT) k_stage(StageArgs<R> a) {
 __global__ void k_reset_state(DevState* st) {
   st->E_last = __longlong_as_double(0x7ff0000000000000LL);  // +inf: no arrest on the first step
   st->E_cur = 0.0;
+  st->dE = 0.0;
   st->gmax = 0.0;
   st->tol = -1.0;
   st->steps = 0;
@@ -250,24 +505,29 @@ __global__ void k_scaled_copy(R* __restrict__ out, const R* __restrict__ in, siz
 }
 
 // ------------------------------------------------------------------ launchers
+template <int TH, typename R>
+static size_t pass_smem(int pass) {
+  return (size_t)(pass == 1 ? 3 : 2) * NComp<TH>::C * FlowTile<R>::SXY * sizeof(R);
+}
+
 template <typename R>
-static StageArgs<R> make_args(const LaunchCtx& c, int stage, int cur) {
-  StageArgs<R> a{};
+static PassArgs<R> make_args(const LaunchCtx& c, int cur) {
+  PassArgs<R> a{};
   const int nxt = cur ^ 1;
   a.phi = static_cast<const R*>(c.phi[cur]);
+  a.phi_prev = static_cast<const R*>(c.phi[nxt]);
   a.v = static_cast<const R*>(c.v[cur]);
-  a.kvin = stage == 3 ? static_cast<const R*>(c.kv[0]) : static_cast<const R*>(c.kv[1]);
   a.kv1 = static_cast<const R*>(c.kv[0]);
   a.kv2 = static_cast<const R*>(c.kv[1]);
-  a.kv3 = static_cast<const R*>(c.kv[2]);
-  a.kv_out = stage <= 3 ? static_cast<R*>(c.kv[stage - 1]) : nullptr;
+  a.kv1_out = static_cast<R*>(c.kv[0]);
+  a.kv2_out = static_cast<R*>(c.kv[1]);
   a.phi_out = static_cast<R*>(c.phi[nxt]);
   a.v_out = static_cast<R*>(c.v[nxt]);
   a.nx = c.nx;
   a.ny = c.ny;
   a.plane = c.plane;
-  a.ntx = c.ntiles_x;
-  a.ntiles = c.ntiles_x * c.ntiles_y;
+  a.ntx = (c.nx + FlowTile<R>::TX - 1) / FlowTile<R>::TX;
+  a.ntiles = a.ntx * ((c.ny + FlowTile<R>::TY - 1) / FlowTile<R>::TY);
   a.dt = (R)c.dt;
   a.h.i12dx = (R)(1.0 / (12.0 * c.dx));
   a.h.i12dy = (R)(1.0 / (12.0 * c.dy));
@@ -282,22 +542,18 @@ static StageArgs<R> make_args(const LaunchCtx& c, int stage, int cur) {
 }
 
 template <int TH, typename R>
-static cudaError_t stage_t(const LaunchCtx& c, int stage, int cur, cudaStream_t s) {
-  const StageArgs<R> a = make_args<R>(c, stage, cur);
+static cudaError_t pass_t(const LaunchCtx& c, int pass, int cur, cudaStream_t s) {
+  const PassArgs<R> a = make_args<R>(c, cur);
   const dim3 blk(BX, BY);
-  switch (stage) {
-    case 1: k_stage<TH, R, 1><<<c.flow_blocks, blk, 0, s>>>(a); break;
-    case 2: k_stage<TH, R, 2><<<c.flow_blocks, blk, 0, s>>>(a); break;
-    case 3: k_stage<TH, R, 3><<<c.flow_blocks, blk, 0, s>>>(a); break;
-    case 4: k_stage<TH, R, 4><<<c.flow_blocks, blk, 0, s>>>(a); break;
-    default: return cudaErrorInvalidValue;
-  }
+  if (pass == 1) k_pass<TH, R, 1><<<c.flow_blocks, blk, pass_smem<TH, R>(1), s>>>(a);
+  else if (pass == 2) k_pass<TH, R, 2><<<c.flow_blocks, blk, pass_smem<TH, R>(2), s>>>(a);
+  else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 
-cudaError_t launch_stage(const LaunchCtx& c, int stage, int cur, cudaStream_t s) {
-  if (c.theory == TH_AH) return c.prec == 1 ? stage_t<TH_AH, float>(c, stage, cur, s) : stage_t<TH_AH, double>(c, stage, cur, s);
-  return c.prec == 1 ? stage_t<TH_CM, float>(c, stage, cur, s) : stage_t<TH_CM, double>(c, stage, cur, s);
+cudaError_t launch_pass(const LaunchCtx& c, int pass, int cur, cudaStream_t s) {
+  if (c.theory == TH_AH) return c.prec == 1 ? pass_t<TH_AH, float>(c, pass, cur, s) : pass_t<TH_AH, double>(c, pass, cur, s);
+  return c.prec == 1 ? pass_t<TH_CM, float>(c, pass, cur, s) : pass_t<TH_CM, double>(c, pass, cur, s);
 }
 
 cudaError_t launch_reset_state(const LaunchCtx& c, cudaStream_t s) {
@@ -322,27 +578,33 @@ cudaError_t launch_scaled_copy(const LaunchCtx& c, void* out, const void* in, do
   return cudaGetLastError();
 }
 
+// Opt the pass kernels into their dynamic shared memory, then size the grid by
+// the smaller occupancy of the two passes.
 template <int TH, typename R>
-static int occupancy_min() {
-  int b1 = 0, b2 = 0, b3 = 0, b4 = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_stage<TH, R, 1>, NT, 0);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_stage<TH, R, 2>, NT, 0);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b3, k_stage<TH, R, 3>, NT, 0);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b4, k_stage<TH, R, 4>, NT, 0);
-  int m = b1;
-  if (b2 < m) m = b2;
-  if (b3 < m) m = b3;
-  if (b4 < m) m = b4;
+static int pass_occupancy() {
+  cudaFuncSetAttribute(k_pass<TH, R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pass_smem<TH, R>(1));
+  cudaFuncSetAttribute(k_pass<TH, R, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pass_smem<TH, R>(2));
+  int b1 = 0, b2 = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_pass<TH, R, 1>, NT, pass_smem<TH, R>(1));
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_pass<TH, R, 2>, NT, pass_smem<TH, R>(2));
+  const int m = b1 < b2 ? b1 : b2;
   return m < 1 ? 1 : m;
 }
 
-int flow_grid(int theory, int prec, int ntiles) {
+int flow_grid(int theory, int prec, int nx, int ny) {
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  int occ;
-  if (theory == TH_AH) occ = prec == 1 ? occupancy_min<TH_AH, float>() : occupancy_min<TH_AH, double>();
-  else occ = prec == 1 ? occupancy_min<TH_CM, float>() : occupancy_min<TH_CM, double>();
+  int occ, ntiles;
+  if (prec == 1) {
+    occ = theory == TH_AH ? pass_occupancy<TH_AH, float>() : pass_occupancy<TH_CM, float>();
+    ntiles = ((nx + FlowTile<float>::TX - 1) / FlowTile<float>::TX) *
+             ((ny + FlowTile<float>::TY - 1) / FlowTile<float>::TY);
+  } else {
+    occ = theory == TH_AH ? pass_occupancy<TH_AH, double>() : pass_occupancy<TH_CM, double>();
+    ntiles = ((nx + FlowTile<double>::TX - 1) / FlowTile<double>::TX) *
+             ((ny + FlowTile<double>::TY - 1) / FlowTile<double>::TY);
+  }
   const int g = nsm * occ;
   return ntiles < g ? ntiles : g;
 }

@@ -18,7 +18,7 @@ struct LaunchCtx {
   double coup[10]; // Couplings layout of ss_device.cuh, in FP64
   void* phi[2];    // ping-pong field buffers [C][ny][nx]
   void* v[2];      // ping-pong velocity buffers
-  void* kv[3];     // RK stage accelerations k_v1..k_v3
+  void* kv[2];     // RK stage accelerations k_v1, k_v2 (k_v3, k_v4 never leave registers)
   DevState* st;
   FlowPartial* fpart;
   ObsPartial* opart;
@@ -27,13 +27,14 @@ struct LaunchCtx {
   int ntiles_x, ntiles_y;
 };
 
-// Stage s in 1..4 of the RK4 step whose current field is phi[cur] (Sec. 3.2).
-cudaError_t launch_stage(const LaunchCtx& c, int stage, int cur, cudaStream_t s);
+// Pass 1 (RK stages 1-2 + reductions + arrest decision) or pass 2 (stages 3-4 +
+// combination) of the RK4 step whose current field is phi[cur] (Sec. 3.2).
+cudaError_t launch_pass(const LaunchCtx& c, int pass, int cur, cudaStream_t s);
 // Control kernels: reset the flow record for new fields; start a run with a
 // convergence threshold (tol < 0: none) and a budget of max_steps further steps.
 cudaError_t launch_reset_state(const LaunchCtx& c, cudaStream_t s);
 cudaError_t launch_set_run(const LaunchCtx& c, double tol, long long max_steps, cudaStream_t s);
-// out = -kv1 (the force G at the head field), optionally zeroing (for velocity).
+// out = scale * in over the C planes of a context.
 cudaError_t launch_scaled_copy(const LaunchCtx& c, void* out, const void* in, double scale, cudaStream_t s);
 // Observables of phi[cur] in FP64 (energy, charge, flux, residual, |n|-1).
 cudaError_t launch_observables(const LaunchCtx& c, int cur, cudaStream_t s);
@@ -41,7 +42,7 @@ cudaError_t launch_observables(const LaunchCtx& c, int cur, cudaStream_t s);
 cudaError_t launch_ansatz(const LaunchCtx& c, const double* d_sol, int n, cudaStream_t s);
 
 // Flow-kernel grid size for a context (occupancy x SMs, capped by the tile count).
-int flow_grid(int theory, int prec, int ntiles);
+int flow_grid(int theory, int prec, int nx, int ny);
 int obs_grid(int theory, int prec, int ntiles);
 
 }  // namespace ss

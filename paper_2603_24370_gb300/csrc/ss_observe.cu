@@ -43,7 +43,7 @@ template <int TH, typename R>
 __global__ void __launch_bounds__(NT) k_observables(ObsArgs<R> a) {
   constexpr int C = NComp<TH>::C;
   __shared__ double sY[C][SY * SX];
-  __shared__ double sred[(NT / 32) * 8];
+  __shared__ double sred[RedSmem<3, 2>::n];
   __shared__ int s_last;
   const int tid = threadIdx.y * BX + threadIdx.x;
   const size_t P = a.plane;
@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(NT) k_observables(ObsArgs<R> a) {
 template <typename R>
 __global__ void __launch_bounds__(NT) k_winding(const R* __restrict__ phi, int nx, int ny, size_t plane,
                                                 DevState* st) {
-  __shared__ double sred[(NT / 32) * 2];
+  __shared__ double sred[RedSmem<1, 1>::n];
   const int tid = threadIdx.y * BX + threadIdx.x;
   const int a = nx - 5, b = ny - 5, L = 2 * a + 2 * b;
   auto site = [&](int k, int& i, int& j) {

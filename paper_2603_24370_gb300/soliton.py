@@ -54,7 +54,8 @@ class ss_soliton(ctypes.Structure):
 
 class ss_status(ctypes.Structure):
     _fields_ = [("energy", ctypes.c_double), ("grad_max", ctypes.c_double), ("steps", ctypes.c_longlong),
-                ("arrests", ctypes.c_longlong), ("converged", ctypes.c_int), ("arrested", ctypes.c_int)]
+                ("arrests", ctypes.c_longlong), ("converged", ctypes.c_int), ("arrested", ctypes.c_int),
+                ("energy_change", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -203,8 +204,10 @@ def ss_observables(ctx) -> dict:
 
 
 def ss_profile_stages(ctx, n_steps: int) -> list[float]:
-    """Mean device milliseconds of RK stages 1..4 over n_steps real flow steps."""
-    ms = (ctypes.c_float * 4)()
+    """Mean device milliseconds of the step's two kernels (pass 1: RK stages 1-2 +
+    reductions + arrest decision; pass 2: RK stages 3-4 + combination) over n_steps
+    real flow steps."""
+    ms = (ctypes.c_float * 2)()
     _check(load_library().ss_profile_stages(ctx, int(n_steps), ms))
     return [float(x) for x in ms]
 
