@@ -179,6 +179,42 @@ int ss_profile_stages(ss_ctx* ctx, int n_steps, float* ms_out);
 /* Release every device and host resource of the context (NULL is a no-op). */
 int ss_destroy(ss_ctx* ctx);
 
+/* Observables of a caller-owned device field without allocating anything.
+ *
+ * The paper has no counterpart: this entry point exists for callers that cannot
+ * call cudaMalloc -- code whose device memory belongs to a framework's caching
+ * allocator or to a fixed arena that must account for every byte, and code where
+ * an allocation would implicitly synchronize the device or could fail because the
+ * device memory is already fully reserved. It computes exactly what ss_observables
+ * computes (same kernels, same FP64 compensated reductions) for the field at
+ * `fields`, without a context, and calls no cudaMalloc, cudaFree or allocating
+ * library routine.
+ *
+ *  theory, params, n_params: as ss_set_theory.
+ *  fields:    device pointer, [C][ny][nx] planes of the given precision (float for
+ *             SS_FP32, double for SS_FP64), halo included. Read only.
+ *  nx, ny, dx, dy: as ss_create_grid; nx, ny <= 65536 and nx * ny <= 2^31, larger
+ *             grids are rejected with SS_ERR_ARG.
+ *  out:       device pointer to 6 doubles, written with {energy, charge, flux,
+ *             grad_max, grad_max_raw, norm_dev} (the ss_obs fields of the same names).
+ *  cuda_stream: the stream to run on (NULL = legacy default stream). The call only
+ *             enqueues work: `out` is valid once that stream's work has completed.
+ *
+ * Scratch: the reduction's block partials, arrival counter and result record live
+ * in one file-scope device array of 128.25 KB (at most 2048 reducing blocks; the
+ * kernel strides over tiles, so every allowed grid fits). Every GPU that loads the
+ * library holds this array until the process exits. All calls on a device share
+ * it and it keeps the last call's contents: each call clears the counter it needs
+ * zeroed, but calls whose GPU work overlaps (different streams or host threads
+ * without ordering between them) race on it and must be serialized by the caller.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.
+ *
+ * Errors: SS_ERR_ARG (NULL pointers, sizes, spacings, theory, params), SS_ERR_CUDA. */
+int ss_observables_noalloc(int theory, const double* params, int n_params, const void* fields, int nx, int ny,
+                           double dx, double dy, int precision, double* out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

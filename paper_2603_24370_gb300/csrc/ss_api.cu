@@ -39,6 +39,8 @@ int fail(int code, const std::string& msg) {
 
 }  // namespace
 
+void ss::set_last_error(const std::string& msg) { g_err = msg; }
+
 #define SS_CK(call)                                                                            \
   do {                                                                                         \
     cudaError_t e_ = (call);                                                                   \

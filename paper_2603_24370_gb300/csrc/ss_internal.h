@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include <string>
+
 #include "ss_device.cuh"
 
 namespace ss {
@@ -40,6 +42,9 @@ cudaError_t launch_scaled_copy(const LaunchCtx& c, void* out, const void* in, do
 cudaError_t launch_observables(const LaunchCtx& c, int cur, cudaStream_t s);
 // Ansatz of n solitons (device array of 5 doubles each) into both field buffers.
 cudaError_t launch_ansatz(const LaunchCtx& c, const double* d_sol, int n, cudaStream_t s);
+
+// Record the calling thread's error message for ss_last_error().
+void set_last_error(const std::string& msg);
 
 // Flow-kernel grid size for a context (occupancy x SMs, capped by the tile count).
 int flow_grid(int theory, int prec, int nx, int ny);

@@ -1,0 +1,148 @@
+// ss_noalloc.cu -- ss_observables_noalloc: the observables reduction for callers
+// that cannot allocate device memory.
+//
+// Some callers cannot call cudaMalloc: code whose device memory is owned by a
+// framework's caching allocator or a fixed arena that must account for every byte,
+// code running where an allocation would implicitly synchronize the device or could
+// fail (a latency-critical loop, a process whose device memory is already fully
+// reserved). For them this entry point evaluates the same observables as
+// ss_observables on a caller-owned device field, with the same kernels, but keeps
+// all of its scratch (the reduction's per-block partials, its arrival counter and
+// the result record) in one file-scope device array of fixed size. It allocates
+// nothing, neither through CUDA nor through any library.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "soliton.h"
+#include "ss_internal.h"
+
+using namespace ss;
+
+namespace {
+
+// At most this many thread blocks take part in the reduction (the kernel strides
+// over tiles, so any grid size fits). 2048 partials of 64 B plus the record: 128.25 KB.
+constexpr int NOALLOC_MAX_BLOCKS = 2048;
+constexpr size_t NOALLOC_RECORD_BYTES = (sizeof(DevState) + 255) & ~size_t(255);
+constexpr size_t NOALLOC_BYTES = NOALLOC_RECORD_BYTES + sizeof(ObsPartial) * NOALLOC_MAX_BLOCKS;
+constexpr int NOALLOC_MAX_DEVICES = 64;
+
+}  // namespace
+
+// The scratch. Every GPU that loads the library holds it until the process exits;
+// all calls on a device share it.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+namespace {
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {nullptr};
+
+// Copy the result record into the caller's output (grad_max = dx dy * max|G|).
+__global__ void k_noalloc_out(const DevState* st, double area, double* out) {
+  out[0] = st->obs_energy;
+  out[1] = st->obs_charge;
+  out[2] = st->obs_flux;
+  out[3] = area * st->obs_gmax_raw;
+  out[4] = st->obs_gmax_raw;
+  out[5] = st->obs_normdev;
+}
+
+// The message is reported by ss_last_error() like every other call's.
+int noalloc_fail(int code, const std::string& msg) {
+  set_last_error(msg);
+  return code;
+}
+
+}  // namespace
+
+extern "C" int ss_observables_noalloc(int theory, const double* params, int n_params, const void* fields, int nx,
+                                      int ny, double dx, double dy, int precision, double* out, void* cuda_stream) {
+  if (!fields || !out) return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: fields and out must be device pointers");
+  if (nx < 5 || ny < 5) return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: nx and ny must be >= 5");
+  if (nx > 65536 || ny > 65536 || (long long)nx * ny > (1LL << 31))
+    return noalloc_fail(SS_ERR_ARG,
+                        "ss_observables_noalloc: grid larger than the supported maximum (nx, ny <= 65536, nx*ny <= 2^31)");
+  if (!(dx > 0.0) || !(dy > 0.0) || !std::isfinite(dx) || !std::isfinite(dy))
+    return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: dx and dy must be positive and finite");
+  if (precision != SS_FP32 && precision != SS_FP64)
+    return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: precision must be SS_FP32 or SS_FP64");
+  if (!params && n_params > 0) return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: params is NULL");
+
+  // couplings, packed as in ss_set_theory
+  double k[10] = {0};
+  if (theory == SS_ABELIAN_HIGGS) {
+    if (n_params < 1 || n_params > 2) return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: Abelian Higgs takes {lambda[, u]}");
+    const double u = n_params > 1 ? params[1] : 1.0;
+    if (!std::isfinite(params[0]) || !std::isfinite(u) || params[0] < 0.0)
+      return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: lambda must be finite and >= 0");
+    k[0] = params[0];
+    k[1] = u * u;
+  } else if (theory == SS_CHIRAL_MAGNET) {
+    if (n_params < 4 || n_params > 5)
+      return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: chiral magnet takes {J, D, K, h[, dmi_type]}");
+    for (int i = 0; i < n_params; ++i)
+      if (!std::isfinite(params[i])) return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: parameters must be finite");
+    if (!(params[0] > 0.0)) return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: J must be > 0");
+    const int type = n_params > 4 ? (int)params[4] : 0;
+    if (type < 0 || type > 2 || (n_params > 4 && params[4] != (double)type))
+      return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: dmi_type must be 0, 1 or 2");
+    for (int i = 0; i < 4; ++i) k[i] = params[i];
+    if (type == 0) { k[5] = 1.0; k[7] = -1.0; }
+    else if (type == 1) { k[4] = 1.0; k[8] = 1.0; }
+    else { k[4] = 1.0; k[8] = -1.0; }
+  } else {
+    return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: unknown theory");
+  }
+
+  // set-up, once per device, with that device current: the device address of the
+  // scratch (the array's name is only a host-side stand-in)
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return noalloc_fail(SS_ERR_CUDA, std::string("ss_observables_noalloc: ") + cudaGetErrorString(e));
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: device index too large");
+  void* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      void* ptr = nullptr;
+      e = cudaGetSymbolAddress((void**)&ptr, g_noalloc_scratch);
+      if (e != cudaSuccess)
+        return noalloc_fail(SS_ERR_CUDA, std::string("ss_observables_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+      g_noalloc_ptr[dev] = ptr;
+    }
+    base = g_noalloc_ptr[dev];
+  }
+
+  LaunchCtx L{};
+  L.theory = theory == SS_ABELIAN_HIGGS ? TH_AH : TH_CM;
+  L.prec = precision;
+  L.nx = nx;
+  L.ny = ny;
+  L.plane = (size_t)nx * ny;
+  L.dx = dx;
+  L.dy = dy;
+  std::memcpy(L.coup, k, sizeof(k));
+  L.phi[0] = const_cast<void*>(fields);
+  L.st = reinterpret_cast<DevState*>(base);
+  L.opart = reinterpret_cast<ObsPartial*>(static_cast<char*>(base) + NOALLOC_RECORD_BYTES);
+  L.ntiles_x = (nx + TX - 1) / TX;
+  L.ntiles_y = (ny + TY - 1) / TY;
+  const int g = obs_grid(L.theory, precision, L.ntiles_x * L.ntiles_y);
+  L.obs_blocks = g < NOALLOC_MAX_BLOCKS ? g : NOALLOC_MAX_BLOCKS;
+
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  // the arrival counter must start at zero; the rest of the record is overwritten
+  e = cudaMemsetAsync(&L.st->obs_ticket, 0, sizeof(unsigned int), s);
+  if (e == cudaSuccess) e = launch_observables(L, 0, s);
+  if (e == cudaSuccess) {
+    k_noalloc_out<<<1, 1, 0, s>>>(L.st, dx * dy, out);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) return noalloc_fail(SS_ERR_CUDA, std::string("ss_observables_noalloc: ") + cudaGetErrorString(e));
+  return SS_OK;
+}

@@ -100,6 +100,7 @@ def load_library(path: str | None = None):
             "ss_minimise": ([vp, d, ll, ctypes.POINTER(ss_status)], i),
             "ss_observables": ([vp, ctypes.POINTER(ss_obs)], i),
             "ss_profile_stages": ([vp, i, ctypes.POINTER(ctypes.c_float)], i),
+            "ss_observables_noalloc": ([i, pd, i, vp, i, i, d, d, i, vp, vp], i),
             "ss_destroy": ([vp], i),
         }
         for name, (args, res) in sig.items():
@@ -210,6 +211,21 @@ def ss_profile_stages(ctx, n_steps: int) -> list[float]:
     ms = (ctypes.c_float * 2)()
     _check(load_library().ss_profile_stages(ctx, int(n_steps), ms))
     return [float(x) for x in ms]
+
+
+def ss_observables_noalloc(theory: int, params, fields, nx: int, ny: int, dx: float, dy: float, precision: int,
+                           out, stream=None) -> None:
+    """Observables of a device field into a device buffer of 6 doubles, with no
+    allocation (see include/soliton.h). ``fields`` and ``out`` are CUDA tensors or
+    device addresses; the call is asynchronous on ``stream``."""
+    p = np.ascontiguousarray(np.asarray(params, dtype=np.float64).reshape(-1))
+    f = ctypes.c_void_p(fields.data_ptr() if hasattr(fields, "data_ptr") else int(fields))
+    o = ctypes.c_void_p(out.data_ptr() if hasattr(out, "data_ptr") else int(out))
+    s = None
+    if stream is not None:
+        s = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    _check(load_library().ss_observables_noalloc(theory, p.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), p.size, f,
+                                                 nx, ny, dx, dy, precision, o, s))
 
 
 def ss_destroy(ctx) -> None:
