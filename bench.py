@@ -3,8 +3,8 @@
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
 
 Workload: chiral magnet (J = D = 1, h = 0.6, K = 0.1, interfacial DMI) on a
-4096 x 4096 grid (dx = 0.2, halo included), FP32 fields with FP64 reductions,
-400 compact skyrmions at seeded positions (minimum separation 8). Its arrays
+4096 x 4096 grid (dx = 0.2, halo included), compensated FP32 fields (value +
+remainder planes) with FP64 reductions, 400 compact skyrmions at seeded positions (minimum separation 8). Its arrays
 (7 x 201 MB) are far larger than the 129 MB L2, so every timed step streams HBM.
 
 One bench step = one call ss_step(ctx, 32): 32 flow steps, each two fused kernels
@@ -41,17 +41,18 @@ SEED = 20264
 CROP = 512          # oracle sample (CPU baseline / reference arm)
 C = 3
 WORKLOAD = ("chiral magnet 4096x4096 (halo incl.), dx=0.2, J=D=1, h=0.6, K=0.1, interfacial DMI, "
-            "400 skyrmions min-sep 8, FP32 fields + FP64 reductions, ANF-RK4 (2 fused kernels/step)")
+            "400 skyrmions min-sep 8, compensated FP32 fields + FP64 reductions, ANF-RK4 (2 fused kernels/step)")
 
 
 def interior(n: int) -> int:
     return (n - 4) * (n - 4)
 
 
-# algorithmic bytes per interior site of each kernel of a step (FP32, C components):
-# pass 1 reads phi, v, phi^{n-1} and writes k_v1, k_v2; pass 2 reads phi, v, k_v1,
-# k_v2 and writes phi', v'.
-PASS_BYTES = {1: 4 * 5 * C, 2: 4 * 6 * C}
+# algorithmic bytes per interior site of each kernel of a step (compensated FP32,
+# C components; phi is two FP32 planes, value and remainder): pass 1 reads phi,
+# v, phi^{n-1} and writes k_v1, k_v2 (7C values); pass 2 reads phi, v, k_v1, k_v2
+# and writes phi', v' (8C values).
+PASS_BYTES = {1: 4 * 7 * C, 2: 4 * 8 * C}
 
 
 def measured_peaks() -> tuple[dict, str]:

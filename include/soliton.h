@@ -18,7 +18,9 @@
  *    [2, nx-3] x [2, ny-3] are updated. Site (i, j) sits at
  *    x = (i - (nx-1)/2) dx, y = (j - (ny-1)/2) dy.
  *  - Field arrays are component planes [C][ny][nx], x fastest, in the context's
- *    precision (float for SS_FP32, double for SS_FP64). C = 4 for the Abelian
+ *    precision (float for SS_FP32 / SS_FP32_PLAIN, double for SS_FP64; with SS_FP32
+ *    the value part is exchanged, and fields set by the caller start with a zero
+ *    remainder). C = 4 for the Abelian
  *    Higgs model (Re psi, Im psi, A_1, A_2), C = 3 for the chiral magnet
  *    (n_1, n_2, n_3).
  *  - Pointers passed in are borrowed for the duration of the call only; the
@@ -50,8 +52,12 @@ extern "C" {
 #define SS_ERR_NOMEM (-7)         /* device or host allocation failed                 */
 
 /* ---- precisions ---- */
-#define SS_FP32 1 /* FP32 fields and stencils, FP64 compensated reductions */
-#define SS_FP64 2 /* all-FP64 reference form                              */
+#define SS_FP32 1       /* compensated FP32: each field component is stored as two   */
+                        /* FP32 planes (value + rounding remainder), stencils in FP32 */
+                        /* applied to each part, reductions in FP64 (compensated)    */
+#define SS_FP64 2       /* all-FP64 reference form                                    */
+#define SS_FP32_PLAIN 3 /* one FP32 plane per component: fastest, but field rounding  */
+                        /* limits the attainable dx dy max|G| to about 1e-5           */
 
 /* ---- theories ---- */
 #define SS_ABELIAN_HIGGS 1 /* Table 1, params {lambda, u}                                */
@@ -108,7 +114,7 @@ const char* ss_last_error(void);
 int ss_version(void);
 
 /* Create a context for an nx x ny grid (halo included; nx, ny >= 5) with spacings
- * dx, dy > 0 (Sec. 3.1 lattice). precision: SS_FP32 or SS_FP64. cuda_stream: a
+ * dx, dy > 0 (Sec. 3.1 lattice). precision: SS_FP32, SS_FP64 or SS_FP32_PLAIN. cuda_stream: a
  * cudaStream_t borrowed for the context's lifetime, or NULL (see above). The
  * context uses the calling thread's current CUDA device. The time step is
  * dt = 0.5 min(dx, dy) (Sec. 3.1, Courant number C = 0.5). Device buffers are

@@ -8,6 +8,7 @@
 //   phi[2], v[2]   ping-pong field and velocity (RK4 reads phi^n around each site
 //                  while writing phi^{n+1}; phi^{n-1} feeds the arrest test),
 //   kv[2]          stage accelerations k_v1, k_v2 (k_v3, k_v4 stay in registers),
+//   lo[2]          compensated FP32 only: the lo parts of phi[2],
 // plus one device status record and per-block reduction partials. Derivatives never
 // touch memory. Steps are enqueued as CUDA graphs of K_CHUNK steps; convergence,
 // arrest and the step budget are decided on the device, so the host only polls a
@@ -28,7 +29,7 @@ using namespace ss;
 namespace {
 
 constexpr int K_CHUNK = 32;  // steps per captured graph (even: parity returns)
-constexpr int NBUF = 6;      // phi[2], v[2], kv[2]
+constexpr int NBUF = 6;      // phi[2], v[2], kv[2] (+ lo[2] when compensated)
 
 thread_local std::string g_err;
 
@@ -127,6 +128,10 @@ int new_fields(ss_ctx* c) {
   const size_t bytes = (size_t)c->C * c->L.plane * c->elem;
   SS_CK(cudaMemsetAsync(c->L.v[0], 0, bytes, c->stream));
   SS_CK(cudaMemsetAsync(c->L.v[1], 0, bytes, c->stream));
+  if (c->prec == SS_FP32) {  // compensated: the given field is exact, lo = 0
+    SS_CK(cudaMemsetAsync(c->L.lo[0], 0, bytes, c->stream));
+    SS_CK(cudaMemsetAsync(c->L.lo[1], 0, bytes, c->stream));
+  }
   SS_CK(launch_reset_state(c->L, c->stream));
   c->cur = 0;
   c->fields_set = true;
@@ -188,7 +193,8 @@ int ss_create_grid(ss_ctx** out, int nx, int ny, double dx, double dy, int preci
   if ((long long)nx * ny > (1LL << 31)) return fail(SS_ERR_ARG, "grid too large (nx * ny > 2^31)");
   if (!(dx > 0.0) || !(dy > 0.0) || !std::isfinite(dx) || !std::isfinite(dy))
     return fail(SS_ERR_ARG, "dx and dy must be positive and finite");
-  if (precision != SS_FP32 && precision != SS_FP64) return fail(SS_ERR_ARG, "precision must be SS_FP32 or SS_FP64");
+  if (precision != SS_FP32 && precision != SS_FP64 && precision != SS_FP32_PLAIN)
+    return fail(SS_ERR_ARG, "precision must be SS_FP32, SS_FP64 or SS_FP32_PLAIN");
   int dev = 0;
   SS_CK(cudaGetDevice(&dev));
   ss_ctx* c = new (std::nothrow) ss_ctx();
@@ -199,7 +205,7 @@ int ss_create_grid(ss_ctx** out, int nx, int ny, double dx, double dy, int preci
   c->dy = dy;
   c->dt = 0.5 * (dx < dy ? dx : dy);  // Sec. 3.1: C = dt / dx = 0.5
   c->prec = precision;
-  c->elem = precision == SS_FP32 ? 4 : 8;
+  c->elem = precision == SS_FP64 ? 8 : 4;
   cudaError_t e = cudaSuccess;
   if (cuda_stream) {
     c->stream = static_cast<cudaStream_t>(cuda_stream);
@@ -269,7 +275,8 @@ int ss_set_theory(ss_ctx* c, int theory, const double* params, int n_params) {
     const size_t stb = align256(sizeof(DevState));
     const size_t fpb = align256(sizeof(FlowPartial) * (size_t)fb);
     const size_t opb = align256(sizeof(ObsPartial) * (size_t)ob);
-    const size_t total = NBUF * pb + stb + fpb + opb;
+    const int nbuf = NBUF + (c->prec == SS_FP32 ? 2 : 0);
+    const size_t total = nbuf * pb + stb + fpb + opb;
     cudaError_t e = cudaMalloc(&c->base, total);
     if (e != cudaSuccess) {
       c->base = nullptr;
@@ -283,6 +290,11 @@ int ss_set_theory(ss_ctx* c, int theory, const double* params, int n_params) {
     c->L.v[0] = p; p += pb;
     c->L.v[1] = p; p += pb;
     for (int i = 0; i < 2; ++i) { c->L.kv[i] = p; p += pb; }
+    c->L.lo[0] = c->L.lo[1] = nullptr;
+    if (c->prec == SS_FP32) {
+      c->L.lo[0] = p; p += pb;
+      c->L.lo[1] = p; p += pb;
+    }
     c->L.st = reinterpret_cast<DevState*>(p); p += stb;
     c->L.fpart = reinterpret_cast<FlowPartial*>(p); p += fpb;
     c->L.opart = reinterpret_cast<ObsPartial*>(p);

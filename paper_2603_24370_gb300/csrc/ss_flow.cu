@@ -10,12 +10,12 @@
 // is the textbook (k_phi, k_v) form with every k_phi eliminated. Y_1 and Y_2 need
 // only (phi, v); Y_3 and Y_4 need only (phi, v, k_v1, k_v2). So a step is two passes
 // with the ordinary width-2 halo and no recomputation:
-//   pass A  (stages 1, 2): reads phi, v (and phi^{n-1}), writes k_v1, k_v2;
-//   pass B  (stages 3, 4): reads phi, v, k_v1, k_v2, writes phi', v'
+//   pass 1  (stages 1, 2): reads phi, v (and phi^{n-1}), writes k_v1, k_v2;
+//   pass 2  (stages 3, 4): reads phi, v, k_v1, k_v2, writes phi', v'
 // (k_v3, k_v4 live in registers). Chiral magnet: every Y_i and phi' are normalised
 // and v' tangent-projected (Sec. 3.2, constraint projection).
 //
-// Pass A also reduces E_h(phi) (a compensated pair per thread, FP64 TwoSum warp
+// Pass 1 also reduces E_h(phi) (a compensated pair per thread, FP64 TwoSum warp
 // trees, one partial per block, the last-arriving block sums the partials in a
 // fixed order), dx dy max|G|, and the energy change since the previous field,
 // dE = sum_I [e(phi^n) - e(phi^{n-1})] in the cancellation-free form of
@@ -23,15 +23,23 @@
 // block then decides on the device, with no host round trip:
 //   arrest    = dE > 0, i.e. E_h(phi^n) > E_h(phi^{n-1})   (Eq. 4)
 //   converged = dx dy max|G| < tol
-// Pass A computes k_v2 with v before the arrest is known. That is exact either way:
+// Pass 1 computes k_v2 with v before the arrest is known. That is exact either way:
 // when the step is arrested v counts as zero, so Y_2 = Y_1 and k_v2 = k_v1, and
-// pass B simply reads k_v1 in place of k_v2 (and zero in place of v).
+// pass 2 simply reads k_v1 in place of k_v2 (and zero in place of v).
+//
+// Compensated FP32 (CP): the field is stored as two FP32 planes, phi = hi + lo with
+// |lo| <= ulp(hi)/2. Every stage input is hi + S with a small part S (lo plus the
+// stage increment), and every derivative is formed as D(hi) + D(S), the differences
+// taken within each part first. Rounding of the stored values therefore never
+// reaches the force through the 1/h^2 of Eq. 2; in single FP32 that amplified
+// rounding (~3e-8 per site) kicks the stiffest modes every step and the arrest test
+// stalls the flow above dx dy max|G| ~ 1e-6. The chiral-magnet normalisation is
+// done in the same split form, and the new field is re-split by TwoSum.
 //
 // Per block a tile of TX x TY sites is staged in shared memory with its halo, the
-// stage inputs formed while loading. Each thread then walks RY rows of one column
-// with a 5-row register window per component, so a component costs 5 shared loads
-// per site (centre + 4 x-neighbours) for Eq. 1, Eq. 2 and the mixed derivative.
-// Blocks stride over tiles; the grid is occupancy x SM count.
+// stage inputs formed while loading (two sites per iteration, loads first). Each
+// thread then walks RY rows of one column with a 5-row register window per
+// component. Blocks stride over tiles; the grid is occupancy x SM count.
 #include "ss_internal.h"
 
 namespace ss {
@@ -45,15 +53,18 @@ struct FlowTile {
 
 template <typename R>
 struct PassArgs {
-  const R* __restrict__ phi;       // phi^n (current field)
-  const R* __restrict__ phi_prev;  // pass A: phi^{n-1} (other ping-pong buffer)
+  const R* __restrict__ phi;       // phi^n (current field; hi part when compensated)
+  const R* __restrict__ lo;        // CP: lo part of phi^n
+  const R* __restrict__ phi_prev;  // pass 1: phi^{n-1} (other ping-pong buffer)
+  const R* __restrict__ lo_prev;   // CP pass 1: lo part of phi^{n-1}
   const R* __restrict__ v;         // v^n
-  const R* __restrict__ kv1;       // pass B
-  const R* __restrict__ kv2;       // pass B
-  R* __restrict__ kv1_out;         // pass A
-  R* __restrict__ kv2_out;         // pass A
-  R* __restrict__ phi_out;         // pass B: phi^{n+1}
-  R* __restrict__ v_out;           // pass B: v^{n+1}
+  const R* __restrict__ kv1;       // pass 2
+  const R* __restrict__ kv2;       // pass 2
+  R* __restrict__ kv1_out;         // pass 1
+  R* __restrict__ kv2_out;         // pass 1
+  R* __restrict__ phi_out;         // pass 2: phi^{n+1} (hi)
+  R* __restrict__ lo_out;          // CP pass 2: lo part of phi^{n+1}
+  R* __restrict__ v_out;           // pass 2: v^{n+1}
   int nx, ny;
   size_t plane;
   int ntx, ntiles;
@@ -80,50 +91,110 @@ __device__ __forceinline__ void normalise(R* y) {
   for (int c = 0; c < C; ++c) y[c] *= s;
 }
 
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bp = s - a;
+  e = (a - (s - bp)) + (b - bp);
+}
+
+// Split-form projection onto the unit sphere: given hi (FP32) and a small part t,
+// return t' with hi + t' = (hi + t) / |hi + t| to about eps^2. With
+// eta = |hi + t|^2 - 1 = (|hi|^2 - 1) + 2 hi.t + |t|^2, where |hi|^2 - 1 is formed
+// exactly (error-free products and sums), 1/|hi + t| = 1 + rho with
+// rho = -eta / (r (1 + r)), r = sqrt(1 + eta), and t' = t + rho (hi + t).
+__device__ __forceinline__ void normalise_split(const float* hi, float* t) {
+  float p[3], e[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    p[c] = hi[c] * hi[c];
+    e[c] = fmaf(hi[c], hi[c], -p[c]);
+  }
+  float s01, e01, s012, e012;
+  two_sum_f(p[0], p[1], s01, e01);
+  two_sum_f(s01, p[2], s012, e012);
+  const float q = (s012 - 1.0f) + (e01 + e012 + e[0] + e[1] + e[2]);  // s012 - 1 is exact near 1
+  const float ht = hi[0] * t[0] + hi[1] * t[1] + hi[2] * t[2];
+  const float tt = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
+  const float eta = q + (2.0f * ht + tt);
+  const float r = sqrtf(1.0f + eta);
+  const float rho = -eta / (r * (1.0f + r));
+#pragma unroll
+  for (int c = 0; c < 3; ++c) t[c] = t[c] + rho * (hi[c] + t[c]);
+}
+
 // Sliding 5-row window over one component plane of the shared tile, for one
-// column. MIX keeps the x-stencil of all five rows for the mixed derivative.
-template <typename R, bool MIX>
+// column. MIX keeps the x-stencil of all five rows for the mixed derivative. With
+// CP every quantity is formed on the hi plane and the small plane separately, then
+// added (differences first within each plane).
+template <typename R, bool MIX, bool CP>
 struct Win {
-  R c[5];   // centre values of rows y-2 .. y+2
+  R c[5];   // centre values of rows y-2 .. y+2 (hi part when CP)
+  R s[5];   // CP: small parts of the centre values
   R g[5];   // MIX: unscaled Eq. 1 along x of rows y-2 .. y+2
   R xx[5];  // MIX: unscaled Eq. 2 along x of rows y-2 .. y+2
 
-  __device__ __forceinline__ void enter(const R* P, int slot) {  // P points at the row's centre
+  __device__ __forceinline__ static void xterms(const R* P, R ce, R& gx, R& gxx) {
+    const R m2 = P[-2], m1 = P[-1], p1 = P[1], p2 = P[2];
+    gx = R(8) * (p1 - m1) - (p2 - m2);
+    gxx = R(16) * ((p1 - ce) + (m1 - ce)) - ((p2 - ce) + (m2 - ce));
+  }
+  // P: the row's centre in the hi (or only) plane; Q: the same in the small plane.
+  __device__ __forceinline__ void enter(const R* P, const R* Q, int slot) {
     const R ce = P[0];
     c[slot] = ce;
+    R cs = R(0);
+    if (CP) {
+      cs = Q[0];
+      s[slot] = cs;
+    }
     if (MIX) {
-      const R m2 = P[-2], m1 = P[-1], p1 = P[1], p2 = P[2];
-      g[slot] = R(8) * (p1 - m1) - (p2 - m2);
-      xx[slot] = R(16) * ((p1 - ce) + (m1 - ce)) - ((p2 - ce) + (m2 - ce));
+      R gx, gxx;
+      xterms(P, ce, gx, gxx);
+      if (CP) {
+        R gs, gxs;
+        xterms(Q, cs, gs, gxs);
+        gx += gs;
+        gxx += gxs;
+      }
+      g[slot] = gx;
+      xx[slot] = gxx;
     }
   }
   __device__ __forceinline__ void shift() {
 #pragma unroll
-    for (int s = 0; s < 4; ++s) {
-      c[s] = c[s + 1];
-      if (MIX) { g[s] = g[s + 1]; xx[s] = xx[s + 1]; }
+    for (int k = 0; k < 4; ++k) {
+      c[k] = c[k + 1];
+      if (CP) s[k] = s[k + 1];
+      if (MIX) { g[k] = g[k + 1]; xx[k] = xx[k + 1]; }
     }
   }
-  // Derivatives at the window's centre row; Pc points at that row's centre.
+  __device__ __forceinline__ static R yd1(const R* a) { return R(8) * (a[3] - a[1]) - (a[4] - a[0]); }
+  __device__ __forceinline__ static R yd2(const R* a) {
+    return R(16) * ((a[3] - a[2]) + (a[1] - a[2])) - ((a[4] - a[2]) + (a[0] - a[2]));
+  }
+  // Derivatives at the window's centre row; Pc / Qc point at that row's centre.
   template <bool SECOND>
-  __device__ __forceinline__ void derivs(const R* Pc, const Spacing<R>& h, R& v, R& fx, R& fy, R& fxx, R& fyy,
-                                         R& fxy) const {
-    const R ce = c[2];
-    v = ce;
+  __device__ __forceinline__ void derivs(const R* Pc, const R* Qc, const Spacing<R>& h, R& v, R& fx, R& fy, R& fxx,
+                                         R& fyy, R& fxy) const {
     R gx, gxx;
     if (MIX) {
       gx = g[2];
       gxx = xx[2];
     } else {
-      const R m2 = Pc[-2], m1 = Pc[-1], p1 = Pc[1], p2 = Pc[2];
-      gx = R(8) * (p1 - m1) - (p2 - m2);
-      gxx = R(16) * ((p1 - ce) + (m1 - ce)) - ((p2 - ce) + (m2 - ce));
+      xterms(Pc, c[2], gx, gxx);
+      if (CP) {
+        R gs, gxs;
+        xterms(Qc, s[2], gs, gxs);
+        gx += gs;
+        gxx += gxs;
+      }
     }
-    fx = gx * h.i12dx;                                       // Eq. 1, x
-    fy = (R(8) * (c[3] - c[1]) - (c[4] - c[0])) * h.i12dy;  // Eq. 1, y
+    v = CP ? c[2] + s[2] : c[2];
+    fx = gx * h.i12dx;                                // Eq. 1, x
+    fy = (CP ? yd1(c) + yd1(s) : yd1(c)) * h.i12dy;  // Eq. 1, y
     if (SECOND) {
-      fxx = gxx * h.i12dx2;                                                                  // Eq. 2, x
-      fyy = (R(16) * ((c[3] - ce) + (c[1] - ce)) - ((c[4] - ce) + (c[0] - ce))) * h.i12dy2;  // Eq. 2, y
+      fxx = gxx * h.i12dx2;                                // Eq. 2, x
+      fyy = (CP ? yd2(c) + yd2(s) : yd2(c)) * h.i12dy2;   // Eq. 2, y
     } else {
       fxx = fyy = R(0);
     }
@@ -132,20 +203,21 @@ struct Win {
 };
 
 // Window set of one stage input: all C components, mixed derivatives for the gauge
-// field of the Abelian Higgs model (components 2, 3).
-template <int TH, typename R>
+// field of the Abelian Higgs model (components 2, 3). H: hi (or only) tile set;
+// Sm: small-part tile set (CP).
+template <int TH, typename R, bool CP>
 struct StageWin {
   static constexpr int C = NComp<TH>::C;
   static constexpr int SXY = FlowTile<R>::SXY;
-  Win<R, false> w0, w1;
-  Win<R, TH == TH_AH> w2;
-  Win<R, TH == TH_AH> w3;  // unused for the chiral magnet
+  Win<R, false, CP> w0, w1;
+  Win<R, TH == TH_AH, CP> w2;
+  Win<R, TH == TH_AH, CP> w3;  // unused for the chiral magnet
 
-  __device__ __forceinline__ void enter(const R* tiles, int off, int slot) {
-    w0.enter(tiles + off, slot);
-    w1.enter(tiles + SXY + off, slot);
-    w2.enter(tiles + 2 * SXY + off, slot);
-    if (C == 4) w3.enter(tiles + 3 * SXY + off, slot);
+  __device__ __forceinline__ void enter(const R* H, const R* Sm, int off, int slot) {
+    w0.enter(H + off, Sm + off, slot);
+    w1.enter(H + SXY + off, Sm + SXY + off, slot);
+    w2.enter(H + 2 * SXY + off, Sm + 2 * SXY + off, slot);
+    if (C == 4) w3.enter(H + 3 * SXY + off, Sm + 3 * SXY + off, slot);
   }
   __device__ __forceinline__ void shift() {
     w0.shift();
@@ -153,24 +225,25 @@ struct StageWin {
     w2.shift();
     if (C == 4) w3.shift();
   }
-  __device__ __forceinline__ void derivs(const R* tiles, int off, const Spacing<R>& h, R* v, R* fx, R* fy, R* fxx,
-                                         R* fyy, R* fxy) const {
-    w0.template derivs<true>(tiles + off, h, v[0], fx[0], fy[0], fxx[0], fyy[0], fxy[0]);
-    w1.template derivs<true>(tiles + SXY + off, h, v[1], fx[1], fy[1], fxx[1], fyy[1], fxy[1]);
-    w2.template derivs<true>(tiles + 2 * SXY + off, h, v[2], fx[2], fy[2], fxx[2], fyy[2], fxy[2]);
-    if (C == 4) w3.template derivs<true>(tiles + 3 * SXY + off, h, v[3], fx[3], fy[3], fxx[3], fyy[3], fxy[3]);
+  __device__ __forceinline__ void derivs(const R* H, const R* Sm, int off, const Spacing<R>& h, R* v, R* fx, R* fy,
+                                         R* fxx, R* fyy, R* fxy) const {
+    w0.template derivs<true>(H + off, Sm + off, h, v[0], fx[0], fy[0], fxx[0], fyy[0], fxy[0]);
+    w1.template derivs<true>(H + SXY + off, Sm + SXY + off, h, v[1], fx[1], fy[1], fxx[1], fyy[1], fxy[1]);
+    w2.template derivs<true>(H + 2 * SXY + off, Sm + 2 * SXY + off, h, v[2], fx[2], fy[2], fxx[2], fyy[2], fxy[2]);
+    if (C == 4)
+      w3.template derivs<true>(H + 3 * SXY + off, Sm + 3 * SXY + off, h, v[3], fx[3], fy[3], fxx[3], fyy[3], fxy[3]);
   }
 };
 
-// First derivatives only (the field difference of the arrest test).
+// First derivatives only (the field difference of the arrest test): one plane set.
 template <int TH, typename R>
 struct DiffWin {
   static constexpr int C = NComp<TH>::C;
   static constexpr int SXY = FlowTile<R>::SXY;
-  Win<R, false> w[C];
+  Win<R, false, false> w[C];
   __device__ __forceinline__ void enter(const R* tiles, int off, int slot) {
 #pragma unroll
-    for (int c = 0; c < C; ++c) w[c].enter(tiles + c * SXY + off, slot);
+    for (int c = 0; c < C; ++c) w[c].enter(tiles + c * SXY + off, nullptr, slot);
   }
   __device__ __forceinline__ void shift() {
 #pragma unroll
@@ -180,7 +253,7 @@ struct DiffWin {
 #pragma unroll
     for (int c = 0; c < C; ++c) {
       R unused0, unused1, unused2;
-      w[c].template derivs<false>(tiles + c * SXY + off, h, v[c], fx[c], fy[c], unused0, unused1, unused2);
+      w[c].template derivs<false>(tiles + c * SXY + off, nullptr, h, v[c], fx[c], fy[c], unused0, unused1, unused2);
     }
   }
 };
@@ -192,19 +265,28 @@ __device__ __forceinline__ void force_at(const Couplings<R>& k, const R* v, cons
   else force_cm<R>(k, v, fx, fy, fxx, fyy, G);
 }
 
-template <int TH, typename R, int PASS>
+// Tile-set layout in shared memory (each set is C planes of SXY values):
+//   pass 1, single: [Y1 | Y2 | delta]           CP: [hi | S1 | S2 | delta]
+//   pass 2, single: [Y3 | Y4]                   CP: [hi | S3 | S4]
+template <int PASS, bool CP>
+struct Sets {
+  static constexpr int n = (PASS == 1 ? 3 : 2) + (CP ? 1 : 0);
+};
+
+template <int TH, typename R, int PASS, bool CP>
 __global__ void __launch_bounds__(NT) k_pass(PassArgs<R> a) {
   using T = FlowTile<R>;
   constexpr int C = NComp<TH>::C;
   constexpr int RY = T::RY;
+  constexpr int PS = C * T::SXY;  // values per tile set
   extern __shared__ __align__(16) unsigned char smraw[];
-  R* sm = reinterpret_cast<R*>(smraw);  // pass A: [Y1 | Y2 | delta][C][SXY]; pass B: [Y3 | Y4][C][SXY]
+  R* sm = reinterpret_cast<R*>(smraw);
   __shared__ double sred[RedSmem<2, 1>::n];
   __shared__ int s_last;
 
   DevState* st = a.st;
-  // Uniform over the grid (the record only changes between launches). Pass A runs
-  // once per field; pass B stops at convergence, at a non-finite value and at the
+  // Uniform over the grid (the record only changes between launches). Pass 1 runs
+  // once per field; pass 2 stops at convergence, at a non-finite value and at the
   // step limit of the current call.
   if (st->converged | st->nonfinite) return;
   if (PASS == 1 ? (st->head_step == st->steps) : (st->steps >= st->step_limit)) return;
@@ -214,66 +296,95 @@ __global__ void __launch_bounds__(NT) k_pass(PassArgs<R> a) {
   const size_t P = a.plane;
   const R dt = a.dt, hdt = R(0.5) * a.dt;
   const R c3 = R(0.25) * dt * dt, c4 = R(0.5) * dt * dt;
-  R* const set0 = sm;
-  R* const set1 = sm + C * T::SXY;
-  R* const set2 = sm + 2 * C * T::SXY;
+  // Set pointers. Single precision / FP64: A = first stage input, B = second stage
+  // input, D = delta (pass 1). CP: H = hi, A = small part of the first stage input,
+  // B = small part of the second, D = delta.
+  R* const setH = sm;                                 // CP only
+  R* const setA = sm + (CP ? PS : 0);
+  R* const setB = sm + (CP ? 2 * PS : PS);
+  R* const setD = sm + (CP ? 3 * PS : 2 * PS);        // pass 1 only
 
   R es = R(0), ec = R(0), ds = R(0), dc = R(0), gmr = R(0);
 
   for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
     const int x0 = (t % a.ntx) * T::TX, y0 = (t / a.ntx) * T::TY;
     __syncthreads();  // the previous tile's shared reads are finished
-    // ---- stage inputs over the tile and its halo
-    int ly = tid / T::SX, lx = tid - ly * T::SX;
-    for (int idx = tid; idx < T::SXY; idx += NT) {
-      const int gx = x0 + lx - 2, gy = y0 + ly - 2;
-      R y0v[C], y1v[C], y2v[C];
-      if (gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny) {
-        const size_t s = (size_t)gy * a.nx + gx;
-        const bool inside = gx >= 2 && gx < a.nx - 2 && gy >= 2 && gy < a.ny - 2;
-        R p[C];
+    // ---- stage inputs over the tile and its halo, two sites per iteration
+    for (int base = tid; base < T::SXY; base += 2 * NT) {
+      R pv[2][C], lv[2][C], vv[2][C], k1v[2][C], k2v[2][C], pp[2][C], lp[2][C];
+      bool in[2], inside[2];
+      size_t sidx[2];
 #pragma unroll
-        for (int c = 0; c < C; ++c) p[c] = a.phi[c * P + s];
+      for (int u = 0; u < 2; ++u) {  // all global loads of both sites first
+        const int idx = base + u * NT;
+        const int ly = idx / T::SX, lx = idx - ly * T::SX;
+        const int gx = x0 + lx - 2, gy = y0 + ly - 2;
+        in[u] = idx < T::SXY && gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny;
+        inside[u] = in[u] && gx >= 2 && gx < a.nx - 2 && gy >= 2 && gy < a.ny - 2;
+        const size_t s = in[u] ? (size_t)gy * a.nx + gx : 0;
+        sidx[u] = s;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          pv[u][c] = in[u] ? a.phi[c * P + s] : R(0);
+          lv[u][c] = (CP && in[u]) ? a.lo[c * P + s] : R(0);
+          vv[u][c] = (inside[u] && !arrest) ? a.v[c * P + s] : R(0);
+          if (PASS == 1) {
+            pp[u][c] = (has_prev && in[u]) ? a.phi_prev[c * P + s] : pv[u][c];
+            lp[u][c] = (CP && has_prev && in[u]) ? a.lo_prev[c * P + s] : lv[u][c];
+          } else {
+            k1v[u][c] = inside[u] ? a.kv1[c * P + s] : R(0);
+            k2v[u][c] = inside[u] ? (arrest ? k1v[u][c] : a.kv2[c * P + s]) : R(0);
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int idx = base + u * NT;
+        if (idx >= T::SXY) break;
+        R ya[C], yb[C], yd[C];
         if (PASS == 1) {
 #pragma unroll
           for (int c = 0; c < C; ++c) {
-            y0v[c] = p[c];
-            y2v[c] = has_prev ? p[c] - a.phi_prev[c * P + s] : R(0);
-            y1v[c] = inside ? p[c] + hdt * a.v[c * P + s] : p[c];  // halo: v = 0
+            // delta = phi^n - phi^{n-1} (differences of neighbouring values: exact per part)
+            yd[c] = CP ? (pv[u][c] - pp[u][c]) + (lv[u][c] - lp[u][c]) : pv[u][c] - pp[u][c];
+            if (CP) {
+              ya[c] = lv[u][c];
+              yb[c] = lv[u][c] + hdt * vv[u][c];
+            } else {
+              ya[c] = pv[u][c];
+              yb[c] = pv[u][c] + hdt * vv[u][c];
+            }
           }
-          if (TH == TH_CM && inside) normalise<C>(y1v);
+          if (TH == TH_CM && inside[u]) {
+            if constexpr (CP) normalise_split(pv[u], yb);
+            else normalise<C>(yb);
+          }
         } else {
-          if (inside) {
 #pragma unroll
-            for (int c = 0; c < C; ++c) {
-              const R vv = arrest ? R(0) : a.v[c * P + s];
-              const R k1 = a.kv1[c * P + s];
-              const R k2 = arrest ? k1 : a.kv2[c * P + s];
-              y0v[c] = p[c] + hdt * vv + c3 * k1;
-              y1v[c] = p[c] + dt * vv + c4 * k2;
+          for (int c = 0; c < C; ++c) {
+            const R base3 = hdt * vv[u][c] + c3 * k1v[u][c];
+            const R base4 = dt * vv[u][c] + c4 * k2v[u][c];
+            ya[c] = CP ? lv[u][c] + base3 : pv[u][c] + base3;
+            yb[c] = CP ? lv[u][c] + base4 : pv[u][c] + base4;
+          }
+          if (TH == TH_CM && inside[u]) {
+            if constexpr (CP) {
+              normalise_split(pv[u], ya);
+              normalise_split(pv[u], yb);
+            } else {
+              normalise<C>(ya);
+              normalise<C>(yb);
             }
-            if (TH == TH_CM) {
-              normalise<C>(y0v);
-              normalise<C>(y1v);
-            }
-          } else {
-#pragma unroll
-            for (int c = 0; c < C; ++c) y0v[c] = y1v[c] = p[c];
           }
         }
-      } else {
 #pragma unroll
-        for (int c = 0; c < C; ++c) y0v[c] = y1v[c] = y2v[c] = R(0);
+        for (int c = 0; c < C; ++c) {
+          if (CP) setH[c * T::SXY + idx] = pv[u][c];
+          setA[c * T::SXY + idx] = ya[c];
+          setB[c * T::SXY + idx] = yb[c];
+          if (PASS == 1) setD[c * T::SXY + idx] = has_prev ? yd[c] : R(0);
+        }
       }
-#pragma unroll
-      for (int c = 0; c < C; ++c) {
-        set0[c * T::SXY + idx] = y0v[c];
-        set1[c * T::SXY + idx] = y1v[c];
-        if (PASS == 1) set2[c * T::SXY + idx] = y2v[c];
-      }
-      lx += NT % T::SX;
-      ly += NT / T::SX;
-      if (lx >= T::SX) { lx -= T::SX; ++ly; }
     }
     __syncthreads();
 
@@ -281,24 +392,28 @@ __global__ void __launch_bounds__(NT) k_pass(PassArgs<R> a) {
     const int sx = threadIdx.x + 2, sy0 = threadIdx.y * RY + 2;
     const int gx = x0 + threadIdx.x, gyb = y0 + threadIdx.y * RY;
     const bool colok = gx >= 2 && gx < a.nx - 2;
+    // window planes: CP reads hi from setH and the small part from the stage set;
+    // otherwise the stage set is the whole input (the small-part pointer is unused).
+    const R* const HA = CP ? setH : setA;
+    const R* const HB = CP ? setH : setB;
 
     if (PASS == 1) {
       // stage 1 at Y_1 = phi: k_v1, e, max|G|, and e(phi^n) - e(phi^{n-1})
       {
-        StageWin<TH, R> W;
+        StageWin<TH, R, CP> W;
         DiffWin<TH, R> D;
 #pragma unroll
         for (int s = 0; s < 5; ++s) {
           const int off = (sy0 - 2 + s) * T::SX + sx;
-          W.enter(set0, off, s);
-          if (has_prev) D.enter(set2, off, s);
+          W.enter(HA, setA, off, s);
+          if (has_prev) D.enter(setD, off, s);
         }
 #pragma unroll
         for (int r = 0; r < RY; ++r) {
           const int off = (sy0 + r) * T::SX + sx;
           const bool ok = colok && gyb + r >= 2 && gyb + r < a.ny - 2;
           R v[C], fx[C], fy[C], fxx[C], fyy[C], fxy[C], G[C];
-          W.derivs(set0, off, a.h, v, fx, fy, fxx, fyy, fxy);
+          W.derivs(HA, setA, off, a.h, v, fx, fy, fxx, fyy, fxy);
           force_at<TH, R>(a.k, v, fx, fy, fxx, fyy, fxy, G);
           if (ok) {
             const size_t s = (size_t)(gyb + r) * a.nx + gx;
@@ -315,7 +430,7 @@ __global__ void __launch_bounds__(NT) k_pass(PassArgs<R> a) {
           }
           if (has_prev) {
             R d[C], dxv[C], dyv[C];
-            D.derivs(set2, off, a.h, d, dxv, dyv);
+            D.derivs(setD, off, a.h, d, dxv, dyv);
             if (ok) {
               const R de = (TH == TH_AH) ? delta_density_ah<R>(a.k, v, fx, fy, d, dxv, dyv)
                                          : delta_density_cm<R>(a.k, v, fx, fy, d, dxv, dyv);
@@ -327,24 +442,24 @@ __global__ void __launch_bounds__(NT) k_pass(PassArgs<R> a) {
           if (r + 1 < RY) {
             const int noff = (sy0 + r + 3) * T::SX + sx;
             W.shift();
-            W.enter(set0, noff, 4);
+            W.enter(HA, setA, noff, 4);
             if (has_prev) {
               D.shift();
-              D.enter(set2, noff, 4);
+              D.enter(setD, noff, 4);
             }
           }
         }
       }
       // stage 2 at Y_2 = phi + dt/2 v: k_v2
       {
-        StageWin<TH, R> W;
+        StageWin<TH, R, CP> W;
 #pragma unroll
-        for (int s = 0; s < 5; ++s) W.enter(set1, (sy0 - 2 + s) * T::SX + sx, s);
+        for (int s = 0; s < 5; ++s) W.enter(HB, setB, (sy0 - 2 + s) * T::SX + sx, s);
 #pragma unroll
         for (int r = 0; r < RY; ++r) {
           const int off = (sy0 + r) * T::SX + sx;
           R v[C], fx[C], fy[C], fxx[C], fyy[C], fxy[C], G[C];
-          W.derivs(set1, off, a.h, v, fx, fy, fxx, fyy, fxy);
+          W.derivs(HB, setB, off, a.h, v, fx, fy, fxx, fyy, fxy);
           force_at<TH, R>(a.k, v, fx, fy, fxx, fyy, fxy, G);
           if (colok && gyb + r >= 2 && gyb + r < a.ny - 2) {
             const size_t s = (size_t)(gyb + r) * a.nx + gx;
@@ -353,7 +468,7 @@ __global__ void __launch_bounds__(NT) k_pass(PassArgs<R> a) {
           }
           if (r + 1 < RY) {
             W.shift();
-            W.enter(set1, (sy0 + r + 3) * T::SX + sx, 4);
+            W.enter(HB, setB, (sy0 + r + 3) * T::SX + sx, 4);
           }
         }
       }
@@ -361,50 +476,61 @@ __global__ void __launch_bounds__(NT) k_pass(PassArgs<R> a) {
       // stage 3 at Y_3: k_v3 kept in registers
       R k3[RY][C];
       {
-        StageWin<TH, R> W;
+        StageWin<TH, R, CP> W;
 #pragma unroll
-        for (int s = 0; s < 5; ++s) W.enter(set0, (sy0 - 2 + s) * T::SX + sx, s);
+        for (int s = 0; s < 5; ++s) W.enter(HA, setA, (sy0 - 2 + s) * T::SX + sx, s);
 #pragma unroll
         for (int r = 0; r < RY; ++r) {
           const int off = (sy0 + r) * T::SX + sx;
           R v[C], fx[C], fy[C], fxx[C], fyy[C], fxy[C], G[C];
-          W.derivs(set0, off, a.h, v, fx, fy, fxx, fyy, fxy);
+          W.derivs(HA, setA, off, a.h, v, fx, fy, fxx, fyy, fxy);
           force_at<TH, R>(a.k, v, fx, fy, fxx, fyy, fxy, G);
 #pragma unroll
           for (int c = 0; c < C; ++c) k3[r][c] = -G[c];
           if (r + 1 < RY) {
             W.shift();
-            W.enter(set0, (sy0 + r + 3) * T::SX + sx, 4);
+            W.enter(HA, setA, (sy0 + r + 3) * T::SX + sx, 4);
           }
         }
       }
       // stage 4 at Y_4, then the RK4 combination
       {
-        StageWin<TH, R> W;
+        StageWin<TH, R, CP> W;
 #pragma unroll
-        for (int s = 0; s < 5; ++s) W.enter(set1, (sy0 - 2 + s) * T::SX + sx, s);
+        for (int s = 0; s < 5; ++s) W.enter(HB, setB, (sy0 - 2 + s) * T::SX + sx, s);
         const R w6 = dt * dt / R(6), u6 = dt / R(6);
 #pragma unroll
         for (int r = 0; r < RY; ++r) {
           const int off = (sy0 + r) * T::SX + sx;
           R v[C], fx[C], fy[C], fxx[C], fyy[C], fxy[C], G[C];
-          W.derivs(set1, off, a.h, v, fx, fy, fxx, fyy, fxy);
+          W.derivs(HB, setB, off, a.h, v, fx, fy, fxx, fyy, fxy);
           force_at<TH, R>(a.k, v, fx, fy, fxx, fyy, fxy, G);
           if (colok && gyb + r >= 2 && gyb + r < a.ny - 2) {
             const size_t s = (size_t)(gyb + r) * a.nx + gx;
-            R pn[C], vn[C];
+            R p0[C], q[C], vn[C];
 #pragma unroll
             for (int c = 0; c < C; ++c) {
-              const R p0 = a.phi[c * P + s];
+              p0[c] = a.phi[c * P + s];
               const R v0 = arrest ? R(0) : a.v[c * P + s];
               const R k1 = a.kv1[c * P + s];
               const R k2 = arrest ? k1 : a.kv2[c * P + s];
               const R k4 = -G[c];
-              pn[c] = p0 + dt * v0 + w6 * (k1 + k2 + k3[r][c]);
+              // increment of phi; with CP it joins the stored lo part before rounding
+              const R inc = dt * v0 + w6 * (k1 + k2 + k3[r][c]);
+              q[c] = CP ? a.lo[c * P + s] + inc : p0[c] + inc;
               vn[c] = v0 + u6 * (k1 + R(2) * (k2 + k3[r][c]) + k4);
             }
+            R pn[C], ln[C];
+            if constexpr (CP) {
+              if (TH == TH_CM) normalise_split(p0, q);
+#pragma unroll
+              for (int c = 0; c < C; ++c) two_sum_f(p0[c], q[c], pn[c], ln[c]);  // hi' = fl(hi + small), lo' = rest
+            } else {
+#pragma unroll
+              for (int c = 0; c < C; ++c) pn[c] = q[c];
+              if (TH == TH_CM) normalise<C>(pn);
+            }
             if (TH == TH_CM) {
-              normalise<C>(pn);
               const R vp = vn[0] * pn[0] + vn[1] * pn[1] + vn[2] * pn[2];
 #pragma unroll
               for (int c = 0; c < C; ++c) vn[c] -= vp * pn[c];
@@ -412,12 +538,13 @@ __global__ void __launch_bounds__(NT) k_pass(PassArgs<R> a) {
 #pragma unroll
             for (int c = 0; c < C; ++c) {
               a.phi_out[c * P + s] = pn[c];
+              if (CP) a.lo_out[c * P + s] = ln[c];
               a.v_out[c * P + s] = vn[c];
             }
           }
           if (r + 1 < RY) {
             W.shift();
-            W.enter(set1, (sy0 + r + 3) * T::SX + sx, 4);
+            W.enter(HB, setB, (sy0 + r + 3) * T::SX + sx, 4);
           }
         }
       }
@@ -505,9 +632,10 @@ __global__ void k_scaled_copy(R* __restrict__ out, const R* __restrict__ in, siz
 }
 
 // ------------------------------------------------------------------ launchers
-template <int TH, typename R>
+template <int TH, typename R, bool CP>
 static size_t pass_smem(int pass) {
-  return (size_t)(pass == 1 ? 3 : 2) * NComp<TH>::C * FlowTile<R>::SXY * sizeof(R);
+  const int sets = pass == 1 ? Sets<1, CP>::n : Sets<2, CP>::n;
+  return (size_t)sets * NComp<TH>::C * FlowTile<R>::SXY * sizeof(R);
 }
 
 template <typename R>
@@ -515,13 +643,16 @@ static PassArgs<R> make_args(const LaunchCtx& c, int cur) {
   PassArgs<R> a{};
   const int nxt = cur ^ 1;
   a.phi = static_cast<const R*>(c.phi[cur]);
+  a.lo = static_cast<const R*>(c.lo[cur]);
   a.phi_prev = static_cast<const R*>(c.phi[nxt]);
+  a.lo_prev = static_cast<const R*>(c.lo[nxt]);
   a.v = static_cast<const R*>(c.v[cur]);
   a.kv1 = static_cast<const R*>(c.kv[0]);
   a.kv2 = static_cast<const R*>(c.kv[1]);
   a.kv1_out = static_cast<R*>(c.kv[0]);
   a.kv2_out = static_cast<R*>(c.kv[1]);
   a.phi_out = static_cast<R*>(c.phi[nxt]);
+  a.lo_out = static_cast<R*>(c.lo[nxt]);
   a.v_out = static_cast<R*>(c.v[nxt]);
   a.nx = c.nx;
   a.ny = c.ny;
@@ -541,19 +672,27 @@ static PassArgs<R> make_args(const LaunchCtx& c, int cur) {
   return a;
 }
 
-template <int TH, typename R>
+template <int TH, typename R, bool CP>
 static cudaError_t pass_t(const LaunchCtx& c, int pass, int cur, cudaStream_t s) {
   const PassArgs<R> a = make_args<R>(c, cur);
   const dim3 blk(BX, BY);
-  if (pass == 1) k_pass<TH, R, 1><<<c.flow_blocks, blk, pass_smem<TH, R>(1), s>>>(a);
-  else if (pass == 2) k_pass<TH, R, 2><<<c.flow_blocks, blk, pass_smem<TH, R>(2), s>>>(a);
+  if (pass == 1) k_pass<TH, R, 1, CP><<<c.flow_blocks, blk, pass_smem<TH, R, CP>(1), s>>>(a);
+  else if (pass == 2) k_pass<TH, R, 2, CP><<<c.flow_blocks, blk, pass_smem<TH, R, CP>(2), s>>>(a);
   else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 
+template <int TH>
+static cudaError_t pass_th(const LaunchCtx& c, int pass, int cur, cudaStream_t s) {
+  switch (c.prec) {
+    case PREC_F32C: return pass_t<TH, float, true>(c, pass, cur, s);
+    case PREC_F64: return pass_t<TH, double, false>(c, pass, cur, s);
+    default: return pass_t<TH, float, false>(c, pass, cur, s);
+  }
+}
+
 cudaError_t launch_pass(const LaunchCtx& c, int pass, int cur, cudaStream_t s) {
-  if (c.theory == TH_AH) return c.prec == 1 ? pass_t<TH_AH, float>(c, pass, cur, s) : pass_t<TH_AH, double>(c, pass, cur, s);
-  return c.prec == 1 ? pass_t<TH_CM, float>(c, pass, cur, s) : pass_t<TH_CM, double>(c, pass, cur, s);
+  return c.theory == TH_AH ? pass_th<TH_AH>(c, pass, cur, s) : pass_th<TH_CM>(c, pass, cur, s);
 }
 
 cudaError_t launch_reset_state(const LaunchCtx& c, cudaStream_t s) {
@@ -573,38 +712,47 @@ cudaError_t launch_scaled_copy(const LaunchCtx& c, void* out, const void* in, do
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const int blocks = (int)((n + 255) / 256 < (size_t)nsm * 8 ? (n + 255) / 256 : (size_t)nsm * 8);
-  if (c.prec == 1) k_scaled_copy<float><<<blocks, 256, 0, s>>>((float*)out, (const float*)in, n, (float)scale);
+  if (c.prec != PREC_F64) k_scaled_copy<float><<<blocks, 256, 0, s>>>((float*)out, (const float*)in, n, (float)scale);
   else k_scaled_copy<double><<<blocks, 256, 0, s>>>((double*)out, (const double*)in, n, scale);
   return cudaGetLastError();
 }
 
 // Opt the pass kernels into their dynamic shared memory, then size the grid by
 // the smaller occupancy of the two passes.
-template <int TH, typename R>
+template <int TH, typename R, bool CP>
 static int pass_occupancy() {
-  cudaFuncSetAttribute(k_pass<TH, R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pass_smem<TH, R>(1));
-  cudaFuncSetAttribute(k_pass<TH, R, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pass_smem<TH, R>(2));
+  cudaFuncSetAttribute(k_pass<TH, R, 1, CP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)pass_smem<TH, R, CP>(1));
+  cudaFuncSetAttribute(k_pass<TH, R, 2, CP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)pass_smem<TH, R, CP>(2));
   int b1 = 0, b2 = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_pass<TH, R, 1>, NT, pass_smem<TH, R>(1));
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_pass<TH, R, 2>, NT, pass_smem<TH, R>(2));
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_pass<TH, R, 1, CP>, NT, pass_smem<TH, R, CP>(1));
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_pass<TH, R, 2, CP>, NT, pass_smem<TH, R, CP>(2));
   const int m = b1 < b2 ? b1 : b2;
   return m < 1 ? 1 : m;
+}
+
+template <int TH>
+static int occupancy_th(int prec) {
+  switch (prec) {
+    case PREC_F32C: return pass_occupancy<TH, float, true>();
+    case PREC_F64: return pass_occupancy<TH, double, false>();
+    default: return pass_occupancy<TH, float, false>();
+  }
 }
 
 int flow_grid(int theory, int prec, int nx, int ny) {
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  int occ, ntiles;
-  if (prec == 1) {
-    occ = theory == TH_AH ? pass_occupancy<TH_AH, float>() : pass_occupancy<TH_CM, float>();
-    ntiles = ((nx + FlowTile<float>::TX - 1) / FlowTile<float>::TX) *
-             ((ny + FlowTile<float>::TY - 1) / FlowTile<float>::TY);
-  } else {
-    occ = theory == TH_AH ? pass_occupancy<TH_AH, double>() : pass_occupancy<TH_CM, double>();
+  const int occ = theory == TH_AH ? occupancy_th<TH_AH>(prec) : occupancy_th<TH_CM>(prec);
+  int ntiles;
+  if (prec == PREC_F64)
     ntiles = ((nx + FlowTile<double>::TX - 1) / FlowTile<double>::TX) *
              ((ny + FlowTile<double>::TY - 1) / FlowTile<double>::TY);
-  }
+  else
+    ntiles = ((nx + FlowTile<float>::TX - 1) / FlowTile<float>::TX) *
+             ((ny + FlowTile<float>::TY - 1) / FlowTile<float>::TY);
   const int g = nsm * occ;
   return ntiles < g ? ntiles : g;
 }

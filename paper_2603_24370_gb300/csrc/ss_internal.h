@@ -10,6 +10,10 @@
 
 namespace ss {
 
+// Precision codes (the SS_FP* values of soliton.h): compensated FP32 fields (hi + lo
+// planes), all-FP64, single-plane FP32.
+enum { PREC_F32C = 1, PREC_F64 = 2, PREC_F32 = 3 };
+
 // Everything a launch needs about one context, prepared by the runtime.
 struct LaunchCtx {
   int theory;      // TH_AH / TH_CM
@@ -18,7 +22,8 @@ struct LaunchCtx {
   size_t plane;    // nx * ny
   double dx, dy, dt;
   double coup[10]; // Couplings layout of ss_device.cuh, in FP64
-  void* phi[2];    // ping-pong field buffers [C][ny][nx]
+  void* phi[2];    // ping-pong field buffers [C][ny][nx] (hi part when compensated)
+  void* lo[2];     // compensated FP32: lo parts of phi[2] (else unused)
   void* v[2];      // ping-pong velocity buffers
   void* kv[2];     // RK stage accelerations k_v1, k_v2 (k_v3, k_v4 never leave registers)
   DevState* st;

@@ -254,8 +254,9 @@ static cudaError_t obs_t(const LaunchCtx& c, int cur, cudaStream_t s) {
 }
 
 cudaError_t launch_observables(const LaunchCtx& c, int cur, cudaStream_t s) {
-  if (c.theory == TH_AH) return c.prec == 1 ? obs_t<TH_AH, float>(c, cur, s) : obs_t<TH_AH, double>(c, cur, s);
-  return c.prec == 1 ? obs_t<TH_CM, float>(c, cur, s) : obs_t<TH_CM, double>(c, cur, s);
+  const bool f = c.prec != PREC_F64;  // every FP32 mode stores its (hi) field in float
+  if (c.theory == TH_AH) return f ? obs_t<TH_AH, float>(c, cur, s) : obs_t<TH_AH, double>(c, cur, s);
+  return f ? obs_t<TH_CM, float>(c, cur, s) : obs_t<TH_CM, double>(c, cur, s);
 }
 
 template <int TH, typename R>
@@ -267,8 +268,9 @@ static cudaError_t ansatz_t(const LaunchCtx& c, const double* sol, int n, cudaSt
 }
 
 cudaError_t launch_ansatz(const LaunchCtx& c, const double* d_sol, int n, cudaStream_t s) {
-  if (c.theory == TH_AH) return c.prec == 1 ? ansatz_t<TH_AH, float>(c, d_sol, n, s) : ansatz_t<TH_AH, double>(c, d_sol, n, s);
-  return c.prec == 1 ? ansatz_t<TH_CM, float>(c, d_sol, n, s) : ansatz_t<TH_CM, double>(c, d_sol, n, s);
+  const bool f = c.prec != PREC_F64;
+  if (c.theory == TH_AH) return f ? ansatz_t<TH_AH, float>(c, d_sol, n, s) : ansatz_t<TH_AH, double>(c, d_sol, n, s);
+  return f ? ansatz_t<TH_CM, float>(c, d_sol, n, s) : ansatz_t<TH_CM, double>(c, d_sol, n, s);
 }
 
 template <int TH, typename R>
@@ -283,8 +285,9 @@ int obs_grid(int theory, int prec, int ntiles) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   int occ;
-  if (theory == TH_AH) occ = prec == 1 ? obs_occ<TH_AH, float>() : obs_occ<TH_AH, double>();
-  else occ = prec == 1 ? obs_occ<TH_CM, float>() : obs_occ<TH_CM, double>();
+  const bool f = prec != PREC_F64;
+  if (theory == TH_AH) occ = f ? obs_occ<TH_AH, float>() : obs_occ<TH_AH, double>();
+  else occ = f ? obs_occ<TH_CM, float>() : obs_occ<TH_CM, double>();
   const int g = nsm * occ;
   return ntiles < g ? ntiles : g;
 }

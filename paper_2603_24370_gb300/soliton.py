@@ -27,8 +27,9 @@ SS_ERR_NONFINITE = -5
 SS_ERR_NOT_CONVERGED = -6
 SS_ERR_NOMEM = -7
 
-SS_FP32 = 1
+SS_FP32 = 1        # compensated FP32 fields (value + remainder planes)
 SS_FP64 = 2
+SS_FP32_PLAIN = 3  # one FP32 plane per component
 SS_ABELIAN_HIGGS = 1
 SS_CHIRAL_MAGNET = 2
 
@@ -249,7 +250,7 @@ class Solver:
         self.theory, self.nx, self.ny, self.dx, self.dy = theory, nx, ny, dx, dy
         self.precision = precision
         self.C = 4 if theory == SS_ABELIAN_HIGGS else 3
-        self.dtype = np.float32 if precision == SS_FP32 else np.float64
+        self.dtype = np.float64 if precision == SS_FP64 else np.float32
         self.ctx = ss_create_grid(nx, ny, dx, dy, precision, stream)
         try:
             ss_set_theory(self.ctx, theory, params)
