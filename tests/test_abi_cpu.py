@@ -51,7 +51,7 @@ def test_version_and_empty_error(lib):
     (10, 10, 0.0, 0.1, 1),     # non-positive spacing
     (10, 10, 0.1, -1.0, 2),
     (10, 10, float("nan"), 0.1, 2),
-    (10, 10, 0.1, 0.1, 3),     # unknown precision
+    (10, 10, 0.1, 0.1, 4),     # unknown precision
 ])
 def test_create_grid_rejects_bad_arguments_on_the_host(lib, nx, ny, dx, dy, prec):
     from paper_2603_24370_gb300 import soliton as S
