@@ -53,8 +53,9 @@ extern "C" {
 
 /* ---- precisions ---- */
 #define SS_FP32 1       /* compensated FP32: each field component is stored as two   */
-                        /* FP32 planes (value + rounding remainder), stencils in FP32 */
-                        /* applied to each part, reductions in FP64 (compensated)    */
+                        /* FP32 planes (value + rounding remainder) so that small    */
+                        /* flow increments accumulate; stencils and forces in FP32,  */
+                        /* reductions in FP64 (compensated)                          */
 #define SS_FP64 2       /* all-FP64 reference form                                    */
 #define SS_FP32_PLAIN 3 /* one FP32 plane per component: fastest, but field rounding  */
                         /* limits the attainable dx dy max|G| to about 1e-5           */
@@ -143,6 +144,11 @@ int ss_set_fields(ss_ctx* ctx, const void* fields, int is_device);
 /* Copy the current field [C][ny][nx] (context precision) out to the caller.
  * Errors: SS_ERR_STATE, SS_ERR_ARG, SS_ERR_CUDA. */
 int ss_get_fields(ss_ctx* ctx, void* fields, int is_device);
+
+/* SS_FP32 contexts: copy the rounding remainder of the current field [C][ny][nx]
+ * (float), so that value + remainder (summed in FP64) is the field the flow holds;
+ * other precisions write zeros. Errors as ss_get_fields. */
+int ss_get_remainder(ss_ctx* ctx, void* remainder, int is_device);
 
 /* Copy the current velocity phi-dot [C][ny][nx] out, with a pending arrest (Eq. 4)
  * applied (zeros if the last step raised the energy). Errors as ss_get_fields. */

@@ -275,7 +275,8 @@ int ss_set_theory(ss_ctx* c, int theory, const double* params, int n_params) {
     const size_t stb = align256(sizeof(DevState));
     const size_t fpb = align256(sizeof(FlowPartial) * (size_t)fb);
     const size_t opb = align256(sizeof(ObsPartial) * (size_t)ob);
-    const int nbuf = NBUF + (c->prec == SS_FP32 ? 2 : 0);
+    const bool comp = c->prec == SS_FP32;
+    const int nbuf = NBUF + (comp ? 2 : 0);
     const size_t total = nbuf * pb + stb + fpb + opb;
     cudaError_t e = cudaMalloc(&c->base, total);
     if (e != cudaSuccess) {
@@ -291,7 +292,7 @@ int ss_set_theory(ss_ctx* c, int theory, const double* params, int n_params) {
     c->L.v[1] = p; p += pb;
     for (int i = 0; i < 2; ++i) { c->L.kv[i] = p; p += pb; }
     c->L.lo[0] = c->L.lo[1] = nullptr;
-    if (c->prec == SS_FP32) {
+    if (comp) {
       c->L.lo[0] = p; p += pb;
       c->L.lo[1] = p; p += pb;
     }
@@ -369,6 +370,23 @@ int ss_get_fields(ss_ctx* c, void* f, int is_device) {
   const size_t bytes = (size_t)c->C * c->L.plane * c->elem;
   SS_CK(cudaMemcpyAsync(f, c->L.phi[c->cur], bytes, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                         c->stream));
+  SS_CK(cudaStreamSynchronize(c->stream));
+  return SS_OK;
+}
+
+int ss_get_remainder(ss_ctx* c, void* lo, int is_device) {
+  int rc = check_ready(c);
+  if (rc != SS_OK) return rc;
+  if (!lo) return fail(SS_ERR_ARG, "remainder is NULL");
+  const size_t bytes = (size_t)c->C * c->L.plane * c->elem;
+  if (c->prec == SS_FP32) {
+    SS_CK(cudaMemcpyAsync(lo, c->L.lo[c->cur], bytes, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                          c->stream));
+  } else if (is_device) {
+    SS_CK(cudaMemsetAsync(lo, 0, bytes, c->stream));
+  } else {
+    std::memset(lo, 0, bytes);
+  }
   SS_CK(cudaStreamSynchronize(c->stream));
   return SS_OK;
 }

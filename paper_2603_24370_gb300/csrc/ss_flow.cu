@@ -27,15 +27,14 @@
 // when the step is arrested v counts as zero, so Y_2 = Y_1 and k_v2 = k_v1, and
 // pass 2 simply reads k_v1 in place of k_v2 (and zero in place of v).
 //
-// Compensated FP32 (CP): the field is stored as two FP32 planes, phi = hi + lo with
-// |lo| <= ulp(hi)/2. Every stage input is hi + S with a small part S (lo plus the
-// stage increment), and every derivative is formed as D(hi) + D(S), the differences
-// taken within each part first. Rounding of the stored values therefore never
-// reaches the force through the 1/h^2 of Eq. 2; in single FP32 that amplified
-// rounding (~3e-8 per site) kicks the stiffest modes every step and the arrest test
-// stalls the flow above dx dy max|G| ~ 1e-6. The chiral-magnet normalisation is
-// done in the same split form, and the new field is re-split by TwoSum.
-//
+// Compensated FP32 (LO): the field is stored as two FP32 planes, phi = hi + lo with
+// |lo| <= ulp(hi)/2, and pass 2 adds each step's increment to lo and re-splits by
+// TwoSum, so increments far below an ulp of the field still accumulate. With a
+// single FP32 plane they are rounded away once the flow is slow, and the flow
+// stalls above dx dy max|G| ~ 1e-6 while arresting every other step. The stage
+// inputs are formed as hi + (lo + increment), normalised in split form for the
+// chiral magnet, and rounded once to FP32 for the stencils.
+
 // Per block a tile of TX x TY sites is staged in shared memory with its halo, the
 // stage inputs formed while loading (two sites per iteration, loads first). Each
 // thread then walks RY rows of one column with a 5-row register window per
@@ -54,16 +53,16 @@ struct FlowTile {
 template <typename R>
 struct PassArgs {
   const R* __restrict__ phi;       // phi^n (current field; hi part when compensated)
-  const R* __restrict__ lo;        // CP: lo part of phi^n
+  const R* __restrict__ lo;        // LO: remainder part of phi^n
   const R* __restrict__ phi_prev;  // pass 1: phi^{n-1} (other ping-pong buffer)
-  const R* __restrict__ lo_prev;   // CP pass 1: lo part of phi^{n-1}
+  const R* __restrict__ lo_prev;   // LO pass 1: remainder part of phi^{n-1}
   const R* __restrict__ v;         // v^n
   const R* __restrict__ kv1;       // pass 2
   const R* __restrict__ kv2;       // pass 2
   R* __restrict__ kv1_out;         // pass 1
   R* __restrict__ kv2_out;         // pass 1
   R* __restrict__ phi_out;         // pass 2: phi^{n+1} (hi)
-  R* __restrict__ lo_out;          // CP pass 2: lo part of phi^{n+1}
+  R* __restrict__ lo_out;          // LO pass 2: remainder part of phi^{n+1}
   R* __restrict__ v_out;           // pass 2: v^{n+1}
   int nx, ny;
   size_t plane;
@@ -123,13 +122,10 @@ __device__ __forceinline__ void normalise_split(const float* hi, float* t) {
 }
 
 // Sliding 5-row window over one component plane of the shared tile, for one
-// column. MIX keeps the x-stencil of all five rows for the mixed derivative. With
-// CP every quantity is formed on the hi plane and the small plane separately, then
-// added (differences first within each plane).
-template <typename R, bool MIX, bool CP>
+// column. MIX keeps the x-stencil of all five rows for the mixed derivative.
+template <typename R, bool MIX>
 struct Win {
-  R c[5];   // centre values of rows y-2 .. y+2 (hi part when CP)
-  R s[5];   // CP: small parts of the centre values
+  R c[5];   // centre values of rows y-2 .. y+2
   R g[5];   // MIX: unscaled Eq. 1 along x of rows y-2 .. y+2
   R xx[5];  // MIX: unscaled Eq. 2 along x of rows y-2 .. y+2
 
@@ -138,33 +134,16 @@ struct Win {
     gx = R(8) * (p1 - m1) - (p2 - m2);
     gxx = R(16) * ((p1 - ce) + (m1 - ce)) - ((p2 - ce) + (m2 - ce));
   }
-  // P: the row's centre in the hi (or only) plane; Q: the same in the small plane.
-  __device__ __forceinline__ void enter(const R* P, const R* Q, int slot) {
+  // P points at the row's centre.
+  __device__ __forceinline__ void enter(const R* P, int slot) {
     const R ce = P[0];
     c[slot] = ce;
-    R cs = R(0);
-    if (CP) {
-      cs = Q[0];
-      s[slot] = cs;
-    }
-    if (MIX) {
-      R gx, gxx;
-      xterms(P, ce, gx, gxx);
-      if (CP) {
-        R gs, gxs;
-        xterms(Q, cs, gs, gxs);
-        gx += gs;
-        gxx += gxs;
-      }
-      g[slot] = gx;
-      xx[slot] = gxx;
-    }
+    if (MIX) xterms(P, ce, g[slot], xx[slot]);
   }
   __device__ __forceinline__ void shift() {
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       c[k] = c[k + 1];
-      if (CP) s[k] = s[k + 1];
       if (MIX) { g[k] = g[k + 1]; xx[k] = xx[k + 1]; }
     }
   }
@@ -172,29 +151,23 @@ struct Win {
   __device__ __forceinline__ static R yd2(const R* a) {
     return R(16) * ((a[3] - a[2]) + (a[1] - a[2])) - ((a[4] - a[2]) + (a[0] - a[2]));
   }
-  // Derivatives at the window's centre row; Pc / Qc point at that row's centre.
+  // Derivatives at the window's centre row; Pc points at that row's centre.
   template <bool SECOND>
-  __device__ __forceinline__ void derivs(const R* Pc, const R* Qc, const Spacing<R>& h, R& v, R& fx, R& fy, R& fxx,
-                                         R& fyy, R& fxy) const {
+  __device__ __forceinline__ void derivs(const R* Pc, const Spacing<R>& h, R& v, R& fx, R& fy, R& fxx, R& fyy,
+                                         R& fxy) const {
     R gx, gxx;
     if (MIX) {
       gx = g[2];
       gxx = xx[2];
     } else {
       xterms(Pc, c[2], gx, gxx);
-      if (CP) {
-        R gs, gxs;
-        xterms(Qc, s[2], gs, gxs);
-        gx += gs;
-        gxx += gxs;
-      }
     }
-    v = CP ? c[2] + s[2] : c[2];
-    fx = gx * h.i12dx;                                // Eq. 1, x
-    fy = (CP ? yd1(c) + yd1(s) : yd1(c)) * h.i12dy;  // Eq. 1, y
+    v = c[2];
+    fx = gx * h.i12dx;        // Eq. 1, x
+    fy = yd1(c) * h.i12dy;    // Eq. 1, y
     if (SECOND) {
-      fxx = gxx * h.i12dx2;                                // Eq. 2, x
-      fyy = (CP ? yd2(c) + yd2(s) : yd2(c)) * h.i12dy2;   // Eq. 2, y
+      fxx = gxx * h.i12dx2;   // Eq. 2, x
+      fyy = yd2(c) * h.i12dy2;  // Eq. 2, y
     } else {
       fxx = fyy = R(0);
     }
@@ -203,21 +176,20 @@ struct Win {
 };
 
 // Window set of one stage input: all C components, mixed derivatives for the gauge
-// field of the Abelian Higgs model (components 2, 3). H: hi (or only) tile set;
-// Sm: small-part tile set (CP).
-template <int TH, typename R, bool CP>
+// field of the Abelian Higgs model (components 2, 3).
+template <int TH, typename R>
 struct StageWin {
   static constexpr int C = NComp<TH>::C;
   static constexpr int SXY = FlowTile<R>::SXY;
-  Win<R, false, CP> w0, w1;
-  Win<R, TH == TH_AH, CP> w2;
-  Win<R, TH == TH_AH, CP> w3;  // unused for the chiral magnet
+  Win<R, false> w0, w1;
+  Win<R, TH == TH_AH> w2;
+  Win<R, TH == TH_AH> w3;  // unused for the chiral magnet
 
-  __device__ __forceinline__ void enter(const R* H, const R* Sm, int off, int slot) {
-    w0.enter(H + off, Sm + off, slot);
-    w1.enter(H + SXY + off, Sm + SXY + off, slot);
-    w2.enter(H + 2 * SXY + off, Sm + 2 * SXY + off, slot);
-    if (C == 4) w3.enter(H + 3 * SXY + off, Sm + 3 * SXY + off, slot);
+  __device__ __forceinline__ void enter(const R* tiles, int off, int slot) {
+    w0.enter(tiles + off, slot);
+    w1.enter(tiles + SXY + off, slot);
+    w2.enter(tiles + 2 * SXY + off, slot);
+    if (C == 4) w3.enter(tiles + 3 * SXY + off, slot);
   }
   __device__ __forceinline__ void shift() {
     w0.shift();
@@ -225,13 +197,12 @@ struct StageWin {
     w2.shift();
     if (C == 4) w3.shift();
   }
-  __device__ __forceinline__ void derivs(const R* H, const R* Sm, int off, const Spacing<R>& h, R* v, R* fx, R* fy,
-                                         R* fxx, R* fyy, R* fxy) const {
-    w0.template derivs<true>(H + off, Sm + off, h, v[0], fx[0], fy[0], fxx[0], fyy[0], fxy[0]);
-    w1.template derivs<true>(H + SXY + off, Sm + SXY + off, h, v[1], fx[1], fy[1], fxx[1], fyy[1], fxy[1]);
-    w2.template derivs<true>(H + 2 * SXY + off, Sm + 2 * SXY + off, h, v[2], fx[2], fy[2], fxx[2], fyy[2], fxy[2]);
-    if (C == 4)
-      w3.template derivs<true>(H + 3 * SXY + off, Sm + 3 * SXY + off, h, v[3], fx[3], fy[3], fxx[3], fyy[3], fxy[3]);
+  __device__ __forceinline__ void derivs(const R* tiles, int off, const Spacing<R>& h, R* v, R* fx, R* fy, R* fxx,
+                                         R* fyy, R* fxy) const {
+    w0.template derivs<true>(tiles + off, h, v[0], fx[0], fy[0], fxx[0], fyy[0], fxy[0]);
+    w1.template derivs<true>(tiles + SXY + off, h, v[1], fx[1], fy[1], fxx[1], fyy[1], fxy[1]);
+    w2.template derivs<true>(tiles + 2 * SXY + off, h, v[2], fx[2], fy[2], fxx[2], fyy[2], fxy[2]);
+    if (C == 4) w3.template derivs<true>(tiles + 3 * SXY + off, h, v[3], fx[3], fy[3], fxx[3], fyy[3], fxy[3]);
   }
 };
 
@@ -240,10 +211,10 @@ template <int TH, typename R>
 struct DiffWin {
   static constexpr int C = NComp<TH>::C;
   static constexpr int SXY = FlowTile<R>::SXY;
-  Win<R, false, false> w[C];
+  Win<R, false> w[C];
   __device__ __forceinline__ void enter(const R* tiles, int off, int slot) {
 #pragma unroll
-    for (int c = 0; c < C; ++c) w[c].enter(tiles + c * SXY + off, nullptr, slot);
+    for (int c = 0; c < C; ++c) w[c].enter(tiles + c * SXY + off, slot);
   }
   __device__ __forceinline__ void shift() {
 #pragma unroll
@@ -253,7 +224,7 @@ struct DiffWin {
 #pragma unroll
     for (int c = 0; c < C; ++c) {
       R unused0, unused1, unused2;
-      w[c].template derivs<false>(tiles + c * SXY + off, nullptr, h, v[c], fx[c], fy[c], unused0, unused1, unused2);
+      w[c].template derivs<false>(tiles + c * SXY + off, h, v[c], fx[c], fy[c], unused0, unused1, unused2);
     }
   }
 };
@@ -265,15 +236,9 @@ __device__ __forceinline__ void force_at(const Couplings<R>& k, const R* v, cons
   else force_cm<R>(k, v, fx, fy, fxx, fyy, G);
 }
 
-// Tile-set layout in shared memory (each set is C planes of SXY values):
-//   pass 1, single: [Y1 | Y2 | delta]           CP: [hi | S1 | S2 | delta]
-//   pass 2, single: [Y3 | Y4]                   CP: [hi | S3 | S4]
-template <int PASS, bool CP>
-struct Sets {
-  static constexpr int n = (PASS == 1 ? 3 : 2) + (CP ? 1 : 0);
-};
-
-template <int TH, typename R, int PASS, bool CP>
+// Tile sets in shared memory (each C planes of SXY values): pass 1 [Y1 | Y2 | delta],
+// pass 2 [Y3 | Y4]. LO: compensated FP32 storage (value + remainder planes).
+template <int TH, typename R, int PASS, bool LO>
 __global__ void __launch_bounds__(NT) k_pass(PassArgs<R> a) {
   using T = FlowTile<R>;
   constexpr int C = NComp<TH>::C;
@@ -296,13 +261,9 @@ __global__ void __launch_bounds__(NT) k_pass(PassArgs<R> a) {
   const size_t P = a.plane;
   const R dt = a.dt, hdt = R(0.5) * a.dt;
   const R c3 = R(0.25) * dt * dt, c4 = R(0.5) * dt * dt;
-  // Set pointers. Single precision / FP64: A = first stage input, B = second stage
-  // input, D = delta (pass 1). CP: H = hi, A = small part of the first stage input,
-  // B = small part of the second, D = delta.
-  R* const setH = sm;                                 // CP only
-  R* const setA = sm + (CP ? PS : 0);
-  R* const setB = sm + (CP ? 2 * PS : PS);
-  R* const setD = sm + (CP ? 3 * PS : 2 * PS);        // pass 1 only
+  R* const setA = sm;           // first stage input of the pass
+  R* const setB = sm + PS;      // second stage input
+  R* const setD = sm + 2 * PS;  // pass 1: phi^n - phi^{n-1}
 
   R es = R(0), ec = R(0), ds = R(0), dc = R(0), gmr = R(0);
 
@@ -326,11 +287,11 @@ __global__ void __launch_bounds__(NT) k_pass(PassArgs<R> a) {
 #pragma unroll
         for (int c = 0; c < C; ++c) {
           pv[u][c] = in[u] ? a.phi[c * P + s] : R(0);
-          lv[u][c] = (CP && in[u]) ? a.lo[c * P + s] : R(0);
+          lv[u][c] = (LO && in[u]) ? a.lo[c * P + s] : R(0);
           vv[u][c] = (inside[u] && !arrest) ? a.v[c * P + s] : R(0);
           if (PASS == 1) {
             pp[u][c] = (has_prev && in[u]) ? a.phi_prev[c * P + s] : pv[u][c];
-            lp[u][c] = (CP && has_prev && in[u]) ? a.lo_prev[c * P + s] : lv[u][c];
+            lp[u][c] = (LO && has_prev && in[u]) ? a.lo_prev[c * P + s] : lv[u][c];
           } else {
             k1v[u][c] = inside[u] ? a.kv1[c * P + s] : R(0);
             k2v[u][c] = inside[u] ? (arrest ? k1v[u][c] : a.kv2[c * P + s]) : R(0);
@@ -346,8 +307,8 @@ __global__ void __launch_bounds__(NT) k_pass(PassArgs<R> a) {
 #pragma unroll
           for (int c = 0; c < C; ++c) {
             // delta = phi^n - phi^{n-1} (differences of neighbouring values: exact per part)
-            yd[c] = CP ? (pv[u][c] - pp[u][c]) + (lv[u][c] - lp[u][c]) : pv[u][c] - pp[u][c];
-            if (CP) {
+            yd[c] = LO ? (pv[u][c] - pp[u][c]) + (lv[u][c] - lp[u][c]) : pv[u][c] - pp[u][c];
+            if (LO) {
               ya[c] = lv[u][c];
               yb[c] = lv[u][c] + hdt * vv[u][c];
             } else {
@@ -356,19 +317,26 @@ __global__ void __launch_bounds__(NT) k_pass(PassArgs<R> a) {
             }
           }
           if (TH == TH_CM && inside[u]) {
-            if constexpr (CP) normalise_split(pv[u], yb);
+            if constexpr (LO) normalise_split(pv[u], yb);
             else normalise<C>(yb);
+          }
+          if (LO) {  // stage inputs: value + small part, rounded once
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+              ya[c] = pv[u][c] + ya[c];
+              yb[c] = pv[u][c] + yb[c];
+            }
           }
         } else {
 #pragma unroll
           for (int c = 0; c < C; ++c) {
             const R base3 = hdt * vv[u][c] + c3 * k1v[u][c];
             const R base4 = dt * vv[u][c] + c4 * k2v[u][c];
-            ya[c] = CP ? lv[u][c] + base3 : pv[u][c] + base3;
-            yb[c] = CP ? lv[u][c] + base4 : pv[u][c] + base4;
+            ya[c] = LO ? lv[u][c] + base3 : pv[u][c] + base3;
+            yb[c] = LO ? lv[u][c] + base4 : pv[u][c] + base4;
           }
           if (TH == TH_CM && inside[u]) {
-            if constexpr (CP) {
+            if constexpr (LO) {
               normalise_split(pv[u], ya);
               normalise_split(pv[u], yb);
             } else {
@@ -376,10 +344,16 @@ __global__ void __launch_bounds__(NT) k_pass(PassArgs<R> a) {
               normalise<C>(yb);
             }
           }
+          if (LO) {
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+              ya[c] = pv[u][c] + ya[c];
+              yb[c] = pv[u][c] + yb[c];
+            }
+          }
         }
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-          if (CP) setH[c * T::SXY + idx] = pv[u][c];
           setA[c * T::SXY + idx] = ya[c];
           setB[c * T::SXY + idx] = yb[c];
           if (PASS == 1) setD[c * T::SXY + idx] = has_prev ? yd[c] : R(0);
@@ -392,20 +366,16 @@ __global__ void __launch_bounds__(NT) k_pass(PassArgs<R> a) {
     const int sx = threadIdx.x + 2, sy0 = threadIdx.y * RY + 2;
     const int gx = x0 + threadIdx.x, gyb = y0 + threadIdx.y * RY;
     const bool colok = gx >= 2 && gx < a.nx - 2;
-    // window planes: CP reads hi from setH and the small part from the stage set;
-    // otherwise the stage set is the whole input (the small-part pointer is unused).
-    const R* const HA = CP ? setH : setA;
-    const R* const HB = CP ? setH : setB;
 
     if (PASS == 1) {
       // stage 1 at Y_1 = phi: k_v1, e, max|G|, and e(phi^n) - e(phi^{n-1})
       {
-        StageWin<TH, R, CP> W;
+        StageWin<TH, R> W;
         DiffWin<TH, R> D;
 #pragma unroll
         for (int s = 0; s < 5; ++s) {
           const int off = (sy0 - 2 + s) * T::SX + sx;
-          W.enter(HA, setA, off, s);
+          W.enter(setA, off, s);
           if (has_prev) D.enter(setD, off, s);
         }
 #pragma unroll
@@ -413,7 +383,7 @@ __global__ void __launch_bounds__(NT) k_pass(PassArgs<R> a) {
           const int off = (sy0 + r) * T::SX + sx;
           const bool ok = colok && gyb + r >= 2 && gyb + r < a.ny - 2;
           R v[C], fx[C], fy[C], fxx[C], fyy[C], fxy[C], G[C];
-          W.derivs(HA, setA, off, a.h, v, fx, fy, fxx, fyy, fxy);
+          W.derivs(setA, off, a.h, v, fx, fy, fxx, fyy, fxy);
           force_at<TH, R>(a.k, v, fx, fy, fxx, fyy, fxy, G);
           if (ok) {
             const size_t s = (size_t)(gyb + r) * a.nx + gx;
@@ -442,7 +412,7 @@ __global__ void __launch_bounds__(NT) k_pass(PassArgs<R> a) {
           if (r + 1 < RY) {
             const int noff = (sy0 + r + 3) * T::SX + sx;
             W.shift();
-            W.enter(HA, setA, noff, 4);
+            W.enter(setA, noff, 4);
             if (has_prev) {
               D.shift();
               D.enter(setD, noff, 4);
@@ -452,14 +422,14 @@ __global__ void __launch_bounds__(NT) k_pass(PassArgs<R> a) {
       }
       // stage 2 at Y_2 = phi + dt/2 v: k_v2
       {
-        StageWin<TH, R, CP> W;
+        StageWin<TH, R> W;
 #pragma unroll
-        for (int s = 0; s < 5; ++s) W.enter(HB, setB, (sy0 - 2 + s) * T::SX + sx, s);
+        for (int s = 0; s < 5; ++s) W.enter(setB, (sy0 - 2 + s) * T::SX + sx, s);
 #pragma unroll
         for (int r = 0; r < RY; ++r) {
           const int off = (sy0 + r) * T::SX + sx;
           R v[C], fx[C], fy[C], fxx[C], fyy[C], fxy[C], G[C];
-          W.derivs(HB, setB, off, a.h, v, fx, fy, fxx, fyy, fxy);
+          W.derivs(setB, off, a.h, v, fx, fy, fxx, fyy, fxy);
           force_at<TH, R>(a.k, v, fx, fy, fxx, fyy, fxy, G);
           if (colok && gyb + r >= 2 && gyb + r < a.ny - 2) {
             const size_t s = (size_t)(gyb + r) * a.nx + gx;
@@ -468,7 +438,7 @@ __global__ void __launch_bounds__(NT) k_pass(PassArgs<R> a) {
           }
           if (r + 1 < RY) {
             W.shift();
-            W.enter(HB, setB, (sy0 + r + 3) * T::SX + sx, 4);
+            W.enter(setB, (sy0 + r + 3) * T::SX + sx, 4);
           }
         }
       }
@@ -476,34 +446,34 @@ __global__ void __launch_bounds__(NT) k_pass(PassArgs<R> a) {
       // stage 3 at Y_3: k_v3 kept in registers
       R k3[RY][C];
       {
-        StageWin<TH, R, CP> W;
+        StageWin<TH, R> W;
 #pragma unroll
-        for (int s = 0; s < 5; ++s) W.enter(HA, setA, (sy0 - 2 + s) * T::SX + sx, s);
+        for (int s = 0; s < 5; ++s) W.enter(setA, (sy0 - 2 + s) * T::SX + sx, s);
 #pragma unroll
         for (int r = 0; r < RY; ++r) {
           const int off = (sy0 + r) * T::SX + sx;
           R v[C], fx[C], fy[C], fxx[C], fyy[C], fxy[C], G[C];
-          W.derivs(HA, setA, off, a.h, v, fx, fy, fxx, fyy, fxy);
+          W.derivs(setA, off, a.h, v, fx, fy, fxx, fyy, fxy);
           force_at<TH, R>(a.k, v, fx, fy, fxx, fyy, fxy, G);
 #pragma unroll
           for (int c = 0; c < C; ++c) k3[r][c] = -G[c];
           if (r + 1 < RY) {
             W.shift();
-            W.enter(HA, setA, (sy0 + r + 3) * T::SX + sx, 4);
+            W.enter(setA, (sy0 + r + 3) * T::SX + sx, 4);
           }
         }
       }
       // stage 4 at Y_4, then the RK4 combination
       {
-        StageWin<TH, R, CP> W;
+        StageWin<TH, R> W;
 #pragma unroll
-        for (int s = 0; s < 5; ++s) W.enter(HB, setB, (sy0 - 2 + s) * T::SX + sx, s);
+        for (int s = 0; s < 5; ++s) W.enter(setB, (sy0 - 2 + s) * T::SX + sx, s);
         const R w6 = dt * dt / R(6), u6 = dt / R(6);
 #pragma unroll
         for (int r = 0; r < RY; ++r) {
           const int off = (sy0 + r) * T::SX + sx;
           R v[C], fx[C], fy[C], fxx[C], fyy[C], fxy[C], G[C];
-          W.derivs(HB, setB, off, a.h, v, fx, fy, fxx, fyy, fxy);
+          W.derivs(setB, off, a.h, v, fx, fy, fxx, fyy, fxy);
           force_at<TH, R>(a.k, v, fx, fy, fxx, fyy, fxy, G);
           if (colok && gyb + r >= 2 && gyb + r < a.ny - 2) {
             const size_t s = (size_t)(gyb + r) * a.nx + gx;
@@ -515,13 +485,13 @@ __global__ void __launch_bounds__(NT) k_pass(PassArgs<R> a) {
               const R k1 = a.kv1[c * P + s];
               const R k2 = arrest ? k1 : a.kv2[c * P + s];
               const R k4 = -G[c];
-              // increment of phi; with CP it joins the stored lo part before rounding
+              // increment of phi; with compensated storage it joins the stored lo part
               const R inc = dt * v0 + w6 * (k1 + k2 + k3[r][c]);
-              q[c] = CP ? a.lo[c * P + s] + inc : p0[c] + inc;
+              q[c] = LO ? a.lo[c * P + s] + inc : p0[c] + inc;
               vn[c] = v0 + u6 * (k1 + R(2) * (k2 + k3[r][c]) + k4);
             }
             R pn[C], ln[C];
-            if constexpr (CP) {
+            if constexpr (LO) {
               if (TH == TH_CM) normalise_split(p0, q);
 #pragma unroll
               for (int c = 0; c < C; ++c) two_sum_f(p0[c], q[c], pn[c], ln[c]);  // hi' = fl(hi + small), lo' = rest
@@ -538,13 +508,13 @@ __global__ void __launch_bounds__(NT) k_pass(PassArgs<R> a) {
 #pragma unroll
             for (int c = 0; c < C; ++c) {
               a.phi_out[c * P + s] = pn[c];
-              if (CP) a.lo_out[c * P + s] = ln[c];
+              if (LO) a.lo_out[c * P + s] = ln[c];
               a.v_out[c * P + s] = vn[c];
             }
           }
           if (r + 1 < RY) {
             W.shift();
-            W.enter(HB, setB, (sy0 + r + 3) * T::SX + sx, 4);
+            W.enter(setB, (sy0 + r + 3) * T::SX + sx, 4);
           }
         }
       }
@@ -632,9 +602,9 @@ __global__ void k_scaled_copy(R* __restrict__ out, const R* __restrict__ in, siz
 }
 
 // ------------------------------------------------------------------ launchers
-template <int TH, typename R, bool CP>
+template <int TH, typename R>
 static size_t pass_smem(int pass) {
-  const int sets = pass == 1 ? Sets<1, CP>::n : Sets<2, CP>::n;
+  const int sets = pass == 1 ? 3 : 2;
   return (size_t)sets * NComp<TH>::C * FlowTile<R>::SXY * sizeof(R);
 }
 
@@ -672,12 +642,12 @@ static PassArgs<R> make_args(const LaunchCtx& c, int cur) {
   return a;
 }
 
-template <int TH, typename R, bool CP>
+template <int TH, typename R, bool LO>
 static cudaError_t pass_t(const LaunchCtx& c, int pass, int cur, cudaStream_t s) {
   const PassArgs<R> a = make_args<R>(c, cur);
   const dim3 blk(BX, BY);
-  if (pass == 1) k_pass<TH, R, 1, CP><<<c.flow_blocks, blk, pass_smem<TH, R, CP>(1), s>>>(a);
-  else if (pass == 2) k_pass<TH, R, 2, CP><<<c.flow_blocks, blk, pass_smem<TH, R, CP>(2), s>>>(a);
+  if (pass == 1) k_pass<TH, R, 1, LO><<<c.flow_blocks, blk, pass_smem<TH, R>(1), s>>>(a);
+  else if (pass == 2) k_pass<TH, R, 2, LO><<<c.flow_blocks, blk, pass_smem<TH, R>(2), s>>>(a);
   else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
@@ -719,15 +689,13 @@ cudaError_t launch_scaled_copy(const LaunchCtx& c, void* out, const void* in, do
 
 // Opt the pass kernels into their dynamic shared memory, then size the grid by
 // the smaller occupancy of the two passes.
-template <int TH, typename R, bool CP>
+template <int TH, typename R, bool LO>
 static int pass_occupancy() {
-  cudaFuncSetAttribute(k_pass<TH, R, 1, CP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)pass_smem<TH, R, CP>(1));
-  cudaFuncSetAttribute(k_pass<TH, R, 2, CP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)pass_smem<TH, R, CP>(2));
+  cudaFuncSetAttribute(k_pass<TH, R, 1, LO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pass_smem<TH, R>(1));
+  cudaFuncSetAttribute(k_pass<TH, R, 2, LO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pass_smem<TH, R>(2));
   int b1 = 0, b2 = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_pass<TH, R, 1, CP>, NT, pass_smem<TH, R, CP>(1));
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_pass<TH, R, 2, CP>, NT, pass_smem<TH, R, CP>(2));
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_pass<TH, R, 1, LO>, NT, pass_smem<TH, R>(1));
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_pass<TH, R, 2, LO>, NT, pass_smem<TH, R>(2));
   const int m = b1 < b2 ? b1 : b2;
   return m < 1 ? 1 : m;
 }

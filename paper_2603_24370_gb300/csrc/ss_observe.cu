@@ -10,6 +10,7 @@
 //          two triangles (n00, n10, n11), (n00, n11, n01)   (chiral magnet)
 //   Q    = (1/2pi) sum of wrapped arg-psi steps around the boundary of I (Abelian Higgs)
 //   max_I |G|, max ||n| - 1|
+// A compensated FP32 field is read as value + remainder, exactly, in FP64.
 #include "ss_internal.h"
 
 namespace ss {
@@ -17,6 +18,7 @@ namespace ss {
 template <typename R>
 struct ObsArgs {
   const R* __restrict__ phi;
+  const R* __restrict__ lo;  // compensated FP32: remainder plane added in FP64 (else null)
   int nx, ny;
   size_t plane;
   int ntx, ntiles;
@@ -59,7 +61,8 @@ __global__ void __launch_bounds__(NT) k_observables(ObsArgs<R> a) {
       const bool in = gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny;
       const size_t s = (size_t)gy * a.nx + gx;
 #pragma unroll
-      for (int c = 0; c < C; ++c) sY[c][idx] = in ? (double)a.phi[c * P + s] : 0.0;
+      for (int c = 0; c < C; ++c)
+        sY[c][idx] = in ? (double)a.phi[c * P + s] + (a.lo ? (double)a.lo[c * P + s] : 0.0) : 0.0;
     }
     __syncthreads();
 #pragma unroll
@@ -229,6 +232,7 @@ template <int TH, typename R>
 static cudaError_t obs_t(const LaunchCtx& c, int cur, cudaStream_t s) {
   ObsArgs<R> a{};
   a.phi = static_cast<const R*>(c.phi[cur]);
+  a.lo = static_cast<const R*>(c.lo[cur]);
   a.nx = c.nx;
   a.ny = c.ny;
   a.plane = c.plane;

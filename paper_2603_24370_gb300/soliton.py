@@ -96,6 +96,7 @@ def load_library(path: str | None = None):
             "ss_set_fields": ([vp, vp, i], i),
             "ss_get_fields": ([vp, vp, i], i),
             "ss_get_velocity": ([vp, vp, i], i),
+            "ss_get_remainder": ([vp, vp, i], i),
             "ss_force": ([vp, vp, i, pd, pd], i),
             "ss_step": ([vp, i, ctypes.POINTER(ss_status)], i),
             "ss_minimise": ([vp, d, ll, ctypes.POINTER(ss_status)], i),
@@ -169,6 +170,11 @@ def ss_set_fields(ctx, fields, dtype) -> None:
 def ss_get_fields(ctx, out) -> None:
     p, dev = _ptr(out, np.float32 if _dtype_of(out) == np.float32 else np.float64)
     _check(load_library().ss_get_fields(ctx, p, dev))
+
+
+def ss_get_remainder(ctx, out) -> None:
+    p, dev = _ptr(out, np.float32 if _dtype_of(out) == np.float32 else np.float64)
+    _check(load_library().ss_get_remainder(ctx, p, dev))
 
 
 def ss_get_velocity(ctx, out) -> None:
@@ -274,6 +280,16 @@ class Solver:
         out = np.empty(self.shape, dtype=self.dtype) if out is None else out
         ss_get_fields(self.ctx, out)
         return out
+
+    def remainder(self):
+        """Rounding remainder of a compensated FP32 field (zeros otherwise)."""
+        out = np.empty(self.shape, dtype=self.dtype)
+        ss_get_remainder(self.ctx, out)
+        return out
+
+    def exact_fields(self):
+        """value + remainder in FP64: the field the flow holds."""
+        return self.fields().astype(np.float64) + self.remainder().astype(np.float64)
 
     def velocity(self):
         out = np.empty(self.shape, dtype=self.dtype)

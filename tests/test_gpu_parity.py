@@ -186,10 +186,9 @@ def test_chiral_magnet_1024_fp32_relaxes_with_exact_charge(S):
     with S.Solver(CM, p.params, p.nx, p.ny, p.dx, p.dy, 1) as s:
         s.init_ansatz(p.soliton_array())
         st = s.minimise(1e-6, 200000)
-        fg = s.fields()
+        f64 = s.exact_fields()  # value + remainder of the compensated FP32 field
         og = s.observables()
     assert st["converged"], st
-    f64 = fg.astype(np.float64)
     oo = O.observables(CM, p.params, f64, p.dx, p.dy)
     assert og["energy"] == pytest.approx(oo["energy"], rel=1e-12)
     assert st["energy"] == pytest.approx(oo["energy"], rel=1e-6)  # the flow's FP32-density energy
