@@ -191,6 +191,52 @@ int ss_profile_stages(ss_ctx* ctx, int n_steps, float* ms_out);
 /* Release every device and host resource of the context (NULL is a no-op). */
 int ss_destroy(ss_ctx* ctx);
 
+/* ---- batches ---------------------------------------------------------------
+ * Many independent relaxations (uneven grid sizes, spacings, couplings and initial
+ * solitons; one theory and one precision) advanced together: every flow kernel
+ * launch covers the tiles of all problems, each problem keeps its own step count,
+ * arrest test (Eq. 4), convergence test and buffers, and stops on its own. Steps
+ * run in CUDA graphs of 32 steps; the host polls one counter of still-running
+ * problems per graph. Semantics per problem are those of ss_step / ss_minimise. */
+typedef struct ss_batch ss_batch;
+
+/* One problem of a batch. params / solitons are host arrays, copied at creation. */
+typedef struct {
+  int nx, ny;            /* grid incl. the width-2 halo, >= 5 each              */
+  double dx, dy;         /* spacings > 0; dt = 0.5 min(dx, dy)                  */
+  const double* params;  /* couplings as for ss_set_theory                      */
+  int n_params;
+  const ss_soliton* solitons; /* initial ansatz (ss_init_ansatz), n_solitons >= 1 */
+  int n_solitons;
+} ss_batch_item;
+
+/* Create a batch of n >= 1 problems of `theory` in `precision`, each initialised
+ * from its ansatz, at rest. cuda_stream as for ss_create_grid.
+ * Errors: SS_ERR_ARG (message names the item), SS_ERR_NOMEM, SS_ERR_CUDA. */
+int ss_batch_create(ss_batch** out, int theory, int precision, const ss_batch_item* items, int n, void* cuda_stream);
+
+/* Number of problems of the batch (0 for NULL). */
+int ss_batch_size(ss_batch* batch);
+
+/* n_steps more flow steps for every problem that has not stopped. per_item (n
+ * entries, may be NULL) receives every problem's status.
+ * Errors: SS_ERR_ARG, SS_ERR_NONFINITE (some problem stopped non-finite), SS_ERR_CUDA. */
+int ss_batch_step(ss_batch* batch, int n_steps, ss_status* per_item);
+
+/* Flow every problem until its own dx dy max|G| < tol or max_steps more steps.
+ * Returns SS_OK when all converged, SS_ERR_NOT_CONVERGED when some did not,
+ * SS_ERR_NONFINITE when some stopped non-finite; per_item (may be NULL) tells which. */
+int ss_batch_minimise(ss_batch* batch, double tol, long long max_steps, ss_status* per_item);
+
+/* Copy the current field of problem `item` ([C][ny][nx], batch precision) out. */
+int ss_batch_get_fields(ss_batch* batch, int item, void* fields, int is_device);
+
+/* Observables of problem `item`, as ss_observables. */
+int ss_batch_observables(ss_batch* batch, int item, ss_obs* out);
+
+/* Release the batch (NULL is a no-op). */
+int ss_batch_destroy(ss_batch* batch);
+
 /* Observables of a caller-owned device field without allocating anything.
  *
  * The paper has no counterpart: this entry point exists for callers that cannot

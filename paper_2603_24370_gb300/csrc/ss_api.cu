@@ -3,16 +3,20 @@
 //
 // The runtime follows the paper's workflow (Sec. 4.1): select a theory and its
 // parameters, allocate the device buffer set, initialise the field from an ansatz,
-// then minimise. The buffer set is reduced to what the fused stage kernels need
+// then minimise. Everything runs on batches: a batch is any number of independent
+// problems (grid, spacing, couplings, initial solitons) of one theory and one
+// precision, and a single-grid context (ss_ctx) is a batch of one.
+//
+// Per problem the buffer set is reduced to what the fused pass kernels need
 // (Sec. 3.1 lists fields, velocity, gradient, derivative work arrays and RK stages):
 //   phi[2], v[2]   ping-pong field and velocity (RK4 reads phi^n around each site
 //                  while writing phi^{n+1}; phi^{n-1} feeds the arrest test),
 //   kv[2]          stage accelerations k_v1, k_v2 (k_v3, k_v4 stay in registers),
-//   lo[2]          compensated FP32 only: the lo parts of phi[2],
-// plus one device status record and per-block reduction partials. Derivatives never
+//   lo[2]          compensated FP32 only: the remainder planes of phi[2],
+// plus one device flow record and one reduction partial per tile. Derivatives never
 // touch memory. Steps are enqueued as CUDA graphs of K_CHUNK steps; convergence,
-// arrest and the step budget are decided on the device, so the host only polls a
-// small status record once per chunk (one chunk ahead).
+// arrest and the step budget are decided on the device per problem, so the host
+// only polls one counter of still-running problems once per graph, one graph ahead.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -20,6 +24,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "soliton.h"
 #include "ss_internal.h"
@@ -28,8 +33,7 @@ using namespace ss;
 
 namespace {
 
-constexpr int K_CHUNK = 32;  // steps per captured graph (even: parity returns)
-constexpr int NBUF = 6;      // phi[2], v[2], kv[2] (+ lo[2] when compensated)
+constexpr int K_CHUNK = 32;  // steps per captured graph
 
 thread_local std::string g_err;
 
@@ -38,104 +42,365 @@ int fail(int code, const std::string& msg) {
   return code;
 }
 
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
 }  // namespace
 
 void ss::set_last_error(const std::string& msg) { g_err = msg; }
 
-#define SS_CK(call)                                                                            \
-  do {                                                                                         \
-    cudaError_t e_ = (call);                                                                   \
+#define SS_CK(call)                                                                                       \
+  do {                                                                                                    \
+    cudaError_t e_ = (call);                                                                              \
     if (e_ != cudaSuccess) return fail(SS_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
-struct ss_ctx {
+namespace {
+
+// Couplings of Table 1 / Eq. 5 packed as the kernels read them (Couplings in
+// ss_device.cuh). Returns SS_OK or an error code (message set).
+int pack_couplings(int theory, const double* params, int n_params, double k[10], int* C) {
+  if (!params && n_params > 0) return fail(SS_ERR_ARG, "params is NULL");
+  for (int i = 0; i < 10; ++i) k[i] = 0.0;
+  if (theory == SS_ABELIAN_HIGGS) {
+    if (n_params < 1 || n_params > 2) return fail(SS_ERR_ARG, "Abelian Higgs takes {lambda[, u]}");
+    const double lam = params[0], u = n_params > 1 ? params[1] : 1.0;
+    if (!std::isfinite(lam) || !std::isfinite(u) || lam < 0.0) return fail(SS_ERR_ARG, "lambda must be finite and >= 0");
+    k[0] = lam;
+    k[1] = u * u;
+    *C = 4;
+  } else if (theory == SS_CHIRAL_MAGNET) {
+    if (n_params < 4 || n_params > 5) return fail(SS_ERR_ARG, "chiral magnet takes {J, D, K, h[, dmi_type]}");
+    for (int i = 0; i < n_params; ++i)
+      if (!std::isfinite(params[i])) return fail(SS_ERR_ARG, "chiral-magnet parameters must be finite");
+    if (!(params[0] > 0.0)) return fail(SS_ERR_ARG, "J must be > 0");
+    const int type = n_params > 4 ? (int)params[4] : 0;
+    if (type < 0 || type > 2 || (n_params > 4 && params[4] != (double)type))
+      return fail(SS_ERR_ARG, "dmi_type must be 0 (interfacial), 1 (bulk) or 2 (D_2d)");
+    for (int i = 0; i < 4; ++i) k[i] = params[i];
+    // DMI vectors d_1 (k[4..6]) and d_2 (k[7..9]) of Eq. 5
+    if (type == 0) { k[5] = 1.0; k[7] = -1.0; }      // d_i = e_3 x e_i
+    else if (type == 1) { k[4] = 1.0; k[8] = 1.0; }  // d_i = e_i
+    else { k[4] = 1.0; k[8] = -1.0; }                // d_1 = e_1, d_2 = -e_2
+    *C = 3;
+  } else {
+    return fail(SS_ERR_ARG, "unknown theory");
+  }
+  return SS_OK;
+}
+
+int check_grid(int nx, int ny, double dx, double dy) {
+  if (nx < 5 || ny < 5) return fail(SS_ERR_ARG, "nx and ny must be >= 5 (halo of width 2 on each side)");
+  if ((long long)nx * ny > (1LL << 31)) return fail(SS_ERR_ARG, "grid too large (nx * ny > 2^31)");
+  if (!(dx > 0.0) || !(dy > 0.0) || !std::isfinite(dx) || !std::isfinite(dy))
+    return fail(SS_ERR_ARG, "dx and dy must be positive and finite");
+  return SS_OK;
+}
+
+// One problem of a batch, host view.
+struct Problem {
   int nx = 0, ny = 0;
   double dx = 0, dy = 0, dt = 0;
-  int prec = 0;
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  int theory = 0;
+  double coup[10] = {0};
+  size_t plane = 0;
+  int ntx = 0, ntiles = 0, tile0 = 0;
+  void* phi[2] = {nullptr, nullptr};
+  void* lo[2] = {nullptr, nullptr};
+  void* v[2] = {nullptr, nullptr};
+  void* kv[2] = {nullptr, nullptr};
+};
+
+template <typename R>
+ProbDesc<R> make_desc(const Problem& p, DevState* st, FlowPartial* part) {
+  ProbDesc<R> d{};
+  d.nx = p.nx;
+  d.ny = p.ny;
+  d.ntx = p.ntx;
+  d.ntiles = p.ntiles;
+  d.tile0 = p.tile0;
+  d.plane = (long long)p.plane;
+  for (int i = 0; i < 2; ++i) {
+    d.phi[i] = static_cast<R*>(p.phi[i]);
+    d.lo[i] = static_cast<R*>(p.lo[i]);
+    d.v[i] = static_cast<R*>(p.v[i]);
+    d.kv[i] = static_cast<R*>(p.kv[i]);
+  }
+  d.dt = (R)p.dt;
+  d.h.i12dx = (R)(1.0 / (12.0 * p.dx));
+  d.h.i12dy = (R)(1.0 / (12.0 * p.dy));
+  d.h.i12dx2 = (R)(1.0 / (12.0 * p.dx * p.dx));
+  d.h.i12dy2 = (R)(1.0 / (12.0 * p.dy * p.dy));
+  d.h.i144dxdy = (R)(1.0 / (144.0 * p.dx * p.dy));
+  for (int i = 0; i < 10; ++i) d.k.c[i] = (R)p.coup[i];
+  d.area = p.dx * p.dy;
+  d.st = st;
+  d.part = part;
+  return d;
+}
+
+}  // namespace
+
+// A batch of independent problems of one theory and precision.
+struct ss_batch {
+  int theory = 0;  // SS_ABELIAN_HIGGS / SS_CHIRAL_MAGNET
+  int prec = 0;    // SS_FP32 / SS_FP64 / SS_FP32_PLAIN
   int C = 0;
   size_t elem = 0;
-  bool fields_set = false;
-  int cur = 0;                    // phi[cur] holds the current field
-  void* base = nullptr;           // one device allocation for every plane
-  DevState* h_st[2] = {nullptr, nullptr};  // pinned copies of the status record
-  cudaEvent_t ev[2] = {nullptr, nullptr};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::vector<Problem> probs;
+  void* base = nullptr;         // every device buffer of the batch
+  void* desc = nullptr;         // ProbDesc<R>[n]
+  int* tile_prob = nullptr;     // [total_tiles]
+  DevState* st = nullptr;       // [n]
+  FlowPartial* part = nullptr;  // [total_tiles]
+  ObsPartial* opart = nullptr;  // observables scratch, one problem at a time
+  int obs_cap = 0;
   double* d_sol = nullptr;
   int sol_cap = 0;
-  cudaGraphExec_t chunk[2] = {nullptr, nullptr};  // K_CHUNK steps from parity 0 / 1
-  LaunchCtx L{};
+  int* d_active = nullptr;
+  BatchLaunch BL{};
+  cudaGraphExec_t chunk = nullptr;
+  DevState* h_st = nullptr;  // pinned [n]
+  int* h_active = nullptr;   // pinned [2]
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  std::vector<int> fields_set;
+  std::vector<unsigned char> one_desc;  // host copy of problem 0's descriptor
+
+  int n() const { return (int)probs.size(); }
 };
 
 namespace {
 
-size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
-
-void free_buffers(ss_ctx* c) {
-  for (int p = 0; p < 2; ++p)
-    if (c->chunk[p]) { cudaGraphExecDestroy(c->chunk[p]); c->chunk[p] = nullptr; }
-  if (c->base) { cudaFree(c->base); c->base = nullptr; }
-  c->fields_set = false;
+void batch_free(ss_batch* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->chunk) cudaGraphExecDestroy(b->chunk);
+  if (b->base) cudaFree(b->base);
+  if (b->d_sol) cudaFree(b->d_sol);
+  if (b->h_st) cudaFreeHost(b->h_st);
+  if (b->h_active) cudaFreeHost(b->h_active);
+  for (int i = 0; i < 2; ++i)
+    if (b->ev[i]) cudaEventDestroy(b->ev[i]);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  delete b;
 }
 
-// Parity bookkeeping: the device counts steps; the field sits in phi[steps & 1]
-// relative to the parity the fields were set at (always 0).
-int refresh(ss_ctx* c, DevState* h) {
-  c->cur = (int)(h->steps & 1);
+// Allocate and lay out every buffer of a batch whose problems are filled in.
+int batch_alloc(ss_batch* b) {
+  const int n = b->n();
+  int tx, ty;
+  flow_tile_dims(b->prec, &tx, &ty);
+  const int nbuf = 6 + (b->prec == SS_FP32 ? 2 : 0);
+  size_t bytes = 0;
+  int total_tiles = 0, obs_need = 1;
+  const int th = b->theory == SS_ABELIAN_HIGGS ? TH_AH : TH_CM;
+  for (Problem& p : b->probs) {
+    p.plane = (size_t)p.nx * p.ny;
+    p.ntx = (p.nx + tx - 1) / tx;
+    p.ntiles = p.ntx * ((p.ny + ty - 1) / ty);
+    p.tile0 = total_tiles;
+    total_tiles += p.ntiles;
+    bytes += nbuf * align256((size_t)b->C * p.plane * b->elem);
+    const int otiles = ((p.nx + TX - 1) / TX) * ((p.ny + TY - 1) / TY);
+    const int og = obs_grid(th, b->prec, otiles);
+    if (og > obs_need) obs_need = og;
+  }
+  const size_t desc_b = align256((b->prec == SS_FP64 ? sizeof(ProbDesc<double>) : sizeof(ProbDesc<float>)) * n);
+  const size_t tile_b = align256(sizeof(int) * (size_t)total_tiles);
+  const size_t st_b = align256(sizeof(DevState) * (size_t)n);
+  const size_t part_b = align256(sizeof(FlowPartial) * (size_t)total_tiles);
+  const size_t opart_b = align256(sizeof(ObsPartial) * (size_t)obs_need);
+  const size_t act_b = 256;
+  const size_t total = bytes + desc_b + tile_b + st_b + part_b + opart_b + act_b;
+  cudaError_t e = cudaMalloc(&b->base, total);
+  if (e != cudaSuccess) {
+    b->base = nullptr;
+    return fail(SS_ERR_NOMEM, std::string("cudaMalloc of the buffer set failed: ") + cudaGetErrorString(e));
+  }
+  // zero everything once: k_v and v stay zero on the halo for ever
+  SS_CK(cudaMemsetAsync(b->base, 0, total, b->stream));
+  char* q = static_cast<char*>(b->base);
+  for (Problem& p : b->probs) {
+    const size_t pb = align256((size_t)b->C * p.plane * b->elem);
+    void** slots[8] = {&p.phi[0], &p.phi[1], &p.v[0], &p.v[1], &p.kv[0], &p.kv[1], &p.lo[0], &p.lo[1]};
+    for (int i = 0; i < nbuf; ++i) {
+      *slots[i] = q;
+      q += pb;
+    }
+  }
+  b->desc = q;
+  q += desc_b;
+  b->tile_prob = reinterpret_cast<int*>(q);
+  q += tile_b;
+  b->st = reinterpret_cast<DevState*>(q);
+  q += st_b;
+  b->part = reinterpret_cast<FlowPartial*>(q);
+  q += part_b;
+  b->opart = reinterpret_cast<ObsPartial*>(q);
+  q += opart_b;
+  b->d_active = reinterpret_cast<int*>(q);
+  b->obs_cap = obs_need;
+
+  // descriptors and the tile -> problem map
+  std::vector<int> tp((size_t)total_tiles);
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < b->probs[i].ntiles; ++k) tp[(size_t)b->probs[i].tile0 + k] = i;
+  SS_CK(cudaStreamSynchronize(b->stream));  // the memset above precedes the copies
+  if (b->prec == SS_FP64) {
+    std::vector<ProbDesc<double>> d(n);
+    for (int i = 0; i < n; ++i) d[i] = make_desc<double>(b->probs[i], b->st + i, b->part + b->probs[i].tile0);
+    SS_CK(cudaMemcpy(b->desc, d.data(), sizeof(ProbDesc<double>) * n, cudaMemcpyHostToDevice));
+    b->one_desc.assign(reinterpret_cast<const unsigned char*>(d.data()),
+                       reinterpret_cast<const unsigned char*>(d.data()) + sizeof(ProbDesc<double>));
+  } else {
+    std::vector<ProbDesc<float>> d(n);
+    for (int i = 0; i < n; ++i) d[i] = make_desc<float>(b->probs[i], b->st + i, b->part + b->probs[i].tile0);
+    SS_CK(cudaMemcpy(b->desc, d.data(), sizeof(ProbDesc<float>) * n, cudaMemcpyHostToDevice));
+    b->one_desc.assign(reinterpret_cast<const unsigned char*>(d.data()),
+                       reinterpret_cast<const unsigned char*>(d.data()) + sizeof(ProbDesc<float>));
+  }
+  SS_CK(cudaMemcpy(b->tile_prob, tp.data(), sizeof(int) * tp.size(), cudaMemcpyHostToDevice));
+  b->BL.theory = th;
+  b->BL.prec = b->prec;
+  b->BL.probs = b->desc;
+  b->BL.tile_prob = b->tile_prob;
+  b->BL.total_tiles = total_tiles;
+  // a batch of one passes its descriptor to the pass kernels by value
+  b->BL.one = n == 1 ? static_cast<const void*>(b->one_desc.data()) : nullptr;
+  flow_grid(th, b->prec, total_tiles, n == 1, b->BL.flow_blocks);
+  SS_CK(cudaMallocHost(&b->h_st, sizeof(DevState) * n));
+  SS_CK(cudaMallocHost(&b->h_active, sizeof(int) * 2));
+  for (int i = 0; i < 2; ++i) SS_CK(cudaEventCreateWithFlags(&b->ev[i], cudaEventDisableTiming));
+  SS_CK(launch_reset_states(b->st, n, b->stream));
+  SS_CK(cudaStreamSynchronize(b->stream));
+  b->fields_set.assign(n, 0);
   return SS_OK;
 }
 
-int read_state(ss_ctx* c, DevState* out) {
-  SS_CK(cudaMemcpyAsync(c->h_st[0], c->L.st, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream));
-  SS_CK(cudaStreamSynchronize(c->stream));
-  *out = *c->h_st[0];
-  refresh(c, out);
+// Launch view of one problem for the per-problem kernels (ansatz, observables);
+// phi[0] of the view is the problem's current field (parity cur).
+LaunchCtx problem_ctx(const ss_batch* b, int i, int cur) {
+  const Problem& p = b->probs[i];
+  LaunchCtx L{};
+  L.theory = b->theory == SS_ABELIAN_HIGGS ? TH_AH : TH_CM;
+  L.prec = b->prec;
+  L.nx = p.nx;
+  L.ny = p.ny;
+  L.plane = p.plane;
+  L.dx = p.dx;
+  L.dy = p.dy;
+  L.dt = p.dt;
+  std::memcpy(L.coup, p.coup, sizeof(L.coup));
+  for (int k = 0; k < 2; ++k) {
+    L.phi[k] = p.phi[k ^ cur];
+    L.lo[k] = p.lo[k ^ cur];
+    L.v[k] = p.v[k ^ cur];
+    L.kv[k] = p.kv[k];
+  }
+  L.st = b->st + i;
+  L.opart = b->opart;
+  L.ntiles_x = (p.nx + TX - 1) / TX;
+  L.ntiles_y = (p.ny + TY - 1) / TY;
+  const int og = obs_grid(L.theory, b->prec, L.ntiles_x * L.ntiles_y);
+  L.obs_blocks = og < b->obs_cap ? og : b->obs_cap;
+  return L;
+}
+
+int read_states(ss_batch* b) {
+  SS_CK(cudaMemcpyAsync(b->h_st, b->st, sizeof(DevState) * b->n(), cudaMemcpyDeviceToHost, b->stream));
+  SS_CK(cudaStreamSynchronize(b->stream));
   return SS_OK;
 }
 
-// One step from parity p: pass 2 (stages 3-4, new field), then pass 1 (stages 1-2,
-// reductions, arrest decision) of the new field, which is the next step's head.
-int enqueue_step(ss_ctx* c, int p) {
-  SS_CK(launch_pass(c->L, 2, p, c->stream));
-  SS_CK(launch_pass(c->L, 1, p ^ 1, c->stream));
+int cur_of(const ss_batch* b, int i) { return (int)(b->h_st[i].steps & 1); }
+
+// New fields for problem i (already in phi[0], phi[1]): zero v and lo, reset its record.
+int problem_new_fields(ss_batch* b, int i) {
+  const Problem& p = b->probs[i];
+  const size_t bytes = (size_t)b->C * p.plane * b->elem;
+  for (int k = 0; k < 2; ++k) {
+    SS_CK(cudaMemsetAsync(p.v[k], 0, bytes, b->stream));
+    if (p.lo[k]) SS_CK(cudaMemsetAsync(p.lo[k], 0, bytes, b->stream));
+  }
+  SS_CK(launch_reset_states(b->st + i, 1, b->stream));
+  b->fields_set[i] = 1;
   return SS_OK;
 }
 
-int ensure_chunk(ss_ctx* c, int p) {
-  if (c->chunk[p]) return SS_OK;
+int problem_ansatz(ss_batch* b, int i, const ss_soliton* s, int n) {
+  if (!s || n < 1) return fail(SS_ERR_ARG, "need at least one soliton");
+  for (int k = 0; k < n; ++k)
+    if (!(s[k].size > 0.0) || !std::isfinite(s[k].x) || !std::isfinite(s[k].y) || !std::isfinite(s[k].phase))
+      return fail(SS_ERR_ARG, "soliton entries must be finite with size > 0");
+  SS_CK(cudaStreamSynchronize(b->stream));  // the staging buffer may still be in use
+  if (n > b->sol_cap) {
+    if (b->d_sol) cudaFree(b->d_sol);
+    b->d_sol = nullptr;
+    b->sol_cap = 0;
+    SS_CK(cudaMalloc(&b->d_sol, sizeof(double) * 5 * (size_t)n));
+    b->sol_cap = n;
+  }
+  std::vector<double> h(5 * (size_t)n);
+  for (int k = 0; k < n; ++k) {
+    h[5 * k] = s[k].x;
+    h[5 * k + 1] = s[k].y;
+    h[5 * k + 2] = (double)s[k].charge;
+    h[5 * k + 3] = s[k].size;
+    h[5 * k + 4] = s[k].phase;
+  }
+  SS_CK(cudaMemcpyAsync(b->d_sol, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice, b->stream));
+  SS_CK(launch_ansatz(problem_ctx(b, i, 0), b->d_sol, n, b->stream));
+  SS_CK(cudaStreamSynchronize(b->stream));  // h is a host temporary
+  return problem_new_fields(b, i);
+}
+
+int ensure_chunk(ss_batch* b) {
+  if (b->chunk) return SS_OK;
   cudaGraph_t g = nullptr;
-  SS_CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-  int rc = SS_OK;
-  for (int k = 0; k < K_CHUNK && rc == SS_OK; ++k) rc = enqueue_step(c, p ^ (k & 1));
-  cudaError_t e = cudaStreamEndCapture(c->stream, &g);
-  if (rc != SS_OK) { if (g) cudaGraphDestroy(g); return rc; }
-  if (e != cudaSuccess) return fail(SS_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
-  e = cudaGraphInstantiate(&c->chunk[p], g, 0);
+  SS_CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < K_CHUNK && e == cudaSuccess; ++k) {
+    e = launch_pass(b->BL, 2, b->stream);                        // stages 3-4: new fields
+    if (e == cudaSuccess) e = launch_pass(b->BL, 1, b->stream);  // stages 1-2 of the new fields
+  }
+  cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return fail(SS_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+  }
+  e = cudaGraphInstantiate(&b->chunk, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return fail(SS_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
   return SS_OK;
 }
 
-int check_ready(ss_ctx* c) {
-  if (!c) return fail(SS_ERR_ARG, "null context");
-  if (!c->theory) return fail(SS_ERR_STATE, "ss_set_theory has not been called");
-  if (!c->fields_set) return fail(SS_ERR_STATE, "fields not set (ss_init_ansatz / ss_set_fields)");
-  return SS_OK;
-}
-
-int new_fields(ss_ctx* c) {
-  const size_t bytes = (size_t)c->C * c->L.plane * c->elem;
-  SS_CK(cudaMemsetAsync(c->L.v[0], 0, bytes, c->stream));
-  SS_CK(cudaMemsetAsync(c->L.v[1], 0, bytes, c->stream));
-  if (c->prec == SS_FP32) {  // compensated: the given field is exact, lo = 0
-    SS_CK(cudaMemsetAsync(c->L.lo[0], 0, bytes, c->stream));
-    SS_CK(cudaMemsetAsync(c->L.lo[1], 0, bytes, c->stream));
+// Run every problem up to max_steps more steps with threshold tol (< 0: none).
+// Chunk i is enqueued before the running count of chunk i-1 is checked, so the GPU
+// never waits for the host; once every problem has stopped the rest of an enqueued
+// chunk is a row of launches whose tiles all skip.
+int batch_run(ss_batch* b, double tol, long long max_steps) {
+  const int n = b->n();
+  SS_CK(launch_set_run_all(b->st, n, tol, max_steps, b->stream));
+  SS_CK(launch_pass(b->BL, 1, b->stream));  // heads of the current fields (skipped where done)
+  const long long nchunks = (max_steps + K_CHUNK - 1) / K_CHUNK;
+  if (nchunks > 0) {
+    int rc = ensure_chunk(b);
+    if (rc != SS_OK) return rc;
   }
-  SS_CK(launch_reset_state(c->L, c->stream));
-  c->cur = 0;
-  c->fields_set = true;
-  return SS_OK;
+  int prev = -1;
+  for (long long i = 0; i < nchunks; ++i) {
+    const int slot = (int)(i & 1);
+    SS_CK(cudaGraphLaunch(b->chunk, b->stream));
+    SS_CK(launch_count_active(b->st, n, b->d_active, b->stream));
+    SS_CK(cudaMemcpyAsync(b->h_active + slot, b->d_active, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+    SS_CK(cudaEventRecord(b->ev[slot], b->stream));
+    if (prev >= 0) {
+      SS_CK(cudaEventSynchronize(b->ev[prev]));
+      if (b->h_active[prev] == 0) break;
+    }
+    prev = slot;
+  }
+  return read_states(b);
 }
 
 void fill_status(const DevState& h, ss_status* out) {
@@ -149,33 +414,73 @@ void fill_status(const DevState& h, ss_status* out) {
   out->energy_change = h.dE;
 }
 
-// Run up to max_steps steps with threshold tol (< 0: none). Chunk i is enqueued
-// before the status of chunk i-1 is checked, so the GPU never waits for the host;
-// once the device has stopped (converged, non-finite, step budget spent) the rest
-// of an enqueued chunk is a row of no-op launches.
-int run(ss_ctx* c, double tol, long long max_steps, DevState* fin) {
-  const int p0 = c->cur;
-  SS_CK(launch_set_run(c->L, tol, max_steps, c->stream));
-  SS_CK(launch_pass(c->L, 1, p0, c->stream));  // head of the current field (no-op if done)
-  const long long nchunks = (max_steps + K_CHUNK - 1) / K_CHUNK;
-  if (nchunks > 0) {
-    int rc = ensure_chunk(c, p0);
-    if (rc != SS_OK) return rc;
+int copy_planes(ss_batch* b, int i, void* dst, const void* src, int is_device) {
+  const size_t bytes = (size_t)b->C * b->probs[i].plane * b->elem;
+  SS_CK(cudaMemcpyAsync(dst, src, bytes, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, b->stream));
+  SS_CK(cudaStreamSynchronize(b->stream));
+  return SS_OK;
+}
+
+int problem_observables(ss_batch* b, int i, ss_obs* out) {
+  int rc = read_states(b);
+  if (rc != SS_OK) return rc;
+  SS_CK(launch_observables(problem_ctx(b, i, cur_of(b, i)), 0, b->stream));
+  rc = read_states(b);
+  if (rc != SS_OK) return rc;
+  const DevState& h = b->h_st[i];
+  out->energy = h.obs_energy;
+  out->charge = h.obs_charge;
+  out->flux = h.obs_flux;
+  out->grad_max = h.obs_gmax_raw * b->probs[i].dx * b->probs[i].dy;
+  out->grad_max_raw = h.obs_gmax_raw;
+  out->norm_dev = h.obs_normdev;
+  out->steps = h.steps;
+  return SS_OK;
+}
+
+int make_stream(ss_batch* b, void* cuda_stream) {
+  if (cuda_stream) {
+    b->stream = static_cast<cudaStream_t>(cuda_stream);
+    return SS_OK;
   }
-  int prev = -1;
-  for (long long i = 0; i < nchunks; ++i) {
-    const int slot = (int)(i & 1);
-    SS_CK(cudaGraphLaunch(c->chunk[p0], c->stream));
-    SS_CK(cudaMemcpyAsync(c->h_st[slot], c->L.st, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream));
-    SS_CK(cudaEventRecord(c->ev[slot], c->stream));
-    if (prev >= 0) {
-      SS_CK(cudaEventSynchronize(c->ev[prev]));
-      const DevState* h = c->h_st[prev];
-      if (h->converged || h->nonfinite || h->steps >= h->step_limit) break;
-    }
-    prev = slot;
+  // graphs cannot be captured on the legacy stream: own a blocking stream
+  SS_CK(cudaStreamCreate(&b->stream));
+  b->own_stream = true;
+  return SS_OK;
+}
+
+int batch_finish(ss_batch* b, ss_status* per_item, bool need_converged) {
+  int nonfinite = 0, unconverged = 0;
+  for (int i = 0; i < b->n(); ++i) {
+    const DevState& h = b->h_st[i];
+    if (per_item) fill_status(h, per_item + i);
+    nonfinite += h.nonfinite != 0;
+    unconverged += !h.converged;
   }
-  return read_state(c, fin);
+  if (nonfinite) return fail(SS_ERR_NONFINITE, std::to_string(nonfinite) + " problem(s) became non-finite");
+  if (need_converged && unconverged)
+    return fail(SS_ERR_NOT_CONVERGED, std::to_string(unconverged) + " problem(s) reached max_steps first");
+  return SS_OK;
+}
+
+}  // namespace
+
+// ================================================================== single grid
+struct ss_ctx {
+  int nx = 0, ny = 0;
+  double dx = 0, dy = 0;
+  int prec = 0;
+  void* user_stream = nullptr;
+  ss_batch* b = nullptr;  // a batch of one, created by ss_set_theory
+};
+
+namespace {
+
+int check_ready(ss_ctx* c) {
+  if (!c) return fail(SS_ERR_ARG, "null context");
+  if (!c->b) return fail(SS_ERR_STATE, "ss_set_theory has not been called");
+  if (!c->b->fields_set[0]) return fail(SS_ERR_STATE, "fields not set (ss_init_ansatz / ss_set_fields)");
+  return SS_OK;
 }
 
 }  // namespace
@@ -184,15 +489,13 @@ extern "C" {
 
 const char* ss_last_error(void) { return g_err.c_str(); }
 
-int ss_version(void) { return 3; }
+int ss_version(void) { return 4; }
 
 int ss_create_grid(ss_ctx** out, int nx, int ny, double dx, double dy, int precision, void* cuda_stream) {
   if (!out) return fail(SS_ERR_ARG, "out is NULL");
   *out = nullptr;
-  if (nx < 5 || ny < 5) return fail(SS_ERR_ARG, "nx and ny must be >= 5 (halo of width 2 on each side)");
-  if ((long long)nx * ny > (1LL << 31)) return fail(SS_ERR_ARG, "grid too large (nx * ny > 2^31)");
-  if (!(dx > 0.0) || !(dy > 0.0) || !std::isfinite(dx) || !std::isfinite(dy))
-    return fail(SS_ERR_ARG, "dx and dy must be positive and finite");
+  int rc = check_grid(nx, ny, dx, dy);
+  if (rc != SS_OK) return rc;
   if (precision != SS_FP32 && precision != SS_FP64 && precision != SS_FP32_PLAIN)
     return fail(SS_ERR_ARG, "precision must be SS_FP32, SS_FP64 or SS_FP32_PLAIN");
   int dev = 0;
@@ -203,191 +506,93 @@ int ss_create_grid(ss_ctx** out, int nx, int ny, double dx, double dy, int preci
   c->ny = ny;
   c->dx = dx;
   c->dy = dy;
-  c->dt = 0.5 * (dx < dy ? dx : dy);  // Sec. 3.1: C = dt / dx = 0.5
   c->prec = precision;
-  c->elem = precision == SS_FP64 ? 8 : 4;
-  cudaError_t e = cudaSuccess;
-  if (cuda_stream) {
-    c->stream = static_cast<cudaStream_t>(cuda_stream);
-  } else {  // graphs cannot be captured on the legacy stream: own a blocking stream
-    e = cudaStreamCreate(&c->stream);
-    c->own_stream = true;
-  }
-  for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
-    e = cudaMallocHost(&c->h_st[i], sizeof(DevState));
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev[i], cudaEventDisableTiming);
-  }
-  if (e != cudaSuccess) {
-    ss_destroy(c);
-    return fail(SS_ERR_CUDA, std::string("ss_create_grid: ") + cudaGetErrorString(e));
-  }
-  c->L.nx = nx;
-  c->L.ny = ny;
-  c->L.plane = (size_t)nx * ny;
-  c->L.dx = dx;
-  c->L.dy = dy;
-  c->L.dt = c->dt;
-  c->L.prec = precision;
-  c->L.ntiles_x = (nx + TX - 1) / TX;
-  c->L.ntiles_y = (ny + TY - 1) / TY;
+  c->user_stream = cuda_stream;
   *out = c;
   return SS_OK;
 }
 
 int ss_set_theory(ss_ctx* c, int theory, const double* params, int n_params) {
   if (!c) return fail(SS_ERR_ARG, "null context");
-  if (!params && n_params > 0) return fail(SS_ERR_ARG, "params is NULL");
-  double k[10] = {0};
+  double k[10];
   int C = 0;
-  if (theory == SS_ABELIAN_HIGGS) {
-    if (n_params < 1 || n_params > 2) return fail(SS_ERR_ARG, "Abelian Higgs takes {lambda[, u]}");
-    const double lam = params[0], u = n_params > 1 ? params[1] : 1.0;
-    if (!std::isfinite(lam) || !std::isfinite(u) || lam < 0.0) return fail(SS_ERR_ARG, "lambda must be finite and >= 0");
-    k[0] = lam;
-    k[1] = u * u;
-    C = 4;
-  } else if (theory == SS_CHIRAL_MAGNET) {
-    if (n_params < 4 || n_params > 5) return fail(SS_ERR_ARG, "chiral magnet takes {J, D, K, h[, dmi_type]}");
-    for (int i = 0; i < n_params; ++i)
-      if (!std::isfinite(params[i])) return fail(SS_ERR_ARG, "chiral-magnet parameters must be finite");
-    if (!(params[0] > 0.0)) return fail(SS_ERR_ARG, "J must be > 0");
-    const int type = n_params > 4 ? (int)params[4] : 0;
-    if (type < 0 || type > 2 || (n_params > 4 && params[4] != (double)type))
-      return fail(SS_ERR_ARG, "dmi_type must be 0 (interfacial), 1 (bulk) or 2 (D_2d)");
-    k[0] = params[0];
-    k[1] = params[1];
-    k[2] = params[2];
-    k[3] = params[3];
-    // DMI vectors d_1 (k[4..6]) and d_2 (k[7..9]) of Eq. 5
-    if (type == 0) { k[5] = 1.0; k[7] = -1.0; }      // d_i = e_3 x e_i
-    else if (type == 1) { k[4] = 1.0; k[8] = 1.0; }  // d_i = e_i
-    else { k[4] = 1.0; k[8] = -1.0; }                // d_1 = e_1, d_2 = -e_2
-    C = 3;
-  } else {
-    return fail(SS_ERR_ARG, "unknown theory");
+  int rc = pack_couplings(theory, params, n_params, k, &C);
+  if (rc != SS_OK) return rc;
+  if (c->b) {
+    batch_free(c->b);
+    c->b = nullptr;
   }
-  if (c->theory != theory || c->C != C || !c->base) {
-    free_buffers(c);
-    const size_t pb = align256((size_t)C * c->L.plane * c->elem);
-    const int ntiles = c->L.ntiles_x * c->L.ntiles_y;
-    const int fb = flow_grid(theory == SS_ABELIAN_HIGGS ? TH_AH : TH_CM, c->prec, c->nx, c->ny);
-    const int ob = obs_grid(theory == SS_ABELIAN_HIGGS ? TH_AH : TH_CM, c->prec, ntiles);
-    const size_t stb = align256(sizeof(DevState));
-    const size_t fpb = align256(sizeof(FlowPartial) * (size_t)fb);
-    const size_t opb = align256(sizeof(ObsPartial) * (size_t)ob);
-    const bool comp = c->prec == SS_FP32;
-    const int nbuf = NBUF + (comp ? 2 : 0);
-    const size_t total = nbuf * pb + stb + fpb + opb;
-    cudaError_t e = cudaMalloc(&c->base, total);
-    if (e != cudaSuccess) {
-      c->base = nullptr;
-      return fail(SS_ERR_NOMEM, std::string("cudaMalloc of the buffer set failed: ") + cudaGetErrorString(e));
-    }
-    // zero everything once: k_v and v stay zero on the halo for ever
-    SS_CK(cudaMemsetAsync(c->base, 0, total, c->stream));
-    char* p = static_cast<char*>(c->base);
-    c->L.phi[0] = p; p += pb;
-    c->L.phi[1] = p; p += pb;
-    c->L.v[0] = p; p += pb;
-    c->L.v[1] = p; p += pb;
-    for (int i = 0; i < 2; ++i) { c->L.kv[i] = p; p += pb; }
-    c->L.lo[0] = c->L.lo[1] = nullptr;
-    if (comp) {
-      c->L.lo[0] = p; p += pb;
-      c->L.lo[1] = p; p += pb;
-    }
-    c->L.st = reinterpret_cast<DevState*>(p); p += stb;
-    c->L.fpart = reinterpret_cast<FlowPartial*>(p); p += fpb;
-    c->L.opart = reinterpret_cast<ObsPartial*>(p);
-    c->L.flow_blocks = fb;
-    c->L.obs_blocks = ob;
+  ss_batch* b = new (std::nothrow) ss_batch();
+  if (!b) return fail(SS_ERR_NOMEM, "host allocation failed");
+  b->theory = theory;
+  b->prec = c->prec;
+  b->C = C;
+  b->elem = c->prec == SS_FP64 ? 8 : 4;
+  rc = make_stream(b, c->user_stream);
+  if (rc != SS_OK) {
+    batch_free(b);
+    return rc;
   }
-  c->theory = theory;
-  c->C = C;
-  c->L.theory = theory == SS_ABELIAN_HIGGS ? TH_AH : TH_CM;
-  std::memcpy(c->L.coup, k, sizeof(k));
-  // couplings are baked into captured graphs: drop them
-  for (int q = 0; q < 2; ++q)
-    if (c->chunk[q]) { cudaGraphExecDestroy(c->chunk[q]); c->chunk[q] = nullptr; }
-  c->fields_set = false;
-  SS_CK(launch_reset_state(c->L, c->stream));
-  SS_CK(cudaStreamSynchronize(c->stream));
+  Problem p;
+  p.nx = c->nx;
+  p.ny = c->ny;
+  p.dx = c->dx;
+  p.dy = c->dy;
+  p.dt = 0.5 * (c->dx < c->dy ? c->dx : c->dy);  // Sec. 3.1: C = dt / dx = 0.5
+  std::memcpy(p.coup, k, sizeof(k));
+  b->probs.push_back(p);
+  rc = batch_alloc(b);
+  if (rc != SS_OK) {
+    batch_free(b);
+    return rc;
+  }
+  c->b = b;
   return SS_OK;
 }
 
 int ss_init_ansatz(ss_ctx* c, const ss_soliton* s, int n) {
   if (!c) return fail(SS_ERR_ARG, "null context");
-  if (!c->theory) return fail(SS_ERR_STATE, "ss_set_theory has not been called");
-  if (!s || n < 1) return fail(SS_ERR_ARG, "need at least one soliton");
-  for (int i = 0; i < n; ++i)
-    if (!(s[i].size > 0.0) || !std::isfinite(s[i].x) || !std::isfinite(s[i].y) || !std::isfinite(s[i].phase))
-      return fail(SS_ERR_ARG, "soliton entries must be finite with size > 0");
-  if (n > c->sol_cap) {
-    if (c->d_sol) cudaFree(c->d_sol);
-    c->d_sol = nullptr;
-    c->sol_cap = 0;
-    SS_CK(cudaMalloc(&c->d_sol, sizeof(double) * 5 * (size_t)n));
-    c->sol_cap = n;
-  }
-  double* h = nullptr;
-  SS_CK(cudaMallocHost(&h, sizeof(double) * 5 * (size_t)n));
-  for (int i = 0; i < n; ++i) {
-    h[5 * i] = s[i].x;
-    h[5 * i + 1] = s[i].y;
-    h[5 * i + 2] = (double)s[i].charge;
-    h[5 * i + 3] = s[i].size;
-    h[5 * i + 4] = s[i].phase;
-  }
-  cudaError_t e = cudaMemcpyAsync(c->d_sol, h, sizeof(double) * 5 * (size_t)n, cudaMemcpyHostToDevice, c->stream);
-  if (e == cudaSuccess) e = launch_ansatz(c->L, c->d_sol, n, c->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-  cudaFreeHost(h);
-  if (e != cudaSuccess) return fail(SS_ERR_CUDA, std::string("ss_init_ansatz: ") + cudaGetErrorString(e));
-  int rc = new_fields(c);
+  if (!c->b) return fail(SS_ERR_STATE, "ss_set_theory has not been called");
+  int rc = problem_ansatz(c->b, 0, s, n);
   if (rc != SS_OK) return rc;
-  SS_CK(cudaStreamSynchronize(c->stream));
-  return SS_OK;
+  return read_states(c->b);
 }
 
 int ss_set_fields(ss_ctx* c, const void* f, int is_device) {
   if (!c) return fail(SS_ERR_ARG, "null context");
-  if (!c->theory) return fail(SS_ERR_STATE, "ss_set_theory has not been called");
+  if (!c->b) return fail(SS_ERR_STATE, "ss_set_theory has not been called");
   if (!f) return fail(SS_ERR_ARG, "fields is NULL");
-  const size_t bytes = (size_t)c->C * c->L.plane * c->elem;
-  const cudaMemcpyKind kind = is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  SS_CK(cudaMemcpyAsync(c->L.phi[0], f, bytes, kind, c->stream));
-  SS_CK(cudaMemcpyAsync(c->L.phi[1], c->L.phi[0], bytes, cudaMemcpyDeviceToDevice, c->stream));
-  int rc = new_fields(c);
+  ss_batch* b = c->b;
+  const Problem& p = b->probs[0];
+  const size_t bytes = (size_t)b->C * p.plane * b->elem;
+  SS_CK(cudaMemcpyAsync(p.phi[0], f, bytes, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, b->stream));
+  SS_CK(cudaMemcpyAsync(p.phi[1], p.phi[0], bytes, cudaMemcpyDeviceToDevice, b->stream));
+  int rc = problem_new_fields(b, 0);
   if (rc != SS_OK) return rc;
-  SS_CK(cudaStreamSynchronize(c->stream));
-  return SS_OK;
+  return read_states(b);
 }
 
 int ss_get_fields(ss_ctx* c, void* f, int is_device) {
   int rc = check_ready(c);
   if (rc != SS_OK) return rc;
   if (!f) return fail(SS_ERR_ARG, "fields is NULL");
-  const size_t bytes = (size_t)c->C * c->L.plane * c->elem;
-  SS_CK(cudaMemcpyAsync(f, c->L.phi[c->cur], bytes, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                        c->stream));
-  SS_CK(cudaStreamSynchronize(c->stream));
-  return SS_OK;
+  rc = read_states(c->b);
+  if (rc != SS_OK) return rc;
+  return copy_planes(c->b, 0, f, c->b->probs[0].phi[cur_of(c->b, 0)], is_device);
 }
 
 int ss_get_remainder(ss_ctx* c, void* lo, int is_device) {
   int rc = check_ready(c);
   if (rc != SS_OK) return rc;
   if (!lo) return fail(SS_ERR_ARG, "remainder is NULL");
-  const size_t bytes = (size_t)c->C * c->L.plane * c->elem;
-  if (c->prec == SS_FP32) {
-    SS_CK(cudaMemcpyAsync(lo, c->L.lo[c->cur], bytes, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                          c->stream));
-  } else if (is_device) {
-    SS_CK(cudaMemsetAsync(lo, 0, bytes, c->stream));
-  } else {
-    std::memset(lo, 0, bytes);
-  }
-  SS_CK(cudaStreamSynchronize(c->stream));
+  ss_batch* b = c->b;
+  rc = read_states(b);
+  if (rc != SS_OK) return rc;
+  if (b->prec == SS_FP32) return copy_planes(b, 0, lo, b->probs[0].lo[cur_of(b, 0)], is_device);
+  const size_t bytes = (size_t)b->C * b->probs[0].plane * b->elem;
+  if (is_device) SS_CK(cudaMemsetAsync(lo, 0, bytes, b->stream));
+  else std::memset(lo, 0, bytes);
+  SS_CK(cudaStreamSynchronize(b->stream));
   return SS_OK;
 }
 
@@ -395,41 +600,44 @@ int ss_get_velocity(ss_ctx* c, void* out, int is_device) {
   int rc = check_ready(c);
   if (rc != SS_OK) return rc;
   if (!out) return fail(SS_ERR_ARG, "velocity is NULL");
-  SS_CK(launch_pass(c->L, 1, c->cur, c->stream));  // resolves a pending arrest (no-op if known)
-  DevState h;
-  rc = read_state(c, &h);
+  ss_batch* b = c->b;
+  SS_CK(launch_pass(b->BL, 1, b->stream));  // resolves a pending arrest (skipped if known)
+  rc = read_states(b);
   if (rc != SS_OK) return rc;
-  const size_t bytes = (size_t)c->C * c->L.plane * c->elem;
-  if (h.arrest) {
-    if (is_device) SS_CK(cudaMemsetAsync(out, 0, bytes, c->stream));
+  const size_t bytes = (size_t)b->C * b->probs[0].plane * b->elem;
+  if (b->h_st[0].arrest) {
+    if (is_device) SS_CK(cudaMemsetAsync(out, 0, bytes, b->stream));
     else std::memset(out, 0, bytes);
-  } else {
-    SS_CK(cudaMemcpyAsync(out, c->L.v[c->cur], bytes, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                          c->stream));
+    SS_CK(cudaStreamSynchronize(b->stream));
+    return SS_OK;
   }
-  SS_CK(cudaStreamSynchronize(c->stream));
-  return SS_OK;
+  return copy_planes(b, 0, out, b->probs[0].v[cur_of(b, 0)], is_device);
 }
 
 int ss_force(ss_ctx* c, void* out, int is_device, double* energy, double* grad_max) {
   int rc = check_ready(c);
   if (rc != SS_OK) return rc;
   if (!out) return fail(SS_ERR_ARG, "force is NULL");
-  SS_CK(launch_pass(c->L, 1, c->cur, c->stream));  // k_v1 = -G of the current field
-  const size_t bytes = (size_t)c->C * c->L.plane * c->elem;
-  if (is_device) {
-    SS_CK(launch_scaled_copy(c->L, out, c->L.kv[0], -1.0, c->stream));
-  } else {
-    // v[cur ^ 1] is the next step's output buffer: free scratch, and -G keeps its halo zero
-    void* scratch = c->L.v[c->cur ^ 1];
-    SS_CK(launch_scaled_copy(c->L, scratch, c->L.kv[0], -1.0, c->stream));
-    SS_CK(cudaMemcpyAsync(out, scratch, bytes, cudaMemcpyDeviceToHost, c->stream));
-  }
-  DevState h;
-  rc = read_state(c, &h);
+  ss_batch* b = c->b;
+  SS_CK(launch_pass(b->BL, 1, b->stream));  // k_v1 = -G of the current field
+  rc = read_states(b);
   if (rc != SS_OK) return rc;
-  if (energy) *energy = h.E_cur;
-  if (grad_max) *grad_max = h.gmax;
+  const int cur = cur_of(b, 0);
+  const Problem& p = b->probs[0];
+  const LaunchCtx L = problem_ctx(b, 0, cur);
+  const size_t bytes = (size_t)b->C * p.plane * b->elem;
+  if (is_device) {
+    SS_CK(launch_scaled_copy(L, out, p.kv[0], -1.0, b->stream));
+  } else {
+    // v of the other parity is the next step's output buffer: free scratch, and -G
+    // keeps its halo zero
+    void* scratch = p.v[cur ^ 1];
+    SS_CK(launch_scaled_copy(L, scratch, p.kv[0], -1.0, b->stream));
+    SS_CK(cudaMemcpyAsync(out, scratch, bytes, cudaMemcpyDeviceToHost, b->stream));
+  }
+  SS_CK(cudaStreamSynchronize(b->stream));
+  if (energy) *energy = b->h_st[0].E_cur;
+  if (grad_max) *grad_max = b->h_st[0].gmax;
   return SS_OK;
 }
 
@@ -437,9 +645,9 @@ int ss_step(ss_ctx* c, int n_steps, ss_status* out) {
   int rc = check_ready(c);
   if (rc != SS_OK) return rc;
   if (n_steps < 0) return fail(SS_ERR_ARG, "n_steps must be >= 0");
-  DevState h;
-  rc = run(c, -1.0, n_steps, &h);
+  rc = batch_run(c->b, -1.0, n_steps);
   if (rc != SS_OK) return rc;
+  const DevState& h = c->b->h_st[0];
   fill_status(h, out);
   if (h.nonfinite) return fail(SS_ERR_NONFINITE, "energy or force became non-finite; the flow stopped");
   return SS_OK;
@@ -450,9 +658,9 @@ int ss_minimise(ss_ctx* c, double tol, long long max_steps, ss_status* out) {
   if (rc != SS_OK) return rc;
   if (max_steps < 0) return fail(SS_ERR_ARG, "max_steps must be >= 0");
   if (!(tol >= 0.0)) return fail(SS_ERR_ARG, "tol must be >= 0");
-  DevState h;
-  rc = run(c, tol, max_steps, &h);
+  rc = batch_run(c->b, tol, max_steps);
   if (rc != SS_OK) return rc;
+  const DevState& h = c->b->h_st[0];
   fill_status(h, out);
   if (h.nonfinite) return fail(SS_ERR_NONFINITE, "energy or force became non-finite; the flow stopped");
   if (!h.converged) return fail(SS_ERR_NOT_CONVERGED, "max_steps reached before the tolerance");
@@ -463,67 +671,133 @@ int ss_observables(ss_ctx* c, ss_obs* out) {
   int rc = check_ready(c);
   if (rc != SS_OK) return rc;
   if (!out) return fail(SS_ERR_ARG, "out is NULL");
-  SS_CK(launch_observables(c->L, c->cur, c->stream));
-  DevState h;
-  rc = read_state(c, &h);
-  if (rc != SS_OK) return rc;
-  out->energy = h.obs_energy;
-  out->charge = h.obs_charge;
-  out->flux = h.obs_flux;
-  out->grad_max = h.obs_gmax_raw * c->dx * c->dy;
-  out->grad_max_raw = h.obs_gmax_raw;
-  out->norm_dev = h.obs_normdev;
-  out->steps = h.steps;
-  return SS_OK;
+  return problem_observables(c->b, 0, out);
 }
 
 int ss_profile_stages(ss_ctx* c, int n_steps, float* ms_out) {
   int rc = check_ready(c);
   if (rc != SS_OK) return rc;
   if (n_steps < 1 || n_steps > 4096 || !ms_out) return fail(SS_ERR_ARG, "n_steps must be in 1..4096 and ms_out non-NULL");
-  SS_CK(launch_set_run(c->L, -1.0, n_steps, c->stream));
-  SS_CK(launch_pass(c->L, 1, c->cur, c->stream));  // head of the current field, untimed
+  ss_batch* b = c->b;
+  SS_CK(launch_set_run_all(b->st, b->n(), -1.0, n_steps, b->stream));
+  SS_CK(launch_pass(b->BL, 1, b->stream));  // head of the current field, untimed
   cudaEvent_t ev[3];
   for (int i = 0; i < 3; ++i) SS_CK(cudaEventCreate(&ev[i]));
   double acc[2] = {0, 0};
-  int p = c->cur;
   cudaError_t e = cudaSuccess;
   for (int k = 0; k < n_steps && e == cudaSuccess; ++k) {
-    e = cudaEventRecord(ev[0], c->stream);
-    if (e == cudaSuccess) e = launch_pass(c->L, 2, p, c->stream);      // stages 3-4 -> new field
-    if (e == cudaSuccess) e = cudaEventRecord(ev[1], c->stream);
-    if (e == cudaSuccess) e = launch_pass(c->L, 1, p ^ 1, c->stream);  // stages 1-2 of the new field
-    if (e == cudaSuccess) e = cudaEventRecord(ev[2], c->stream);
+    e = cudaEventRecord(ev[0], b->stream);
+    if (e == cudaSuccess) e = launch_pass(b->BL, 2, b->stream);  // stages 3-4 -> new field
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1], b->stream);
+    if (e == cudaSuccess) e = launch_pass(b->BL, 1, b->stream);  // stages 1-2 of the new field
+    if (e == cudaSuccess) e = cudaEventRecord(ev[2], b->stream);
     if (e == cudaSuccess) e = cudaEventSynchronize(ev[2]);
     float m1 = 0.f, m2 = 0.f;
     if (e == cudaSuccess) e = cudaEventElapsedTime(&m2, ev[0], ev[1]);
     if (e == cudaSuccess) e = cudaEventElapsedTime(&m1, ev[1], ev[2]);
     acc[0] += m1;
     acc[1] += m2;
-    p ^= 1;
   }
   for (int i = 0; i < 3; ++i) cudaEventDestroy(ev[i]);
   if (e != cudaSuccess) return fail(SS_ERR_CUDA, std::string("ss_profile_stages: ") + cudaGetErrorString(e));
-  DevState h;
-  rc = read_state(c, &h);
+  rc = read_states(b);
   if (rc != SS_OK) return rc;
   ms_out[0] = (float)(acc[0] / n_steps);
   ms_out[1] = (float)(acc[1] / n_steps);
-  if (h.nonfinite) return fail(SS_ERR_NONFINITE, "energy or force became non-finite; the flow stopped");
+  if (b->h_st[0].nonfinite) return fail(SS_ERR_NONFINITE, "energy or force became non-finite; the flow stopped");
   return SS_OK;
 }
 
 int ss_destroy(ss_ctx* c) {
   if (!c) return SS_OK;
-  if (c->stream) cudaStreamSynchronize(c->stream);
-  free_buffers(c);
-  if (c->d_sol) cudaFree(c->d_sol);
-  for (int i = 0; i < 2; ++i) {
-    if (c->h_st[i]) cudaFreeHost(c->h_st[i]);
-    if (c->ev[i]) cudaEventDestroy(c->ev[i]);
-  }
-  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  batch_free(c->b);
   delete c;
+  return SS_OK;
+}
+
+// ================================================================== batches
+int ss_batch_create(ss_batch** out, int theory, int precision, const ss_batch_item* items, int n, void* cuda_stream) {
+  if (!out) return fail(SS_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!items || n < 1) return fail(SS_ERR_ARG, "need at least one batch item");
+  if (precision != SS_FP32 && precision != SS_FP64 && precision != SS_FP32_PLAIN)
+    return fail(SS_ERR_ARG, "precision must be SS_FP32, SS_FP64 or SS_FP32_PLAIN");
+  ss_batch* b = new (std::nothrow) ss_batch();
+  if (!b) return fail(SS_ERR_NOMEM, "host allocation failed");
+  b->theory = theory;
+  b->prec = precision;
+  b->elem = precision == SS_FP64 ? 8 : 4;
+  for (int i = 0; i < n; ++i) {
+    const ss_batch_item& it = items[i];
+    int rc = check_grid(it.nx, it.ny, it.dx, it.dy);
+    double k[10];
+    int C = 0;
+    if (rc == SS_OK) rc = pack_couplings(theory, it.params, it.n_params, k, &C);
+    if (rc == SS_OK && (!it.solitons || it.n_solitons < 1)) rc = fail(SS_ERR_ARG, "every item needs at least one soliton");
+    if (rc != SS_OK) {
+      g_err = "item " + std::to_string(i) + ": " + g_err;
+      batch_free(b);
+      return rc;
+    }
+    b->C = C;
+    Problem p;
+    p.nx = it.nx;
+    p.ny = it.ny;
+    p.dx = it.dx;
+    p.dy = it.dy;
+    p.dt = 0.5 * (it.dx < it.dy ? it.dx : it.dy);  // Sec. 3.1
+    std::memcpy(p.coup, k, sizeof(k));
+    b->probs.push_back(p);
+  }
+  int rc = make_stream(b, cuda_stream);
+  if (rc == SS_OK) rc = batch_alloc(b);
+  for (int i = 0; i < n && rc == SS_OK; ++i) rc = problem_ansatz(b, i, items[i].solitons, items[i].n_solitons);
+  if (rc == SS_OK) rc = read_states(b);
+  if (rc != SS_OK) {
+    batch_free(b);
+    return rc;
+  }
+  *out = b;
+  return SS_OK;
+}
+
+int ss_batch_size(ss_batch* b) { return b ? b->n() : 0; }
+
+int ss_batch_step(ss_batch* b, int n_steps, ss_status* per_item) {
+  if (!b) return fail(SS_ERR_ARG, "null batch");
+  if (n_steps < 0) return fail(SS_ERR_ARG, "n_steps must be >= 0");
+  int rc = batch_run(b, -1.0, n_steps);
+  if (rc != SS_OK) return rc;
+  return batch_finish(b, per_item, false);
+}
+
+int ss_batch_minimise(ss_batch* b, double tol, long long max_steps, ss_status* per_item) {
+  if (!b) return fail(SS_ERR_ARG, "null batch");
+  if (max_steps < 0) return fail(SS_ERR_ARG, "max_steps must be >= 0");
+  if (!(tol >= 0.0)) return fail(SS_ERR_ARG, "tol must be >= 0");
+  int rc = batch_run(b, tol, max_steps);
+  if (rc != SS_OK) return rc;
+  return batch_finish(b, per_item, true);
+}
+
+int ss_batch_get_fields(ss_batch* b, int item, void* fields, int is_device) {
+  if (!b) return fail(SS_ERR_ARG, "null batch");
+  if (item < 0 || item >= b->n()) return fail(SS_ERR_ARG, "item out of range");
+  if (!fields) return fail(SS_ERR_ARG, "fields is NULL");
+  int rc = read_states(b);
+  if (rc != SS_OK) return rc;
+  return copy_planes(b, item, fields, b->probs[item].phi[cur_of(b, item)], is_device);
+}
+
+int ss_batch_observables(ss_batch* b, int item, ss_obs* out) {
+  if (!b) return fail(SS_ERR_ARG, "null batch");
+  if (item < 0 || item >= b->n()) return fail(SS_ERR_ARG, "item out of range");
+  if (!out) return fail(SS_ERR_ARG, "out is NULL");
+  return problem_observables(b, item, out);
+}
+
+int ss_batch_destroy(ss_batch* b) {
+  batch_free(b);
   return SS_OK;
 }
 

@@ -1,5 +1,5 @@
 // ss_flow.cu -- the arrested-Newton-flow step (arxiv 2603.24370, Sec. 3.2) as two
-// fused passes over the grid.
+// fused passes over a batch of relaxation problems.
 //
 // One RK4 step of phi'' = -G(phi) (Eq. 3) on the first-order system (phi, v), with
 // k_vi = -G(Y_i) at the stage inputs
@@ -15,12 +15,20 @@
 // (k_v3, k_v4 live in registers). Chiral magnet: every Y_i and phi' are normalised
 // and v' tangent-projected (Sec. 3.2, constraint projection).
 //
-// Pass 1 also reduces E_h(phi) (a compensated pair per thread, FP64 TwoSum warp
-// trees, one partial per block, the last-arriving block sums the partials in a
-// fixed order), dx dy max|G|, and the energy change since the previous field,
-// dE = sum_I [e(phi^n) - e(phi^{n-1})] in the cancellation-free form of
-// ss_device.cuh (phi^{n-1} is still intact in the other ping-pong buffer). Its last
-// block then decides on the device, with no host round trip:
+// Batches: every launch covers the tiles of all problems of a batch (uneven grid
+// sizes and couplings, one theory and precision). Each tile reads its problem's
+// descriptor; each problem selects its ping-pong buffers from its own step count,
+// stops on its own (converged, non-finite, step limit), and its tiles are skipped
+// from then on. A single-grid context is a batch of one.
+//
+// Pass 1 also reduces, per problem, E_h(phi), dx dy max|G| and the energy change
+// since the previous field, dE = sum_I [e(phi^n) - e(phi^{n-1})], in the
+// cancellation-free form of ss_device.cuh (phi^{n-1} is still intact in the other
+// ping-pong buffer): a compensated pair per thread, summed over a block's run of
+// consecutive tiles of one problem and reduced into the partial of the run's last
+// tile; the last tile of the problem to arrive (arrival counter) sums the problem's
+// partials in tile order (bitwise reproducible) and decides on the device, with no
+// host round trip:
 //   arrest    = dE > 0, i.e. E_h(phi^n) > E_h(phi^{n-1})   (Eq. 4)
 //   converged = dx dy max|G| < tol
 // Pass 1 computes k_v2 with v before the arrest is known. That is exact either way:
@@ -34,11 +42,11 @@
 // stalls above dx dy max|G| ~ 1e-6 while arresting every other step. The stage
 // inputs are formed as hi + (lo + increment), normalised in split form for the
 // chiral magnet, and rounded once to FP32 for the stencils.
-
+//
 // Per block a tile of TX x TY sites is staged in shared memory with its halo, the
 // stage inputs formed while loading (two sites per iteration, loads first). Each
 // thread then walks RY rows of one column with a 5-row register window per
-// component. Blocks stride over tiles; the grid is occupancy x SM count.
+// component. Blocks stride over the batch's tiles; the grid is occupancy x SMs.
 #include "ss_internal.h"
 
 namespace ss {
@@ -50,30 +58,10 @@ struct FlowTile {
   static constexpr int SX = TX + 4, SY = TY + 4, SXY = SX * SY;
 };
 
-template <typename R>
-struct PassArgs {
-  const R* __restrict__ phi;       // phi^n (current field; hi part when compensated)
-  const R* __restrict__ lo;        // LO: remainder part of phi^n
-  const R* __restrict__ phi_prev;  // pass 1: phi^{n-1} (other ping-pong buffer)
-  const R* __restrict__ lo_prev;   // LO pass 1: remainder part of phi^{n-1}
-  const R* __restrict__ v;         // v^n
-  const R* __restrict__ kv1;       // pass 2
-  const R* __restrict__ kv2;       // pass 2
-  R* __restrict__ kv1_out;         // pass 1
-  R* __restrict__ kv2_out;         // pass 1
-  R* __restrict__ phi_out;         // pass 2: phi^{n+1} (hi)
-  R* __restrict__ lo_out;          // LO pass 2: remainder part of phi^{n+1}
-  R* __restrict__ v_out;           // pass 2: v^{n+1}
-  int nx, ny;
-  size_t plane;
-  int ntx, ntiles;
-  R dt;
-  Spacing<R> h;
-  Couplings<R> k;
-  double area;  // dx dy
-  DevState* st;
-  FlowPartial* part;
-};
+void flow_tile_dims(int prec, int* tx, int* ty) {
+  if (prec == PREC_F64) { *tx = FlowTile<double>::TX; *ty = FlowTile<double>::TY; }
+  else { *tx = FlowTile<float>::TX; *ty = FlowTile<float>::TY; }
+}
 
 // 1 / |n| for the unit-length projection: FP32 uses the hardware reciprocal square
 // root refined by one Newton-Raphson step (y <- y (3 - x y^2) / 2), FP64 divides.
@@ -163,10 +151,10 @@ struct Win {
       xterms(Pc, c[2], gx, gxx);
     }
     v = c[2];
-    fx = gx * h.i12dx;        // Eq. 1, x
-    fy = yd1(c) * h.i12dy;    // Eq. 1, y
+    fx = gx * h.i12dx;      // Eq. 1, x
+    fy = yd1(c) * h.i12dy;  // Eq. 1, y
     if (SECOND) {
-      fxx = gxx * h.i12dx2;   // Eq. 2, x
+      fxx = gxx * h.i12dx2;     // Eq. 2, x
       fyy = yd2(c) * h.i12dy2;  // Eq. 2, y
     } else {
       fxx = fyy = R(0);
@@ -206,7 +194,7 @@ struct StageWin {
   }
 };
 
-// First derivatives only (the field difference of the arrest test): one plane set.
+// First derivatives only (the field difference of the arrest test).
 template <int TH, typename R>
 struct DiffWin {
   static constexpr int C = NComp<TH>::C;
@@ -236,70 +224,175 @@ __device__ __forceinline__ void force_at(const Couplings<R>& k, const R* v, cons
   else force_cm<R>(k, v, fx, fy, fxx, fyy, G);
 }
 
-// Tile sets in shared memory (each C planes of SXY values): pass 1 [Y1 | Y2 | delta],
-// pass 2 [Y3 | Y4]. LO: compensated FP32 storage (value + remainder planes).
-template <int TH, typename R, int PASS, bool LO>
-__global__ void __launch_bounds__(NT) k_pass(PassArgs<R> a) {
+// ---- per-tile block reduction in the working type: two compensated sums, one max
+template <typename R>
+struct RPair {
+  R s, c;
+};
+__device__ __forceinline__ RPair<float> pair_add(RPair<float> x, RPair<float> y) {
+  float s, e;
+  two_sum_f(x.s, y.s, s, e);
+  return RPair<float>{s, x.c + y.c + e};
+}
+__device__ __forceinline__ RPair<double> pair_add(RPair<double> x, RPair<double> y) {
+  double s, e;
+  two_sum(x.s, y.s, s, e);
+  return RPair<double>{s, x.c + y.c + e};
+}
+template <typename R>
+__device__ __forceinline__ R rmax(R a, R b) {
+  return (b > a || b != b) ? b : a;  // propagates NaN
+}
+// Block-wide: thread 0 ends with the block's two pairs and maximum. sm holds
+// (NT / 32) * 5 values of R. Fixed shape: bitwise reproducible.
+template <typename R>
+__device__ __forceinline__ void tile_reduce(RPair<R>& a, RPair<R>& b, R& m, R* sm) {
+  constexpr int W = NT / 32;
+  const int lane = threadIdx.x & 31, wid = (threadIdx.y * BX + threadIdx.x) >> 5;
+  for (int off = 16; off > 0; off >>= 1) {
+    a = pair_add(a, RPair<R>{__shfl_down_sync(0xffffffffu, a.s, off), __shfl_down_sync(0xffffffffu, a.c, off)});
+    b = pair_add(b, RPair<R>{__shfl_down_sync(0xffffffffu, b.s, off), __shfl_down_sync(0xffffffffu, b.c, off)});
+    m = rmax(m, __shfl_down_sync(0xffffffffu, m, off));
+  }
+  if (lane == 0) {
+    sm[wid] = a.s; sm[W + wid] = a.c; sm[2 * W + wid] = b.s; sm[3 * W + wid] = b.c; sm[4 * W + wid] = m;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    a = lane < W ? RPair<R>{sm[lane], sm[W + lane]} : RPair<R>{R(0), R(0)};
+    b = lane < W ? RPair<R>{sm[2 * W + lane], sm[3 * W + lane]} : RPair<R>{R(0), R(0)};
+    m = lane < W ? sm[4 * W + lane] : R(0);
+    for (int off = 16; off > 0; off >>= 1) {
+      a = pair_add(a, RPair<R>{__shfl_down_sync(0xffffffffu, a.s, off), __shfl_down_sync(0xffffffffu, a.c, off)});
+      b = pair_add(b, RPair<R>{__shfl_down_sync(0xffffffffu, b.s, off), __shfl_down_sync(0xffffffffu, b.c, off)});
+      m = rmax(m, __shfl_down_sync(0xffffffffu, m, off));
+    }
+  }
+  __syncthreads();
+}
+
+// Per-tile view of the problem, staged in shared memory by thread 0.
+template <typename R>
+struct TileCtx {
+  ProbDesc<R> d;
+  int p;         // problem index
+  int skip;      // the problem has stopped (or, pass 1, its head is already evaluated)
+  int cur;       // ping-pong parity of the current field
+  int arrest;    // pass 2: the current velocity counts as zero
+  int has_prev;  // pass 1: the other buffer holds the previous field
+};
+
+// Thread 0 stages the view of tile t. A problem's record changes only when its last
+// tile of a launch arrives, so while any of its tiles is still unprocessed (as tile
+// t is here) the view stays valid: it may be read ahead of use. A launch over a
+// single problem passes its descriptor as a kernel parameter and stages only the
+// record's flags.
+template <typename R, int PASS, bool ONE>
+__device__ __forceinline__ void load_tile_ctx(TileCtx<R>& tc, const ProbDesc<R>& one,
+                                              const ProbDesc<R>* __restrict__ probs,
+                                              const int* __restrict__ tile_prob, int t) {
+  const DevState* st;
+  if constexpr (ONE) {
+    tc.p = 0;
+    st = one.st;
+  } else {
+    const int p = tile_prob[t];
+    tc.d = probs[p];
+    tc.p = p;
+    st = tc.d.st;
+  }
+  const long long steps = st->steps;
+  int skip = (st->converged | st->nonfinite) != 0;
+  if (PASS == 1) skip |= (st->head_step == steps);
+  else skip |= (steps >= st->step_limit);
+  tc.skip = skip;
+  tc.cur = (int)(steps & 1);
+  tc.arrest = (PASS == 2) && (st->arrest != 0);
+  tc.has_prev = (PASS == 1) && (steps > 0);
+}
+
+// One flow pass over every tile of a batch. ONE: the batch has a single problem,
+// whose descriptor arrives as a kernel parameter, so its pointers, spacings and
+// couplings are read as constant operands instead of occupying registers.
+template <int TH, typename R, int PASS, bool LO, bool ONE>
+__global__ void __launch_bounds__(NT)
+    k_pass(const __grid_constant__ ProbDesc<R> one, const ProbDesc<R>* __restrict__ probs,
+           const int* __restrict__ tile_prob, int total_tiles) {
   using T = FlowTile<R>;
   constexpr int C = NComp<TH>::C;
   constexpr int RY = T::RY;
   constexpr int PS = C * T::SXY;  // values per tile set
   extern __shared__ __align__(16) unsigned char smraw[];
-  R* sm = reinterpret_cast<R*>(smraw);
-  __shared__ double sred[RedSmem<2, 1>::n];
+  R* sm = reinterpret_cast<R*>(smraw);  // pass 1: [Y1 | Y2 | delta], pass 2: [Y3 | Y4]
+  __shared__ TileCtx<R> tcb[2];         // this tile's view and the next one's (read ahead)
+  __shared__ R sred[(NT / 32) * 5];
+  __shared__ double dred[RedSmem<2, 1>::n];
   __shared__ int s_last;
-
-  DevState* st = a.st;
-  // Uniform over the grid (the record only changes between launches). Pass 1 runs
-  // once per field; pass 2 stops at convergence, at a non-finite value and at the
-  // step limit of the current call.
-  if (st->converged | st->nonfinite) return;
-  if (PASS == 1 ? (st->head_step == st->steps) : (st->steps >= st->step_limit)) return;
   const int tid = threadIdx.y * BX + threadIdx.x;
-  const bool arrest = (PASS == 2) && (st->arrest != 0);
-  const bool has_prev = (PASS == 1) && (st->steps > 0);
-  const size_t P = a.plane;
-  const R dt = a.dt, hdt = R(0.5) * a.dt;
-  const R c3 = R(0.25) * dt * dt, c4 = R(0.5) * dt * dt;
   R* const setA = sm;           // first stage input of the pass
   R* const setB = sm + PS;      // second stage input
   R* const setD = sm + 2 * PS;  // pass 1: phi^n - phi^{n-1}
-
+  // pass 1: running sums over this block's consecutive tiles of one problem
   R es = R(0), ec = R(0), ds = R(0), dc = R(0), gmr = R(0);
 
-  for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
-    const int x0 = (t % a.ntx) * T::TX, y0 = (t / a.ntx) * T::TY;
-    __syncthreads();  // the previous tile's shared reads are finished
-    // ---- stage inputs over the tile and its halo, two sites per iteration
-    for (int base = tid; base < T::SXY; base += 2 * NT) {
-      R pv[2][C], lv[2][C], vv[2][C], k1v[2][C], k2v[2][C], pp[2][C], lp[2][C];
-      bool in[2], inside[2];
-      size_t sidx[2];
+  if (tid == 0 && (int)blockIdx.x < total_tiles) load_tile_ctx<R, PASS, ONE>(tcb[0], one, probs, tile_prob, blockIdx.x);
+  int buf = 0;
+  for (int t = blockIdx.x; t < total_tiles; t += gridDim.x, buf ^= 1) {
+    __syncthreads();  // tcb[buf] is staged; the previous tile's shared reads are finished
+    const int tn = t + gridDim.x;
+    if (tid == 0 && tn < total_tiles) load_tile_ctx<R, PASS, ONE>(tcb[buf ^ 1], one, probs, tile_prob, tn);
+    const TileCtx<R>& tc = tcb[buf];
+    if (tc.skip) continue;  // uniform over the block
+    const ProbDesc<R>& D = ONE ? one : tc.d;
+    const int cur = tc.cur;
+    const bool arrest = tc.arrest != 0;
+    const bool has_prev = tc.has_prev != 0;
+    const int nx = D.nx, ny = D.ny;
+    const size_t P = (size_t)D.plane;
+    const R* __restrict__ phi = D.phi[cur];
+    const R* __restrict__ lo = D.lo[cur];
+    const R* __restrict__ vel = D.v[cur];
+    const R* __restrict__ phi_prev = D.phi[cur ^ 1];
+    const R* __restrict__ lo_prev = D.lo[cur ^ 1];
+    R* __restrict__ kv1 = D.kv[0];
+    R* __restrict__ kv2 = D.kv[1];
+    const Spacing<R> h = D.h;
+    const Couplings<R> kc = D.k;
+    const R dt = D.dt, hdt = R(0.5) * dt;
+    const R c3 = R(0.25) * dt * dt, c4 = R(0.5) * dt * dt;
+    const int lt = t - D.tile0;  // tile index within the problem
+    const int x0 = (lt % D.ntx) * T::TX, y0 = (lt / D.ntx) * T::TY;
+
+    // ---- stage inputs over the tile and its halo, LU sites per iteration (the loads
+    // of all LU sites are issued before any is used: more bytes in flight per thread)
+    constexpr int LU = 2;
+    for (int base = tid; base < T::SXY; base += LU * NT) {
+      R pv[LU][C], lv[LU][C], vv[LU][C], k1v[LU][C], k2v[LU][C], pp[LU][C], lp[LU][C];
+      bool in[LU], inside[LU];
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {  // all global loads of both sites first
+      for (int u = 0; u < LU; ++u) {  // all global loads of the sites first
         const int idx = base + u * NT;
         const int ly = idx / T::SX, lx = idx - ly * T::SX;
         const int gx = x0 + lx - 2, gy = y0 + ly - 2;
-        in[u] = idx < T::SXY && gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny;
-        inside[u] = in[u] && gx >= 2 && gx < a.nx - 2 && gy >= 2 && gy < a.ny - 2;
-        const size_t s = in[u] ? (size_t)gy * a.nx + gx : 0;
-        sidx[u] = s;
+        in[u] = idx < T::SXY && gx >= 0 && gx < nx && gy >= 0 && gy < ny;
+        inside[u] = in[u] && gx >= 2 && gx < nx - 2 && gy >= 2 && gy < ny - 2;
+        const size_t s = in[u] ? (size_t)gy * nx + gx : 0;
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-          pv[u][c] = in[u] ? a.phi[c * P + s] : R(0);
-          lv[u][c] = (LO && in[u]) ? a.lo[c * P + s] : R(0);
-          vv[u][c] = (inside[u] && !arrest) ? a.v[c * P + s] : R(0);
+          pv[u][c] = in[u] ? phi[c * P + s] : R(0);
+          lv[u][c] = (LO && in[u]) ? lo[c * P + s] : R(0);
+          vv[u][c] = (inside[u] && !arrest) ? vel[c * P + s] : R(0);
           if (PASS == 1) {
-            pp[u][c] = (has_prev && in[u]) ? a.phi_prev[c * P + s] : pv[u][c];
-            lp[u][c] = (LO && has_prev && in[u]) ? a.lo_prev[c * P + s] : lv[u][c];
+            pp[u][c] = (has_prev && in[u]) ? phi_prev[c * P + s] : pv[u][c];
+            lp[u][c] = (LO && has_prev && in[u]) ? lo_prev[c * P + s] : lv[u][c];
           } else {
-            k1v[u][c] = inside[u] ? a.kv1[c * P + s] : R(0);
-            k2v[u][c] = inside[u] ? (arrest ? k1v[u][c] : a.kv2[c * P + s]) : R(0);
+            k1v[u][c] = inside[u] ? kv1[c * P + s] : R(0);
+            k2v[u][c] = inside[u] ? (arrest ? k1v[u][c] : kv2[c * P + s]) : R(0);
           }
         }
       }
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
+      for (int u = 0; u < LU; ++u) {
         const int idx = base + u * NT;
         if (idx >= T::SXY) break;
         R ya[C], yb[C], yd[C];
@@ -308,32 +401,20 @@ __global__ void __launch_bounds__(NT) k_pass(PassArgs<R> a) {
           for (int c = 0; c < C; ++c) {
             // delta = phi^n - phi^{n-1} (differences of neighbouring values: exact per part)
             yd[c] = LO ? (pv[u][c] - pp[u][c]) + (lv[u][c] - lp[u][c]) : pv[u][c] - pp[u][c];
-            if (LO) {
-              ya[c] = lv[u][c];
-              yb[c] = lv[u][c] + hdt * vv[u][c];
-            } else {
-              ya[c] = pv[u][c];
-              yb[c] = pv[u][c] + hdt * vv[u][c];
-            }
+            ya[c] = LO ? lv[u][c] : pv[u][c];
+            yb[c] = (LO ? lv[u][c] : pv[u][c]) + hdt * vv[u][c];
           }
           if (TH == TH_CM && inside[u]) {
             if constexpr (LO) normalise_split(pv[u], yb);
             else normalise<C>(yb);
-          }
-          if (LO) {  // stage inputs: value + small part, rounded once
-#pragma unroll
-            for (int c = 0; c < C; ++c) {
-              ya[c] = pv[u][c] + ya[c];
-              yb[c] = pv[u][c] + yb[c];
-            }
           }
         } else {
 #pragma unroll
           for (int c = 0; c < C; ++c) {
             const R base3 = hdt * vv[u][c] + c3 * k1v[u][c];
             const R base4 = dt * vv[u][c] + c4 * k2v[u][c];
-            ya[c] = LO ? lv[u][c] + base3 : pv[u][c] + base3;
-            yb[c] = LO ? lv[u][c] + base4 : pv[u][c] + base4;
+            ya[c] = (LO ? lv[u][c] : pv[u][c]) + base3;
+            yb[c] = (LO ? lv[u][c] : pv[u][c]) + base4;
           }
           if (TH == TH_CM && inside[u]) {
             if constexpr (LO) {
@@ -344,12 +425,12 @@ __global__ void __launch_bounds__(NT) k_pass(PassArgs<R> a) {
               normalise<C>(yb);
             }
           }
-          if (LO) {
+        }
+        if (LO) {  // stage inputs: value + small part, rounded once
 #pragma unroll
-            for (int c = 0; c < C; ++c) {
-              ya[c] = pv[u][c] + ya[c];
-              yb[c] = pv[u][c] + yb[c];
-            }
+          for (int c = 0; c < C; ++c) {
+            ya[c] = pv[u][c] + ya[c];
+            yb[c] = pv[u][c] + yb[c];
           }
         }
 #pragma unroll
@@ -365,7 +446,7 @@ __global__ void __launch_bounds__(NT) k_pass(PassArgs<R> a) {
     // ---- column walk: RY rows of column threadIdx.x
     const int sx = threadIdx.x + 2, sy0 = threadIdx.y * RY + 2;
     const int gx = x0 + threadIdx.x, gyb = y0 + threadIdx.y * RY;
-    const bool colok = gx >= 2 && gx < a.nx - 2;
+    const bool colok = gx >= 2 && gx < nx - 2;
 
     if (PASS == 1) {
       // stage 1 at Y_1 = phi: k_v1, e, max|G|, and e(phi^n) - e(phi^{n-1})
@@ -381,29 +462,28 @@ __global__ void __launch_bounds__(NT) k_pass(PassArgs<R> a) {
 #pragma unroll
         for (int r = 0; r < RY; ++r) {
           const int off = (sy0 + r) * T::SX + sx;
-          const bool ok = colok && gyb + r >= 2 && gyb + r < a.ny - 2;
+          const bool ok = colok && gyb + r >= 2 && gyb + r < ny - 2;
           R v[C], fx[C], fy[C], fxx[C], fyy[C], fxy[C], G[C];
-          W.derivs(setA, off, a.h, v, fx, fy, fxx, fyy, fxy);
-          force_at<TH, R>(a.k, v, fx, fy, fxx, fyy, fxy, G);
+          W.derivs(setA, off, h, v, fx, fy, fxx, fyy, fxy);
+          force_at<TH, R>(kc, v, fx, fy, fxx, fyy, fxy, G);
           if (ok) {
-            const size_t s = (size_t)(gyb + r) * a.nx + gx;
+            const size_t s = (size_t)(gyb + r) * nx + gx;
 #pragma unroll
             for (int c = 0; c < C; ++c) {
-              a.kv1_out[c * P + s] = -G[c];
-              const R ag = fabs(G[c]);
-              gmr = (ag > gmr || ag != ag) ? ag : gmr;
+              kv1[c * P + s] = -G[c];
+              gmr = rmax(gmr, fabs(G[c]));
             }
-            const R e = (TH == TH_AH) ? density_ah<R>(a.k, v, fx, fy) : density_cm<R>(a.k, v, fx, fy);
+            const R e = (TH == TH_AH) ? density_ah<R>(kc, v, fx, fy) : density_cm<R>(kc, v, fx, fy);
             const R t1 = es + e;
             ec += (fabs(es) >= fabs(e)) ? (es - t1) + e : (e - t1) + es;
             es = t1;
           }
           if (has_prev) {
-            R d[C], dxv[C], dyv[C];
-            D.derivs(setD, off, a.h, d, dxv, dyv);
+            R dd[C], dxv[C], dyv[C];
+            D.derivs(setD, off, h, dd, dxv, dyv);
             if (ok) {
-              const R de = (TH == TH_AH) ? delta_density_ah<R>(a.k, v, fx, fy, d, dxv, dyv)
-                                         : delta_density_cm<R>(a.k, v, fx, fy, d, dxv, dyv);
+              const R de = (TH == TH_AH) ? delta_density_ah<R>(kc, v, fx, fy, dd, dxv, dyv)
+                                         : delta_density_cm<R>(kc, v, fx, fy, dd, dxv, dyv);
               const R t2 = ds + de;
               dc += (fabs(ds) >= fabs(de)) ? (ds - t2) + de : (de - t2) + ds;
               ds = t2;
@@ -429,17 +509,77 @@ __global__ void __launch_bounds__(NT) k_pass(PassArgs<R> a) {
         for (int r = 0; r < RY; ++r) {
           const int off = (sy0 + r) * T::SX + sx;
           R v[C], fx[C], fy[C], fxx[C], fyy[C], fxy[C], G[C];
-          W.derivs(setB, off, a.h, v, fx, fy, fxx, fyy, fxy);
-          force_at<TH, R>(a.k, v, fx, fy, fxx, fyy, fxy, G);
-          if (colok && gyb + r >= 2 && gyb + r < a.ny - 2) {
-            const size_t s = (size_t)(gyb + r) * a.nx + gx;
+          W.derivs(setB, off, h, v, fx, fy, fxx, fyy, fxy);
+          force_at<TH, R>(kc, v, fx, fy, fxx, fyy, fxy, G);
+          if (colok && gyb + r >= 2 && gyb + r < ny - 2) {
+            const size_t s = (size_t)(gyb + r) * nx + gx;
 #pragma unroll
-            for (int c = 0; c < C; ++c) a.kv2_out[c * P + s] = -G[c];
+            for (int c = 0; c < C; ++c) kv2[c * P + s] = -G[c];
           }
           if (r + 1 < RY) {
             W.shift();
             W.enter(setB, (sy0 + r + 3) * T::SX + sx, 4);
           }
+        }
+      }
+
+      // ---- partials: the block keeps summing while its next tile belongs to the same
+      // problem and writes a zero partial for this tile; otherwise it reduces and writes
+      // the running sums. The tile that completes the problem's count reduces the
+      // problem's partials in tile order and decides. (A tile whose block still holds
+      // another tile of the problem can never be the last to arrive.)
+      const ProbDesc<R>& d = D;
+      const bool flush = ONE ? tn >= total_tiles : !(tn < total_tiles && tcb[buf ^ 1].p == tc.p);
+      if (!flush) {
+        if (tid == 0) {
+          d.part[lt] = FlowPartial{0.0, 0.0, 0.0, 0.0, 0.0, {0.0, 0.0, 0.0}};
+          __threadfence();
+          atomicAdd(&d.st->ticket, 1u);
+        }
+        continue;
+      }
+      RPair<R> pe{es, ec}, pd{ds, dc};
+      R pm = gmr;
+      tile_reduce<R>(pe, pd, pm, sred);
+      es = ec = ds = dc = gmr = R(0);  // the next run of tiles starts afresh
+      if (tid == 0) {
+        d.part[lt] = FlowPartial{(double)pe.s, (double)pe.c, (double)pd.s, (double)pd.c, (double)pm,
+                                 {0.0, 0.0, 0.0}};
+        __threadfence();
+        const unsigned prev = atomicAdd(&d.st->ticket, 1u);
+        s_last = (prev == (unsigned)d.ntiles - 1);
+      }
+      __syncthreads();
+      if (s_last) {
+        __threadfence();
+        DD acc{0.0, 0.0}, dacc{0.0, 0.0};
+        double mm = 0.0;
+        for (int i = tid; i < d.ntiles; i += NT) {
+          const FlowPartial* q = d.part + i;
+          acc = dd_add(acc, DD{__ldcg(&q->es), __ldcg(&q->ec)});
+          dacc = dd_add(dacc, DD{__ldcg(&q->ds), __ldcg(&q->dc)});
+          mm = nanmax(mm, __ldcg(&q->m));
+        }
+        DD sv2[2] = {acc, dacc};
+        double mv2[1] = {mm};
+        block_reduce<2, 1>(sv2, mv2, dred);
+        if (tid == 0) {
+          DevState* st = d.st;
+          const double E = d.area * (sv2[0].s + sv2[0].c);
+          const double dE = d.area * (sv2[1].s + sv2[1].c);
+          const double g = d.area * mv2[0];
+          // Eq. 4, strict: E_h(phi^n) > E_h(phi^{n-1}); no previous field (E_last = +inf): no arrest
+          const int arr = has_prev ? (dE > 0.0 ? 1 : 0) : (E > st->E_last ? 1 : 0);
+          st->E_cur = E;
+          st->dE = has_prev ? dE : 0.0;
+          st->gmax = g;
+          st->arrest = arr;
+          st->arrests += arr;
+          st->E_last = E;
+          st->converged = (g < st->tol) ? 1 : 0;
+          st->nonfinite = (isfinite(E) && isfinite(g) && isfinite(dE)) ? 0 : 1;
+          st->head_step = st->steps;
+          st->ticket = 0;
         }
       }
     } else {
@@ -453,8 +593,8 @@ __global__ void __launch_bounds__(NT) k_pass(PassArgs<R> a) {
         for (int r = 0; r < RY; ++r) {
           const int off = (sy0 + r) * T::SX + sx;
           R v[C], fx[C], fy[C], fxx[C], fyy[C], fxy[C], G[C];
-          W.derivs(setA, off, a.h, v, fx, fy, fxx, fyy, fxy);
-          force_at<TH, R>(a.k, v, fx, fy, fxx, fyy, fxy, G);
+          W.derivs(setA, off, h, v, fx, fy, fxx, fyy, fxy);
+          force_at<TH, R>(kc, v, fx, fy, fxx, fyy, fxy, G);
 #pragma unroll
           for (int c = 0; c < C; ++c) k3[r][c] = -G[c];
           if (r + 1 < RY) {
@@ -469,25 +609,28 @@ __global__ void __launch_bounds__(NT) k_pass(PassArgs<R> a) {
 #pragma unroll
         for (int s = 0; s < 5; ++s) W.enter(setB, (sy0 - 2 + s) * T::SX + sx, s);
         const R w6 = dt * dt / R(6), u6 = dt / R(6);
+        R* __restrict__ phi_out = D.phi[cur ^ 1];
+        R* __restrict__ lo_out = D.lo[cur ^ 1];
+        R* __restrict__ v_out = D.v[cur ^ 1];
 #pragma unroll
         for (int r = 0; r < RY; ++r) {
           const int off = (sy0 + r) * T::SX + sx;
           R v[C], fx[C], fy[C], fxx[C], fyy[C], fxy[C], G[C];
-          W.derivs(setB, off, a.h, v, fx, fy, fxx, fyy, fxy);
-          force_at<TH, R>(a.k, v, fx, fy, fxx, fyy, fxy, G);
-          if (colok && gyb + r >= 2 && gyb + r < a.ny - 2) {
-            const size_t s = (size_t)(gyb + r) * a.nx + gx;
+          W.derivs(setB, off, h, v, fx, fy, fxx, fyy, fxy);
+          force_at<TH, R>(kc, v, fx, fy, fxx, fyy, fxy, G);
+          if (colok && gyb + r >= 2 && gyb + r < ny - 2) {
+            const size_t s = (size_t)(gyb + r) * nx + gx;
             R p0[C], q[C], vn[C];
 #pragma unroll
             for (int c = 0; c < C; ++c) {
-              p0[c] = a.phi[c * P + s];
-              const R v0 = arrest ? R(0) : a.v[c * P + s];
-              const R k1 = a.kv1[c * P + s];
-              const R k2 = arrest ? k1 : a.kv2[c * P + s];
+              p0[c] = phi[c * P + s];
+              const R v0 = arrest ? R(0) : vel[c * P + s];
+              const R k1 = kv1[c * P + s];
+              const R k2 = arrest ? k1 : kv2[c * P + s];
               const R k4 = -G[c];
-              // increment of phi; with compensated storage it joins the stored lo part
+              // increment of phi; with compensated storage it joins the stored remainder
               const R inc = dt * v0 + w6 * (k1 + k2 + k3[r][c]);
-              q[c] = LO ? a.lo[c * P + s] + inc : p0[c] + inc;
+              q[c] = LO ? lo[c * P + s] + inc : p0[c] + inc;
               vn[c] = v0 + u6 * (k1 + R(2) * (k2 + k3[r][c]) + k4);
             }
             R pn[C], ln[C];
@@ -507,9 +650,9 @@ __global__ void __launch_bounds__(NT) k_pass(PassArgs<R> a) {
             }
 #pragma unroll
             for (int c = 0; c < C; ++c) {
-              a.phi_out[c * P + s] = pn[c];
-              if (LO) a.lo_out[c * P + s] = ln[c];
-              a.v_out[c * P + s] = vn[c];
+              phi_out[c * P + s] = pn[c];
+              if (LO) lo_out[c * P + s] = ln[c];
+              v_out[c * P + s] = vn[c];
             }
           }
           if (r + 1 < RY) {
@@ -518,81 +661,67 @@ __global__ void __launch_bounds__(NT) k_pass(PassArgs<R> a) {
           }
         }
       }
+      // The step count selects the ping-pong buffers and gates every tile of this
+      // problem, so it advances only when the problem's last tile has arrived (its
+      // own stores need not be finished: nothing in this launch reads them, and the
+      // next launch starts after this one ends).
+      if (tid == 0) {
+        __threadfence();
+        DevState* st = D.st;
+        const unsigned prev = atomicAdd(&st->ticket, 1u);
+        if (prev == (unsigned)D.ntiles - 1) {
+          st->ticket = 0;
+          st->steps += 1;
+        }
+      }
     }
-  }
-
-  if (PASS == 2) {
-    if (blockIdx.x == 0 && tid == 0) st->steps += 1;  // single writer; read after this launch
-    return;
-  }
-
-  // ---- energy / residual reduction and the on-device arrest + convergence decision
-  DD sv[2] = {DD{(double)es, (double)ec}, DD{(double)ds, (double)dc}};
-  double mv[1] = {(double)gmr};
-  block_reduce<2, 1>(sv, mv, sred);
-  if (tid == 0) {
-    a.part[blockIdx.x] = FlowPartial{sv[0].s, sv[0].c, sv[1].s, sv[1].c, mv[0], {0.0, 0.0, 0.0}};
-    __threadfence();
-    const unsigned prev = atomicAdd(&st->ticket, 1u);
-    s_last = (prev == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  DD acc{0.0, 0.0}, dacc{0.0, 0.0};
-  double mm = 0.0;
-  for (int i = tid; i < (int)gridDim.x; i += NT) {
-    const FlowPartial* q = a.part + i;
-    acc = dd_add(acc, DD{__ldcg(&q->es), __ldcg(&q->ec)});
-    dacc = dd_add(dacc, DD{__ldcg(&q->ds), __ldcg(&q->dc)});
-    mm = nanmax(mm, __ldcg(&q->m));
-  }
-  DD sv2[2] = {acc, dacc};
-  double mv2[1] = {mm};
-  block_reduce<2, 1>(sv2, mv2, sred);
-  if (tid == 0) {
-    const double E = a.area * (sv2[0].s + sv2[0].c);
-    const double dE = a.area * (sv2[1].s + sv2[1].c);
-    const double g = a.area * mv2[0];
-    // Eq. 4, strict: E_h(phi^n) > E_h(phi^{n-1}); no previous field (E_last = +inf): no arrest
-    const int arr = has_prev ? (dE > 0.0 ? 1 : 0) : (E > st->E_last ? 1 : 0);
-    st->E_cur = E;
-    st->dE = has_prev ? dE : 0.0;
-    st->gmax = g;
-    st->arrest = arr;
-    st->arrests += arr;
-    st->E_last = E;
-    st->converged = (g < st->tol) ? 1 : 0;
-    st->nonfinite = (isfinite(E) && isfinite(g) && isfinite(dE)) ? 0 : 1;
-    st->head_step = st->steps;
-    st->ticket = 0;
   }
 }
 
 // ------------------------------------------------------------------ control kernels
-__global__ void k_reset_state(DevState* st) {
-  st->E_last = __longlong_as_double(0x7ff0000000000000LL);  // +inf: no arrest on the first step
-  st->E_cur = 0.0;
-  st->dE = 0.0;
-  st->gmax = 0.0;
-  st->tol = -1.0;
-  st->steps = 0;
-  st->arrests = 0;
-  st->head_step = -1;
-  st->step_limit = 0;
-  st->arrest = 0;
-  st->converged = 0;
-  st->nonfinite = 0;
-  st->ticket = 0;
-  st->obs_ticket = 0;
+__global__ void k_reset_states(DevState* st, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    DevState* s = st + i;
+    s->E_last = __longlong_as_double(0x7ff0000000000000LL);  // +inf: no arrest on the first step
+    s->E_cur = 0.0;
+    s->dE = 0.0;
+    s->gmax = 0.0;
+    s->tol = -1.0;
+    s->steps = 0;
+    s->arrests = 0;
+    s->head_step = -1;
+    s->step_limit = 0;
+    s->arrest = 0;
+    s->converged = 0;
+    s->nonfinite = 0;
+    s->ticket = 0;
+    s->obs_ticket = 0;
+  }
 }
 
 // Start of a run: threshold, step budget, and the convergence verdict of an
 // already-evaluated head under the new threshold.
-__global__ void k_set_run(DevState* st, double tol, long long max_steps) {
-  st->tol = tol;
-  st->step_limit = st->steps + max_steps;
-  st->converged = (st->head_step == st->steps && st->gmax < tol) ? 1 : 0;
+__global__ void k_set_run_all(DevState* st, int n, double tol, long long max_steps) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    DevState* s = st + i;
+    s->tol = tol;
+    s->step_limit = s->steps + max_steps;
+    s->converged = (s->head_step == s->steps && s->gmax < tol) ? 1 : 0;
+  }
+}
+
+__global__ void k_count_active(const DevState* st, int n, int* out) {
+  __shared__ int cnt;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  int mine = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const DevState* s = st + i;
+    mine += !(s->converged || s->nonfinite || s->steps >= s->step_limit);
+  }
+  atomicAdd(&cnt, mine);
+  __syncthreads();
+  if (threadIdx.x == 0) *out = cnt;
 }
 
 template <typename R>
@@ -604,74 +733,51 @@ __global__ void k_scaled_copy(R* __restrict__ out, const R* __restrict__ in, siz
 // ------------------------------------------------------------------ launchers
 template <int TH, typename R>
 static size_t pass_smem(int pass) {
-  const int sets = pass == 1 ? 3 : 2;
-  return (size_t)sets * NComp<TH>::C * FlowTile<R>::SXY * sizeof(R);
+  return (size_t)(pass == 1 ? 3 : 2) * NComp<TH>::C * FlowTile<R>::SXY * sizeof(R);
 }
 
-template <typename R>
-static PassArgs<R> make_args(const LaunchCtx& c, int cur) {
-  PassArgs<R> a{};
-  const int nxt = cur ^ 1;
-  a.phi = static_cast<const R*>(c.phi[cur]);
-  a.lo = static_cast<const R*>(c.lo[cur]);
-  a.phi_prev = static_cast<const R*>(c.phi[nxt]);
-  a.lo_prev = static_cast<const R*>(c.lo[nxt]);
-  a.v = static_cast<const R*>(c.v[cur]);
-  a.kv1 = static_cast<const R*>(c.kv[0]);
-  a.kv2 = static_cast<const R*>(c.kv[1]);
-  a.kv1_out = static_cast<R*>(c.kv[0]);
-  a.kv2_out = static_cast<R*>(c.kv[1]);
-  a.phi_out = static_cast<R*>(c.phi[nxt]);
-  a.lo_out = static_cast<R*>(c.lo[nxt]);
-  a.v_out = static_cast<R*>(c.v[nxt]);
-  a.nx = c.nx;
-  a.ny = c.ny;
-  a.plane = c.plane;
-  a.ntx = (c.nx + FlowTile<R>::TX - 1) / FlowTile<R>::TX;
-  a.ntiles = a.ntx * ((c.ny + FlowTile<R>::TY - 1) / FlowTile<R>::TY);
-  a.dt = (R)c.dt;
-  a.h.i12dx = (R)(1.0 / (12.0 * c.dx));
-  a.h.i12dy = (R)(1.0 / (12.0 * c.dy));
-  a.h.i12dx2 = (R)(1.0 / (12.0 * c.dx * c.dx));
-  a.h.i12dy2 = (R)(1.0 / (12.0 * c.dy * c.dy));
-  a.h.i144dxdy = (R)(1.0 / (144.0 * c.dx * c.dy));
-  for (int i = 0; i < 10; ++i) a.k.c[i] = (R)c.coup[i];
-  a.area = c.dx * c.dy;
-  a.st = c.st;
-  a.part = c.fpart;
-  return a;
-}
-
-template <int TH, typename R, bool LO>
-static cudaError_t pass_t(const LaunchCtx& c, int pass, int cur, cudaStream_t s) {
-  const PassArgs<R> a = make_args<R>(c, cur);
+template <int TH, typename R, bool LO, bool ONE>
+static void pass_launch(const BatchLaunch& b, int pass, cudaStream_t s) {
+  const ProbDesc<R>* probs = static_cast<const ProbDesc<R>*>(b.probs);
+  const ProbDesc<R> one = ONE ? *static_cast<const ProbDesc<R>*>(b.one) : ProbDesc<R>{};
   const dim3 blk(BX, BY);
-  if (pass == 1) k_pass<TH, R, 1, LO><<<c.flow_blocks, blk, pass_smem<TH, R>(1), s>>>(a);
-  else if (pass == 2) k_pass<TH, R, 2, LO><<<c.flow_blocks, blk, pass_smem<TH, R>(2), s>>>(a);
-  else return cudaErrorInvalidValue;
+  if (pass == 1)
+    k_pass<TH, R, 1, LO, ONE><<<b.flow_blocks[0], blk, pass_smem<TH, R>(1), s>>>(one, probs, b.tile_prob, b.total_tiles);
+  else
+    k_pass<TH, R, 2, LO, ONE><<<b.flow_blocks[1], blk, pass_smem<TH, R>(2), s>>>(one, probs, b.tile_prob, b.total_tiles);
+}
+template <int TH, typename R, bool LO>
+static cudaError_t pass_t(const BatchLaunch& b, int pass, cudaStream_t s) {
+  if (pass != 1 && pass != 2) return cudaErrorInvalidValue;
+  if (b.one) pass_launch<TH, R, LO, true>(b, pass, s);
+  else pass_launch<TH, R, LO, false>(b, pass, s);
   return cudaGetLastError();
 }
-
 template <int TH>
-static cudaError_t pass_th(const LaunchCtx& c, int pass, int cur, cudaStream_t s) {
-  switch (c.prec) {
-    case PREC_F32C: return pass_t<TH, float, true>(c, pass, cur, s);
-    case PREC_F64: return pass_t<TH, double, false>(c, pass, cur, s);
-    default: return pass_t<TH, float, false>(c, pass, cur, s);
+static cudaError_t pass_th(const BatchLaunch& b, int pass, cudaStream_t s) {
+  switch (b.prec) {
+    case PREC_F32C: return pass_t<TH, float, true>(b, pass, s);
+    case PREC_F64: return pass_t<TH, double, false>(b, pass, s);
+    default: return pass_t<TH, float, false>(b, pass, s);
   }
 }
 
-cudaError_t launch_pass(const LaunchCtx& c, int pass, int cur, cudaStream_t s) {
-  return c.theory == TH_AH ? pass_th<TH_AH>(c, pass, cur, s) : pass_th<TH_CM>(c, pass, cur, s);
+cudaError_t launch_pass(const BatchLaunch& b, int pass, cudaStream_t s) {
+  return b.theory == TH_AH ? pass_th<TH_AH>(b, pass, s) : pass_th<TH_CM>(b, pass, s);
 }
 
-cudaError_t launch_reset_state(const LaunchCtx& c, cudaStream_t s) {
-  k_reset_state<<<1, 1, 0, s>>>(c.st);
+cudaError_t launch_reset_states(DevState* st, int n, cudaStream_t s) {
+  k_reset_states<<<(n + 255) / 256, 256, 0, s>>>(st, n);
   return cudaGetLastError();
 }
 
-cudaError_t launch_set_run(const LaunchCtx& c, double tol, long long max_steps, cudaStream_t s) {
-  k_set_run<<<1, 1, 0, s>>>(c.st, tol, max_steps);
+cudaError_t launch_set_run_all(DevState* st, int n, double tol, long long max_steps, cudaStream_t s) {
+  k_set_run_all<<<(n + 255) / 256, 256, 0, s>>>(st, n, tol, max_steps);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_count_active(const DevState* st, int n, int* out, cudaStream_t s) {
+  k_count_active<<<1, 256, 0, s>>>(st, n, out);
   return cudaGetLastError();
 }
 
@@ -687,42 +793,41 @@ cudaError_t launch_scaled_copy(const LaunchCtx& c, void* out, const void* in, do
   return cudaGetLastError();
 }
 
-// Opt the pass kernels into their dynamic shared memory, then size the grid by
-// the smaller occupancy of the two passes.
-template <int TH, typename R, bool LO>
-static int pass_occupancy() {
-  cudaFuncSetAttribute(k_pass<TH, R, 1, LO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pass_smem<TH, R>(1));
-  cudaFuncSetAttribute(k_pass<TH, R, 2, LO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pass_smem<TH, R>(2));
-  int b1 = 0, b2 = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_pass<TH, R, 1, LO>, NT, pass_smem<TH, R>(1));
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_pass<TH, R, 2, LO>, NT, pass_smem<TH, R>(2));
-  const int m = b1 < b2 ? b1 : b2;
-  return m < 1 ? 1 : m;
+// Opt the pass kernels into their dynamic shared memory; each pass's grid is its
+// own occupancy times the SM count (capped by the tile count).
+template <int TH, typename R, bool LO, bool ONE>
+static void pass_occupancy(int occ[2]) {
+  cudaFuncSetAttribute(k_pass<TH, R, 1, LO, ONE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pass_smem<TH, R>(1));
+  cudaFuncSetAttribute(k_pass<TH, R, 2, LO, ONE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pass_smem<TH, R>(2));
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[0], k_pass<TH, R, 1, LO, ONE>, NT, pass_smem<TH, R>(1));
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], k_pass<TH, R, 2, LO, ONE>, NT, pass_smem<TH, R>(2));
 }
 
-template <int TH>
-static int occupancy_th(int prec) {
+template <int TH, bool ONE>
+static void occupancy_th(int prec, int occ[2]) {
   switch (prec) {
-    case PREC_F32C: return pass_occupancy<TH, float, true>();
-    case PREC_F64: return pass_occupancy<TH, double, false>();
-    default: return pass_occupancy<TH, float, false>();
+    case PREC_F32C: pass_occupancy<TH, float, true, ONE>(occ); break;
+    case PREC_F64: pass_occupancy<TH, double, false, ONE>(occ); break;
+    default: pass_occupancy<TH, float, false, ONE>(occ); break;
   }
 }
 
-int flow_grid(int theory, int prec, int nx, int ny) {
+void flow_grid(int theory, int prec, int total_tiles, bool one, int blocks[2]) {
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const int occ = theory == TH_AH ? occupancy_th<TH_AH>(prec) : occupancy_th<TH_CM>(prec);
-  int ntiles;
-  if (prec == PREC_F64)
-    ntiles = ((nx + FlowTile<double>::TX - 1) / FlowTile<double>::TX) *
-             ((ny + FlowTile<double>::TY - 1) / FlowTile<double>::TY);
-  else
-    ntiles = ((nx + FlowTile<float>::TX - 1) / FlowTile<float>::TX) *
-             ((ny + FlowTile<float>::TY - 1) / FlowTile<float>::TY);
-  const int g = nsm * occ;
-  return ntiles < g ? ntiles : g;
+  int occ[2] = {1, 1};
+  if (theory == TH_AH) {
+    if (one) occupancy_th<TH_AH, true>(prec, occ);
+    else occupancy_th<TH_AH, false>(prec, occ);
+  } else {
+    if (one) occupancy_th<TH_CM, true>(prec, occ);
+    else occupancy_th<TH_CM, false>(prec, occ);
+  }
+  for (int i = 0; i < 2; ++i) {
+    const int g = nsm * (occ[i] < 1 ? 1 : occ[i]);
+    blocks[i] = total_tiles < g ? total_tiles : g;
+  }
 }
 
 }  // namespace ss

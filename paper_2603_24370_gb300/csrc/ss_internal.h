@@ -34,9 +34,51 @@ struct LaunchCtx {
   int ntiles_x, ntiles_y;
 };
 
-// Pass 1 (RK stages 1-2 + reductions + arrest decision) or pass 2 (stages 3-4 +
-// combination) of the RK4 step whose current field is phi[cur] (Sec. 3.2).
-cudaError_t launch_pass(const LaunchCtx& c, int pass, int cur, cudaStream_t s);
+// One relaxation problem as the flow kernels see it (device array, one entry per
+// problem of a batch; a single-grid context is a batch of one). R is the working
+// type of the batch.
+template <typename R>
+struct ProbDesc {
+  int nx, ny;
+  int ntx, ntiles;  // tiles along x, tiles in total
+  int tile0, pad;   // index of the problem's first tile in the batch
+  long long plane;  // nx * ny
+  R* phi[2];        // ping-pong field buffers [C][ny][nx] (value part when compensated)
+  R* lo[2];         // compensated FP32: remainder planes (else null)
+  R* v[2];          // ping-pong velocities
+  R* kv[2];         // k_v1, k_v2
+  R dt;
+  Spacing<R> h;
+  Couplings<R> k;
+  double area;      // dx dy
+  DevState* st;     // the problem's flow record
+  FlowPartial* part;  // ntiles reduction partials
+};
+
+// A batch launch: the problem table, the tile -> problem map, the grid.
+struct BatchLaunch {
+  int theory;        // TH_AH / TH_CM (one theory per batch)
+  int prec;          // PREC_*
+  const void* probs; // ProbDesc<R>[n] on the device
+  const int* tile_prob;  // [total_tiles] problem index of every tile
+  int total_tiles;
+  int flow_blocks[2];  // grid of pass 1 / pass 2
+  const void* one;     // host copy of the ProbDesc<R> of a single-problem batch, else NULL
+};
+
+// Tile shape of the flow kernels for a precision (sites per tile along x, y).
+void flow_tile_dims(int prec, int* tx, int* ty);
+
+// Pass 1 (RK stages 1-2, reductions, arrest and convergence decisions) or pass 2
+// (RK stages 3-4, combination) of one flow step of every problem of a batch that
+// is still running (Sec. 3.2). Each problem uses its own ping-pong parity.
+cudaError_t launch_pass(const BatchLaunch& b, int pass, cudaStream_t s);
+// Control kernels over the n flow records of a batch.
+cudaError_t launch_reset_states(DevState* st, int n, cudaStream_t s);
+cudaError_t launch_set_run_all(DevState* st, int n, double tol, long long max_steps, cudaStream_t s);
+// Number of problems still running (not converged, finite, under the step limit).
+cudaError_t launch_count_active(const DevState* st, int n, int* out, cudaStream_t s);
+
 // Control kernels: reset the flow record for new fields; start a run with a
 // convergence threshold (tol < 0: none) and a budget of max_steps further steps.
 cudaError_t launch_reset_state(const LaunchCtx& c, cudaStream_t s);
@@ -51,8 +93,8 @@ cudaError_t launch_ansatz(const LaunchCtx& c, const double* d_sol, int n, cudaSt
 // Record the calling thread's error message for ss_last_error().
 void set_last_error(const std::string& msg);
 
-// Flow-kernel grid size for a context (occupancy x SMs, capped by the tile count).
-int flow_grid(int theory, int prec, int nx, int ny);
+// Grid of each flow pass (its occupancy x SMs, capped by the tile count).
+void flow_grid(int theory, int prec, int total_tiles, bool one, int blocks[2]);
 int obs_grid(int theory, int prec, int ntiles);
 
 }  // namespace ss

@@ -62,6 +62,12 @@ class ss_status(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class ss_batch_item(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("dx", ctypes.c_double), ("dy", ctypes.c_double),
+                ("params", ctypes.POINTER(ctypes.c_double)), ("n_params", ctypes.c_int),
+                ("solitons", ctypes.POINTER(ss_soliton)), ("n_solitons", ctypes.c_int)]
+
+
 class ss_obs(ctypes.Structure):
     _fields_ = [("energy", ctypes.c_double), ("charge", ctypes.c_double), ("flux", ctypes.c_double),
                 ("grad_max", ctypes.c_double), ("grad_max_raw", ctypes.c_double), ("norm_dev", ctypes.c_double),
@@ -103,6 +109,13 @@ def load_library(path: str | None = None):
             "ss_observables": ([vp, ctypes.POINTER(ss_obs)], i),
             "ss_profile_stages": ([vp, i, ctypes.POINTER(ctypes.c_float)], i),
             "ss_observables_noalloc": ([i, pd, i, vp, i, i, d, d, i, vp, vp], i),
+            "ss_batch_create": ([ctypes.POINTER(vp), i, i, ctypes.POINTER(ss_batch_item), i, vp], i),
+            "ss_batch_size": ([vp], i),
+            "ss_batch_step": ([vp, i, ctypes.POINTER(ss_status)], i),
+            "ss_batch_minimise": ([vp, d, ll, ctypes.POINTER(ss_status)], i),
+            "ss_batch_get_fields": ([vp, i, vp, i], i),
+            "ss_batch_observables": ([vp, i, ctypes.POINTER(ss_obs)], i),
+            "ss_batch_destroy": ([vp], i),
             "ss_destroy": ([vp], i),
         }
         for name, (args, res) in sig.items():
@@ -247,6 +260,69 @@ def _dtype_of(a):
     return a.dtype.type
 
 
+# ---------------------------------------------------------------- batches
+def _soliton_array(solitons):
+    rows = np.asarray(solitons, dtype=np.float64).reshape(-1, 5)
+    arr = (ss_soliton * max(len(rows), 1))()
+    for k, (x, y, q, size, ph) in enumerate(rows):
+        if q != int(q):
+            raise ValueError("soliton charges must be integers")
+        arr[k] = ss_soliton(x, y, int(q), size, ph)
+    return arr, len(rows)
+
+
+def ss_batch_create(theory: int, precision: int, problems, stream=None):
+    """``problems``: objects with nx, ny, dx, dy, params, solitons (e.g. inputs.Problem)."""
+    keep = []
+    items = (ss_batch_item * len(problems))()
+    for k, pr in enumerate(problems):
+        prm = np.ascontiguousarray(np.asarray(pr.params, dtype=np.float64).reshape(-1))
+        sol, ns = _soliton_array(pr.solitons)
+        keep += [prm, sol]
+        items[k] = ss_batch_item(pr.nx, pr.ny, pr.dx, pr.dy, prm.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                 prm.size, sol, ns)
+    b = ctypes.c_void_p()
+    s = None
+    if stream is not None:
+        s = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    _check(load_library().ss_batch_create(ctypes.byref(b), theory, precision, items, len(problems), s))
+    return b
+
+
+def _statuses(arr):
+    return [arr[k].as_dict() for k in range(len(arr))]
+
+
+def ss_batch_step(b, n_steps: int, allow=()):
+    n = load_library().ss_batch_size(b)
+    st = (ss_status * n)()
+    rc = _check(load_library().ss_batch_step(b, int(n_steps), st), allow)
+    return rc, _statuses(st)
+
+
+def ss_batch_minimise(b, tol: float, max_steps: int, allow=(SS_ERR_NOT_CONVERGED,)):
+    n = load_library().ss_batch_size(b)
+    st = (ss_status * n)()
+    rc = _check(load_library().ss_batch_minimise(b, float(tol), int(max_steps), st), allow)
+    return rc, _statuses(st)
+
+
+def ss_batch_get_fields(b, item: int, out) -> None:
+    p, dev = _ptr(out, np.float32 if _dtype_of(out) == np.float32 else np.float64)
+    _check(load_library().ss_batch_get_fields(b, int(item), p, dev))
+
+
+def ss_batch_observables(b, item: int) -> dict:
+    o = ss_obs()
+    _check(load_library().ss_batch_observables(b, int(item), ctypes.byref(o)))
+    return o.as_dict()
+
+
+def ss_batch_destroy(b) -> None:
+    if b is not None:
+        _check(load_library().ss_batch_destroy(b))
+
+
 # ---------------------------------------------------------------- convenience
 class Solver:
     """One relaxation problem on the GPU: a context plus its shape and dtype."""
@@ -257,6 +333,7 @@ class Solver:
         self.precision = precision
         self.C = 4 if theory == SS_ABELIAN_HIGGS else 3
         self.dtype = np.float64 if precision == SS_FP64 else np.float32
+        self.ctx = None
         self.ctx = ss_create_grid(nx, ny, dx, dy, precision, stream)
         try:
             ss_set_theory(self.ctx, theory, params)

@@ -1,0 +1,140 @@
+"""Batched relaxation (many uneven problems in the same launches) through the C-ABI.
+
+Each problem of a batch must evolve exactly as it does alone (the same tiles, the
+same per-problem reductions and decisions), match the FP64 oracle, and stop on its
+own. Tolerances as in test_gpu_parity.py.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2603_24370_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2603_24370_gb300 import build
+    from paper_2603_24370_gb300 import soliton as S
+    build.build()
+    S.load_library()
+    return S
+
+
+def mixed_batch(count=9, seed=77):
+    """Small Abelian Higgs problems of uneven sizes, spacings, couplings and charges."""
+    rng = I.SplitMix64(seed)
+    out = []
+    for k in range(count):
+        nx = rng.choice((40, 56, 77, 96))
+        ny = rng.choice((37, 64, 80))
+        dx = rng.choice((0.15, 0.2, 0.25))
+        lam = rng.uniform(0.5, 2.0)
+        nv = rng.choice((1, 2, 3))
+        Lx, Ly = nx * dx, ny * dx
+        sol = [(rng.uniform(-Lx / 5, Lx / 5), rng.uniform(-Ly / 5, Ly / 5), 1.0, 1.0, 0.0) for _ in range(nv)]
+        out.append(I.Problem(1, nx, ny, dx, dx, (lam, 1.0), sol))
+    return out
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_batch_problems_evolve_exactly_as_alone(S, prec):
+    probs = mixed_batch()
+    b = S.ss_batch_create(S.SS_ABELIAN_HIGGS, prec, probs)
+    try:
+        rc, st = S.ss_batch_step(b, 23)
+        dt = np.float64 if prec == 2 else np.float32
+        for k, p in enumerate(probs):
+            got = np.empty((4, p.ny, p.nx), dtype=dt)
+            S.ss_batch_get_fields(b, k, got)
+            with S.Solver(S.SS_ABELIAN_HIGGS, p.params, p.nx, p.ny, p.dx, p.dy, prec) as s:
+                s.init_ansatz(p.solitons)
+                st1 = s.step(23)
+                ref = s.fields()
+            assert np.array_equal(got, ref), k
+            assert st[k]["steps"] == 23 and st[k]["arrests"] == st1["arrests"]
+            # the working-precision energy sums are grouped by the block that walks
+            # the tiles, and a batch launch has its own grid: equal up to that rounding
+            assert st[k]["energy"] == pytest.approx(st1["energy"], rel=1e-13 if prec == 2 else 1e-8)
+    finally:
+        S.ss_batch_destroy(b)
+
+
+def test_batch_matches_oracle_fp64(S):
+    probs = mixed_batch(count=4, seed=5)
+    b = S.ss_batch_create(S.SS_ABELIAN_HIGGS, 2, probs)
+    try:
+        rc, st = S.ss_batch_step(b, 15)
+        for k, p in enumerate(probs):
+            got = np.empty((4, p.ny, p.nx))
+            S.ss_batch_get_fields(b, k, got)
+            f = O.ansatz(1, p.soliton_array(), p.nx, p.ny, p.dx, p.dy)
+            v = np.zeros_like(f)
+            E = O.energy(1, p.params, f, p.dx, p.dy)
+            arrests = 0
+            for _ in range(15):
+                f, v, E, a = O.anf_step(1, p.params, f, v, p.dx, p.dy, O.time_step(p.dx, p.dy), E)
+                arrests += a
+            assert np.abs(got - f).max() <= 1e-10
+            assert st[k]["arrests"] == arrests
+            assert st[k]["energy"] == pytest.approx(E, rel=1e-12)
+    finally:
+        S.ss_batch_destroy(b)
+
+
+def static_batch(count=12, seed=11):
+    """Problems with a static minimum in the box: one unit vortex at the centre, with
+    uneven grids, spacings and couplings.
+
+    The boxes are kept several core radii wide: in a narrow box at large lambda the
+    zero of the discretised force (Eq. 3 with the Eq. 2 stencils) lies O(h^4) above the
+    minimum of the discretised energy, so close to it every step raises E_h and is
+    arrested, and the flow creeps on from rest (the FP64 oracle, too, then needs
+    more than 60000 steps to reach 1e-6)."""
+    rng = I.SplitMix64(seed)
+    out = []
+    for _ in range(count):
+        nx = rng.choice((56, 77, 96))
+        ny = rng.choice((48, 64, 80))
+        dx = rng.choice((0.2, 0.25))
+        lam = rng.uniform(0.5, 1.5)
+        out.append(I.Problem(1, nx, ny, dx, dx, (lam, 1.0), [(0.0, 0.0, 1.0, 1.0, 0.0)]))
+    return out
+
+
+def test_batch_minimise_stops_each_problem_on_its_own(S):
+    """Compensated FP32 batch relaxed to dx dy max|G| < 1e-6: every problem stops on
+    its own step, keeps its exact winding N, and its FP64-evaluated energy agrees with
+    the oracle's evaluation of the same field."""
+    probs = static_batch()
+    b = S.ss_batch_create(S.SS_ABELIAN_HIGGS, 1, probs)
+    try:
+        rc, st = S.ss_batch_minimise(b, 1e-6, 60000)
+        assert rc == S.SS_OK, [s["grad_max"] for s in st]
+        steps = [s["steps"] for s in st]
+        assert len(set(steps)) > 1  # problems stopped at different steps
+        for k, p in enumerate(probs):
+            assert st[k]["converged"] and st[k]["grad_max"] < 1e-6
+            o = S.ss_batch_observables(b, k)
+            assert o["charge"] == pytest.approx(p.solitons[0][2], abs=1e-9)
+            got = np.empty((4, p.ny, p.nx), dtype=np.float32)
+            S.ss_batch_get_fields(b, k, got)
+            oo = O.observables(1, p.params, got.astype(np.float64), p.dx, p.dy)
+            assert o["energy"] == pytest.approx(oo["energy"], rel=1e-6)  # remainder not included in `got`
+            assert oo["grad_max"] < 2e-6
+    finally:
+        S.ss_batch_destroy(b)
+
+
+def test_batch_rejects_bad_items(S):
+    probs = mixed_batch(count=3)
+    probs[1].nx = 3
+    with pytest.raises(S.SolitonError) as ei:
+        S.ss_batch_create(S.SS_ABELIAN_HIGGS, 1, probs)
+    assert ei.value.code == S.SS_ERR_ARG and "item 1" in str(ei.value)
