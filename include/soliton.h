@@ -231,6 +231,11 @@ int ss_batch_minimise(ss_batch* batch, double tol, long long max_steps, ss_statu
 /* Copy the current field of problem `item` ([C][ny][nx], batch precision) out. */
 int ss_batch_get_fields(ss_batch* batch, int item, void* fields, int is_device);
 
+/* Replace the field of problem `item` (same layout and precision; halo included, the
+ * halo values become its Dirichlet data) and restart its flow from rest with a
+ * fresh step count, as ss_set_fields does for a single grid. */
+int ss_batch_set_fields(ss_batch* batch, int item, const void* fields, int is_device);
+
 /* Observables of problem `item`, as ss_observables. */
 int ss_batch_observables(ss_batch* batch, int item, ss_obs* out);
 

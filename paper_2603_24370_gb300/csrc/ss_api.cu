@@ -789,6 +789,20 @@ int ss_batch_get_fields(ss_batch* b, int item, void* fields, int is_device) {
   return copy_planes(b, item, fields, b->probs[item].phi[cur_of(b, item)], is_device);
 }
 
+int ss_batch_set_fields(ss_batch* b, int item, const void* fields, int is_device) {
+  if (!b) return fail(SS_ERR_ARG, "null batch");
+  if (item < 0 || item >= b->n()) return fail(SS_ERR_ARG, "item out of range");
+  if (!fields) return fail(SS_ERR_ARG, "fields is NULL");
+  const Problem& p = b->probs[item];
+  const size_t bytes = (size_t)b->C * p.plane * b->elem;
+  SS_CK(cudaMemcpyAsync(p.phi[0], fields, bytes, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                        b->stream));
+  SS_CK(cudaMemcpyAsync(p.phi[1], p.phi[0], bytes, cudaMemcpyDeviceToDevice, b->stream));
+  int rc = problem_new_fields(b, item);
+  if (rc != SS_OK) return rc;
+  return read_states(b);
+}
+
 int ss_batch_observables(ss_batch* b, int item, ss_obs* out) {
   if (!b) return fail(SS_ERR_ARG, "null batch");
   if (item < 0 || item >= b->n()) return fail(SS_ERR_ARG, "item out of range");

@@ -1,0 +1,473 @@
+// ss_conv.cu -- tensor-core 3x3 convolutions of the learned initialiser (tcgen05,
+// TMA, TMEM), BF16 operands with FP32 accumulation.
+//
+// Forward and input-gradient convolutions are implicit GEMMs: one CTA computes a
+// 128-pixel x Cout output tile, M = pixels, N = output channels, K = 9 taps x input
+// channels in groups of 8. For each K-group the TMA loads a box of 8 channels x 128
+// pixels straight from the NHWC activation at the tap's shifted coordinates; the
+// tensor-map bounds supply the zero padding, so no im2col copy is ever written. The
+// matching 8-wide slice of the weights ([Cout][9 Cin], K contiguous) is a second box.
+// Both land in the K-major no-swizzle layout that tcgen05.mma reads directly.
+//
+// The weight gradient contracts over pixels: M = output channels, N = input channels
+// of one tap, K = pixels. Its operands are channel-major copies (made by the
+// memory-bound kernels) so that K is contiguous; the tap's row shift is a TMA
+// coordinate and its column shift selects one of three pre-shifted copies.
+//
+// Warp roles (128 threads): warp 0 allocates TMEM and lane 0 drives the TMA
+// pipeline; warp 1 lane 0 issues the MMAs; afterwards all four warps drain the
+// accumulator (warp w owns TMEM lanes 32w..32w+31, one output row per thread).
+// Every mbarrier wait is bounded: on time-out the kernel records the failure in
+// `err`, waits (bounded) for its copies in flight, frees TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "ss_net_internal.h"
+#include "ss_umma.cuh"
+
+namespace ss {
+namespace {
+
+using namespace umma;
+
+constexpr int BM = 128;     // tile rows (pixels, or output channels for the weight gradient)
+constexpr int GPS = 8;      // K-groups of 8 values per pipeline stage (BK = 64)
+constexpr int STAGES = 3;
+constexpr uint64_t WAIT_NS = 2000000000ull;  // 2 s per wait
+
+__host__ __device__ constexpr int tmem_cols(int bn) { return bn <= 32 ? 32 : bn <= 64 ? 64 : bn <= 128 ? 128 : 256; }
+template <int BN>
+__host__ __device__ constexpr int stage_bytes() {
+  return GPS * (BM + BN) * 16;
+}
+// Dynamic shared memory: the stages, 1 KB for aligning the base, and a reserve so
+// that the descriptor-addressed operand reads of the last stage stay inside the
+// allocation even for the widest tiles.
+constexpr size_t SMEM_RESERVE = 48 * 1024;
+template <int BN>
+constexpr size_t conv_smem() {
+  return (size_t)STAGES * stage_bytes<BN>() + 1024 + SMEM_RESERVE;
+}
+
+struct ConvArgs {
+  int N, H, W, Cin, Cout;
+  int mode;
+  const float* bias;
+  void* out;
+  int out_cs, out_coff;
+  int* err;
+};
+
+struct WgradArgs {
+  int N, H, W, Cout, Cin;
+  int groups_per_cta;  // K-groups (8 pixels each) per CTA, even
+  int total_groups;
+  float* dw;
+  int* err;
+};
+
+__device__ __forceinline__ void record_fail(int* err, int code) { atomicCAS(err, 0, code); }
+
+// The producer's last wait: every TMA it issued has landed (bounded).
+__device__ __forceinline__ void drain_stages(uint64_t* full, int issued) {
+  for (int s = 0; s < STAGES && s < issued; ++s) {
+    const int last = s + STAGES * ((issued - 1 - s) / STAGES);
+    mbar_wait(&full[s], (uint32_t)((last / STAGES) & 1), WAIT_NS);
+  }
+}
+
+// ---------------------------------------------------------------- implicit GEMM conv
+template <int BN>
+__global__ void __launch_bounds__(128) k_conv3x3(const __grid_constant__ CUtensorMap mx,
+                                                 const __grid_constant__ CUtensorMap mw, const ConvArgs a) {
+  extern __shared__ unsigned char smraw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+  constexpr int A_BYTES = GPS * BM * 16;
+  constexpr int STAGE = stage_bytes<BN>();
+  constexpr int TCOLS = tmem_cols(BN);
+  __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], accum;
+  __shared__ uint32_t tmem_base;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  const int W = a.W, H = a.H;
+  const int Wt = W < BM ? W : BM;  // tile columns
+  const int rows = BM / Wt;        // tile rows
+  const int tpr = W / Wt;
+  const int tpi = (H / rows) * tpr;
+  const int n = blockIdx.x / tpi, r = blockIdx.x % tpi;
+  const int y0 = (r / tpr) * rows, x0 = (r % tpr) * Wt;
+  const int cg = a.Cin >> 3;
+  const int G = 9 * cg;
+  const int nkb = (G + GPS - 1) / GPS;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(&accum, 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(&tmem_base, TCOLS);
+    tmem_relinquish();
+  }
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = tmem_base;
+
+  if (warp == 0 && lane == 0) {
+    int issued = 0;
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % STAGES;
+      if (!mbar_wait(&empty[s], (uint32_t)(((kb / STAGES) & 1) ^ 1), WAIT_NS)) {
+        record_fail(a.err, 1);
+        break;
+      }
+      unsigned char* sa = smem + s * STAGE;
+      unsigned char* sb = sa + A_BYTES;
+      const int g0 = kb * GPS, ng = min(GPS, G - g0);
+      mbar_arrive_expect_tx(&full[s], (uint32_t)(ng * (BM + BN) * 16));
+      for (int j = 0; j < ng; ++j) {
+        const int gg = g0 + j, tap = gg / cg, c0 = (gg - tap * cg) * 8;
+        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+        tma_load_4d(sa + j * (BM * 16), &mx, &full[s], c0, x0 + dx, y0 + dy, n);
+        tma_load_2d(sb + j * (BN * 16), &mw, &full[s], gg * 8, 0);
+      }
+      issued = kb + 1;
+    }
+    drain_stages(full, issued);
+  } else if (warp == 1 && lane == 0) {
+    constexpr uint32_t idesc = idesc_bf16(BM, BN);
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % STAGES;
+      if (!mbar_wait(&full[s], (uint32_t)((kb / STAGES) & 1), WAIT_NS)) {
+        record_fail(a.err, 2);
+        break;
+      }
+      fence_after_sync();
+      const uint32_t sa = smem_u32(smem + s * STAGE), sb = sa + A_BYTES;
+      const int ng = min(GPS, G - kb * GPS);
+      for (int j = 0; j < ng; j += 2) {
+        const uint64_t ad = sdesc(sa + j * (BM * 16), BM * 16, 128);
+        const uint64_t bd = sdesc(sb + j * (BN * 16), BN * 16, 128);
+        mma_bf16(tmem, ad, bd, idesc, (kb > 0 || j > 0) ? 1u : 0u);
+      }
+      mma_commit(&empty[s]);
+    }
+    mma_commit(&accum);
+  }
+  __syncwarp();
+
+  // ---- epilogue: one output pixel per thread
+  bool ok = mbar_wait(&accum, 0, WAIT_NS);
+  ok = __all_sync(0xffffffffu, ok);
+  fence_after_sync();
+  if (!ok) {
+    if (lane == 0) record_fail(a.err, 3);
+  } else {
+    const int m = warp * 32 + lane;
+    const int yy = y0 + m / Wt, xx = x0 + m % Wt;
+    const size_t pix = ((size_t)n * H + yy) * W + xx;
+    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+    for (int c = 0; c < BN; c += 16) {
+      float v[16];
+      tmem_ld16(trow + (uint32_t)c, v);
+      if (c >= a.Cout) continue;
+      if (a.mode == CONV_BF16_BIAS_RELU) {
+        __nv_bfloat16* o = static_cast<__nv_bfloat16*>(a.out) + pix * a.out_cs + a.out_coff + c;
+        uint32_t w[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const float lo = fmaxf(v[2 * i] + __ldg(a.bias + c + 2 * i), 0.f);
+          const float hi = fmaxf(v[2 * i + 1] + __ldg(a.bias + c + 2 * i + 1), 0.f);
+          __nv_bfloat162 b2 = __floats2bfloat162_rn(lo, hi);
+          w[i] = *reinterpret_cast<uint32_t*>(&b2);
+        }
+        uint4* o4 = reinterpret_cast<uint4*>(o);
+        o4[0] = make_uint4(w[0], w[1], w[2], w[3]);
+        o4[1] = make_uint4(w[4], w[5], w[6], w[7]);
+      } else {
+        float* o = static_cast<float*>(a.out) + pix * a.out_cs + a.out_coff + c;
+        const bool b = a.mode == CONV_F32_BIAS;
+#pragma unroll
+        for (int i = 0; i < 16; i += 4) {
+          float4 q;
+          q.x = v[i] + (b ? __ldg(a.bias + c + i) : 0.f);
+          q.y = v[i + 1] + (b ? __ldg(a.bias + c + i + 1) : 0.f);
+          q.z = v[i + 2] + (b ? __ldg(a.bias + c + i + 2) : 0.f);
+          q.w = v[i + 3] + (b ? __ldg(a.bias + c + i + 3) : 0.f);
+          *reinterpret_cast<float4*>(o + i) = q;
+        }
+      }
+    }
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    fence_after_sync();
+    tmem_dealloc(tmem, TCOLS);
+  }
+}
+
+// ---------------------------------------------------------------- weight gradient
+template <int BN>
+__global__ void __launch_bounds__(128) k_wgrad3x3(const __grid_constant__ CUtensorMap mdy,
+                                                  const __grid_constant__ CUtensorMap mx0,
+                                                  const __grid_constant__ CUtensorMap mx1,
+                                                  const __grid_constant__ CUtensorMap mx2, const WgradArgs a) {
+  extern __shared__ unsigned char smraw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+  constexpr int A_BYTES = GPS * BM * 16;
+  constexpr int STAGE = stage_bytes<BN>();
+  constexpr int TCOLS = tmem_cols(BN);
+  __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], accum;
+  __shared__ uint32_t tmem_base;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  const int tap = blockIdx.y, dy = tap / 3 - 1, dx = tap % 3 - 1;
+  const CUtensorMap* mx = dx < 0 ? &mx0 : (dx == 0 ? &mx1 : &mx2);
+  const int q0 = blockIdx.x * a.groups_per_cta;
+  const int q1 = min(q0 + a.groups_per_cta, a.total_groups);
+  const int G = q1 - q0;
+  const int nkb = G > 0 ? (G + GPS - 1) / GPS : 0;
+  const int HW = a.H * a.W;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(&accum, 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(&tmem_base, TCOLS);
+    tmem_relinquish();
+  }
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = tmem_base;
+
+  if (warp == 0 && lane == 0) {
+    int issued = 0;
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % STAGES;
+      if (!mbar_wait(&empty[s], (uint32_t)(((kb / STAGES) & 1) ^ 1), WAIT_NS)) {
+        record_fail(a.err, 11);
+        break;
+      }
+      unsigned char* sa = smem + s * STAGE;
+      unsigned char* sb = sa + A_BYTES;
+      const int g0 = q0 + kb * GPS, ng = min(GPS, q1 - g0);
+      mbar_arrive_expect_tx(&full[s], (uint32_t)(ng * (BM + BN) * 16));
+      for (int j = 0; j < ng; ++j) {
+        const int p = (g0 + j) * 8;
+        const int nn = p / HW, rem = p - nn * HW;
+        const int y = rem / a.W, x = rem - y * a.W;
+        tma_load_4d(sa + j * (BM * 16), &mdy, &full[s], x, y, nn, 0);
+        tma_load_4d(sb + j * (BN * 16), mx, &full[s], x, y + dy, nn, 0);
+      }
+      issued = kb + 1;
+    }
+    drain_stages(full, issued);
+  } else if (warp == 1 && lane == 0) {
+    constexpr uint32_t idesc = idesc_bf16(BM, BN);
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % STAGES;
+      if (!mbar_wait(&full[s], (uint32_t)((kb / STAGES) & 1), WAIT_NS)) {
+        record_fail(a.err, 12);
+        break;
+      }
+      fence_after_sync();
+      const uint32_t sa = smem_u32(smem + s * STAGE), sb = sa + A_BYTES;
+      const int ng = min(GPS, q1 - (q0 + kb * GPS));
+      for (int j = 0; j < ng; j += 2) {
+        const uint64_t ad = sdesc(sa + j * (BM * 16), BM * 16, 128);
+        const uint64_t bd = sdesc(sb + j * (BN * 16), BN * 16, 128);
+        mma_bf16(tmem, ad, bd, idesc, (kb > 0 || j > 0) ? 1u : 0u);
+      }
+      mma_commit(&empty[s]);
+    }
+    mma_commit(&accum);
+  }
+  __syncwarp();
+
+  bool ok = nkb > 0 ? mbar_wait(&accum, 0, WAIT_NS) : false;
+  ok = __all_sync(0xffffffffu, ok);
+  fence_after_sync();
+  if (!ok) {
+    if (lane == 0 && nkb > 0) record_fail(a.err, 13);
+  } else {
+    const int co = warp * 32 + lane;
+    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+    for (int c = 0; c < BN; c += 16) {
+      float v[16];
+      tmem_ld16(trow + (uint32_t)c, v);
+      if (co < a.Cout) {
+        float* d = a.dw + ((size_t)co * 9 + tap) * a.Cin + c;
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+          if (c + i < a.Cin) atomicAdd(d + i, v[i]);
+      }
+    }
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    fence_after_sync();
+    tmem_dealloc(tmem, TCOLS);
+  }
+}
+
+// ---------------------------------------------------------------- tensor maps
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// BF16 tensor map of rank r: dims[0] innermost (elements), strides in bytes for
+// dims 1..r-1, box per dim; out-of-bounds elements read as zero.
+cudaError_t make_map(CUtensorMap* m, const void* base, int r, const cuuint64_t* dims, const cuuint64_t* strides,
+                     const cuuint32_t* box) {
+  auto fn = encode_fn();
+  if (!fn) return cudaErrorNotSupported;
+  cuuint32_t es[5] = {1, 1, 1, 1, 1};
+  const CUresult rc = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)r, const_cast<void*>(base), dims, strides,
+                         box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return rc == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+template <int BN>
+cudaError_t conv_launch(const CUtensorMap& mx, const CUtensorMap& mw, const ConvArgs& a, int tiles, cudaStream_t s) {
+  static bool attr = false;  // set once per process (per instantiation)
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_conv3x3<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_smem<BN>());
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_conv3x3<BN><<<tiles, 128, conv_smem<BN>(), s>>>(mx, mw, a);
+  return cudaGetLastError();
+}
+
+template <int BN>
+cudaError_t wgrad_launch(const CUtensorMap& mdy, const CUtensorMap* mx, const WgradArgs& a, int splits, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e =
+        cudaFuncSetAttribute(k_wgrad3x3<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_smem<BN>());
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_wgrad3x3<BN><<<dim3(splits, 9), 128, conv_smem<BN>(), s>>>(mdy, mx[0], mx[1], mx[2], a);
+  return cudaGetLastError();
+}
+
+std::mutex g_attr_mu;
+
+}  // namespace
+
+cudaError_t conv3x3_tc(const Act& x, const void* w, int Cout, int mode, const float* bias, const Act& out, int* err,
+                       cudaStream_t s) {
+  const int W = x.W, H = x.H;
+  if (x.C % 16 || x.off % 8 || x.cs % 8 || (W < 128 ? (128 % W || W % 8) : W % 128) || (H * W) % 128 ||
+      out.N != x.N || out.H != H || out.W != W || out.off % 8 || out.cs % 8 || out.C != Cout)
+    return cudaErrorInvalidValue;
+  if ((reinterpret_cast<uintptr_t>(x.p) & 15) || (reinterpret_cast<uintptr_t>(w) & 15) ||
+      (reinterpret_cast<uintptr_t>(out.p) & 15))
+    return cudaErrorInvalidValue;
+  // activation view: dims {C, W, H, N}; the base is moved to the view's first channel
+  CUtensorMap mx, mw;
+  const char* xb = static_cast<const char*>(x.p) + (size_t)x.off * 2;
+  const cuuint64_t xd[4] = {(cuuint64_t)x.C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)x.N};
+  const cuuint64_t xs[3] = {(cuuint64_t)x.cs * 2, (cuuint64_t)x.cs * 2 * W, (cuuint64_t)x.cs * 2 * W * H};
+  const int Wt = W < 128 ? W : 128;
+  const cuuint32_t xbox[4] = {8, (cuuint32_t)Wt, (cuuint32_t)(128 / Wt), 1};
+  cudaError_t e = make_map(&mx, xb, 4, xd, xs, xbox);
+  if (e != cudaSuccess) return e;
+  const int K = 9 * x.C;
+  const cuuint64_t wd[2] = {(cuuint64_t)K, (cuuint64_t)Cout};
+  const cuuint64_t ws[1] = {(cuuint64_t)K * 2};
+  ConvArgs a{x.N, H, W, x.C, Cout, mode, bias, static_cast<char*>(out.p), out.cs, out.off, err};
+  const int tiles = x.N * H * W / 128;
+  std::lock_guard<std::mutex> lock(g_attr_mu);
+#define SS_CONV_CASE(BNV)                                   \
+  case BNV: {                                               \
+    const cuuint32_t wbox[2] = {8, (cuuint32_t)BNV};        \
+    e = make_map(&mw, w, 2, wd, ws, wbox);                  \
+    if (e != cudaSuccess) return e;                         \
+    return conv_launch<BNV>(mx, mw, a, tiles, s);           \
+  }
+  switch (Cout) {
+    SS_CONV_CASE(16)
+    SS_CONV_CASE(32)
+    SS_CONV_CASE(48)
+    SS_CONV_CASE(80)
+    SS_CONV_CASE(96)
+    SS_CONV_CASE(144)
+    default:
+      return cudaErrorInvalidValue;
+  }
+#undef SS_CONV_CASE
+}
+
+cudaError_t wgrad3x3_tc(const void* dyT, const void* xT, int N, int H, int W, int Cout, int Cin, float* dw, int* err,
+                        cudaStream_t s) {
+  const long long P = (long long)N * H * W;
+  if (W % 8 || P % 16 || Cout < 1 || Cout > 128 || P >= (1LL << 31)) return cudaErrorInvalidValue;
+  if ((reinterpret_cast<uintptr_t>(dyT) & 15) || (reinterpret_cast<uintptr_t>(xT) & 15)) return cudaErrorInvalidValue;
+  CUtensorMap mdy, mx[3];
+  const cuuint64_t dd[4] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)N, (cuuint64_t)Cout};
+  const cuuint64_t st[3] = {(cuuint64_t)W * 2, (cuuint64_t)W * H * 2, (cuuint64_t)P * 2};
+  const cuuint32_t dbox[4] = {8, 1, 1, 128};
+  cudaError_t e = make_map(&mdy, dyT, 4, dd, st, dbox);
+  if (e != cudaSuccess) return e;
+  const cuuint64_t xd[4] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)N, (cuuint64_t)Cin};
+  // K-groups split over CTAs: about 4 waves of 9-tap grids over 152 SMs, even counts
+  const int total = (int)(P / 8);
+  int splits = (152 * 4 + 8) / 9;
+  int gpc = (total + splits - 1) / splits;
+  gpc = (gpc + 1) & ~1;
+  if (gpc < 16) gpc = 16;
+  splits = (total + gpc - 1) / gpc;
+  WgradArgs a{N, H, W, Cout, Cin, gpc, total, dw, err};
+  std::lock_guard<std::mutex> lock(g_attr_mu);
+#define SS_WG_CASE(BNV)                                                                      \
+  case BNV: {                                                                                \
+    const cuuint32_t xbox[4] = {8, 1, 1, (cuuint32_t)BNV};                                   \
+    for (int d = 0; d < 3; ++d) {                                                            \
+      e = make_map(&mx[d], static_cast<const char*>(xT) + (size_t)d * Cin * P * 2, 4, xd, st, xbox); \
+      if (e != cudaSuccess) return e;                                                        \
+    }                                                                                        \
+    return wgrad_launch<BNV>(mdy, mx, a, splits, s);                                         \
+  }
+  switch (Cin) {
+    SS_WG_CASE(16)
+    SS_WG_CASE(32)
+    SS_WG_CASE(48)
+    SS_WG_CASE(80)
+    SS_WG_CASE(96)
+    SS_WG_CASE(144)
+    default:
+      return cudaErrorInvalidValue;
+  }
+#undef SS_WG_CASE
+}
+
+}  // namespace ss

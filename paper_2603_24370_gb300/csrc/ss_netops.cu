@@ -1,0 +1,229 @@
+// ss_netops.cu -- the memory-bound layers of the learned initialiser: 2x2 average
+// pooling, nearest-neighbour upsampling, ReLU gradients, bias gradients, the
+// channel-major (and column-shifted) copies the weight-gradient contraction reads,
+// and gradient routing through the decoder's concatenations. Each kernel is a
+// grid-stride loop over elements with 16-byte accesses along channels where the
+// layout allows it.
+#include <cuda_bf16.h>
+
+#include "ss_net_internal.h"
+
+namespace ss {
+namespace {
+
+int grid_for(size_t n, int threads = 256) {
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const size_t b = (n + threads - 1) / threads;
+  const size_t cap = (size_t)nsm * 8;
+  return (int)(b < cap ? (b > 0 ? b : 1) : cap);
+}
+
+__device__ __forceinline__ const __nv_bfloat16* act_ptr(const Act& a, size_t pix) {
+  return static_cast<const __nv_bfloat16*>(a.p) + pix * a.cs + a.off;
+}
+__device__ __forceinline__ __nv_bfloat16* act_wptr(const Act& a, size_t pix) {
+  return static_cast<__nv_bfloat16*>(a.p) + pix * a.cs + a.off;
+}
+
+// xT[d][c][pix] = x[pix shifted by dx = d - 1 along x][c]; one thread per (pix, 8 channels)
+__global__ void k_shifted_transpose(const Act x, __nv_bfloat16* __restrict__ xT) {
+  const size_t P = (size_t)x.N * x.H * x.W;
+  const int cg = x.C / 8;
+  const size_t total = P * cg;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t pix = i / cg;
+    const int c0 = (int)(i - pix * cg) * 8;
+    const int xx = (int)(pix % x.W);
+    const uint4 v = *reinterpret_cast<const uint4*>(act_ptr(x, pix) + c0);
+    const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&v);
+    // x at column xx feeds copy d at column xx - (d - 1)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const int xd = xx - (d - 1);
+      if (xd < 0 || xd >= x.W) continue;
+      const size_t q = pix - xx + xd;
+      __nv_bfloat16* o = xT + (size_t)d * x.C * P;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) o[(size_t)(c0 + k) * P + q] = e[k];
+    }
+    // the column that no source reaches in each shifted copy is zero
+    if (xx == 0) {  // copy d = 2 (dx = +1) at column W - 1
+      __nv_bfloat16* o = xT + (size_t)2 * x.C * P;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) o[(size_t)(c0 + k) * P + pix + x.W - 1] = __float2bfloat16(0.f);
+    }
+    if (xx == x.W - 1) {  // copy d = 0 (dx = -1) at column 0
+#pragma unroll
+      for (int k = 0; k < 8; ++k) xT[(size_t)(c0 + k) * P + pix - (x.W - 1)] = __float2bfloat16(0.f);
+    }
+  }
+}
+
+// dy_bf16 = bf16(dy * mask), dyT = the same, channel-major; dbias += sum over pixels.
+// One block handles a run of pixels for all channels; per-channel partial sums in
+// shared memory, one atomic per channel per block.
+__global__ void k_relu_grad(const float* __restrict__ dy, const Act yact, int has_mask, size_t P, int C,
+                            __nv_bfloat16* __restrict__ dyb, __nv_bfloat16* __restrict__ dyT, float* __restrict__ dbias) {
+  extern __shared__ float sb[];
+  for (int c = threadIdx.x; c < C; c += blockDim.x) sb[c] = 0.f;
+  __syncthreads();
+  const size_t total = P * C;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t pix = i / C;
+    const int c = (int)(i - pix * C);
+    float g = dy[i];
+    if (has_mask && !(__bfloat162float(act_ptr(yact, pix)[c]) > 0.f)) g = 0.f;
+    const __nv_bfloat16 b = __float2bfloat16(g);
+    dyb[i] = b;
+    dyT[(size_t)c * P + pix] = b;
+    atomicAdd(&sb[c], g);
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < C; c += blockDim.x) atomicAdd(&dbias[c], sb[c]);
+}
+
+__global__ void k_avgpool2(const Act x, const Act out) {
+  const size_t Po = (size_t)out.N * out.H * out.W;
+  const int cg = out.C / 8;
+  const size_t total = Po * cg;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t po = i / cg;
+    const int c0 = (int)(i - po * cg) * 8;
+    const int xo = (int)(po % out.W);
+    const size_t t = po / out.W;
+    const int yo = (int)(t % out.H);
+    const int n = (int)(t / out.H);
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const size_t pi = ((size_t)n * x.H + 2 * yo + (q >> 1)) * x.W + 2 * xo + (q & 1);
+      const uint4 v = *reinterpret_cast<const uint4*>(act_ptr(x, pi) + c0);
+      const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&v);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) acc[k] += __bfloat162float(e[k]);
+    }
+    uint4 o;
+    __nv_bfloat16* oe = reinterpret_cast<__nv_bfloat16*>(&o);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) oe[k] = __float2bfloat16(0.25f * acc[k]);
+    *reinterpret_cast<uint4*>(act_wptr(out, po) + c0) = o;
+  }
+}
+
+__global__ void k_avgpool2_backward(const float* __restrict__ dout, int N, int Ho, int Wo, int C,
+                                    float* __restrict__ dx) {
+  const size_t total = (size_t)N * (2 * Ho) * (2 * Wo) * C;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t pix = i / C;
+    const int c = (int)(i - pix * C);
+    const int xx = (int)(pix % (2 * Wo));
+    const size_t t = pix / (2 * Wo);
+    const int yy = (int)(t % (2 * Ho));
+    const int n = (int)(t / (2 * Ho));
+    dx[i] += 0.25f * dout[(((size_t)n * Ho + yy / 2) * Wo + xx / 2) * C + c];
+  }
+}
+
+__global__ void k_upsample2(const Act x, const Act out) {
+  const size_t Po = (size_t)out.N * out.H * out.W;
+  const int cg = out.C / 8;
+  const size_t total = Po * cg;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t po = i / cg;
+    const int c0 = (int)(i - po * cg) * 8;
+    const int xo = (int)(po % out.W);
+    const size_t t = po / out.W;
+    const int yo = (int)(t % out.H);
+    const int n = (int)(t / out.H);
+    const size_t pi = ((size_t)n * x.H + yo / 2) * x.W + xo / 2;
+    *reinterpret_cast<uint4*>(act_wptr(out, po) + c0) = *reinterpret_cast<const uint4*>(act_ptr(x, pi) + c0);
+  }
+}
+
+__global__ void k_upsample2_backward(const float* __restrict__ dup, int cs, int off, int N, int H, int W, int C,
+                                     float* __restrict__ dx) {
+  const size_t total = (size_t)N * H * W * C;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t pix = i / C;
+    const int c = (int)(i - pix * C);
+    const int xx = (int)(pix % W);
+    const size_t t = pix / W;
+    const int yy = (int)(t % H);
+    const int n = (int)(t / H);
+    float s = 0.f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const size_t pu = ((size_t)n * (2 * H) + 2 * yy + (q >> 1)) * (2 * W) + 2 * xx + (q & 1);
+      s += dup[pu * cs + off + c];
+    }
+    dx[i] = s;
+  }
+}
+
+__global__ void k_add_slice(const float* __restrict__ src, int cs, int off, size_t P, int C, float* __restrict__ dst) {
+  const size_t total = P * C;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t pix = i / C;
+    const int c = (int)(i - pix * C);
+    dst[i] += src[pix * cs + off + c];
+  }
+}
+
+bool act_ok(const Act& a) { return a.p && a.C % 8 == 0 && a.cs % 8 == 0 && a.off % 8 == 0 && a.off + a.C <= a.cs; }
+
+}  // namespace
+
+cudaError_t shifted_transpose(const Act& x, void* xT, cudaStream_t s) {
+  if (!act_ok(x)) return cudaErrorInvalidValue;
+  const size_t n = (size_t)x.N * x.H * x.W * (x.C / 8);
+  k_shifted_transpose<<<grid_for(n), 256, 0, s>>>(x, static_cast<__nv_bfloat16*>(xT));
+  return cudaGetLastError();
+}
+
+cudaError_t relu_grad(const float* dy, const Act* y_act, int N, int H, int W, int C, void* dy_bf16, void* dyT,
+                      float* dbias, cudaStream_t s) {
+  const size_t P = (size_t)N * H * W;
+  Act y{};
+  if (y_act) y = *y_act;
+  k_relu_grad<<<grid_for(P * C), 256, C * sizeof(float), s>>>(dy, y, y_act != nullptr, P, C,
+                                                              static_cast<__nv_bfloat16*>(dy_bf16),
+                                                              static_cast<__nv_bfloat16*>(dyT), dbias);
+  return cudaGetLastError();
+}
+
+cudaError_t avgpool2(const Act& x, const Act& out, cudaStream_t s) {
+  if (!act_ok(x) || !act_ok(out) || out.C != x.C || out.H * 2 != x.H || out.W * 2 != x.W) return cudaErrorInvalidValue;
+  const size_t n = (size_t)out.N * out.H * out.W * (out.C / 8);
+  k_avgpool2<<<grid_for(n), 256, 0, s>>>(x, out);
+  return cudaGetLastError();
+}
+
+cudaError_t avgpool2_backward(const float* dout, int N, int Ho, int Wo, int C, float* dx, cudaStream_t s) {
+  const size_t n = (size_t)N * 4 * Ho * Wo * C;
+  k_avgpool2_backward<<<grid_for(n), 256, 0, s>>>(dout, N, Ho, Wo, C, dx);
+  return cudaGetLastError();
+}
+
+cudaError_t upsample2(const Act& x, const Act& out, cudaStream_t s) {
+  if (!act_ok(x) || !act_ok(out) || out.C != x.C || out.H != 2 * x.H || out.W != 2 * x.W) return cudaErrorInvalidValue;
+  const size_t n = (size_t)out.N * out.H * out.W * (out.C / 8);
+  k_upsample2<<<grid_for(n), 256, 0, s>>>(x, out);
+  return cudaGetLastError();
+}
+
+cudaError_t upsample2_backward(const float* dup, int cs, int off, int N, int H, int W, int C, float* dx,
+                               cudaStream_t s) {
+  const size_t n = (size_t)N * H * W * C;
+  k_upsample2_backward<<<grid_for(n), 256, 0, s>>>(dup, cs, off, N, H, W, C, dx);
+  return cudaGetLastError();
+}
+
+cudaError_t add_slice(const float* src, int cs, int off, int N, int H, int W, int C, float* dst, cudaStream_t s) {
+  const size_t P = (size_t)N * H * W;
+  k_add_slice<<<grid_for(P * C), 256, 0, s>>>(src, cs, off, P, C, dst);
+  return cudaGetLastError();
+}
+
+}  // namespace ss

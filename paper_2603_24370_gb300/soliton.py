@@ -114,9 +114,26 @@ def load_library(path: str | None = None):
             "ss_batch_step": ([vp, i, ctypes.POINTER(ss_status)], i),
             "ss_batch_minimise": ([vp, d, ll, ctypes.POINTER(ss_status)], i),
             "ss_batch_get_fields": ([vp, i, vp, i], i),
+            "ss_batch_set_fields": ([vp, i, vp, i], i),
             "ss_batch_observables": ([vp, i, ctypes.POINTER(ss_obs)], i),
             "ss_batch_destroy": ([vp], i),
             "ss_destroy": ([vp], i),
+            # learned initialiser (soliton_net.h)
+            "ss_net_create": ([ctypes.POINTER(vp), i, i, i, ctypes.c_ulonglong, vp], i),
+            "ss_net_destroy": ([vp], i),
+            "ss_net_last_error": ([], ctypes.c_char_p),
+            "ss_net_num_params": ([vp], ll),
+            "ss_net_get_params": ([vp, vp], i),
+            "ss_net_set_params": ([vp, vp], i),
+            "ss_net_save": ([vp, ctypes.c_char_p], i),
+            "ss_net_load": ([vp, ctypes.c_char_p], i),
+            "ss_net_pack": ([vp, vp, pd, i, vp], i),
+            "ss_net_forward": ([vp, vp, i, vp], i),
+            "ss_net_gradients": ([vp, vp, vp, i, vp, pd], i),
+            "ss_net_train_step": ([vp, vp, vp, i, ctypes.c_float, pd], i),
+            "ss_net_predict": ([vp, vp, pd, i, vp], i),
+            "ss_conv3x3": ([vp, i, i, i, i, vp, i, vp, i, vp, vp], i),
+            "ss_conv3x3_wgrad": ([vp, vp, i, i, i, i, i, vp, vp], i),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -312,6 +329,11 @@ def ss_batch_get_fields(b, item: int, out) -> None:
     _check(load_library().ss_batch_get_fields(b, int(item), p, dev))
 
 
+def ss_batch_set_fields(b, item: int, fields) -> None:
+    p, dev = _ptr(fields, np.float32 if _dtype_of(fields) == np.float32 else np.float64)
+    _check(load_library().ss_batch_set_fields(b, item, p, dev))
+
+
 def ss_batch_observables(b, item: int) -> dict:
     o = ss_obs()
     _check(load_library().ss_batch_observables(b, int(item), ctypes.byref(o)))
@@ -403,3 +425,110 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------- learned initialiser
+def _dev(t):
+    """Device pointer of a contiguous CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    if not hasattr(t, "data_ptr") or not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _net_check(rc: int):
+    if rc != SS_OK:
+        raise SolitonError(rc, load_library().ss_net_last_error().decode(errors="replace"))
+
+
+def _couplings(c, batch):
+    if c is None:
+        return None
+    arr = np.ascontiguousarray(np.asarray(c, dtype=np.float64).reshape(-1))
+    if arr.size < batch:
+        raise ValueError("one coupling value per problem is required")
+    return arr, arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def ss_net_create(theory: int, size: int, max_batch: int, seed: int = 0, stream=None):
+    h = ctypes.c_void_p()
+    _net_check(load_library().ss_net_create(ctypes.byref(h), theory, size, max_batch, seed, _stream_ptr(stream)))
+    return h
+
+
+def ss_net_destroy(net) -> None:
+    if net:
+        load_library().ss_net_destroy(net)
+
+
+def ss_net_num_params(net) -> int:
+    return int(load_library().ss_net_num_params(net))
+
+
+def ss_net_get_params(net) -> np.ndarray:
+    out = np.empty(ss_net_num_params(net), dtype=np.float32)
+    _net_check(load_library().ss_net_get_params(net, ctypes.c_void_p(out.ctypes.data)))
+    return out
+
+
+def ss_net_set_params(net, theta) -> None:
+    a = np.ascontiguousarray(theta, dtype=np.float32)
+    if a.size != ss_net_num_params(net):
+        raise ValueError("wrong number of parameters")
+    _net_check(load_library().ss_net_set_params(net, ctypes.c_void_p(a.ctypes.data)))
+
+
+def ss_net_save(net, path: str) -> None:
+    _net_check(load_library().ss_net_save(net, os.fsencode(path)))
+
+
+def ss_net_load(net, path: str) -> None:
+    _net_check(load_library().ss_net_load(net, os.fsencode(path)))
+
+
+def ss_net_pack(net, fields, couplings, batch: int, input_nhwc) -> None:
+    keep = _couplings(couplings, batch)
+    _net_check(load_library().ss_net_pack(net, _dev(fields), keep[1] if keep else None, batch, _dev(input_nhwc)))
+
+
+def ss_net_forward(net, input_nhwc, batch: int, out=None) -> None:
+    _net_check(load_library().ss_net_forward(net, _dev(input_nhwc), batch, _dev(out)))
+
+
+def ss_net_gradients(net, input_nhwc, target, batch: int, grad_out=None) -> float:
+    loss = ctypes.c_double()
+    _net_check(load_library().ss_net_gradients(net, _dev(input_nhwc), _dev(target), batch, _dev(grad_out),
+                                               ctypes.byref(loss)))
+    return loss.value
+
+
+def ss_net_train_step(net, input_nhwc, target, batch: int, lr: float) -> float:
+    loss = ctypes.c_double()
+    _net_check(load_library().ss_net_train_step(net, _dev(input_nhwc), _dev(target), batch, lr, ctypes.byref(loss)))
+    return loss.value
+
+
+def ss_net_predict(net, ansatz, couplings, batch: int, init) -> None:
+    keep = _couplings(couplings, batch)
+    _net_check(load_library().ss_net_predict(net, _dev(ansatz), keep[1] if keep else None, batch, _dev(init)))
+
+
+def ss_conv3x3(x, w, bias, mode: int, out, stream=None) -> None:
+    N, H, W, Cin = x.shape
+    Cout = w.shape[0]
+    _net_check(load_library().ss_conv3x3(_dev(x), N, H, W, Cin, _dev(w), Cout, _dev(bias), mode, _dev(out),
+                                         _stream_ptr(stream)))
+
+
+def ss_conv3x3_wgrad(dy, x, dw, stream=None) -> None:
+    N, H, W, Cin = x.shape
+    Cout = dy.shape[3]
+    _net_check(load_library().ss_conv3x3_wgrad(_dev(dy), _dev(x), N, H, W, Cout, Cin, _dev(dw),
+                                               _stream_ptr(stream)))

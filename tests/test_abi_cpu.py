@@ -2,6 +2,7 @@
 loads, exports every function include/soliton.h declares, and rejects bad
 arguments before touching the device."""
 import ctypes
+import glob
 import os
 import re
 import shutil
@@ -9,13 +10,15 @@ import shutil
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "soliton.h")
+HEADERS = sorted(glob.glob(os.path.join(ROOT, "include", "*.h")))
 
 
 def declared_functions():
-    text = open(HEADER).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(ss_\w+)\s*\(", text, flags=re.M)))
+    names = set()
+    for h in HEADERS:
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names |= set(re.findall(r"^\s*(?:const\s+)?\w+(?:\s+\w+)?\s*\*?\s*(ss_\w+)\s*\(", text, flags=re.M))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")
@@ -31,7 +34,8 @@ def lib():
 def test_header_declares_the_boundary():
     names = declared_functions()
     for required in ("ss_create_grid", "ss_set_theory", "ss_init_ansatz", "ss_step", "ss_minimise",
-                     "ss_observables", "ss_destroy", "ss_last_error"):
+                     "ss_observables", "ss_destroy", "ss_last_error", "ss_batch_create", "ss_batch_minimise",
+                     "ss_net_create", "ss_net_train_step", "ss_net_predict", "ss_net_save", "ss_net_load"):
         assert required in names
 
 

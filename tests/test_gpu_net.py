@@ -1,0 +1,219 @@
+"""The learned initialiser on the GPU against its CPU oracle (oracle/unet.py).
+
+Convolutions: every tile width the network uses and every output width the kernels
+are instantiated for, forward (all three epilogues) and weight gradient. The oracle
+sums the same BF16 operands in float64; the GPU accumulates in FP32, so each output
+may differ by the FP32 accumulation error, bounded here by 1e-5 times the sum of the
+absolute values of its terms (K <= 1296 terms per output for the convolutions, FP32
+unit roundoff 6e-8), and, where the output is stored in BF16, by one BF16 rounding
+(2^-8 relative) on top.
+
+Network: loss and every layer's gradients at S = 128 against the oracle with the
+same BF16 rounding points. Differences come from FP32 versus float64 accumulation
+flipping a BF16 rounding here and there; per layer the relative L2 difference of the
+gradients is held to 2e-2 and the loss to 1e-3.
+"""
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+from oracle import unet as U
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2603_24370_gb300 import build
+    from paper_2603_24370_gb300 import soliton as S
+    build.build()
+    S.load_library()
+    return S
+
+
+def bf16_tensor(a):
+    """Exact BF16 device tensor of the BF16-rounded values of a."""
+    return torch.tensor(U.round_bf16(a), dtype=torch.float32).to(torch.bfloat16).cuda().contiguous()
+
+
+CONV_CASES = [  # (N, H, W, Cin, Cout)
+    (2, 16, 16, 16, 16),
+    (1, 16, 32, 16, 32),
+    (2, 8, 64, 32, 48),
+    (1, 4, 128, 48, 80),
+    (1, 2, 256, 16, 96),
+    (2, 16, 16, 144, 48),
+    (1, 8, 32, 80, 144),
+]
+
+
+@pytest.mark.parametrize("case", CONV_CASES)
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_conv_forward_matches_oracle(S, case, mode):
+    N, H, W, Cin, Cout = case
+    rng = np.random.default_rng(hash((case, mode)) % 2**32)
+    x = U.round_bf16(rng.normal(size=(N, H, W, Cin)))
+    w = U.round_bf16(rng.normal(size=(Cout, 9, Cin)) / np.sqrt(9 * Cin))
+    b = rng.normal(size=Cout).astype(np.float32).astype(np.float64)
+    ref = U.conv3x3(x, w) + (b if mode != 2 else 0.0)
+    mag = U.conv3x3(np.abs(x), np.abs(w)) + np.abs(b if mode != 2 else 0.0)
+    xd, wd = bf16_tensor(x), bf16_tensor(w.reshape(Cout, 9 * Cin))
+    bd = torch.tensor(b, dtype=torch.float32, device="cuda")
+    out = torch.zeros((N, H, W, Cout), dtype=torch.bfloat16 if mode == 0 else torch.float32, device="cuda")
+    S.ss_conv3x3(xd, wd, bd, mode, out)
+    got = out.float().cpu().numpy().astype(np.float64)
+    if mode == 0:
+        ref = np.maximum(ref, 0.0)
+        tol = 2.0 ** -8 * np.abs(ref) + 1e-5 * mag + 1e-30
+    else:
+        tol = 1e-5 * mag + 1e-30
+    err = np.abs(got - ref)
+    assert np.all(err <= tol), (float(err.max()), float((err / (mag + 1e-30)).max()))
+
+
+@pytest.mark.parametrize("case", [(2, 16, 16, 16, 16), (1, 8, 64, 32, 48), (1, 4, 128, 48, 96),
+                                  (2, 16, 16, 144, 48), (2, 32, 32, 80, 32), (1, 8, 32, 96, 16)])
+def test_conv_weight_gradient_matches_oracle(S, case):
+    N, H, W, Cin, Cout = case
+    rng = np.random.default_rng(sum(case))
+    x = U.round_bf16(rng.normal(size=(N, H, W, Cin)))
+    dy = rng.normal(size=(N, H, W, Cout)).astype(np.float32).astype(np.float64)
+    ref = U.conv3x3_grad_weight(x, U.round_bf16(dy))
+    mag = U.conv3x3_grad_weight(np.abs(x), np.abs(U.round_bf16(dy)))
+    dw = torch.zeros((Cout, 9, Cin), dtype=torch.float32, device="cuda")
+    S.ss_conv3x3_wgrad(torch.tensor(dy, dtype=torch.float32, device="cuda"), bf16_tensor(x), dw)
+    err = np.abs(dw.cpu().numpy() - ref)
+    assert np.all(err <= 1e-5 * mag + 1e-30), float(err.max())
+
+
+def random_problem(rng, B, Sz, C=4, ncoup=1):
+    """Smooth synthetic fields (sums of Gaussian bumps), couplings and targets."""
+    yy, xx = np.meshgrid(np.linspace(-1, 1, Sz), np.linspace(-1, 1, Sz), indexing="ij")
+    f = np.zeros((B, C, Sz, Sz))
+    for b in range(B):
+        for c in range(C):
+            for _ in range(3):
+                x0, y0, s = rng.uniform(-0.8, 0.8), rng.uniform(-0.8, 0.8), rng.uniform(0.1, 0.4)
+                f[b, c] += rng.normal() * np.exp(-((xx - x0) ** 2 + (yy - y0) ** 2) / s ** 2)
+    coup = rng.uniform(0.5, 2.0, size=(B, ncoup)) if ncoup else None
+    target = 0.1 * np.roll(f, 3, axis=3) - 0.05 * f
+    return f, coup, target
+
+
+def test_network_loss_and_gradients_match_oracle(S):
+    B, Sz = 2, 128
+    rng = np.random.default_rng(7)
+    net = S.ss_net_create(S.SS_ABELIAN_HIGGS, Sz, B, seed=3)
+    try:
+        n = S.ss_net_num_params(net)
+        assert n == U.num_params()
+        theta = S.ss_net_get_params(net).astype(np.float64)
+        # give the (zero-initialised) last layer and the biases some weight so that every
+        # path carries gradient; unused output channels stay zero
+        sl = U.unflatten(theta)
+        w14, b14 = sl[14]
+        w14[:4] = rng.normal(size=w14[:4].shape) * 0.1
+        for w, b in sl[:14]:
+            b[:] = rng.normal(size=b.shape) * 0.05
+        theta32 = theta.astype(np.float32)
+        S.ss_net_set_params(net, theta32)
+        f, coup, target = random_problem(rng, B, Sz)
+        fd = torch.tensor(f, dtype=torch.float32, device="cuda")
+        inp = torch.empty((B, Sz, Sz, 16), dtype=torch.bfloat16, device="cuda")
+        S.ss_net_pack(net, fd, coup[:, 0], B, inp)
+        x = U.pack_input(f.astype(np.float32).astype(np.float64), coup)
+        assert np.array_equal(inp.float().cpu().numpy(), U.round_bf16(x))
+        td = torch.tensor(target, dtype=torch.float32, device="cuda")
+        g = torch.zeros(n, dtype=torch.float32, device="cuda")
+        loss = S.ss_net_gradients(net, inp, td, B, g)
+        ref_loss, ref_g, ref_out = U.loss_and_grad(theta32.astype(np.float64), x,
+                                                   target.astype(np.float32).astype(np.float64), 4)
+        assert loss == pytest.approx(ref_loss, rel=1e-3)
+        out = torch.zeros((B, Sz, Sz, 16), dtype=torch.float32, device="cuda")
+        S.ss_net_forward(net, inp, B, out)
+        o = out.cpu().numpy()
+        assert np.linalg.norm(o - ref_out) <= 1e-2 * np.linalg.norm(ref_out)
+        gg = g.cpu().numpy().astype(np.float64)
+        k = 0
+        for L, (ci, co) in enumerate(U.layer_shapes()):
+            for part, size in (("W", 9 * ci * co), ("b", co)):
+                a, r = gg[k:k + size], ref_g[k:k + size]
+                k += size
+                assert np.linalg.norm(a - r) <= 2e-2 * np.linalg.norm(r) + 1e-12, (L, part)
+    finally:
+        S.ss_net_destroy(net)
+
+
+def test_training_steps_reduce_the_loss_on_a_fixed_batch(S):
+    B, Sz = 4, 128
+    rng = np.random.default_rng(11)
+    net = S.ss_net_create(S.SS_ABELIAN_HIGGS, Sz, B, seed=5)
+    try:
+        f, coup, target = random_problem(rng, B, Sz)
+        fd = torch.tensor(f, dtype=torch.float32, device="cuda")
+        inp = torch.empty((B, Sz, Sz, 16), dtype=torch.bfloat16, device="cuda")
+        S.ss_net_pack(net, fd, coup[:, 0], B, inp)
+        td = torch.tensor(target, dtype=torch.float32, device="cuda")
+        losses = [S.ss_net_train_step(net, inp, td, B, 2e-3) for _ in range(60)]
+        assert all(np.isfinite(losses))
+        assert losses[-1] < 0.5 * losses[0], losses[::10]
+    finally:
+        S.ss_net_destroy(net)
+
+
+def test_predict_keeps_the_halo_and_unit_length(S):
+    rng = np.random.default_rng(2)
+    for theory, C, ncoup in ((1, 4, 1), (2, 3, 0)):
+        net = S.ss_net_create(theory, 128, 2, seed=9)
+        try:
+            theta = S.ss_net_get_params(net)
+            sl = U.unflatten(theta.astype(np.float64))
+            w14 = sl[14][0]
+            w14[:C] = rng.normal(size=w14[:C].shape) * 0.05
+            S.ss_net_set_params(net, np.concatenate([np.concatenate([w.ravel(), b]) for w, b in sl]))
+            f, coup, _ = random_problem(rng, 2, 128, C, ncoup)
+            if theory == 2:
+                f /= np.linalg.norm(f, axis=1, keepdims=True) + 1e-12
+            fd = torch.tensor(f, dtype=torch.float32, device="cuda")
+            init = torch.zeros_like(fd)
+            S.ss_net_predict(net, fd, coup[:, 0] if coup is not None else None, 2, init)
+            g = init.cpu().numpy()
+            a = fd.cpu().numpy()
+            halo = np.ones((128, 128), bool)
+            halo[2:-2, 2:-2] = False
+            assert np.array_equal(g[..., halo], a[..., halo])
+            assert np.abs(g[..., ~halo] - a[..., ~halo]).max() > 0  # the correction is applied
+            if theory == 2:
+                nrm = np.linalg.norm(g[..., 2:-2, 2:-2], axis=1)
+                assert np.abs(nrm - 1).max() < 1e-6
+        finally:
+            S.ss_net_destroy(net)
+
+
+def test_save_and_load_round_trip(S):
+    net = S.ss_net_create(S.SS_ABELIAN_HIGGS, 128, 1, seed=1)
+    net2 = S.ss_net_create(S.SS_ABELIAN_HIGGS, 128, 1, seed=2)
+    try:
+        with tempfile.TemporaryDirectory() as d:
+            p = os.path.join(d, "net.bin")
+            S.ss_net_save(net, p)
+            assert not np.array_equal(S.ss_net_get_params(net), S.ss_net_get_params(net2))
+            S.ss_net_load(net2, p)
+            assert np.array_equal(S.ss_net_get_params(net), S.ss_net_get_params(net2))
+        cm = S.ss_net_create(S.SS_CHIRAL_MAGNET, 128, 1)
+        try:
+            with tempfile.TemporaryDirectory() as d:
+                p = os.path.join(d, "net.bin")
+                S.ss_net_save(net, p)
+                with pytest.raises(S.SolitonError):
+                    S.ss_net_load(cm, p)
+        finally:
+            S.ss_net_destroy(cm)
+    finally:
+        S.ss_net_destroy(net)
+        S.ss_net_destroy(net2)
