@@ -61,19 +61,23 @@ int ss_net_load(ss_net* net, const char* path);
  * FP32 SoA [batch][C][size][size]) and `couplings` (host, batch values for the
  * Abelian Higgs lambda; may be NULL for the chiral magnet). */
 int ss_net_pack(ss_net* net, const float* fields, const double* couplings, int batch, void* input);
-/* Forward pass; `out` (device, FP32 NHWC [batch][size][size][16]) may be NULL. */
-int ss_net_forward(ss_net* net, const void* input, int batch, float* out);
+/* Forward pass on the input packed from `ansatz` (device, FP32 SoA) and `couplings`
+ * (as ss_net_pack); `out` (device, FP32 NHWC [batch][size][size][16]) may be NULL. */
+int ss_net_forward(ss_net* net, const float* ansatz, const double* couplings, int batch, float* out);
 /* Loss = mean over the interior sites (the halo of width 2 excluded) and the first
- * C channels of (output - target)^2, target (device) FP32 SoA [batch][C][size][size]
- * (relaxed field minus ansatz); its gradient with respect to every parameter into
- * `grad_out` (device, ss_net_num_params floats; may be NULL) and the loss into
- * *loss_out (host; may be NULL). The weights are not changed. */
-int ss_net_gradients(ss_net* net, const void* input, const float* target, int batch, float* grad_out,
-                     double* loss_out);
+ * C channels of (output - (relaxed - ansatz))^2, where the output is the network's
+ * on the input packed from `ansatz` and `couplings`, and `relaxed` (device, FP32 SoA
+ * [batch][C][size][size]) is the flow's relaxed field of the same problems; its
+ * gradient with respect to every parameter into `grad_out` (device,
+ * ss_net_num_params floats; may be NULL) and the loss into *loss_out (host; may be
+ * NULL). The weights are not changed. */
+int ss_net_gradients(ss_net* net, const float* ansatz, const double* couplings, const float* relaxed, int batch,
+                     float* grad_out, double* loss_out);
 /* ss_net_gradients followed by one Adam update (beta1 0.9, beta2 0.999, eps 1e-8,
  * bias-corrected) with learning rate lr. The update is enqueued on the network's
  * stream and completes before the next call on it. */
-int ss_net_train_step(ss_net* net, const void* input, const float* target, int batch, float lr, double* loss_out);
+int ss_net_train_step(ss_net* net, const float* ansatz, const double* couplings, const float* relaxed, int batch,
+                      float lr, double* loss_out);
 /* Initial fields (device, FP32 SoA [batch][C][size][size]) = ansatz + correction on
  * the interior, the ansatz itself on the halo (the Dirichlet values stay exact);
  * chiral magnet: renormalised to unit length. `ansatz` (device) in the same layout. */

@@ -77,10 +77,11 @@ __global__ void k_pack_input(const float* __restrict__ fields, int C, const floa
   }
 }
 
-// loss = mean over interior sites and the first C channels of (out - target)^2;
-// dout = its gradient (zero elsewhere). target: SoA [B][C][S][S].
-__global__ void k_mse(const float* __restrict__ out, const float* __restrict__ target, int C, int B, int S,
-                      float* __restrict__ dout, double* __restrict__ loss) {
+// loss = mean over interior sites and the first C channels of (out - target)^2 with
+// target = relaxed - ansatz; dout = its gradient (zero elsewhere). Fields: SoA [B][C][S][S].
+__global__ void k_mse(const float* __restrict__ out, const float* __restrict__ ansatz,
+                      const float* __restrict__ relaxed, int C, int B, int S, float* __restrict__ dout,
+                      double* __restrict__ loss) {
   __shared__ double red[8];
   const size_t P = (size_t)S * S;
   const size_t total = (size_t)B * P;
@@ -94,7 +95,8 @@ __global__ void k_mse(const float* __restrict__ out, const float* __restrict__ t
     for (int c = 0; c < COUT_LAST; ++c) {
       float g = 0.f;
       if (inside && c < C) {
-        const float d = out[i * COUT_LAST + c] - target[(b * C + c) * P + q];
+        const size_t f = (b * C + c) * P + q;
+        const float d = out[i * COUT_LAST + c] - (relaxed[f] - ansatz[f]);
         acc += (double)d * d;
         g = (float)(2.0 * inv) * d;
       }
@@ -535,27 +537,36 @@ extern "C" int ss_net_set_params(ss_net* n, const float* host_in) {
   return SS_OK;
 }
 
-extern "C" int ss_net_pack(ss_net* n, const float* fields, const double* couplings, int batch, void* input) {
-  int rc = check_batch(n, batch);
-  if (rc) return rc;
-  if (!fields || !input || (n->ncoup > 0 && !couplings)) return nfail(SS_ERR_ARG, "NULL argument");
-  std::vector<float> c((size_t)batch * n->ncoup);
-  for (size_t i = 0; i < c.size(); ++i) c[i] = (float)couplings[i];
-  if (!c.empty())
+// Input packing without the host synchronisation of the public call (the coupling
+// values are staged in the network's own device buffer).
+int pack(ss_net* n, const float* fields, const double* couplings, int batch, void* input) {
+  if (n->ncoup > 0) {
+    if (!couplings) return nfail(SS_ERR_ARG, "couplings are required for this theory");
+    std::vector<float> c((size_t)batch * n->ncoup);
+    for (size_t i = 0; i < c.size(); ++i) c[i] = (float)couplings[i];
     NET_CK(cudaMemcpyAsync(n->coup, c.data(), sizeof(float) * c.size(), cudaMemcpyHostToDevice, n->stream));
+    NET_CK(cudaStreamSynchronize(n->stream));  // the staging vector goes out of scope
+  }
   k_pack_input<<<grid_of((size_t)batch * n->S * n->S), 256, 0, n->stream>>>(
       fields, n->C, n->coup, n->ncoup, batch, n->S, static_cast<__nv_bfloat16*>(input));
   NET_CK(cudaGetLastError());
-  NET_CK(cudaStreamSynchronize(n->stream));  // the host coupling buffer goes out of scope
   return SS_OK;
 }
 
-extern "C" int ss_net_forward(ss_net* n, const void* input, int batch, float* out) {
+extern "C" int ss_net_pack(ss_net* n, const float* fields, const double* couplings, int batch, void* input) {
   int rc = check_batch(n, batch);
   if (rc) return rc;
-  if (!input) return nfail(SS_ERR_ARG, "input is NULL");
-  NET_CK(cudaMemcpyAsync(n->in0.p, input, sizeof(__nv_bfloat16) * (size_t)batch * n->S * n->S * CIN_PAD,
-                         cudaMemcpyDeviceToDevice, n->stream));
+  if (!fields || !input) return nfail(SS_ERR_ARG, "NULL argument");
+  if ((rc = pack(n, fields, couplings, batch, input))) return rc;
+  NET_CK(cudaStreamSynchronize(n->stream));
+  return SS_OK;
+}
+
+extern "C" int ss_net_forward(ss_net* n, const float* ansatz, const double* couplings, int batch, float* out) {
+  int rc = check_batch(n, batch);
+  if (rc) return rc;
+  if (!ansatz) return nfail(SS_ERR_ARG, "ansatz is NULL");
+  if ((rc = pack(n, ansatz, couplings, batch, n->in0.p))) return rc;
   if ((rc = forward(n, batch))) return rc;
   if (out)
     NET_CK(cudaMemcpyAsync(out, n->out, sizeof(float) * (size_t)batch * n->S * n->S * COUT_LAST,
@@ -564,17 +575,16 @@ extern "C" int ss_net_forward(ss_net* n, const void* input, int batch, float* ou
 }
 
 // Loss and parameter gradient at the current weights (no update).
-extern "C" int ss_net_gradients(ss_net* n, const void* input, const float* target, int batch, float* grad_out,
-                                double* loss_out) {
+extern "C" int ss_net_gradients(ss_net* n, const float* ansatz, const double* couplings, const float* relaxed,
+                                int batch, float* grad_out, double* loss_out) {
   int rc = check_batch(n, batch);
   if (rc) return rc;
-  if (!input || !target) return nfail(SS_ERR_ARG, "NULL argument");
-  NET_CK(cudaMemcpyAsync(n->in0.p, input, sizeof(__nv_bfloat16) * (size_t)batch * n->S * n->S * CIN_PAD,
-                         cudaMemcpyDeviceToDevice, n->stream));
+  if (!ansatz || !relaxed) return nfail(SS_ERR_ARG, "NULL argument");
+  if ((rc = pack(n, ansatz, couplings, batch, n->in0.p))) return rc;
   if ((rc = forward(n, batch))) return rc;
   NET_CK(cudaMemsetAsync(n->loss, 0, sizeof(double), n->stream));
-  k_mse<<<grid_of((size_t)batch * n->S * n->S), 256, 0, n->stream>>>(n->out, target, n->C, batch, n->S, n->g_out,
-                                                                      n->loss);
+  k_mse<<<grid_of((size_t)batch * n->S * n->S), 256, 0, n->stream>>>(n->out, ansatz, relaxed, n->C, batch, n->S,
+                                                                      n->g_out, n->loss);
   NET_CK(cudaGetLastError());
   if ((rc = backward(n, batch))) return rc;
   if (grad_out)
@@ -585,10 +595,10 @@ extern "C" int ss_net_gradients(ss_net* n, const void* input, const float* targe
   return SS_OK;
 }
 
-extern "C" int ss_net_train_step(ss_net* n, const void* input, const float* target, int batch, float lr,
-                                 double* loss_out) {
+extern "C" int ss_net_train_step(ss_net* n, const float* ansatz, const double* couplings, const float* relaxed,
+                                 int batch, float lr, double* loss_out) {
   if (!(lr > 0.f) || !std::isfinite(lr)) return nfail(SS_ERR_ARG, "lr must be positive and finite");
-  int rc = ss_net_gradients(n, input, target, batch, nullptr, loss_out);
+  int rc = ss_net_gradients(n, ansatz, couplings, relaxed, batch, nullptr, loss_out);
   if (rc) return rc;
   n->t += 1;
   const float b1 = 0.9f, b2 = 0.999f;
@@ -603,7 +613,7 @@ extern "C" int ss_net_predict(ss_net* n, const float* ansatz, const double* coup
   int rc = check_batch(n, batch);
   if (rc) return rc;
   if (!ansatz || !init) return nfail(SS_ERR_ARG, "NULL argument");
-  if ((rc = ss_net_pack(n, ansatz, couplings, batch, n->in0.p))) return rc;
+  if ((rc = pack(n, ansatz, couplings, batch, n->in0.p))) return rc;
   if ((rc = forward(n, batch))) return rc;
   k_apply<<<grid_of((size_t)batch * n->S * n->S), 256, 0, n->stream>>>(
       ansatz, n->out, n->C, batch, n->S, n->theory == SS_CHIRAL_MAGNET, init);

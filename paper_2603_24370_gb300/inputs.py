@@ -114,6 +114,13 @@ def ah_batch(count: int = 256, seed: int = 20262, sides=(64, 128, 256, 512), dx:
     return out
 
 
+def ah_learned_set(count: int = 20000, seed: int = 20263, side: int = 256, dx: float = 0.1,
+                   lam_range=(0.5, 2.0), charges=(1, 2, 3, 4, 5, 6)) -> list[Problem]:
+    """Training set of the learned initialiser: Abelian Higgs on side x side grids,
+    lambda ~ U[0.5, 2], N ~ U{1..6} unit vortices uniform in the central half."""
+    return ah_batch(count, seed, (side,), dx, lam_range, charges)
+
+
 def smooth_field(theory: int, nx: int, ny: int, dx: float, dy: float, seed: int, bumps: int = 6,
                  amplitude: float = 0.3) -> np.ndarray:
     """A smooth random test field, float64 [C][ny][nx].

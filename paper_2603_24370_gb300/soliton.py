@@ -128,9 +128,9 @@ def load_library(path: str | None = None):
             "ss_net_save": ([vp, ctypes.c_char_p], i),
             "ss_net_load": ([vp, ctypes.c_char_p], i),
             "ss_net_pack": ([vp, vp, pd, i, vp], i),
-            "ss_net_forward": ([vp, vp, i, vp], i),
-            "ss_net_gradients": ([vp, vp, vp, i, vp, pd], i),
-            "ss_net_train_step": ([vp, vp, vp, i, ctypes.c_float, pd], i),
+            "ss_net_forward": ([vp, vp, pd, i, vp], i),
+            "ss_net_gradients": ([vp, vp, pd, vp, i, vp, pd], i),
+            "ss_net_train_step": ([vp, vp, pd, vp, i, ctypes.c_float, pd], i),
             "ss_net_predict": ([vp, vp, pd, i, vp], i),
             "ss_conv3x3": ([vp, i, i, i, i, vp, i, vp, i, vp, vp], i),
             "ss_conv3x3_wgrad": ([vp, vp, i, i, i, i, i, vp, vp], i),
@@ -498,20 +498,24 @@ def ss_net_pack(net, fields, couplings, batch: int, input_nhwc) -> None:
     _net_check(load_library().ss_net_pack(net, _dev(fields), keep[1] if keep else None, batch, _dev(input_nhwc)))
 
 
-def ss_net_forward(net, input_nhwc, batch: int, out=None) -> None:
-    _net_check(load_library().ss_net_forward(net, _dev(input_nhwc), batch, _dev(out)))
+def ss_net_forward(net, ansatz, couplings, batch: int, out=None) -> None:
+    keep = _couplings(couplings, batch)
+    _net_check(load_library().ss_net_forward(net, _dev(ansatz), keep[1] if keep else None, batch, _dev(out)))
 
 
-def ss_net_gradients(net, input_nhwc, target, batch: int, grad_out=None) -> float:
+def ss_net_gradients(net, ansatz, couplings, relaxed, batch: int, grad_out=None) -> float:
+    keep = _couplings(couplings, batch)
     loss = ctypes.c_double()
-    _net_check(load_library().ss_net_gradients(net, _dev(input_nhwc), _dev(target), batch, _dev(grad_out),
-                                               ctypes.byref(loss)))
+    _net_check(load_library().ss_net_gradients(net, _dev(ansatz), keep[1] if keep else None, _dev(relaxed), batch,
+                                               _dev(grad_out), ctypes.byref(loss)))
     return loss.value
 
 
-def ss_net_train_step(net, input_nhwc, target, batch: int, lr: float) -> float:
+def ss_net_train_step(net, ansatz, couplings, relaxed, batch: int, lr: float) -> float:
+    keep = _couplings(couplings, batch)
     loss = ctypes.c_double()
-    _net_check(load_library().ss_net_train_step(net, _dev(input_nhwc), _dev(target), batch, lr, ctypes.byref(loss)))
+    _net_check(load_library().ss_net_train_step(net, _dev(ansatz), keep[1] if keep else None, _dev(relaxed), batch,
+                                                lr, ctypes.byref(loss)))
     return loss.value
 
 

@@ -128,14 +128,15 @@ def test_network_loss_and_gradients_match_oracle(S):
         S.ss_net_pack(net, fd, coup[:, 0], B, inp)
         x = U.pack_input(f.astype(np.float32).astype(np.float64), coup)
         assert np.array_equal(inp.float().cpu().numpy(), U.round_bf16(x))
-        td = torch.tensor(target, dtype=torch.float32, device="cuda")
+        relaxed = (f + target).astype(np.float32)
+        rd = torch.tensor(relaxed, dtype=torch.float32, device="cuda")
         g = torch.zeros(n, dtype=torch.float32, device="cuda")
-        loss = S.ss_net_gradients(net, inp, td, B, g)
-        ref_loss, ref_g, ref_out = U.loss_and_grad(theta32.astype(np.float64), x,
-                                                   target.astype(np.float32).astype(np.float64), 4)
+        loss = S.ss_net_gradients(net, fd, coup[:, 0], rd, B, g)
+        tgt = (relaxed - f.astype(np.float32)).astype(np.float64)  # formed in FP32 as on the GPU
+        ref_loss, ref_g, ref_out = U.loss_and_grad(theta32.astype(np.float64), x, tgt, 4)
         assert loss == pytest.approx(ref_loss, rel=1e-3)
         out = torch.zeros((B, Sz, Sz, 16), dtype=torch.float32, device="cuda")
-        S.ss_net_forward(net, inp, B, out)
+        S.ss_net_forward(net, fd, coup[:, 0], B, out)
         o = out.cpu().numpy()
         assert np.linalg.norm(o - ref_out) <= 1e-2 * np.linalg.norm(ref_out)
         gg = g.cpu().numpy().astype(np.float64)
@@ -156,10 +157,8 @@ def test_training_steps_reduce_the_loss_on_a_fixed_batch(S):
     try:
         f, coup, target = random_problem(rng, B, Sz)
         fd = torch.tensor(f, dtype=torch.float32, device="cuda")
-        inp = torch.empty((B, Sz, Sz, 16), dtype=torch.bfloat16, device="cuda")
-        S.ss_net_pack(net, fd, coup[:, 0], B, inp)
-        td = torch.tensor(target, dtype=torch.float32, device="cuda")
-        losses = [S.ss_net_train_step(net, inp, td, B, 2e-3) for _ in range(60)]
+        rd = torch.tensor(f + target, dtype=torch.float32, device="cuda")
+        losses = [S.ss_net_train_step(net, fd, coup[:, 0], rd, B, 2e-3) for _ in range(60)]
         assert all(np.isfinite(losses))
         assert losses[-1] < 0.5 * losses[0], losses[::10]
     finally:
