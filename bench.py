@@ -4,8 +4,9 @@
 
 Workload: chiral magnet (J = D = 1, h = 0.6, K = 0.1, interfacial DMI) on a
 4096 x 4096 grid (dx = 0.2, halo included), compensated FP32 fields (value +
-remainder planes) with FP64 reductions, 400 compact skyrmions at seeded positions (minimum separation 8). Its arrays
-(7 x 201 MB) are far larger than the 129 MB L2, so every timed step streams HBM.
+remainder planes) with FP64 reductions, 400 compact skyrmions at seeded positions
+(minimum separation 8). Its arrays (8 x 201 MB) are far larger than the 129 MB L2,
+so every timed step streams HBM.
 
 One bench step = one call ss_step(ctx, 32): 32 flow steps, each two fused kernels
 (pass 1: RK stages 1-2 with the energy / residual / energy-change reductions and
@@ -15,6 +16,11 @@ e2e: the same calls with the field copied in from pinned host memory and out
 again every bench step (ss_set_fields / ss_step / ss_get_fields on host buffers).
 --impl reference: the FP64 CPU oracle on the host cores, same metric, each step one
 oracle flow step on a 512 x 512 crop of the same workload.
+
+--workload ah-batch: time per solve to dx dy max|G| < 1e-6 on the batched Abelian
+Higgs set (256 problems, sides 64..512, dx = 0.1, lambda ~ U[0.5, 2], N in 1..4):
+one bench step = the whole set relaxed in one batch (compensated FP32), against
+the all-FP64 flow run one problem at a time on a seeded subsample of every side.
 """
 from __future__ import annotations
 
@@ -141,7 +147,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_sample(steps_budget_s: float = 12.0, max_steps: int = 40, min_steps: int = 3):
+def cpu_sample(steps_budget_s: float = 12.0, max_steps: int = 2000, min_steps: int = 3):
     """Oracle (FP64, as it stands) flow steps on a 512^2 crop of the workload."""
     import numpy as np
     import oracle as O
@@ -219,6 +225,7 @@ def run_native(args) -> int:
     stream = torch.cuda.Stream()
     s = S.Solver(S.SS_CHIRAL_MAGNET, p.params, n, n, DX, DX, S.SS_FP32, stream=stream)
     s.init_ansatz(p.soliton_array())
+    tuned = s.autotune(4)  # tile shape and pass grids for this grid (the flow restarts from rest)
     f_init = s.fields()
     launches_per_call = 2 + ((INNER + 31) // 32) * 32 * 2  # set_run + head + graph chunk(s)
 
@@ -291,7 +298,8 @@ def run_native(args) -> int:
             "config": {"workload": WORKLOAD if n == N else WORKLOAD.replace("4096x4096", f"{n}x{n}"),
                        "flow_steps_per_bench_step": INNER, "grid": [n, n],
                        "interior_sites": interior(n), "parallelism": "replicas" if world > 1 else "single",
-                       "l2": f"working set {7 * C * n * n * 4 / 1e9:.2f} GB vs 129 MB L2"},
+                       "autotuned": tuned,
+                       "l2": f"working set {8 * C * n * n * 4 / 1e9:.2f} GB vs 129 MB L2"},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": e_units / e_sec, "unit": "site-updates/s", "h2d_bytes_per_step": nbytes,
@@ -299,6 +307,101 @@ def run_native(args) -> int:
             "gpu_launches": launches_per_call * args.steps,
             "clocks": clk,
             "final_energy": st["energy"], "final_grad_max": st["grad_max"],
+        }
+        print(json.dumps(line))
+    if world > 1:
+        tdist.destroy_process_group()
+    return 0
+
+
+BATCH_COUNT = 256
+BATCH_SEED = 20262
+BATCH_TOL = 1e-6
+BATCH_CAP = 40000
+BATCH_WORKLOAD = ("256 Abelian Higgs relaxations in one batch, sides U{64,128,256,512} (halo incl.), dx=0.1, "
+                  "lambda U[0.5,2], N U{1..4} unit vortices uniform in the central half, compensated FP32 "
+                  "fields + FP64 reductions, to dx dy max|G| < 1e-6")
+
+
+def run_solve(args) -> int:
+    """Time per solve: the batched set against the all-FP64 flow one problem at a time."""
+    rank, local_rank, world = D.env_rank()
+    D.pin_visible_device(local_rank, world)
+    import numpy as np
+    import torch
+    import torch.distributed as tdist
+
+    if world > 1:
+        torch.cuda.set_device(0)
+        tdist.init_process_group("nccl")
+    from paper_2603_24370_gb300 import build as B
+    from paper_2603_24370_gb300 import inputs as I
+    from paper_2603_24370_gb300 import soliton as S
+    B.build()
+    S.load_library()
+    # weak scaling: every rank relaxes its own seeded set of the same recipe
+    probs = I.ah_batch(BATCH_COUNT, BATCH_SEED + 1000 * rank)
+    warm = I.ah_batch(8, BATCH_SEED + 999, sides=(64, 128))
+    for _ in range(args.warmup):
+        b = S.ss_batch_create(S.SS_ABELIAN_HIGGS, S.SS_FP32, warm)
+        S.ss_batch_minimise(b, BATCH_TOL, 2000)
+        S.ss_batch_destroy(b)
+    D.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    steps_all, conv = [], 0
+    tuned = None
+    for _ in range(args.steps):
+        b = S.ss_batch_create(S.SS_ABELIAN_HIGGS, S.SS_FP32, probs)
+        tuned = S.ss_batch_autotune(b, 4)
+        _, st = S.ss_batch_minimise(b, BATCH_TOL, BATCH_CAP)
+        S.ss_batch_destroy(b)
+        steps_all = [x["steps"] for x in st]
+        conv = sum(1 for x in st if x["converged"])
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    D.barrier()
+    units, job_sec = D.aggregate(BATCH_COUNT * args.steps, sec)
+    per_solve = job_sec / units
+
+    # all-FP64 flow, one problem at a time, on a seeded subsample of every side;
+    # the set's mean is the size-weighted mean of the per-side means
+    plain = None
+    if rank == 0:
+        rng = I.SplitMix64(4242)
+        by_side = {}
+        for p in probs:
+            by_side.setdefault(p.nx, []).append(p)
+        per_side, sample = {}, 0
+        for side, ps in sorted(by_side.items()):
+            pick = [ps[rng.next_u64() % len(ps)] for _ in range(args.fp64_per_side)]
+            times, conv64 = [], 0
+            for p in pick:
+                with S.Solver(S.SS_ABELIAN_HIGGS, p.params, p.nx, p.ny, p.dx, p.dy, S.SS_FP64) as sv:
+                    sv.init_ansatz(p.soliton_array())
+                    torch.cuda.synchronize()
+                    t1 = time.perf_counter()
+                    r = sv.minimise(BATCH_TOL, BATCH_CAP)
+                    torch.cuda.synchronize()
+                    times.append(time.perf_counter() - t1)
+                    conv64 += 1 if r["converged"] else 0
+            per_side[side] = {"mean_s": float(np.mean(times)), "sampled": len(pick), "converged": conv64,
+                              "problems_in_set": len(ps)}
+            sample += len(pick)
+        mean64 = sum(v["mean_s"] * v["problems_in_set"] for v in per_side.values()) / len(probs)
+        plain = {"s_per_solve": mean64, "per_side": per_side,
+                 "sample": f"{sample} problems ({args.fp64_per_side} per side), one at a time, FP64"}
+    if rank == 0:
+        line = {
+            "metric": "time per solve to dx dy max|G| < 1e-6", "value": per_solve, "unit": "s/solve",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * job_sec / args.steps,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": BATCH_WORKLOAD, "problems_per_rank": BATCH_COUNT, "step_cap": BATCH_CAP,
+                       "autotuned": tuned,
+                       "parallelism": "independent problem sets per rank" if world > 1 else "single"},
+            "converged": conv, "mean_flow_steps": float(np.mean(steps_all)), "max_flow_steps": int(max(steps_all)),
+            "plain_fp64": plain,
+            "speedup_vs_plain_fp64": (plain["s_per_solve"] / per_solve) if plain else None,
         }
         print(json.dumps(line))
     if world > 1:
@@ -314,11 +417,15 @@ def main() -> int:
     ap.add_argument("--impl", choices=("native", "reference"), default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grid", type=int, default=N, help="grid side (default: the 4096 workload; smaller for ncu)")
+    ap.add_argument("--workload", choices=("cm4096", "ah-batch"), default="cm4096")
+    ap.add_argument("--fp64-per-side", type=int, default=2, help="ah-batch: FP64 problems timed per side")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "ah-batch":
+        return run_solve(args)
     return run_native(args)
 
 

@@ -145,6 +145,10 @@ int ss_set_fields(ss_ctx* ctx, const void* fields, int is_device);
  * Errors: SS_ERR_STATE, SS_ERR_ARG, SS_ERR_CUDA. */
 int ss_get_fields(ss_ctx* ctx, void* fields, int is_device);
 
+/* ss_batch_autotune for a single-grid context (see there); the context's field is
+ * kept, the flow restarts from rest. */
+int ss_autotune(ss_ctx* ctx, int trial_steps, int* choice);
+
 /* SS_FP32 contexts: copy the rounding remainder of the current field [C][ny][nx]
  * (float), so that value + remainder (summed in FP64) is the field the flow holds;
  * other precisions write zeros. Errors as ss_get_fields. */
@@ -235,6 +239,16 @@ int ss_batch_get_fields(ss_batch* batch, int item, void* fields, int is_device);
  * halo values become its Dirichlet data) and restart its flow from rest with a
  * fresh step count, as ss_set_fields does for a single grid. */
 int ss_batch_set_fields(ss_batch* batch, int item, const void* fields, int is_device);
+
+/* Autotuner (no counterpart in the paper): times every tile shape of the flow kernels
+ * (FP32: 32 x 16 or 32 x 32 sites, FP64: 32 x 8 or 32 x 16) and every grid size of
+ * each pass (1 .. occupancy blocks per SM x SMs) with CUDA events over trial_steps
+ * (1..1000) flow steps of the batch's own problems, and keeps the fastest. Every
+ * problem is then reset to the field it had at the call, at rest (v = 0), with its
+ * step count back at 0. choice (may be NULL) receives {tile shape 0|1, pass-1 blocks,
+ * pass-2 blocks}. Uses a temporary device copy of the fields.
+ * Errors: SS_ERR_ARG, SS_ERR_NOMEM, SS_ERR_CUDA. */
+int ss_batch_autotune(ss_batch* batch, int trial_steps, int* choice);
 
 /* Observables of problem `item`, as ss_observables. */
 int ss_batch_observables(ss_batch* batch, int item, ss_obs* out);

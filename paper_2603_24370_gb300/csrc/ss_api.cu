@@ -185,21 +185,67 @@ void batch_free(ss_batch* b) {
   delete b;
 }
 
+template <typename R>
+int upload_descs(ss_batch* b) {
+  const int n = b->n();
+  std::vector<ProbDesc<R>> d(n);
+  for (int i = 0; i < n; ++i) d[i] = make_desc<R>(b->probs[i], b->st + i, b->part + b->probs[i].tile0);
+  SS_CK(cudaMemcpy(b->desc, d.data(), sizeof(ProbDesc<R>) * n, cudaMemcpyHostToDevice));
+  b->one_desc.assign(reinterpret_cast<const unsigned char*>(d.data()),
+                     reinterpret_cast<const unsigned char*>(d.data()) + sizeof(ProbDesc<R>));
+  return SS_OK;
+}
+
+// Tile the batch with tile shape ts (0 small, 1 large): every problem's tiles, the
+// tile -> problem map, the descriptors and the pass grids (`blocks`, or each pass's
+// occupancy x SMs when NULL). The captured step graph is dropped and re-captured.
+// Call only while no launch of the batch is in flight.
+int batch_layout(ss_batch* b, int ts, const int* blocks) {
+  const int n = b->n();
+  int tx, ty;
+  flow_tile_dims(b->prec, ts, &tx, &ty);
+  int total = 0;
+  for (Problem& p : b->probs) {
+    p.ntx = (p.nx + tx - 1) / tx;
+    p.ntiles = p.ntx * ((p.ny + ty - 1) / ty);
+    p.tile0 = total;
+    total += p.ntiles;
+  }
+  std::vector<int> tp((size_t)total);
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < b->probs[i].ntiles; ++k) tp[(size_t)b->probs[i].tile0 + k] = i;
+  SS_CK(cudaStreamSynchronize(b->stream));
+  int rc = b->prec == SS_FP64 ? upload_descs<double>(b) : upload_descs<float>(b);
+  if (rc != SS_OK) return rc;
+  SS_CK(cudaMemcpy(b->tile_prob, tp.data(), sizeof(int) * tp.size(), cudaMemcpyHostToDevice));
+  b->BL.total_tiles = total;
+  b->BL.ts = ts;
+  // a batch of one passes its descriptor to the pass kernels by value
+  b->BL.one = n == 1 ? static_cast<const void*>(b->one_desc.data()) : nullptr;
+  const int th = b->theory == SS_ABELIAN_HIGGS ? TH_AH : TH_CM;
+  flow_grid(th, b->prec, ts, total, n == 1, b->BL.flow_blocks);
+  if (blocks) {
+    for (int i = 0; i < 2; ++i) b->BL.flow_blocks[i] = blocks[i] < total ? blocks[i] : total;
+  }
+  if (b->chunk) {
+    cudaGraphExecDestroy(b->chunk);
+    b->chunk = nullptr;
+  }
+  return SS_OK;
+}
+
 // Allocate and lay out every buffer of a batch whose problems are filled in.
 int batch_alloc(ss_batch* b) {
   const int n = b->n();
   int tx, ty;
-  flow_tile_dims(b->prec, &tx, &ty);
+  flow_tile_dims(b->prec, 0, &tx, &ty);  // the small tile shape has the most tiles
   const int nbuf = 6 + (b->prec == SS_FP32 ? 2 : 0);
   size_t bytes = 0;
   int total_tiles = 0, obs_need = 1;
   const int th = b->theory == SS_ABELIAN_HIGGS ? TH_AH : TH_CM;
   for (Problem& p : b->probs) {
     p.plane = (size_t)p.nx * p.ny;
-    p.ntx = (p.nx + tx - 1) / tx;
-    p.ntiles = p.ntx * ((p.ny + ty - 1) / ty);
-    p.tile0 = total_tiles;
-    total_tiles += p.ntiles;
+    total_tiles += ((p.nx + tx - 1) / tx) * ((p.ny + ty - 1) / ty);
     bytes += nbuf * align256((size_t)b->C * p.plane * b->elem);
     const int otiles = ((p.nx + TX - 1) / TX) * ((p.ny + TY - 1) / TY);
     const int og = obs_grid(th, b->prec, otiles);
@@ -241,33 +287,13 @@ int batch_alloc(ss_batch* b) {
   b->d_active = reinterpret_cast<int*>(q);
   b->obs_cap = obs_need;
 
-  // descriptors and the tile -> problem map
-  std::vector<int> tp((size_t)total_tiles);
-  for (int i = 0; i < n; ++i)
-    for (int k = 0; k < b->probs[i].ntiles; ++k) tp[(size_t)b->probs[i].tile0 + k] = i;
   SS_CK(cudaStreamSynchronize(b->stream));  // the memset above precedes the copies
-  if (b->prec == SS_FP64) {
-    std::vector<ProbDesc<double>> d(n);
-    for (int i = 0; i < n; ++i) d[i] = make_desc<double>(b->probs[i], b->st + i, b->part + b->probs[i].tile0);
-    SS_CK(cudaMemcpy(b->desc, d.data(), sizeof(ProbDesc<double>) * n, cudaMemcpyHostToDevice));
-    b->one_desc.assign(reinterpret_cast<const unsigned char*>(d.data()),
-                       reinterpret_cast<const unsigned char*>(d.data()) + sizeof(ProbDesc<double>));
-  } else {
-    std::vector<ProbDesc<float>> d(n);
-    for (int i = 0; i < n; ++i) d[i] = make_desc<float>(b->probs[i], b->st + i, b->part + b->probs[i].tile0);
-    SS_CK(cudaMemcpy(b->desc, d.data(), sizeof(ProbDesc<float>) * n, cudaMemcpyHostToDevice));
-    b->one_desc.assign(reinterpret_cast<const unsigned char*>(d.data()),
-                       reinterpret_cast<const unsigned char*>(d.data()) + sizeof(ProbDesc<float>));
-  }
-  SS_CK(cudaMemcpy(b->tile_prob, tp.data(), sizeof(int) * tp.size(), cudaMemcpyHostToDevice));
   b->BL.theory = th;
   b->BL.prec = b->prec;
   b->BL.probs = b->desc;
   b->BL.tile_prob = b->tile_prob;
-  b->BL.total_tiles = total_tiles;
-  // a batch of one passes its descriptor to the pass kernels by value
-  b->BL.one = n == 1 ? static_cast<const void*>(b->one_desc.data()) : nullptr;
-  flow_grid(th, b->prec, total_tiles, n == 1, b->BL.flow_blocks);
+  int rc = batch_layout(b, 1, nullptr);  // large tiles by default
+  if (rc != SS_OK) return rc;
   SS_CK(cudaMallocHost(&b->h_st, sizeof(DevState) * n));
   SS_CK(cudaMallocHost(&b->h_active, sizeof(int) * 2));
   for (int i = 0; i < 2; ++i) SS_CK(cudaEventCreateWithFlags(&b->ev[i], cudaEventDisableTiming));
@@ -801,6 +827,130 @@ int ss_batch_set_fields(ss_batch* b, int item, const void* fields, int is_device
   int rc = problem_new_fields(b, item);
   if (rc != SS_OK) return rc;
   return read_states(b);
+}
+
+// Autotuner of the flow launch: tile shape (32 x 16 or 32 x 32 sites in FP32) and the
+// grid of each pass (1 .. occupancy blocks per SM), each candidate timed with CUDA
+// events over trial_steps flow steps of the batch's own problems, starting from
+// their current fields. The fastest combination is kept; every problem is then
+// reset to its field at the call, at rest, with a fresh step count.
+int batch_autotune(ss_batch* b, int trial_steps, int* choice) {
+  if (trial_steps < 1 || trial_steps > 1000) return fail(SS_ERR_ARG, "trial_steps must be in 1..1000");
+  int rc = read_states(b);
+  if (rc != SS_OK) return rc;
+  const int n = b->n();
+  const bool lo = b->prec == SS_FP32;
+  std::vector<size_t> off(n + 1, 0);
+  for (int i = 0; i < n; ++i) off[i + 1] = off[i] + (size_t)b->C * b->probs[i].plane * b->elem * (lo ? 2 : 1);
+  char* snap = nullptr;
+  SS_CK(cudaMalloc(&snap, off[n]));
+  auto release = [&](int code) {
+    cudaStreamSynchronize(b->stream);
+    cudaFree(snap);
+    return code;
+  };
+  for (int i = 0; i < n; ++i) {
+    const Problem& p = b->probs[i];
+    const size_t bytes = (size_t)b->C * p.plane * b->elem;
+    const int cur = cur_of(b, i);
+    if (cudaMemcpyAsync(snap + off[i], p.phi[cur], bytes, cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess ||
+        (lo && cudaMemcpyAsync(snap + off[i] + bytes, p.lo[cur], bytes, cudaMemcpyDeviceToDevice, b->stream) !=
+                   cudaSuccess))
+      return release(fail(SS_ERR_CUDA, "autotune: snapshot copy failed"));
+  }
+  auto restore = [&]() -> int {
+    for (int i = 0; i < n; ++i) {
+      const Problem& p = b->probs[i];
+      const size_t bytes = (size_t)b->C * p.plane * b->elem;
+      int r = problem_new_fields(b, i);
+      if (r != SS_OK) return r;
+      for (int k = 0; k < 2; ++k) {
+        SS_CK(cudaMemcpyAsync(p.phi[k], snap + off[i], bytes, cudaMemcpyDeviceToDevice, b->stream));
+        if (lo) SS_CK(cudaMemcpyAsync(p.lo[k], snap + off[i] + bytes, bytes, cudaMemcpyDeviceToDevice, b->stream));
+      }
+    }
+    return SS_OK;
+  };
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int th = b->theory == SS_ABELIAN_HIGGS ? TH_AH : TH_CM;
+  cudaEvent_t ev[3];
+  for (int i = 0; i < 3; ++i)
+    if (cudaEventCreate(&ev[i]) != cudaSuccess) return release(fail(SS_ERR_CUDA, "autotune: event creation failed"));
+  auto destroy_events = [&]() {
+    for (int i = 0; i < 3; ++i) cudaEventDestroy(ev[i]);
+  };
+  double best = 1e300;
+  int best_ts = 1, best_blocks[2] = {0, 0};
+  for (int ts = 0; ts < 2; ++ts) {
+    int occ[2];
+    flow_occupancy(th, b->prec, ts, n == 1, occ);
+    const int kmax = occ[0] > occ[1] ? occ[0] : occ[1];
+    double tbest[2] = {1e300, 1e300};
+    int kbest[2] = {1, 1};
+    for (int k = 1; k <= kmax; ++k) {
+      const int blocks[2] = {(k < occ[0] ? k : occ[0]) * nsm, (k < occ[1] ? k : occ[1]) * nsm};
+      if ((rc = batch_layout(b, ts, blocks)) != SS_OK || (rc = restore()) != SS_OK) {
+        destroy_events();
+        return release(rc);
+      }
+      cudaError_t e = launch_set_run_all(b->st, n, -1.0, trial_steps + 1, b->stream);
+      if (e == cudaSuccess) e = launch_pass(b->BL, 1, b->stream);  // head, untimed
+      if (e == cudaSuccess) e = launch_pass(b->BL, 2, b->stream);  // one untimed step
+      if (e == cudaSuccess) e = launch_pass(b->BL, 1, b->stream);
+      double acc[2] = {0.0, 0.0};
+      for (int step = 0; step < trial_steps && e == cudaSuccess; ++step) {
+        e = cudaEventRecord(ev[0], b->stream);
+        if (e == cudaSuccess) e = launch_pass(b->BL, 2, b->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[1], b->stream);
+        if (e == cudaSuccess) e = launch_pass(b->BL, 1, b->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[2], b->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[2]);
+        float m1 = 0.f, m2 = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&m2, ev[0], ev[1]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&m1, ev[1], ev[2]);
+        acc[0] += m1;
+        acc[1] += m2;
+      }
+      if (e != cudaSuccess) {
+        destroy_events();
+        return release(fail(SS_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e)));
+      }
+      for (int q = 0; q < 2; ++q)
+        if (k <= occ[q] && acc[q] < tbest[q]) {
+          tbest[q] = acc[q];
+          kbest[q] = k;
+        }
+    }
+    if (tbest[0] + tbest[1] < best) {
+      best = tbest[0] + tbest[1];
+      best_ts = ts;
+      best_blocks[0] = kbest[0] * nsm;
+      best_blocks[1] = kbest[1] * nsm;
+    }
+  }
+  destroy_events();
+  if ((rc = batch_layout(b, best_ts, best_blocks)) != SS_OK || (rc = restore()) != SS_OK) return release(rc);
+  rc = release(read_states(b));
+  if (rc != SS_OK) return rc;
+  if (choice) {
+    choice[0] = best_ts;
+    choice[1] = b->BL.flow_blocks[0];
+    choice[2] = b->BL.flow_blocks[1];
+  }
+  return SS_OK;
+}
+
+int ss_batch_autotune(ss_batch* b, int trial_steps, int* choice) {
+  if (!b) return fail(SS_ERR_ARG, "null batch");
+  return batch_autotune(b, trial_steps, choice);
+}
+
+int ss_autotune(ss_ctx* c, int trial_steps, int* choice) {
+  int rc = check_ready(c);
+  if (rc != SS_OK) return rc;
+  return batch_autotune(c->b, trial_steps, choice);
 }
 
 int ss_batch_observables(ss_batch* b, int item, ss_obs* out) {

@@ -43,13 +43,12 @@ template <int BN>
 __host__ __device__ constexpr int stage_bytes() {
   return GPS * (BM + BN) * 16;
 }
-// Dynamic shared memory: the stages, 1 KB for aligning the base, and a reserve so
-// that the descriptor-addressed operand reads of the last stage stay inside the
-// allocation even for the widest tiles.
-constexpr size_t SMEM_RESERVE = 48 * 1024;
+// Dynamic shared memory: the stages and 1 KB for aligning the base. The MMA reads
+// of a stage stay inside it: A spans 16 row groups x SBO 128 B plus K-groups at
+// LBO 2048 B, B likewise with LBO = BN * 16 B.
 template <int BN>
 constexpr size_t conv_smem() {
-  return (size_t)STAGES * stage_bytes<BN>() + 1024 + SMEM_RESERVE;
+  return (size_t)STAGES * stage_bytes<BN>() + 1024;
 }
 
 struct ConvArgs {

@@ -51,16 +51,18 @@
 
 namespace ss {
 
-template <typename R>
+// Tile shape: TS = 0 (small) or 1 (large) selects the rows each thread walks,
+// FP32 2 or 4 (tiles of 32 x 16 or 32 x 32 sites), FP64 1 or 2 (32 x 8 or 32 x 16).
+template <typename R, int TS>
 struct FlowTile {
-  static constexpr int RY = sizeof(R) == 4 ? 4 : 2;  // rows per thread
+  static constexpr int RY = (sizeof(R) == 4 ? 2 : 1) << TS;  // rows per thread
   static constexpr int TX = 32, TY = BY * RY;
   static constexpr int SX = TX + 4, SY = TY + 4, SXY = SX * SY;
 };
 
-void flow_tile_dims(int prec, int* tx, int* ty) {
-  if (prec == PREC_F64) { *tx = FlowTile<double>::TX; *ty = FlowTile<double>::TY; }
-  else { *tx = FlowTile<float>::TX; *ty = FlowTile<float>::TY; }
+void flow_tile_dims(int prec, int ts, int* tx, int* ty) {
+  *tx = 32;
+  *ty = BY * ((prec == PREC_F64 ? 1 : 2) << (ts ? 1 : 0));
 }
 
 // 1 / |n| for the unit-length projection: FP32 uses the hardware reciprocal square
@@ -165,10 +167,10 @@ struct Win {
 
 // Window set of one stage input: all C components, mixed derivatives for the gauge
 // field of the Abelian Higgs model (components 2, 3).
-template <int TH, typename R>
+template <int TH, typename R, int SXY_>
 struct StageWin {
   static constexpr int C = NComp<TH>::C;
-  static constexpr int SXY = FlowTile<R>::SXY;
+  static constexpr int SXY = SXY_;
   Win<R, false> w0, w1;
   Win<R, TH == TH_AH> w2;
   Win<R, TH == TH_AH> w3;  // unused for the chiral magnet
@@ -195,10 +197,10 @@ struct StageWin {
 };
 
 // First derivatives only (the field difference of the arrest test).
-template <int TH, typename R>
+template <int TH, typename R, int SXY_>
 struct DiffWin {
   static constexpr int C = NComp<TH>::C;
-  static constexpr int SXY = FlowTile<R>::SXY;
+  static constexpr int SXY = SXY_;
   Win<R, false> w[C];
   __device__ __forceinline__ void enter(const R* tiles, int off, int slot) {
 #pragma unroll
@@ -314,11 +316,11 @@ __device__ __forceinline__ void load_tile_ctx(TileCtx<R>& tc, const ProbDesc<R>&
 // One flow pass over every tile of a batch. ONE: the batch has a single problem,
 // whose descriptor arrives as a kernel parameter, so its pointers, spacings and
 // couplings are read as constant operands instead of occupying registers.
-template <int TH, typename R, int PASS, bool LO, bool ONE>
+template <int TH, typename R, int PASS, bool LO, bool ONE, int TS>
 __global__ void __launch_bounds__(NT)
     k_pass(const __grid_constant__ ProbDesc<R> one, const ProbDesc<R>* __restrict__ probs,
            const int* __restrict__ tile_prob, int total_tiles) {
-  using T = FlowTile<R>;
+  using T = FlowTile<R, TS>;
   constexpr int C = NComp<TH>::C;
   constexpr int RY = T::RY;
   constexpr int PS = C * T::SXY;  // values per tile set
@@ -451,8 +453,8 @@ __global__ void __launch_bounds__(NT)
     if (PASS == 1) {
       // stage 1 at Y_1 = phi: k_v1, e, max|G|, and e(phi^n) - e(phi^{n-1})
       {
-        StageWin<TH, R> W;
-        DiffWin<TH, R> D;
+        StageWin<TH, R, T::SXY> W;
+        DiffWin<TH, R, T::SXY> D;
 #pragma unroll
         for (int s = 0; s < 5; ++s) {
           const int off = (sy0 - 2 + s) * T::SX + sx;
@@ -502,7 +504,7 @@ __global__ void __launch_bounds__(NT)
       }
       // stage 2 at Y_2 = phi + dt/2 v: k_v2
       {
-        StageWin<TH, R> W;
+        StageWin<TH, R, T::SXY> W;
 #pragma unroll
         for (int s = 0; s < 5; ++s) W.enter(setB, (sy0 - 2 + s) * T::SX + sx, s);
 #pragma unroll
@@ -586,7 +588,7 @@ __global__ void __launch_bounds__(NT)
       // stage 3 at Y_3: k_v3 kept in registers
       R k3[RY][C];
       {
-        StageWin<TH, R> W;
+        StageWin<TH, R, T::SXY> W;
 #pragma unroll
         for (int s = 0; s < 5; ++s) W.enter(setA, (sy0 - 2 + s) * T::SX + sx, s);
 #pragma unroll
@@ -605,7 +607,7 @@ __global__ void __launch_bounds__(NT)
       }
       // stage 4 at Y_4, then the RK4 combination
       {
-        StageWin<TH, R> W;
+        StageWin<TH, R, T::SXY> W;
 #pragma unroll
         for (int s = 0; s < 5; ++s) W.enter(setB, (sy0 - 2 + s) * T::SX + sx, s);
         const R w6 = dt * dt / R(6), u6 = dt / R(6);
@@ -731,26 +733,33 @@ __global__ void k_scaled_copy(R* __restrict__ out, const R* __restrict__ in, siz
 }
 
 // ------------------------------------------------------------------ launchers
-template <int TH, typename R>
+template <int TH, typename R, int TS>
 static size_t pass_smem(int pass) {
-  return (size_t)(pass == 1 ? 3 : 2) * NComp<TH>::C * FlowTile<R>::SXY * sizeof(R);
+  return (size_t)(pass == 1 ? 3 : 2) * NComp<TH>::C * FlowTile<R, TS>::SXY * sizeof(R);
 }
 
-template <int TH, typename R, bool LO, bool ONE>
+template <int TH, typename R, bool LO, bool ONE, int TS>
 static void pass_launch(const BatchLaunch& b, int pass, cudaStream_t s) {
   const ProbDesc<R>* probs = static_cast<const ProbDesc<R>*>(b.probs);
   const ProbDesc<R> one = ONE ? *static_cast<const ProbDesc<R>*>(b.one) : ProbDesc<R>{};
   const dim3 blk(BX, BY);
   if (pass == 1)
-    k_pass<TH, R, 1, LO, ONE><<<b.flow_blocks[0], blk, pass_smem<TH, R>(1), s>>>(one, probs, b.tile_prob, b.total_tiles);
+    k_pass<TH, R, 1, LO, ONE, TS><<<b.flow_blocks[0], blk, pass_smem<TH, R, TS>(1), s>>>(one, probs, b.tile_prob,
+                                                                                          b.total_tiles);
   else
-    k_pass<TH, R, 2, LO, ONE><<<b.flow_blocks[1], blk, pass_smem<TH, R>(2), s>>>(one, probs, b.tile_prob, b.total_tiles);
+    k_pass<TH, R, 2, LO, ONE, TS><<<b.flow_blocks[1], blk, pass_smem<TH, R, TS>(2), s>>>(one, probs, b.tile_prob,
+                                                                                          b.total_tiles);
 }
 template <int TH, typename R, bool LO>
 static cudaError_t pass_t(const BatchLaunch& b, int pass, cudaStream_t s) {
   if (pass != 1 && pass != 2) return cudaErrorInvalidValue;
-  if (b.one) pass_launch<TH, R, LO, true>(b, pass, s);
-  else pass_launch<TH, R, LO, false>(b, pass, s);
+  if (b.one) {
+    if (b.ts) pass_launch<TH, R, LO, true, 1>(b, pass, s);
+    else pass_launch<TH, R, LO, true, 0>(b, pass, s);
+  } else {
+    if (b.ts) pass_launch<TH, R, LO, false, 1>(b, pass, s);
+    else pass_launch<TH, R, LO, false, 0>(b, pass, s);
+  }
   return cudaGetLastError();
 }
 template <int TH>
@@ -793,39 +802,55 @@ cudaError_t launch_scaled_copy(const LaunchCtx& c, void* out, const void* in, do
   return cudaGetLastError();
 }
 
-// Opt the pass kernels into their dynamic shared memory; each pass's grid is its
-// own occupancy times the SM count (capped by the tile count).
-template <int TH, typename R, bool LO, bool ONE>
+// Opt the pass kernels into their dynamic shared memory and report how many blocks
+// of each pass fit on one SM.
+template <int TH, typename R, bool LO, bool ONE, int TS>
 static void pass_occupancy(int occ[2]) {
-  cudaFuncSetAttribute(k_pass<TH, R, 1, LO, ONE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pass_smem<TH, R>(1));
-  cudaFuncSetAttribute(k_pass<TH, R, 2, LO, ONE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pass_smem<TH, R>(2));
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[0], k_pass<TH, R, 1, LO, ONE>, NT, pass_smem<TH, R>(1));
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], k_pass<TH, R, 2, LO, ONE>, NT, pass_smem<TH, R>(2));
+  cudaFuncSetAttribute(k_pass<TH, R, 1, LO, ONE, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)pass_smem<TH, R, TS>(1));
+  cudaFuncSetAttribute(k_pass<TH, R, 2, LO, ONE, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)pass_smem<TH, R, TS>(2));
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[0], k_pass<TH, R, 1, LO, ONE, TS>, NT, pass_smem<TH, R, TS>(1));
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], k_pass<TH, R, 2, LO, ONE, TS>, NT, pass_smem<TH, R, TS>(2));
 }
 
-template <int TH, bool ONE>
+template <int TH, bool ONE, int TS>
 static void occupancy_th(int prec, int occ[2]) {
   switch (prec) {
-    case PREC_F32C: pass_occupancy<TH, float, true, ONE>(occ); break;
-    case PREC_F64: pass_occupancy<TH, double, false, ONE>(occ); break;
-    default: pass_occupancy<TH, float, false, ONE>(occ); break;
+    case PREC_F32C: pass_occupancy<TH, float, true, ONE, TS>(occ); break;
+    case PREC_F64: pass_occupancy<TH, double, false, ONE, TS>(occ); break;
+    default: pass_occupancy<TH, float, false, ONE, TS>(occ); break;
   }
 }
 
-void flow_grid(int theory, int prec, int total_tiles, bool one, int blocks[2]) {
+template <int TH>
+static void occupancy_sel(int prec, int ts, bool one, int occ[2]) {
+  if (one) {
+    if (ts) occupancy_th<TH, true, 1>(prec, occ);
+    else occupancy_th<TH, true, 0>(prec, occ);
+  } else {
+    if (ts) occupancy_th<TH, false, 1>(prec, occ);
+    else occupancy_th<TH, false, 0>(prec, occ);
+  }
+}
+
+void flow_occupancy(int theory, int prec, int ts, bool one, int occ[2]) {
+  occ[0] = occ[1] = 1;
+  if (theory == TH_AH) occupancy_sel<TH_AH>(prec, ts, one, occ);
+  else occupancy_sel<TH_CM>(prec, ts, one, occ);
+  for (int i = 0; i < 2; ++i)
+    if (occ[i] < 1) occ[i] = 1;
+}
+
+// Default grid of each pass: its occupancy x SMs, capped by the tile count.
+void flow_grid(int theory, int prec, int ts, int total_tiles, bool one, int blocks[2]) {
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  int occ[2] = {1, 1};
-  if (theory == TH_AH) {
-    if (one) occupancy_th<TH_AH, true>(prec, occ);
-    else occupancy_th<TH_AH, false>(prec, occ);
-  } else {
-    if (one) occupancy_th<TH_CM, true>(prec, occ);
-    else occupancy_th<TH_CM, false>(prec, occ);
-  }
+  int occ[2];
+  flow_occupancy(theory, prec, ts, one, occ);
   for (int i = 0; i < 2; ++i) {
-    const int g = nsm * (occ[i] < 1 ? 1 : occ[i]);
+    const int g = nsm * occ[i];
     blocks[i] = total_tiles < g ? total_tiles : g;
   }
 }

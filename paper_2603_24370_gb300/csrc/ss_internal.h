@@ -64,10 +64,11 @@ struct BatchLaunch {
   int total_tiles;
   int flow_blocks[2];  // grid of pass 1 / pass 2
   const void* one;     // host copy of the ProbDesc<R> of a single-problem batch, else NULL
+  int ts;              // tile shape: 0 small, 1 large (flow_tile_dims)
 };
 
 // Tile shape of the flow kernels for a precision (sites per tile along x, y).
-void flow_tile_dims(int prec, int* tx, int* ty);
+void flow_tile_dims(int prec, int ts, int* tx, int* ty);
 
 // Pass 1 (RK stages 1-2, reductions, arrest and convergence decisions) or pass 2
 // (RK stages 3-4, combination) of one flow step of every problem of a batch that
@@ -94,7 +95,9 @@ cudaError_t launch_ansatz(const LaunchCtx& c, const double* d_sol, int n, cudaSt
 void set_last_error(const std::string& msg);
 
 // Grid of each flow pass (its occupancy x SMs, capped by the tile count).
-void flow_grid(int theory, int prec, int total_tiles, bool one, int blocks[2]);
+void flow_grid(int theory, int prec, int ts, int total_tiles, bool one, int blocks[2]);
+// Blocks of each pass that fit on one SM.
+void flow_occupancy(int theory, int prec, int ts, bool one, int occ[2]);
 int obs_grid(int theory, int prec, int ntiles);
 
 }  // namespace ss

@@ -115,6 +115,8 @@ def load_library(path: str | None = None):
             "ss_batch_minimise": ([vp, d, ll, ctypes.POINTER(ss_status)], i),
             "ss_batch_get_fields": ([vp, i, vp, i], i),
             "ss_batch_set_fields": ([vp, i, vp, i], i),
+            "ss_batch_autotune": ([vp, i, ctypes.POINTER(ctypes.c_int)], i),
+            "ss_autotune": ([vp, i, ctypes.POINTER(ctypes.c_int)], i),
             "ss_batch_observables": ([vp, i, ctypes.POINTER(ss_obs)], i),
             "ss_batch_destroy": ([vp], i),
             "ss_destroy": ([vp], i),
@@ -334,6 +336,18 @@ def ss_batch_set_fields(b, item: int, fields) -> None:
     _check(load_library().ss_batch_set_fields(b, item, p, dev))
 
 
+def ss_batch_autotune(b, trial_steps: int = 8) -> dict:
+    c = (ctypes.c_int * 3)()
+    _check(load_library().ss_batch_autotune(b, trial_steps, c))
+    return {"tile_shape": c[0], "blocks": [c[1], c[2]]}
+
+
+def ss_autotune(ctx, trial_steps: int = 8) -> dict:
+    c = (ctypes.c_int * 3)()
+    _check(load_library().ss_autotune(ctx, trial_steps, c))
+    return {"tile_shape": c[0], "blocks": [c[1], c[2]]}
+
+
 def ss_batch_observables(b, item: int) -> dict:
     o = ss_obs()
     _check(load_library().ss_batch_observables(b, int(item), ctypes.byref(o)))
@@ -402,6 +416,10 @@ class Solver:
 
     def step(self, n: int, allow=()):
         return ss_step(self.ctx, n, allow)
+
+    def autotune(self, trial_steps: int = 8) -> dict:
+        """Pick the fastest tile shape and pass grids (the flow restarts from rest)."""
+        return ss_autotune(self.ctx, trial_steps)
 
     def minimise(self, tol: float, max_steps: int):
         return ss_minimise(self.ctx, tol, max_steps)

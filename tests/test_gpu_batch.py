@@ -138,3 +138,43 @@ def test_batch_rejects_bad_items(S):
     with pytest.raises(S.SolitonError) as ei:
         S.ss_batch_create(S.SS_ABELIAN_HIGGS, 1, probs)
     assert ei.value.code == S.SS_ERR_ARG and "item 1" in str(ei.value)
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_autotune_keeps_the_fields_and_the_trajectory(S, prec):
+    """The tuner times the flow on the batch's own problems, then restores them: the
+    tuned batch evolves exactly like an untuned one (the per-site update does not
+    depend on the tile shape or the grid)."""
+    probs = mixed_batch(count=5, seed=3)
+    b = S.ss_batch_create(S.SS_ABELIAN_HIGGS, prec, probs)
+    b2 = S.ss_batch_create(S.SS_ABELIAN_HIGGS, prec, probs)
+    try:
+        S.ss_batch_step(b, 7)  # tune from a state that is not the ansatz
+        S.ss_batch_step(b2, 7)
+        dt = np.float64 if prec == 2 else np.float32
+        mid = [np.empty((4, p.ny, p.nx), dtype=dt) for p in probs]
+        for k in range(len(probs)):
+            S.ss_batch_get_fields(b2, k, mid[k])
+            S.ss_batch_set_fields(b2, k, mid[k])  # the tuner restarts from rest: so does the reference
+        choice = S.ss_batch_autotune(b, 3)
+        assert choice["tile_shape"] in (0, 1) and min(choice["blocks"]) > 0
+        for k in range(len(probs)):
+            got = np.empty((4, probs[k].ny, probs[k].nx), dtype=dt)
+            S.ss_batch_get_fields(b, k, got)
+            if prec == 2:
+                assert np.array_equal(got, mid[k])
+        _, st = S.ss_batch_step(b, 15)
+        _, st2 = S.ss_batch_step(b2, 15)
+        for k, p in enumerate(probs):
+            g1 = np.empty((4, p.ny, p.nx), dtype=dt)
+            g2 = np.empty_like(g1)
+            S.ss_batch_get_fields(b, k, g1)
+            S.ss_batch_get_fields(b2, k, g2)
+            assert st[k]["steps"] == st2[k]["steps"] == 15
+            if prec == 2 and st[k]["arrests"] == st2[k]["arrests"]:
+                assert np.array_equal(g1, g2), k
+            else:  # compensated FP32: the reference restarted without the remainder planes
+                assert np.abs(g1 - g2).max() <= 1e-5, k
+    finally:
+        S.ss_batch_destroy(b)
+        S.ss_batch_destroy(b2)
