@@ -77,9 +77,9 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was
-    taken on the current kernel source (else None)."""
+def ncu_traffic(kernel: str, tile_shape: int):
+    """DRAM bytes per launch of `kernel` at tile shape `tile_shape` from the committed
+    ncu summary, if it was taken on the current kernel source (else None)."""
     p = os.path.join(ROOT, "profiles", "stage_traffic.json")
     if not os.path.exists(p):
         return None
@@ -87,7 +87,7 @@ def ncu_traffic(kernel: str):
         d = json.load(fh)
     if d.get("source_hash") != kernel_source_hash():
         return None
-    return d.get("bytes_per_launch", {}).get(kernel)
+    return d.get("bytes_per_launch", {}).get(f"ts{tile_shape}", {}).get(kernel)
 
 
 class ClockSampler:
@@ -225,7 +225,11 @@ def run_native(args) -> int:
     stream = torch.cuda.Stream()
     s = S.Solver(S.SS_CHIRAL_MAGNET, p.params, n, n, DX, DX, S.SS_FP32, stream=stream)
     s.init_ansatz(p.soliton_array())
-    tuned = s.autotune(4)  # tile shape and pass grids for this grid (the flow restarts from rest)
+    if args.tile_shape == "auto":
+        tuned = s.autotune(4)  # tile shape and pass grids for this grid (the flow restarts from rest)
+    else:
+        s.set_launch(int(args.tile_shape))
+        tuned = {"tile_shape": int(args.tile_shape), "blocks": None, "set_by_hand": True}
     f_init = s.fields()
     launches_per_call = 2 + ((INNER + 31) // 32) * 32 * 2  # set_run + head + graph chunk(s)
 
@@ -257,7 +261,7 @@ def run_native(args) -> int:
     kname = f"k_pass<CM, float, {dominant}>"
     alg = PASS_BYTES[dominant] * interior(n)
     achieved = alg / (stage_ms[dominant - 1] * 1e-3) / 1e9
-    traffic = ncu_traffic(f"pass{dominant}")
+    traffic = ncu_traffic(f"pass{dominant}", tuned["tile_shape"])
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "kernel": kname,
                 "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else "fallback 6.8 TB/s",
@@ -418,6 +422,8 @@ def main() -> int:
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grid", type=int, default=N, help="grid side (default: the 4096 workload; smaller for ncu)")
     ap.add_argument("--workload", choices=("cm4096", "ah-batch"), default="cm4096")
+    ap.add_argument("--tile-shape", choices=("auto", "0", "1"), default="auto",
+                    help="flow tile shape: autotuned (default) or fixed (for profiling one shape)")
     ap.add_argument("--fp64-per-side", type=int, default=2, help="ah-batch: FP64 problems timed per side")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -148,6 +148,8 @@ int ss_get_fields(ss_ctx* ctx, void* fields, int is_device);
 /* ss_batch_autotune for a single-grid context (see there); the context's field is
  * kept, the flow restarts from rest. */
 int ss_autotune(ss_ctx* ctx, int trial_steps, int* choice);
+/* ss_batch_set_launch for a single-grid context. */
+int ss_set_launch(ss_ctx* ctx, int tile_shape, const int* blocks);
 
 /* SS_FP32 contexts: copy the rounding remainder of the current field [C][ny][nx]
  * (float), so that value + remainder (summed in FP64) is the field the flow holds;
@@ -249,6 +251,12 @@ int ss_batch_set_fields(ss_batch* batch, int item, const void* fields, int is_de
  * pass-2 blocks}. Uses a temporary device copy of the fields.
  * Errors: SS_ERR_ARG, SS_ERR_NOMEM, SS_ERR_CUDA. */
 int ss_batch_autotune(ss_batch* batch, int trial_steps, int* choice);
+
+/* Set the flow launch by hand (what ss_batch_autotune chooses): tile_shape 0 (small)
+ * or 1 (large, the default); blocks = {pass-1 grid, pass-2 grid}, or NULL for each
+ * pass's occupancy x SMs (capped by the tile count). Fields and flow state are kept.
+ * Errors: SS_ERR_ARG, SS_ERR_CUDA. */
+int ss_batch_set_launch(ss_batch* batch, int tile_shape, const int* blocks);
 
 /* Observables of problem `item`, as ss_observables. */
 int ss_batch_observables(ss_batch* batch, int item, ss_obs* out);

@@ -942,6 +942,23 @@ int batch_autotune(ss_batch* b, int trial_steps, int* choice) {
   return SS_OK;
 }
 
+int batch_set_launch(ss_batch* b, int tile_shape, const int* blocks) {
+  if (tile_shape != 0 && tile_shape != 1) return fail(SS_ERR_ARG, "tile_shape must be 0 or 1");
+  if (blocks && (blocks[0] < 1 || blocks[1] < 1)) return fail(SS_ERR_ARG, "block counts must be >= 1");
+  return batch_layout(b, tile_shape, blocks);
+}
+
+int ss_batch_set_launch(ss_batch* b, int tile_shape, const int* blocks) {
+  if (!b) return fail(SS_ERR_ARG, "null batch");
+  return batch_set_launch(b, tile_shape, blocks);
+}
+
+int ss_set_launch(ss_ctx* c, int tile_shape, const int* blocks) {
+  int rc = check_ready(c);
+  if (rc != SS_OK) return rc;
+  return batch_set_launch(c->b, tile_shape, blocks);
+}
+
 int ss_batch_autotune(ss_batch* b, int trial_steps, int* choice) {
   if (!b) return fail(SS_ERR_ARG, "null batch");
   return batch_autotune(b, trial_steps, choice);

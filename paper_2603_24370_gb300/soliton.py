@@ -117,6 +117,8 @@ def load_library(path: str | None = None):
             "ss_batch_set_fields": ([vp, i, vp, i], i),
             "ss_batch_autotune": ([vp, i, ctypes.POINTER(ctypes.c_int)], i),
             "ss_autotune": ([vp, i, ctypes.POINTER(ctypes.c_int)], i),
+            "ss_batch_set_launch": ([vp, i, ctypes.POINTER(ctypes.c_int)], i),
+            "ss_set_launch": ([vp, i, ctypes.POINTER(ctypes.c_int)], i),
             "ss_batch_observables": ([vp, i, ctypes.POINTER(ss_obs)], i),
             "ss_batch_destroy": ([vp], i),
             "ss_destroy": ([vp], i),
@@ -348,6 +350,21 @@ def ss_autotune(ctx, trial_steps: int = 8) -> dict:
     return {"tile_shape": c[0], "blocks": [c[1], c[2]]}
 
 
+def _blocks(blocks):
+    if blocks is None:
+        return None
+    arr = (ctypes.c_int * 2)(int(blocks[0]), int(blocks[1]))
+    return arr
+
+
+def ss_batch_set_launch(b, tile_shape: int, blocks=None) -> None:
+    _check(load_library().ss_batch_set_launch(b, tile_shape, _blocks(blocks)))
+
+
+def ss_set_launch(ctx, tile_shape: int, blocks=None) -> None:
+    _check(load_library().ss_set_launch(ctx, tile_shape, _blocks(blocks)))
+
+
 def ss_batch_observables(b, item: int) -> dict:
     o = ss_obs()
     _check(load_library().ss_batch_observables(b, int(item), ctypes.byref(o)))
@@ -420,6 +437,9 @@ class Solver:
     def autotune(self, trial_steps: int = 8) -> dict:
         """Pick the fastest tile shape and pass grids (the flow restarts from rest)."""
         return ss_autotune(self.ctx, trial_steps)
+
+    def set_launch(self, tile_shape: int, blocks=None) -> None:
+        ss_set_launch(self.ctx, tile_shape, blocks)
 
     def minimise(self, tol: float, max_steps: int):
         return ss_minimise(self.ctx, tol, max_steps)
