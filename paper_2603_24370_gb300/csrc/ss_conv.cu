@@ -14,9 +14,10 @@
 // memory-bound kernels) so that K is contiguous; the tap's row shift is a TMA
 // coordinate and its column shift selects one of three pre-shifted copies.
 //
-// Warp roles (128 threads): warp 0 allocates TMEM and lane 0 drives the TMA
-// pipeline; warp 1 lane 0 issues the MMAs; afterwards all four warps drain the
-// accumulator (warp w owns TMEM lanes 32w..32w+31, one output row per thread).
+// The convolution kernel is persistent with three warp roles (see k_conv3x3_p); the
+// weight gradient uses one CTA per (tap, pixel range): warp 0 allocates TMEM and
+// lane 0 drives the TMA pipeline, warp 1 lane 0 issues the MMAs, then all four warps
+// drain the accumulator (warp w owns TMEM lanes 32w..32w+31, one row per thread).
 // Every mbarrier wait is bounded: on time-out the kernel records the failure in
 // `err`, waits (bounded) for its copies in flight, frees TMEM and returns.
 #include <cuda.h>
@@ -78,36 +79,65 @@ __device__ __forceinline__ void drain_stages(uint64_t* full, int issued) {
   }
 }
 
-// ---------------------------------------------------------------- implicit GEMM conv
+// ---------------------------------------------------------------- persistent conv
+// The same implicit GEMM, persistent: each CTA walks tiles blockIdx.x, +gridDim.x,
+// ... with three roles (192 threads): warp 0 lane 0 streams the activation boxes
+// (and, once, the whole weight matrix when it fits in shared memory) through a
+// STAGES-deep ring; warp 1 lane 0 issues the MMAs into one of two TMEM
+// accumulators; warps 2..5 drain the other accumulator into the epilogue, so a
+// tile's epilogue overlaps the next tile's MMAs. TMEM lanes: warp w reads the
+// quarter w % 4. Every wait is bounded (2 s); on time-out the roles stop, the
+// failure is recorded in `err`, TMEM is freed and the kernel returns.
+constexpr int P_STAGES = 4;
+constexpr int W_RESIDENT_MAX = 64 * 1024;  // weight bytes kept in shared memory
+
+__host__ __device__ constexpr int ptcols(int bn) {
+  return 2 * bn <= 32 ? 32 : 2 * bn <= 64 ? 64 : 2 * bn <= 128 ? 128 : 2 * bn <= 256 ? 256 : 512;
+}
+
+struct PConvArgs {
+  ConvArgs c;
+  int tiles;
+  int resident;  // 1: all weight groups in shared memory, loaded once
+  int wbytes;    // BN * K * 2
+};
+
 template <int BN>
-__global__ void __launch_bounds__(128) k_conv3x3(const __grid_constant__ CUtensorMap mx,
-                                                 const __grid_constant__ CUtensorMap mw, const ConvArgs a) {
+__global__ void __launch_bounds__(192) k_conv3x3_p(const __grid_constant__ CUtensorMap mx,
+                                                   const __grid_constant__ CUtensorMap mw, const PConvArgs pa) {
   extern __shared__ unsigned char smraw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+  const ConvArgs& a = pa.c;
   constexpr int A_BYTES = GPS * BM * 16;
-  constexpr int STAGE = stage_bytes<BN>();
-  constexpr int TCOLS = tmem_cols(BN);
-  __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], accum;
+  constexpr int TCOLS = ptcols(BN);
+  const bool resident = pa.resident != 0;
+  const int stage = A_BYTES + (resident ? 0 : GPS * BN * 16);
+  unsigned char* wsm = smem + P_STAGES * stage;  // resident weights: group g at g * BN * 16
+  __shared__ __align__(8) uint64_t full[P_STAGES], empty[P_STAGES], tfull[2], tempty[2], wbar;
   __shared__ uint32_t tmem_base;
+  __shared__ int s_fail;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   const int W = a.W, H = a.H;
-  const int Wt = W < BM ? W : BM;  // tile columns
-  const int rows = BM / Wt;        // tile rows
+  const int Wt = W < BM ? W : BM;
+  const int rows = BM / Wt;
   const int tpr = W / Wt;
   const int tpi = (H / rows) * tpr;
-  const int n = blockIdx.x / tpi, r = blockIdx.x % tpi;
-  const int y0 = (r / tpr) * rows, x0 = (r % tpr) * Wt;
   const int cg = a.Cin >> 3;
   const int G = 9 * cg;
   const int nkb = (G + GPS - 1) / GPS;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
+    for (int s = 0; s < P_STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(&accum, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 4);
+    }
+    mbar_init(&wbar, 1);
+    s_fail = 0;
     fence_mbar_init();
   }
   if (warp == 0) {
@@ -119,91 +149,140 @@ __global__ void __launch_bounds__(128) k_conv3x3(const __grid_constant__ CUtenso
   fence_after_sync();
   const uint32_t tmem = tmem_base;
 
-  if (warp == 0 && lane == 0) {
-    int issued = 0;
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % STAGES;
-      if (!mbar_wait(&empty[s], (uint32_t)(((kb / STAGES) & 1) ^ 1), WAIT_NS)) {
-        record_fail(a.err, 1);
-        break;
+  if (warp == 0) {
+    if (lane == 0) {  // ---- producer
+      if (resident) {
+        mbar_arrive_expect_tx(&wbar, (uint32_t)(G * BN * 16));
+        for (int g = 0; g < G; ++g) tma_load_2d(wsm + g * (BN * 16), &mw, &wbar, g * 8, 0);
       }
-      unsigned char* sa = smem + s * STAGE;
-      unsigned char* sb = sa + A_BYTES;
-      const int g0 = kb * GPS, ng = min(GPS, G - g0);
-      mbar_arrive_expect_tx(&full[s], (uint32_t)(ng * (BM + BN) * 16));
-      for (int j = 0; j < ng; ++j) {
-        const int gg = g0 + j, tap = gg / cg, c0 = (gg - tap * cg) * 8;
-        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
-        tma_load_4d(sa + j * (BM * 16), &mx, &full[s], c0, x0 + dx, y0 + dy, n);
-        tma_load_2d(sb + j * (BN * 16), &mw, &full[s], gg * 8, 0);
+      int q = 0;  // k-blocks issued so far (ring position)
+      for (int t = blockIdx.x; t < pa.tiles && !*static_cast<volatile int*>(&s_fail); t += gridDim.x) {
+        const int n = t / tpi, r = t % tpi;
+        const int y0 = (r / tpr) * rows, x0 = (r % tpr) * Wt;
+        for (int kb = 0; kb < nkb; ++kb, ++q) {
+          const int s = q % P_STAGES;
+          if (!mbar_wait(&empty[s], (uint32_t)(((q / P_STAGES) & 1) ^ 1), WAIT_NS)) {
+            record_fail(a.err, 21);
+            s_fail = 1;
+            break;
+          }
+          unsigned char* sa = smem + s * stage;
+          unsigned char* sb = sa + A_BYTES;
+          const int g0 = kb * GPS, ng = min(GPS, G - g0);
+          mbar_arrive_expect_tx(&full[s], (uint32_t)(ng * (BM + (resident ? 0 : BN)) * 16));
+          for (int j = 0; j < ng; ++j) {
+            const int gg = g0 + j, tap = gg / cg, c0 = (gg - tap * cg) * 8;
+            tma_load_4d(sa + j * (BM * 16), &mx, &full[s], c0, x0 + tap % 3 - 1, y0 + tap / 3 - 1, n);
+            if (!resident) tma_load_2d(sb + j * (BN * 16), &mw, &full[s], gg * 8, 0);
+          }
+        }
       }
-      issued = kb + 1;
+      // every issued copy has landed before the CTA may end (bounded)
+      for (int s = 0; s < P_STAGES && s < q; ++s) {
+        const int last = s + P_STAGES * ((q - 1 - s) / P_STAGES);
+        mbar_wait(&full[s], (uint32_t)((last / P_STAGES) & 1), WAIT_NS);
+      }
+      if (resident) mbar_wait(&wbar, 0, WAIT_NS);
     }
-    drain_stages(full, issued);
-  } else if (warp == 1 && lane == 0) {
-    constexpr uint32_t idesc = idesc_bf16(BM, BN);
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % STAGES;
-      if (!mbar_wait(&full[s], (uint32_t)((kb / STAGES) & 1), WAIT_NS)) {
-        record_fail(a.err, 2);
+  } else if (warp == 1) {
+    if (lane == 0) {  // ---- MMA issuer
+      constexpr uint32_t idesc = idesc_bf16(BM, BN);
+      bool ok = !resident || mbar_wait(&wbar, 0, WAIT_NS);
+      if (!ok) {
+        record_fail(a.err, 22);
+        s_fail = 1;
+      }
+      const uint32_t wbase = smem_u32(wsm);
+      int q = 0, it = 0;
+      for (int t = blockIdx.x; ok && t < pa.tiles && !*static_cast<volatile int*>(&s_fail); t += gridDim.x, ++it) {
+        const int b = it & 1;
+        if (!mbar_wait(&tempty[b], (uint32_t)(((it >> 1) & 1) ^ 1), WAIT_NS)) {
+          record_fail(a.err, 23);
+          s_fail = 1;
+          break;
+        }
+        fence_after_sync();
+        const uint32_t acc = tmem + (uint32_t)(b * BN);
+        for (int kb = 0; kb < nkb; ++kb, ++q) {
+          const int s = q % P_STAGES;
+          if (!mbar_wait(&full[s], (uint32_t)((q / P_STAGES) & 1), WAIT_NS)) {
+            record_fail(a.err, 24);
+            s_fail = 1;
+            ok = false;
+            break;
+          }
+          fence_after_sync();
+          const uint32_t sa = smem_u32(smem + s * stage), sb = sa + A_BYTES;
+          const int g0 = kb * GPS, ng = min(GPS, G - g0);
+          for (int j = 0; j < ng; j += 2) {
+            const uint64_t ad = sdesc(sa + j * (BM * 16), BM * 16, 128);
+            const uint64_t bd = resident ? sdesc(wbase + (g0 + j) * (BN * 16), BN * 16, 128)
+                                         : sdesc(sb + j * (BN * 16), BN * 16, 128);
+            mma_bf16(acc, ad, bd, idesc, (kb > 0 || j > 0) ? 1u : 0u);
+          }
+          mma_commit(&empty[s]);
+        }
+        mma_commit(&tfull[b]);
+      }
+    }
+  } else {
+    // ---- epilogue warps 2..5: TMEM lane quarter warp % 4
+    const int qd = warp & 3;
+    const int m = qd * 32 + lane;
+    int it = 0;
+    for (int t = blockIdx.x; t < pa.tiles; t += gridDim.x, ++it) {
+      const int b = it & 1;
+      bool ok = mbar_wait(&tfull[b], (uint32_t)((it >> 1) & 1), WAIT_NS);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) {
+        if (lane == 0) {
+          record_fail(a.err, 25);
+          s_fail = 1;
+        }
         break;
       }
       fence_after_sync();
-      const uint32_t sa = smem_u32(smem + s * STAGE), sb = sa + A_BYTES;
-      const int ng = min(GPS, G - kb * GPS);
-      for (int j = 0; j < ng; j += 2) {
-        const uint64_t ad = sdesc(sa + j * (BM * 16), BM * 16, 128);
-        const uint64_t bd = sdesc(sb + j * (BN * 16), BN * 16, 128);
-        mma_bf16(tmem, ad, bd, idesc, (kb > 0 || j > 0) ? 1u : 0u);
-      }
-      mma_commit(&empty[s]);
-    }
-    mma_commit(&accum);
-  }
-  __syncwarp();
-
-  // ---- epilogue: one output pixel per thread
-  bool ok = mbar_wait(&accum, 0, WAIT_NS);
-  ok = __all_sync(0xffffffffu, ok);
-  fence_after_sync();
-  if (!ok) {
-    if (lane == 0) record_fail(a.err, 3);
-  } else {
-    const int m = warp * 32 + lane;
-    const int yy = y0 + m / Wt, xx = x0 + m % Wt;
-    const size_t pix = ((size_t)n * H + yy) * W + xx;
-    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+      const int n = t / tpi, r = t % tpi;
+      const int y0 = (r / tpr) * rows, x0 = (r % tpr) * Wt;
+      const int yy = y0 + m / Wt, xx = x0 + m % Wt;
+      const size_t pix = ((size_t)n * H + yy) * W + xx;
+      const uint32_t trow = tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(b * BN);
 #pragma unroll 1
-    for (int c = 0; c < BN; c += 16) {
-      float v[16];
-      tmem_ld16(trow + (uint32_t)c, v);
-      if (c >= a.Cout) continue;
-      if (a.mode == CONV_BF16_BIAS_RELU) {
-        __nv_bfloat16* o = static_cast<__nv_bfloat16*>(a.out) + pix * a.out_cs + a.out_coff + c;
-        uint32_t w[8];
+      for (int c = 0; c < BN; c += 16) {
+        float v[16];
+        tmem_ld16(trow + (uint32_t)c, v);
+        if (c >= a.Cout) continue;
+        if (a.mode == CONV_BF16_BIAS_RELU) {
+          __nv_bfloat16* o = static_cast<__nv_bfloat16*>(a.out) + pix * a.out_cs + a.out_coff + c;
+          uint32_t w[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const float lo = fmaxf(v[2 * i] + __ldg(a.bias + c + 2 * i), 0.f);
-          const float hi = fmaxf(v[2 * i + 1] + __ldg(a.bias + c + 2 * i + 1), 0.f);
-          __nv_bfloat162 b2 = __floats2bfloat162_rn(lo, hi);
-          w[i] = *reinterpret_cast<uint32_t*>(&b2);
-        }
-        uint4* o4 = reinterpret_cast<uint4*>(o);
-        o4[0] = make_uint4(w[0], w[1], w[2], w[3]);
-        o4[1] = make_uint4(w[4], w[5], w[6], w[7]);
-      } else {
-        float* o = static_cast<float*>(a.out) + pix * a.out_cs + a.out_coff + c;
-        const bool b = a.mode == CONV_F32_BIAS;
+          for (int i = 0; i < 8; ++i) {
+            const float lo = fmaxf(v[2 * i] + __ldg(a.bias + c + 2 * i), 0.f);
+            const float hi = fmaxf(v[2 * i + 1] + __ldg(a.bias + c + 2 * i + 1), 0.f);
+            __nv_bfloat162 b2 = __floats2bfloat162_rn(lo, hi);
+            w[i] = *reinterpret_cast<uint32_t*>(&b2);
+          }
+          uint4* o4 = reinterpret_cast<uint4*>(o);
+          o4[0] = make_uint4(w[0], w[1], w[2], w[3]);
+          o4[1] = make_uint4(w[4], w[5], w[6], w[7]);
+        } else {
+          float* o = static_cast<float*>(a.out) + pix * a.out_cs + a.out_coff + c;
+          const bool bb = a.mode == CONV_F32_BIAS;
 #pragma unroll
-        for (int i = 0; i < 16; i += 4) {
-          float4 q;
-          q.x = v[i] + (b ? __ldg(a.bias + c + i) : 0.f);
-          q.y = v[i + 1] + (b ? __ldg(a.bias + c + i + 1) : 0.f);
-          q.z = v[i + 2] + (b ? __ldg(a.bias + c + i + 2) : 0.f);
-          q.w = v[i + 3] + (b ? __ldg(a.bias + c + i + 3) : 0.f);
-          *reinterpret_cast<float4*>(o + i) = q;
+          for (int i = 0; i < 16; i += 4) {
+            float4 qv;
+            qv.x = v[i] + (bb ? __ldg(a.bias + c + i) : 0.f);
+            qv.y = v[i + 1] + (bb ? __ldg(a.bias + c + i + 1) : 0.f);
+            qv.z = v[i + 2] + (bb ? __ldg(a.bias + c + i + 2) : 0.f);
+            qv.w = v[i + 3] + (bb ? __ldg(a.bias + c + i + 3) : 0.f);
+            *reinterpret_cast<float4*>(o + i) = qv;
+          }
         }
       }
+      // the accumulator is read: hand it back to the MMA issuer
+      fence_before_sync();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[b]);
     }
   }
   fence_before_sync();
@@ -354,14 +433,27 @@ cudaError_t make_map(CUtensorMap* m, const void* base, int r, const cuuint64_t* 
 }
 
 template <int BN>
-cudaError_t conv_launch(const CUtensorMap& mx, const CUtensorMap& mw, const ConvArgs& a, int tiles, cudaStream_t s) {
-  static bool attr = false;  // set once per process (per instantiation)
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_conv3x3<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_smem<BN>());
+cudaError_t conv_launch_p(const CUtensorMap& mx, const CUtensorMap& mw, const ConvArgs& a, int tiles, int K,
+                          cudaStream_t s) {
+  PConvArgs pa{a, tiles, 0, BN * K * 2};
+  pa.resident = pa.wbytes <= W_RESIDENT_MAX ? 1 : 0;
+  const size_t smem = (size_t)P_STAGES * (GPS * BM * 16 + (pa.resident ? 0 : GPS * BN * 16)) +
+                      (pa.resident ? (size_t)pa.wbytes : 0) + 1024;
+  static int max_smem_set = 0;  // per instantiation, under g_attr_mu
+  if ((int)smem > max_smem_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_conv3x3_p<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    attr = true;
+    max_smem_set = (int)smem;
   }
-  k_conv3x3<BN><<<tiles, 128, conv_smem<BN>(), s>>>(mx, mw, a);
+  int dev = 0, nsm = 0, occ = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_conv3x3_p<BN>, 192, smem);
+  const int by_tmem = 512 / ptcols(BN);
+  int per_sm = occ < by_tmem ? occ : by_tmem;
+  if (per_sm < 1) per_sm = 1;
+  const int grid = tiles < nsm * per_sm ? tiles : nsm * per_sm;
+  k_conv3x3_p<BN><<<grid, 192, smem, s>>>(mx, mw, pa);
   return cudaGetLastError();
 }
 
@@ -411,7 +503,7 @@ cudaError_t conv3x3_tc(const Act& x, const void* w, int Cout, int mode, const fl
     const cuuint32_t wbox[2] = {8, (cuuint32_t)BNV};        \
     e = make_map(&mw, w, 2, wd, ws, wbox);                  \
     if (e != cudaSuccess) return e;                         \
-    return conv_launch<BNV>(mx, mw, a, tiles, s);           \
+    return conv_launch_p<BNV>(mx, mw, a, tiles, K, s);      \
   }
   switch (Cout) {
     SS_CONV_CASE(16)
