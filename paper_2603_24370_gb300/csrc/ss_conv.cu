@@ -405,6 +405,166 @@ __global__ void __launch_bounds__(128) k_wgrad3x3(const __grid_constant__ CUtens
   }
 }
 
+
+// ---------------------------------------------------------------- weight gradient, 64-pixel K-blocks
+// For rows of at least 64 pixels: each K-block is 64 consecutive pixels of one image
+// row, fetched as one 128-byte-swizzled TMA box per operand (the output gradient,
+// M = 128 rows of output channels, zero beyond Cout; and the shifted input of each
+// tap, N = Cin rows). With 9 Cin <= 512 TMEM columns one CTA accumulates all nine
+// taps (TPC = 9), so the output-gradient tile is loaded once per K-block.
+struct WgSwArgs {
+  int N, H, W, Cout, Cin;
+  int kb_per_cta, total_kb;
+  int stages;
+  float* dw;
+  int* err;
+};
+
+template <int BN, int TPC>
+__global__ void __launch_bounds__(128) k_wgrad_sw(const __grid_constant__ CUtensorMap mdy,
+                                                  const __grid_constant__ CUtensorMap mx0,
+                                                  const __grid_constant__ CUtensorMap mx1,
+                                                  const __grid_constant__ CUtensorMap mx2, const WgSwArgs a) {
+  extern __shared__ unsigned char smraw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+  constexpr int A_BYTES = BM * 128;
+  constexpr int B_BYTES = BN * 128;
+  constexpr int STAGE = A_BYTES + TPC * B_BYTES;
+  constexpr int NCOL = TPC * BN;
+  constexpr int TCOLS = NCOL <= 32 ? 32 : NCOL <= 64 ? 64 : NCOL <= 128 ? 128 : NCOL <= 256 ? 256 : 512;
+  constexpr int MAXS = 4;
+  __shared__ __align__(8) uint64_t full[MAXS], empty[MAXS], accum;
+  __shared__ uint32_t tmem_base;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int S = a.stages;
+  const int tap0 = blockIdx.y * TPC;
+  const int kb0 = blockIdx.x * a.kb_per_cta;
+  const int kb1 = min(kb0 + a.kb_per_cta, a.total_kb);
+  const int nkb = kb1 > kb0 ? kb1 - kb0 : 0;
+  const int HW = a.H * a.W;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < MAXS; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(&accum, 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(&tmem_base, TCOLS);
+    tmem_relinquish();
+  }
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = tmem_base;
+
+  if (warp == 0 && lane == 0) {
+    int issued = 0;
+    for (int i = 0; i < nkb; ++i) {
+      const int s = i % S;
+      if (!mbar_wait(&empty[s], (uint32_t)(((i / S) & 1) ^ 1), WAIT_NS)) {
+        record_fail(a.err, 31);
+        break;
+      }
+      unsigned char* sa = smem + s * STAGE;
+      const int p0 = (kb0 + i) * 64;
+      const int n = p0 / HW, rem = p0 - n * HW;
+      const int y = rem / a.W, x = rem - y * a.W;
+      mbar_arrive_expect_tx(&full[s], (uint32_t)STAGE);
+      tma_load_4d(sa, &mdy, &full[s], x, y, n, 0);
+#pragma unroll
+      for (int j = 0; j < TPC; ++j) {
+        const int tap = tap0 + j, dy = tap / 3 - 1, dx = tap % 3 - 1;
+        const CUtensorMap* mx = dx < 0 ? &mx0 : (dx == 0 ? &mx1 : &mx2);
+        tma_load_4d(sa + A_BYTES + j * B_BYTES, mx, &full[s], x, y + dy, n, 0);
+      }
+      issued = i + 1;
+    }
+    for (int s = 0; s < S && s < issued; ++s) {
+      const int last = s + S * ((issued - 1 - s) / S);
+      mbar_wait(&full[s], (uint32_t)((last / S) & 1), WAIT_NS);
+    }
+  } else if (warp == 1 && lane == 0) {
+    constexpr uint32_t idesc = idesc_bf16(BM, BN);
+    for (int i = 0; i < nkb; ++i) {
+      const int s = i % S;
+      if (!mbar_wait(&full[s], (uint32_t)((i / S) & 1), WAIT_NS)) {
+        record_fail(a.err, 32);
+        break;
+      }
+      fence_after_sync();
+      const uint32_t sa = smem_u32(smem + s * STAGE);
+#pragma unroll
+      for (int j = 0; j < TPC; ++j) {
+        const uint32_t sb = sa + A_BYTES + j * B_BYTES;
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+          mma_bf16(tmem + (uint32_t)(j * BN), sdesc_sw128(sa + kk * 32), sdesc_sw128(sb + kk * 32), idesc,
+                   (i > 0 || kk > 0) ? 1u : 0u);
+      }
+      mma_commit(&empty[s]);
+    }
+    mma_commit(&accum);
+  }
+  __syncwarp();
+
+  bool ok = nkb > 0 ? mbar_wait(&accum, 0, WAIT_NS) : false;
+  ok = __all_sync(0xffffffffu, ok);
+  fence_after_sync();
+  if (!ok) {
+    if (lane == 0 && nkb > 0) record_fail(a.err, 33);
+  } else {
+    const int co = warp * 32 + lane;
+    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+    for (int j = 0; j < TPC; ++j) {
+#pragma unroll 1
+      for (int c = 0; c < BN; c += 16) {
+        float v[16];
+        tmem_ld16(trow + (uint32_t)(j * BN + c), v);
+        if (co < a.Cout) {
+          float* d = a.dw + ((size_t)co * 9 + tap0 + j) * a.Cin + c;
+#pragma unroll
+          for (int q = 0; q < 16; ++q) atomicAdd(d + q, v[q]);
+        }
+      }
+    }
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    fence_after_sync();
+    tmem_dealloc(tmem, TCOLS);
+  }
+}
+
+template <int BN, int TPC>
+cudaError_t wgrad_sw_launch(const CUtensorMap& mdy, const CUtensorMap* mx, WgSwArgs a, cudaStream_t s) {
+  constexpr int STAGE = BM * 128 + TPC * BN * 128;
+  int stages = (110 * 1024) / STAGE;
+  stages = stages < 2 ? 2 : (stages > 4 ? 4 : stages);
+  a.stages = stages;
+  const size_t smem = (size_t)stages * STAGE + 1024;
+  static int max_smem_set = 0;
+  if ((int)smem > max_smem_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_wgrad_sw<BN, TPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    max_smem_set = (int)smem;
+  }
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int ytaps = 9 / TPC;
+  int splits = (nsm * 2 + ytaps - 1) / ytaps;  // about two CTAs per SM in total
+  a.kb_per_cta = (a.total_kb + splits - 1) / splits;
+  if (a.kb_per_cta < 4) a.kb_per_cta = 4;
+  splits = (a.total_kb + a.kb_per_cta - 1) / a.kb_per_cta;
+  k_wgrad_sw<BN, TPC><<<dim3(splits, ytaps), 128, smem, s>>>(mdy, mx[0], mx[1], mx[2], a);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- tensor maps
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -422,12 +582,13 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 // BF16 tensor map of rank r: dims[0] innermost (elements), strides in bytes for
 // dims 1..r-1, box per dim; out-of-bounds elements read as zero.
 cudaError_t make_map(CUtensorMap* m, const void* base, int r, const cuuint64_t* dims, const cuuint64_t* strides,
-                     const cuuint32_t* box) {
+                     const cuuint32_t* box, bool swizzle128 = false) {
   auto fn = encode_fn();
   if (!fn) return cudaErrorNotSupported;
   cuuint32_t es[5] = {1, 1, 1, 1, 1};
   const CUresult rc = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)r, const_cast<void*>(base), dims, strides,
-                         box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return rc == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
@@ -526,10 +687,38 @@ cudaError_t wgrad3x3_tc(const void* dyT, const void* xT, int N, int H, int W, in
   CUtensorMap mdy, mx[3];
   const cuuint64_t dd[4] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)N, (cuuint64_t)Cout};
   const cuuint64_t st[3] = {(cuuint64_t)W * 2, (cuuint64_t)W * H * 2, (cuuint64_t)P * 2};
-  const cuuint32_t dbox[4] = {8, 1, 1, 128};
-  cudaError_t e = make_map(&mdy, dyT, 4, dd, st, dbox);
-  if (e != cudaSuccess) return e;
   const cuuint64_t xd[4] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)N, (cuuint64_t)Cin};
+  cudaError_t e;
+  if (W % 64 == 0) {  // 64-pixel K-blocks in 128-byte-swizzled boxes
+    const cuuint32_t dbox[4] = {64, 1, 1, 128};
+    e = make_map(&mdy, dyT, 4, dd, st, dbox, true);
+    if (e != cudaSuccess) return e;
+    WgSwArgs a{N, H, W, Cout, Cin, 0, (int)(P / 64), 0, dw, err};
+    std::lock_guard<std::mutex> lock(g_attr_mu);
+#define SS_WGS_CASE(BNV, TPCV)                                                                          \
+  case BNV: {                                                                                           \
+    const cuuint32_t xbox[4] = {64, 1, 1, (cuuint32_t)BNV};                                             \
+    for (int d = 0; d < 3; ++d) {                                                                       \
+      e = make_map(&mx[d], static_cast<const char*>(xT) + (size_t)d * Cin * P * 2, 4, xd, st, xbox, true); \
+      if (e != cudaSuccess) return e;                                                                   \
+    }                                                                                                   \
+    return wgrad_sw_launch<BNV, TPCV>(mdy, mx, a, s);                                                   \
+  }
+    switch (Cin) {
+      SS_WGS_CASE(16, 9)
+      SS_WGS_CASE(32, 9)
+      SS_WGS_CASE(48, 9)
+      SS_WGS_CASE(80, 1)
+      SS_WGS_CASE(96, 1)
+      SS_WGS_CASE(144, 1)
+      default:
+        return cudaErrorInvalidValue;
+    }
+#undef SS_WGS_CASE
+  }
+  const cuuint32_t dbox[4] = {8, 1, 1, 128};
+  e = make_map(&mdy, dyT, 4, dd, st, dbox);
+  if (e != cudaSuccess) return e;
   // K-groups split over CTAs: about 4 waves of 9-tap grids over 152 SMs, even counts
   const int total = (int)(P / 8);
   int splits = (152 * 4 + 8) / 9;
