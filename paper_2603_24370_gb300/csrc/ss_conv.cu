@@ -524,10 +524,10 @@ __global__ void __launch_bounds__(128) k_wgrad_sw(const __grid_constant__ CUtens
       for (int c = 0; c < BN; c += 16) {
         float v[16];
         tmem_ld16(trow + (uint32_t)(j * BN + c), v);
-        if (co < a.Cout) {
-          float* d = a.dw + ((size_t)co * 9 + tap0 + j) * a.Cin + c;
+        if (co < a.Cout) {  // 16-byte vector atomics (dw rows are 16-byte aligned: Cin % 16 == 0)
+          float4* d = reinterpret_cast<float4*>(a.dw + ((size_t)co * 9 + tap0 + j) * a.Cin + c);
 #pragma unroll
-          for (int q = 0; q < 16; ++q) atomicAdd(d + q, v[q]);
+          for (int q = 0; q < 4; ++q) atomicAdd(d + q, make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]));
         }
       }
     }
@@ -557,7 +557,9 @@ cudaError_t wgrad_sw_launch(const CUtensorMap& mdy, const CUtensorMap* mx, WgSwA
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const int ytaps = 9 / TPC;
-  int splits = (nsm * 2 + ytaps - 1) / ytaps;  // about two CTAs per SM in total
+  // one wave: every CTA adds its partial sums once, so fewer, longer CTAs also mean
+  // fewer atomics on the same weight-gradient entries
+  int splits = (nsm + ytaps - 1) / ytaps;
   a.kb_per_cta = (a.total_kb + splits - 1) / splits;
   if (a.kb_per_cta < 4) a.kb_per_cta = 4;
   splits = (a.total_kb + a.kb_per_cta - 1) / a.kb_per_cta;
@@ -606,12 +608,16 @@ cudaError_t conv_launch_p(const CUtensorMap& mx, const CUtensorMap& mw, const Co
     if (e != cudaSuccess) return e;
     max_smem_set = (int)smem;
   }
-  int dev = 0, nsm = 0, occ = 1;
+  // CTAs per SM from the shared-memory budget (1 KB reserved per CTA), the 512 TMEM
+  // columns and the thread limit
+  int dev = 0, nsm = 0, sm_smem = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_conv3x3_p<BN>, 192, smem);
+  cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  const int by_smem = sm_smem / (int)(smem + 2048);
   const int by_tmem = 512 / ptcols(BN);
-  int per_sm = occ < by_tmem ? occ : by_tmem;
+  int per_sm = by_smem < by_tmem ? by_smem : by_tmem;
+  if (per_sm > 2048 / 192) per_sm = 2048 / 192;
   if (per_sm < 1) per_sm = 1;
   const int grid = tiles < nsm * per_sm ? tiles : nsm * per_sm;
   k_conv3x3_p<BN><<<grid, 192, smem, s>>>(mx, mw, pa);

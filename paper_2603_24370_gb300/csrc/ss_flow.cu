@@ -366,8 +366,9 @@ __global__ void __launch_bounds__(NT)
     const int x0 = (lt % D.ntx) * T::TX, y0 = (lt / D.ntx) * T::TY;
 
     // ---- stage inputs over the tile and its halo, LU sites per iteration (the loads
-    // of all LU sites are issued before any is used: more bytes in flight per thread)
-    constexpr int LU = 2;
+    // of all LU sites are issued before any is used: more bytes in flight per thread;
+    // measured best: 3 for pass 1, 2 for pass 2, whose loads per site are heavier)
+    constexpr int LU = PASS == 1 ? 3 : 2;
     for (int base = tid; base < T::SXY; base += LU * NT) {
       R pv[LU][C], lv[LU][C], vv[LU][C], k1v[LU][C], k2v[LU][C], pp[LU][C], lp[LU][C];
       bool in[LU], inside[LU];

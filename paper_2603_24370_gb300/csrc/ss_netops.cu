@@ -171,12 +171,95 @@ __global__ void k_add_slice(const float* __restrict__ src, int cs, int off, size
   }
 }
 
+// One image row per block: the row's C channels are staged in shared memory as
+// [C][W + 2] (the padding staggers the channels across banks), then each thread
+// writes 8 consecutive pixels of one channel of one shifted copy as a 16-byte store.
+__global__ void k_shifted_transpose_rows(const Act x, __nv_bfloat16* __restrict__ xT) {
+  extern __shared__ __nv_bfloat16 row[];  // [C][W + 2]
+  const size_t P = (size_t)x.N * x.H * x.W;
+  const int W = x.W, C = x.C, cg = C / 8, RS = W + 2;
+  const int nrows = x.N * x.H;
+  const __nv_bfloat16 zero = __float2bfloat16(0.f);
+  for (int rr = blockIdx.x; rr < nrows; rr += gridDim.x) {
+    const size_t pix0 = (size_t)rr * W;
+    __syncthreads();  // the previous row's reads are done
+    for (int i = threadIdx.x; i < W * cg; i += blockDim.x) {
+      const int xx = i / cg, c0 = (i - xx * cg) * 8;
+      const uint4 v = *reinterpret_cast<const uint4*>(act_ptr(x, pix0 + xx) + c0);
+      const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&v);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) row[(c0 + k) * RS + xx] = e[k];
+    }
+    __syncthreads();
+    const int chunks = W / 8;
+    for (int i = threadIdx.x; i < 3 * C * chunks; i += blockDim.x) {
+      const int d = i / (C * chunks), rem = i - d * C * chunks;
+      const int c = rem / chunks, x0 = (rem - c * chunks) * 8;
+      uint4 o;
+      __nv_bfloat16* oe = reinterpret_cast<__nv_bfloat16*>(&o);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int src = x0 + k + d - 1;  // copy d holds x[x + d - 1]
+        oe[k] = (src >= 0 && src < W) ? row[c * RS + src] : zero;
+      }
+      *reinterpret_cast<uint4*>(xT + ((size_t)d * C + c) * P + pix0 + x0) = o;
+    }
+  }
+}
+
+// dy (FP32 NHWC) -> masked gradient: BF16 NHWC (dyb) and channel-major (dyT), and the
+// bias gradient. A block takes 128 pixels at a time, stages the BF16 values as
+// [C][128] in shared memory for the channel-major writes, and sums each channel's
+// FP32 values there (one atomic per channel per block at the end).
+constexpr int RG_TP = 128;
+__global__ void k_relu_grad_tiles(const float* __restrict__ dy, const Act yact, int has_mask, size_t P, int C,
+                                  __nv_bfloat16* __restrict__ dyb, __nv_bfloat16* __restrict__ dyT,
+                                  float* __restrict__ dbias) {
+  extern __shared__ unsigned char rg_smem[];
+  float* g = reinterpret_cast<float*>(rg_smem);                       // [RG_TP][C] FP32
+  float* csum = g + RG_TP * C;                                        // [C]
+  for (int c = threadIdx.x; c < C; c += blockDim.x) csum[c] = 0.f;
+  const size_t ntiles = (P + RG_TP - 1) / RG_TP;
+  for (size_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const size_t pix0 = tile * RG_TP;
+    const int np = (int)((P - pix0) < (size_t)RG_TP ? (P - pix0) : (size_t)RG_TP);
+    __syncthreads();
+    for (int i = threadIdx.x; i < np * C; i += blockDim.x) {  // NHWC order: coalesced
+      const int pp = i / C, c = i - pp * C;
+      const size_t e = (pix0 + pp) * C + c;
+      float v = dy[e];
+      if (has_mask && !(__bfloat162float(act_ptr(yact, pix0 + pp)[c]) > 0.f)) v = 0.f;
+      g[pp * C + c] = v;
+      dyb[e] = __float2bfloat16(v);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < C * np; i += blockDim.x) {  // channel-major: coalesced
+      const int c = i / np, pp = i - c * np;
+      dyT[(size_t)c * P + pix0 + pp] = __float2bfloat16(g[pp * C + c]);
+    }
+    for (int c = threadIdx.x; c < C; c += blockDim.x) {  // per-channel sums of this tile
+      float acc = 0.f;
+      for (int pp = 0; pp < np; ++pp) acc += g[pp * C + c];
+      csum[c] += acc;
+    }
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < C; c += blockDim.x) atomicAdd(&dbias[c], csum[c]);
+}
+
 bool act_ok(const Act& a) { return a.p && a.C % 8 == 0 && a.cs % 8 == 0 && a.off % 8 == 0 && a.off + a.C <= a.cs; }
 
 }  // namespace
 
 cudaError_t shifted_transpose(const Act& x, void* xT, cudaStream_t s) {
   if (!act_ok(x)) return cudaErrorInvalidValue;
+  const size_t row_bytes = (size_t)x.C * (x.W + 2) * sizeof(__nv_bfloat16);
+  if (row_bytes <= 48 * 1024 && x.W % 8 == 0) {  // one image row per block, staged in shared memory
+    const int rows = x.N * x.H;
+    k_shifted_transpose_rows<<<grid_for((size_t)rows * 256) < rows ? grid_for((size_t)rows * 256) : rows, 256,
+                               row_bytes, s>>>(x, static_cast<__nv_bfloat16*>(xT));
+    return cudaGetLastError();
+  }
   const size_t n = (size_t)x.N * x.H * x.W * (x.C / 8);
   k_shifted_transpose<<<grid_for(n), 256, 0, s>>>(x, static_cast<__nv_bfloat16*>(xT));
   return cudaGetLastError();
@@ -187,6 +270,15 @@ cudaError_t relu_grad(const float* dy, const Act* y_act, int N, int H, int W, in
   const size_t P = (size_t)N * H * W;
   Act y{};
   if (y_act) y = *y_act;
+  const size_t smem = (size_t)(RG_TP + 1) * C * sizeof(float);
+  if (smem <= 48 * 1024) {
+    const size_t ntiles = (P + RG_TP - 1) / RG_TP;
+    int blocks = grid_for(ntiles * 256);
+    if ((size_t)blocks > ntiles) blocks = (int)ntiles;
+    k_relu_grad_tiles<<<blocks, 256, smem, s>>>(dy, y, y_act != nullptr, P, C, static_cast<__nv_bfloat16*>(dy_bf16),
+                                                static_cast<__nv_bfloat16*>(dyT), dbias);
+    return cudaGetLastError();
+  }
   k_relu_grad<<<grid_for(P * C), 256, C * sizeof(float), s>>>(dy, y, y_act != nullptr, P, C,
                                                               static_cast<__nv_bfloat16*>(dy_bf16),
                                                               static_cast<__nv_bfloat16*>(dyT), dbias);
