@@ -17,6 +17,10 @@ again every bench step (ss_set_fields / ss_step / ss_get_fields on host buffers)
 --impl reference: the FP64 CPU oracle on the host cores, same metric, each step one
 oracle flow step on a 512 x 512 crop of the same workload.
 
+--workload configs: time to dx dy max|G| < 1e-6 of the single-problem configurations
+(Abelian Higgs 128^2 FP64, chiral magnet 1024^2, chiral magnet 4096^2) on the GPU and
+with the FP64 oracle on the host cores.
+
 --workload ah-batch: time per solve to dx dy max|G| < 1e-6 on the batched Abelian
 Higgs set (256 problems, sides 64..512, dx = 0.1, lambda ~ U[0.5, 2], N in 1..4):
 one bench step = the whole set relaxed in one batch (compensated FP32), against
@@ -292,6 +296,12 @@ def run_native(args) -> int:
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_sample()
+    solve = None
+    if world == 1 and args.grid == N and not args.no_solve:
+        try:
+            solve = solve_summary(S, I, np)
+        except Exception as exc:  # recorded, never fatal for the throughput line
+            solve = {"error": str(exc)[:200]}
 
     s.close()
     if rank == 0:
@@ -311,6 +321,7 @@ def run_native(args) -> int:
             "gpu_launches": launches_per_call * args.steps,
             "clocks": clk,
             "final_energy": st["energy"], "final_grad_max": st["grad_max"],
+            "time_per_solve": solve,
         }
         print(json.dumps(line))
     if world > 1:
@@ -325,6 +336,39 @@ BATCH_CAP = 40000
 BATCH_WORKLOAD = ("256 Abelian Higgs relaxations in one batch, sides U{64,128,256,512} (halo incl.), dx=0.1, "
                   "lambda U[0.5,2], N U{1..4} unit vortices uniform in the central half, compensated FP32 "
                   "fields + FP64 reductions, to dx dy max|G| < 1e-6")
+
+
+def solve_summary(S, I, np, count: int = 64, fp64_per_side: int = 1) -> dict:
+    """Time per solve of a 64-problem slice of the batched Abelian Higgs set (the
+    ah-batch recipe) relaxed as one compensated-FP32 batch, against the all-FP64 flow
+    one problem at a time on one problem of each side (size-weighted)."""
+    import torch
+    probs = I.ah_batch(count, BATCH_SEED)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b = S.ss_batch_create(S.SS_ABELIAN_HIGGS, S.SS_FP32, probs)
+    S.ss_batch_autotune(b, 4)
+    _, st = S.ss_batch_minimise(b, BATCH_TOL, BATCH_CAP)
+    S.ss_batch_destroy(b)
+    torch.cuda.synchronize()
+    batched = (time.perf_counter() - t0) / count
+    by_side = {}
+    for p in probs:
+        by_side.setdefault(p.nx, []).append(p)
+    t64 = {}
+    for side, ps in sorted(by_side.items()):
+        p = ps[0]
+        with S.Solver(S.SS_ABELIAN_HIGGS, p.params, p.nx, p.ny, p.dx, p.dy, S.SS_FP64) as sv:
+            sv.init_ansatz(p.soliton_array())
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            sv.minimise(BATCH_TOL, BATCH_CAP)
+            torch.cuda.synchronize()
+            t64[side] = time.perf_counter() - t1
+    plain = sum(t64[side] * len(ps) for side, ps in by_side.items()) / count
+    return {"problems": count, "batched_fp32_s_per_solve": batched, "plain_fp64_s_per_solve": plain,
+            "speedup": plain / batched, "converged": sum(1 for x in st if x["converged"]),
+            "fp64_sample": f"{len(t64)} problems, one per side", "tol": BATCH_TOL, "step_cap": BATCH_CAP}
 
 
 def run_solve(args) -> int:
@@ -413,6 +457,87 @@ def run_solve(args) -> int:
     return 0
 
 
+def run_configs(args) -> int:
+    """Time to dx dy max|G| < 1e-6 for each single-problem workload configuration, on
+    the GPU (all-FP64 flow and compensated FP32) and with the FP64 oracle on the host
+    cores (in full where that takes seconds, else its per-step time on a bounded
+    sample times the GPU FP64 step count, stated as such)."""
+    rank, local_rank, world = D.env_rank()
+    if rank != 0:
+        return 0
+    D.pin_visible_device(local_rank, 1)
+    import numpy as np
+    import torch
+    import oracle as O
+    from paper_2603_24370_gb300 import build as B
+    from paper_2603_24370_gb300 import inputs as I
+    from paper_2603_24370_gb300 import soliton as S
+    B.build()
+    O.build()
+    S.load_library()
+
+    def gpu_solve(p, prec, tune=True):
+        with S.Solver(p.theory, p.params, p.nx, p.ny, p.dx, p.dy, prec) as sv:
+            sv.init_ansatz(p.soliton_array())
+            if tune:
+                sv.autotune(4)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = sv.minimise(1e-6, 100000)
+            torch.cuda.synchronize()
+            sec = time.perf_counter() - t0
+            o = sv.observables()
+        return {"seconds": sec, "steps": r["steps"], "converged": bool(r["converged"]), "energy": o["energy"],
+                "charge": o["charge"]}
+
+    def oracle_step_rate(p, n_crop=None, steps=3):
+        nx = n_crop or p.nx
+        sol = p.soliton_array()
+        if n_crop:
+            half = 0.5 * n_crop * p.dx - 4
+            sol = np.array([s for s in sol if abs(s[0]) < half and abs(s[1]) < half]) if len(sol) else sol
+            if len(sol) == 0:
+                sol = p.soliton_array()[:1] * np.array([0, 0, 1, 1, 1])
+        f = O.ansatz(p.theory, sol, nx, nx, p.dx, p.dy)
+        v = np.zeros_like(f)
+        E = O.energy(p.theory, p.params, f, p.dx, p.dy)
+        dt = O.time_step(p.dx, p.dy)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            f, v, E, _ = O.anf_step(p.theory, p.params, f, v, p.dx, p.dy, dt, E)
+        return (time.perf_counter() - t0) / steps, (nx - 4) ** 2
+
+    out = {}
+    # configuration 0: Abelian Higgs 128^2, one vortex, lambda = 1
+    p0 = I.ah_single_vortex()
+    g64 = gpu_solve(p0, S.SS_FP64)
+    f0 = O.ansatz(p0.theory, p0.soliton_array(), p0.nx, p0.ny, p0.dx, p0.dy)
+    t0 = time.perf_counter()
+    r0 = O.minimise(p0.theory, p0.params, f0, p0.dx, p0.dy, 1e-6, 100000)
+    out["ah128_fp64"] = {"gpu_fp64": g64, "gpu_fp32c": gpu_solve(p0, S.SS_FP32),
+                         "oracle": {"seconds": time.perf_counter() - t0, "steps": r0["steps"],
+                                    "converged": r0["converged"], "energy": r0["energy"], "timed": "in full"}}
+    # configuration 1: chiral magnet 1024^2, 8 skyrmions
+    p1 = I.cm_skyrmions()
+    g64 = gpu_solve(p1, S.SS_FP64)
+    sec_step, sites = oracle_step_rate(p1)
+    out["cm1024"] = {"gpu_fp64": g64, "gpu_fp32c": gpu_solve(p1, S.SS_FP32),
+                     "oracle": {"seconds": sec_step * g64["steps"], "steps": g64["steps"],
+                                "timed": f"3 oracle steps on the full grid x the GPU FP64 step count"}}
+    # large: chiral magnet 4096^2, 400 skyrmions (oracle on the 512^2 crop, scaled by sites)
+    p4 = I.cm_skyrmions(n=N, count=COUNT, seed=SEED)
+    g32 = gpu_solve(p4, S.SS_FP32)
+    sec_step, sites = oracle_step_rate(p4, n_crop=CROP)
+    out["cm4096"] = {"gpu_fp32c": g32,
+                     "oracle": {"seconds": sec_step * interior(N) / sites * g32["steps"], "steps": g32["steps"],
+                                "timed": "3 oracle steps on the 512^2 crop, scaled by interior sites and the GPU "
+                                         "FP32 step count"}}
+    line = {"metric": "time to dx dy max|G| < 1e-6 per configuration", "unit": "s", "higher_is_better": False,
+            "n_gpus": 1, "data": "synthetic", "oracle_cores": O.num_threads(), "configs": out}
+    print(json.dumps(line))
+    return 0
+
+
 def main() -> int:
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -421,10 +546,11 @@ def main() -> int:
     ap.add_argument("--impl", choices=("native", "reference"), default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grid", type=int, default=N, help="grid side (default: the 4096 workload; smaller for ncu)")
-    ap.add_argument("--workload", choices=("cm4096", "ah-batch"), default="cm4096")
+    ap.add_argument("--workload", choices=("cm4096", "ah-batch", "configs"), default="cm4096")
     ap.add_argument("--tile-shape", choices=("auto", "0", "1"), default="auto",
                     help="flow tile shape: autotuned (default) or fixed (for profiling one shape)")
     ap.add_argument("--fp64-per-side", type=int, default=2, help="ah-batch: FP64 problems timed per side")
+    ap.add_argument("--no-solve", action="store_true", help="skip the time-per-solve record of the default run")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -432,6 +558,8 @@ def main() -> int:
         return run_reference(args)
     if args.workload == "ah-batch":
         return run_solve(args)
+    if args.workload == "configs":
+        return run_configs(args)
     return run_native(args)
 
 

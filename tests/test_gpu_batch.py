@@ -178,3 +178,34 @@ def test_autotune_keeps_the_fields_and_the_trajectory(S, prec):
     finally:
         S.ss_batch_destroy(b)
         S.ss_batch_destroy(b2)
+
+
+def test_manual_launch_settings_do_not_change_the_flow(S):
+    """The tile shape and grid only regroup the same per-site updates: FP64 fields are
+    bitwise equal across launch settings (the arrest decisions agree here)."""
+    probs = mixed_batch(count=4, seed=8)
+    results = []
+    for ts, blocks in ((1, None), (0, None), (0, [37, 55]), (1, [152, 152])):
+        b = S.ss_batch_create(S.SS_ABELIAN_HIGGS, 2, probs)
+        try:
+            S.ss_batch_set_launch(b, ts, blocks)
+            _, st = S.ss_batch_step(b, 19)
+            fields = []
+            for k, p in enumerate(probs):
+                f = np.empty((4, p.ny, p.nx))
+                S.ss_batch_get_fields(b, k, f)
+                fields.append(f)
+            results.append((st, fields))
+        finally:
+            S.ss_batch_destroy(b)
+    st0, f0 = results[0]
+    for st, f in results[1:]:
+        for k in range(len(probs)):
+            assert st[k]["arrests"] == st0[k]["arrests"]
+            assert np.array_equal(f[k], f0[k]), k
+    with pytest.raises(S.SolitonError):
+        b = S.ss_batch_create(S.SS_ABELIAN_HIGGS, 2, probs)
+        try:
+            S.ss_batch_set_launch(b, 2)
+        finally:
+            S.ss_batch_destroy(b)
