@@ -101,6 +101,14 @@ int ss_conv3x3(const void* x, int N, int H, int W, int Cin, const void* w, int C
 int ss_conv3x3_wgrad(const void* dy, const void* x, int N, int H, int W, int Cout, int Cin, float* dw,
                      void* cuda_stream);
 
+/* Self-test of the failure path (no counterpart in the paper): runs the bounded
+ * mbarrier wait that every tensor-core kernel uses, on a barrier that nothing
+ * completes, with a limit of limit_us microseconds (1..1e6). The wait gives up, the
+ * kernel records the failure and returns, and the call reports SS_ERR_TIMEOUT, the
+ * code the network calls return when one of their waits gives up; the device stays
+ * usable. Returns SS_ERR_STATE if the wait completed. Synchronises `cuda_stream`. */
+int ss_wait_selftest(int limit_us, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

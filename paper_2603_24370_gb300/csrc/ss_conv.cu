@@ -756,4 +756,23 @@ cudaError_t wgrad3x3_tc(const void* dyT, const void* xT, int N, int H, int W, in
 #undef SS_WG_CASE
 }
 
+
+// ---------------------------------------------------------------- wait self-test
+// The bounded mbarrier wait of the kernels above, on a barrier nothing completes:
+// it gives up after limit_ns and records code 99 (the failure path of a stalled copy).
+__global__ void k_wait_selftest(uint64_t limit_ns, int* err) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait(&bar, 0, limit_ns)) record_fail(err, 99);
+}
+
+cudaError_t wait_selftest(uint64_t limit_ns, int* err, cudaStream_t s) {
+  k_wait_selftest<<<1, 32, 0, s>>>(limit_ns, err);
+  return cudaGetLastError();
+}
+
 }  // namespace ss

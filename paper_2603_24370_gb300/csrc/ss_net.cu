@@ -706,3 +706,19 @@ extern "C" int ss_conv3x3_wgrad(const void* dy, const void* x, int N, int H, int
   if (h) return nfail(SS_ERR_TIMEOUT, "ss_conv3x3_wgrad: a wait gave up (code " + std::to_string(h) + ")");
   return SS_OK;
 }
+
+extern "C" int ss_wait_selftest(int limit_us, void* cuda_stream) {
+  if (limit_us < 1 || limit_us > 1000000) return nfail(SS_ERR_ARG, "limit_us must be in 1..1000000");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  int* d_err = nullptr;
+  NET_CK(cudaMalloc(&d_err, sizeof(int)));
+  int h = 0;
+  cudaError_t e = cudaMemsetAsync(d_err, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = wait_selftest((uint64_t)limit_us * 1000ull, d_err, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(d_err);
+  if (e != cudaSuccess) return nfail(SS_ERR_CUDA, std::string("ss_wait_selftest: ") + cudaGetErrorString(e));
+  if (h) return nfail(SS_ERR_TIMEOUT, "ss_wait_selftest: the wait gave up as it must (code " + std::to_string(h) + ")");
+  return nfail(SS_ERR_STATE, "ss_wait_selftest: the wait completed although nothing signals it");
+}

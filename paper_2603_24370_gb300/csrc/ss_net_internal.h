@@ -43,6 +43,10 @@ cudaError_t conv3x3_tc(const Act& x, const void* w, int Cout, int mode, const fl
 cudaError_t wgrad3x3_tc(const void* dyT, const void* xT, int N, int H, int W, int Cout, int Cin, float* dw, int* err,
                         cudaStream_t s);
 
+// The kernels' bounded mbarrier wait on a barrier nothing completes: records code 99
+// in `err` after limit_ns (tests the time-out path without stalling the device).
+cudaError_t wait_selftest(uint64_t limit_ns, int* err, cudaStream_t s);
+
 // ---- memory-bound layers (ss_netops.cu)
 // xT[dx + 1][c, n, y, x] = x[n, y, x + dx, c] (0 outside), dx = -1, 0, 1.
 cudaError_t shifted_transpose(const Act& x, void* xT, cudaStream_t s);

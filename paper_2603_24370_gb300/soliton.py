@@ -138,6 +138,7 @@ def load_library(path: str | None = None):
             "ss_net_predict": ([vp, vp, pd, i, vp], i),
             "ss_conv3x3": ([vp, i, i, i, i, vp, i, vp, i, vp, vp], i),
             "ss_conv3x3_wgrad": ([vp, vp, i, i, i, i, i, vp, vp], i),
+            "ss_wait_selftest": ([i, vp], i),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -574,3 +575,8 @@ def ss_conv3x3_wgrad(dy, x, dw, stream=None) -> None:
     Cout = dy.shape[3]
     _net_check(load_library().ss_conv3x3_wgrad(_dev(dy), _dev(x), N, H, W, Cout, Cin, _dev(dw),
                                                _stream_ptr(stream)))
+
+
+def ss_wait_selftest(limit_us: int, stream=None) -> int:
+    """Return code of the bounded-wait self-test (SS_ERR_TIMEOUT when it works)."""
+    return int(load_library().ss_wait_selftest(limit_us, _stream_ptr(stream)))

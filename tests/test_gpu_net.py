@@ -219,3 +219,13 @@ def test_save_and_load_round_trip(S):
     finally:
         S.ss_net_destroy(net)
         S.ss_net_destroy(net2)
+
+
+def test_a_stalled_wait_times_out_and_the_device_stays_usable(S):
+    """The kernels' bounded wait on a barrier nothing completes gives up after its
+    limit and reports SS_ERR_TIMEOUT; a convolution afterwards still matches."""
+    import time
+    t0 = time.perf_counter()
+    assert S.ss_wait_selftest(50000) == S.SS_ERR_TIMEOUT  # 50 ms limit
+    assert time.perf_counter() - t0 < 5.0
+    test_conv_forward_matches_oracle(S, CONV_CASES[0], 2)
