@@ -121,6 +121,22 @@ def ah_learned_set(count: int = 20000, seed: int = 20263, side: int = 256, dx: f
     return ah_batch(count, seed, (side,), dx, lam_range, charges)
 
 
+def cm_learned_set(count: int = 2048, seed: int = 20265, side: int = 256, dx: float = 0.2, max_count: int = 4,
+                   radius: float = 2.0, min_sep: float = 8.0, margin: float = 8.0, params=CM_DEFAULT) -> list[Problem]:
+    """Training set of the chiral-magnet initialiser: side x side grids with 1..max_count
+    compact skyrmions (R = 2) at seeded positions, the separation and margin of the
+    4096^2 workload, the same couplings."""
+    rng = SplitMix64(seed)
+    half = 0.5 * (side - 1) * dx
+    out = []
+    for _ in range(count):
+        k = 1 + (rng.next_u64() % max_count)
+        pts = _separated_positions(rng, k, half, half, margin, min_sep)
+        sol = [(x, y, 1.0, radius, 0.0) for x, y in pts]
+        out.append(Problem(CHIRAL_MAGNET, side, side, dx, dx, tuple(params), sol))
+    return out
+
+
 def smooth_field(theory: int, nx: int, ny: int, dx: float, dy: float, seed: int, bumps: int = 6,
                  amplitude: float = 0.3) -> np.ndarray:
     """A smooth random test field, float64 [C][ny][nx].

@@ -14,6 +14,7 @@ and owns device buffers (through PyTorch tensors).
 
 Command line (one GPU):
     python -m paper_2603_24370_gb300.learned --count 2048 --epochs 40 --out ah256.net
+    python -m paper_2603_24370_gb300.learned --theory cm --count 2048 --large   # + the 4096^2 workload
 """
 from __future__ import annotations
 
@@ -118,6 +119,37 @@ def solve(problems, tol: float, max_steps: int, init=None, precision: int = S.SS
     return sec, st, obs
 
 
+def large_start(net, a) -> dict:
+    """The 4096^2, 400-skyrmion chiral magnet relaxed to a.tol from the ansatz and from
+    the network's prediction (the trained weights applied at that size)."""
+    torch = _torch()
+    p = I.cm_skyrmions(n=4096, count=400, seed=20264)
+    big = S.ss_net_create(S.SS_CHIRAL_MAGNET, 4096, 1, seed=0)
+    try:
+        S.ss_net_set_params(big, S.ss_net_get_params(net))
+        out = {}
+        for start in ("ansatz", "network"):
+            with S.Solver(S.SS_CHIRAL_MAGNET, p.params, p.nx, p.ny, p.dx, p.dy, S.SS_FP32) as sv:
+                sv.init_ansatz(p.soliton_array())
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                if start == "network":
+                    f = torch.empty((1, 3, p.ny, p.nx), dtype=torch.float32, device="cuda")
+                    S.ss_get_fields(sv.ctx, f[0])
+                    init = torch.empty_like(f)
+                    S.ss_net_predict(big, f, None, 1, init)
+                    sv.set_fields(init[0].contiguous())
+                sv.autotune(4)
+                st = sv.minimise(a.tol, 100000)
+                torch.cuda.synchronize()
+                o = sv.observables()
+                out[start] = {"seconds": time.perf_counter() - t0, "steps": st["steps"],
+                              "converged": bool(st["converged"]), "energy": o["energy"], "charge": o["charge"]}
+        return out
+    finally:
+        S.ss_net_destroy(big)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--count", type=int, default=2048, help="training problems")
@@ -133,18 +165,25 @@ def main(argv=None):
     ap.add_argument("--report", default=None, help="write a JSON summary here")
     ap.add_argument("--horizon", type=int, default=0,
                     help="train on the flow's state after this many steps instead of the converged field")
+    ap.add_argument("--theory", choices=("ah", "cm"), default="ah")
+    ap.add_argument("--large", action="store_true",
+                    help="chiral magnet: also start the 4096^2, 400-skyrmion workload from the network")
     a = ap.parse_args(argv)
     torch = _torch()
     torch.cuda.init()
     S.load_library()
-    probs = I.ah_learned_set(a.count + a.test, a.seed, side=a.side)
+    theory = S.SS_ABELIAN_HIGGS if a.theory == "ah" else S.SS_CHIRAL_MAGNET
+    if theory == S.SS_ABELIAN_HIGGS:
+        probs = I.ah_learned_set(a.count + a.test, a.seed, side=a.side)
+    else:
+        probs = I.cm_learned_set(a.count + a.test, a.seed + 2, side=a.side)
     train_p, test_p = probs[:a.count], probs[a.count:]
     t0 = time.perf_counter()
     ansatz, relaxed, cp, st = relax_set(train_p, a.tol, a.max_steps, horizon=a.horizon)
     t_data = time.perf_counter() - t0
     conv = sum(1 for s in st if s["converged"])
     print(f"relaxed {a.count} training problems in {t_data:.1f} s ({conv} converged)", flush=True)
-    net = S.ss_net_create(S.SS_ABELIAN_HIGGS, a.side, a.batch, seed=a.seed)
+    net = S.ss_net_create(theory, a.side, a.batch, seed=a.seed)
     try:
         t0 = time.perf_counter()
         hist = train(net, ansatz, relaxed, cp, a.epochs, a.batch, a.lr, seed=a.seed,
@@ -168,6 +207,7 @@ def main(argv=None):
                                   "plain_seconds": s_p, "learned_seconds": s_n}
         sec_plain, st_plain, ob_plain = solve(test_p, a.tol, a.max_steps)
         sec_net, st_net, ob_net = solve(test_p, a.tol, a.max_steps, init=init)
+        large = large_start(net, a) if (a.large and theory == S.SS_CHIRAL_MAGNET) else None
     finally:
         S.ss_net_destroy(net)
     rep = {
@@ -182,6 +222,7 @@ def main(argv=None):
                                          for x, y in zip(ob_net, ob_plain))),
         "charges_equal": all(round(x["charge"]) == round(y["charge"]) for x, y in zip(ob_net, ob_plain)),
         "looser_tolerances": ladder,
+        "large": large,
     }
     print(json.dumps(rep), flush=True)
     if a.report:
