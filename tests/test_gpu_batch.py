@@ -209,3 +209,62 @@ def test_manual_launch_settings_do_not_change_the_flow(S):
             S.ss_batch_set_launch(b, 2)
         finally:
             S.ss_batch_destroy(b)
+
+
+def cm_batch(count=5, seed=21):
+    """Chiral-magnet problems of uneven sizes with 1..3 skyrmions each."""
+    rng = I.SplitMix64(seed)
+    out = []
+    for _ in range(count):
+        n = rng.choice((64, 77, 96))
+        m = rng.choice((56, 64, 80))
+        k = 1 + rng.next_u64() % 3
+        half_x, half_y = 0.5 * (n - 1) * 0.2, 0.5 * (m - 1) * 0.2
+        pts = I._separated_positions(rng, int(k), half_x, half_y, 2.5, 4.0)
+        out.append(I.Problem(2, n, m, 0.2, 0.2, I.CM_DEFAULT, [(x, y, 1.0, 1.2, 0.0) for x, y in pts]))
+    return out
+
+
+@pytest.mark.parametrize("prec", [1, 2, 3])
+def test_chiral_magnet_batch_evolves_as_alone_and_keeps_unit_length(S, prec):
+    probs = cm_batch()
+    b = S.ss_batch_create(S.SS_CHIRAL_MAGNET, prec, probs)
+    try:
+        _, st = S.ss_batch_step(b, 17)
+        dt = np.float64 if prec == 2 else np.float32
+        for k, p in enumerate(probs):
+            got = np.empty((3, p.ny, p.nx), dtype=dt)
+            S.ss_batch_get_fields(b, k, got)
+            with S.Solver(S.SS_CHIRAL_MAGNET, p.params, p.nx, p.ny, p.dx, p.dy, prec) as s:
+                s.init_ansatz(p.solitons)
+                st1 = s.step(17)
+                ref = s.fields()
+            assert np.array_equal(got, ref), k
+            assert st[k]["arrests"] == st1["arrests"]
+            norm = np.linalg.norm(got.astype(np.float64), axis=0)
+            assert np.abs(norm - 1).max() < (1e-12 if prec == 2 else 1e-6)
+            o = S.ss_batch_observables(b, k)
+            assert round(o["charge"]) == -len(p.solitons)
+    finally:
+        S.ss_batch_destroy(b)
+
+
+def test_chiral_magnet_batch_matches_the_oracle_fp64(S):
+    probs = cm_batch(count=3, seed=4)
+    b = S.ss_batch_create(S.SS_CHIRAL_MAGNET, 2, probs)
+    try:
+        _, st = S.ss_batch_step(b, 12)
+        for k, p in enumerate(probs):
+            got = np.empty((3, p.ny, p.nx))
+            S.ss_batch_get_fields(b, k, got)
+            f = O.ansatz(2, p.soliton_array(), p.nx, p.ny, p.dx, p.dy)
+            v = np.zeros_like(f)
+            E = O.energy(2, p.params, f, p.dx, p.dy)
+            arrests = 0
+            for _ in range(12):
+                f, v, E, a = O.anf_step(2, p.params, f, v, p.dx, p.dy, O.time_step(p.dx, p.dy), E)
+                arrests += a
+            assert np.abs(got - f).max() <= 1e-10
+            assert st[k]["arrests"] == arrests
+    finally:
+        S.ss_batch_destroy(b)
