@@ -12,6 +12,8 @@ appearance, see ``soliton_oracle.cpp``):
 * ``force``                -- Euler-Lagrange residual G driving Eq. 3
 * ``energy_grad_exact``    -- exact dE_h/dphi, only for pinning ``force``
 * ``anf_step`` / ``minimise`` -- arrested Newton flow, RK4 + Eq. 4 (Sec. 3.2)
+* ``gd_step`` / ``gd_minimise`` / ``gd_step_limit`` -- the first-order gradient
+  descent Sec. 3.2 names as the slower alternative (explicit Euler, see the C++)
 * ``observables``          -- energy, topological charge, flux, residual, |n|-1
 * ``ansatz``               -- vortex / skyrmion initial data (Sec. 3.4; standard forms)
 
@@ -84,6 +86,12 @@ def _load():
             lib.or_anf_step.restype = i
             lib.or_minimise.argtypes = [i, _D, _D, _D, i, i, d, d, d, d, ll, _D]
             lib.or_minimise.restype = i
+            lib.or_gd_step.argtypes = [i, _D, _D, i, i, d, d, d, _D]
+            lib.or_gd_step.restype = i
+            lib.or_gd_step_limit.argtypes = [d, d]
+            lib.or_gd_step_limit.restype = d
+            lib.or_gd_minimise.argtypes = [i, _D, _D, i, i, d, d, d, d, ll, _D]
+            lib.or_gd_minimise.restype = i
             lib.or_observables.argtypes = [i, _D, _D, i, i, d, d, _D]
             lib.or_observables.restype = None
             lib.or_ansatz.argtypes = [i, _D, i, _D, i, i, d, d]
@@ -177,6 +185,33 @@ def minimise(theory: int, params, f, dx: float, dy: float, tol: float, max_steps
                                _p(out))
     return {"f": f, "v": v, "energy": out[0], "grad_max": out[1], "steps": int(out[2]), "arrests": int(out[3]),
             "converged": bool(conv)}
+
+
+def gd_step_limit(dx: float, dy: float) -> float:
+    """Euler stability limit of gradient descent for the Eq. 2 Laplacian."""
+    return _load().or_gd_step_limit(dx, dy)
+
+
+def gd_step(theory: int, params, f, dx: float, dy: float, dtau: float, E: float):
+    """One gradient-descent step phi - dtau G(phi). Returns (f_new, E_new, energy_rose)."""
+    f = _f64(f).copy()
+    _, ny, nx = f.shape
+    e = np.array([E], dtype=np.float64)
+    rose = _load().or_gd_step(theory, _p(_params(params)), _p(f), nx, ny, dx, dy, dtau, _p(e))
+    return f, float(e[0]), bool(rose)
+
+
+def gd_minimise(theory: int, params, f, dx: float, dy: float, tol: float, max_steps: int, dtau=None,
+                step_factor: float = 0.8) -> dict:
+    """Gradient descent until dx dy max|G| < tol; dtau defaults to step_factor x the stability limit."""
+    f = _f64(f).copy()
+    _, ny, nx = f.shape
+    dtau = step_factor * gd_step_limit(dx, dy) if dtau is None else dtau
+    out = np.zeros(4)
+    conv = _load().or_gd_minimise(theory, _p(_params(params)), _p(f), nx, ny, dx, dy, dtau, tol, int(max_steps),
+                                  _p(out))
+    return {"f": f, "energy": out[0], "grad_max": out[1], "steps": int(out[2]), "rises": int(out[3]),
+            "converged": bool(conv), "dtau": dtau}
 
 
 def observables(theory: int, params, f, dx: float, dy: float) -> dict:

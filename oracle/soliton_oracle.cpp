@@ -491,6 +491,61 @@ int or_minimise(int theory, const double* prm, double* f, double* v, int nx, int
   return converged;
 }
 
+// ---------------------------------------------------------------- gradient descent
+// The first-order alternative of Sec. 3.2: descent along -grad E_h without
+// fictitious inertia. The paper names it but gives no scheme; it is read here as
+// the explicit Euler step of the gradient flow  d phi / d tau = -G(phi):
+//   phi^{n+1} = phi^n - dtau G(phi^n)   on I (the halo stays fixed),
+// the chiral magnet renormalised to |n| = 1 afterwards (the projection the arrested
+// flow applies to its new field). Nothing is arrested; an energy increase
+// E_h(phi^{n+1}) > E_h(phi^n) is only counted (it means dtau is past the stability
+// limit). *E_io holds E_h(phi^n) on entry and E_h(phi^{n+1}) on exit; returns 1 if
+// the energy rose.
+int or_gd_step(int theory, const double* prm, double* f, int nx, int ny, double dx, double dy, double dtau,
+               double* E_io) {
+  const Grid g{nx, ny, dx, dy};
+  const int C = ncomp(theory);
+  const size_t N = (size_t)C * g.plane();
+  std::vector<double> G(N);
+  force(theory, prm, f, g, G.data());  // zero on the halo
+  for (size_t k = 0; k < N; ++k) f[k] -= dtau * G[k];
+  if (theory == TH_CHIRAL_MAGNET) normalise(f, g);
+  const double E_new = energy(theory, prm, f, g);
+  const int rose = E_new > *E_io ? 1 : 0;
+  *E_io = E_new;
+  return rose;
+}
+
+// Stability limit of that Euler step for the stencil Laplacian: Eq. 2 has the
+// symbol -(30 - 32 cos t + 2 cos 2t) / (12 h^2) along each axis, largest in
+// magnitude at t = pi (16 / (3 h^2)), so -lap has the largest eigenvalue
+// lambda = (16/3)(1/dx^2 + 1/dy^2) and the step is stable for dtau < 2 / lambda.
+double or_gd_step_limit(double dx, double dy) { return 2.0 / ((16.0 / 3.0) * (1.0 / (dx * dx) + 1.0 / (dy * dy))); }
+
+// Gradient descent from phi until max_I |dx dy G(phi)| < tol or max_steps steps.
+// out = {E, norm (dx dy max|G|), steps, energy rises}. Returns 1 if converged.
+int or_gd_minimise(int theory, const double* prm, double* f, int nx, int ny, double dx, double dy, double dtau,
+                   double tol, long long max_steps, double* out) {
+  const Grid g{nx, ny, dx, dy};
+  const int C = ncomp(theory);
+  const size_t N = (size_t)C * g.plane();
+  std::vector<double> G(N);
+  double E = energy(theory, prm, f, g);
+  long long steps = 0, rises = 0;
+  double norm = 0.0;
+  int converged = 0;
+  for (;;) {
+    force(theory, prm, f, g, G.data());
+    norm = dx * dy * max_abs(G.data(), N);
+    if (norm < tol) { converged = 1; break; }
+    if (steps >= max_steps) break;
+    rises += or_gd_step(theory, prm, f, nx, ny, dx, dy, dtau, &E);
+    ++steps;
+  }
+  out[0] = E; out[1] = norm; out[2] = (double)steps; out[3] = (double)rises;
+  return converged;
+}
+
 // Signed solid angle of the spherical triangle (a, b, c):
 // tan(Omega/2) = a.(b x c) / (1 + a.b + b.c + c.a)   (Berg and Luescher, 1981).
 static double solid_angle(const double a[3], const double b[3], const double c[3]) {

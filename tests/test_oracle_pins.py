@@ -357,6 +357,91 @@ def test_cm_flow_keeps_unit_length():
     assert O.observables(CM, p.params, f, p.dx, p.dy)["charge"] == pytest.approx(-2.0, abs=1e-10)
 
 
+# ---------------------------------------------------------------- gradient descent (Sec. 3.2's first-order alternative)
+def test_gd_on_harmonic_field_is_the_closed_form_geometric_decay():
+    """e = k phi^2 / 2 on one interior site: each step multiplies phi by (1 - dtau k)
+    exactly; the energy rises on every step once |1 - dtau k| > 1, never before; the
+    minimiser stops at the first n with dx dy k |phi_n| < tol."""
+    k = 4.0
+    for dtau, rising in ((0.1, False), (0.45, False), (0.55, True)):
+        f = np.zeros((1, 5, 5))
+        f[0, 2, 2] = 1.0
+        E = 0.5 * k
+        for n in range(1, 40):
+            f, E, rose = O.gd_step(HARM, (k,), f, 1.0, 1.0, dtau, E)
+            assert f[0, 2, 2] == pytest.approx((1.0 - dtau * k) ** n, rel=1e-13, abs=1e-300)
+            assert E == pytest.approx(0.5 * k * (1.0 - dtau * k) ** (2 * n), rel=1e-12, abs=1e-300)
+            assert rose == rising
+            assert np.count_nonzero(f) == 1  # halo untouched
+    f = np.zeros((1, 5, 5))
+    f[0, 2, 2] = 1.0
+    tol, dtau = 1e-9, 0.1
+    r = O.gd_minimise(HARM, (k,), f, 1.0, 1.0, tol=tol, max_steps=10_000, dtau=dtau)
+    n_exp = math.ceil(math.log(tol / k) / math.log(1.0 - dtau * k))
+    assert r["converged"] and r["steps"] == n_exp and r["rises"] == 0
+    r2 = O.gd_minimise(HARM, (k,), f, 1.0, 1.0, tol=tol, max_steps=5, dtau=dtau)
+    assert not r2["converged"] and r2["steps"] == 5
+
+
+@pytest.mark.parametrize("theory", [AH, CM])
+def test_gd_step_descends_along_the_exact_gradient(theory):
+    """d/dtau E_h(phi - dtau G) at 0 is -sum dE_h/dphi . G exactly (chain rule; the
+    chiral-magnet renormalisation is second order since G is tangent). The exact
+    gradient is pinned by brute force above, so this fixes the step's direction and
+    scale; Richardson extrapolation in dtau removes the O(dtau) term."""
+    nx, ny, dx, dy = 24, 21, 0.3, 0.25
+    prm = AH_PRM if theory == AH else (1.0, 0.8, 0.15, 0.5, 0.0)
+    f = I.smooth_field(theory, nx, ny, dx, dy, seed=5, amplitude=0.5)
+    E0 = O.energy(theory, prm, f, dx, dy)
+    G = O.force(theory, prm, f, dx, dy)
+    slope = -(O.energy_grad_exact(theory, prm, f, dx, dy) * G).sum()
+    d = []
+    for t in (2e-5, 1e-5):
+        _, E1, _ = O.gd_step(theory, prm, f, dx, dy, t, E0)
+        d.append((E1 - E0) / t)
+    rich = 2.0 * d[1] - d[0]
+    assert slope < 0.0
+    assert rich == pytest.approx(slope, rel=1e-6)
+
+
+@pytest.mark.parametrize("theory", [AH, CM])
+def test_gd_step_limit_is_sharp(theory):
+    """Below the Eq. 2 stability limit the descent never raises the energy; just above
+    it the checkerboard modes grow and the energy rises. Fixes the limit to a few %."""
+    nx, ny, dx, dy = 40, 36, 0.3, 0.25
+    prm = AH_PRM if theory == AH else (1.0, 0.8, 0.15, 0.5, 0.0)
+    f = I.smooth_field(theory, nx, ny, dx, dy, seed=3, amplitude=0.3)
+    rng = np.random.default_rng(1)
+    f[:, 2:-2, 2:-2] += 1e-3 * rng.standard_normal(f[:, 2:-2, 2:-2].shape)
+    if theory == CM:
+        f[:, 2:-2, 2:-2] /= np.sqrt((f[:, 2:-2, 2:-2] ** 2).sum(axis=0))
+    lim = O.gd_step_limit(dx, dy)
+    assert lim == pytest.approx(3.0 / 8.0 / (1.0 / dx**2 + 1.0 / dy**2), rel=1e-15)
+    rises = {}
+    for s in (0.95, 1.02):
+        g, E, n = f.copy(), O.energy(theory, prm, f, dx, dy), 0
+        for _ in range(300):
+            g, E, r = O.gd_step(theory, prm, g, dx, dy, s * lim, E)
+            n += r
+        rises[s] = n
+    assert rises[0.95] == 0 and rises[1.02] > 50
+    if theory == CM:
+        assert np.abs(np.sqrt((g * g).sum(axis=0)) - 1.0).max() < 1e-14
+
+
+def test_gd_and_arrested_flow_reach_the_same_vortex():
+    """Both minimisers stop at a stationary point of the same E_h: for one centred
+    vortex (a unique minimum) the energies agree far below the lattice error."""
+    n, dx = 48, 0.25
+    f = O.ansatz(AH, [[0.0, 0.0, 1.0, 1.0, 0.0]], n, n, dx, dx)
+    a = O.minimise(AH, AH_PRM, f, dx, dx, tol=1e-6, max_steps=20_000)
+    g = O.gd_minimise(AH, AH_PRM, f, dx, dx, tol=1e-6, max_steps=100_000)
+    assert a["converged"] and g["converged"] and g["rises"] == 0
+    assert abs(a["energy"] - g["energy"]) < 1e-8 * a["energy"]
+    assert np.abs(a["f"] - g["f"]).max() < 1e-4  # ~ tol / lowest Hessian eigenvalue
+    assert g["steps"] > a["steps"]  # the first-order flow needs more (cheaper) steps
+
+
 # ---------------------------------------------------------------- observables and physics
 def test_berg_luescher_charge_is_exact_integer():
     n, dx = 96, 0.2
