@@ -66,6 +66,13 @@ extern "C" {
                            /* dmi_type 0 interfacial (d_i = e_3 x e_i), 1 bulk (d_i = e_i),*/
                            /* 2 D_2d "Heusler" (d_1 = e_1, d_2 = -e_2)                     */
 
+/* ---- minimisers ---- */
+#define SS_METHOD_ANF 0      /* arrested Newton flow, RK4 + Eq. 4 (Sec. 3.2): the default */
+#define SS_METHOD_GRADIENT 1 /* gradient descent, the first-order method Sec. 3.2 compares */
+                             /* against: phi <- phi - dtau G(phi) (explicit Euler on the   */
+                             /* gradient flow; chiral magnet renormalised), one launch a   */
+                             /* step                                                        */
+
 typedef struct ss_ctx ss_ctx;
 
 /* One soliton of an initial configuration (Sec. 3.4 "model-specific ansatz"; the
@@ -83,7 +90,12 @@ typedef struct {
   double size, phase;
 } ss_soliton;
 
-/* Flow status after ss_step / ss_minimise. */
+/* Flow status after ss_step / ss_minimise. Under SS_METHOD_GRADIENT nothing is
+ * arrested: `arrests` counts the steps that raised the energy (a sign that dtau is
+ * past the stability limit), `arrested` tells whether the last one did, and
+ * `energy_change` is the plain difference of the two energies. Those energies are
+ * summed in the working precision, so with FP32 fields the count also picks up
+ * rounding noise once the per-step decrease falls below it (near convergence). */
 typedef struct {
   double energy;      /* E_h of the current field (FP64 accumulation)                  */
   double grad_max;    /* dx dy max_I |G| of the current field: the convergence measure */
@@ -148,6 +160,8 @@ int ss_get_fields(ss_ctx* ctx, void* fields, int is_device);
 /* ss_batch_autotune for a single-grid context (see there); the context's field is
  * kept, the flow restarts from rest. */
 int ss_autotune(ss_ctx* ctx, int trial_steps, int* choice);
+/* ss_batch_set_method for a single-grid context (needs ss_set_theory first). */
+int ss_set_method(ss_ctx* ctx, int method, double step_factor);
 /* ss_batch_set_launch for a single-grid context. */
 int ss_set_launch(ss_ctx* ctx, int tile_shape, const int* blocks);
 
@@ -157,7 +171,8 @@ int ss_set_launch(ss_ctx* ctx, int tile_shape, const int* blocks);
 int ss_get_remainder(ss_ctx* ctx, void* remainder, int is_device);
 
 /* Copy the current velocity phi-dot [C][ny][nx] out, with a pending arrest (Eq. 4)
- * applied (zeros if the last step raised the energy). Errors as ss_get_fields. */
+ * applied (zeros if the last step raised the energy; always zeros under
+ * SS_METHOD_GRADIENT). Errors as ss_get_fields. */
 int ss_get_velocity(ss_ctx* ctx, void* velocity, int is_device);
 
 /* Euler-Lagrange force G of the current field (the right-hand side of Eq. 3 up to
@@ -166,7 +181,8 @@ int ss_get_velocity(ss_ctx* ctx, void* velocity, int is_device);
  * Errors: SS_ERR_STATE, SS_ERR_ARG, SS_ERR_CUDA. */
 int ss_force(ss_ctx* ctx, void* force, int is_device, double* energy, double* grad_max);
 
-/* Take n_steps >= 0 arrested-Newton-flow RK4 steps (Sec. 3.2, Eq. 3, Eq. 4). The
+/* Take n_steps >= 0 arrested-Newton-flow RK4 steps (Sec. 3.2, Eq. 3, Eq. 4), or
+ * gradient-descent steps after ss_set_method(SS_METHOD_GRADIENT). The
  * energy of each new field is reduced on the device and compared with the previous
  * one there; the host is not involved between steps. out (may be NULL) receives
  * the status of the resulting field. Errors: SS_ERR_STATE, SS_ERR_ARG,
@@ -190,7 +206,8 @@ int ss_observables(ss_ctx* ctx, ss_obs* out);
  * mean device duration in milliseconds of the two kernels of a step:
  * ms_out[0] = pass 1 (RK stages 1-2 with the energy / residual / energy-change
  * reductions and the on-device arrest decision of Eq. 4), ms_out[1] = pass 2 (RK
- * stages 3-4 and the RK4 combination). The steps advance the flow.
+ * stages 3-4 and the RK4 combination). Under SS_METHOD_GRADIENT ms_out[0] is the
+ * descent kernel (one per step) and ms_out[1] = 0. The steps advance the flow.
  * Errors: SS_ERR_STATE, SS_ERR_ARG, SS_ERR_CUDA, SS_ERR_NONFINITE. */
 int ss_profile_stages(ss_ctx* ctx, int n_steps, float* ms_out);
 
@@ -255,8 +272,24 @@ int ss_batch_autotune(ss_batch* batch, int trial_steps, int* choice);
 /* Set the flow launch by hand (what ss_batch_autotune chooses): tile_shape 0 (small)
  * or 1 (large, the default); blocks = {pass-1 grid, pass-2 grid}, or NULL for each
  * pass's occupancy x SMs (capped by the tile count). Fields and flow state are kept.
+ * Under SS_METHOD_GRADIENT blocks[0] is the grid of the descent kernel and
+ * blocks[1] is ignored; ss_batch_autotune likewise times only that kernel and
+ * returns {tile shape, descent blocks, 0}.
  * Errors: SS_ERR_ARG, SS_ERR_CUDA. */
 int ss_batch_set_launch(ss_batch* batch, int tile_shape, const int* blocks);
+
+/* Select the minimiser of every problem (SS_METHOD_ANF, the default, or
+ * SS_METHOD_GRADIENT). step_factor sets gradient descent's step as a fraction of
+ * the Euler stability limit of the Eq. 2 Laplacian, dtau = step_factor * (3/8) /
+ * (1/dx^2 + 1/dy^2) per problem; it must be in (0, 1], and <= 0 selects 0.8. (The
+ * limit is 2 / lambda_max with lambda_max = (16/3)(1/dx^2 + 1/dy^2), the stencil's
+ * largest eigenvalue; the couplings' own terms shift it by O(dx^2).) Every problem
+ * whose fields are set restarts from its current field at rest, with its step
+ * count and flow record cleared; tile shape and grids are kept. Descent takes one
+ * kernel launch per step: it evaluates E_h, dx dy max|G| and -G of the current field
+ * (so ss_force stays valid), writes the next field, and stops as ss_minimise
+ * describes. Errors: SS_ERR_ARG, SS_ERR_CUDA. */
+int ss_batch_set_method(ss_batch* batch, int method, double step_factor);
 
 /* Observables of problem `item`, as ss_observables. */
 int ss_batch_observables(ss_batch* batch, int item, ss_obs* out);

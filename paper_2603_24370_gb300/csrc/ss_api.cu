@@ -96,10 +96,19 @@ int check_grid(int nx, int ny, double dx, double dy) {
   return SS_OK;
 }
 
+// Gradient descent: dtau = factor x the Euler stability limit of the Eq. 2
+// Laplacian, 2 / lambda_max with lambda_max = (16/3)(1/dx^2 + 1/dy^2) (the stencil's
+// largest eigenvalue, at the checkerboard mode).
+double descent_step(double dx, double dy, double factor) {
+  return factor * 2.0 / ((16.0 / 3.0) * (1.0 / (dx * dx) + 1.0 / (dy * dy)));
+}
+constexpr double DEFAULT_STEP_FACTOR = 0.8;
+
 // One problem of a batch, host view.
 struct Problem {
   int nx = 0, ny = 0;
   double dx = 0, dy = 0, dt = 0;
+  double tau = 0;  // gradient-descent step
   double coup[10] = {0};
   size_t plane = 0;
   int ntx = 0, ntiles = 0, tile0 = 0;
@@ -125,6 +134,7 @@ ProbDesc<R> make_desc(const Problem& p, DevState* st, FlowPartial* part) {
     d.kv[i] = static_cast<R*>(p.kv[i]);
   }
   d.dt = (R)p.dt;
+  d.tau = (R)p.tau;
   d.h.i12dx = (R)(1.0 / (12.0 * p.dx));
   d.h.i12dy = (R)(1.0 / (12.0 * p.dy));
   d.h.i12dx2 = (R)(1.0 / (12.0 * p.dx * p.dx));
@@ -159,7 +169,8 @@ struct ss_batch {
   int sol_cap = 0;
   int* d_active = nullptr;
   BatchLaunch BL{};
-  cudaGraphExec_t chunk = nullptr;
+  int method = METHOD_ANF;      // SS_METHOD_ANF / SS_METHOD_GRADIENT
+  cudaGraphExec_t chunk = nullptr;  // K_CHUNK steps of the current method
   DevState* h_st = nullptr;  // pinned [n]
   int* h_active = nullptr;   // pinned [2]
   cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -197,9 +208,10 @@ int upload_descs(ss_batch* b) {
 }
 
 // Tile the batch with tile shape ts (0 small, 1 large): every problem's tiles, the
-// tile -> problem map, the descriptors and the pass grids (`blocks`, or each pass's
-// occupancy x SMs when NULL). The captured step graph is dropped and re-captured.
-// Call only while no launch of the batch is in flight.
+// tile -> problem map, the descriptors and the pass grids (`blocks`: passes 1 and 2
+// of the arrested flow, or blocks[0] for the descent pass under gradient descent;
+// each pass's occupancy x SMs when NULL). The captured step graph is dropped and
+// re-captured. Call only while no launch of the batch is in flight.
 int batch_layout(ss_batch* b, int ts, const int* blocks) {
   const int n = b->n();
   int tx, ty;
@@ -225,7 +237,9 @@ int batch_layout(ss_batch* b, int ts, const int* blocks) {
   const int th = b->theory == SS_ABELIAN_HIGGS ? TH_AH : TH_CM;
   flow_grid(th, b->prec, ts, total, n == 1, b->BL.flow_blocks);
   if (blocks) {
-    for (int i = 0; i < 2; ++i) b->BL.flow_blocks[i] = blocks[i] < total ? blocks[i] : total;
+    if (b->method == METHOD_GD) b->BL.flow_blocks[2] = blocks[0] < total ? blocks[0] : total;
+    else
+      for (int i = 0; i < 2; ++i) b->BL.flow_blocks[i] = blocks[i] < total ? blocks[i] : total;
   }
   if (b->chunk) {
     cudaGraphExecDestroy(b->chunk);
@@ -386,6 +400,10 @@ int ensure_chunk(ss_batch* b) {
   SS_CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = cudaSuccess;
   for (int k = 0; k < K_CHUNK && e == cudaSuccess; ++k) {
+    if (b->method == METHOD_GD) {
+      e = launch_pass(b->BL, PASS_GD, b->stream);  // evaluate, then step
+      continue;
+    }
     e = launch_pass(b->BL, 2, b->stream);                        // stages 3-4: new fields
     if (e == cudaSuccess) e = launch_pass(b->BL, 1, b->stream);  // stages 1-2 of the new fields
   }
@@ -404,11 +422,15 @@ int ensure_chunk(ss_batch* b) {
 // Chunk i is enqueued before the running count of chunk i-1 is checked, so the GPU
 // never waits for the host; once every problem has stopped the rest of an enqueued
 // chunk is a row of launches whose tiles all skip.
+// Under gradient descent each pass evaluates a field and then steps, so a run takes
+// max_steps + 1 passes, the last one evaluating the final field.
 int batch_run(ss_batch* b, double tol, long long max_steps) {
   const int n = b->n();
   SS_CK(launch_set_run_all(b->st, n, tol, max_steps, b->stream));
-  SS_CK(launch_pass(b->BL, 1, b->stream));  // heads of the current fields (skipped where done)
-  const long long nchunks = (max_steps + K_CHUNK - 1) / K_CHUNK;
+  long long passes = max_steps;
+  if (b->method == METHOD_GD) passes += 1;
+  else SS_CK(launch_pass(b->BL, 1, b->stream));  // heads of the current fields (skipped where done)
+  const long long nchunks = (passes + K_CHUNK - 1) / K_CHUNK;
   if (nchunks > 0) {
     int rc = ensure_chunk(b);
     if (rc != SS_OK) return rc;
@@ -565,6 +587,7 @@ int ss_set_theory(ss_ctx* c, int theory, const double* params, int n_params) {
   p.dx = c->dx;
   p.dy = c->dy;
   p.dt = 0.5 * (c->dx < c->dy ? c->dx : c->dy);  // Sec. 3.1: C = dt / dx = 0.5
+  p.tau = descent_step(p.dx, p.dy, DEFAULT_STEP_FACTOR);
   std::memcpy(p.coup, k, sizeof(k));
   b->probs.push_back(p);
   rc = batch_alloc(b);
@@ -627,11 +650,11 @@ int ss_get_velocity(ss_ctx* c, void* out, int is_device) {
   if (rc != SS_OK) return rc;
   if (!out) return fail(SS_ERR_ARG, "velocity is NULL");
   ss_batch* b = c->b;
-  SS_CK(launch_pass(b->BL, 1, b->stream));  // resolves a pending arrest (skipped if known)
+  if (b->method != METHOD_GD) SS_CK(launch_pass(b->BL, 1, b->stream));  // resolves a pending arrest
   rc = read_states(b);
   if (rc != SS_OK) return rc;
   const size_t bytes = (size_t)b->C * b->probs[0].plane * b->elem;
-  if (b->h_st[0].arrest) {
+  if (b->method == METHOD_GD || b->h_st[0].arrest) {  // gradient descent has no velocity
     if (is_device) SS_CK(cudaMemsetAsync(out, 0, bytes, b->stream));
     else std::memset(out, 0, bytes);
     SS_CK(cudaStreamSynchronize(b->stream));
@@ -705,13 +728,24 @@ int ss_profile_stages(ss_ctx* c, int n_steps, float* ms_out) {
   if (rc != SS_OK) return rc;
   if (n_steps < 1 || n_steps > 4096 || !ms_out) return fail(SS_ERR_ARG, "n_steps must be in 1..4096 and ms_out non-NULL");
   ss_batch* b = c->b;
+  const bool gd = b->method == METHOD_GD;
   SS_CK(launch_set_run_all(b->st, b->n(), -1.0, n_steps, b->stream));
-  SS_CK(launch_pass(b->BL, 1, b->stream));  // head of the current field, untimed
+  if (!gd) SS_CK(launch_pass(b->BL, 1, b->stream));  // head of the current field, untimed
   cudaEvent_t ev[3];
   for (int i = 0; i < 3; ++i) SS_CK(cudaEventCreate(&ev[i]));
   double acc[2] = {0, 0};
   cudaError_t e = cudaSuccess;
-  for (int k = 0; k < n_steps && e == cudaSuccess; ++k) {
+  for (int k = 0; k < n_steps && e == cudaSuccess && gd; ++k) {  // gradient descent: one pass per step
+    e = cudaEventRecord(ev[0], b->stream);
+    if (e == cudaSuccess) e = launch_pass(b->BL, PASS_GD, b->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1], b->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+    float m = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&m, ev[0], ev[1]);
+    acc[0] += m;
+  }
+  if (gd && e == cudaSuccess) e = launch_pass(b->BL, PASS_GD, b->stream);  // evaluates the last field
+  for (int k = 0; k < n_steps && e == cudaSuccess && !gd; ++k) {
     e = cudaEventRecord(ev[0], b->stream);
     if (e == cudaSuccess) e = launch_pass(b->BL, 2, b->stream);  // stages 3-4 -> new field
     if (e == cudaSuccess) e = cudaEventRecord(ev[1], b->stream);
@@ -772,6 +806,7 @@ int ss_batch_create(ss_batch** out, int theory, int precision, const ss_batch_it
     p.dx = it.dx;
     p.dy = it.dy;
     p.dt = 0.5 * (it.dx < it.dy ? it.dx : it.dy);  // Sec. 3.1
+    p.tau = descent_step(p.dx, p.dy, DEFAULT_STEP_FACTOR);
     std::memcpy(p.coup, k, sizeof(k));
     b->probs.push_back(p);
   }
@@ -881,13 +916,16 @@ int batch_autotune(ss_batch* b, int trial_steps, int* choice) {
   auto destroy_events = [&]() {
     for (int i = 0; i < 3; ++i) cudaEventDestroy(ev[i]);
   };
+  // gradient descent: the descent pass alone, its grid in blocks[0] / occ[0]
+  const bool gd = b->method == METHOD_GD;
   double best = 1e300;
   int best_ts = 1, best_blocks[2] = {0, 0};
   for (int ts = 0; ts < 2; ++ts) {
-    int occ[2];
+    int occ[3];
     flow_occupancy(th, b->prec, ts, n == 1, occ);
+    if (gd) occ[0] = occ[1] = occ[2];
     const int kmax = occ[0] > occ[1] ? occ[0] : occ[1];
-    double tbest[2] = {1e300, 1e300};
+    double tbest[2] = {1e300, gd ? 0.0 : 1e300};
     int kbest[2] = {1, 1};
     for (int k = 1; k <= kmax; ++k) {
       const int blocks[2] = {(k < occ[0] ? k : occ[0]) * nsm, (k < occ[1] ? k : occ[1]) * nsm};
@@ -896,11 +934,24 @@ int batch_autotune(ss_batch* b, int trial_steps, int* choice) {
         return release(rc);
       }
       cudaError_t e = launch_set_run_all(b->st, n, -1.0, trial_steps + 1, b->stream);
-      if (e == cudaSuccess) e = launch_pass(b->BL, 1, b->stream);  // head, untimed
-      if (e == cudaSuccess) e = launch_pass(b->BL, 2, b->stream);  // one untimed step
-      if (e == cudaSuccess) e = launch_pass(b->BL, 1, b->stream);
       double acc[2] = {0.0, 0.0};
-      for (int step = 0; step < trial_steps && e == cudaSuccess; ++step) {
+      if (gd) {
+        if (e == cudaSuccess) e = launch_pass(b->BL, PASS_GD, b->stream);  // one untimed step
+        for (int step = 0; step < trial_steps && e == cudaSuccess; ++step) {
+          e = cudaEventRecord(ev[0], b->stream);
+          if (e == cudaSuccess) e = launch_pass(b->BL, PASS_GD, b->stream);
+          if (e == cudaSuccess) e = cudaEventRecord(ev[1], b->stream);
+          if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+          float m = 0.f;
+          if (e == cudaSuccess) e = cudaEventElapsedTime(&m, ev[0], ev[1]);
+          acc[0] += m;
+        }
+      } else {
+        if (e == cudaSuccess) e = launch_pass(b->BL, 1, b->stream);  // head, untimed
+        if (e == cudaSuccess) e = launch_pass(b->BL, 2, b->stream);  // one untimed step
+        if (e == cudaSuccess) e = launch_pass(b->BL, 1, b->stream);
+      }
+      for (int step = 0; step < trial_steps && e == cudaSuccess && !gd; ++step) {
         e = cudaEventRecord(ev[0], b->stream);
         if (e == cudaSuccess) e = launch_pass(b->BL, 2, b->stream);
         if (e == cudaSuccess) e = cudaEventRecord(ev[1], b->stream);
@@ -917,7 +968,7 @@ int batch_autotune(ss_batch* b, int trial_steps, int* choice) {
         destroy_events();
         return release(fail(SS_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e)));
       }
-      for (int q = 0; q < 2; ++q)
+      for (int q = 0; q < (gd ? 1 : 2); ++q)
         if (k <= occ[q] && acc[q] < tbest[q]) {
           tbest[q] = acc[q];
           kbest[q] = k;
@@ -936,16 +987,51 @@ int batch_autotune(ss_batch* b, int trial_steps, int* choice) {
   if (rc != SS_OK) return rc;
   if (choice) {
     choice[0] = best_ts;
-    choice[1] = b->BL.flow_blocks[0];
-    choice[2] = b->BL.flow_blocks[1];
+    choice[1] = gd ? b->BL.flow_blocks[2] : b->BL.flow_blocks[0];
+    choice[2] = gd ? 0 : b->BL.flow_blocks[1];
   }
   return SS_OK;
 }
 
 int batch_set_launch(ss_batch* b, int tile_shape, const int* blocks) {
   if (tile_shape != 0 && tile_shape != 1) return fail(SS_ERR_ARG, "tile_shape must be 0 or 1");
-  if (blocks && (blocks[0] < 1 || blocks[1] < 1)) return fail(SS_ERR_ARG, "block counts must be >= 1");
+  if (blocks && (blocks[0] < 1 || (b->method != METHOD_GD && blocks[1] < 1)))
+    return fail(SS_ERR_ARG, "block counts must be >= 1");
   return batch_layout(b, tile_shape, blocks);
+}
+
+// Switch the minimiser. Every problem whose fields are set restarts from its
+// current field at rest: the field goes into both ping-pong buffers, velocity and
+// step count are cleared, and the flow record is reset (the two methods keep
+// different state: velocity and previous field for the arrested flow, none for
+// descent).
+int batch_set_method(ss_batch* b, int method, double step_factor) {
+  if (method != SS_METHOD_ANF && method != SS_METHOD_GRADIENT)
+    return fail(SS_ERR_ARG, "method must be SS_METHOD_ANF or SS_METHOD_GRADIENT");
+  if (step_factor <= 0.0) step_factor = DEFAULT_STEP_FACTOR;
+  if (!std::isfinite(step_factor) || step_factor > 1.0)
+    return fail(SS_ERR_ARG, "step_factor must be in (0, 1] (<= 0 selects the default)");
+  int rc = read_states(b);
+  if (rc != SS_OK) return rc;
+  for (int i = 0; i < b->n(); ++i) {
+    Problem& p = b->probs[i];
+    p.tau = descent_step(p.dx, p.dy, step_factor);
+    if (!b->fields_set[i]) continue;
+    const int cur = cur_of(b, i);
+    const size_t bytes = (size_t)b->C * p.plane * b->elem;
+    SS_CK(cudaMemcpyAsync(p.phi[cur ^ 1], p.phi[cur], bytes, cudaMemcpyDeviceToDevice, b->stream));
+    if (p.lo[0]) SS_CK(cudaMemcpyAsync(p.lo[cur ^ 1], p.lo[cur], bytes, cudaMemcpyDeviceToDevice, b->stream));
+    for (int k = 0; k < 2; ++k) SS_CK(cudaMemsetAsync(p.v[k], 0, bytes, b->stream));
+    SS_CK(launch_reset_states(b->st + i, 1, b->stream));
+  }
+  b->method = method;
+  const int blocks_keep[2] = {b->BL.flow_blocks[0], b->BL.flow_blocks[1]};
+  b->BL.flow_blocks[2] = 0;
+  rc = batch_layout(b, b->BL.ts, nullptr);  // new descriptors (dtau), default grids, graph dropped
+  if (rc != SS_OK) return rc;
+  b->BL.flow_blocks[0] = blocks_keep[0];  // an arrested-flow grid set before stays in force
+  b->BL.flow_blocks[1] = blocks_keep[1];
+  return read_states(b);
 }
 
 int ss_batch_set_launch(ss_batch* b, int tile_shape, const int* blocks) {
@@ -957,6 +1043,17 @@ int ss_set_launch(ss_ctx* c, int tile_shape, const int* blocks) {
   int rc = check_ready(c);
   if (rc != SS_OK) return rc;
   return batch_set_launch(c->b, tile_shape, blocks);
+}
+
+int ss_batch_set_method(ss_batch* b, int method, double step_factor) {
+  if (!b) return fail(SS_ERR_ARG, "null batch");
+  return batch_set_method(b, method, step_factor);
+}
+
+int ss_set_method(ss_ctx* c, int method, double step_factor) {
+  if (!c) return fail(SS_ERR_ARG, "null context");
+  if (!c->b) return fail(SS_ERR_STATE, "ss_set_theory has not been called");
+  return batch_set_method(c->b, method, step_factor);
 }
 
 int ss_batch_autotune(ss_batch* b, int trial_steps, int* choice) {

@@ -1,5 +1,6 @@
 // ss_flow.cu -- the arrested-Newton-flow step (arxiv 2603.24370, Sec. 3.2) as two
-// fused passes over a batch of relaxation problems.
+// fused passes over a batch of relaxation problems, and the gradient-descent step
+// it is compared with as a third pass built from the same parts.
 //
 // One RK4 step of phi'' = -G(phi) (Eq. 3) on the first-order system (phi, v), with
 // k_vi = -G(Y_i) at the stage inputs
@@ -42,6 +43,18 @@
 // stalls above dx dy max|G| ~ 1e-6 while arresting every other step. The stage
 // inputs are formed as hi + (lo + increment), normalised in split form for the
 // chiral magnet, and rounded once to FP32 for the stencils.
+//
+// Gradient descent (pass 3), the first-order alternative Sec. 3.2 sets the flow
+// against, read as the explicit Euler step of d phi / d tau = -G(phi):
+//   phi^{n+1} = phi^n - dtau G(phi^n)   (chiral magnet: renormalised),
+// one launch per step with the same tile staging, stencils, forces, reductions and
+// device-side decision as pass 1: it reads phi^n, writes -G into k_v1 (so the
+// force of the head field is always at hand) and phi^{n+1} into the other buffer,
+// and the last tile of a problem advances its step count unless the field it
+// evaluated has converged or the step budget is spent. Nothing is arrested; a rise
+// E_h(phi^n) > E_h(phi^{n-1}) is counted (it means dtau is past the stability limit).
+// The rise is judged on the two working-precision sums, not in the cancellation-free
+// form of pass 1: that needs phi^{n-1}, whose buffer this launch is overwriting.
 //
 // Per block a tile of TX x TY sites is staged in shared memory with its halo, the
 // stage inputs formed while loading (two sites per iteration, loads first). Each
@@ -282,6 +295,7 @@ struct TileCtx {
   int cur;       // ping-pong parity of the current field
   int arrest;    // pass 2: the current velocity counts as zero
   int has_prev;  // pass 1: the other buffer holds the previous field
+  int adv;       // pass 3: the step budget allows a new field
 };
 
 // Thread 0 stages the view of tile t. A problem's record changes only when its last
@@ -306,11 +320,13 @@ __device__ __forceinline__ void load_tile_ctx(TileCtx<R>& tc, const ProbDesc<R>&
   const long long steps = st->steps;
   int skip = (st->converged | st->nonfinite) != 0;
   if (PASS == 1) skip |= (st->head_step == steps);
-  else skip |= (steps >= st->step_limit);
+  else if (PASS == 2) skip |= (steps >= st->step_limit);
+  else skip |= (st->head_step == steps && steps >= st->step_limit);  // evaluated, budget spent
   tc.skip = skip;
   tc.cur = (int)(steps & 1);
   tc.arrest = (PASS == 2) && (st->arrest != 0);
   tc.has_prev = (PASS == 1) && (steps > 0);
+  tc.adv = (PASS == 3) && (steps < st->step_limit);
 }
 
 // One flow pass over every tile of a batch. ONE: the batch has a single problem,
@@ -325,7 +341,7 @@ __global__ void __launch_bounds__(NT)
   constexpr int RY = T::RY;
   constexpr int PS = C * T::SXY;  // values per tile set
   extern __shared__ __align__(16) unsigned char smraw[];
-  R* sm = reinterpret_cast<R*>(smraw);  // pass 1: [Y1 | Y2 | delta], pass 2: [Y3 | Y4]
+  R* sm = reinterpret_cast<R*>(smraw);  // pass 1: [Y1 | Y2 | delta], pass 2: [Y3 | Y4], pass 3: [phi]
   __shared__ TileCtx<R> tcb[2];         // this tile's view and the next one's (read ahead)
   __shared__ R sred[(NT / 32) * 5];
   __shared__ double dred[RedSmem<2, 1>::n];
@@ -334,7 +350,7 @@ __global__ void __launch_bounds__(NT)
   R* const setA = sm;           // first stage input of the pass
   R* const setB = sm + PS;      // second stage input
   R* const setD = sm + 2 * PS;  // pass 1: phi^n - phi^{n-1}
-  // pass 1: running sums over this block's consecutive tiles of one problem
+  // passes 1, 3: running sums over this block's consecutive tiles of one problem
   R es = R(0), ec = R(0), ds = R(0), dc = R(0), gmr = R(0);
 
   if (tid == 0 && (int)blockIdx.x < total_tiles) load_tile_ctx<R, PASS, ONE>(tcb[0], one, probs, tile_prob, blockIdx.x);
@@ -349,6 +365,7 @@ __global__ void __launch_bounds__(NT)
     const int cur = tc.cur;
     const bool arrest = tc.arrest != 0;
     const bool has_prev = tc.has_prev != 0;
+    const bool adv = tc.adv != 0;
     const int nx = D.nx, ny = D.ny;
     const size_t P = (size_t)D.plane;
     const R* __restrict__ phi = D.phi[cur];
@@ -367,8 +384,9 @@ __global__ void __launch_bounds__(NT)
 
     // ---- stage inputs over the tile and its halo, LU sites per iteration (the loads
     // of all LU sites are issued before any is used: more bytes in flight per thread;
-    // measured best: 3 for pass 1, 2 for pass 2, whose loads per site are heavier)
-    constexpr int LU = PASS == 1 ? 3 : 2;
+    // measured best: 3 for pass 1, 2 for pass 2, whose loads per site are heavier;
+    // pass 3 loads only phi)
+    constexpr int LU = PASS == 1 ? 3 : (PASS == 2 ? 2 : 4);
     for (int base = tid; base < T::SXY; base += LU * NT) {
       R pv[LU][C], lv[LU][C], vv[LU][C], k1v[LU][C], k2v[LU][C], pp[LU][C], lp[LU][C];
       bool in[LU], inside[LU];
@@ -384,11 +402,11 @@ __global__ void __launch_bounds__(NT)
         for (int c = 0; c < C; ++c) {
           pv[u][c] = in[u] ? phi[c * P + s] : R(0);
           lv[u][c] = (LO && in[u]) ? lo[c * P + s] : R(0);
-          vv[u][c] = (inside[u] && !arrest) ? vel[c * P + s] : R(0);
+          vv[u][c] = (PASS != 3 && inside[u] && !arrest) ? vel[c * P + s] : R(0);
           if (PASS == 1) {
             pp[u][c] = (has_prev && in[u]) ? phi_prev[c * P + s] : pv[u][c];
             lp[u][c] = (LO && has_prev && in[u]) ? lo_prev[c * P + s] : lv[u][c];
-          } else {
+          } else if (PASS == 2) {
             k1v[u][c] = inside[u] ? kv1[c * P + s] : R(0);
             k2v[u][c] = inside[u] ? (arrest ? k1v[u][c] : kv2[c * P + s]) : R(0);
           }
@@ -411,7 +429,7 @@ __global__ void __launch_bounds__(NT)
             if constexpr (LO) normalise_split(pv[u], yb);
             else normalise<C>(yb);
           }
-        } else {
+        } else if (PASS == 2) {
 #pragma unroll
           for (int c = 0; c < C; ++c) {
             const R base3 = hdt * vv[u][c] + c3 * k1v[u][c];
@@ -428,18 +446,21 @@ __global__ void __launch_bounds__(NT)
               normalise<C>(yb);
             }
           }
+        } else {
+#pragma unroll
+          for (int c = 0; c < C; ++c) ya[c] = LO ? lv[u][c] : pv[u][c];
         }
         if (LO) {  // stage inputs: value + small part, rounded once
 #pragma unroll
           for (int c = 0; c < C; ++c) {
             ya[c] = pv[u][c] + ya[c];
-            yb[c] = pv[u][c] + yb[c];
+            if (PASS != 3) yb[c] = pv[u][c] + yb[c];
           }
         }
 #pragma unroll
         for (int c = 0; c < C; ++c) {
           setA[c * T::SXY + idx] = ya[c];
-          setB[c * T::SXY + idx] = yb[c];
+          if (PASS != 3) setB[c * T::SXY + idx] = yb[c];
           if (PASS == 1) setD[c * T::SXY + idx] = has_prev ? yd[c] : R(0);
         }
       }
@@ -451,7 +472,8 @@ __global__ void __launch_bounds__(NT)
     const int gx = x0 + threadIdx.x, gyb = y0 + threadIdx.y * RY;
     const bool colok = gx >= 2 && gx < nx - 2;
 
-    if (PASS == 1) {
+    if (PASS != 2) {
+      if (PASS == 1) {
       // stage 1 at Y_1 = phi: k_v1, e, max|G|, and e(phi^n) - e(phi^{n-1})
       {
         StageWin<TH, R, T::SXY> W;
@@ -525,6 +547,62 @@ __global__ void __launch_bounds__(NT)
           }
         }
       }
+      } else {
+      // gradient descent at phi: -G into k_v1, e, max|G|, and phi - dtau G
+      {
+        StageWin<TH, R, T::SXY> W;
+#pragma unroll
+        for (int s = 0; s < 5; ++s) W.enter(setA, (sy0 - 2 + s) * T::SX + sx, s);
+        const R tau = D.tau;
+        R* __restrict__ phi_out = D.phi[cur ^ 1];
+        R* __restrict__ lo_out = D.lo[cur ^ 1];
+#pragma unroll
+        for (int r = 0; r < RY; ++r) {
+          const int off = (sy0 + r) * T::SX + sx;
+          R v[C], fx[C], fy[C], fxx[C], fyy[C], fxy[C], G[C];
+          W.derivs(setA, off, h, v, fx, fy, fxx, fyy, fxy);
+          force_at<TH, R>(kc, v, fx, fy, fxx, fyy, fxy, G);
+          if (colok && gyb + r >= 2 && gyb + r < ny - 2) {
+            const size_t s = (size_t)(gyb + r) * nx + gx;
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+              kv1[c * P + s] = -G[c];
+              gmr = rmax(gmr, fabs(G[c]));
+            }
+            const R e = (TH == TH_AH) ? density_ah<R>(kc, v, fx, fy) : density_cm<R>(kc, v, fx, fy);
+            const R t1 = es + e;
+            ec += (fabs(es) >= fabs(e)) ? (es - t1) + e : (e - t1) + es;
+            es = t1;
+            if (adv) {
+              R p0[C], q[C], pn[C], ln[C];
+#pragma unroll
+              for (int c = 0; c < C; ++c) {
+                p0[c] = phi[c * P + s];
+                q[c] = (LO ? lo[c * P + s] : p0[c]) - tau * G[c];
+              }
+              if constexpr (LO) {
+                if (TH == TH_CM) normalise_split(p0, q);
+#pragma unroll
+                for (int c = 0; c < C; ++c) two_sum_f(p0[c], q[c], pn[c], ln[c]);
+              } else {
+#pragma unroll
+                for (int c = 0; c < C; ++c) pn[c] = q[c];
+                if (TH == TH_CM) normalise<C>(pn);
+              }
+#pragma unroll
+              for (int c = 0; c < C; ++c) {
+                phi_out[c * P + s] = pn[c];
+                if (LO) lo_out[c * P + s] = ln[c];
+              }
+            }
+          }
+          if (r + 1 < RY) {
+            W.shift();
+            W.enter(setA, (sy0 + r + 3) * T::SX + sx, 4);
+          }
+        }
+      }
+      }
 
       // ---- partials: the block keeps summing while its next tile belongs to the same
       // problem and writes a zero partial for this tile; otherwise it reduces and writes
@@ -566,7 +644,7 @@ __global__ void __launch_bounds__(NT)
         DD sv2[2] = {acc, dacc};
         double mv2[1] = {mm};
         block_reduce<2, 1>(sv2, mv2, dred);
-        if (tid == 0) {
+        if (tid == 0 && PASS == 1) {
           DevState* st = d.st;
           const double E = d.area * (sv2[0].s + sv2[0].c);
           const double dE = d.area * (sv2[1].s + sv2[1].c);
@@ -582,6 +660,27 @@ __global__ void __launch_bounds__(NT)
           st->converged = (g < st->tol) ? 1 : 0;
           st->nonfinite = (isfinite(E) && isfinite(g) && isfinite(dE)) ? 0 : 1;
           st->head_step = st->steps;
+          st->ticket = 0;
+        } else if (tid == 0) {
+          // descent: record the evaluated field, count a rise, then take the step
+          // (its new field is already written) unless converged or out of budget
+          DevState* st = d.st;
+          const double E = d.area * (sv2[0].s + sv2[0].c);
+          const double g = d.area * mv2[0];
+          const double El = st->E_last;
+          const int rose = E > El ? 1 : 0;  // E_last = +inf before the first field
+          st->E_cur = E;
+          st->dE = isfinite(El) ? E - El : 0.0;
+          st->gmax = g;
+          st->arrest = rose;
+          st->arrests += rose;
+          st->E_last = E;
+          const int conv = (g < st->tol) ? 1 : 0;
+          const int bad = (isfinite(E) && isfinite(g)) ? 0 : 1;
+          st->converged = conv;
+          st->nonfinite = bad;
+          st->head_step = st->steps;
+          if (!conv && !bad && st->steps < st->step_limit) st->steps += 1;
           st->ticket = 0;
         }
       }
@@ -720,7 +819,9 @@ __global__ void k_count_active(const DevState* st, int n, int* out) {
   int mine = 0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const DevState* s = st + i;
-    mine += !(s->converged || s->nonfinite || s->steps >= s->step_limit);
+    // running: not stopped, and either budget left or the last field not yet
+    // evaluated (a descent pass evaluates the field its last step produced)
+    mine += !(s->converged || s->nonfinite || (s->steps >= s->step_limit && s->head_step == s->steps));
   }
   atomicAdd(&cnt, mine);
   __syncthreads();
@@ -736,7 +837,7 @@ __global__ void k_scaled_copy(R* __restrict__ out, const R* __restrict__ in, siz
 // ------------------------------------------------------------------ launchers
 template <int TH, typename R, int TS>
 static size_t pass_smem(int pass) {
-  return (size_t)(pass == 1 ? 3 : 2) * NComp<TH>::C * FlowTile<R, TS>::SXY * sizeof(R);
+  return (size_t)(pass == 1 ? 3 : (pass == 2 ? 2 : 1)) * NComp<TH>::C * FlowTile<R, TS>::SXY * sizeof(R);
 }
 
 template <int TH, typename R, bool LO, bool ONE, int TS>
@@ -747,13 +848,16 @@ static void pass_launch(const BatchLaunch& b, int pass, cudaStream_t s) {
   if (pass == 1)
     k_pass<TH, R, 1, LO, ONE, TS><<<b.flow_blocks[0], blk, pass_smem<TH, R, TS>(1), s>>>(one, probs, b.tile_prob,
                                                                                           b.total_tiles);
-  else
+  else if (pass == 2)
     k_pass<TH, R, 2, LO, ONE, TS><<<b.flow_blocks[1], blk, pass_smem<TH, R, TS>(2), s>>>(one, probs, b.tile_prob,
+                                                                                          b.total_tiles);
+  else
+    k_pass<TH, R, 3, LO, ONE, TS><<<b.flow_blocks[2], blk, pass_smem<TH, R, TS>(3), s>>>(one, probs, b.tile_prob,
                                                                                           b.total_tiles);
 }
 template <int TH, typename R, bool LO>
 static cudaError_t pass_t(const BatchLaunch& b, int pass, cudaStream_t s) {
-  if (pass != 1 && pass != 2) return cudaErrorInvalidValue;
+  if (pass < 1 || pass > 3) return cudaErrorInvalidValue;
   if (b.one) {
     if (b.ts) pass_launch<TH, R, LO, true, 1>(b, pass, s);
     else pass_launch<TH, R, LO, true, 0>(b, pass, s);
@@ -805,18 +909,22 @@ cudaError_t launch_scaled_copy(const LaunchCtx& c, void* out, const void* in, do
 
 // Opt the pass kernels into their dynamic shared memory and report how many blocks
 // of each pass fit on one SM.
+template <int TH, typename R, int PASS, bool LO, bool ONE, int TS>
+static void one_occupancy(int* occ) {
+  cudaFuncSetAttribute(k_pass<TH, R, PASS, LO, ONE, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)pass_smem<TH, R, TS>(PASS));
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_pass<TH, R, PASS, LO, ONE, TS>, NT,
+                                                pass_smem<TH, R, TS>(PASS));
+}
 template <int TH, typename R, bool LO, bool ONE, int TS>
-static void pass_occupancy(int occ[2]) {
-  cudaFuncSetAttribute(k_pass<TH, R, 1, LO, ONE, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)pass_smem<TH, R, TS>(1));
-  cudaFuncSetAttribute(k_pass<TH, R, 2, LO, ONE, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)pass_smem<TH, R, TS>(2));
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[0], k_pass<TH, R, 1, LO, ONE, TS>, NT, pass_smem<TH, R, TS>(1));
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], k_pass<TH, R, 2, LO, ONE, TS>, NT, pass_smem<TH, R, TS>(2));
+static void pass_occupancy(int occ[3]) {
+  one_occupancy<TH, R, 1, LO, ONE, TS>(&occ[0]);
+  one_occupancy<TH, R, 2, LO, ONE, TS>(&occ[1]);
+  one_occupancy<TH, R, 3, LO, ONE, TS>(&occ[2]);
 }
 
 template <int TH, bool ONE, int TS>
-static void occupancy_th(int prec, int occ[2]) {
+static void occupancy_th(int prec, int occ[3]) {
   switch (prec) {
     case PREC_F32C: pass_occupancy<TH, float, true, ONE, TS>(occ); break;
     case PREC_F64: pass_occupancy<TH, double, false, ONE, TS>(occ); break;
@@ -825,7 +933,7 @@ static void occupancy_th(int prec, int occ[2]) {
 }
 
 template <int TH>
-static void occupancy_sel(int prec, int ts, bool one, int occ[2]) {
+static void occupancy_sel(int prec, int ts, bool one, int occ[3]) {
   if (one) {
     if (ts) occupancy_th<TH, true, 1>(prec, occ);
     else occupancy_th<TH, true, 0>(prec, occ);
@@ -835,22 +943,22 @@ static void occupancy_sel(int prec, int ts, bool one, int occ[2]) {
   }
 }
 
-void flow_occupancy(int theory, int prec, int ts, bool one, int occ[2]) {
-  occ[0] = occ[1] = 1;
+void flow_occupancy(int theory, int prec, int ts, bool one, int occ[3]) {
+  occ[0] = occ[1] = occ[2] = 1;
   if (theory == TH_AH) occupancy_sel<TH_AH>(prec, ts, one, occ);
   else occupancy_sel<TH_CM>(prec, ts, one, occ);
-  for (int i = 0; i < 2; ++i)
+  for (int i = 0; i < 3; ++i)
     if (occ[i] < 1) occ[i] = 1;
 }
 
 // Default grid of each pass: its occupancy x SMs, capped by the tile count.
-void flow_grid(int theory, int prec, int ts, int total_tiles, bool one, int blocks[2]) {
+void flow_grid(int theory, int prec, int ts, int total_tiles, bool one, int blocks[3]) {
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  int occ[2];
+  int occ[3];
   flow_occupancy(theory, prec, ts, one, occ);
-  for (int i = 0; i < 2; ++i) {
+  for (int i = 0; i < 3; ++i) {
     const int g = nsm * occ[i];
     blocks[i] = total_tiles < g ? total_tiles : g;
   }

@@ -48,12 +48,19 @@ struct ProbDesc {
   R* v[2];          // ping-pong velocities
   R* kv[2];         // k_v1, k_v2
   R dt;
+  R tau;            // gradient descent: the step dtau of phi <- phi - dtau G
   Spacing<R> h;
   Couplings<R> k;
   double area;      // dx dy
   DevState* st;     // the problem's flow record
   FlowPartial* part;  // ntiles reduction partials
 };
+
+// Minimisers (the SS_METHOD_* values of soliton.h).
+enum { METHOD_ANF = 0, METHOD_GD = 1 };
+
+// Pass numbers of launch_pass: the arrested flow's two passes and the descent pass.
+enum { PASS_ANF1 = 1, PASS_ANF2 = 2, PASS_GD = 3 };
 
 // A batch launch: the problem table, the tile -> problem map, the grid.
 struct BatchLaunch {
@@ -62,7 +69,7 @@ struct BatchLaunch {
   const void* probs; // ProbDesc<R>[n] on the device
   const int* tile_prob;  // [total_tiles] problem index of every tile
   int total_tiles;
-  int flow_blocks[2];  // grid of pass 1 / pass 2
+  int flow_blocks[3];  // grid of pass 1 / pass 2 / the descent pass
   const void* one;     // host copy of the ProbDesc<R> of a single-problem batch, else NULL
   int ts;              // tile shape: 0 small, 1 large (flow_tile_dims)
 };
@@ -72,12 +79,15 @@ void flow_tile_dims(int prec, int ts, int* tx, int* ty);
 
 // Pass 1 (RK stages 1-2, reductions, arrest and convergence decisions) or pass 2
 // (RK stages 3-4, combination) of one flow step of every problem of a batch that
-// is still running (Sec. 3.2). Each problem uses its own ping-pong parity.
+// is still running (Sec. 3.2), or pass 3: one gradient-descent step (force,
+// reductions, decision and the new field in one launch). Each problem uses its own
+// ping-pong parity.
 cudaError_t launch_pass(const BatchLaunch& b, int pass, cudaStream_t s);
 // Control kernels over the n flow records of a batch.
 cudaError_t launch_reset_states(DevState* st, int n, cudaStream_t s);
 cudaError_t launch_set_run_all(DevState* st, int n, double tol, long long max_steps, cudaStream_t s);
-// Number of problems still running (not converged, finite, under the step limit).
+// Number of problems still running (not converged, finite, and under the step
+// limit or with the field of its last step not yet evaluated).
 cudaError_t launch_count_active(const DevState* st, int n, int* out, cudaStream_t s);
 
 // Control kernels: reset the flow record for new fields; start a run with a
@@ -94,10 +104,10 @@ cudaError_t launch_ansatz(const LaunchCtx& c, const double* d_sol, int n, cudaSt
 // Record the calling thread's error message for ss_last_error().
 void set_last_error(const std::string& msg);
 
-// Grid of each flow pass (its occupancy x SMs, capped by the tile count).
-void flow_grid(int theory, int prec, int ts, int total_tiles, bool one, int blocks[2]);
-// Blocks of each pass that fit on one SM.
-void flow_occupancy(int theory, int prec, int ts, bool one, int occ[2]);
+// Grid of each flow pass 1, 2, 3 (its occupancy x SMs, capped by the tile count).
+void flow_grid(int theory, int prec, int ts, int total_tiles, bool one, int blocks[3]);
+// Blocks of each pass 1, 2, 3 that fit on one SM.
+void flow_occupancy(int theory, int prec, int ts, bool one, int occ[3]);
 int obs_grid(int theory, int prec, int ntiles);
 
 }  // namespace ss

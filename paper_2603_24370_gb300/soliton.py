@@ -32,6 +32,8 @@ SS_FP64 = 2
 SS_FP32_PLAIN = 3  # one FP32 plane per component
 SS_ABELIAN_HIGGS = 1
 SS_CHIRAL_MAGNET = 2
+SS_METHOD_ANF = 0       # arrested Newton flow (default)
+SS_METHOD_GRADIENT = 1  # gradient descent phi <- phi - dtau G
 
 _ERR_NAMES = {
     SS_ERR_ARG: "SS_ERR_ARG", SS_ERR_STATE: "SS_ERR_STATE", SS_ERR_CUDA: "SS_ERR_CUDA",
@@ -119,6 +121,8 @@ def load_library(path: str | None = None):
             "ss_autotune": ([vp, i, ctypes.POINTER(ctypes.c_int)], i),
             "ss_batch_set_launch": ([vp, i, ctypes.POINTER(ctypes.c_int)], i),
             "ss_set_launch": ([vp, i, ctypes.POINTER(ctypes.c_int)], i),
+            "ss_batch_set_method": ([vp, i, d], i),
+            "ss_set_method": ([vp, i, d], i),
             "ss_batch_observables": ([vp, i, ctypes.POINTER(ss_obs)], i),
             "ss_batch_destroy": ([vp], i),
             "ss_destroy": ([vp], i),
@@ -249,7 +253,7 @@ def ss_observables(ctx) -> dict:
 def ss_profile_stages(ctx, n_steps: int) -> list[float]:
     """Mean device milliseconds of the step's two kernels (pass 1: RK stages 1-2 +
     reductions + arrest decision; pass 2: RK stages 3-4 + combination) over n_steps
-    real flow steps."""
+    real flow steps; under gradient descent [descent kernel, 0.0]."""
     ms = (ctypes.c_float * 2)()
     _check(load_library().ss_profile_stages(ctx, int(n_steps), ms))
     return [float(x) for x in ms]
@@ -366,6 +370,14 @@ def ss_set_launch(ctx, tile_shape: int, blocks=None) -> None:
     _check(load_library().ss_set_launch(ctx, tile_shape, _blocks(blocks)))
 
 
+def ss_batch_set_method(b, method: int, step_factor: float = 0.0) -> None:
+    _check(load_library().ss_batch_set_method(b, int(method), float(step_factor)))
+
+
+def ss_set_method(ctx, method: int, step_factor: float = 0.0) -> None:
+    _check(load_library().ss_set_method(ctx, int(method), float(step_factor)))
+
+
 def ss_batch_observables(b, item: int) -> dict:
     o = ss_obs()
     _check(load_library().ss_batch_observables(b, int(item), ctypes.byref(o)))
@@ -441,6 +453,11 @@ class Solver:
 
     def set_launch(self, tile_shape: int, blocks=None) -> None:
         ss_set_launch(self.ctx, tile_shape, blocks)
+
+    def set_method(self, method: int, step_factor: float = 0.0) -> None:
+        """SS_METHOD_ANF or SS_METHOD_GRADIENT (dtau = step_factor x the stability
+        limit, 0.8 when <= 0); the flow restarts from the current field at rest."""
+        ss_set_method(self.ctx, method, step_factor)
 
     def minimise(self, tol: float, max_steps: int):
         return ss_minimise(self.ctx, tol, max_steps)

@@ -1,0 +1,217 @@
+"""Gradient descent (the first-order method Sec. 3.2 compares the arrested flow
+against) on the CUDA path vs the FP64 oracle, through the C-ABI.
+
+The descent step phi - dtau G(phi) shares the flow kernels' staging, stencils and
+forces, so the tolerances are those of test_gpu_parity.py: FP64 fields 1e-10 of
+their scale after tens of steps, energies 1e-12 relative; FP32 (compensated or
+plain) 2e-5 of the field scale and 1e-5 relative in energy. The step dtau is
+0.8 x the stability limit on both sides, each computed by its own code.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2603_24370_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+AH, CM = 1, 2
+AH_PRM = (1.0, 1.0)
+CM_PRM = (1.0, 1.0, 0.1, 0.6, 0.0)
+GRIDS = {AH: (77, 45, 0.2, 0.17), CM: (83, 38, 0.2, 0.23)}  # ragged tiles, unequal spacings
+
+
+@pytest.fixture(scope="module")
+def S():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2603_24370_gb300 import build
+    from paper_2603_24370_gb300 import soliton as S
+    build.build()
+    S.load_library()
+    return S
+
+
+def prm(theory):
+    return AH_PRM if theory == AH else CM_PRM
+
+
+def dtype_of(prec):
+    return np.float64 if prec == 2 else np.float32
+
+
+def oracle_descent(theory, f, dx, dy, n, factor=0.8):
+    fo = f.astype(np.float64)
+    E = O.energy(theory, prm(theory), fo, dx, dy)
+    dtau = factor * O.gd_step_limit(dx, dy)
+    rises = 0
+    for _ in range(n):
+        fo, E, r = O.gd_step(theory, prm(theory), fo, dx, dy, dtau, E)
+        rises += r
+    return fo, E, rises
+
+
+@pytest.mark.parametrize("theory", [AH, CM])
+@pytest.mark.parametrize("prec", [1, 2, 3])
+def test_descent_trajectory_matches_oracle(S, theory, prec):
+    nx, ny, dx, dy = GRIDS[theory]
+    n = 40
+    f = I.smooth_field(theory, nx, ny, dx, dy, seed=505).astype(dtype_of(prec))
+    with S.Solver(theory, prm(theory), nx, ny, dx, dy, prec) as s:
+        s.set_fields(f)
+        s.set_method(S.SS_METHOD_GRADIENT)
+        st = s.step(n)
+        fg = s.exact_fields() if prec == 1 else s.fields().astype(np.float64)
+        vg = s.velocity()
+        G, Eg, gmax = s.force()
+        og = s.observables()
+    fo, Eo, rises = oracle_descent(theory, f, dx, dy, n)
+    tol = 1e-10 if prec == 2 else 2e-5
+    assert np.abs(fg - fo).max() <= tol * max(1.0, np.abs(fo).max())
+    assert st["steps"] == n and st["arrests"] == rises == 0 and not st["arrested"]
+    assert not vg.any()  # first-order flow: no velocity
+    # the status describes the final field (the run ends with its evaluation)
+    assert st["energy"] == pytest.approx(Eo, rel=1e-12 if prec == 2 else 1e-5)
+    assert og["energy"] == pytest.approx(Eo, rel=1e-12 if prec == 2 else 1e-5)
+    Go = O.force(theory, prm(theory), fo, dx, dy)
+    assert np.abs(G.astype(np.float64) - Go).max() <= (1e-9 if prec == 2 else 3e-4) * np.abs(Go).max()
+    assert Eg == st["energy"] and gmax == st["grad_max"]
+    if theory == CM:
+        assert np.abs(np.sqrt((fg * fg).sum(axis=0)) - 1.0).max() < (1e-13 if prec == 2 else 1e-6)
+
+
+@pytest.mark.parametrize("theory", [AH, CM])
+def test_descent_minimise_reaches_the_oracles_minimum(S, theory):
+    """Small well-resolved problems to dx dy max|G| < 1e-6 in FP64 and compensated
+    FP32: the same step count as the oracle (FP64: +-1 for a residual at the
+    threshold), the same energy, and more steps than the arrested flow needs."""
+    if theory == AH:
+        nx = ny = 48
+        dx = dy = 0.25
+        sol, pr = [[0.0, 0.0, 1, 1.0, 0.0]], AH_PRM
+    else:
+        p = I.cm_skyrmions(n=48, count=1, seed=3, min_sep=8.0, margin=4.0)
+        nx, ny, dx, dy, sol, pr = p.nx, p.ny, p.dx, p.dy, p.soliton_array().tolist(), p.params
+    f = O.ansatz(theory, sol, nx, ny, dx, dy)
+    ref = O.gd_minimise(theory, pr, f, dx, dy, tol=1e-6, max_steps=200_000)
+    anf = O.minimise(theory, pr, f, dx, dy, tol=1e-6, max_steps=50_000)
+    assert ref["converged"] and anf["converged"]
+    for prec in (2, 1):
+        with S.Solver(theory, pr, nx, ny, dx, dy, prec) as s:
+            s.init_ansatz(sol)
+            s.set_method(S.SS_METHOD_GRADIENT)
+            st = s.minimise(1e-6, 200_000)
+            fg = s.exact_fields() if prec == 1 else s.fields()
+        assert st["converged"]
+        # rises are judged on the working-precision energies: exact enough in FP64;
+        # in FP32 near convergence the per-step decrease is below the sum's rounding
+        if prec == 2:
+            assert st["arrests"] == 0
+        # FP32: the residual's rounding noise near 1e-6 moves the stopping step by
+        # (noise / residual) / (dtau lambda_min) steps: a few % of the total
+        slack = 1 if prec == 2 else max(5, ref["steps"] // 20)
+        assert abs(st["steps"] - ref["steps"]) <= slack, (prec, st["steps"], ref["steps"])
+        # the working-precision energy, and the FP64 energy of the field reached (FP32:
+        # stopping up to `slack` steps off moves E by that many per-step decreases,
+        # ~1e-8 of E here)
+        assert st["energy"] == pytest.approx(ref["energy"], rel=1e-10 if prec == 2 else 1e-5)
+        assert O.energy(theory, pr, fg, dx, dy) == pytest.approx(ref["energy"], rel=1e-10 if prec == 2 else 1e-7)
+        # FP32: over ~1e4 steps the force's rounding noise drifts along the slowest
+        # modes; two fields that both meet 1e-6 lie ~1e-4 apart along them (as the
+        # oracle's arrested-flow and descent minima do)
+        assert np.abs(fg - ref["f"]).max() < (1e-8 if prec == 2 else 1e-4)
+        assert st["steps"] > anf["steps"]
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_descent_batch_problems_evolve_exactly_as_alone(S, prec):
+    from test_gpu_batch import mixed_batch
+    probs = mixed_batch(count=6, seed=31)
+    b = S.ss_batch_create(S.SS_ABELIAN_HIGGS, prec, probs)
+    try:
+        S.ss_batch_set_method(b, S.SS_METHOD_GRADIENT, 0.7)
+        rc, st = S.ss_batch_step(b, 37)
+        dt = np.float64 if prec == 2 else np.float32
+        for k, p in enumerate(probs):
+            got = np.empty((4, p.ny, p.nx), dtype=dt)
+            S.ss_batch_get_fields(b, k, got)
+            with S.Solver(S.SS_ABELIAN_HIGGS, p.params, p.nx, p.ny, p.dx, p.dy, prec) as s:
+                s.init_ansatz(p.solitons)
+                s.set_method(S.SS_METHOD_GRADIENT, 0.7)
+                st1 = s.step(37)
+                ref = s.fields()
+            assert np.array_equal(got, ref), k
+            assert st[k]["steps"] == 37 and st[k]["arrests"] == 0
+            assert st[k]["energy"] == pytest.approx(st1["energy"], rel=1e-13 if prec == 2 else 1e-8)
+            if prec == 2:
+                f = O.ansatz(1, p.soliton_array(), p.nx, p.ny, p.dx, p.dy)
+                dtau = 0.7 * O.gd_step_limit(p.dx, p.dy)
+                E = O.energy(1, p.params, f, p.dx, p.dy)
+                for _ in range(37):
+                    f, E, _ = O.gd_step(1, p.params, f, p.dx, p.dy, dtau, E)
+                assert np.abs(got - f).max() <= 1e-10 * np.abs(f).max()
+    finally:
+        S.ss_batch_destroy(b)
+
+
+def test_method_switch_restarts_from_the_current_field(S):
+    """Descent, then the arrested flow from the field descent reached (at rest, step
+    count restarted), then descent again: each leg matches the oracle from the field
+    the previous leg left."""
+    nx, ny, dx, dy = GRIDS[AH]
+    f0 = I.smooth_field(AH, nx, ny, dx, dy, seed=606)
+    with S.Solver(AH, AH_PRM, nx, ny, dx, dy, 2) as s:
+        s.set_fields(f0)
+        s.set_method(S.SS_METHOD_GRADIENT)
+        s.step(7)  # odd: the field sits in the second ping-pong buffer
+        f1 = s.fields()
+        s.set_method(S.SS_METHOD_ANF)
+        st = s.step(9)
+        f2 = s.fields()
+        v2 = s.velocity()
+        s.set_method(S.SS_METHOD_GRADIENT, 0.5)
+        st3 = s.step(5)
+        f3 = s.fields()
+    fo, _, _ = oracle_descent(AH, f0, dx, dy, 7)
+    assert np.abs(f1 - fo).max() <= 1e-11
+    fa, va = fo.copy(), np.zeros_like(fo)
+    E = O.energy(AH, AH_PRM, fa, dx, dy)
+    arrests = 0
+    for _ in range(9):
+        fa, va, E, a = O.anf_step(AH, AH_PRM, fa, va, dx, dy, O.time_step(dx, dy), E)
+        arrests += a
+    assert st["steps"] == 9 and st["arrests"] == arrests
+    assert np.abs(f2 - fa).max() <= 1e-10 and np.abs(v2 - va).max() <= 1e-9
+    fg, _, _ = oracle_descent(AH, fa, dx, dy, 5, factor=0.5)
+    assert st3["steps"] == 5 and np.abs(f3 - fg).max() <= 1e-10
+
+
+def test_descent_budget_edges_and_arguments(S):
+    nx, ny, dx, dy = GRIDS[CM]
+    f = I.smooth_field(CM, nx, ny, dx, dy, seed=707)
+    with S.Solver(CM, CM_PRM, nx, ny, dx, dy, 2) as s:
+        s.set_fields(f)
+        s.set_method(S.SS_METHOD_GRADIENT)
+        st0 = s.step(0)  # evaluates the field, takes no step
+        assert st0["steps"] == 0
+        assert st0["energy"] == pytest.approx(O.energy(CM, CM_PRM, f, dx, dy), rel=1e-12)
+        st = s.minimise(1e-300, 3)  # budget runs out first
+        assert not st["converged"] and st["steps"] == 3
+        st = s.minimise(1e3, 10)  # already below a loose tolerance: no step
+        assert st["converged"] and st["steps"] == 3
+        with pytest.raises(S.SolitonError):
+            s.set_method(S.SS_METHOD_GRADIENT, 1.5)
+        with pytest.raises(S.SolitonError):
+            s.set_method(7)
+        choice = s.autotune(4)  # times the descent kernel alone
+        assert choice["tile_shape"] in (0, 1) and choice["blocks"][0] >= 1 and choice["blocks"][1] == 0
+        s.set_launch(0, [152, 1])
+        st = s.step(4)
+        assert st["steps"] == 4
+        ms = S.ss_profile_stages(s.ctx, 3)
+        assert ms[0] > 0.0 and ms[1] == 0.0
+        fg = s.fields()
+    # autotune restarted from the field at the call (after 3 steps); then 4 + 3 steps
+    fo, _, _ = oracle_descent(CM, f, dx, dy, 10)
+    assert np.abs(fg - fo).max() <= 1e-10
