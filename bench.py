@@ -21,6 +21,11 @@ oracle flow step on a 512 x 512 crop of the same workload.
 (Abelian Higgs 128^2 FP64, chiral magnet 1024^2, chiral magnet 4096^2) on the GPU and
 with the FP64 oracle on the host cores.
 
+--workload methods: arrested Newton flow against gradient descent (the first-order
+method Sec. 3.2 compares it with; explicit Euler at 0.8 x its stability limit) on
+the same configurations and precisions, each to dx dy max|G| < 1e-6 or a step cap:
+steps, force evaluations (4 per flow step, 1 per descent step) and seconds.
+
 --workload ah-batch: time per solve to dx dy max|G| < 1e-6 on the batched Abelian
 Higgs set (256 problems, sides 64..512, dx = 0.1, lambda ~ U[0.5, 2], N in 1..4):
 one bench step = the whole set relaxed in one batch (compensated FP32), against
@@ -538,6 +543,53 @@ def run_configs(args) -> int:
     return 0
 
 
+def run_methods(args) -> int:
+    """Arrested Newton flow vs gradient descent, to dx dy max|G| < 1e-6 or a cap."""
+    rank, local_rank, world = D.env_rank()
+    if rank != 0:
+        return 0
+    D.pin_visible_device(local_rank, 1)
+    import torch
+    from paper_2603_24370_gb300 import build as B
+    from paper_2603_24370_gb300 import inputs as I
+    from paper_2603_24370_gb300 import soliton as S
+    B.build()
+    S.load_library()
+
+    def solve(p, prec, method, cap):
+        with S.Solver(p.theory, p.params, p.nx, p.ny, p.dx, p.dy, prec) as sv:
+            sv.init_ansatz(p.soliton_array())
+            sv.set_method(method)
+            sv.autotune(4)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = sv.minimise(1e-6, cap)
+            torch.cuda.synchronize()
+            sec = time.perf_counter() - t0
+            o = sv.observables()
+        per = 4 if method == S.SS_METHOD_ANF else 1
+        return {"seconds": round(sec, 4), "steps": r["steps"], "force_evals": per * r["steps"],
+                "converged": bool(r["converged"]), "grad_max": r["grad_max"], "energy": o["energy"],
+                "charge": o["charge"], "arrests_or_rises": r["arrests"], "step_cap": cap}
+
+    cases = [("ah128", I.ah_single_vortex(), S.SS_FP64, 2_000_000),
+             ("cm1024", I.cm_skyrmions(), S.SS_FP32, 2_000_000),
+             ("cm4096", I.cm_skyrmions(n=N, count=COUNT, seed=SEED), S.SS_FP32, 200_000)]
+    out = {}
+    for name, p, prec, gd_cap in cases:
+        anf = solve(p, prec, S.SS_METHOD_ANF, 100_000)
+        gd = solve(p, prec, S.SS_METHOD_GRADIENT, gd_cap)
+        out[name] = {"precision": {1: "fp32c", 2: "fp64", 3: "fp32"}[prec], "anf": anf, "gradient": gd,
+                     "gd_over_anf": {"steps": round(gd["steps"] / max(anf["steps"], 1), 2),
+                                     "force_evals": round(gd["force_evals"] / max(anf["force_evals"], 1), 2),
+                                     "seconds": round(gd["seconds"] / max(anf["seconds"], 1e-9), 2)}}
+        print(json.dumps({name: out[name]}), file=sys.stderr, flush=True)
+    line = {"metric": "minimiser comparison to dx dy max|G| < 1e-6", "unit": "s", "higher_is_better": False,
+            "n_gpus": 1, "data": "synthetic", "gd_step": "0.8 x (3/8) / (1/dx^2 + 1/dy^2)", "configs": out}
+    print(json.dumps(line))
+    return 0
+
+
 def main() -> int:
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -546,7 +598,7 @@ def main() -> int:
     ap.add_argument("--impl", choices=("native", "reference"), default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grid", type=int, default=N, help="grid side (default: the 4096 workload; smaller for ncu)")
-    ap.add_argument("--workload", choices=("cm4096", "ah-batch", "configs"), default="cm4096")
+    ap.add_argument("--workload", choices=("cm4096", "ah-batch", "configs", "methods"), default="cm4096")
     ap.add_argument("--tile-shape", choices=("auto", "0", "1"), default="auto",
                     help="flow tile shape: autotuned (default) or fixed (for profiling one shape)")
     ap.add_argument("--fp64-per-side", type=int, default=2, help="ah-batch: FP64 problems timed per side")
@@ -560,6 +612,8 @@ def main() -> int:
         return run_solve(args)
     if args.workload == "configs":
         return run_configs(args)
+    if args.workload == "methods":
+        return run_methods(args)
     return run_native(args)
 
 
