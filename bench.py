@@ -68,6 +68,9 @@ def interior(n: int) -> int:
 # v, phi^{n-1} and writes k_v1, k_v2 (7C values); pass 2 reads phi, v, k_v1, k_v2
 # and writes phi', v' (8C values).
 PASS_BYTES = {1: 4 * 7 * C, 2: 4 * 8 * C}
+# the gradient-descent kernel (--method gradient) reads phi (value, remainder) and
+# writes phi' (value, remainder) and -G: 5C values
+GD_BYTES = 4 * 5 * C
 
 
 def measured_peaks() -> tuple[dict, str]:
@@ -234,6 +237,9 @@ def run_native(args) -> int:
     stream = torch.cuda.Stream()
     s = S.Solver(S.SS_CHIRAL_MAGNET, p.params, n, n, DX, DX, S.SS_FP32, stream=stream)
     s.init_ansatz(p.soliton_array())
+    gd = args.method == "gradient"
+    if gd:
+        s.set_method(S.SS_METHOD_GRADIENT)
     if args.tile_shape == "auto":
         tuned = s.autotune(4)  # tile shape and pass grids for this grid (the flow restarts from rest)
     else:
@@ -241,6 +247,8 @@ def run_native(args) -> int:
         tuned = {"tile_shape": int(args.tile_shape), "blocks": None, "set_by_hand": True}
     f_init = s.fields()
     launches_per_call = 2 + ((INNER + 31) // 32) * 32 * 2  # set_run + head + graph chunk(s)
+    if gd:  # set_run + INNER + 1 descent launches (the last evaluates the final field)
+        launches_per_call = 1 + INNER + 1
 
     for _ in range(args.warmup):
         s.step(INNER)
@@ -269,15 +277,19 @@ def run_native(args) -> int:
     peaks, src = measured_peaks()
     kname = f"k_pass<CM, float, {dominant}>"
     alg = PASS_BYTES[dominant] * interior(n)
-    achieved = alg / (stage_ms[dominant - 1] * 1e-3) / 1e9
+    if gd:
+        dominant, kname, alg = 3, "k_pass<CM, float, 3> (gradient descent)", GD_BYTES * interior(n)
+    kernel_ms = stage_ms[0] if gd else stage_ms[dominant - 1]
+    achieved = alg / (kernel_ms * 1e-3) / 1e9
     traffic = ncu_traffic(f"pass{dominant}", tuned["tile_shape"])
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "kernel": kname,
                 "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else "fallback 6.8 TB/s",
                 "algorithmic_bytes_per_launch": alg,
                 "pass_ms": stage_ms,
-                "step_bytes_per_site_update": sum(PASS_BYTES.values()),
-                "step_frac": (sum(PASS_BYTES.values()) * interior(n) / (sum(stage_ms) * 1e-3) / 1e9) / peaks["hbm_gbs"]}
+                "step_bytes_per_site_update": GD_BYTES if gd else sum(PASS_BYTES.values()),
+                "step_frac": ((GD_BYTES if gd else sum(PASS_BYTES.values())) * interior(n)
+                              / (sum(stage_ms) * 1e-3) / 1e9) / peaks["hbm_gbs"]}
 
     # end to end through the C-ABI with host buffers: field in from pinned memory,
     # 32 flow steps, field out to pinned memory, every bench step
@@ -302,7 +314,7 @@ def run_native(args) -> int:
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_sample()
     solve = None
-    if world == 1 and args.grid == N and not args.no_solve:
+    if world == 1 and args.grid == N and not args.no_solve and not gd:
         try:
             solve = solve_summary(S, I, np)
         except Exception as exc:  # recorded, never fatal for the throughput line
@@ -314,7 +326,9 @@ def run_native(args) -> int:
             "metric": "site-updates/s", "value": value, "unit": "site-updates/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * job_sec / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD if n == N else WORKLOAD.replace("4096x4096", f"{n}x{n}"),
+            "config": {"workload": (WORKLOAD if n == N else WORKLOAD.replace("4096x4096", f"{n}x{n}")).replace(
+                           "ANF-RK4 (2 fused kernels/step)",
+                           "gradient descent (1 fused kernel/step)" if gd else "ANF-RK4 (2 fused kernels/step)"),
                        "flow_steps_per_bench_step": INNER, "grid": [n, n],
                        "interior_sites": interior(n), "parallelism": "replicas" if world > 1 else "single",
                        "autotuned": tuned,
@@ -603,6 +617,8 @@ def main() -> int:
                     help="flow tile shape: autotuned (default) or fixed (for profiling one shape)")
     ap.add_argument("--fp64-per-side", type=int, default=2, help="ah-batch: FP64 problems timed per side")
     ap.add_argument("--no-solve", action="store_true", help="skip the time-per-solve record of the default run")
+    ap.add_argument("--method", choices=("anf", "gradient"), default="anf",
+                    help="minimiser timed by the default workload (gradient: one descent kernel per step)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -430,12 +430,15 @@ int batch_run(ss_batch* b, double tol, long long max_steps) {
   long long passes = max_steps;
   if (b->method == METHOD_GD) passes += 1;
   else SS_CK(launch_pass(b->BL, 1, b->stream));  // heads of the current fields (skipped where done)
-  const long long nchunks = (passes + K_CHUNK - 1) / K_CHUNK;
+  // whole chunks as graphs, the remainder (< K_CHUNK steps) as direct launches
+  const long long nchunks = passes / K_CHUNK;
+  const int rem = (int)(passes % K_CHUNK);
   if (nchunks > 0) {
     int rc = ensure_chunk(b);
     if (rc != SS_OK) return rc;
   }
   int prev = -1;
+  bool stopped = false;
   for (long long i = 0; i < nchunks; ++i) {
     const int slot = (int)(i & 1);
     SS_CK(cudaGraphLaunch(b->chunk, b->stream));
@@ -444,9 +447,20 @@ int batch_run(ss_batch* b, double tol, long long max_steps) {
     SS_CK(cudaEventRecord(b->ev[slot], b->stream));
     if (prev >= 0) {
       SS_CK(cudaEventSynchronize(b->ev[prev]));
-      if (b->h_active[prev] == 0) break;
+      if (b->h_active[prev] == 0) {
+        stopped = true;
+        break;
+      }
     }
     prev = slot;
+  }
+  for (int k = 0; k < rem && !stopped; ++k) {
+    if (b->method == METHOD_GD) {
+      SS_CK(launch_pass(b->BL, PASS_GD, b->stream));
+    } else {
+      SS_CK(launch_pass(b->BL, 2, b->stream));
+      SS_CK(launch_pass(b->BL, 1, b->stream));
+    }
   }
   return read_states(b);
 }

@@ -104,6 +104,10 @@ __device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) 
 // eta = |hi + t|^2 - 1 = (|hi|^2 - 1) + 2 hi.t + |t|^2, where |hi|^2 - 1 is formed
 // exactly (error-free products and sums), 1/|hi + t| = 1 + rho with
 // rho = -eta / (r (1 + r)), r = sqrt(1 + eta), and t' = t + rho (hi + t).
+// rho enters only as a correction of size |eta| / 2, so a few ulps of relative
+// error in it are harmless: r comes from the hardware reciprocal square root
+// (r = x rsqrt(x)) and the quotient from the fast division, which keeps the IEEE
+// division's range checks and slow path out of the kernels' inner loops.
 __device__ __forceinline__ void normalise_split(const float* hi, float* t) {
   float p[3], e[3];
 #pragma unroll
@@ -118,8 +122,9 @@ __device__ __forceinline__ void normalise_split(const float* hi, float* t) {
   const float ht = hi[0] * t[0] + hi[1] * t[1] + hi[2] * t[2];
   const float tt = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
   const float eta = q + (2.0f * ht + tt);
-  const float r = sqrtf(1.0f + eta);
-  const float rho = -eta / (r * (1.0f + r));
+  const float x = 1.0f + eta;
+  const float r = x * rsqrtf(x);
+  const float rho = __fdividef(-eta, r * (1.0f + r));
 #pragma unroll
   for (int c = 0; c < 3; ++c) t[c] = t[c] + rho * (hi[c] + t[c]);
 }
@@ -257,6 +262,16 @@ __device__ __forceinline__ RPair<double> pair_add(RPair<double> x, RPair<double>
 template <typename R>
 __device__ __forceinline__ R rmax(R a, R b) {
   return (b > a || b != b) ? b : a;  // propagates NaN
+}
+// Running maximum of |g| for a >= 0: on non-negative values the IEEE bit patterns
+// order as unsigned integers, with every NaN above +Inf, so one integer max keeps
+// the maximum and propagates NaN (as rmax does).
+__device__ __forceinline__ float absmax(float a, float g) {
+  return __uint_as_float(max(__float_as_uint(a), __float_as_uint(fabsf(g))));
+}
+__device__ __forceinline__ double absmax(double a, double g) {
+  return __longlong_as_double((long long)max((unsigned long long)__double_as_longlong(a),
+                                             (unsigned long long)__double_as_longlong(fabs(g))));
 }
 // Block-wide: thread 0 ends with the block's two pairs and maximum. sm holds
 // (NT / 32) * 5 values of R. Fixed shape: bitwise reproducible.
@@ -496,7 +511,7 @@ __global__ void __launch_bounds__(NT)
 #pragma unroll
             for (int c = 0; c < C; ++c) {
               kv1[c * P + s] = -G[c];
-              gmr = rmax(gmr, fabs(G[c]));
+              gmr = absmax(gmr, G[c]);
             }
             const R e = (TH == TH_AH) ? density_ah<R>(kc, v, fx, fy) : density_cm<R>(kc, v, fx, fy);
             const R t1 = es + e;
@@ -567,7 +582,7 @@ __global__ void __launch_bounds__(NT)
 #pragma unroll
             for (int c = 0; c < C; ++c) {
               kv1[c * P + s] = -G[c];
-              gmr = rmax(gmr, fabs(G[c]));
+              gmr = absmax(gmr, G[c]);
             }
             const R e = (TH == TH_AH) ? density_ah<R>(kc, v, fx, fy) : density_cm<R>(kc, v, fx, fy);
             const R t1 = es + e;
