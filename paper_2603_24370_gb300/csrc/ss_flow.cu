@@ -62,6 +62,33 @@
 // component. Blocks stride over the batch's tiles; the grid is occupancy x SMs.
 #include "ss_internal.h"
 
+// Launch-shape knobs of the three passes: sites staged per iteration of the tile
+// loading loop (their loads are all issued before any is used), and the resident
+// blocks per SM the register allocation of the single-problem chiral-magnet FP32
+// kernels must allow (1: no constraint; the other instances, whose descriptors
+// occupy registers or whose working type is wider, would spill and keep their
+// natural allocation).
+// Defaults measured best at 4096^2: pass 1 gains 4% from 3 blocks / SM with two
+// sites in flight, pass 2 2% from 5, the descent pass 8% from 6.
+#ifndef SS_LU1
+#define SS_LU1 2
+#endif
+#ifndef SS_LU2
+#define SS_LU2 2
+#endif
+#ifndef SS_LU3
+#define SS_LU3 4
+#endif
+#ifndef SS_MINB1
+#define SS_MINB1 3
+#endif
+#ifndef SS_MINB2
+#define SS_MINB2 5
+#endif
+#ifndef SS_MINB3
+#define SS_MINB3 6
+#endif
+
 namespace ss {
 
 // Tile shape: TS = 0 (small) or 1 (large) selects the rows each thread walks,
@@ -347,8 +374,13 @@ __device__ __forceinline__ void load_tile_ctx(TileCtx<R>& tc, const ProbDesc<R>&
 // One flow pass over every tile of a batch. ONE: the batch has a single problem,
 // whose descriptor arrives as a kernel parameter, so its pointers, spacings and
 // couplings are read as constant operands instead of occupying registers.
+template <int TH, typename R, int PASS, bool ONE>
+constexpr int pass_min_blocks() {
+  return (TH == TH_CM && sizeof(R) == 4 && ONE) ? (PASS == 1 ? SS_MINB1 : (PASS == 2 ? SS_MINB2 : SS_MINB3)) : 1;
+}
+
 template <int TH, typename R, int PASS, bool LO, bool ONE, int TS>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
     k_pass(const __grid_constant__ ProbDesc<R> one, const ProbDesc<R>* __restrict__ probs,
            const int* __restrict__ tile_prob, int total_tiles) {
   using T = FlowTile<R, TS>;
@@ -398,10 +430,8 @@ __global__ void __launch_bounds__(NT)
     const int x0 = (lt % D.ntx) * T::TX, y0 = (lt / D.ntx) * T::TY;
 
     // ---- stage inputs over the tile and its halo, LU sites per iteration (the loads
-    // of all LU sites are issued before any is used: more bytes in flight per thread;
-    // measured best: 3 for pass 1, 2 for pass 2, whose loads per site are heavier;
-    // pass 3 loads only phi)
-    constexpr int LU = PASS == 1 ? 3 : (PASS == 2 ? 2 : 4);
+    // of all LU sites are issued before any is used: more bytes in flight per thread)
+    constexpr int LU = PASS == 1 ? SS_LU1 : (PASS == 2 ? SS_LU2 : SS_LU3);
     for (int base = tid; base < T::SXY; base += LU * NT) {
       R pv[LU][C], lv[LU][C], vv[LU][C], k1v[LU][C], k2v[LU][C], pp[LU][C], lp[LU][C];
       bool in[LU], inside[LU];
