@@ -12,7 +12,7 @@
 //   Eq. 3  arrested Newton flow  phi'' = -grad E_h       (Sec. 3.2)
 //   Eq. 4  arrest test  E_h[phi^{n+1}] > E_h[phi^n]      (Sec. 3.2)
 //   Eq. 5  chiral-magnet energy functional               (Sec. 4.2)
-//   Table 1  energy functionals (Abelian Higgs row)      (Sec. 2.3)
+//   Table 1  energy functionals (Abelian Higgs and Baby Skyrme rows)  (Sec. 2.3)
 //
 // Readings of points the paper leaves open (each is listed with its reason in the
 // design notes of the repository):
@@ -32,6 +32,9 @@
 //     default, no demagnetising term; the unit-length constraint is enforced by
 //     normalising every RK stage input and the new field, tangent-projecting the
 //     force and the new velocity (Sec. 3.2, projection paragraph).
+//   * Baby Skyrme (Table 1): the Skyrme term's double sum over i, j is
+//     kappa^2/2 |d_1 m x d_2 m|^2; potential mu^2 (1 - m_3) + nu^2/2 m_1^2; the unit
+//     vector is projected exactly as the chiral magnet's.
 //   * Arrest compares potential energies with a strict '>' (Eq. 4).
 //   * Convergence measure: max over I and components of |dx dy G|.
 #include <cmath>
@@ -46,7 +49,10 @@ namespace {
 
 const double PI = 3.14159265358979323846;
 
-enum { TH_ABELIAN_HIGGS = 1, TH_CHIRAL_MAGNET = 2, TH_HARMONIC_TEST = 99 };
+enum { TH_ABELIAN_HIGGS = 1, TH_CHIRAL_MAGNET = 2, TH_BABY_SKYRME = 3, TH_HARMONIC_TEST = 99 };
+
+// Theories whose field is a unit 3-vector (normalised after every update).
+bool unit_vector(int theory) { return theory == TH_CHIRAL_MAGNET || theory == TH_BABY_SKYRME; }
 
 struct Grid {
   int nx, ny;
@@ -59,6 +65,7 @@ int ncomp(int theory) {
   switch (theory) {
     case TH_ABELIAN_HIGGS: return 4;   // psi_1, psi_2, A_1, A_2 (Table 1)
     case TH_CHIRAL_MAGNET: return 3;   // n_1, n_2, n_3 (Eq. 5)
+    case TH_BABY_SKYRME: return 3;     // m_1, m_2, m_3 (Table 1)
     case TH_HARMONIC_TEST: return 1;   // scalar test field
     default: return 0;
   }
@@ -177,6 +184,20 @@ double density_cm(const double* prm, const Site& s) {
   return ex + dmi + K * (1.0 - n[2] * n[2]) + h * (1.0 - n[2]);
 }
 
+// Baby Skyrme (Table 1): e = 1/2 |d m|^2 + kappa^2/4 sum_{i,j} |d_i m x d_j m|^2 + V(m).
+// The double sum counts d_1 m x d_2 m twice and the diagonal terms vanish, so the
+// Skyrme term is kappa^2/2 |d_1 m x d_2 m|^2. Potential family
+// V = mu^2 (1 - m_3) + nu^2/2 m_1^2 (the standard potential at nu = 0, the easy-plane
+// one at mu = 0). prm = {kappa, mu, nu}.
+double density_bs(const double* prm, const Site& s) {
+  const double k2 = prm[0] * prm[0], mu2 = prm[1] * prm[1], nu2 = prm[2] * prm[2];
+  const double a[3] = {s.fx[0], s.fx[1], s.fx[2]}, b[3] = {s.fy[0], s.fy[1], s.fy[2]};
+  double X[3];
+  cross(a, b, X);
+  return 0.5 * (dot3(a, a) + dot3(b, b)) + 0.5 * k2 * dot3(X, X) + mu2 * (1.0 - s.v[2]) +
+         0.5 * nu2 * s.v[0] * s.v[0];
+}
+
 // Harmonic test theory (oracle only, pins the time integrator): e = k/2 phi^2.
 double density_harm(const double* prm, const Site& s) { return 0.5 * prm[0] * s.v[0] * s.v[0]; }
 
@@ -184,6 +205,7 @@ double density(int theory, const double* prm, const Site& s) {
   switch (theory) {
     case TH_ABELIAN_HIGGS: return density_ah(prm, s);
     case TH_CHIRAL_MAGNET: return density_cm(prm, s);
+    case TH_BABY_SKYRME: return density_bs(prm, s);
     default: return density_harm(prm, s);
   }
 }
@@ -228,10 +250,32 @@ void force_cm(const double* prm, const Site& s, double G[3]) {
   for (int a = 0; a < 3; ++a) G[a] -= gn * n[a];
 }
 
+// Baby Skyrme: with a = d_1 m, b = d_2 m the Skyrme term S = kappa^2/2 (|a|^2 |b|^2 - (a.b)^2)
+// has dS/da = kappa^2 (|b|^2 a - (a.b) b), dS/db = kappa^2 (|a|^2 b - (a.b) a), and
+//   -d_1 dS/da - d_2 dS/db = -kappa^2 [ |b|^2 m_11 + |a|^2 m_22 - 2 (a.b) m_12
+//                                       + (b.m_12 - a.m_22) a + (a.m_12 - b.m_11) b ].
+// G = -lap m + that + dV/dm, then G <- G - (G . m) m.
+void force_bs(const double* prm, const Site& s, double G[3]) {
+  const double k2 = prm[0] * prm[0], mu2 = prm[1] * prm[1], nu2 = prm[2] * prm[2];
+  const double a[3] = {s.fx[0], s.fx[1], s.fx[2]}, b[3] = {s.fy[0], s.fy[1], s.fy[2]};
+  const double m11[3] = {s.fxx[0], s.fxx[1], s.fxx[2]}, m22[3] = {s.fyy[0], s.fyy[1], s.fyy[2]};
+  const double m12[3] = {s.fxy[0], s.fxy[1], s.fxy[2]};
+  const double aa = dot3(a, a), bb = dot3(b, b), ab = dot3(a, b);
+  const double ca = dot3(b, m12) - dot3(a, m22), cb = dot3(a, m12) - dot3(b, m11);
+  for (int c = 0; c < 3; ++c)
+    G[c] = -(m11[c] + m22[c]) - k2 * (bb * m11[c] + aa * m22[c] - 2.0 * ab * m12[c] + ca * a[c] + cb * b[c]);
+  G[0] += nu2 * s.v[0];
+  G[2] -= mu2;
+  const double n[3] = {s.v[0], s.v[1], s.v[2]};
+  const double gn = dot3(G, n);
+  for (int c = 0; c < 3; ++c) G[c] -= gn * n[c];
+}
+
 void force_site(int theory, const double* prm, const Site& s, double* G) {
   switch (theory) {
     case TH_ABELIAN_HIGGS: force_ah(prm, s, G); break;
     case TH_CHIRAL_MAGNET: force_cm(prm, s, G); break;
+    case TH_BABY_SKYRME: force_bs(prm, s, G); break;
     default: G[0] = prm[0] * s.v[0]; break;
   }
 }
@@ -273,6 +317,16 @@ void partials(int theory, const double* prm, const Site& s, double dv[4], double
       dv[a] = D * (b1[a] + b2[a]);
     }
     dv[2] += -2.0 * K * n[2] - h;
+  } else if (theory == TH_BABY_SKYRME) {
+    const double k2 = prm[0] * prm[0], mu2 = prm[1] * prm[1], nu2 = prm[2] * prm[2];
+    const double a[3] = {s.fx[0], s.fx[1], s.fx[2]}, b[3] = {s.fy[0], s.fy[1], s.fy[2]};
+    const double aa = dot3(a, a), bb = dot3(b, b), ab = dot3(a, b);
+    for (int c = 0; c < 3; ++c) {
+      dgx[c] = a[c] + k2 * (bb * a[c] - ab * b[c]);
+      dgy[c] = b[c] + k2 * (aa * b[c] - ab * a[c]);
+    }
+    dv[0] = nu2 * s.v[0];
+    dv[2] = -mu2;
   } else {
     dv[0] = prm[0] * s.v[0];
   }
@@ -426,7 +480,7 @@ int or_anf_step(int theory, const double* prm, double* f, double* v, int nx, int
   const Grid g{nx, ny, dx, dy};
   const int C = ncomp(theory);
   const size_t N = (size_t)C * g.plane();
-  const bool cm = (theory == TH_CHIRAL_MAGNET);
+  const bool cm = unit_vector(theory);
   // v and every G vanish on the halo, so every k_phi and k_v does too and the halo
   // stays fixed without special cases.
   std::vector<double> k1p(N), k1v(N), k2p(N), k2v(N), k3p(N), k3v(N), k4p(N), k4v(N), y(N);
@@ -509,7 +563,7 @@ int or_gd_step(int theory, const double* prm, double* f, int nx, int ny, double 
   std::vector<double> G(N);
   force(theory, prm, f, g, G.data());  // zero on the halo
   for (size_t k = 0; k < N; ++k) f[k] -= dtau * G[k];
-  if (theory == TH_CHIRAL_MAGNET) normalise(f, g);
+  if (unit_vector(theory)) normalise(f, g);
   const double E_new = energy(theory, prm, f, g);
   const int rose = E_new > *E_io ? 1 : 0;
   *E_io = E_new;
@@ -573,7 +627,7 @@ void or_observables(int theory, const double* prm, const double* f, int nx, int 
   const double gmax = max_abs(G.data(), N);
   out[0] = energy(theory, prm, f, g);
   out[1] = 0.0; out[2] = 0.0; out[3] = dx * dy * gmax; out[4] = gmax; out[5] = 0.0;
-  if (theory == TH_CHIRAL_MAGNET) {
+  if (unit_vector(theory)) {
     auto unit = [&](int i, int j, double n[3]) {
       const size_t k = (size_t)j * nx + i;
       const double r = std::sqrt(f[k] * f[k] + f[P + k] * f[P + k] + f[2 * P + k] * f[2 * P + k]);
@@ -651,7 +705,7 @@ void or_ansatz(int theory, const double* sol, int nsol, double* f, int nx, int n
         f[P + k] = mod * std::sin(ph);
         f[2 * P + k] = A1;
         f[3 * P + k] = A2;
-      } else if (theory == TH_CHIRAL_MAGNET) {
+      } else if (unit_vector(theory)) {
         double n1 = 0.0, n2 = 0.0, n3 = 1.0;
         for (int s = 0; s < nsol; ++s) {
           const double X = x - sol[5 * s], Y = y - sol[5 * s + 1];

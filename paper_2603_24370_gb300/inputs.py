@@ -40,6 +40,7 @@ class SplitMix64:
 # theory ids (same numbering as the C-ABI and the oracle)
 ABELIAN_HIGGS = 1
 CHIRAL_MAGNET = 2
+BABY_SKYRME = 3
 
 # Couplings of the workloads. Abelian Higgs: (lambda, u). Chiral magnet:
 # (J, D, K, h, dmi_type) with interfacial DMI (type 0).
@@ -142,9 +143,10 @@ def smooth_field(theory: int, nx: int, ny: int, dx: float, dy: float, seed: int,
     """A smooth random test field, float64 [C][ny][nx].
 
     Abelian Higgs: psi = (1 + s_1) + i s_2, A = (s_3, s_4), each s_c a sum of
-    Gaussian bumps with seeded centres, widths and amplitudes. Chiral magnet: a
-    unit field from smooth angles, n = (sin T cos P, sin T sin P, cos T) with
-    T, P sums of Gaussian bumps (unit length by construction, no normalisation).
+    Gaussian bumps with seeded centres, widths and amplitudes. Chiral magnet and
+    Baby Skyrme: a unit field from smooth angles, n = (sin T cos P, sin T sin P,
+    cos T) with T, P sums of Gaussian bumps (unit length by construction, no
+    normalisation).
     """
     rng = SplitMix64(seed)
     x = (np.arange(nx) - 0.5 * (nx - 1)) * dx
@@ -163,7 +165,7 @@ def smooth_field(theory: int, nx: int, ny: int, dx: float, dy: float, seed: int,
 
     if theory == ABELIAN_HIGGS:
         return np.stack([1.0 + bumpsum(), bumpsum(), bumpsum(), bumpsum()])
-    if theory == CHIRAL_MAGNET:
+    if theory in (CHIRAL_MAGNET, BABY_SKYRME):
         T = 0.6 + 3.0 * bumpsum()
         P = 5.0 * bumpsum()
         return np.stack([np.sin(T) * np.cos(P), np.sin(T) * np.sin(P), np.cos(T)])

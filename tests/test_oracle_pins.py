@@ -18,6 +18,8 @@ import oracle as O
 from paper_2603_24370_gb300 import inputs as I
 
 AH, CM, HARM = O.ABELIAN_HIGGS, O.CHIRAL_MAGNET, O.HARMONIC_TEST
+BS = O.BABY_SKYRME
+BS_PRM = (1.0, 0.7, 0.3)  # kappa, mu, nu
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_constants.json")
 AH_PRM = (1.0, 1.0)
 CM_PRM = (1.0, 1.0, 0.1, 0.6, 0.0)
@@ -256,11 +258,170 @@ def test_gauge_invariance_fourth_order():
     assert errs_g[0] / errs_g[1] > 12.0 and errs_g[1] < 1e-2
 
 
+# ---------------------------------------------------------------- Baby Skyrme (Table 1)
+def _bs_radial_energy(prm, w, N):
+    """2 pi int r dr [1/2 (f'^2 + N^2 sin^2 f / r^2) + kappa^2/2 N^2 sin^2 f f'^2 / r^2
+    + mu^2 (1 - cos f)] + pi int r dr nu^2/2 sin^2 f  (m_1^2 averages to sin^2 f / 2)."""
+    from scipy.integrate import quad
+    kappa, mu, nu = prm
+
+    def integrand(r):
+        f = math.pi * math.exp(-(r / w) ** 2)
+        fp = -2.0 * r / (w * w) * f
+        s2 = math.sin(f) ** 2
+        sig = 0.5 * (fp * fp + N * N * s2 / (r * r))
+        sky = 0.5 * kappa * kappa * N * N * s2 * fp * fp / (r * r)
+        pot = mu * mu * (1.0 - math.cos(f)) + 0.25 * nu * nu * s2
+        return (sig + sky + pot) * r
+
+    val, _ = quad(integrand, 1e-12, 40.0, epsabs=1e-13, epsrel=1e-13, limit=400)
+    return 2 * math.pi * val
+
+
+@pytest.mark.parametrize("N,prm", [(1, (1.0, 0.7, 0.0)), (2, (0.8, 0.5, 0.6))])
+def test_bs_energy_matches_radial_reduction(N, prm):
+    """Lattice energy of a smooth hedgehog m = (sin f cos N theta, sin f sin N theta, cos f),
+    f = pi exp(-r^2/w^2), converges at fourth order to the radial reduction of Table 1's
+    Baby Skyrme functional (Skyrme term kappa^2/2 |d_1 m x d_2 m|^2)."""
+    w = 2.5
+    Econt = _bs_radial_energy(prm, w, N)
+    errs = []
+    for n in (121, 241):
+        L = 24.0
+        dx = L / (n - 1)
+        X, Y = grid(n, n, dx, dx)
+        r = np.hypot(X, Y)
+        th = N * np.arctan2(Y, X)
+        f = np.pi * np.exp(-(r / w) ** 2)
+        field = np.stack([np.sin(f) * np.cos(th), np.sin(f) * np.sin(th), np.cos(f)])
+        errs.append(abs(O.energy(BS, prm, field, dx, dx) - Econt))
+    assert errs[1] < 2e-5 * Econt
+    assert 12.0 < errs[0] / errs[1] < 20.0
+
+
+def test_bs_skyrme_term_vanishes_on_one_dimensional_fields():
+    """For m = m(x) the vectors d_1 m and d_2 m are parallel (d_2 m = 0): E_h and G do
+    not depend on kappa at all."""
+    nx, ny, dx, dy = 30, 20, 0.3, 0.25
+    x = (np.arange(nx) - 0.5 * (nx - 1)) * dx
+    T = 0.4 + 0.9 * np.sin(0.5 * x)
+    P = 0.7 * np.cos(0.3 * x)
+    f = np.stack([np.broadcast_to(v, (ny, nx)) for v in (np.sin(T) * np.cos(P), np.sin(T) * np.sin(P), np.cos(T))])
+    E = [O.energy(BS, (k, 0.6, 0.4), f, dx, dy) for k in (0.0, 1.3)]
+    G = [O.force(BS, (k, 0.6, 0.4), f, dx, dy) for k in (0.0, 1.3)]
+    assert E[1] == pytest.approx(E[0], rel=1e-14)
+    np.testing.assert_allclose(G[1], G[0], rtol=0, atol=1e-13 * np.abs(G[0]).max())
+    # and the kappa term is not zero in general
+    g2 = I.smooth_field(BS, nx, ny, dx, dy, seed=9)
+    assert O.energy(BS, (1.3, 0.6, 0.4), g2, dx, dy) > O.energy(BS, (0.0, 0.6, 0.4), g2, dx, dy) + 1e-3
+
+
+def test_bs_uniform_fields_and_vacuum():
+    nx, ny, dx, dy = 14, 10, 0.3, 0.2
+    area = (nx - 4) * (ny - 4) * dx * dy
+    kappa, mu, nu = 1.1, 0.7, 0.45
+    m = np.array([0.48, -0.6, 0.64])
+    f = np.broadcast_to(m[:, None, None], (3, ny, nx)).copy()
+    exp = area * (mu * mu * (1 - m[2]) + 0.5 * nu * nu * m[0] ** 2)
+    assert O.energy(BS, (kappa, mu, nu), f, dx, dy) == pytest.approx(exp, rel=1e-13)
+    # force of a uniform field: the tangent part of dV/dm = (nu^2 m_1, 0, -mu^2)
+    g = np.array([nu * nu * m[0], 0.0, -mu * mu])
+    g = g - g.dot(m) * m
+    G = O.force(BS, (kappa, mu, nu), f, dx, dy)
+    np.testing.assert_allclose(G[:, 2:-2, 2:-2], np.broadcast_to(g[:, None, None], (3, ny - 4, nx - 4)), atol=1e-14)
+    vac = np.zeros((3, ny, nx))
+    vac[2] = 1.0
+    assert O.energy(BS, (kappa, mu, nu), vac, dx, dy) == 0.0
+    assert np.abs(O.force(BS, (kappa, mu, nu), vac, dx, dy)).max() == 0.0
+
+
+def test_bs_exact_symmetries():
+    """Table 1's Baby Skyrme functional is invariant under a joint rotation of space and
+    spin about e_3 when nu = 0 (90 degrees), and under the 180-degree one for any nu."""
+    n, dx = 24, 0.25
+    f = I.smooth_field(BS, n, n, dx, dx, seed=13)
+    g90 = np.stack([-_rot90_scalar(f[1]), _rot90_scalar(f[0]), _rot90_scalar(f[2])])
+    prm0 = (1.2, 0.6, 0.0)
+    assert O.energy(BS, prm0, g90, dx, dx) == pytest.approx(O.energy(BS, prm0, f, dx, dx), rel=1e-13)
+    Gf, Gg = O.force(BS, prm0, f, dx, dx), O.force(BS, prm0, g90, dx, dx)
+    Grot = np.stack([-_rot90_scalar(Gf[1]), _rot90_scalar(Gf[0]), _rot90_scalar(Gf[2])])
+    np.testing.assert_allclose(Gg, Grot, rtol=0, atol=1e-11 * np.abs(Gf).max())
+    r180 = lambda a: _rot90_scalar(_rot90_scalar(a))
+    g180 = np.stack([-r180(f[0]), -r180(f[1]), r180(f[2])])
+    assert O.energy(BS, BS_PRM, g180, dx, dx) == pytest.approx(O.energy(BS, BS_PRM, f, dx, dx), rel=1e-13)
+    # with nu > 0 the 90-degree rotation is not a symmetry
+    assert abs(O.energy(BS, BS_PRM, g90, dx, dx) - O.energy(BS, BS_PRM, f, dx, dx)) > 1e-6
+
+
+def _bs_hedgehog_minimum(kappa, mu):
+    """Energy of the charge-1 hedgehog minimum from the radial Euler-Lagrange ODE of
+    2 pi int r dr [f'^2/2 + sin^2 f/(2 r^2) + kappa^2 sin^2 f f'^2/(2 r^2) + mu^2 (1 - cos f)],
+    f(0) = pi, f -> 0: shooting on f'(0) by bisection, then quadrature."""
+    from scipy.integrate import quad, solve_ivp
+    k2, m2 = kappa * kappa, mu * mu
+
+    def rhs(r, y):
+        f, fp = y
+        s, c = math.sin(f), math.cos(f)
+        num = -fp + k2 * s * s * fp / (r * r) - k2 * s * c * fp * fp / r + s * c / r + m2 * r * s
+        return [fp, num / (r + k2 * s * s / r)]
+
+    def shoot(slope):
+        r0 = 1e-4
+        crosses = lambda r, y: y[0]
+        return solve_ivp(rhs, (r0, 14.0), [math.pi - slope * r0, -slope], rtol=1e-11, atol=1e-13,
+                         dense_output=True, events=[crosses])
+
+    lo, hi = 0.1, 5.0
+    for _ in range(60):
+        mid = 0.5 * (lo + hi)
+        if shoot(mid).t_events[0].size:
+            hi = mid
+        else:
+            lo = mid
+    sol = shoot(lo)
+    rs = np.linspace(1e-4, sol.t[-1], 20000)
+    rcut = rs[np.argmin(np.abs(sol.sol(rs)[0]))]
+
+    def dens(r):
+        f, fp = sol.sol(r)
+        s2 = math.sin(f) ** 2
+        return r * (0.5 * (fp * fp + s2 / (r * r)) + 0.5 * k2 * s2 * fp * fp / (r * r) + m2 * (1 - math.cos(f)))
+
+    return 2 * math.pi * quad(dens, 1e-4, rcut, limit=500, epsabs=1e-12, epsrel=1e-12)[0]
+
+
+@pytest.mark.slow
+def test_bs_skyrmion_relaxes_to_the_radial_minimum():
+    """The arrested flow relaxes a compact charge-1 ansatz to the baby skyrmion: its
+    energy converges at fourth order in dx to the minimum of the radial reduction
+    (independent shooting solution), above the bound 4 pi |Q| of the sigma-model term,
+    with the charge exact and |m| = 1."""
+    prm = (1.0, 0.7, 0.0)
+    Eref = _bs_hedgehog_minimum(prm[0], prm[1])
+    assert 4 * math.pi < Eref < 3 * 4 * math.pi
+    errs = []
+    for n, dx in ((96, 0.2), (192, 0.1)):
+        f = O.ansatz(BS, [[0.0, 0.0, 1.0, 2.5, 0.0]], n, n, dx, dx)
+        r = O.minimise(BS, prm, f, dx, dx, tol=1e-7, max_steps=20000)
+        assert r["converged"]
+        o = O.observables(BS, prm, r["f"], dx, dx)
+        assert o["charge"] == pytest.approx(-1.0, abs=1e-10)
+        assert o["norm_dev"] < 1e-14
+        errs.append(abs(o["energy"] - Eref))
+    assert errs[1] < 1e-4 * Eref
+    assert 12.0 < errs[0] / errs[1] < 20.0
+
+
 # ---------------------------------------------------------------- force (Eq. 3's right-hand side)
-@pytest.mark.parametrize("theory", [AH, CM])
+def _prm(theory):
+    return {AH: AH_PRM, CM: (1.0, 0.8, 0.15, 0.5, 0.0), BS: BS_PRM}[theory]
+
+
+@pytest.mark.parametrize("theory", [AH, CM, BS])
 def test_exact_gradient_matches_brute_force(theory):
     nx, ny, dx, dy = 12, 11, 0.3, 0.25
-    prm = AH_PRM if theory == AH else (1.0, 0.8, 0.15, 0.5, 0.0)
+    prm = _prm(theory)
     f = I.smooth_field(theory, nx, ny, dx, dy, seed=21, amplitude=0.5)
     grad = O.energy_grad_exact(theory, prm, f, dx, dy)
     eps = 1e-6
@@ -273,20 +434,21 @@ def test_exact_gradient_matches_brute_force(theory):
     np.testing.assert_allclose(grad, fd, rtol=0, atol=1e-7 * np.abs(grad).max())
 
 
-@pytest.mark.parametrize("theory", [AH, CM])
+@pytest.mark.parametrize("theory", [AH, CM, BS])
 def test_force_is_energy_gradient_to_fourth_order(theory):
-    """dx dy G and dE_h/dphi (tangent part for the chiral magnet) are two O(h^4)
+    """dx dy G and dE_h/dphi (tangent part for the unit-vector theories) are two O(h^4)
     discretisations of the same Euler-Lagrange expression: their gap shrinks ~16x per halving."""
-    prm = AH_PRM if theory == AH else (1.0, 0.8, 0.15, 0.5, 0.0)
+    prm = _prm(theory)
     errs = []
     for n in (41, 81):
         L = 8.0
         dx = L / (n - 1)
         dy = 0.9 * dx
-        f = I.smooth_field(theory, n, n, dx, dy, seed=7)
+        # the quartic Skyrme term needs a gentler field to be in the asymptotic regime
+        f = I.smooth_field(theory, n, n, dx, dy, seed=7, amplitude=0.15 if theory == BS else 0.3)
         G = O.force(theory, prm, f, dx, dy)
         gr = O.energy_grad_exact(theory, prm, f, dx, dy) / (dx * dy)
-        if theory == CM:
+        if theory in (CM, BS):
             gr = gr - (gr * f).sum(axis=0, keepdims=True) * f
         k = 4 if n == 41 else 8  # same physical margin on both grids
         errs.append(np.abs(G - gr)[:, k:-k, k:-k].max() / np.abs(G).max())
