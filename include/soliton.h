@@ -65,6 +65,10 @@ extern "C" {
 #define SS_CHIRAL_MAGNET 2 /* Eq. 5 without demag, params {J, D, K, h, dmi_type}:       */
                            /* dmi_type 0 interfacial (d_i = e_3 x e_i), 1 bulk (d_i = e_i),*/
                            /* 2 D_2d "Heusler" (d_1 = e_1, d_2 = -e_2)                     */
+#define SS_BABY_SKYRME 3   /* Table 1, params {kappa, mu[, nu]}: unit 3-vector m with       */
+                           /* e = |d m|^2/2 + kappa^2/2 |d_1 m x d_2 m|^2 + V(m),            */
+                           /* V = mu^2 (1 - m_3) + nu^2/2 m_1^2 (standard potential at nu = 0,*/
+                           /* easy-plane at mu = 0); projected like the chiral magnet       */
 
 /* ---- minimisers ---- */
 #define SS_METHOD_ANF 0      /* arrested Newton flow, RK4 + Eq. 4 (Sec. 3.2): the default */
@@ -79,7 +83,7 @@ typedef struct ss_ctx ss_ctx;
  * paper gives no formula, the standard forms are used):
  *  Abelian Higgs: psi = prod_k tanh(r_k/size_k)^|charge_k| exp(i (charge_k theta_k + phase_k)),
  *                 A = sum_k charge_k tanh(r_k/size_k)^2 (-(y-y_k), x-x_k) / r_k^2.
- *  Chiral magnet: compact skyrmion of radius R = size, vorticity m = charge,
+ *  Chiral magnet and Baby Skyrme: compact skyrmion of radius R = size, vorticity m = charge,
  *                 helicity gamma = phase: n = (sin f cos(m theta + gamma),
  *                 sin f sin(m theta + gamma), cos f), f = pi (1 - r/R) for r < R,
  *                 n = e_3 outside every disc; the first disc containing a site wins.
@@ -137,7 +141,8 @@ int ss_create_grid(ss_ctx** out, int nx, int ny, double dx, double dy, int preci
 /* Select the theory and its couplings (Sec. 3.1 "theory-specific parameters packed
  * into device arrays"; Table 1; Eq. 5). params is a host array of n_params
  * doubles: Abelian Higgs {lambda, u} (u defaults to 1 if n_params == 1); chiral
- * magnet {J, D, K, h, dmi_type} (dmi_type defaults to 0 if n_params == 4).
+ * magnet {J, D, K, h, dmi_type} (dmi_type defaults to 0 if n_params == 4); Baby
+ * Skyrme {kappa, mu, nu} (nu defaults to 0 if n_params == 2).
  * Allocates the device buffers; previous fields are discarded.
  * Errors: SS_ERR_ARG (unknown theory, bad n_params, J <= 0), SS_ERR_NOMEM, SS_ERR_CUDA. */
 int ss_set_theory(ss_ctx* ctx, int theory, const double* params, int n_params);

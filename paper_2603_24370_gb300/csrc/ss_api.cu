@@ -82,10 +82,24 @@ int pack_couplings(int theory, const double* params, int n_params, double k[10],
     else if (type == 1) { k[4] = 1.0; k[8] = 1.0; }  // d_i = e_i
     else { k[4] = 1.0; k[8] = -1.0; }                // d_1 = e_1, d_2 = -e_2
     *C = 3;
+  } else if (theory == SS_BABY_SKYRME) {
+    if (n_params < 2 || n_params > 3) return fail(SS_ERR_ARG, "Baby Skyrme takes {kappa, mu[, nu]}");
+    for (int i = 0; i < n_params; ++i)
+      if (!std::isfinite(params[i])) return fail(SS_ERR_ARG, "Baby Skyrme parameters must be finite");
+    const double nu = n_params > 2 ? params[2] : 0.0;
+    k[0] = params[0] * params[0];  // kappa^2 (Skyrme term)
+    k[1] = params[1] * params[1];  // mu^2 (1 - m_3)
+    k[2] = nu * nu;                // nu^2 / 2 m_1^2
+    *C = 3;
   } else {
     return fail(SS_ERR_ARG, "unknown theory");
   }
   return SS_OK;
+}
+
+// Kernel theory tag of an SS_* theory code.
+int th_of(int theory) {
+  return theory == SS_ABELIAN_HIGGS ? TH_AH : (theory == SS_CHIRAL_MAGNET ? TH_CM : TH_BS);
 }
 
 int check_grid(int nx, int ny, double dx, double dy) {
@@ -151,7 +165,7 @@ ProbDesc<R> make_desc(const Problem& p, DevState* st, FlowPartial* part) {
 
 // A batch of independent problems of one theory and precision.
 struct ss_batch {
-  int theory = 0;  // SS_ABELIAN_HIGGS / SS_CHIRAL_MAGNET
+  int theory = 0;  // SS_ABELIAN_HIGGS / SS_CHIRAL_MAGNET / SS_BABY_SKYRME
   int prec = 0;    // SS_FP32 / SS_FP64 / SS_FP32_PLAIN
   int C = 0;
   size_t elem = 0;
@@ -234,7 +248,7 @@ int batch_layout(ss_batch* b, int ts, const int* blocks) {
   b->BL.ts = ts;
   // a batch of one passes its descriptor to the pass kernels by value
   b->BL.one = n == 1 ? static_cast<const void*>(b->one_desc.data()) : nullptr;
-  const int th = b->theory == SS_ABELIAN_HIGGS ? TH_AH : TH_CM;
+  const int th = th_of(b->theory);
   flow_grid(th, b->prec, ts, total, n == 1, b->BL.flow_blocks);
   if (blocks) {
     if (b->method == METHOD_GD) b->BL.flow_blocks[2] = blocks[0] < total ? blocks[0] : total;
@@ -256,7 +270,7 @@ int batch_alloc(ss_batch* b) {
   const int nbuf = 6 + (b->prec == SS_FP32 ? 2 : 0);
   size_t bytes = 0;
   int total_tiles = 0, obs_need = 1;
-  const int th = b->theory == SS_ABELIAN_HIGGS ? TH_AH : TH_CM;
+  const int th = th_of(b->theory);
   for (Problem& p : b->probs) {
     p.plane = (size_t)p.nx * p.ny;
     total_tiles += ((p.nx + tx - 1) / tx) * ((p.ny + ty - 1) / ty);
@@ -322,7 +336,7 @@ int batch_alloc(ss_batch* b) {
 LaunchCtx problem_ctx(const ss_batch* b, int i, int cur) {
   const Problem& p = b->probs[i];
   LaunchCtx L{};
-  L.theory = b->theory == SS_ABELIAN_HIGGS ? TH_AH : TH_CM;
+  L.theory = th_of(b->theory);
   L.prec = b->prec;
   L.nx = p.nx;
   L.ny = p.ny;
@@ -923,7 +937,7 @@ int batch_autotune(ss_batch* b, int trial_steps, int* choice) {
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const int th = b->theory == SS_ABELIAN_HIGGS ? TH_AH : TH_CM;
+  const int th = th_of(b->theory);
   cudaEvent_t ev[3];
   for (int i = 0; i < 3; ++i)
     if (cudaEventCreate(&ev[i]) != cudaSuccess) return release(fail(SS_ERR_CUDA, "autotune: event creation failed"));

@@ -22,11 +22,15 @@ constexpr int HALO = 2;
 constexpr int SX = TX + 2 * HALO, SY = TY + 2 * HALO;
 constexpr int ROWS_PER_THREAD = TY / BY;
 
-enum { TH_AH = 1, TH_CM = 2 };
+enum { TH_AH = 1, TH_CM = 2, TH_BS = 3 };
 
 template <int TH> struct NComp;
 template <> struct NComp<TH_AH> { static constexpr int C = 4; };
 template <> struct NComp<TH_CM> { static constexpr int C = 3; };
+template <> struct NComp<TH_BS> { static constexpr int C = 3; };
+
+// Theories whose field is a unit 3-vector (projected onto the sphere).
+template <int TH> struct UnitVector { static constexpr bool value = TH == TH_CM || TH == TH_BS; };
 
 // ------------------------------------------------------------------ flow state
 // One per context, in device memory. Written only by the single last-arriving
@@ -187,6 +191,7 @@ SS_HD Deriv<R> stencil(const R* P, int sx, int sy, const Spacing<R>& h) {
 // ------------------------------------------------------------------ theories
 // Couplings in the working type. Abelian Higgs: c[0] = lambda, c[1] = u^2.
 // Chiral magnet: c[0] = J, c[1] = D, c[2] = K, c[3] = h, c[4..6] = d_1, c[7..9] = d_2.
+// Baby Skyrme: c[0] = kappa^2, c[1] = mu^2, c[2] = nu^2.
 template <typename R>
 struct Couplings {
   R c[10];
@@ -260,6 +265,40 @@ SS_HD void force_cm(const Couplings<R>& k, const R* n, const R* fx, const R* fy,
   for (int a = 0; a < 3; ++a) G[a] -= gn * n[a];
 }
 
+// Baby Skyrme (Table 1): e = 1/2 |d m|^2 + kappa^2/4 sum_{i,j} |d_i m x d_j m|^2 + V(m)
+//   = 1/2 (|a|^2 + |b|^2) + kappa^2/2 |a x b|^2 + mu^2 (1 - m_3) + nu^2/2 m_1^2,
+// with a = d_1 m, b = d_2 m (the double sum counts a x b twice).
+template <typename R>
+SS_HD R density_bs(const Couplings<R>& k, const R* m, const R* a, const R* b) {
+  R X[3];
+  cross3(a, b, X);
+  const R sig = a[0] * a[0] + a[1] * a[1] + a[2] * a[2] + b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+  return R(0.5) * sig + R(0.5) * k.c[0] * (X[0] * X[0] + X[1] * X[1] + X[2] * X[2]) + k.c[1] * (R(1) - m[2]) +
+         R(0.5) * k.c[2] * m[0] * m[0];
+}
+
+// Euler-Lagrange force of the Baby Skyrme energy. The Skyrme term S = kappa^2/2
+// (|a|^2 |b|^2 - (a.b)^2) contributes -d_1 dS/da - d_2 dS/db =
+//   -kappa^2 [ |b|^2 m_11 + |a|^2 m_22 - 2 (a.b) m_12 + (b.m_12 - a.m_22) a + (a.m_12 - b.m_11) b ],
+// the potential (nu^2 m_1, 0, -mu^2); then G <- G - (G.m) m.
+template <typename R>
+SS_HD void force_bs(const Couplings<R>& k, const R* m, const R* a, const R* b, const R* m11, const R* m22,
+                    const R* m12, R* G) {
+  const R aa = a[0] * a[0] + a[1] * a[1] + a[2] * a[2];
+  const R bb = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+  const R ab = a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+  const R ca = (b[0] * m12[0] + b[1] * m12[1] + b[2] * m12[2]) - (a[0] * m22[0] + a[1] * m22[1] + a[2] * m22[2]);
+  const R cb = (a[0] * m12[0] + a[1] * m12[1] + a[2] * m12[2]) - (b[0] * m11[0] + b[1] * m11[1] + b[2] * m11[2]);
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+    G[c] = -(m11[c] + m22[c]) - k.c[0] * (bb * m11[c] + aa * m22[c] - R(2) * ab * m12[c] + ca * a[c] + cb * b[c]);
+  G[0] += k.c[2] * m[0];
+  G[2] -= k.c[1];
+  const R gn = G[0] * m[0] + G[1] * m[1] + G[2] * m[2];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) G[c] -= gn * m[c];
+}
+
 // ------------------------------------------------------------------ energy differences
 // Eq. 4 compares E_h(phi^{n+1}) with E_h(phi^n). Both energy densities are
 // polynomials in (phi, d phi), so with a = phi^{n+1} and delta = phi^{n+1} - phi^n
@@ -318,11 +357,51 @@ SS_HD R delta_density_cm(const Couplings<R>& k, const R* a, const R* ax, const R
   return k.c[0] * ex + k.c[1] * dmi - k.c[2] * d[2] * (R(2) * a[2] - d[2]) - k.c[3] * d[2];
 }
 
+// Baby Skyrme: with X = a_x x a_y of the new field and the exact difference
+//   dX = X(a) - X(a - delta) = a_x x delta_y + delta_x x a_y - delta_x x delta_y,
+//   sigma     sum_i d_i delta . (d_i a - d_i delta / 2)
+//   Skyrme    kappa^2/2 (2 X - dX) . dX
+//   potential -mu^2 delta_3 + nu^2/2 delta_1 (2 a_1 - delta_1).
 template <typename R>
-__device__ __forceinline__ R rsqrt_t(R x);
-template <>
-__device__ __forceinline__ float rsqrt_t<float>(float x) { return 1.0f / sqrtf(x); }
-template <>
-__device__ __forceinline__ double rsqrt_t<double>(double x) { return 1.0 / sqrt(x); }
+SS_HD R delta_density_bs(const Couplings<R>& k, const R* a, const R* ax, const R* ay, const R* d, const R* dx,
+                         const R* dy) {
+  R sig = R(0);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) sig += dx[c] * (ax[c] - R(0.5) * dx[c]) + dy[c] * (ay[c] - R(0.5) * dy[c]);
+  R X[3], u1[3], u2[3], u3[3];
+  cross3(ax, ay, X);
+  cross3(ax, dy, u1);
+  cross3(dx, ay, u2);
+  cross3(dx, dy, u3);
+  R sky = R(0);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const R dX = u1[c] + u2[c] - u3[c];
+    sky += (R(2) * X[c] - dX) * dX;
+  }
+  return sig + R(0.5) * k.c[0] * sky - k.c[1] * d[2] + R(0.5) * k.c[2] * d[0] * (R(2) * a[0] - d[0]);
+}
+
+// Energy density, force and energy difference of theory TH.
+template <int TH, typename R>
+SS_HD R density_at(const Couplings<R>& k, const R* v, const R* fx, const R* fy) {
+  if (TH == TH_AH) return density_ah<R>(k, v, fx, fy);
+  if (TH == TH_CM) return density_cm<R>(k, v, fx, fy);
+  return density_bs<R>(k, v, fx, fy);
+}
+template <int TH, typename R>
+SS_HD R delta_density_at(const Couplings<R>& k, const R* a, const R* ax, const R* ay, const R* d, const R* dx,
+                         const R* dy) {
+  if (TH == TH_AH) return delta_density_ah<R>(k, a, ax, ay, d, dx, dy);
+  if (TH == TH_CM) return delta_density_cm<R>(k, a, ax, ay, d, dx, dy);
+  return delta_density_bs<R>(k, a, ax, ay, d, dx, dy);
+}
+template <int TH, typename R>
+SS_HD void force_of(const Couplings<R>& k, const R* v, const R* fx, const R* fy, const R* fxx, const R* fyy,
+                    const R* fxy, R* G) {
+  if (TH == TH_AH) force_ah<R>(k, v, fx, fy, fxx, fyy, fxy, G);
+  else if (TH == TH_CM) force_cm<R>(k, v, fx, fy, fxx, fyy, G);
+  else force_bs<R>(k, v, fx, fy, fxx, fyy, fxy, G);
+}
 
 }  // namespace ss

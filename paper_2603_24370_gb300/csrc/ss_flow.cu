@@ -216,9 +216,9 @@ template <int TH, typename R, int SXY_>
 struct StageWin {
   static constexpr int C = NComp<TH>::C;
   static constexpr int SXY = SXY_;
-  Win<R, false> w0, w1;
-  Win<R, TH == TH_AH> w2;
-  Win<R, TH == TH_AH> w3;  // unused for the chiral magnet
+  Win<R, TH == TH_BS> w0, w1;  // Baby Skyrme: mixed derivatives of every component
+  Win<R, TH == TH_AH || TH == TH_BS> w2;
+  Win<R, TH == TH_AH> w3;  // unused for three-component theories
 
   __device__ __forceinline__ void enter(const R* tiles, int off, int slot) {
     w0.enter(tiles + off, slot);
@@ -267,8 +267,7 @@ struct DiffWin {
 template <int TH, typename R>
 __device__ __forceinline__ void force_at(const Couplings<R>& k, const R* v, const R* fx, const R* fy, const R* fxx,
                                          const R* fyy, const R* fxy, R* G) {
-  if (TH == TH_AH) force_ah<R>(k, v, fx, fy, fxx, fyy, fxy, G);
-  else force_cm<R>(k, v, fx, fy, fxx, fyy, G);
+  force_of<TH, R>(k, v, fx, fy, fxx, fyy, fxy, G);
 }
 
 // ---- per-tile block reduction in the working type: two compensated sums, one max
@@ -470,7 +469,7 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
             ya[c] = LO ? lv[u][c] : pv[u][c];
             yb[c] = (LO ? lv[u][c] : pv[u][c]) + hdt * vv[u][c];
           }
-          if (TH == TH_CM && inside[u]) {
+          if (UnitVector<TH>::value && inside[u]) {
             if constexpr (LO) normalise_split(pv[u], yb);
             else normalise<C>(yb);
           }
@@ -482,7 +481,7 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
             ya[c] = (LO ? lv[u][c] : pv[u][c]) + base3;
             yb[c] = (LO ? lv[u][c] : pv[u][c]) + base4;
           }
-          if (TH == TH_CM && inside[u]) {
+          if (UnitVector<TH>::value && inside[u]) {
             if constexpr (LO) {
               normalise_split(pv[u], ya);
               normalise_split(pv[u], yb);
@@ -543,7 +542,7 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
               kv1[c * P + s] = -G[c];
               gmr = absmax(gmr, G[c]);
             }
-            const R e = (TH == TH_AH) ? density_ah<R>(kc, v, fx, fy) : density_cm<R>(kc, v, fx, fy);
+            const R e = density_at<TH, R>(kc, v, fx, fy);
             const R t1 = es + e;
             ec += (fabs(es) >= fabs(e)) ? (es - t1) + e : (e - t1) + es;
             es = t1;
@@ -552,8 +551,7 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
             R dd[C], dxv[C], dyv[C];
             D.derivs(setD, off, h, dd, dxv, dyv);
             if (ok) {
-              const R de = (TH == TH_AH) ? delta_density_ah<R>(kc, v, fx, fy, dd, dxv, dyv)
-                                         : delta_density_cm<R>(kc, v, fx, fy, dd, dxv, dyv);
+              const R de = delta_density_at<TH, R>(kc, v, fx, fy, dd, dxv, dyv);
               const R t2 = ds + de;
               dc += (fabs(ds) >= fabs(de)) ? (ds - t2) + de : (de - t2) + ds;
               ds = t2;
@@ -614,7 +612,7 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
               kv1[c * P + s] = -G[c];
               gmr = absmax(gmr, G[c]);
             }
-            const R e = (TH == TH_AH) ? density_ah<R>(kc, v, fx, fy) : density_cm<R>(kc, v, fx, fy);
+            const R e = density_at<TH, R>(kc, v, fx, fy);
             const R t1 = es + e;
             ec += (fabs(es) >= fabs(e)) ? (es - t1) + e : (e - t1) + es;
             es = t1;
@@ -626,13 +624,13 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
                 q[c] = (LO ? lo[c * P + s] : p0[c]) - tau * G[c];
               }
               if constexpr (LO) {
-                if (TH == TH_CM) normalise_split(p0, q);
+                if (UnitVector<TH>::value) normalise_split(p0, q);
 #pragma unroll
                 for (int c = 0; c < C; ++c) two_sum_f(p0[c], q[c], pn[c], ln[c]);
               } else {
 #pragma unroll
                 for (int c = 0; c < C; ++c) pn[c] = q[c];
-                if (TH == TH_CM) normalise<C>(pn);
+                if (UnitVector<TH>::value) normalise<C>(pn);
               }
 #pragma unroll
               for (int c = 0; c < C; ++c) {
@@ -782,15 +780,15 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
             }
             R pn[C], ln[C];
             if constexpr (LO) {
-              if (TH == TH_CM) normalise_split(p0, q);
+              if (UnitVector<TH>::value) normalise_split(p0, q);
 #pragma unroll
               for (int c = 0; c < C; ++c) two_sum_f(p0[c], q[c], pn[c], ln[c]);  // hi' = fl(hi + small), lo' = rest
             } else {
 #pragma unroll
               for (int c = 0; c < C; ++c) pn[c] = q[c];
-              if (TH == TH_CM) normalise<C>(pn);
+              if (UnitVector<TH>::value) normalise<C>(pn);
             }
-            if (TH == TH_CM) {
+            if (UnitVector<TH>::value) {
               const R vp = vn[0] * pn[0] + vn[1] * pn[1] + vn[2] * pn[2];
 #pragma unroll
               for (int c = 0; c < C; ++c) vn[c] -= vp * pn[c];
@@ -922,7 +920,9 @@ static cudaError_t pass_th(const BatchLaunch& b, int pass, cudaStream_t s) {
 }
 
 cudaError_t launch_pass(const BatchLaunch& b, int pass, cudaStream_t s) {
-  return b.theory == TH_AH ? pass_th<TH_AH>(b, pass, s) : pass_th<TH_CM>(b, pass, s);
+  if (b.theory == TH_AH) return pass_th<TH_AH>(b, pass, s);
+  if (b.theory == TH_CM) return pass_th<TH_CM>(b, pass, s);
+  return pass_th<TH_BS>(b, pass, s);
 }
 
 cudaError_t launch_reset_states(DevState* st, int n, cudaStream_t s) {
@@ -991,7 +991,8 @@ static void occupancy_sel(int prec, int ts, bool one, int occ[3]) {
 void flow_occupancy(int theory, int prec, int ts, bool one, int occ[3]) {
   occ[0] = occ[1] = occ[2] = 1;
   if (theory == TH_AH) occupancy_sel<TH_AH>(prec, ts, one, occ);
-  else occupancy_sel<TH_CM>(prec, ts, one, occ);
+  else if (theory == TH_CM) occupancy_sel<TH_CM>(prec, ts, one, occ);
+  else occupancy_sel<TH_BS>(prec, ts, one, occ);
   for (int i = 0; i < 3; ++i)
     if (occ[i] < 1) occ[i] = 1;
 }

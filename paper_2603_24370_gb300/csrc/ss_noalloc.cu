@@ -95,6 +95,15 @@ extern "C" int ss_observables_noalloc(int theory, const double* params, int n_pa
     if (type == 0) { k[5] = 1.0; k[7] = -1.0; }
     else if (type == 1) { k[4] = 1.0; k[8] = 1.0; }
     else { k[4] = 1.0; k[8] = -1.0; }
+  } else if (theory == SS_BABY_SKYRME) {
+    if (n_params < 2 || n_params > 3)
+      return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: Baby Skyrme takes {kappa, mu[, nu]}");
+    for (int i = 0; i < n_params; ++i)
+      if (!std::isfinite(params[i])) return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: parameters must be finite");
+    const double nu = n_params > 2 ? params[2] : 0.0;
+    k[0] = params[0] * params[0];
+    k[1] = params[1] * params[1];
+    k[2] = nu * nu;
   } else {
     return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: unknown theory");
   }
@@ -119,7 +128,7 @@ extern "C" int ss_observables_noalloc(int theory, const double* params, int n_pa
   }
 
   LaunchCtx L{};
-  L.theory = theory == SS_ABELIAN_HIGGS ? TH_AH : TH_CM;
+  L.theory = theory == SS_ABELIAN_HIGGS ? TH_AH : (theory == SS_CHIRAL_MAGNET ? TH_CM : TH_BS);
   L.prec = precision;
   L.nx = nx;
   L.ny = ny;

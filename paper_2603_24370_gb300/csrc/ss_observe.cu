@@ -7,7 +7,7 @@
 //   E_h  = dx dy sum_I e                              (Table 1 / Eq. 5 densities)
 //   flux = dx dy sum_I (d_1 A_2 - d_2 A_1)            (Abelian Higgs)
 //   Q    = (1/4pi) sum over plaquettes of the Berg-Luescher solid angles of the
-//          two triangles (n00, n10, n11), (n00, n11, n01)   (chiral magnet)
+//          two triangles (n00, n10, n11), (n00, n11, n01)   (chiral magnet, Baby Skyrme)
 //   Q    = (1/2pi) sum of wrapped arg-psi steps around the boundary of I (Abelian Higgs)
 //   max_I |G|, max ||n| - 1|
 // A compensated FP32 field is read as value + remainder, exactly, in FP64.
@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(NT) k_observables(ObsArgs<R> a) {
       const int gx = x0 + lx, gy = y0 + ly;
       if (gx >= a.nx || gy >= a.ny) continue;
       const int sx = lx + HALO, sy = ly + HALO;
-      if (TH == TH_CM) {
+      if (UnitVector<TH>::value) {
         const int o = sy * SX + sx;
         const double n00[3] = {sY[0][o], sY[1][o], sY[2][o]};
         nd = nanmax(nd, fabs(sqrt(dot3d(n00, n00)) - 1.0));
@@ -92,8 +92,9 @@ __global__ void __launch_bounds__(NT) k_observables(ObsArgs<R> a) {
       double v[C], fx[C], fy[C], fxx[C], fyy[C], fxy[C];
 #pragma unroll
       for (int c = 0; c < C; ++c) {
-        const Deriv<double> d = (TH == TH_AH && c >= 2) ? stencil<double, true, true>(sY[c], sx, sy, a.h)
-                                                        : stencil<double, true, false>(sY[c], sx, sy, a.h);
+        const Deriv<double> d = ((TH == TH_AH && c >= 2) || TH == TH_BS)
+                                    ? stencil<double, true, true>(sY[c], sx, sy, a.h)
+                                    : stencil<double, true, false>(sY[c], sx, sy, a.h);
         v[c] = d.v; fx[c] = d.fx; fy[c] = d.fy; fxx[c] = d.fxx; fyy[c] = d.fyy; fxy[c] = d.fxy;
       }
       double G[C];
@@ -102,8 +103,8 @@ __global__ void __launch_bounds__(NT) k_observables(ObsArgs<R> a) {
         neumaier(se, density_ah<double>(a.k, v, fx, fy));
         neumaier(sf, fx[3] - fy[2]);
       } else {
-        force_cm<double>(a.k, v, fx, fy, fxx, fyy, G);
-        neumaier(se, density_cm<double>(a.k, v, fx, fy));
+        force_of<TH, double>(a.k, v, fx, fy, fxx, fyy, fxy, G);
+        neumaier(se, density_at<TH, double>(a.k, v, fx, fy));
       }
 #pragma unroll
       for (int c = 0; c < C; ++c) gm = nanmax(gm, fabs(G[c]));
@@ -139,7 +140,7 @@ __global__ void __launch_bounds__(NT) k_observables(ObsArgs<R> a) {
     DevState* st = a.st;
     st->obs_energy = a.area * (sv2[0].s + sv2[0].c);
     st->obs_flux = a.area * (sv2[1].s + sv2[1].c);
-    if (TH == TH_CM) st->obs_charge = (sv2[2].s + sv2[2].c) / (4.0 * 3.14159265358979323846);
+    if (UnitVector<TH>::value) st->obs_charge = (sv2[2].s + sv2[2].c) / (4.0 * 3.14159265358979323846);
     st->obs_gmax_raw = mv2[0];
     st->obs_normdev = mv2[1];
     st->obs_ticket = 0;
@@ -260,7 +261,8 @@ static cudaError_t obs_t(const LaunchCtx& c, int cur, cudaStream_t s) {
 cudaError_t launch_observables(const LaunchCtx& c, int cur, cudaStream_t s) {
   const bool f = c.prec != PREC_F64;  // every FP32 mode stores its (hi) field in float
   if (c.theory == TH_AH) return f ? obs_t<TH_AH, float>(c, cur, s) : obs_t<TH_AH, double>(c, cur, s);
-  return f ? obs_t<TH_CM, float>(c, cur, s) : obs_t<TH_CM, double>(c, cur, s);
+  if (c.theory == TH_CM) return f ? obs_t<TH_CM, float>(c, cur, s) : obs_t<TH_CM, double>(c, cur, s);
+  return f ? obs_t<TH_BS, float>(c, cur, s) : obs_t<TH_BS, double>(c, cur, s);
 }
 
 template <int TH, typename R>
@@ -274,6 +276,7 @@ static cudaError_t ansatz_t(const LaunchCtx& c, const double* sol, int n, cudaSt
 cudaError_t launch_ansatz(const LaunchCtx& c, const double* d_sol, int n, cudaStream_t s) {
   const bool f = c.prec != PREC_F64;
   if (c.theory == TH_AH) return f ? ansatz_t<TH_AH, float>(c, d_sol, n, s) : ansatz_t<TH_AH, double>(c, d_sol, n, s);
+  // both unit-vector theories take the compact skyrmion
   return f ? ansatz_t<TH_CM, float>(c, d_sol, n, s) : ansatz_t<TH_CM, double>(c, d_sol, n, s);
 }
 
@@ -291,7 +294,8 @@ int obs_grid(int theory, int prec, int ntiles) {
   int occ;
   const bool f = prec != PREC_F64;
   if (theory == TH_AH) occ = f ? obs_occ<TH_AH, float>() : obs_occ<TH_AH, double>();
-  else occ = f ? obs_occ<TH_CM, float>() : obs_occ<TH_CM, double>();
+  else if (theory == TH_CM) occ = f ? obs_occ<TH_CM, float>() : obs_occ<TH_CM, double>();
+  else occ = f ? obs_occ<TH_BS, float>() : obs_occ<TH_BS, double>();
   const int g = nsm * occ;
   return ntiles < g ? ntiles : g;
 }

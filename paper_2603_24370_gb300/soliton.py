@@ -32,6 +32,7 @@ SS_FP64 = 2
 SS_FP32_PLAIN = 3  # one FP32 plane per component
 SS_ABELIAN_HIGGS = 1
 SS_CHIRAL_MAGNET = 2
+SS_BABY_SKYRME = 3
 SS_METHOD_ANF = 0       # arrested Newton flow (default)
 SS_METHOD_GRADIENT = 1  # gradient descent phi <- phi - dtau G
 
