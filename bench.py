@@ -26,6 +26,11 @@ method Sec. 3.2 compares it with; explicit Euler at 0.8 x its stability limit) o
 the same configurations and precisions, each to dx dy max|G| < 1e-6 or a step cap:
 steps, force evaluations (4 per flow step, 1 per descent step) and seconds.
 
+--workload baby-skyrme: the Baby Skyrme model (Table 1; kappa = 1, mu = 0.7, standard
+potential) through the same kernels: flow throughput on 2048^2 with 100 skyrmions
+(compensated FP32), and time to dx dy max|G| < 1e-6 of a 256^2 box with 4 skyrmions
+on the GPU (FP64, compensated FP32) against the FP64 oracle on the host cores.
+
 --workload ah-batch: time per solve to dx dy max|G| < 1e-6 on the batched Abelian
 Higgs set (256 problems, sides 64..512, dx = 0.1, lambda ~ U[0.5, 2], N in 1..4):
 one bench step = the whole set relaxed in one batch (compensated FP32), against
@@ -604,6 +609,75 @@ def run_methods(args) -> int:
     return 0
 
 
+def run_baby_skyrme(args) -> int:
+    """Baby Skyrme: flow throughput and time to solution (see the module docstring)."""
+    rank, local_rank, world = D.env_rank()
+    if rank != 0:
+        return 0
+    D.pin_visible_device(local_rank, 1)
+    import numpy as np
+    import torch
+    import oracle as O
+    from paper_2603_24370_gb300 import build as B
+    from paper_2603_24370_gb300 import inputs as I
+    from paper_2603_24370_gb300 import soliton as S
+    B.build()
+    O.build()
+    S.load_library()
+    peaks, src = measured_peaks()
+    n = 2048
+    p = I.bs_skyrmions(n=n)
+    with S.Solver(S.SS_BABY_SKYRME, p.params, n, n, p.dx, p.dy, S.SS_FP32) as sv:
+        sv.init_ansatz(p.soliton_array())
+        tuned = sv.autotune(4)
+        for _ in range(args.warmup):
+            sv.step(INNER)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            sv.step(INNER)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        ms = S.ss_profile_stages(sv.ctx, 8)
+        o = sv.observables()
+    thr = {"site_updates_per_s": interior(n) * INNER * args.steps / sec, "pass_ms": ms, "autotuned": tuned,
+           "hbm_frac_of_measured": [PASS_BYTES[k + 1] * interior(n) / (ms[k] * 1e-3) / 1e9 / peaks["hbm_gbs"]
+                                    for k in range(2)],
+           "charge_after": o["charge"], "skyrmions": len(p.solitons)}
+
+    q = I.bs_skyrmions(n=256, count=4, seed=20266)
+    sol = q.soliton_array()
+    gpu = {}
+    for name, prec in (("fp64", S.SS_FP64), ("fp32c", S.SS_FP32)):
+        with S.Solver(S.SS_BABY_SKYRME, q.params, q.nx, q.ny, q.dx, q.dy, prec) as sv:
+            sv.init_ansatz(sol)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = sv.minimise(1e-6, 100000)
+            torch.cuda.synchronize()
+            o = sv.observables()
+            gpu[name] = {"seconds": time.perf_counter() - t0, "steps": r["steps"], "converged": bool(r["converged"]),
+                         "energy": o["energy"], "charge": o["charge"]}
+    f = O.ansatz(q.theory, sol, q.nx, q.ny, q.dx, q.dy)
+    v = np.zeros_like(f)
+    E = O.energy(q.theory, q.params, f, q.dx, q.dy)
+    t0 = time.perf_counter()
+    k = 0
+    while time.perf_counter() - t0 < 10.0 and k < 2000:
+        f, v, E, _ = O.anf_step(q.theory, q.params, f, v, q.dx, q.dy, O.time_step(q.dx, q.dy), E)
+        k += 1
+    oracle_step = (time.perf_counter() - t0) / k
+    line = {"metric": "Baby Skyrme: site-updates/s at 2048^2; time to dx dy max|G| < 1e-6 at 256^2", "unit": "s",
+            "n_gpus": 1, "data": "synthetic", "dtype": "f32 (throughput); f64 and f32c (time to solution)",
+            "config": {"workload": "Baby Skyrme kappa=1, mu=0.7, nu=0, dx=0.2; 2048^2 with 100 compact skyrmions "
+                                   "(R 2.5, min-sep 10); 256^2 with 4", "flow_steps_per_bench_step": INNER},
+            "throughput": thr, "time_to_solution": {"gpu": gpu, "oracle": {
+                "seconds": oracle_step * gpu["fp64"]["steps"], "per_step_s": oracle_step, "sampled_steps": k,
+                "cores": O.num_threads(), "timed": "oracle steps for ~10 s x the GPU FP64 step count"}}}
+    print(json.dumps(line))
+    return 0
+
+
 def main() -> int:
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -612,7 +686,8 @@ def main() -> int:
     ap.add_argument("--impl", choices=("native", "reference"), default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grid", type=int, default=N, help="grid side (default: the 4096 workload; smaller for ncu)")
-    ap.add_argument("--workload", choices=("cm4096", "ah-batch", "configs", "methods"), default="cm4096")
+    ap.add_argument("--workload", choices=("cm4096", "ah-batch", "configs", "methods", "baby-skyrme"),
+                    default="cm4096")
     ap.add_argument("--tile-shape", choices=("auto", "0", "1"), default="auto",
                     help="flow tile shape: autotuned (default) or fixed (for profiling one shape)")
     ap.add_argument("--fp64-per-side", type=int, default=2, help="ah-batch: FP64 problems timed per side")
@@ -630,6 +705,8 @@ def main() -> int:
         return run_configs(args)
     if args.workload == "methods":
         return run_methods(args)
+    if args.workload == "baby-skyrme":
+        return run_baby_skyrme(args)
     return run_native(args)
 
 

@@ -99,6 +99,20 @@ def cm_skyrmions(n: int = 1024, count: int = 8, dx: float = 0.2, seed: int = 202
     return Problem(CHIRAL_MAGNET, n, n, dx, dx, tuple(params), sol)
 
 
+BS_DEFAULT = (1.0, 0.7, 0.0)  # kappa, mu, nu: standard potential
+
+
+def bs_skyrmions(n: int = 2048, count: int = 100, dx: float = 0.2, seed: int = 20265, radius: float = 2.5,
+                 min_sep: float = 10.0, margin: float = 8.0, params=BS_DEFAULT) -> Problem:
+    """Baby Skyrme model with ``count`` compact charge-1 skyrmions (R = 2.5) at seeded
+    uniform positions, minimum separation 10 and margin 8 from the edge."""
+    rng = SplitMix64(seed)
+    half = 0.5 * (n - 1) * dx
+    pts = _separated_positions(rng, count, half, half, margin, min_sep)
+    sol = [(x, y, 1.0, radius, 0.0) for x, y in pts]
+    return Problem(BABY_SKYRME, n, n, dx, dx, tuple(params), sol)
+
+
 def ah_batch(count: int = 256, seed: int = 20262, sides=(64, 128, 256, 512), dx: float = 0.1,
              lam_range=(0.5, 2.0), charges=(1, 2, 3, 4)) -> list[Problem]:
     """Batched Abelian Higgs set: side ~ U(sides), lambda ~ U[0.5, 2], N ~ U(charges),
