@@ -16,7 +16,7 @@ appearance, see ``soliton_oracle.cpp``):
 * ``gd_step`` / ``gd_minimise`` / ``gd_step_limit`` -- the first-order gradient
   descent Sec. 3.2 names as the slower alternative (explicit Euler, see the C++)
 * ``observables``          -- energy, topological charge, flux, residual, |n|-1
-* ``ansatz``               -- vortex / skyrmion initial data (Sec. 3.4; standard forms)
+* ``ansatz`` / ``ansatz_bec`` -- vortex / skyrmion initial data (Sec. 3.4; standard forms)
 
 All functions are pinned by the ``-m "not gpu"`` tests in ``tests/test_oracle_pins.py``.
 """
@@ -33,6 +33,7 @@ import numpy as np
 ABELIAN_HIGGS = 1
 CHIRAL_MAGNET = 2
 BABY_SKYRME = 3
+BEC = 4
 HARMONIC_TEST = 99
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -97,6 +98,8 @@ def _load():
             lib.or_observables.argtypes = [i, _D, _D, i, i, d, d, _D]
             lib.or_observables.restype = None
             lib.or_ansatz.argtypes = [i, _D, i, _D, i, i, d, d]
+            lib.or_ansatz_bec.argtypes = [_D, _D, i, _D, i, i, d, d]
+            lib.or_ansatz_bec.restype = None
             lib.or_ansatz.restype = None
             _lib = lib
     return _lib
@@ -219,10 +222,18 @@ def gd_minimise(theory: int, params, f, dx: float, dy: float, tol: float, max_st
 def observables(theory: int, params, f, dx: float, dy: float) -> dict:
     f = _f64(f)
     _, ny, nx = f.shape
-    out = np.zeros(6)
+    out = np.zeros(8)
     _load().or_observables(theory, _p(_params(params)), _p(f), nx, ny, dx, dy, _p(out))
     return {"energy": out[0], "charge": out[1], "flux": out[2], "grad_max": out[3], "grad_max_raw": out[4],
-            "norm_dev": out[5]}
+            "norm_dev": out[5], "atoms": out[6], "angular_momentum": out[7]}
+
+
+def ansatz_bec(params, vortices, nx: int, ny: int, dx: float, dy: float) -> np.ndarray:
+    """Thomas-Fermi amplitude times vortex factors; ``vortices`` rows (x, y, n, size, phase)."""
+    s = _f64(np.asarray(vortices, dtype=np.float64).reshape(-1, 5))
+    f = np.zeros((2, ny, nx))
+    _load().or_ansatz_bec(_p(_params(params)), _p(s), s.shape[0], _p(f), nx, ny, dx, dy)
+    return f
 
 
 def ansatz(theory: int, solitons, nx: int, ny: int, dx: float, dy: float) -> np.ndarray:

@@ -35,6 +35,10 @@
 //   * Baby Skyrme (Table 1): the Skyrme term's double sum over i, j is
 //     kappa^2/2 |d_1 m x d_2 m|^2; potential mu^2 (1 - m_3) + nu^2/2 m_1^2; the unit
 //     vector is projected exactly as the chiral magnet's.
+//   * Rotating BEC (Table 1; the BEC section): dimensionless (hbar = m = omega = 1),
+//     in the grand-canonical form at chemical potential mu: the functional minimised is
+//     E - mu N, which fixes the atom number N at the minimum; Re(psi* L_z psi) is the
+//     rotation density (its imaginary part is a total derivative).
 //   * Arrest compares potential energies with a strict '>' (Eq. 4).
 //   * Convergence measure: max over I and components of |dx dy G|.
 #include <cmath>
@@ -49,7 +53,7 @@ namespace {
 
 const double PI = 3.14159265358979323846;
 
-enum { TH_ABELIAN_HIGGS = 1, TH_CHIRAL_MAGNET = 2, TH_BABY_SKYRME = 3, TH_HARMONIC_TEST = 99 };
+enum { TH_ABELIAN_HIGGS = 1, TH_CHIRAL_MAGNET = 2, TH_BABY_SKYRME = 3, TH_BEC = 4, TH_HARMONIC_TEST = 99 };
 
 // Theories whose field is a unit 3-vector (normalised after every update).
 bool unit_vector(int theory) { return theory == TH_CHIRAL_MAGNET || theory == TH_BABY_SKYRME; }
@@ -66,6 +70,7 @@ int ncomp(int theory) {
     case TH_ABELIAN_HIGGS: return 4;   // psi_1, psi_2, A_1, A_2 (Table 1)
     case TH_CHIRAL_MAGNET: return 3;   // n_1, n_2, n_3 (Eq. 5)
     case TH_BABY_SKYRME: return 3;     // m_1, m_2, m_3 (Table 1)
+    case TH_BEC: return 2;             // Re psi, Im psi (Table 1)
     case TH_HARMONIC_TEST: return 1;   // scalar test field
     default: return 0;
   }
@@ -112,13 +117,16 @@ double d12(const double* p, const Grid& g, int i, int j) {
          (12.0 * g.dy);
 }
 
-// All derivatives of every component at one interior site.
+// All derivatives of every component at one interior site, and its coordinates.
 struct Site {
   double v[4], fx[4], fy[4], fxx[4], fyy[4], fxy[4];
+  double x, y;
 };
 
 Site gather(const double* f, int C, const Grid& g, int i, int j, bool second) {
   Site s;
+  s.x = (i - 0.5 * (g.nx - 1)) * g.dx;
+  s.y = (j - 0.5 * (g.ny - 1)) * g.dy;
   for (int c = 0; c < C; ++c) {
     const double* p = f + c * g.plane();
     s.v[c] = p[(size_t)j * g.nx + i];
@@ -198,6 +206,20 @@ double density_bs(const double* prm, const Site& s) {
          0.5 * nu2 * s.v[0] * s.v[0];
 }
 
+// Rotating trapped BEC (Table 1), dimensionless (hbar = m = omega = 1), grand canonical:
+//   e = 1/2 |grad psi|^2 + 1/2 r^2 |psi|^2 + g/2 |psi|^4 - mu |psi|^2 - Omega Re(psi* L_z psi),
+// L_z = -i (x d_y - y d_x); with psi = u + i v and D = x d_y - y d_x,
+//   psi* L_z psi = (u D v - v D u) - i/2 D(u^2 + v^2),
+// whose imaginary part integrates to zero. prm = {g, Omega, mu}.
+double density_bec(const double* prm, const Site& s) {
+  const double g = prm[0], Om = prm[1], mu = prm[2];
+  const double u = s.v[0], v = s.v[1];
+  const double Du = s.x * s.fy[0] - s.y * s.fx[0], Dv = s.x * s.fy[1] - s.y * s.fx[1];
+  const double n = u * u + v * v, r2 = s.x * s.x + s.y * s.y;
+  const double kin = 0.5 * (s.fx[0] * s.fx[0] + s.fy[0] * s.fy[0] + s.fx[1] * s.fx[1] + s.fy[1] * s.fy[1]);
+  return kin + 0.5 * r2 * n + 0.5 * g * n * n - mu * n - Om * (u * Dv - v * Du);
+}
+
 // Harmonic test theory (oracle only, pins the time integrator): e = k/2 phi^2.
 double density_harm(const double* prm, const Site& s) { return 0.5 * prm[0] * s.v[0] * s.v[0]; }
 
@@ -206,6 +228,7 @@ double density(int theory, const double* prm, const Site& s) {
     case TH_ABELIAN_HIGGS: return density_ah(prm, s);
     case TH_CHIRAL_MAGNET: return density_cm(prm, s);
     case TH_BABY_SKYRME: return density_bs(prm, s);
+    case TH_BEC: return density_bec(prm, s);
     default: return density_harm(prm, s);
   }
 }
@@ -271,11 +294,24 @@ void force_bs(const double* prm, const Site& s, double G[3]) {
   for (int c = 0; c < 3; ++c) G[c] -= gn * n[c];
 }
 
+// BEC: delta E / delta u = -lap u + r^2 u + 2 g |psi|^2 u - 2 mu u - 2 Omega D v,
+//      delta E / delta v = -lap v + r^2 v + 2 g |psi|^2 v - 2 mu v + 2 Omega D u
+// (half of it is the Gross-Pitaevskii operator minus mu: -lap/2 + r^2/2 + g|psi|^2 - Omega L_z - mu).
+void force_bec(const double* prm, const Site& s, double G[2]) {
+  const double g = prm[0], Om = prm[1], mu = prm[2];
+  const double u = s.v[0], v = s.v[1];
+  const double Du = s.x * s.fy[0] - s.y * s.fx[0], Dv = s.x * s.fy[1] - s.y * s.fx[1];
+  const double w = s.x * s.x + s.y * s.y + 2.0 * g * (u * u + v * v) - 2.0 * mu;
+  G[0] = -(s.fxx[0] + s.fyy[0]) + w * u - 2.0 * Om * Dv;
+  G[1] = -(s.fxx[1] + s.fyy[1]) + w * v + 2.0 * Om * Du;
+}
+
 void force_site(int theory, const double* prm, const Site& s, double* G) {
   switch (theory) {
     case TH_ABELIAN_HIGGS: force_ah(prm, s, G); break;
     case TH_CHIRAL_MAGNET: force_cm(prm, s, G); break;
     case TH_BABY_SKYRME: force_bs(prm, s, G); break;
+    case TH_BEC: force_bec(prm, s, G); break;
     default: G[0] = prm[0] * s.v[0]; break;
   }
 }
@@ -327,6 +363,17 @@ void partials(int theory, const double* prm, const Site& s, double dv[4], double
     }
     dv[0] = nu2 * s.v[0];
     dv[2] = -mu2;
+  } else if (theory == TH_BEC) {
+    const double g = prm[0], Om = prm[1], mu = prm[2];
+    const double u = s.v[0], v = s.v[1];
+    const double Du = s.x * s.fy[0] - s.y * s.fx[0], Dv = s.x * s.fy[1] - s.y * s.fx[1];
+    const double w = s.x * s.x + s.y * s.y + 2.0 * g * (u * u + v * v) - 2.0 * mu;
+    // -Omega (u D v - v D u): d/d(d_x u) = -Omega v y, d/d(d_y u) = Omega v x,
+    // d/d(d_x v) = Omega u y, d/d(d_y v) = -Omega u x, d/du = -Omega D v, d/dv = Omega D u
+    dgx[0] = s.fx[0] - Om * v * s.y;  dgy[0] = s.fy[0] + Om * v * s.x;
+    dgx[1] = s.fx[1] + Om * u * s.y;  dgy[1] = s.fy[1] - Om * u * s.x;
+    dv[0] = w * u - Om * Dv;
+    dv[1] = w * v + Om * Du;
   } else {
     dv[0] = prm[0] * s.v[0];
   }
@@ -616,7 +663,9 @@ static double solid_angle(const double a[3], const double b[3], const double c[3
 //          (counter-clockwise), divided by 2 pi.
 // out[2] = magnetic flux dx dy sum_I (d_1 A_2 - d_2 A_1) (Abelian Higgs), 0 otherwise
 // out[3] = dx dy max_I |G|, out[4] = max_I |G|
-// out[5] = max over all sites of ||n| - 1| (chiral magnet), 0 otherwise
+// out[5] = max over all sites of ||n| - 1| (chiral magnet, Baby Skyrme), 0 otherwise
+// out[6] = BEC atom number N = dx dy sum_I |psi|^2, out[7] = BEC angular momentum
+//          dx dy sum_I Re(psi* L_z psi); 0 otherwise
 void or_observables(int theory, const double* prm, const double* f, int nx, int ny, double dx, double dy,
                     double* out) {
   const Grid g{nx, ny, dx, dy};
@@ -626,7 +675,18 @@ void or_observables(int theory, const double* prm, const double* f, int nx, int 
   force(theory, prm, f, g, G.data());
   const double gmax = max_abs(G.data(), N);
   out[0] = energy(theory, prm, f, g);
-  out[1] = 0.0; out[2] = 0.0; out[3] = dx * dy * gmax; out[4] = gmax; out[5] = 0.0;
+  out[1] = 0.0; out[2] = 0.0; out[3] = dx * dy * gmax; out[4] = gmax; out[5] = 0.0; out[6] = 0.0; out[7] = 0.0;
+  if (theory == TH_BEC) {
+    Neumaier na, lz;
+    for (int j = 2; j <= ny - 3; ++j)
+      for (int i = 2; i <= nx - 3; ++i) {
+        const Site s = gather(f, 2, g, i, j, false);
+        na.add(s.v[0] * s.v[0] + s.v[1] * s.v[1]);
+        lz.add(s.v[0] * (s.x * s.fy[1] - s.y * s.fx[1]) - s.v[1] * (s.x * s.fy[0] - s.y * s.fx[0]));
+      }
+    out[6] = dx * dy * na.value();
+    out[7] = dx * dy * lz.value();
+  }
   if (unit_vector(theory)) {
     auto unit = [&](int i, int j, double n[3]) {
       const size_t k = (size_t)j * nx + i;
@@ -681,6 +741,27 @@ void or_observables(int theory, const double* prm, const double* f, int nx, int 
 //   n = (sin f cos(m theta + gamma), sin f sin(m theta + gamma), cos f),
 //   f = pi (1 - r/R) for r < R, else 0 (n = e_3); the first disc containing a site wins.
 // sol[k*5 + 0..4] = {x, y, charge, size, phase}.
+// BEC: Thomas-Fermi amplitude times vortex factors,
+//   psi = sqrt(max(0, mu - r^2/2) / g) prod_k tanh(r_k/s_k)^{|n_k|} exp(i (n_k theta_k + chi_k)).
+void or_ansatz_bec(const double* prm, const double* sol, int nsol, double* f, int nx, int ny, double dx, double dy) {
+  const size_t P = (size_t)nx * ny;
+  const double g = prm[0], mu = prm[2];
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      const double x = (i - 0.5 * (nx - 1)) * dx, y = (j - 0.5 * (ny - 1)) * dy;
+      double mod = std::sqrt(std::fmax(0.0, mu - 0.5 * (x * x + y * y)) / g), ph = 0.0;
+      for (int s = 0; s < nsol; ++s) {
+        const double X = x - sol[5 * s], Y = y - sol[5 * s + 1];
+        const double n = sol[5 * s + 2], sz = sol[5 * s + 3], chi = sol[5 * s + 4];
+        mod *= std::pow(std::tanh(std::sqrt(X * X + Y * Y) / sz), std::fabs(n));
+        ph += n * std::atan2(Y, X) + chi;
+      }
+      const size_t k = (size_t)j * nx + i;
+      f[k] = mod * std::cos(ph);
+      f[P + k] = mod * std::sin(ph);
+    }
+}
+
 void or_ansatz(int theory, const double* sol, int nsol, double* f, int nx, int ny, double dx, double dy) {
   const size_t P = (size_t)nx * ny;
   for (int j = 0; j < ny; ++j)

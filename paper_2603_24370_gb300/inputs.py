@@ -41,6 +41,7 @@ class SplitMix64:
 ABELIAN_HIGGS = 1
 CHIRAL_MAGNET = 2
 BABY_SKYRME = 3
+BEC = 4
 
 # Couplings of the workloads. Abelian Higgs: (lambda, u). Chiral magnet:
 # (J, D, K, h, dmi_type) with interfacial DMI (type 0).
@@ -160,7 +161,8 @@ def smooth_field(theory: int, nx: int, ny: int, dx: float, dy: float, seed: int,
     Gaussian bumps with seeded centres, widths and amplitudes. Chiral magnet and
     Baby Skyrme: a unit field from smooth angles, n = (sin T cos P, sin T sin P,
     cos T) with T, P sums of Gaussian bumps (unit length by construction, no
-    normalisation).
+    normalisation). BEC: psi = env (1 + s_1) + i env s_2 with a Gaussian envelope
+    env that is small at the edge of the box.
     """
     rng = SplitMix64(seed)
     x = (np.arange(nx) - 0.5 * (nx - 1)) * dx
@@ -179,6 +181,9 @@ def smooth_field(theory: int, nx: int, ny: int, dx: float, dy: float, seed: int,
 
     if theory == ABELIAN_HIGGS:
         return np.stack([1.0 + bumpsum(), bumpsum(), bumpsum(), bumpsum()])
+    if theory == BEC:
+        env = np.exp(-(X * X + Y * Y) / (0.25 * min(Lx, Ly) ** 2))
+        return np.stack([env * (1.0 + bumpsum()), env * bumpsum()])
     if theory in (CHIRAL_MAGNET, BABY_SKYRME):
         T = 0.6 + 3.0 * bumpsum()
         P = 5.0 * bumpsum()

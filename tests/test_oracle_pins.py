@@ -20,6 +20,8 @@ from paper_2603_24370_gb300 import inputs as I
 AH, CM, HARM = O.ABELIAN_HIGGS, O.CHIRAL_MAGNET, O.HARMONIC_TEST
 BS = O.BABY_SKYRME
 BS_PRM = (1.0, 0.7, 0.3)  # kappa, mu, nu
+BEC = O.BEC
+BEC_PRM = (1.3, 0.6, 2.0)  # g, Omega, mu
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_constants.json")
 AH_PRM = (1.0, 1.0)
 CM_PRM = (1.0, 1.0, 0.1, 0.6, 0.0)
@@ -413,12 +415,137 @@ def test_bs_skyrmion_relaxes_to_the_radial_minimum():
     assert 12.0 < errs[0] / errs[1] < 20.0
 
 
+# ---------------------------------------------------------------- rotating BEC (Table 1)
+def _bec_radial(w, m, r):
+    """f(r) = (r / w)^|m| exp(-r^2 / w^2) and f'(r)."""
+    f = (r / w) ** abs(m) * math.exp(-(r / w) ** 2)
+    fp = f * (abs(m) / r - 2.0 * r / (w * w)) if r > 0 else 0.0
+    return f, fp
+
+
+@pytest.mark.parametrize("m", [0, 1, 2])
+def test_bec_energy_and_rotation_match_the_radial_reduction(m):
+    """psi = f(r) e^{i m theta}: the lattice energy converges at fourth order to
+    2 pi int r dr [(f'^2 + m^2 f^2 / r^2)/2 + r^2 f^2 / 2 + g f^4 / 2 - mu f^2] - Omega m N,
+    and the angular momentum Re int psi* L_z psi to m N (L_z = -i d_theta)."""
+    from scipy.integrate import quad
+    g, Om, mu = BEC_PRM
+    w = 2.0
+
+    def dens(r):
+        f, fp = _bec_radial(w, m, r)
+        kin = 0.5 * (fp * fp + (m * m * f * f / (r * r) if r > 0 else 0.0))
+        return r * (kin + 0.5 * r * r * f * f + 0.5 * g * f ** 4 - mu * f * f)
+
+    N = 2 * math.pi * quad(lambda r: r * _bec_radial(w, m, r)[0] ** 2, 0, 30, epsabs=1e-14, epsrel=1e-13)[0]
+    Econt = 2 * math.pi * quad(dens, 0, 30, epsabs=1e-13, epsrel=1e-13, limit=400)[0] - Om * m * N
+    errs, lz = [], []
+    for n in (81, 161):
+        L = 16.0
+        dx = L / (n - 1)
+        X, Y = grid(n, n, dx, dx)
+        r = np.hypot(X, Y)
+        f = (r / w) ** abs(m) * np.exp(-(r / w) ** 2)
+        th = m * np.arctan2(Y, X)
+        psi = np.stack([f * np.cos(th), f * np.sin(th)])
+        errs.append(abs(O.energy(BEC, BEC_PRM, psi, dx, dx) - Econt))
+        o = O.observables(BEC, BEC_PRM, psi, dx, dx)
+        lz.append(abs(o["angular_momentum"] - m * o["atoms"]) + abs(o["atoms"] - N))
+    assert errs[1] < 3e-5 * max(1.0, abs(Econt))
+    assert 12.0 < errs[0] / errs[1] < 20.0
+    assert lz[1] < 1e-4 * N
+    if m:
+        assert 12.0 < lz[0] / lz[1] < 20.0
+
+
+def test_bec_symmetries():
+    """The functional is invariant under a global phase (exactly: psi -> e^{i a} psi
+    rotates G with psi) and, on a centred square grid, under 90-degree rotations of
+    space (trap and L_z are rotation invariant)."""
+    n, dx = 40, 0.3
+    f = I.smooth_field(BEC, n, n, dx, dx, seed=17)
+    a = 0.83
+    c, s_ = math.cos(a), math.sin(a)
+    fr = np.stack([c * f[0] - s_ * f[1], s_ * f[0] + c * f[1]])
+    assert O.energy(BEC, BEC_PRM, fr, dx, dx) == pytest.approx(O.energy(BEC, BEC_PRM, f, dx, dx), rel=1e-13)
+    Gf, Gr = O.force(BEC, BEC_PRM, f, dx, dx), O.force(BEC, BEC_PRM, fr, dx, dx)
+    np.testing.assert_allclose(Gr, np.stack([c * Gf[0] - s_ * Gf[1], s_ * Gf[0] + c * Gf[1]]), rtol=0,
+                               atol=1e-12 * np.abs(Gf).max())
+    g90 = np.stack([_rot90_scalar(f[0]), _rot90_scalar(f[1])])
+    assert O.energy(BEC, BEC_PRM, g90, dx, dx) == pytest.approx(O.energy(BEC, BEC_PRM, f, dx, dx), rel=1e-13)
+    G90 = O.force(BEC, BEC_PRM, g90, dx, dx)
+    np.testing.assert_allclose(G90, np.stack([_rot90_scalar(Gf[0]), _rot90_scalar(Gf[1])]), rtol=0,
+                               atol=1e-11 * np.abs(Gf).max())
+    # the rotation term is odd in Omega: the force changes under Omega -> -Omega
+    assert np.abs(O.force(BEC, (1.3, -0.6, 2.0), f, dx, dx) - Gf).max() > 1e-3 * np.abs(Gf).max()
+
+
+def _bec_ground_state(g, mu):
+    """Radial Gross-Pitaevskii ground state at chemical potential mu (Omega = 0):
+    -f''/2 - f'/(2r) + r^2 f/2 + g f^3 = mu f, f'(0) = 0, f -> 0; shooting on f(0)."""
+    from scipy.integrate import quad, solve_ivp
+
+    def rhs(r, y):
+        f, fp = y
+        return [fp, -fp / r + (r * r + 2 * g * f * f - 2 * mu) * f]
+
+    def shoot(f0):
+        r0 = 1e-6
+        c = (2 * g * f0 ** 3 - 2 * mu * f0) / 4
+        return solve_ivp(rhs, (r0, 10.0), [f0 + c * r0 * r0, 2 * c * r0], rtol=1e-12, atol=1e-14,
+                         dense_output=True, events=[lambda r, y: y[0], lambda r, y: y[1]])
+
+    lo, hi = 0.1, 1.5 * math.sqrt(mu / g)
+    for _ in range(80):
+        mid = 0.5 * (lo + hi)
+        if shoot(mid).t_events[0].size:
+            lo = mid  # crosses zero: f(0) too small
+        else:
+            hi = mid
+    sol = shoot(lo)
+    rs = np.linspace(1e-6, sol.t[-1], 40000)
+    rc = rs[np.argmin(np.abs(sol.sol(rs)[0]))]
+
+    def edens(r):
+        f, fp = sol.sol(r)
+        return r * (0.5 * fp * fp + 0.5 * r * r * f * f + 0.5 * g * f ** 4 - mu * f * f)
+
+    E = 2 * math.pi * quad(edens, 1e-6, rc, limit=500)[0]
+    N = 2 * math.pi * quad(lambda r: r * sol.sol(r)[0] ** 2, 1e-6, rc, limit=500)[0]
+    return E, N, lo
+
+
+@pytest.mark.slow
+def test_bec_ground_state_is_the_radial_solution_and_near_thomas_fermi():
+    """Omega = 0: the arrested flow from the Thomas-Fermi ansatz relaxes to the radial
+    Gross-Pitaevskii ground state (independent shooting solution), its energy at fourth
+    order in dx; at mu = 10 the density is close to the Thomas-Fermi profile
+    (mu - r^2/2)/g: N within 2% of pi mu^2 / g and the centre density within 1% of mu/g."""
+    g, mu = 1.0, 10.0
+    E, N, f0 = _bec_ground_state(g, mu)
+    assert abs(N / (math.pi * mu * mu / g) - 1) < 0.02
+    assert abs(f0 * f0 / (mu / g) - 1) < 0.01
+    errs = []
+    for n, dx in ((81, 0.2), (161, 0.1)):
+        f = O.ansatz_bec((g, 0.0, mu), [], n, n, dx, dx)
+        r = O.minimise(BEC, (g, 0.0, mu), f, dx, dx, tol=1e-7, max_steps=20000)
+        assert r["converged"]
+        o = O.observables(BEC, (g, 0.0, mu), r["f"], dx, dx)
+        errs.append(abs(o["energy"] - E))
+        assert o["atoms"] == pytest.approx(N, rel=1e-5)
+        assert o["angular_momentum"] == pytest.approx(0.0, abs=1e-8)
+        c = n // 2
+        assert r["f"][0, c, c] ** 2 + r["f"][1, c, c] ** 2 == pytest.approx(f0 * f0, rel=1e-4)
+    assert errs[1] < 1e-6 * abs(E)
+    assert 12.0 < errs[0] / errs[1] < 20.0
+
+
 # ---------------------------------------------------------------- force (Eq. 3's right-hand side)
 def _prm(theory):
-    return {AH: AH_PRM, CM: (1.0, 0.8, 0.15, 0.5, 0.0), BS: BS_PRM}[theory]
+    return {AH: AH_PRM, CM: (1.0, 0.8, 0.15, 0.5, 0.0), BS: BS_PRM, BEC: BEC_PRM}[theory]
 
 
-@pytest.mark.parametrize("theory", [AH, CM, BS])
+@pytest.mark.parametrize("theory", [AH, CM, BS, BEC])
 def test_exact_gradient_matches_brute_force(theory):
     nx, ny, dx, dy = 12, 11, 0.3, 0.25
     prm = _prm(theory)
@@ -434,7 +561,7 @@ def test_exact_gradient_matches_brute_force(theory):
     np.testing.assert_allclose(grad, fd, rtol=0, atol=1e-7 * np.abs(grad).max())
 
 
-@pytest.mark.parametrize("theory", [AH, CM, BS])
+@pytest.mark.parametrize("theory", [AH, CM, BS, BEC])
 def test_force_is_energy_gradient_to_fourth_order(theory):
     """dx dy G and dE_h/dphi (tangent part for the unit-vector theories) are two O(h^4)
     discretisations of the same Euler-Lagrange expression: their gap shrinks ~16x per halving."""
