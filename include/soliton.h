@@ -69,6 +69,13 @@ extern "C" {
                            /* e = |d m|^2/2 + kappa^2/2 |d_1 m x d_2 m|^2 + V(m),            */
                            /* V = mu^2 (1 - m_3) + nu^2/2 m_1^2 (standard potential at nu = 0,*/
                            /* easy-plane at mu = 0); projected like the chiral magnet       */
+#define SS_BEC 4           /* rotating trapped BEC (Table 1), params {g, Omega, mu}, g > 0: */
+                           /* psi = u + i v, dimensionless (hbar = m = omega = 1), in the   */
+                           /* grand-canonical form at chemical potential mu:                */
+                           /* e = |grad psi|^2/2 + r^2/2 |psi|^2 + g/2 |psi|^4 - mu |psi|^2 */
+                           /*     - Omega Re(psi* L_z psi), L_z = -i (x d_y - y d_x),       */
+                           /* (x, y) measured from the grid centre; the atom number N and  */
+                           /* the angular momentum are observables (ss_obs)                 */
 
 /* ---- minimisers ---- */
 #define SS_METHOD_ANF 0      /* arrested Newton flow, RK4 + Eq. 4 (Sec. 3.2): the default */
@@ -87,7 +94,10 @@ typedef struct ss_ctx ss_ctx;
  *                 helicity gamma = phase: n = (sin f cos(m theta + gamma),
  *                 sin f sin(m theta + gamma), cos f), f = pi (1 - r/R) for r < R,
  *                 n = e_3 outside every disc; the first disc containing a site wins.
- *                 Its lattice charge is -m. */
+ *                 Its lattice charge is -m.
+ *  BEC: the Thomas-Fermi amplitude sqrt(max(0, mu - r^2/2) / g) times a vortex factor
+ *       tanh(r_k/size_k)^|charge_k| exp(i (charge_k theta_k + phase_k)) per entry (an
+ *       entry of charge 0 and phase 0 gives the Thomas-Fermi profile alone). */
 typedef struct {
   double x, y;
   int charge;
@@ -121,6 +131,8 @@ typedef struct {
   double grad_max_raw; /* max_I |G|                                                     */
   double norm_dev;     /* chiral magnet: max over sites of ||n| - 1|; else 0            */
   long long steps;     /* steps taken since the fields were last set                    */
+  double atoms;        /* BEC: N = dx dy sum_I |psi|^2; else 0                          */
+  double angular_momentum; /* BEC: dx dy sum_I Re(psi* L_z psi); else 0                 */
 } ss_obs;
 
 /* Message for the calling thread's last failed call ("" if none). Owned by the
@@ -142,7 +154,8 @@ int ss_create_grid(ss_ctx** out, int nx, int ny, double dx, double dy, int preci
  * into device arrays"; Table 1; Eq. 5). params is a host array of n_params
  * doubles: Abelian Higgs {lambda, u} (u defaults to 1 if n_params == 1); chiral
  * magnet {J, D, K, h, dmi_type} (dmi_type defaults to 0 if n_params == 4); Baby
- * Skyrme {kappa, mu, nu} (nu defaults to 0 if n_params == 2).
+ * Skyrme {kappa, mu, nu} (nu defaults to 0 if n_params == 2); BEC {g, Omega, mu}
+ * with g > 0 (the BEC's charge observable is 0: see atoms, angular_momentum).
  * Allocates the device buffers; previous fields are discarded.
  * Errors: SS_ERR_ARG (unknown theory, bad n_params, J <= 0), SS_ERR_NOMEM, SS_ERR_CUDA. */
 int ss_set_theory(ss_ctx* ctx, int theory, const double* params, int n_params);
@@ -288,7 +301,9 @@ int ss_batch_set_launch(ss_batch* batch, int tile_shape, const int* blocks);
  * the Euler stability limit of the Eq. 2 Laplacian, dtau = step_factor * (3/8) /
  * (1/dx^2 + 1/dy^2) per problem; it must be in (0, 1], and <= 0 selects 0.8. (The
  * limit is 2 / lambda_max with lambda_max = (16/3)(1/dx^2 + 1/dy^2), the stencil's
- * largest eigenvalue; the couplings' own terms shift it by O(dx^2).) Every problem
+ * largest eigenvalue; the couplings' own terms shift it by O(dx^2). For SS_BEC,
+ * lambda_max also carries bounds of the trap, r_max^2, the interaction, 4 |mu|,
+ * and the rotation, 2 |Omega| r_max 1.3722 / min(dx, dy), over the grid.) Every problem
  * whose fields are set restarts from its current field at rest, with its step
  * count and flow record cleared; tile shape and grids are kept. Descent takes one
  * kernel launch per step: it evaluates E_h, dx dy max|G| and -G of the current field

@@ -82,6 +82,15 @@ int pack_couplings(int theory, const double* params, int n_params, double k[10],
     else if (type == 1) { k[4] = 1.0; k[8] = 1.0; }  // d_i = e_i
     else { k[4] = 1.0; k[8] = -1.0; }                // d_1 = e_1, d_2 = -e_2
     *C = 3;
+  } else if (theory == SS_BEC) {
+    if (n_params != 3) return fail(SS_ERR_ARG, "BEC takes {g, Omega, mu}");
+    for (int i = 0; i < 3; ++i)
+      if (!std::isfinite(params[i])) return fail(SS_ERR_ARG, "BEC parameters must be finite");
+    if (!(params[0] > 0.0)) return fail(SS_ERR_ARG, "g must be > 0 (the functional is unbounded below otherwise)");
+    k[0] = params[0];  // g
+    k[1] = params[1];  // Omega
+    k[2] = params[2];  // mu
+    *C = 2;
   } else if (theory == SS_BABY_SKYRME) {
     if (n_params < 2 || n_params > 3) return fail(SS_ERR_ARG, "Baby Skyrme takes {kappa, mu[, nu]}");
     for (int i = 0; i < n_params; ++i)
@@ -99,7 +108,12 @@ int pack_couplings(int theory, const double* params, int n_params, double k[10],
 
 // Kernel theory tag of an SS_* theory code.
 int th_of(int theory) {
-  return theory == SS_ABELIAN_HIGGS ? TH_AH : (theory == SS_CHIRAL_MAGNET ? TH_CM : TH_BS);
+  switch (theory) {
+    case SS_ABELIAN_HIGGS: return TH_AH;
+    case SS_CHIRAL_MAGNET: return TH_CM;
+    case SS_BABY_SKYRME: return TH_BS;
+    default: return TH_BEC;
+  }
 }
 
 int check_grid(int nx, int ny, double dx, double dy) {
@@ -110,11 +124,21 @@ int check_grid(int nx, int ny, double dx, double dy) {
   return SS_OK;
 }
 
-// Gradient descent: dtau = factor x the Euler stability limit of the Eq. 2
-// Laplacian, 2 / lambda_max with lambda_max = (16/3)(1/dx^2 + 1/dy^2) (the stencil's
-// largest eigenvalue, at the checkerboard mode).
-double descent_step(double dx, double dy, double factor) {
-  return factor * 2.0 / ((16.0 / 3.0) * (1.0 / (dx * dx) + 1.0 / (dy * dy)));
+// Gradient descent: dtau = factor x the Euler stability limit 2 / lambda_max. For the
+// Eq. 2 Laplacian lambda_max = (16/3)(1/dx^2 + 1/dy^2) (the stencil's largest
+// eigenvalue, at the checkerboard mode). The BEC adds bounds on its position-dependent
+// terms over the grid: the trap r_max^2, the interaction at the Thomas-Fermi density
+// 4 |mu|, and the rotation 2 |Omega| r_max s1 with s1 = 1.3722 / min(dx, dy), the
+// largest magnitude of the Eq. 1 symbol.
+double descent_step(double dx, double dy, double factor, int theory = 0, int nx = 0, int ny = 0,
+                    const double* coup = nullptr) {
+  double lam = (16.0 / 3.0) * (1.0 / (dx * dx) + 1.0 / (dy * dy));
+  if (theory == SS_BEC && coup) {
+    const double hx = 0.5 * (nx - 1) * dx, hy = 0.5 * (ny - 1) * dy;
+    const double r2 = hx * hx + hy * hy;
+    lam += r2 + 4.0 * std::fabs(coup[2]) + 2.0 * std::fabs(coup[1]) * std::sqrt(r2) * 1.3722 / (dx < dy ? dx : dy);
+  }
+  return factor * 2.0 / lam;
 }
 constexpr double DEFAULT_STEP_FACTOR = 0.8;
 
@@ -149,6 +173,8 @@ ProbDesc<R> make_desc(const Problem& p, DevState* st, FlowPartial* part) {
   }
   d.dt = (R)p.dt;
   d.tau = (R)p.tau;
+  d.hx = (R)p.dx;
+  d.hy = (R)p.dy;
   d.h.i12dx = (R)(1.0 / (12.0 * p.dx));
   d.h.i12dy = (R)(1.0 / (12.0 * p.dy));
   d.h.i12dx2 = (R)(1.0 / (12.0 * p.dx * p.dx));
@@ -511,6 +537,8 @@ int problem_observables(ss_batch* b, int i, ss_obs* out) {
   out->grad_max_raw = h.obs_gmax_raw;
   out->norm_dev = h.obs_normdev;
   out->steps = h.steps;
+  out->atoms = h.obs_atoms;
+  out->angular_momentum = h.obs_lz;
   return SS_OK;
 }
 
@@ -565,7 +593,7 @@ extern "C" {
 
 const char* ss_last_error(void) { return g_err.c_str(); }
 
-int ss_version(void) { return 4; }
+int ss_version(void) { return 5; }
 
 int ss_create_grid(ss_ctx** out, int nx, int ny, double dx, double dy, int precision, void* cuda_stream) {
   if (!out) return fail(SS_ERR_ARG, "out is NULL");
@@ -615,7 +643,7 @@ int ss_set_theory(ss_ctx* c, int theory, const double* params, int n_params) {
   p.dx = c->dx;
   p.dy = c->dy;
   p.dt = 0.5 * (c->dx < c->dy ? c->dx : c->dy);  // Sec. 3.1: C = dt / dx = 0.5
-  p.tau = descent_step(p.dx, p.dy, DEFAULT_STEP_FACTOR);
+  p.tau = descent_step(p.dx, p.dy, DEFAULT_STEP_FACTOR, theory, p.nx, p.ny, k);
   std::memcpy(p.coup, k, sizeof(k));
   b->probs.push_back(p);
   rc = batch_alloc(b);
@@ -834,7 +862,7 @@ int ss_batch_create(ss_batch** out, int theory, int precision, const ss_batch_it
     p.dx = it.dx;
     p.dy = it.dy;
     p.dt = 0.5 * (it.dx < it.dy ? it.dx : it.dy);  // Sec. 3.1
-    p.tau = descent_step(p.dx, p.dy, DEFAULT_STEP_FACTOR);
+    p.tau = descent_step(p.dx, p.dy, DEFAULT_STEP_FACTOR, theory, p.nx, p.ny, k);
     std::memcpy(p.coup, k, sizeof(k));
     b->probs.push_back(p);
   }
@@ -1043,7 +1071,7 @@ int batch_set_method(ss_batch* b, int method, double step_factor) {
   if (rc != SS_OK) return rc;
   for (int i = 0; i < b->n(); ++i) {
     Problem& p = b->probs[i];
-    p.tau = descent_step(p.dx, p.dy, step_factor);
+    p.tau = descent_step(p.dx, p.dy, step_factor, b->theory, p.nx, p.ny, p.coup);
     if (!b->fields_set[i]) continue;
     const int cur = cur_of(b, i);
     const size_t bytes = (size_t)b->C * p.plane * b->elem;

@@ -22,12 +22,13 @@ constexpr int HALO = 2;
 constexpr int SX = TX + 2 * HALO, SY = TY + 2 * HALO;
 constexpr int ROWS_PER_THREAD = TY / BY;
 
-enum { TH_AH = 1, TH_CM = 2, TH_BS = 3 };
+enum { TH_AH = 1, TH_CM = 2, TH_BS = 3, TH_BEC = 4 };
 
 template <int TH> struct NComp;
 template <> struct NComp<TH_AH> { static constexpr int C = 4; };
 template <> struct NComp<TH_CM> { static constexpr int C = 3; };
 template <> struct NComp<TH_BS> { static constexpr int C = 3; };
+template <> struct NComp<TH_BEC> { static constexpr int C = 2; };
 
 // Theories whose field is a unit 3-vector (projected onto the sphere).
 template <int TH> struct UnitVector { static constexpr bool value = TH == TH_CM || TH == TH_BS; };
@@ -54,6 +55,7 @@ struct DevState {
   unsigned int obs_ticket;  // arrival counter of the observables reduction
   // observables (FP64 evaluation)
   double obs_energy, obs_charge, obs_flux, obs_gmax_raw, obs_normdev;
+  double obs_atoms, obs_lz;  // BEC: dx dy sum_I |psi|^2 and dx dy sum_I Re(psi* L_z psi)
 };
 
 struct FlowPartial {  // per-block part of the flow reduction (64 B)
@@ -192,6 +194,7 @@ SS_HD Deriv<R> stencil(const R* P, int sx, int sy, const Spacing<R>& h) {
 // Couplings in the working type. Abelian Higgs: c[0] = lambda, c[1] = u^2.
 // Chiral magnet: c[0] = J, c[1] = D, c[2] = K, c[3] = h, c[4..6] = d_1, c[7..9] = d_2.
 // Baby Skyrme: c[0] = kappa^2, c[1] = mu^2, c[2] = nu^2.
+// BEC: c[0] = g, c[1] = Omega, c[2] = mu (chemical potential).
 template <typename R>
 struct Couplings {
   R c[10];
@@ -299,6 +302,30 @@ SS_HD void force_bs(const Couplings<R>& k, const R* m, const R* a, const R* b, c
   for (int c = 0; c < 3; ++c) G[c] -= gn * m[c];
 }
 
+// Rotating trapped BEC (Table 1), dimensionless (hbar = m = omega = 1), in the
+// grand-canonical form at chemical potential mu, psi = u + i v, D = x d_y - y d_x:
+//   e = 1/2 |grad psi|^2 + (r^2/2 + g/2 |psi|^2 - mu) |psi|^2 - Omega (u D v - v D u)
+// (u D v - v D u is the real part of psi* L_z psi; the imaginary part is a total
+// derivative). (x, y) is the site's position, origin at the grid centre.
+template <typename R>
+SS_HD R density_bec(const Couplings<R>& k, const R* v, const R* fx, const R* fy, R x, R y) {
+  const R n = v[0] * v[0] + v[1] * v[1];
+  const R Du = x * fy[0] - y * fx[0], Dv = x * fy[1] - y * fx[1];
+  const R kin = R(0.5) * (fx[0] * fx[0] + fy[0] * fy[0] + fx[1] * fx[1] + fy[1] * fy[1]);
+  return kin + (R(0.5) * (x * x + y * y) + R(0.5) * k.c[0] * n - k.c[2]) * n - k.c[1] * (v[0] * Dv - v[1] * Du);
+}
+
+// G_u = -lap u + (r^2 + 2 g |psi|^2 - 2 mu) u - 2 Omega D v,
+// G_v = -lap v + (r^2 + 2 g |psi|^2 - 2 mu) v + 2 Omega D u.
+template <typename R>
+SS_HD void force_bec(const Couplings<R>& k, const R* v, const R* fx, const R* fy, const R* fxx, const R* fyy, R x,
+                     R y, R* G) {
+  const R w = (x * x + y * y) + R(2) * k.c[0] * (v[0] * v[0] + v[1] * v[1]) - R(2) * k.c[2];
+  const R Du = x * fy[0] - y * fx[0], Dv = x * fy[1] - y * fx[1];
+  G[0] = -(fxx[0] + fyy[0]) + w * v[0] - R(2) * k.c[1] * Dv;
+  G[1] = -(fxx[1] + fyy[1]) + w * v[1] + R(2) * k.c[1] * Du;
+}
+
 // ------------------------------------------------------------------ energy differences
 // Eq. 4 compares E_h(phi^{n+1}) with E_h(phi^n). Both energy densities are
 // polynomials in (phi, d phi), so with a = phi^{n+1} and delta = phi^{n+1} - phi^n
@@ -382,26 +409,49 @@ SS_HD R delta_density_bs(const Couplings<R>& k, const R* a, const R* ax, const R
   return sig + R(0.5) * k.c[0] * sky - k.c[1] * d[2] + R(0.5) * k.c[2] * d[0] * (R(2) * a[0] - d[0]);
 }
 
-// Energy density, force and energy difference of theory TH.
+// BEC: with n = |psi|^2 and the exact difference dn = sum_c delta_c (2 a_c - delta_c),
+//   kinetic   sum_i d_i delta . (d_i a - d_i delta / 2)
+//   trap      r^2/2 dn,  interaction g/2 (2 n - dn) dn,  chemical potential -mu dn
+//   rotation  -Omega [B(a, delta) + B(delta, a) - B(delta, delta)],
+// B(p, q) = p_u D q_v - p_v D q_u being bilinear with B(a, a) the rotation density.
+template <typename R>
+SS_HD R delta_density_bec(const Couplings<R>& k, const R* a, const R* ax, const R* ay, const R* d, const R* dx,
+                          const R* dy, R x, R y) {
+  R kin = R(0);
+#pragma unroll
+  for (int c = 0; c < 2; ++c) kin += dx[c] * (ax[c] - R(0.5) * dx[c]) + dy[c] * (ay[c] - R(0.5) * dy[c]);
+  const R n = a[0] * a[0] + a[1] * a[1];
+  const R dn = d[0] * (R(2) * a[0] - d[0]) + d[1] * (R(2) * a[1] - d[1]);
+  const R Da0 = x * ay[0] - y * ax[0], Da1 = x * ay[1] - y * ax[1];
+  const R Dd0 = x * dy[0] - y * dx[0], Dd1 = x * dy[1] - y * dx[1];
+  const R rot = (a[0] * Dd1 - a[1] * Dd0) + (d[0] * Da1 - d[1] * Da0) - (d[0] * Dd1 - d[1] * Dd0);
+  return kin + (R(0.5) * (x * x + y * y) - k.c[2]) * dn + R(0.5) * k.c[0] * (R(2) * n - dn) * dn - k.c[1] * rot;
+}
+
+// Energy density, force and energy difference of theory TH at a site at (x, y)
+// (the position enters only the BEC's trap and rotation terms).
 template <int TH, typename R>
-SS_HD R density_at(const Couplings<R>& k, const R* v, const R* fx, const R* fy) {
+SS_HD R density_at(const Couplings<R>& k, const R* v, const R* fx, const R* fy, R x = R(0), R y = R(0)) {
   if (TH == TH_AH) return density_ah<R>(k, v, fx, fy);
   if (TH == TH_CM) return density_cm<R>(k, v, fx, fy);
-  return density_bs<R>(k, v, fx, fy);
+  if (TH == TH_BS) return density_bs<R>(k, v, fx, fy);
+  return density_bec<R>(k, v, fx, fy, x, y);
 }
 template <int TH, typename R>
 SS_HD R delta_density_at(const Couplings<R>& k, const R* a, const R* ax, const R* ay, const R* d, const R* dx,
-                         const R* dy) {
+                         const R* dy, R x = R(0), R y = R(0)) {
   if (TH == TH_AH) return delta_density_ah<R>(k, a, ax, ay, d, dx, dy);
   if (TH == TH_CM) return delta_density_cm<R>(k, a, ax, ay, d, dx, dy);
-  return delta_density_bs<R>(k, a, ax, ay, d, dx, dy);
+  if (TH == TH_BS) return delta_density_bs<R>(k, a, ax, ay, d, dx, dy);
+  return delta_density_bec<R>(k, a, ax, ay, d, dx, dy, x, y);
 }
 template <int TH, typename R>
 SS_HD void force_of(const Couplings<R>& k, const R* v, const R* fx, const R* fy, const R* fxx, const R* fyy,
-                    const R* fxy, R* G) {
+                    const R* fxy, R* G, R x = R(0), R y = R(0)) {
   if (TH == TH_AH) force_ah<R>(k, v, fx, fy, fxx, fyy, fxy, G);
   else if (TH == TH_CM) force_cm<R>(k, v, fx, fy, fxx, fyy, G);
-  else force_bs<R>(k, v, fx, fy, fxx, fyy, fxy, G);
+  else if (TH == TH_BS) force_bs<R>(k, v, fx, fy, fxx, fyy, fxy, G);
+  else force_bec<R>(k, v, fx, fy, fxx, fyy, x, y, G);
 }
 
 }  // namespace ss

@@ -218,25 +218,25 @@ struct StageWin {
   static constexpr int SXY = SXY_;
   Win<R, TH == TH_BS> w0, w1;  // Baby Skyrme: mixed derivatives of every component
   Win<R, TH == TH_AH || TH == TH_BS> w2;
-  Win<R, TH == TH_AH> w3;  // unused for three-component theories
+  Win<R, TH == TH_AH> w3;  // unused for two- and three-component theories
 
   __device__ __forceinline__ void enter(const R* tiles, int off, int slot) {
     w0.enter(tiles + off, slot);
     w1.enter(tiles + SXY + off, slot);
-    w2.enter(tiles + 2 * SXY + off, slot);
+    if (C >= 3) w2.enter(tiles + 2 * SXY + off, slot);
     if (C == 4) w3.enter(tiles + 3 * SXY + off, slot);
   }
   __device__ __forceinline__ void shift() {
     w0.shift();
     w1.shift();
-    w2.shift();
+    if (C >= 3) w2.shift();
     if (C == 4) w3.shift();
   }
   __device__ __forceinline__ void derivs(const R* tiles, int off, const Spacing<R>& h, R* v, R* fx, R* fy, R* fxx,
                                          R* fyy, R* fxy) const {
     w0.template derivs<true>(tiles + off, h, v[0], fx[0], fy[0], fxx[0], fyy[0], fxy[0]);
     w1.template derivs<true>(tiles + SXY + off, h, v[1], fx[1], fy[1], fxx[1], fyy[1], fxy[1]);
-    w2.template derivs<true>(tiles + 2 * SXY + off, h, v[2], fx[2], fy[2], fxx[2], fyy[2], fxy[2]);
+    if (C >= 3) w2.template derivs<true>(tiles + 2 * SXY + off, h, v[2], fx[2], fy[2], fxx[2], fyy[2], fxy[2]);
     if (C == 4) w3.template derivs<true>(tiles + 3 * SXY + off, h, v[3], fx[3], fy[3], fxx[3], fyy[3], fxy[3]);
   }
 };
@@ -266,8 +266,8 @@ struct DiffWin {
 
 template <int TH, typename R>
 __device__ __forceinline__ void force_at(const Couplings<R>& k, const R* v, const R* fx, const R* fy, const R* fxx,
-                                         const R* fyy, const R* fxy, R* G) {
-  force_of<TH, R>(k, v, fx, fy, fxx, fyy, fxy, G);
+                                         const R* fyy, const R* fxy, R* G, R x = R(0), R y = R(0)) {
+  force_of<TH, R>(k, v, fx, fy, fxx, fyy, fxy, G, x, y);
 }
 
 // ---- per-tile block reduction in the working type: two compensated sums, one max
@@ -515,6 +515,10 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
     const int sx = threadIdx.x + 2, sy0 = threadIdx.y * RY + 2;
     const int gx = x0 + threadIdx.x, gyb = y0 + threadIdx.y * RY;
     const bool colok = gx >= 2 && gx < nx - 2;
+    // site position, origin at the grid centre (only the BEC's trap and rotation use it)
+    const R hy = D.hy;
+    const R xs = TH == TH_BEC ? (R(gx) - R(0.5) * R(nx - 1)) * D.hx : R(0);
+    auto ypos = [&](int r) { return TH == TH_BEC ? (R(gyb + r) - R(0.5) * R(ny - 1)) * hy : R(0); };
 
     if (PASS != 2) {
       if (PASS == 1) {
@@ -534,7 +538,7 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
           const bool ok = colok && gyb + r >= 2 && gyb + r < ny - 2;
           R v[C], fx[C], fy[C], fxx[C], fyy[C], fxy[C], G[C];
           W.derivs(setA, off, h, v, fx, fy, fxx, fyy, fxy);
-          force_at<TH, R>(kc, v, fx, fy, fxx, fyy, fxy, G);
+          force_at<TH, R>(kc, v, fx, fy, fxx, fyy, fxy, G, xs, ypos(r));
           if (ok) {
             const size_t s = (size_t)(gyb + r) * nx + gx;
 #pragma unroll
@@ -542,7 +546,7 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
               kv1[c * P + s] = -G[c];
               gmr = absmax(gmr, G[c]);
             }
-            const R e = density_at<TH, R>(kc, v, fx, fy);
+            const R e = density_at<TH, R>(kc, v, fx, fy, xs, ypos(r));
             const R t1 = es + e;
             ec += (fabs(es) >= fabs(e)) ? (es - t1) + e : (e - t1) + es;
             es = t1;
@@ -551,7 +555,7 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
             R dd[C], dxv[C], dyv[C];
             D.derivs(setD, off, h, dd, dxv, dyv);
             if (ok) {
-              const R de = delta_density_at<TH, R>(kc, v, fx, fy, dd, dxv, dyv);
+              const R de = delta_density_at<TH, R>(kc, v, fx, fy, dd, dxv, dyv, xs, ypos(r));
               const R t2 = ds + de;
               dc += (fabs(ds) >= fabs(de)) ? (ds - t2) + de : (de - t2) + ds;
               ds = t2;
@@ -578,7 +582,7 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
           const int off = (sy0 + r) * T::SX + sx;
           R v[C], fx[C], fy[C], fxx[C], fyy[C], fxy[C], G[C];
           W.derivs(setB, off, h, v, fx, fy, fxx, fyy, fxy);
-          force_at<TH, R>(kc, v, fx, fy, fxx, fyy, fxy, G);
+          force_at<TH, R>(kc, v, fx, fy, fxx, fyy, fxy, G, xs, ypos(r));
           if (colok && gyb + r >= 2 && gyb + r < ny - 2) {
             const size_t s = (size_t)(gyb + r) * nx + gx;
 #pragma unroll
@@ -604,7 +608,7 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
           const int off = (sy0 + r) * T::SX + sx;
           R v[C], fx[C], fy[C], fxx[C], fyy[C], fxy[C], G[C];
           W.derivs(setA, off, h, v, fx, fy, fxx, fyy, fxy);
-          force_at<TH, R>(kc, v, fx, fy, fxx, fyy, fxy, G);
+          force_at<TH, R>(kc, v, fx, fy, fxx, fyy, fxy, G, xs, ypos(r));
           if (colok && gyb + r >= 2 && gyb + r < ny - 2) {
             const size_t s = (size_t)(gyb + r) * nx + gx;
 #pragma unroll
@@ -612,7 +616,7 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
               kv1[c * P + s] = -G[c];
               gmr = absmax(gmr, G[c]);
             }
-            const R e = density_at<TH, R>(kc, v, fx, fy);
+            const R e = density_at<TH, R>(kc, v, fx, fy, xs, ypos(r));
             const R t1 = es + e;
             ec += (fabs(es) >= fabs(e)) ? (es - t1) + e : (e - t1) + es;
             es = t1;
@@ -739,7 +743,7 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
           const int off = (sy0 + r) * T::SX + sx;
           R v[C], fx[C], fy[C], fxx[C], fyy[C], fxy[C], G[C];
           W.derivs(setA, off, h, v, fx, fy, fxx, fyy, fxy);
-          force_at<TH, R>(kc, v, fx, fy, fxx, fyy, fxy, G);
+          force_at<TH, R>(kc, v, fx, fy, fxx, fyy, fxy, G, xs, ypos(r));
 #pragma unroll
           for (int c = 0; c < C; ++c) k3[r][c] = -G[c];
           if (r + 1 < RY) {
@@ -762,7 +766,7 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
           const int off = (sy0 + r) * T::SX + sx;
           R v[C], fx[C], fy[C], fxx[C], fyy[C], fxy[C], G[C];
           W.derivs(setB, off, h, v, fx, fy, fxx, fyy, fxy);
-          force_at<TH, R>(kc, v, fx, fy, fxx, fyy, fxy, G);
+          force_at<TH, R>(kc, v, fx, fy, fxx, fyy, fxy, G, xs, ypos(r));
           if (colok && gyb + r >= 2 && gyb + r < ny - 2) {
             const size_t s = (size_t)(gyb + r) * nx + gx;
             R p0[C], q[C], vn[C];
@@ -922,7 +926,8 @@ static cudaError_t pass_th(const BatchLaunch& b, int pass, cudaStream_t s) {
 cudaError_t launch_pass(const BatchLaunch& b, int pass, cudaStream_t s) {
   if (b.theory == TH_AH) return pass_th<TH_AH>(b, pass, s);
   if (b.theory == TH_CM) return pass_th<TH_CM>(b, pass, s);
-  return pass_th<TH_BS>(b, pass, s);
+  if (b.theory == TH_BS) return pass_th<TH_BS>(b, pass, s);
+  return pass_th<TH_BEC>(b, pass, s);
 }
 
 cudaError_t launch_reset_states(DevState* st, int n, cudaStream_t s) {
@@ -941,7 +946,7 @@ cudaError_t launch_count_active(const DevState* st, int n, int* out, cudaStream_
 }
 
 cudaError_t launch_scaled_copy(const LaunchCtx& c, void* out, const void* in, double scale, cudaStream_t s) {
-  const int C = c.theory == TH_AH ? 4 : 3;
+  const int C = c.theory == TH_AH ? 4 : (c.theory == TH_BEC ? 2 : 3);
   const size_t n = (size_t)C * c.plane;
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
@@ -992,7 +997,8 @@ void flow_occupancy(int theory, int prec, int ts, bool one, int occ[3]) {
   occ[0] = occ[1] = occ[2] = 1;
   if (theory == TH_AH) occupancy_sel<TH_AH>(prec, ts, one, occ);
   else if (theory == TH_CM) occupancy_sel<TH_CM>(prec, ts, one, occ);
-  else occupancy_sel<TH_BS>(prec, ts, one, occ);
+  else if (theory == TH_BS) occupancy_sel<TH_BS>(prec, ts, one, occ);
+  else occupancy_sel<TH_BEC>(prec, ts, one, occ);
   for (int i = 0; i < 3; ++i)
     if (occ[i] < 1) occ[i] = 1;
 }

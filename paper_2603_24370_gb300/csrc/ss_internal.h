@@ -49,6 +49,7 @@ struct ProbDesc {
   R* kv[2];         // k_v1, k_v2
   R dt;
   R tau;            // gradient descent: the step dtau of phi <- phi - dtau G
+  R hx, hy;         // dx, dy (site positions of the BEC's trap and rotation terms)
   Spacing<R> h;
   Couplings<R> k;
   double area;      // dx dy

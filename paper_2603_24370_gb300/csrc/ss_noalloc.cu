@@ -95,6 +95,14 @@ extern "C" int ss_observables_noalloc(int theory, const double* params, int n_pa
     if (type == 0) { k[5] = 1.0; k[7] = -1.0; }
     else if (type == 1) { k[4] = 1.0; k[8] = 1.0; }
     else { k[4] = 1.0; k[8] = -1.0; }
+  } else if (theory == SS_BEC) {
+    if (n_params != 3) return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: BEC takes {g, Omega, mu}");
+    for (int i = 0; i < 3; ++i)
+      if (!std::isfinite(params[i])) return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: parameters must be finite");
+    if (!(params[0] > 0.0)) return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: g must be > 0");
+    k[0] = params[0];
+    k[1] = params[1];
+    k[2] = params[2];
   } else if (theory == SS_BABY_SKYRME) {
     if (n_params < 2 || n_params > 3)
       return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: Baby Skyrme takes {kappa, mu[, nu]}");
@@ -128,7 +136,10 @@ extern "C" int ss_observables_noalloc(int theory, const double* params, int n_pa
   }
 
   LaunchCtx L{};
-  L.theory = theory == SS_ABELIAN_HIGGS ? TH_AH : (theory == SS_CHIRAL_MAGNET ? TH_CM : TH_BS);
+  L.theory = theory == SS_ABELIAN_HIGGS ? TH_AH
+             : theory == SS_CHIRAL_MAGNET ? TH_CM
+             : theory == SS_BABY_SKYRME   ? TH_BS
+                                          : TH_BEC;
   L.prec = precision;
   L.nx = nx;
   L.ny = ny;

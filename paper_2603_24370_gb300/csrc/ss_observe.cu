@@ -10,6 +10,7 @@
 //          two triangles (n00, n10, n11), (n00, n11, n01)   (chiral magnet, Baby Skyrme)
 //   Q    = (1/2pi) sum of wrapped arg-psi steps around the boundary of I (Abelian Higgs)
 //   max_I |G|, max ||n| - 1|
+//   N    = dx dy sum_I |psi|^2, L = dx dy sum_I Re(psi* L_z psi)   (BEC)
 // A compensated FP32 field is read as value + remainder, exactly, in FP64.
 #include "ss_internal.h"
 
@@ -23,6 +24,7 @@ struct ObsArgs {
   size_t plane;
   int ntx, ntiles;
   Spacing<double> h;
+  double hx, hy;  // dx, dy
   Couplings<double> k;
   double area;
   DevState* st;
@@ -102,6 +104,12 @@ __global__ void __launch_bounds__(NT) k_observables(ObsArgs<R> a) {
         force_ah<double>(a.k, v, fx, fy, fxx, fyy, fxy, G);
         neumaier(se, density_ah<double>(a.k, v, fx, fy));
         neumaier(sf, fx[3] - fy[2]);
+      } else if (TH == TH_BEC) {
+        const double x = (gx - 0.5 * (a.nx - 1)) * a.hx, y = (gy - 0.5 * (a.ny - 1)) * a.hy;
+        force_of<TH, double>(a.k, v, fx, fy, fxx, fyy, fxy, G, x, y);
+        neumaier(se, density_at<TH, double>(a.k, v, fx, fy, x, y));
+        neumaier(sf, v[0] * v[0] + v[1] * v[1]);  // atoms
+        neumaier(sq, v[0] * (x * fy[1] - y * fx[1]) - v[1] * (x * fy[0] - y * fx[0]));  // Re(psi* L_z psi)
       } else {
         force_of<TH, double>(a.k, v, fx, fy, fxx, fyy, fxy, G);
         neumaier(se, density_at<TH, double>(a.k, v, fx, fy));
@@ -139,8 +147,11 @@ __global__ void __launch_bounds__(NT) k_observables(ObsArgs<R> a) {
   if (tid == 0) {
     DevState* st = a.st;
     st->obs_energy = a.area * (sv2[0].s + sv2[0].c);
-    st->obs_flux = a.area * (sv2[1].s + sv2[1].c);
+    st->obs_flux = TH == TH_AH ? a.area * (sv2[1].s + sv2[1].c) : 0.0;
+    st->obs_atoms = TH == TH_BEC ? a.area * (sv2[1].s + sv2[1].c) : 0.0;
+    st->obs_lz = TH == TH_BEC ? a.area * (sv2[2].s + sv2[2].c) : 0.0;
     if (UnitVector<TH>::value) st->obs_charge = (sv2[2].s + sv2[2].c) / (4.0 * 3.14159265358979323846);
+    if (TH == TH_BEC) st->obs_charge = 0.0;
     st->obs_gmax_raw = mv2[0];
     st->obs_normdev = mv2[1];
     st->obs_ticket = 0;
@@ -180,14 +191,29 @@ __global__ void __launch_bounds__(NT) k_winding(const R* __restrict__ phi, int n
 
 // Initial data (Sec. 3.4 "model-specific ansatz"; standard forms, see soliton.h),
 // evaluated in FP64 and rounded once to the storage type, into both field buffers.
+// BEC: psi = sqrt(max(0, mu - r^2/2) / g) prod_k tanh(r_k/s_k)^{|n_k|} exp(i (n_k theta_k + chi_k))
+// (Thomas-Fermi amplitude times vortex factors); cp = {g, mu}.
 template <int TH, typename R>
 __global__ void k_ansatz(R* __restrict__ f0, R* __restrict__ f1, int nx, int ny, size_t plane, double dx, double dy,
-                         const double* __restrict__ sol, int ns) {
+                         const double* __restrict__ sol, int ns, double cg, double cmu) {
   const double PI = 3.14159265358979323846;
   for (size_t s = (size_t)blockIdx.x * blockDim.x + threadIdx.x; s < plane; s += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(s % nx), j = (int)(s / nx);
     const double x = (i - 0.5 * (nx - 1)) * dx, y = (j - 0.5 * (ny - 1)) * dy;
-    if (TH == TH_AH) {
+    if (TH == TH_BEC) {
+      double mod = sqrt(fmax(0.0, cmu - 0.5 * (x * x + y * y)) / cg), ph = 0.0;
+      for (int k = 0; k < ns; ++k) {
+        const double X = x - sol[5 * k], Y = y - sol[5 * k + 1];
+        const double n = sol[5 * k + 2], sz = sol[5 * k + 3], chi = sol[5 * k + 4];
+        mod *= pow(tanh(sqrt(X * X + Y * Y) / sz), fabs(n));
+        ph += n * atan2(Y, X) + chi;
+      }
+      double sn, cs;
+      sincos(ph, &sn, &cs);
+      const R v[2] = {(R)(mod * cs), (R)(mod * sn)};
+#pragma unroll
+      for (int c = 0; c < 2; ++c) { f0[c * plane + s] = v[c]; f1[c * plane + s] = v[c]; }
+    } else if (TH == TH_AH) {
       double mod = 1.0, ph = 0.0, A1 = 0.0, A2 = 0.0;
       for (int k = 0; k < ns; ++k) {
         const double X = x - sol[5 * k], Y = y - sol[5 * k + 1];
@@ -244,6 +270,8 @@ static cudaError_t obs_t(const LaunchCtx& c, int cur, cudaStream_t s) {
   a.h.i12dx2 = 1.0 / (12.0 * c.dx * c.dx);
   a.h.i12dy2 = 1.0 / (12.0 * c.dy * c.dy);
   a.h.i144dxdy = 1.0 / (144.0 * c.dx * c.dy);
+  a.hx = c.dx;
+  a.hy = c.dy;
   for (int i = 0; i < 10; ++i) a.k.c[i] = c.coup[i];
   a.area = c.dx * c.dy;
   a.st = c.st;
@@ -262,20 +290,23 @@ cudaError_t launch_observables(const LaunchCtx& c, int cur, cudaStream_t s) {
   const bool f = c.prec != PREC_F64;  // every FP32 mode stores its (hi) field in float
   if (c.theory == TH_AH) return f ? obs_t<TH_AH, float>(c, cur, s) : obs_t<TH_AH, double>(c, cur, s);
   if (c.theory == TH_CM) return f ? obs_t<TH_CM, float>(c, cur, s) : obs_t<TH_CM, double>(c, cur, s);
-  return f ? obs_t<TH_BS, float>(c, cur, s) : obs_t<TH_BS, double>(c, cur, s);
+  if (c.theory == TH_BS) return f ? obs_t<TH_BS, float>(c, cur, s) : obs_t<TH_BS, double>(c, cur, s);
+  return f ? obs_t<TH_BEC, float>(c, cur, s) : obs_t<TH_BEC, double>(c, cur, s);
 }
 
 template <int TH, typename R>
 static cudaError_t ansatz_t(const LaunchCtx& c, const double* sol, int n, cudaStream_t s) {
   const int blocks = (int)((c.plane + 255) / 256 < 4096 ? (c.plane + 255) / 256 : 4096);
   k_ansatz<TH, R><<<blocks, 256, 0, s>>>(static_cast<R*>(c.phi[0]), static_cast<R*>(c.phi[1]), c.nx, c.ny, c.plane,
-                                         c.dx, c.dy, sol, n);
+                                         c.dx, c.dy, sol, n, c.coup[0], c.coup[2]);
   return cudaGetLastError();
 }
 
 cudaError_t launch_ansatz(const LaunchCtx& c, const double* d_sol, int n, cudaStream_t s) {
   const bool f = c.prec != PREC_F64;
   if (c.theory == TH_AH) return f ? ansatz_t<TH_AH, float>(c, d_sol, n, s) : ansatz_t<TH_AH, double>(c, d_sol, n, s);
+  if (c.theory == TH_BEC)
+    return f ? ansatz_t<TH_BEC, float>(c, d_sol, n, s) : ansatz_t<TH_BEC, double>(c, d_sol, n, s);
   // both unit-vector theories take the compact skyrmion
   return f ? ansatz_t<TH_CM, float>(c, d_sol, n, s) : ansatz_t<TH_CM, double>(c, d_sol, n, s);
 }
@@ -295,7 +326,8 @@ int obs_grid(int theory, int prec, int ntiles) {
   const bool f = prec != PREC_F64;
   if (theory == TH_AH) occ = f ? obs_occ<TH_AH, float>() : obs_occ<TH_AH, double>();
   else if (theory == TH_CM) occ = f ? obs_occ<TH_CM, float>() : obs_occ<TH_CM, double>();
-  else occ = f ? obs_occ<TH_BS, float>() : obs_occ<TH_BS, double>();
+  else if (theory == TH_BS) occ = f ? obs_occ<TH_BS, float>() : obs_occ<TH_BS, double>();
+  else occ = f ? obs_occ<TH_BEC, float>() : obs_occ<TH_BEC, double>();
   const int g = nsm * occ;
   return ntiles < g ? ntiles : g;
 }

@@ -194,7 +194,7 @@ def smooth_field(theory: int, nx: int, ny: int, dx: float, dy: float, seed: int,
 def smooth_velocity(theory: int, nx: int, ny: int, dx: float, dy: float, seed: int, amplitude: float = 0.05):
     """A smooth random velocity field, zero on the width-2 halo (for trajectory tests)."""
     rng = SplitMix64(seed)
-    C = 4 if theory == ABELIAN_HIGGS else 3
+    C = {ABELIAN_HIGGS: 4, BEC: 2}.get(theory, 3)
     x = (np.arange(nx) - 0.5 * (nx - 1)) * dx
     y = (np.arange(ny) - 0.5 * (ny - 1)) * dy
     X, Y = np.meshgrid(x, y)

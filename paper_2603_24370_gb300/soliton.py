@@ -33,6 +33,7 @@ SS_FP32_PLAIN = 3  # one FP32 plane per component
 SS_ABELIAN_HIGGS = 1
 SS_CHIRAL_MAGNET = 2
 SS_BABY_SKYRME = 3
+SS_BEC = 4
 SS_METHOD_ANF = 0       # arrested Newton flow (default)
 SS_METHOD_GRADIENT = 1  # gradient descent phi <- phi - dtau G
 
@@ -74,7 +75,7 @@ class ss_batch_item(ctypes.Structure):
 class ss_obs(ctypes.Structure):
     _fields_ = [("energy", ctypes.c_double), ("charge", ctypes.c_double), ("flux", ctypes.c_double),
                 ("grad_max", ctypes.c_double), ("grad_max_raw", ctypes.c_double), ("norm_dev", ctypes.c_double),
-                ("steps", ctypes.c_longlong)]
+                ("steps", ctypes.c_longlong), ("atoms", ctypes.c_double), ("angular_momentum", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -398,7 +399,7 @@ class Solver:
                  stream=None):
         self.theory, self.nx, self.ny, self.dx, self.dy = theory, nx, ny, dx, dy
         self.precision = precision
-        self.C = 4 if theory == SS_ABELIAN_HIGGS else 3
+        self.C = {SS_ABELIAN_HIGGS: 4, SS_BEC: 2}.get(theory, 3)
         self.dtype = np.float64 if precision == SS_FP64 else np.float32
         self.ctx = None
         self.ctx = ss_create_grid(nx, ny, dx, dy, precision, stream)
