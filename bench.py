@@ -31,6 +31,11 @@ potential) through the same kernels: flow throughput on 2048^2 with 100 skyrmion
 (compensated FP32), and time to dx dy max|G| < 1e-6 of a 256^2 box with 4 skyrmions
 on the GPU (FP64, compensated FP32) against the FP64 oracle on the host cores.
 
+--workload bec: the rotating trapped BEC (Table 1; grand canonical, g = 1): flow
+throughput on 2048^2 (mu = 40, Omega = 0.9, box 24 x 24) in compensated FP32, and
+the vortex-lattice relaxation of the tests (96^2, mu = 10, Omega = 0.85, to
+dx dy max|G| < 1e-4) on the GPU against the FP64 oracle on the host cores.
+
 --workload ah-batch: time per solve to dx dy max|G| < 1e-6 on the batched Abelian
 Higgs set (256 problems, sides 64..512, dx = 0.1, lambda ~ U[0.5, 2], N in 1..4):
 one bench step = the whole set relaxed in one batch (compensated FP32), against
@@ -678,6 +683,76 @@ def run_baby_skyrme(args) -> int:
     return 0
 
 
+def run_bec(args) -> int:
+    """Rotating BEC: flow throughput and vortex-lattice time to solution."""
+    rank, local_rank, world = D.env_rank()
+    if rank != 0:
+        return 0
+    D.pin_visible_device(local_rank, 1)
+    import math
+    import numpy as np
+    import torch
+    import oracle as O
+    from paper_2603_24370_gb300 import build as B
+    from paper_2603_24370_gb300 import soliton as S
+    B.build()
+    O.build()
+    S.load_library()
+    peaks, src = measured_peaks()
+    n, L = 2048, 24.0
+    dx = L / (n - 1)
+    prm = (1.0, 0.9, 40.0)
+    ring = [[3.0 * math.cos(a), 3.0 * math.sin(a), 1, 0.3, 0.0] for a in np.linspace(0, 2 * math.pi, 9)[:-1]]
+    with S.Solver(S.SS_BEC, prm, n, n, dx, dx, S.SS_FP32) as sv:
+        sv.init_ansatz(ring)
+        tuned = sv.autotune(4)
+        for _ in range(args.warmup):
+            sv.step(INNER)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            sv.step(INNER)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        ms = S.ss_profile_stages(sv.ctx, 8)
+        o = sv.observables()
+    bytes2 = {1: 4 * 7 * 2, 2: 4 * 8 * 2}  # compensated FP32, C = 2
+    thr = {"site_updates_per_s": interior(n) * INNER * args.steps / sec, "pass_ms": ms, "autotuned": tuned,
+           "hbm_frac_of_measured": [bytes2[k + 1] * interior(n) / (ms[k] * 1e-3) / 1e9 / peaks["hbm_gbs"]
+                                    for k in range(2)],
+           "atoms": o["atoms"], "angular_momentum_per_atom": o["angular_momentum"] / o["atoms"]}
+    n2, dx2 = 96, 0.15
+    prm2 = (1.0, 0.85, 10.0)
+    vort = [[1.2 * math.cos(a), 1.2 * math.sin(a), 1, 0.4, 0.0] for a in np.linspace(0, 2 * math.pi, 6)[:-1]]
+    gpu = {}
+    for name, prec in (("fp64", S.SS_FP64), ("fp32c", S.SS_FP32)):
+        with S.Solver(S.SS_BEC, prm2, n2, n2, dx2, dx2, prec) as sv:
+            sv.init_ansatz(vort)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = sv.minimise(1e-4, 30000)
+            torch.cuda.synchronize()
+            o = sv.observables()
+            gpu[name] = {"seconds": time.perf_counter() - t0, "steps": r["steps"], "converged": bool(r["converged"]),
+                         "energy": o["energy"], "atoms": o["atoms"],
+                         "angular_momentum_per_atom": o["angular_momentum"] / o["atoms"]}
+    f = O.ansatz_bec(prm2, vort, n2, n2, dx2, dx2)
+    t0 = time.perf_counter()
+    ref = O.minimise(4, prm2, f, dx2, dx2, 1e-4, 30000)
+    osec = time.perf_counter() - t0
+    line = {"metric": "BEC: site-updates/s at 2048^2; time to dx dy max|G| < 1e-4 of a vortex lattice at 96^2",
+            "unit": "s", "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": "rotating BEC, grand canonical, g=1; throughput 2048^2 box 24, mu=40, Omega=0.9, "
+                                   "8-vortex ring ansatz, compensated FP32; lattice 96^2 dx=0.15, mu=10, "
+                                   "Omega=0.85, 5-vortex ring ansatz", "flow_steps_per_bench_step": INNER},
+            "throughput": thr,
+            "time_to_solution": {"gpu": gpu, "oracle": {"seconds": osec, "steps": ref["steps"],
+                                                         "energy": ref["energy"], "cores": O.num_threads(),
+                                                         "timed": "in full"}}}
+    print(json.dumps(line))
+    return 0
+
+
 def main() -> int:
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -686,7 +761,7 @@ def main() -> int:
     ap.add_argument("--impl", choices=("native", "reference"), default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grid", type=int, default=N, help="grid side (default: the 4096 workload; smaller for ncu)")
-    ap.add_argument("--workload", choices=("cm4096", "ah-batch", "configs", "methods", "baby-skyrme"),
+    ap.add_argument("--workload", choices=("cm4096", "ah-batch", "configs", "methods", "baby-skyrme", "bec"),
                     default="cm4096")
     ap.add_argument("--tile-shape", choices=("auto", "0", "1"), default="auto",
                     help="flow tile shape: autotuned (default) or fixed (for profiling one shape)")
@@ -707,6 +782,8 @@ def main() -> int:
         return run_methods(args)
     if args.workload == "baby-skyrme":
         return run_baby_skyrme(args)
+    if args.workload == "bec":
+        return run_bec(args)
     return run_native(args)
 
 
