@@ -8,8 +8,8 @@ Every function follows the paper step by step (equation numbers in order of
 appearance, see ``soliton_oracle.cpp``):
 
 * ``derivatives``          -- Eq. 1, Eq. 2 and the composed mixed derivative (Sec. 3.1)
-* ``energy`` / ``energy_density`` -- E_h of Table 1 (Abelian Higgs, Baby Skyrme) and Eq. 5
-  (chiral magnet)
+* ``energy`` / ``energy_density`` -- E_h of Table 1 (Abelian Higgs, Baby Skyrme, BEC, s+id)
+  and Eq. 5 (chiral magnet)
 * ``force``                -- Euler-Lagrange residual G driving Eq. 3
 * ``energy_grad_exact``    -- exact dE_h/dphi, only for pinning ``force``
 * ``anf_step`` / ``minimise`` -- arrested Newton flow, RK4 + Eq. 4 (Sec. 3.2)
@@ -34,6 +34,7 @@ ABELIAN_HIGGS = 1
 CHIRAL_MAGNET = 2
 BABY_SKYRME = 3
 BEC = 4
+SID = 5
 HARMONIC_TEST = 99
 
 _HERE = os.path.dirname(os.path.abspath(__file__))

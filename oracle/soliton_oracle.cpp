@@ -39,6 +39,10 @@
 //     in the grand-canonical form at chemical potential mu: the functional minimised is
 //     E - mu N, which fixes the atom number N at the minimum; Re(psi* L_z psi) is the
 //     rotation density (its imaginary part is a total derivative).
+//   * s+id superconductor (Table 1): gradient tensor gamma^{ss}_{jk} = gamma^{dd}_{jk} =
+//     delta_jk and gamma^{sd}_{jk} = gamma^{ds}_{jk} = nu diag(1, -1)_{jk} (the
+//     d_{x^2-y^2} mixed gradient), unit charge D = d - i A, components
+//     (Re, Im Delta_s, Re, Im Delta_d, A_1, A_2). params = {a1, a2, b1, b2, b3, b4, nu}.
 //   * Arrest compares potential energies with a strict '>' (Eq. 4).
 //   * Convergence measure: max over I and components of |dx dy G|.
 #include <cmath>
@@ -53,7 +57,8 @@ namespace {
 
 const double PI = 3.14159265358979323846;
 
-enum { TH_ABELIAN_HIGGS = 1, TH_CHIRAL_MAGNET = 2, TH_BABY_SKYRME = 3, TH_BEC = 4, TH_HARMONIC_TEST = 99 };
+enum { TH_ABELIAN_HIGGS = 1, TH_CHIRAL_MAGNET = 2, TH_BABY_SKYRME = 3, TH_BEC = 4, TH_SID = 5,
+       TH_HARMONIC_TEST = 99 };
 
 // Theories whose field is a unit 3-vector (normalised after every update).
 bool unit_vector(int theory) { return theory == TH_CHIRAL_MAGNET || theory == TH_BABY_SKYRME; }
@@ -71,6 +76,7 @@ int ncomp(int theory) {
     case TH_CHIRAL_MAGNET: return 3;   // n_1, n_2, n_3 (Eq. 5)
     case TH_BABY_SKYRME: return 3;     // m_1, m_2, m_3 (Table 1)
     case TH_BEC: return 2;             // Re psi, Im psi (Table 1)
+    case TH_SID: return 6;             // Delta_s, Delta_d (Re, Im), A_1, A_2 (Table 1)
     case TH_HARMONIC_TEST: return 1;   // scalar test field
     default: return 0;
   }
@@ -119,7 +125,7 @@ double d12(const double* p, const Grid& g, int i, int j) {
 
 // All derivatives of every component at one interior site, and its coordinates.
 struct Site {
-  double v[4], fx[4], fy[4], fxx[4], fyy[4], fxy[4];
+  double v[6], fx[6], fy[6], fxx[6], fyy[6], fxy[6];
   double x, y;
 };
 
@@ -220,6 +226,49 @@ double density_bec(const double* prm, const Site& s) {
   return kin + 0.5 * r2 * n + 0.5 * g * n * n - mu * n - Om * (u * Dv - v * Du);
 }
 
+// s+id two-band Ginzburg-Landau model (Table 1):
+//   e = 1/2 gamma^{ab}_{jk} (D_j Delta_a)* D_k Delta_b + 1/2 B^2 + a1 |Ds|^2 + a2 |Dd|^2
+//       + b1 |Ds|^4 + b2 |Dd|^4 + b3 |Ds|^2 |Dd|^2 + b4 (Ds^2 conj(Dd)^2 + c.c.),
+// with Ds = Delta_s, Dd = Delta_d. In real components, for band a = (u_a + i w_a):
+//   X_aj = Re D_j Delta_a = d_j u_a + A_j w_a,  Y_aj = Im D_j Delta_a = d_j w_a - A_j u_a,
+// the gradient energy is 1/2 sum_{a,j} (X_aj^2 + Y_aj^2) + nu sum_j eta_j (X_sj X_dj + Y_sj Y_dj),
+// eta = (1, -1); with p + i q = Ds conj(Dd), Ds^2 conj(Dd)^2 + c.c. = 2 (p^2 - q^2).
+struct SidTerms {
+  double X[2][2], Y[2][2];  // [band][direction]
+  double S, Dd, p, q, B;
+};
+SidTerms sid_terms(const Site& s) {
+  SidTerms t;
+  const double A[2] = {s.v[4], s.v[5]};
+  for (int a = 0; a < 2; ++a) {
+    const double u = s.v[2 * a], w = s.v[2 * a + 1];
+    const double du[2] = {s.fx[2 * a], s.fy[2 * a]}, dw[2] = {s.fx[2 * a + 1], s.fy[2 * a + 1]};
+    for (int j = 0; j < 2; ++j) {
+      t.X[a][j] = du[j] + A[j] * w;
+      t.Y[a][j] = dw[j] - A[j] * u;
+    }
+  }
+  t.S = s.v[0] * s.v[0] + s.v[1] * s.v[1];
+  t.Dd = s.v[2] * s.v[2] + s.v[3] * s.v[3];
+  t.p = s.v[0] * s.v[2] + s.v[1] * s.v[3];
+  t.q = s.v[1] * s.v[2] - s.v[0] * s.v[3];
+  t.B = s.fx[5] - s.fy[4];
+  return t;
+}
+double density_sid(const double* prm, const Site& s) {
+  const double a1 = prm[0], a2 = prm[1], b1 = prm[2], b2 = prm[3], b3 = prm[4], b4 = prm[5], nu = prm[6];
+  const SidTerms t = sid_terms(s);
+  double grad = 0.0;
+  for (int a = 0; a < 2; ++a)
+    for (int j = 0; j < 2; ++j) grad += 0.5 * (t.X[a][j] * t.X[a][j] + t.Y[a][j] * t.Y[a][j]);
+  const double eta[2] = {1.0, -1.0};
+  double mix = 0.0;
+  for (int j = 0; j < 2; ++j) mix += eta[j] * (t.X[0][j] * t.X[1][j] + t.Y[0][j] * t.Y[1][j]);
+  const double V = a1 * t.S + a2 * t.Dd + b1 * t.S * t.S + b2 * t.Dd * t.Dd + b3 * t.S * t.Dd +
+                   2.0 * b4 * (t.p * t.p - t.q * t.q);
+  return grad + nu * mix + 0.5 * t.B * t.B + V;
+}
+
 // Harmonic test theory (oracle only, pins the time integrator): e = k/2 phi^2.
 double density_harm(const double* prm, const Site& s) { return 0.5 * prm[0] * s.v[0] * s.v[0]; }
 
@@ -229,6 +278,7 @@ double density(int theory, const double* prm, const Site& s) {
     case TH_CHIRAL_MAGNET: return density_cm(prm, s);
     case TH_BABY_SKYRME: return density_bs(prm, s);
     case TH_BEC: return density_bec(prm, s);
+    case TH_SID: return density_sid(prm, s);
     default: return density_harm(prm, s);
   }
 }
@@ -306,20 +356,66 @@ void force_bec(const double* prm, const Site& s, double G[2]) {
   G[1] = -(s.fxx[1] + s.fyy[1]) + w * v + 2.0 * Om * Du;
 }
 
+// s+id: with P_aj = X_aj + nu eta_j X_bj, Q_aj = Y_aj + nu eta_j Y_bj (b the other band),
+// the conjugates of d_j u_a and d_j w_a, the Euler-Lagrange expressions are
+//   G_{u_a} = -sum_j [A_j Q_aj + d_j P_aj] + dV/du_a,  G_{w_a} = sum_j [A_j P_aj - d_j Q_aj] + dV/dw_a,
+//   G_{A_1} = d_2 B + sum_a (P_a1 w_a - Q_a1 u_a),  G_{A_2} = -d_1 B + sum_a (P_a2 w_a - Q_a2 u_a),
+// where d_j X_aj = d_j^2 u_a + (d_j A_j) w_a + A_j d_j w_a, d_j Y_aj = d_j^2 w_a - (d_j A_j) u_a - A_j d_j u_a.
+void force_sid(const double* prm, const Site& s, double G[6]) {
+  const double a1 = prm[0], a2 = prm[1], b1 = prm[2], b2 = prm[3], b3 = prm[4], b4 = prm[5], nu = prm[6];
+  const SidTerms t = sid_terms(s);
+  const double A[2] = {s.v[4], s.v[5]}, dA[2] = {s.fx[4], s.fy[5]};
+  const double eta[2] = {1.0, -1.0};
+  double dX[2][2], dY[2][2];  // d_j X_aj, d_j Y_aj
+  for (int a = 0; a < 2; ++a) {
+    const double u = s.v[2 * a], w = s.v[2 * a + 1];
+    const double du[2] = {s.fx[2 * a], s.fy[2 * a]}, dw[2] = {s.fx[2 * a + 1], s.fy[2 * a + 1]};
+    const double uu[2] = {s.fxx[2 * a], s.fyy[2 * a]}, ww[2] = {s.fxx[2 * a + 1], s.fyy[2 * a + 1]};
+    for (int j = 0; j < 2; ++j) {
+      dX[a][j] = uu[j] + dA[j] * w + A[j] * dw[j];
+      dY[a][j] = ww[j] - dA[j] * u - A[j] * du[j];
+    }
+  }
+  // potential derivatives
+  const double s1 = s.v[0], s2 = s.v[1], d1 = s.v[2], d2 = s.v[3];
+  double dV[4];
+  dV[0] = 2 * a1 * s1 + 4 * b1 * t.S * s1 + 2 * b3 * t.Dd * s1 + 4 * b4 * (t.p * d1 + t.q * d2);
+  dV[1] = 2 * a1 * s2 + 4 * b1 * t.S * s2 + 2 * b3 * t.Dd * s2 + 4 * b4 * (t.p * d2 - t.q * d1);
+  dV[2] = 2 * a2 * d1 + 4 * b2 * t.Dd * d1 + 2 * b3 * t.S * d1 + 4 * b4 * (t.p * s1 - t.q * s2);
+  dV[3] = 2 * a2 * d2 + 4 * b2 * t.Dd * d2 + 2 * b3 * t.S * d2 + 4 * b4 * (t.p * s2 + t.q * s1);
+  G[4] = s.fxy[5] - s.fyy[4];   //  d_2 B
+  G[5] = s.fxy[4] - s.fxx[5];   // -d_1 B
+  for (int a = 0; a < 2; ++a) {
+    const int b = 1 - a;
+    const double u = s.v[2 * a], w = s.v[2 * a + 1];
+    double gu = dV[2 * a], gw = dV[2 * a + 1];
+    for (int j = 0; j < 2; ++j) {
+      const double P = t.X[a][j] + nu * eta[j] * t.X[b][j], Q = t.Y[a][j] + nu * eta[j] * t.Y[b][j];
+      const double dP = dX[a][j] + nu * eta[j] * dX[b][j], dQ = dY[a][j] + nu * eta[j] * dY[b][j];
+      gu += -A[j] * Q - dP;
+      gw += A[j] * P - dQ;
+      G[4 + j] += P * w - Q * u;
+    }
+    G[2 * a] = gu;
+    G[2 * a + 1] = gw;
+  }
+}
+
 void force_site(int theory, const double* prm, const Site& s, double* G) {
   switch (theory) {
     case TH_ABELIAN_HIGGS: force_ah(prm, s, G); break;
     case TH_CHIRAL_MAGNET: force_cm(prm, s, G); break;
     case TH_BABY_SKYRME: force_bs(prm, s, G); break;
     case TH_BEC: force_bec(prm, s, G); break;
+    case TH_SID: force_sid(prm, s, G); break;
     default: G[0] = prm[0] * s.v[0]; break;
   }
 }
 
 // ---------------------------------------------------------------- partial derivatives of e
 // d e / d phi_c and d e / d(d_i phi_c), used only by the exact gradient of E_h.
-void partials(int theory, const double* prm, const Site& s, double dv[4], double dgx[4], double dgy[4]) {
-  for (int c = 0; c < 4; ++c) dv[c] = dgx[c] = dgy[c] = 0.0;
+void partials(int theory, const double* prm, const Site& s, double dv[6], double dgx[6], double dgy[6]) {
+  for (int c = 0; c < 6; ++c) dv[c] = dgx[c] = dgy[c] = 0.0;
   if (theory == TH_ABELIAN_HIGGS) {
     const double lam = prm[0], u = prm[1];
     const double p1 = s.v[0], p2 = s.v[1], A1 = s.v[2], A2 = s.v[3];
@@ -363,6 +459,31 @@ void partials(int theory, const double* prm, const Site& s, double dv[4], double
     }
     dv[0] = nu2 * s.v[0];
     dv[2] = -mu2;
+  } else if (theory == TH_SID) {
+    const double a1 = prm[0], a2 = prm[1], b1 = prm[2], b2 = prm[3], b3 = prm[4], b4 = prm[5], nu = prm[6];
+    const SidTerms t = sid_terms(s);
+    const double A[2] = {s.v[4], s.v[5]};
+    const double eta[2] = {1.0, -1.0};
+    double* dg[2] = {dgx, dgy};
+    for (int a = 0; a < 2; ++a) {
+      const int b = 1 - a;
+      const double u = s.v[2 * a], w = s.v[2 * a + 1];
+      for (int j = 0; j < 2; ++j) {
+        const double P = t.X[a][j] + nu * eta[j] * t.X[b][j], Q = t.Y[a][j] + nu * eta[j] * t.Y[b][j];
+        dg[j][2 * a] = P;       // d e / d(d_j u_a)
+        dg[j][2 * a + 1] = Q;   // d e / d(d_j w_a)
+        dv[2 * a] += -A[j] * Q;
+        dv[2 * a + 1] += A[j] * P;
+        dv[4 + j] += P * w - Q * u;
+      }
+    }
+    dgx[5] = t.B;
+    dgy[4] = -t.B;
+    const double s1 = s.v[0], s2 = s.v[1], d1 = s.v[2], d2 = s.v[3];
+    dv[0] += 2 * a1 * s1 + 4 * b1 * t.S * s1 + 2 * b3 * t.Dd * s1 + 4 * b4 * (t.p * d1 + t.q * d2);
+    dv[1] += 2 * a1 * s2 + 4 * b1 * t.S * s2 + 2 * b3 * t.Dd * s2 + 4 * b4 * (t.p * d2 - t.q * d1);
+    dv[2] += 2 * a2 * d1 + 4 * b2 * t.Dd * d1 + 2 * b3 * t.S * d1 + 4 * b4 * (t.p * s1 - t.q * s2);
+    dv[3] += 2 * a2 * d2 + 4 * b2 * t.Dd * d2 + 2 * b3 * t.S * d2 + 4 * b4 * (t.p * s2 + t.q * s1);
   } else if (theory == TH_BEC) {
     const double g = prm[0], Om = prm[1], mu = prm[2];
     const double u = s.v[0], v = s.v[1];
@@ -399,7 +520,7 @@ void force(int theory, const double* prm, const double* f, const Grid& g, double
 #pragma omp parallel for schedule(static)
   for (int j = 2; j <= g.ny - 3; ++j)
     for (int i = 2; i <= g.nx - 3; ++i) {
-      double Gs[4];
+      double Gs[6];
       force_site(theory, prm, gather(f, C, g, i, j, true), Gs);
       for (int c = 0; c < C; ++c) G[c * g.plane() + (size_t)j * g.nx + i] = Gs[c];
     }
@@ -498,7 +619,7 @@ void or_energy_grad_exact(int theory, const double* prm, const double* f, int nx
   const double A = dx * dy;
   for (int j = 2; j <= ny - 3; ++j)
     for (int i = 2; i <= nx - 3; ++i) {
-      double dv[4], dgx[4], dgy[4];
+      double dv[6], dgx[6], dgy[6];
       partials(theory, prm, gather(f, C, g, i, j, false), dv, dgx, dgy);
       for (int c = 0; c < C; ++c) {
         double* gc = grad + c * P;

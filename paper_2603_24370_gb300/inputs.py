@@ -42,6 +42,7 @@ ABELIAN_HIGGS = 1
 CHIRAL_MAGNET = 2
 BABY_SKYRME = 3
 BEC = 4
+SID = 5
 
 # Couplings of the workloads. Abelian Higgs: (lambda, u). Chiral magnet:
 # (J, D, K, h, dmi_type) with interfacial DMI (type 0).
@@ -162,7 +163,8 @@ def smooth_field(theory: int, nx: int, ny: int, dx: float, dy: float, seed: int,
     Baby Skyrme: a unit field from smooth angles, n = (sin T cos P, sin T sin P,
     cos T) with T, P sums of Gaussian bumps (unit length by construction, no
     normalisation). BEC: psi = env (1 + s_1) + i env s_2 with a Gaussian envelope
-    env that is small at the edge of the box.
+    env that is small at the edge of the box. s+id: Delta_s = (1 + s_1) + i s_2,
+    Delta_d = (0.5 + s_3) + i (0.5 + s_4), A = (s_5, s_6).
     """
     rng = SplitMix64(seed)
     x = (np.arange(nx) - 0.5 * (nx - 1)) * dx
@@ -184,6 +186,8 @@ def smooth_field(theory: int, nx: int, ny: int, dx: float, dy: float, seed: int,
     if theory == BEC:
         env = np.exp(-(X * X + Y * Y) / (0.25 * min(Lx, Ly) ** 2))
         return np.stack([env * (1.0 + bumpsum()), env * bumpsum()])
+    if theory == SID:
+        return np.stack([1.0 + bumpsum(), bumpsum(), 0.5 + bumpsum(), 0.5 + bumpsum(), bumpsum(), bumpsum()])
     if theory in (CHIRAL_MAGNET, BABY_SKYRME):
         T = 0.6 + 3.0 * bumpsum()
         P = 5.0 * bumpsum()
@@ -194,7 +198,7 @@ def smooth_field(theory: int, nx: int, ny: int, dx: float, dy: float, seed: int,
 def smooth_velocity(theory: int, nx: int, ny: int, dx: float, dy: float, seed: int, amplitude: float = 0.05):
     """A smooth random velocity field, zero on the width-2 halo (for trajectory tests)."""
     rng = SplitMix64(seed)
-    C = {ABELIAN_HIGGS: 4, BEC: 2}.get(theory, 3)
+    C = {ABELIAN_HIGGS: 4, BEC: 2, SID: 6}.get(theory, 3)
     x = (np.arange(nx) - 0.5 * (nx - 1)) * dx
     y = (np.arange(ny) - 0.5 * (ny - 1)) * dy
     X, Y = np.meshgrid(x, y)

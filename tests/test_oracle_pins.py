@@ -22,6 +22,8 @@ BS = O.BABY_SKYRME
 BS_PRM = (1.0, 0.7, 0.3)  # kappa, mu, nu
 BEC = O.BEC
 BEC_PRM = (1.3, 0.6, 2.0)  # g, Omega, mu
+SID = O.SID
+SID_PRM = (-1.0, -0.6, 0.5, 0.4, 0.3, 0.15, 0.35)  # a1, a2, b1, b2, b3, b4, nu
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_constants.json")
 AH_PRM = (1.0, 1.0)
 CM_PRM = (1.0, 1.0, 0.1, 0.6, 0.0)
@@ -540,12 +542,102 @@ def test_bec_ground_state_is_the_radial_solution_and_near_thomas_fermi():
     assert 12.0 < errs[0] / errs[1] < 20.0
 
 
+# ---------------------------------------------------------------- s+id superconductor (Table 1)
+@pytest.mark.parametrize("nu", [0.0, 0.35])
+def test_sid_reduces_to_abelian_higgs_without_the_d_band(nu):
+    """Delta_d = 0: the s+id functional is the Abelian Higgs one with
+    lambda/8 (u^2 - |psi|^2)^2 = a1 |psi|^2 + b1 |psi|^4 + lambda u^4 / 8 (a1 = -lambda u^2 / 4,
+    b1 = lambda / 8), so E_h differs by area(I) lambda u^4 / 8 and the forces on Delta_s and
+    A are the Abelian Higgs ones; the d band feels a force only through the mixed
+    gradient (nu != 0)."""
+    nx, ny, dx, dy = 30, 26, 0.3, 0.25
+    lam, u = 1.4, 1.1
+    ah = I.smooth_field(AH, nx, ny, dx, dy, seed=31)
+    f = np.zeros((6, ny, nx))
+    f[0], f[1], f[4], f[5] = ah[0], ah[1], ah[2], ah[3]
+    prm = (-lam * u * u / 4, -0.6, lam / 8, 0.4, 0.3, 0.15, nu)
+    area = (nx - 4) * (ny - 4) * dx * dy
+    assert O.energy(SID, prm, f, dx, dy) == pytest.approx(O.energy(AH, (lam, u), ah, dx, dy) - area * lam * u ** 4 / 8,
+                                                         rel=1e-13)
+    G, Ga = O.force(SID, prm, f, dx, dy), O.force(AH, (lam, u), ah, dx, dy)
+    sc = np.abs(Ga).max()
+    for c, ca in ((0, 0), (1, 1), (4, 2), (5, 3)):
+        np.testing.assert_allclose(G[c], Ga[ca], rtol=0, atol=1e-12 * sc)
+    if nu == 0.0:
+        assert not G[2].any() and not G[3].any()
+    else:
+        assert np.abs(G[2:4]).max() > 1e-3 * sc
+
+
+def test_sid_d_wave_rotation_and_band_symmetries():
+    """The mixed gradient nu (|D_1 . |^2-type with eta = (1, -1)) has d_{x^2-y^2} symmetry: a
+    90-degree rotation of space and A together with Delta_d -> -Delta_d leaves E_h exactly
+    invariant (without the sign flip it does not, for nu != 0). Exchanging the bands with
+    their couplings (a1 <-> a2, b1 <-> b2) is exact too."""
+    n, dx = 26, 0.3
+    f = I.smooth_field(SID, n, n, dx, dx, seed=41)
+    r = _rot90_scalar
+    E0 = O.energy(SID, SID_PRM, f, dx, dx)
+    g = np.stack([r(f[0]), r(f[1]), -r(f[2]), -r(f[3]), -r(f[5]), r(f[4])])
+    assert O.energy(SID, SID_PRM, g, dx, dx) == pytest.approx(E0, rel=1e-13)
+    g2 = g.copy()
+    g2[2:4] *= -1
+    assert abs(O.energy(SID, SID_PRM, g2, dx, dx) - E0) > 1e-4 * abs(E0)
+    Gf, Gg = O.force(SID, SID_PRM, f, dx, dx), O.force(SID, SID_PRM, g, dx, dx)
+    Grot = np.stack([r(Gf[0]), r(Gf[1]), -r(Gf[2]), -r(Gf[3]), -r(Gf[5]), r(Gf[4])])
+    np.testing.assert_allclose(Gg, Grot, rtol=0, atol=1e-11 * np.abs(Gf).max())
+    a1, a2, b1, b2, b3, b4, nu = SID_PRM
+    sw = np.stack([f[2], f[3], f[0], f[1], f[4], f[5]])
+    assert O.energy(SID, (a2, a1, b2, b1, b3, b4, nu), sw, dx, dx) == pytest.approx(E0, rel=1e-13)
+
+
+def test_sid_gauge_invariance_fourth_order():
+    """Delta_a -> e^{i chi} Delta_a, A -> A + grad chi: E_h changes at O(h^4)."""
+    errs = []
+    for n in (41, 81):
+        L = 8.0
+        dx = L / (n - 1)
+        dy = 0.9 * dx
+        X, Y = grid(n, n, dx, dy)
+        f = I.smooth_field(SID, n, n, dx, dy, seed=6)
+        chi = 0.7 * np.sin(0.5 * X + 0.2) * np.cos(0.6 * Y) + 0.1 * X * Y
+        cx = 0.35 * np.cos(0.5 * X + 0.2) * np.cos(0.6 * Y) + 0.1 * Y
+        cy = -0.42 * np.sin(0.5 * X + 0.2) * np.sin(0.6 * Y) + 0.1 * X
+        c, s_ = np.cos(chi), np.sin(chi)
+        g = np.stack([c * f[0] - s_ * f[1], s_ * f[0] + c * f[1], c * f[2] - s_ * f[3], s_ * f[2] + c * f[3],
+                      f[4] + cx, f[5] + cy])
+        errs.append(abs(O.energy(SID, SID_PRM, g, dx, dy) - O.energy(SID, SID_PRM, f, dx, dy)))
+    assert errs[0] / errs[1] > 12.0 and errs[1] < 2e-4
+
+
+def test_sid_uniform_ground_state_closed_form():
+    """Uniform fields: only the potential survives. For b4 > 0 the relative phase pi/2
+    (s + i d) minimises it, and a1 + 2 b1 S + (b3 - 2 b4) D = a2 + 2 b2 D + (b3 - 2 b4) S = 0
+    fixes S = |Delta_s|^2, D = |Delta_d|^2 (here S = 1, D = 0.75): the force vanishes there
+    and E_h is area(I) times the potential's minimum; a relative phase 0 raises it."""
+    a1, a2, b1, b2, b3, b4, nu = SID_PRM
+    b3e = b3 - 2 * b4
+    S, D = np.linalg.solve([[2 * b1, b3e], [b3e, 2 * b2]], [-a1, -a2])
+    assert S == pytest.approx(1.0) and D == pytest.approx(0.75)
+    nx, ny, dx, dy = 14, 12, 0.3, 0.2
+    f = np.zeros((6, ny, nx))
+    f[0] = math.sqrt(S)
+    f[3] = math.sqrt(D)  # Delta_d = i sqrt(D): relative phase pi/2
+    area = (nx - 4) * (ny - 4) * dx * dy
+    Vmin = a1 * S + a2 * D + b1 * S * S + b2 * D * D + b3e * S * D
+    assert O.energy(SID, SID_PRM, f, dx, dy) == pytest.approx(area * Vmin, rel=1e-13)
+    assert np.abs(O.force(SID, SID_PRM, f, dx, dy)).max() < 1e-14
+    g = f.copy()
+    g[2], g[3] = math.sqrt(D), 0.0  # relative phase 0
+    assert O.energy(SID, SID_PRM, g, dx, dy) > O.energy(SID, SID_PRM, f, dx, dy) + area * 4 * b4 * S * D * 0.99
+
+
 # ---------------------------------------------------------------- force (Eq. 3's right-hand side)
 def _prm(theory):
-    return {AH: AH_PRM, CM: (1.0, 0.8, 0.15, 0.5, 0.0), BS: BS_PRM, BEC: BEC_PRM}[theory]
+    return {AH: AH_PRM, CM: (1.0, 0.8, 0.15, 0.5, 0.0), BS: BS_PRM, BEC: BEC_PRM, SID: SID_PRM}[theory]
 
 
-@pytest.mark.parametrize("theory", [AH, CM, BS, BEC])
+@pytest.mark.parametrize("theory", [AH, CM, BS, BEC, SID])
 def test_exact_gradient_matches_brute_force(theory):
     nx, ny, dx, dy = 12, 11, 0.3, 0.25
     prm = _prm(theory)
@@ -561,7 +653,7 @@ def test_exact_gradient_matches_brute_force(theory):
     np.testing.assert_allclose(grad, fd, rtol=0, atol=1e-7 * np.abs(grad).max())
 
 
-@pytest.mark.parametrize("theory", [AH, CM, BS, BEC])
+@pytest.mark.parametrize("theory", [AH, CM, BS, BEC, SID])
 def test_force_is_energy_gradient_to_fourth_order(theory):
     """dx dy G and dE_h/dphi (tangent part for the unit-vector theories) are two O(h^4)
     discretisations of the same Euler-Lagrange expression: their gap shrinks ~16x per halving."""
