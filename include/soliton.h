@@ -76,6 +76,13 @@ extern "C" {
                            /*     - Omega Re(psi* L_z psi), L_z = -i (x d_y - y d_x),       */
                            /* (x, y) measured from the grid centre; the atom number N and  */
                            /* the angular momentum are observables (ss_obs)                 */
+#define SS_SID 5           /* s+id two-band superconductor (Table 1), params               */
+                           /* {a1, a2, b1, b2, b3, b4, nu}: Delta_s, Delta_d, A (6 planes:  */
+                           /* Re, Im Delta_s, Re, Im Delta_d, A_1, A_2), D = d - i A,       */
+                           /* gradient tensor identity per band and nu diag(1, -1) between  */
+                           /* them (d_{x^2-y^2}); V = a1|Ds|^2 + a2|Dd|^2 + b1|Ds|^4 +      */
+                           /* b2|Dd|^4 + b3|Ds|^2|Dd|^2 + b4 (Ds^2 conj(Dd)^2 + c.c.);      */
+                           /* needs |nu| < 1, b1, b2 > 0, 4 b1 b2 > (b3 - 2|b4|)^2          */
 
 /* ---- minimisers ---- */
 #define SS_METHOD_ANF 0      /* arrested Newton flow, RK4 + Eq. 4 (Sec. 3.2): the default */
@@ -95,6 +102,10 @@ typedef struct ss_ctx ss_ctx;
  *                 sin f sin(m theta + gamma), cos f), f = pi (1 - r/R) for r < R,
  *                 n = e_3 outside every disc; the first disc containing a site wins.
  *                 Its lattice charge is -m.
+ *  s+id: the Abelian Higgs vortex product (same windings and sizes) scaled by the
+ *       uniform minimum of the potential: Delta_s = sqrt(S) x it, Delta_d = sqrt(D)
+ *       e^{i phi} x it with the relative phase phi = pi/2 for b4 > 0 (else 0); A as for
+ *       the Abelian Higgs model. Charge: winding of Delta_s; flux as Abelian Higgs.
  *  BEC: the Thomas-Fermi amplitude sqrt(max(0, mu - r^2/2) / g) times a vortex factor
  *       tanh(r_k/size_k)^|charge_k| exp(i (charge_k theta_k + phase_k)) per entry (an
  *       entry of charge 0 and phase 0 gives the Thomas-Fermi profile alone). */
@@ -155,7 +166,8 @@ int ss_create_grid(ss_ctx** out, int nx, int ny, double dx, double dy, int preci
  * doubles: Abelian Higgs {lambda, u} (u defaults to 1 if n_params == 1); chiral
  * magnet {J, D, K, h, dmi_type} (dmi_type defaults to 0 if n_params == 4); Baby
  * Skyrme {kappa, mu, nu} (nu defaults to 0 if n_params == 2); BEC {g, Omega, mu}
- * with g > 0 (the BEC's charge observable is 0: see atoms, angular_momentum).
+ * with g > 0 (the BEC's charge observable is 0: see atoms, angular_momentum); s+id
+ * {a1, a2, b1, b2, b3, b4, nu} (see SS_SID for the constraints).
  * Allocates the device buffers; previous fields are discarded.
  * Errors: SS_ERR_ARG (unknown theory, bad n_params, J <= 0), SS_ERR_NOMEM, SS_ERR_CUDA. */
 int ss_set_theory(ss_ctx* ctx, int theory, const double* params, int n_params);

@@ -16,7 +16,7 @@ appearance, see ``soliton_oracle.cpp``):
 * ``gd_step`` / ``gd_minimise`` / ``gd_step_limit`` -- the first-order gradient
   descent Sec. 3.2 names as the slower alternative (explicit Euler, see the C++)
 * ``observables``          -- energy, topological charge, flux, residual, |n|-1
-* ``ansatz`` / ``ansatz_bec`` -- vortex / skyrmion initial data (Sec. 3.4; standard forms)
+* ``ansatz`` / ``ansatz_bec`` / ``ansatz_sid`` -- initial data (Sec. 3.4; standard forms)
 
 All functions are pinned by the ``-m "not gpu"`` tests in ``tests/test_oracle_pins.py``.
 """
@@ -100,6 +100,8 @@ def _load():
             lib.or_observables.restype = None
             lib.or_ansatz.argtypes = [i, _D, i, _D, i, i, d, d]
             lib.or_ansatz_bec.argtypes = [_D, _D, i, _D, i, i, d, d]
+            lib.or_ansatz_sid.argtypes = [_D, _D, i, _D, i, i, d, d, _D]
+            lib.or_ansatz_sid.restype = None
             lib.or_ansatz_bec.restype = None
             lib.or_ansatz.restype = None
             _lib = lib
@@ -235,6 +237,15 @@ def ansatz_bec(params, vortices, nx: int, ny: int, dx: float, dy: float) -> np.n
     f = np.zeros((2, ny, nx))
     _load().or_ansatz_bec(_p(_params(params)), _p(s), s.shape[0], _p(f), nx, ny, dx, dy)
     return f
+
+
+def ansatz_sid(params, vortices, nx: int, ny: int, dx: float, dy: float):
+    """s+id vortices on the uniform minimum; returns (field, (S, D, relative phase))."""
+    s = _f64(np.asarray(vortices, dtype=np.float64).reshape(-1, 5))
+    f = np.zeros((6, ny, nx))
+    m = np.zeros(3)
+    _load().or_ansatz_sid(_p(_params(params)), _p(s), s.shape[0], _p(f), nx, ny, dx, dy, _p(m))
+    return f, tuple(m)
 
 
 def ansatz(theory: int, solitons, nx: int, ny: int, dx: float, dy: float) -> np.ndarray:

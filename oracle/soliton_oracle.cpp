@@ -782,7 +782,7 @@ static double solid_angle(const double a[3], const double b[3], const double c[3
 //          plaquettes, two triangles each, oriented like n.(d_1 n x d_2 n), divided by
 //          4 pi; Abelian Higgs winding of arg psi around the boundary of I
 //          (counter-clockwise), divided by 2 pi.
-// out[2] = magnetic flux dx dy sum_I (d_1 A_2 - d_2 A_1) (Abelian Higgs), 0 otherwise
+// out[2] = magnetic flux dx dy sum_I (d_1 A_2 - d_2 A_1) (Abelian Higgs, s+id), 0 otherwise
 // out[3] = dx dy max_I |G|, out[4] = max_I |G|
 // out[5] = max over all sites of ||n| - 1| (chiral magnet, Baby Skyrme), 0 otherwise
 // out[6] = BEC atom number N = dx dy sum_I |psi|^2, out[7] = BEC angular momentum
@@ -827,8 +827,8 @@ void or_observables(int theory, const double* prm, const double* f, int nx, int 
     for (size_t k = 0; k < P; ++k)
       dev = std::fmax(dev, std::fabs(std::sqrt(f[k] * f[k] + f[P + k] * f[P + k] + f[2 * P + k] * f[2 * P + k]) - 1.0));
     out[5] = dev;
-  } else if (theory == TH_ABELIAN_HIGGS) {
-    // loop of boundary sites of I, counter-clockwise
+  } else if (theory == TH_ABELIAN_HIGGS || theory == TH_SID) {
+    // loop of boundary sites of I, counter-clockwise (s+id: the winding of Delta_s)
     std::vector<int> li, lj;
     for (int i = 2; i < nx - 3; ++i) { li.push_back(i); lj.push_back(2); }
     for (int j = 2; j < ny - 3; ++j) { li.push_back(nx - 3); lj.push_back(j); }
@@ -845,8 +845,8 @@ void or_observables(int theory, const double* prm, const double* f, int nx, int 
     }
     out[1] = w.value() / (2.0 * PI);
     Neumaier flux;
-    const double* A1 = f + 2 * P;
-    const double* A2 = f + 3 * P;
+    const double* A1 = f + (theory == TH_SID ? 4 : 2) * P;
+    const double* A2 = f + (theory == TH_SID ? 5 : 3) * P;
     for (int j = 2; j <= ny - 3; ++j)
       for (int i = 2; i <= nx - 3; ++i) flux.add(d1x(A2, g, i, j) - d1y(A1, g, i, j));
     out[2] = dx * dy * flux.value();
@@ -880,6 +880,53 @@ void or_ansatz_bec(const double* prm, const double* sol, int nsol, double* f, in
       const size_t k = (size_t)j * nx + i;
       f[k] = mod * std::cos(ph);
       f[P + k] = mod * std::sin(ph);
+    }
+}
+
+// s+id: the uniform minimum of the potential over S = |Delta_s|^2, D = |Delta_d|^2 >= 0 with
+// the relative phase phi that minimises b4 (Ds^2 conj(Dd)^2 + c.c.) = 2 b4 S D cos(2 phi)
+// (phi = pi/2 for b4 > 0, else 0), then Delta_s = sqrt(S) w, Delta_d = sqrt(D) e^{i phi} w,
+// with w = prod_k tanh(r_k/s_k)^{|n_k|} e^{i (n_k theta_k + chi_k)}, and A as for the
+// Abelian Higgs vortices. out_min (may be NULL) receives {S, D, phi}.
+void or_ansatz_sid(const double* prm, const double* sol, int nsol, double* f, int nx, int ny, double dx, double dy,
+                   double* out_min) {
+  const double a1 = prm[0], a2 = prm[1], b1 = prm[2], b2 = prm[3], b4 = prm[5];
+  const double phi = b4 > 0.0 ? 0.5 * PI : 0.0;
+  const double c = prm[4] + 2.0 * b4 * std::cos(2.0 * phi);  // effective S D coefficient
+  auto V = [&](double S, double D) { return a1 * S + a2 * D + b1 * S * S + b2 * D * D + c * S * D; };
+  double S = 0.0, D = 0.0, best = 0.0;
+  // candidates: the interior stationary point and the two one-band minima
+  const double det = 4.0 * b1 * b2 - c * c;
+  double cand[3][2] = {{det != 0.0 ? (c * a2 - 2.0 * b2 * a1) / det : -1.0, det != 0.0 ? (c * a1 - 2.0 * b1 * a2) / det : -1.0},
+                       {-a1 / (2.0 * b1), 0.0},
+                       {0.0, -a2 / (2.0 * b2)}};
+  for (auto& q : cand)
+    if (q[0] >= 0.0 && q[1] >= 0.0 && V(q[0], q[1]) < best) { S = q[0]; D = q[1]; best = V(S, D); }
+  if (out_min) { out_min[0] = S; out_min[1] = D; out_min[2] = phi; }
+  const size_t P = (size_t)nx * ny;
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      const double x = (i - 0.5 * (nx - 1)) * dx, y = (j - 0.5 * (ny - 1)) * dy;
+      double mod = 1.0, ph = 0.0, A1 = 0.0, A2 = 0.0;
+      for (int k = 0; k < nsol; ++k) {
+        const double X = x - sol[5 * k], Y = y - sol[5 * k + 1];
+        const double n = sol[5 * k + 2], sz = sol[5 * k + 3], chi = sol[5 * k + 4];
+        const double r2 = X * X + Y * Y;
+        const double t = std::tanh(std::sqrt(r2) / sz);
+        mod *= std::pow(t, std::fabs(n));
+        ph += n * std::atan2(Y, X) + chi;
+        if (r2 > 0.0) {
+          A1 += n * t * t * (-Y) / r2;
+          A2 += n * t * t * X / r2;
+        }
+      }
+      const size_t q = (size_t)j * nx + i;
+      f[q] = std::sqrt(S) * mod * std::cos(ph);
+      f[P + q] = std::sqrt(S) * mod * std::sin(ph);
+      f[2 * P + q] = std::sqrt(D) * mod * std::cos(ph + phi);
+      f[3 * P + q] = std::sqrt(D) * mod * std::sin(ph + phi);
+      f[4 * P + q] = A1;
+      f[5 * P + q] = A2;
     }
 }
 

@@ -82,6 +82,16 @@ int pack_couplings(int theory, const double* params, int n_params, double k[10],
     else if (type == 1) { k[4] = 1.0; k[8] = 1.0; }  // d_i = e_i
     else { k[4] = 1.0; k[8] = -1.0; }                // d_1 = e_1, d_2 = -e_2
     *C = 3;
+  } else if (theory == SS_SID) {
+    if (n_params != 7) return fail(SS_ERR_ARG, "s+id takes {a1, a2, b1, b2, b3, b4, nu}");
+    for (int i = 0; i < 7; ++i)
+      if (!std::isfinite(params[i])) return fail(SS_ERR_ARG, "s+id parameters must be finite");
+    const double b1 = params[2], b2 = params[3], b3e = params[4] - 2.0 * std::fabs(params[5]);
+    if (!(b1 > 0.0) || !(b2 > 0.0) || !(4.0 * b1 * b2 > b3e * b3e))
+      return fail(SS_ERR_ARG, "s+id quartic potential must be bounded below (b1, b2 > 0, 4 b1 b2 > (b3 - 2|b4|)^2)");
+    if (!(std::fabs(params[6]) < 1.0)) return fail(SS_ERR_ARG, "|nu| must be < 1 (positive gradient energy)");
+    for (int i = 0; i < 7; ++i) k[i] = params[i];
+    *C = 6;
   } else if (theory == SS_BEC) {
     if (n_params != 3) return fail(SS_ERR_ARG, "BEC takes {g, Omega, mu}");
     for (int i = 0; i < 3; ++i)
@@ -112,6 +122,7 @@ int th_of(int theory) {
     case SS_ABELIAN_HIGGS: return TH_AH;
     case SS_CHIRAL_MAGNET: return TH_CM;
     case SS_BABY_SKYRME: return TH_BS;
+    case SS_SID: return TH_SID;
     default: return TH_BEC;
   }
 }
@@ -129,10 +140,12 @@ int check_grid(int nx, int ny, double dx, double dy) {
 // eigenvalue, at the checkerboard mode). The BEC adds bounds on its position-dependent
 // terms over the grid: the trap r_max^2, the interaction at the Thomas-Fermi density
 // 4 |mu|, and the rotation 2 |Omega| r_max s1 with s1 = 1.3722 / min(dx, dy), the
-// largest magnitude of the Eq. 1 symbol.
+// largest magnitude of the Eq. 1 symbol. The s+id mixed gradient scales the Laplacian
+// bound by 1 + |nu|.
 double descent_step(double dx, double dy, double factor, int theory = 0, int nx = 0, int ny = 0,
                     const double* coup = nullptr) {
   double lam = (16.0 / 3.0) * (1.0 / (dx * dx) + 1.0 / (dy * dy));
+  if (theory == SS_SID && coup) lam *= 1.0 + std::fabs(coup[6]);  // the mixed gradient's band coupling
   if (theory == SS_BEC && coup) {
     const double hx = 0.5 * (nx - 1) * dx, hy = 0.5 * (ny - 1) * dy;
     const double r2 = hx * hx + hy * hy;

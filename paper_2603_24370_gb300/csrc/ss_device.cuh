@@ -22,13 +22,14 @@ constexpr int HALO = 2;
 constexpr int SX = TX + 2 * HALO, SY = TY + 2 * HALO;
 constexpr int ROWS_PER_THREAD = TY / BY;
 
-enum { TH_AH = 1, TH_CM = 2, TH_BS = 3, TH_BEC = 4 };
+enum { TH_AH = 1, TH_CM = 2, TH_BS = 3, TH_BEC = 4, TH_SID = 5 };
 
 template <int TH> struct NComp;
 template <> struct NComp<TH_AH> { static constexpr int C = 4; };
 template <> struct NComp<TH_CM> { static constexpr int C = 3; };
 template <> struct NComp<TH_BS> { static constexpr int C = 3; };
 template <> struct NComp<TH_BEC> { static constexpr int C = 2; };
+template <> struct NComp<TH_SID> { static constexpr int C = 6; };
 
 // Theories whose field is a unit 3-vector (projected onto the sphere).
 template <int TH> struct UnitVector { static constexpr bool value = TH == TH_CM || TH == TH_BS; };
@@ -195,6 +196,7 @@ SS_HD Deriv<R> stencil(const R* P, int sx, int sy, const Spacing<R>& h) {
 // Chiral magnet: c[0] = J, c[1] = D, c[2] = K, c[3] = h, c[4..6] = d_1, c[7..9] = d_2.
 // Baby Skyrme: c[0] = kappa^2, c[1] = mu^2, c[2] = nu^2.
 // BEC: c[0] = g, c[1] = Omega, c[2] = mu (chemical potential).
+// s+id: c[0..6] = a1, a2, b1, b2, b3, b4, nu.
 template <typename R>
 struct Couplings {
   R c[10];
@@ -326,6 +328,84 @@ SS_HD void force_bec(const Couplings<R>& k, const R* v, const R* fx, const R* fy
   G[1] = -(fxx[1] + fyy[1]) + w * v[1] + R(2) * k.c[1] * Du;
 }
 
+// s+id two-band superconductor (Table 1), components (Re, Im Delta_s, Re, Im Delta_d,
+// A_1, A_2), D = d - i A. Gradient tensor: identity within each band, nu diag(1, -1)
+// between the bands (d_{x^2-y^2}). With X_aj = d_j u_a + A_j w_a, Y_aj = d_j w_a - A_j u_a
+// (real and imaginary parts of D_j Delta_a), S = |Delta_s|^2, D = |Delta_d|^2 and
+// p + i q = Delta_s conj(Delta_d):
+//   e = 1/2 sum (X^2 + Y^2) + nu sum_j eta_j (X_sj X_dj + Y_sj Y_dj) + B^2 / 2
+//       + a1 S + a2 D + b1 S^2 + b2 D^2 + b3 S D + 2 b4 (p^2 - q^2),   eta = (1, -1).
+template <typename R>
+SS_HD R density_sid(const Couplings<R>& k, const R* v, const R* fx, const R* fy) {
+  const R A1 = v[4], A2 = v[5];
+  const R Xs1 = fx[0] + A1 * v[1], Ys1 = fx[1] - A1 * v[0], Xs2 = fy[0] + A2 * v[1], Ys2 = fy[1] - A2 * v[0];
+  const R Xd1 = fx[2] + A1 * v[3], Yd1 = fx[3] - A1 * v[2], Xd2 = fy[2] + A2 * v[3], Yd2 = fy[3] - A2 * v[2];
+  const R grad = R(0.5) * (Xs1 * Xs1 + Ys1 * Ys1 + Xs2 * Xs2 + Ys2 * Ys2 + Xd1 * Xd1 + Yd1 * Yd1 + Xd2 * Xd2 +
+                           Yd2 * Yd2);
+  const R mix = (Xs1 * Xd1 + Ys1 * Yd1) - (Xs2 * Xd2 + Ys2 * Yd2);
+  const R B = fx[5] - fy[4];
+  const R S = v[0] * v[0] + v[1] * v[1], D = v[2] * v[2] + v[3] * v[3];
+  const R p = v[0] * v[2] + v[1] * v[3], q = v[1] * v[2] - v[0] * v[3];
+  return grad + k.c[6] * mix + R(0.5) * B * B + k.c[0] * S + k.c[1] * D + k.c[2] * S * S + k.c[3] * D * D +
+         k.c[4] * S * D + R(2) * k.c[5] * (p * p - q * q);
+}
+
+// s+id force: with the conjugates P_aj = X_aj + nu eta_j X_bj, Q_aj = Y_aj + nu eta_j Y_bj
+// (b the other band) and d_j X_aj = d_j^2 u_a + (d_j A_j) w_a + A_j d_j w_a,
+// d_j Y_aj = d_j^2 w_a - (d_j A_j) u_a - A_j d_j u_a:
+//   G_{u_a} = dV/du_a - sum_j (A_j Q_aj + d_j P_aj),  G_{w_a} = dV/dw_a + sum_j (A_j P_aj - d_j Q_aj),
+//   G_{A_1} = d_2 B + sum_a (P_a1 w_a - Q_a1 u_a),   G_{A_2} = -d_1 B + sum_a (P_a2 w_a - Q_a2 u_a).
+template <typename R>
+SS_HD void force_sid(const Couplings<R>& k, const R* v, const R* fx, const R* fy, const R* fxx, const R* fyy,
+                     const R* fxy, R* G) {
+  const R A[2] = {v[4], v[5]}, dA[2] = {fx[4], fy[5]};
+  const R nu = k.c[6];
+  R X[2][2], Y[2][2], dX[2][2], dY[2][2];
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    const R u = v[2 * a], w = v[2 * a + 1];
+    const R du[2] = {fx[2 * a], fy[2 * a]}, dw[2] = {fx[2 * a + 1], fy[2 * a + 1]};
+    const R uu[2] = {fxx[2 * a], fyy[2 * a]}, ww[2] = {fxx[2 * a + 1], fyy[2 * a + 1]};
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      X[a][j] = du[j] + A[j] * w;
+      Y[a][j] = dw[j] - A[j] * u;
+      dX[a][j] = uu[j] + dA[j] * w + A[j] * dw[j];
+      dY[a][j] = ww[j] - dA[j] * u - A[j] * du[j];
+    }
+  }
+  const R s1 = v[0], s2 = v[1], d1 = v[2], d2 = v[3];
+  const R S = s1 * s1 + s2 * s2, D = d1 * d1 + d2 * d2;
+  const R p = s1 * d1 + s2 * d2, q = s2 * d1 - s1 * d2;
+  const R cs = R(2) * k.c[0] + R(4) * k.c[2] * S + R(2) * k.c[4] * D;
+  const R cd = R(2) * k.c[1] + R(4) * k.c[3] * D + R(2) * k.c[4] * S;
+  const R f4 = R(4) * k.c[5];
+  R dV[4];
+  dV[0] = cs * s1 + f4 * (p * d1 + q * d2);
+  dV[1] = cs * s2 + f4 * (p * d2 - q * d1);
+  dV[2] = cd * d1 + f4 * (p * s1 - q * s2);
+  dV[3] = cd * d2 + f4 * (p * s2 + q * s1);
+  G[4] = fxy[5] - fyy[4];
+  G[5] = fxy[4] - fxx[5];
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    const int b = 1 - a;
+    const R u = v[2 * a], w = v[2 * a + 1];
+    R gu = dV[2 * a], gw = dV[2 * a + 1];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const R nj = j == 0 ? nu : -nu;
+      const R P = X[a][j] + nj * X[b][j], Q = Y[a][j] + nj * Y[b][j];
+      const R dP = dX[a][j] + nj * dX[b][j], dQ = dY[a][j] + nj * dY[b][j];
+      gu -= A[j] * Q + dP;
+      gw += A[j] * P - dQ;
+      G[4 + j] += P * w - Q * u;
+    }
+    G[2 * a] = gu;
+    G[2 * a + 1] = gw;
+  }
+}
+
 // ------------------------------------------------------------------ energy differences
 // Eq. 4 compares E_h(phi^{n+1}) with E_h(phi^n). Both energy densities are
 // polynomials in (phi, d phi), so with a = phi^{n+1} and delta = phi^{n+1} - phi^n
@@ -428,6 +508,52 @@ SS_HD R delta_density_bec(const Couplings<R>& k, const R* a, const R* ax, const 
   return kin + (R(0.5) * (x * x + y * y) - k.c[2]) * dn + R(0.5) * k.c[0] * (R(2) * n - dn) * dn - k.c[1] * rot;
 }
 
+// s+id: exact differences of every factor (the Abelian Higgs identities per band),
+//   dX_aj = d_j delta_u + A_j delta_w + delta_A_j (w - delta_w),
+//   dY_aj = d_j delta_w - A_j delta_u - delta_A_j (u - delta_u),
+// then 1/2 (2 X - dX) dX per square, X_s X_d - X_s' X_d' = dX_s X_d + X_s dX_d - dX_s dX_d
+// for the mixed products, and likewise for S, D, p, q in the potential.
+template <typename R>
+SS_HD R delta_density_sid(const Couplings<R>& k, const R* a, const R* ax, const R* ay, const R* d, const R* dx,
+                          const R* dy) {
+  const R A[2] = {a[4], a[5]}, dA[2] = {d[4], d[5]};
+  R X[2][2], Y[2][2], eX[2][2], eY[2][2];
+#pragma unroll
+  for (int b = 0; b < 2; ++b) {
+    const R u = a[2 * b], w = a[2 * b + 1], du = d[2 * b], dw = d[2 * b + 1];
+    const R gu[2] = {ax[2 * b], ay[2 * b]}, gw[2] = {ax[2 * b + 1], ay[2 * b + 1]};
+    const R hu[2] = {dx[2 * b], dy[2 * b]}, hw[2] = {dx[2 * b + 1], dy[2 * b + 1]};
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      X[b][j] = gu[j] + A[j] * w;
+      Y[b][j] = gw[j] - A[j] * u;
+      eX[b][j] = hu[j] + (A[j] * dw + dA[j] * (w - dw));
+      eY[b][j] = hw[j] - (A[j] * du + dA[j] * (u - du));
+    }
+  }
+  R sq = R(0), mix = R(0);
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+#pragma unroll
+    for (int b = 0; b < 2; ++b) sq += (R(2) * X[b][j] - eX[b][j]) * eX[b][j] + (R(2) * Y[b][j] - eY[b][j]) * eY[b][j];
+    const R m = (eX[0][j] * X[1][j] + X[0][j] * eX[1][j] - eX[0][j] * eX[1][j]) +
+                (eY[0][j] * Y[1][j] + Y[0][j] * eY[1][j] - eY[0][j] * eY[1][j]);
+    mix += j == 0 ? m : -m;
+  }
+  const R B = ax[5] - ay[4], dB = dx[5] - dy[4];
+  const R s1 = a[0], s2 = a[1], d1 = a[2], d2 = a[3];
+  const R e1 = d[0], e2 = d[1], f1 = d[2], f2 = d[3];
+  const R S = s1 * s1 + s2 * s2, D = d1 * d1 + d2 * d2;
+  const R dS = e1 * (R(2) * s1 - e1) + e2 * (R(2) * s2 - e2);
+  const R dD = f1 * (R(2) * d1 - f1) + f2 * (R(2) * d2 - f2);
+  const R p = s1 * d1 + s2 * d2, q = s2 * d1 - s1 * d2;
+  const R dp = (e1 * d1 + s1 * f1 - e1 * f1) + (e2 * d2 + s2 * f2 - e2 * f2);
+  const R dq = (e2 * d1 + s2 * f1 - e2 * f1) - (e1 * d2 + s1 * f2 - e1 * f2);
+  return R(0.5) * sq + k.c[6] * mix + R(0.5) * (R(2) * B - dB) * dB + k.c[0] * dS + k.c[1] * dD +
+         k.c[2] * (R(2) * S - dS) * dS + k.c[3] * (R(2) * D - dD) * dD + k.c[4] * (dS * D + S * dD - dS * dD) +
+         R(2) * k.c[5] * ((R(2) * p - dp) * dp - (R(2) * q - dq) * dq);
+}
+
 // Energy density, force and energy difference of theory TH at a site at (x, y)
 // (the position enters only the BEC's trap and rotation terms).
 template <int TH, typename R>
@@ -435,6 +561,7 @@ SS_HD R density_at(const Couplings<R>& k, const R* v, const R* fx, const R* fy, 
   if (TH == TH_AH) return density_ah<R>(k, v, fx, fy);
   if (TH == TH_CM) return density_cm<R>(k, v, fx, fy);
   if (TH == TH_BS) return density_bs<R>(k, v, fx, fy);
+  if (TH == TH_SID) return density_sid<R>(k, v, fx, fy);
   return density_bec<R>(k, v, fx, fy, x, y);
 }
 template <int TH, typename R>
@@ -443,6 +570,7 @@ SS_HD R delta_density_at(const Couplings<R>& k, const R* a, const R* ax, const R
   if (TH == TH_AH) return delta_density_ah<R>(k, a, ax, ay, d, dx, dy);
   if (TH == TH_CM) return delta_density_cm<R>(k, a, ax, ay, d, dx, dy);
   if (TH == TH_BS) return delta_density_bs<R>(k, a, ax, ay, d, dx, dy);
+  if (TH == TH_SID) return delta_density_sid<R>(k, a, ax, ay, d, dx, dy);
   return delta_density_bec<R>(k, a, ax, ay, d, dx, dy, x, y);
 }
 template <int TH, typename R>
@@ -451,6 +579,7 @@ SS_HD void force_of(const Couplings<R>& k, const R* v, const R* fx, const R* fy,
   if (TH == TH_AH) force_ah<R>(k, v, fx, fy, fxx, fyy, fxy, G);
   else if (TH == TH_CM) force_cm<R>(k, v, fx, fy, fxx, fyy, G);
   else if (TH == TH_BS) force_bs<R>(k, v, fx, fy, fxx, fyy, fxy, G);
+  else if (TH == TH_SID) force_sid<R>(k, v, fx, fy, fxx, fyy, fxy, G);
   else force_bec<R>(k, v, fx, fy, fxx, fyy, x, y, G);
 }
 

@@ -1,830 +1,15 @@
-// ss_flow.cu -- the arrested-Newton-flow step (arxiv 2603.24370, Sec. 3.2) as two
-// fused passes over a batch of relaxation problems, and the gradient-descent step
-// it is compared with as a third pass built from the same parts.
-//
-// One RK4 step of phi'' = -G(phi) (Eq. 3) on the first-order system (phi, v), with
-// k_vi = -G(Y_i) at the stage inputs
-//   Y_1 = phi,                       Y_2 = phi + dt/2 v,
-//   Y_3 = phi + dt/2 v + dt^2/4 k_v1, Y_4 = phi + dt v + dt^2/2 k_v2,
-//   phi' = phi + dt v + dt^2/6 (k_v1 + k_v2 + k_v3),
-//   v'   = v + dt/6 (k_v1 + 2 k_v2 + 2 k_v3 + k_v4),
-// is the textbook (k_phi, k_v) form with every k_phi eliminated. Y_1 and Y_2 need
-// only (phi, v); Y_3 and Y_4 need only (phi, v, k_v1, k_v2). So a step is two passes
-// with the ordinary width-2 halo and no recomputation:
-//   pass 1  (stages 1, 2): reads phi, v (and phi^{n-1}), writes k_v1, k_v2;
-//   pass 2  (stages 3, 4): reads phi, v, k_v1, k_v2, writes phi', v'
-// (k_v3, k_v4 live in registers). Chiral magnet: every Y_i and phi' are normalised
-// and v' tangent-projected (Sec. 3.2, constraint projection).
-//
-// Batches: every launch covers the tiles of all problems of a batch (uneven grid
-// sizes and couplings, one theory and precision). Each tile reads its problem's
-// descriptor; each problem selects its ping-pong buffers from its own step count,
-// stops on its own (converged, non-finite, step limit), and its tiles are skipped
-// from then on. A single-grid context is a batch of one.
-//
-// Pass 1 also reduces, per problem, E_h(phi), dx dy max|G| and the energy change
-// since the previous field, dE = sum_I [e(phi^n) - e(phi^{n-1})], in the
-// cancellation-free form of ss_device.cuh (phi^{n-1} is still intact in the other
-// ping-pong buffer): a compensated pair per thread, summed over a block's run of
-// consecutive tiles of one problem and reduced into the partial of the run's last
-// tile; the last tile of the problem to arrive (arrival counter) sums the problem's
-// partials in tile order (bitwise reproducible) and decides on the device, with no
-// host round trip:
-//   arrest    = dE > 0, i.e. E_h(phi^n) > E_h(phi^{n-1})   (Eq. 4)
-//   converged = dx dy max|G| < tol
-// Pass 1 computes k_v2 with v before the arrest is known. That is exact either way:
-// when the step is arrested v counts as zero, so Y_2 = Y_1 and k_v2 = k_v1, and
-// pass 2 simply reads k_v1 in place of k_v2 (and zero in place of v).
-//
-// Compensated FP32 (LO): the field is stored as two FP32 planes, phi = hi + lo with
-// |lo| <= ulp(hi)/2, and pass 2 adds each step's increment to lo and re-splits by
-// TwoSum, so increments far below an ulp of the field still accumulate. With a
-// single FP32 plane they are rounded away once the flow is slow, and the flow
-// stalls above dx dy max|G| ~ 1e-6 while arresting every other step. The stage
-// inputs are formed as hi + (lo + increment), normalised in split form for the
-// chiral magnet, and rounded once to FP32 for the stencils.
-//
-// Gradient descent (pass 3), the first-order alternative Sec. 3.2 sets the flow
-// against, read as the explicit Euler step of d phi / d tau = -G(phi):
-//   phi^{n+1} = phi^n - dtau G(phi^n)   (chiral magnet: renormalised),
-// one launch per step with the same tile staging, stencils, forces, reductions and
-// device-side decision as pass 1: it reads phi^n, writes -G into k_v1 (so the
-// force of the head field is always at hand) and phi^{n+1} into the other buffer,
-// and the last tile of a problem advances its step count unless the field it
-// evaluated has converged or the step budget is spent. Nothing is arrested; a rise
-// E_h(phi^n) > E_h(phi^{n-1}) is counted (it means dtau is past the stability limit).
-// The rise is judged on the two working-precision sums, not in the cancellation-free
-// form of pass 1: that needs phi^{n-1}, whose buffer this launch is overwriting.
-//
-// Per block a tile of TX x TY sites is staged in shared memory with its halo, the
-// stage inputs formed while loading (two sites per iteration, loads first). Each
-// thread then walks RY rows of one column with a 5-row register window per
-// component. Blocks stride over the batch's tiles; the grid is occupancy x SMs.
+// ss_flow.cu -- host side of the flow passes (arxiv 2603.24370, Sec. 3.2): the
+// per-theory dispatch of the pass launches and occupancy queries, the pass grids,
+// and the control kernels over the per-problem flow records. The pass kernels
+// themselves are in ss_flow_kernel.cuh, instantiated per theory in ss_flow_ah.cu,
+// ss_flow_cm.cu, ss_flow_bs.cu, ss_flow_bec.cu and ss_flow_sid.cu.
 #include "ss_internal.h"
 
-// Launch-shape knobs of the three passes: sites staged per iteration of the tile
-// loading loop (their loads are all issued before any is used), and the resident
-// blocks per SM the register allocation of the single-problem chiral-magnet FP32
-// kernels must allow (1: no constraint; the other instances, whose descriptors
-// occupy registers or whose working type is wider, would spill and keep their
-// natural allocation).
-// Defaults measured best at 4096^2: pass 1 gains 4% from 3 blocks / SM with two
-// sites in flight, pass 2 2% from 5, the descent pass 8% from 6.
-#ifndef SS_LU1
-#define SS_LU1 2
-#endif
-#ifndef SS_LU2
-#define SS_LU2 2
-#endif
-#ifndef SS_LU3
-#define SS_LU3 4
-#endif
-#ifndef SS_MINB1
-#define SS_MINB1 3
-#endif
-#ifndef SS_MINB2
-#define SS_MINB2 5
-#endif
-#ifndef SS_MINB3
-#define SS_MINB3 6
-#endif
-
 namespace ss {
-
-// Tile shape: TS = 0 (small) or 1 (large) selects the rows each thread walks,
-// FP32 2 or 4 (tiles of 32 x 16 or 32 x 32 sites), FP64 1 or 2 (32 x 8 or 32 x 16).
-template <typename R, int TS>
-struct FlowTile {
-  static constexpr int RY = (sizeof(R) == 4 ? 2 : 1) << TS;  // rows per thread
-  static constexpr int TX = 32, TY = BY * RY;
-  static constexpr int SX = TX + 4, SY = TY + 4, SXY = SX * SY;
-};
 
 void flow_tile_dims(int prec, int ts, int* tx, int* ty) {
   *tx = 32;
   *ty = BY * ((prec == PREC_F64 ? 1 : 2) << (ts ? 1 : 0));
-}
-
-// 1 / |n| for the unit-length projection: FP32 uses the hardware reciprocal square
-// root refined by one Newton-Raphson step (y <- y (3 - x y^2) / 2), FP64 divides.
-__device__ __forceinline__ float inv_norm(float x) {
-  float y = rsqrtf(x);
-  return y * (1.5f - 0.5f * x * y * y);
-}
-__device__ __forceinline__ double inv_norm(double x) { return 1.0 / sqrt(x); }
-
-template <int C, typename R>
-__device__ __forceinline__ void normalise(R* y) {
-  const R s = inv_norm(y[0] * y[0] + y[1] * y[1] + y[2] * y[2]);
-#pragma unroll
-  for (int c = 0; c < C; ++c) y[c] *= s;
-}
-
-__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float bp = s - a;
-  e = (a - (s - bp)) + (b - bp);
-}
-
-// Split-form projection onto the unit sphere: given hi (FP32) and a small part t,
-// return t' with hi + t' = (hi + t) / |hi + t| to about eps^2. With
-// eta = |hi + t|^2 - 1 = (|hi|^2 - 1) + 2 hi.t + |t|^2, where |hi|^2 - 1 is formed
-// exactly (error-free products and sums), 1/|hi + t| = 1 + rho with
-// rho = -eta / (r (1 + r)), r = sqrt(1 + eta), and t' = t + rho (hi + t).
-// rho enters only as a correction of size |eta| / 2, so a few ulps of relative
-// error in it are harmless: r comes from the hardware reciprocal square root
-// (r = x rsqrt(x)) and the quotient from the fast division, which keeps the IEEE
-// division's range checks and slow path out of the kernels' inner loops.
-__device__ __forceinline__ void normalise_split(const float* hi, float* t) {
-  float p[3], e[3];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    p[c] = hi[c] * hi[c];
-    e[c] = fmaf(hi[c], hi[c], -p[c]);
-  }
-  float s01, e01, s012, e012;
-  two_sum_f(p[0], p[1], s01, e01);
-  two_sum_f(s01, p[2], s012, e012);
-  const float q = (s012 - 1.0f) + (e01 + e012 + e[0] + e[1] + e[2]);  // s012 - 1 is exact near 1
-  const float ht = hi[0] * t[0] + hi[1] * t[1] + hi[2] * t[2];
-  const float tt = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
-  const float eta = q + (2.0f * ht + tt);
-  const float x = 1.0f + eta;
-  const float r = x * rsqrtf(x);
-  const float rho = __fdividef(-eta, r * (1.0f + r));
-#pragma unroll
-  for (int c = 0; c < 3; ++c) t[c] = t[c] + rho * (hi[c] + t[c]);
-}
-
-// Sliding 5-row window over one component plane of the shared tile, for one
-// column. MIX keeps the x-stencil of all five rows for the mixed derivative.
-template <typename R, bool MIX>
-struct Win {
-  R c[5];   // centre values of rows y-2 .. y+2
-  R g[5];   // MIX: unscaled Eq. 1 along x of rows y-2 .. y+2
-  R xx[5];  // MIX: unscaled Eq. 2 along x of rows y-2 .. y+2
-
-  __device__ __forceinline__ static void xterms(const R* P, R ce, R& gx, R& gxx) {
-    const R m2 = P[-2], m1 = P[-1], p1 = P[1], p2 = P[2];
-    gx = R(8) * (p1 - m1) - (p2 - m2);
-    gxx = R(16) * ((p1 - ce) + (m1 - ce)) - ((p2 - ce) + (m2 - ce));
-  }
-  // P points at the row's centre.
-  __device__ __forceinline__ void enter(const R* P, int slot) {
-    const R ce = P[0];
-    c[slot] = ce;
-    if (MIX) xterms(P, ce, g[slot], xx[slot]);
-  }
-  __device__ __forceinline__ void shift() {
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      c[k] = c[k + 1];
-      if (MIX) { g[k] = g[k + 1]; xx[k] = xx[k + 1]; }
-    }
-  }
-  __device__ __forceinline__ static R yd1(const R* a) { return R(8) * (a[3] - a[1]) - (a[4] - a[0]); }
-  __device__ __forceinline__ static R yd2(const R* a) {
-    return R(16) * ((a[3] - a[2]) + (a[1] - a[2])) - ((a[4] - a[2]) + (a[0] - a[2]));
-  }
-  // Derivatives at the window's centre row; Pc points at that row's centre.
-  template <bool SECOND>
-  __device__ __forceinline__ void derivs(const R* Pc, const Spacing<R>& h, R& v, R& fx, R& fy, R& fxx, R& fyy,
-                                         R& fxy) const {
-    R gx, gxx;
-    if (MIX) {
-      gx = g[2];
-      gxx = xx[2];
-    } else {
-      xterms(Pc, c[2], gx, gxx);
-    }
-    v = c[2];
-    fx = gx * h.i12dx;      // Eq. 1, x
-    fy = yd1(c) * h.i12dy;  // Eq. 1, y
-    if (SECOND) {
-      fxx = gxx * h.i12dx2;     // Eq. 2, x
-      fyy = yd2(c) * h.i12dy2;  // Eq. 2, y
-    } else {
-      fxx = fyy = R(0);
-    }
-    fxy = MIX ? (R(8) * (g[3] - g[1]) - (g[4] - g[0])) * h.i144dxdy : R(0);  // Eq. 1 in y of Eq. 1 in x
-  }
-};
-
-// Window set of one stage input: all C components, mixed derivatives for the gauge
-// field of the Abelian Higgs model (components 2, 3).
-template <int TH, typename R, int SXY_>
-struct StageWin {
-  static constexpr int C = NComp<TH>::C;
-  static constexpr int SXY = SXY_;
-  Win<R, TH == TH_BS> w0, w1;  // Baby Skyrme: mixed derivatives of every component
-  Win<R, TH == TH_AH || TH == TH_BS> w2;
-  Win<R, TH == TH_AH> w3;  // unused for two- and three-component theories
-
-  __device__ __forceinline__ void enter(const R* tiles, int off, int slot) {
-    w0.enter(tiles + off, slot);
-    w1.enter(tiles + SXY + off, slot);
-    if (C >= 3) w2.enter(tiles + 2 * SXY + off, slot);
-    if (C == 4) w3.enter(tiles + 3 * SXY + off, slot);
-  }
-  __device__ __forceinline__ void shift() {
-    w0.shift();
-    w1.shift();
-    if (C >= 3) w2.shift();
-    if (C == 4) w3.shift();
-  }
-  __device__ __forceinline__ void derivs(const R* tiles, int off, const Spacing<R>& h, R* v, R* fx, R* fy, R* fxx,
-                                         R* fyy, R* fxy) const {
-    w0.template derivs<true>(tiles + off, h, v[0], fx[0], fy[0], fxx[0], fyy[0], fxy[0]);
-    w1.template derivs<true>(tiles + SXY + off, h, v[1], fx[1], fy[1], fxx[1], fyy[1], fxy[1]);
-    if (C >= 3) w2.template derivs<true>(tiles + 2 * SXY + off, h, v[2], fx[2], fy[2], fxx[2], fyy[2], fxy[2]);
-    if (C == 4) w3.template derivs<true>(tiles + 3 * SXY + off, h, v[3], fx[3], fy[3], fxx[3], fyy[3], fxy[3]);
-  }
-};
-
-// First derivatives only (the field difference of the arrest test).
-template <int TH, typename R, int SXY_>
-struct DiffWin {
-  static constexpr int C = NComp<TH>::C;
-  static constexpr int SXY = SXY_;
-  Win<R, false> w[C];
-  __device__ __forceinline__ void enter(const R* tiles, int off, int slot) {
-#pragma unroll
-    for (int c = 0; c < C; ++c) w[c].enter(tiles + c * SXY + off, slot);
-  }
-  __device__ __forceinline__ void shift() {
-#pragma unroll
-    for (int c = 0; c < C; ++c) w[c].shift();
-  }
-  __device__ __forceinline__ void derivs(const R* tiles, int off, const Spacing<R>& h, R* v, R* fx, R* fy) const {
-#pragma unroll
-    for (int c = 0; c < C; ++c) {
-      R unused0, unused1, unused2;
-      w[c].template derivs<false>(tiles + c * SXY + off, h, v[c], fx[c], fy[c], unused0, unused1, unused2);
-    }
-  }
-};
-
-template <int TH, typename R>
-__device__ __forceinline__ void force_at(const Couplings<R>& k, const R* v, const R* fx, const R* fy, const R* fxx,
-                                         const R* fyy, const R* fxy, R* G, R x = R(0), R y = R(0)) {
-  force_of<TH, R>(k, v, fx, fy, fxx, fyy, fxy, G, x, y);
-}
-
-// ---- per-tile block reduction in the working type: two compensated sums, one max
-template <typename R>
-struct RPair {
-  R s, c;
-};
-__device__ __forceinline__ RPair<float> pair_add(RPair<float> x, RPair<float> y) {
-  float s, e;
-  two_sum_f(x.s, y.s, s, e);
-  return RPair<float>{s, x.c + y.c + e};
-}
-__device__ __forceinline__ RPair<double> pair_add(RPair<double> x, RPair<double> y) {
-  double s, e;
-  two_sum(x.s, y.s, s, e);
-  return RPair<double>{s, x.c + y.c + e};
-}
-template <typename R>
-__device__ __forceinline__ R rmax(R a, R b) {
-  return (b > a || b != b) ? b : a;  // propagates NaN
-}
-// Running maximum of |g| for a >= 0: on non-negative values the IEEE bit patterns
-// order as unsigned integers, with every NaN above +Inf, so one integer max keeps
-// the maximum and propagates NaN (as rmax does).
-__device__ __forceinline__ float absmax(float a, float g) {
-  return __uint_as_float(max(__float_as_uint(a), __float_as_uint(fabsf(g))));
-}
-__device__ __forceinline__ double absmax(double a, double g) {
-  return __longlong_as_double((long long)max((unsigned long long)__double_as_longlong(a),
-                                             (unsigned long long)__double_as_longlong(fabs(g))));
-}
-// Block-wide: thread 0 ends with the block's two pairs and maximum. sm holds
-// (NT / 32) * 5 values of R. Fixed shape: bitwise reproducible.
-template <typename R>
-__device__ __forceinline__ void tile_reduce(RPair<R>& a, RPair<R>& b, R& m, R* sm) {
-  constexpr int W = NT / 32;
-  const int lane = threadIdx.x & 31, wid = (threadIdx.y * BX + threadIdx.x) >> 5;
-  for (int off = 16; off > 0; off >>= 1) {
-    a = pair_add(a, RPair<R>{__shfl_down_sync(0xffffffffu, a.s, off), __shfl_down_sync(0xffffffffu, a.c, off)});
-    b = pair_add(b, RPair<R>{__shfl_down_sync(0xffffffffu, b.s, off), __shfl_down_sync(0xffffffffu, b.c, off)});
-    m = rmax(m, __shfl_down_sync(0xffffffffu, m, off));
-  }
-  if (lane == 0) {
-    sm[wid] = a.s; sm[W + wid] = a.c; sm[2 * W + wid] = b.s; sm[3 * W + wid] = b.c; sm[4 * W + wid] = m;
-  }
-  __syncthreads();
-  if (wid == 0) {
-    a = lane < W ? RPair<R>{sm[lane], sm[W + lane]} : RPair<R>{R(0), R(0)};
-    b = lane < W ? RPair<R>{sm[2 * W + lane], sm[3 * W + lane]} : RPair<R>{R(0), R(0)};
-    m = lane < W ? sm[4 * W + lane] : R(0);
-    for (int off = 16; off > 0; off >>= 1) {
-      a = pair_add(a, RPair<R>{__shfl_down_sync(0xffffffffu, a.s, off), __shfl_down_sync(0xffffffffu, a.c, off)});
-      b = pair_add(b, RPair<R>{__shfl_down_sync(0xffffffffu, b.s, off), __shfl_down_sync(0xffffffffu, b.c, off)});
-      m = rmax(m, __shfl_down_sync(0xffffffffu, m, off));
-    }
-  }
-  __syncthreads();
-}
-
-// Per-tile view of the problem, staged in shared memory by thread 0.
-template <typename R>
-struct TileCtx {
-  ProbDesc<R> d;
-  int p;         // problem index
-  int skip;      // the problem has stopped (or, pass 1, its head is already evaluated)
-  int cur;       // ping-pong parity of the current field
-  int arrest;    // pass 2: the current velocity counts as zero
-  int has_prev;  // pass 1: the other buffer holds the previous field
-  int adv;       // pass 3: the step budget allows a new field
-};
-
-// Thread 0 stages the view of tile t. A problem's record changes only when its last
-// tile of a launch arrives, so while any of its tiles is still unprocessed (as tile
-// t is here) the view stays valid: it may be read ahead of use. A launch over a
-// single problem passes its descriptor as a kernel parameter and stages only the
-// record's flags.
-template <typename R, int PASS, bool ONE>
-__device__ __forceinline__ void load_tile_ctx(TileCtx<R>& tc, const ProbDesc<R>& one,
-                                              const ProbDesc<R>* __restrict__ probs,
-                                              const int* __restrict__ tile_prob, int t) {
-  const DevState* st;
-  if constexpr (ONE) {
-    tc.p = 0;
-    st = one.st;
-  } else {
-    const int p = tile_prob[t];
-    tc.d = probs[p];
-    tc.p = p;
-    st = tc.d.st;
-  }
-  const long long steps = st->steps;
-  int skip = (st->converged | st->nonfinite) != 0;
-  if (PASS == 1) skip |= (st->head_step == steps);
-  else if (PASS == 2) skip |= (steps >= st->step_limit);
-  else skip |= (st->head_step == steps && steps >= st->step_limit);  // evaluated, budget spent
-  tc.skip = skip;
-  tc.cur = (int)(steps & 1);
-  tc.arrest = (PASS == 2) && (st->arrest != 0);
-  tc.has_prev = (PASS == 1) && (steps > 0);
-  tc.adv = (PASS == 3) && (steps < st->step_limit);
-}
-
-// One flow pass over every tile of a batch. ONE: the batch has a single problem,
-// whose descriptor arrives as a kernel parameter, so its pointers, spacings and
-// couplings are read as constant operands instead of occupying registers.
-template <int TH, typename R, int PASS, bool ONE>
-constexpr int pass_min_blocks() {
-  return (TH == TH_CM && sizeof(R) == 4 && ONE) ? (PASS == 1 ? SS_MINB1 : (PASS == 2 ? SS_MINB2 : SS_MINB3)) : 1;
-}
-
-template <int TH, typename R, int PASS, bool LO, bool ONE, int TS>
-__global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
-    k_pass(const __grid_constant__ ProbDesc<R> one, const ProbDesc<R>* __restrict__ probs,
-           const int* __restrict__ tile_prob, int total_tiles) {
-  using T = FlowTile<R, TS>;
-  constexpr int C = NComp<TH>::C;
-  constexpr int RY = T::RY;
-  constexpr int PS = C * T::SXY;  // values per tile set
-  extern __shared__ __align__(16) unsigned char smraw[];
-  R* sm = reinterpret_cast<R*>(smraw);  // pass 1: [Y1 | Y2 | delta], pass 2: [Y3 | Y4], pass 3: [phi]
-  __shared__ TileCtx<R> tcb[2];         // this tile's view and the next one's (read ahead)
-  __shared__ R sred[(NT / 32) * 5];
-  __shared__ double dred[RedSmem<2, 1>::n];
-  __shared__ int s_last;
-  const int tid = threadIdx.y * BX + threadIdx.x;
-  R* const setA = sm;           // first stage input of the pass
-  R* const setB = sm + PS;      // second stage input
-  R* const setD = sm + 2 * PS;  // pass 1: phi^n - phi^{n-1}
-  // passes 1, 3: running sums over this block's consecutive tiles of one problem
-  R es = R(0), ec = R(0), ds = R(0), dc = R(0), gmr = R(0);
-
-  if (tid == 0 && (int)blockIdx.x < total_tiles) load_tile_ctx<R, PASS, ONE>(tcb[0], one, probs, tile_prob, blockIdx.x);
-  int buf = 0;
-  for (int t = blockIdx.x; t < total_tiles; t += gridDim.x, buf ^= 1) {
-    __syncthreads();  // tcb[buf] is staged; the previous tile's shared reads are finished
-    const int tn = t + gridDim.x;
-    if (tid == 0 && tn < total_tiles) load_tile_ctx<R, PASS, ONE>(tcb[buf ^ 1], one, probs, tile_prob, tn);
-    const TileCtx<R>& tc = tcb[buf];
-    if (tc.skip) continue;  // uniform over the block
-    const ProbDesc<R>& D = ONE ? one : tc.d;
-    const int cur = tc.cur;
-    const bool arrest = tc.arrest != 0;
-    const bool has_prev = tc.has_prev != 0;
-    const bool adv = tc.adv != 0;
-    const int nx = D.nx, ny = D.ny;
-    const size_t P = (size_t)D.plane;
-    const R* __restrict__ phi = D.phi[cur];
-    const R* __restrict__ lo = D.lo[cur];
-    const R* __restrict__ vel = D.v[cur];
-    const R* __restrict__ phi_prev = D.phi[cur ^ 1];
-    const R* __restrict__ lo_prev = D.lo[cur ^ 1];
-    R* __restrict__ kv1 = D.kv[0];
-    R* __restrict__ kv2 = D.kv[1];
-    const Spacing<R> h = D.h;
-    const Couplings<R> kc = D.k;
-    const R dt = D.dt, hdt = R(0.5) * dt;
-    const R c3 = R(0.25) * dt * dt, c4 = R(0.5) * dt * dt;
-    const int lt = t - D.tile0;  // tile index within the problem
-    const int x0 = (lt % D.ntx) * T::TX, y0 = (lt / D.ntx) * T::TY;
-
-    // ---- stage inputs over the tile and its halo, LU sites per iteration (the loads
-    // of all LU sites are issued before any is used: more bytes in flight per thread)
-    constexpr int LU = PASS == 1 ? SS_LU1 : (PASS == 2 ? SS_LU2 : SS_LU3);
-    for (int base = tid; base < T::SXY; base += LU * NT) {
-      R pv[LU][C], lv[LU][C], vv[LU][C], k1v[LU][C], k2v[LU][C], pp[LU][C], lp[LU][C];
-      bool in[LU], inside[LU];
-#pragma unroll
-      for (int u = 0; u < LU; ++u) {  // all global loads of the sites first
-        const int idx = base + u * NT;
-        const int ly = idx / T::SX, lx = idx - ly * T::SX;
-        const int gx = x0 + lx - 2, gy = y0 + ly - 2;
-        in[u] = idx < T::SXY && gx >= 0 && gx < nx && gy >= 0 && gy < ny;
-        inside[u] = in[u] && gx >= 2 && gx < nx - 2 && gy >= 2 && gy < ny - 2;
-        const size_t s = in[u] ? (size_t)gy * nx + gx : 0;
-#pragma unroll
-        for (int c = 0; c < C; ++c) {
-          pv[u][c] = in[u] ? phi[c * P + s] : R(0);
-          lv[u][c] = (LO && in[u]) ? lo[c * P + s] : R(0);
-          vv[u][c] = (PASS != 3 && inside[u] && !arrest) ? vel[c * P + s] : R(0);
-          if (PASS == 1) {
-            pp[u][c] = (has_prev && in[u]) ? phi_prev[c * P + s] : pv[u][c];
-            lp[u][c] = (LO && has_prev && in[u]) ? lo_prev[c * P + s] : lv[u][c];
-          } else if (PASS == 2) {
-            k1v[u][c] = inside[u] ? kv1[c * P + s] : R(0);
-            k2v[u][c] = inside[u] ? (arrest ? k1v[u][c] : kv2[c * P + s]) : R(0);
-          }
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < LU; ++u) {
-        const int idx = base + u * NT;
-        if (idx >= T::SXY) break;
-        R ya[C], yb[C], yd[C];
-        if (PASS == 1) {
-#pragma unroll
-          for (int c = 0; c < C; ++c) {
-            // delta = phi^n - phi^{n-1} (differences of neighbouring values: exact per part)
-            yd[c] = LO ? (pv[u][c] - pp[u][c]) + (lv[u][c] - lp[u][c]) : pv[u][c] - pp[u][c];
-            ya[c] = LO ? lv[u][c] : pv[u][c];
-            yb[c] = (LO ? lv[u][c] : pv[u][c]) + hdt * vv[u][c];
-          }
-          if (UnitVector<TH>::value && inside[u]) {
-            if constexpr (LO) normalise_split(pv[u], yb);
-            else normalise<C>(yb);
-          }
-        } else if (PASS == 2) {
-#pragma unroll
-          for (int c = 0; c < C; ++c) {
-            const R base3 = hdt * vv[u][c] + c3 * k1v[u][c];
-            const R base4 = dt * vv[u][c] + c4 * k2v[u][c];
-            ya[c] = (LO ? lv[u][c] : pv[u][c]) + base3;
-            yb[c] = (LO ? lv[u][c] : pv[u][c]) + base4;
-          }
-          if (UnitVector<TH>::value && inside[u]) {
-            if constexpr (LO) {
-              normalise_split(pv[u], ya);
-              normalise_split(pv[u], yb);
-            } else {
-              normalise<C>(ya);
-              normalise<C>(yb);
-            }
-          }
-        } else {
-#pragma unroll
-          for (int c = 0; c < C; ++c) ya[c] = LO ? lv[u][c] : pv[u][c];
-        }
-        if (LO) {  // stage inputs: value + small part, rounded once
-#pragma unroll
-          for (int c = 0; c < C; ++c) {
-            ya[c] = pv[u][c] + ya[c];
-            if (PASS != 3) yb[c] = pv[u][c] + yb[c];
-          }
-        }
-#pragma unroll
-        for (int c = 0; c < C; ++c) {
-          setA[c * T::SXY + idx] = ya[c];
-          if (PASS != 3) setB[c * T::SXY + idx] = yb[c];
-          if (PASS == 1) setD[c * T::SXY + idx] = has_prev ? yd[c] : R(0);
-        }
-      }
-    }
-    __syncthreads();
-
-    // ---- column walk: RY rows of column threadIdx.x
-    const int sx = threadIdx.x + 2, sy0 = threadIdx.y * RY + 2;
-    const int gx = x0 + threadIdx.x, gyb = y0 + threadIdx.y * RY;
-    const bool colok = gx >= 2 && gx < nx - 2;
-    // site position, origin at the grid centre (only the BEC's trap and rotation use it)
-    const R hy = D.hy;
-    const R xs = TH == TH_BEC ? (R(gx) - R(0.5) * R(nx - 1)) * D.hx : R(0);
-    auto ypos = [&](int r) { return TH == TH_BEC ? (R(gyb + r) - R(0.5) * R(ny - 1)) * hy : R(0); };
-
-    if (PASS != 2) {
-      if (PASS == 1) {
-      // stage 1 at Y_1 = phi: k_v1, e, max|G|, and e(phi^n) - e(phi^{n-1})
-      {
-        StageWin<TH, R, T::SXY> W;
-        DiffWin<TH, R, T::SXY> D;
-#pragma unroll
-        for (int s = 0; s < 5; ++s) {
-          const int off = (sy0 - 2 + s) * T::SX + sx;
-          W.enter(setA, off, s);
-          if (has_prev) D.enter(setD, off, s);
-        }
-#pragma unroll
-        for (int r = 0; r < RY; ++r) {
-          const int off = (sy0 + r) * T::SX + sx;
-          const bool ok = colok && gyb + r >= 2 && gyb + r < ny - 2;
-          R v[C], fx[C], fy[C], fxx[C], fyy[C], fxy[C], G[C];
-          W.derivs(setA, off, h, v, fx, fy, fxx, fyy, fxy);
-          force_at<TH, R>(kc, v, fx, fy, fxx, fyy, fxy, G, xs, ypos(r));
-          if (ok) {
-            const size_t s = (size_t)(gyb + r) * nx + gx;
-#pragma unroll
-            for (int c = 0; c < C; ++c) {
-              kv1[c * P + s] = -G[c];
-              gmr = absmax(gmr, G[c]);
-            }
-            const R e = density_at<TH, R>(kc, v, fx, fy, xs, ypos(r));
-            const R t1 = es + e;
-            ec += (fabs(es) >= fabs(e)) ? (es - t1) + e : (e - t1) + es;
-            es = t1;
-          }
-          if (has_prev) {
-            R dd[C], dxv[C], dyv[C];
-            D.derivs(setD, off, h, dd, dxv, dyv);
-            if (ok) {
-              const R de = delta_density_at<TH, R>(kc, v, fx, fy, dd, dxv, dyv, xs, ypos(r));
-              const R t2 = ds + de;
-              dc += (fabs(ds) >= fabs(de)) ? (ds - t2) + de : (de - t2) + ds;
-              ds = t2;
-            }
-          }
-          if (r + 1 < RY) {
-            const int noff = (sy0 + r + 3) * T::SX + sx;
-            W.shift();
-            W.enter(setA, noff, 4);
-            if (has_prev) {
-              D.shift();
-              D.enter(setD, noff, 4);
-            }
-          }
-        }
-      }
-      // stage 2 at Y_2 = phi + dt/2 v: k_v2
-      {
-        StageWin<TH, R, T::SXY> W;
-#pragma unroll
-        for (int s = 0; s < 5; ++s) W.enter(setB, (sy0 - 2 + s) * T::SX + sx, s);
-#pragma unroll
-        for (int r = 0; r < RY; ++r) {
-          const int off = (sy0 + r) * T::SX + sx;
-          R v[C], fx[C], fy[C], fxx[C], fyy[C], fxy[C], G[C];
-          W.derivs(setB, off, h, v, fx, fy, fxx, fyy, fxy);
-          force_at<TH, R>(kc, v, fx, fy, fxx, fyy, fxy, G, xs, ypos(r));
-          if (colok && gyb + r >= 2 && gyb + r < ny - 2) {
-            const size_t s = (size_t)(gyb + r) * nx + gx;
-#pragma unroll
-            for (int c = 0; c < C; ++c) kv2[c * P + s] = -G[c];
-          }
-          if (r + 1 < RY) {
-            W.shift();
-            W.enter(setB, (sy0 + r + 3) * T::SX + sx, 4);
-          }
-        }
-      }
-      } else {
-      // gradient descent at phi: -G into k_v1, e, max|G|, and phi - dtau G
-      {
-        StageWin<TH, R, T::SXY> W;
-#pragma unroll
-        for (int s = 0; s < 5; ++s) W.enter(setA, (sy0 - 2 + s) * T::SX + sx, s);
-        const R tau = D.tau;
-        R* __restrict__ phi_out = D.phi[cur ^ 1];
-        R* __restrict__ lo_out = D.lo[cur ^ 1];
-#pragma unroll
-        for (int r = 0; r < RY; ++r) {
-          const int off = (sy0 + r) * T::SX + sx;
-          R v[C], fx[C], fy[C], fxx[C], fyy[C], fxy[C], G[C];
-          W.derivs(setA, off, h, v, fx, fy, fxx, fyy, fxy);
-          force_at<TH, R>(kc, v, fx, fy, fxx, fyy, fxy, G, xs, ypos(r));
-          if (colok && gyb + r >= 2 && gyb + r < ny - 2) {
-            const size_t s = (size_t)(gyb + r) * nx + gx;
-#pragma unroll
-            for (int c = 0; c < C; ++c) {
-              kv1[c * P + s] = -G[c];
-              gmr = absmax(gmr, G[c]);
-            }
-            const R e = density_at<TH, R>(kc, v, fx, fy, xs, ypos(r));
-            const R t1 = es + e;
-            ec += (fabs(es) >= fabs(e)) ? (es - t1) + e : (e - t1) + es;
-            es = t1;
-            if (adv) {
-              R p0[C], q[C], pn[C], ln[C];
-#pragma unroll
-              for (int c = 0; c < C; ++c) {
-                p0[c] = phi[c * P + s];
-                q[c] = (LO ? lo[c * P + s] : p0[c]) - tau * G[c];
-              }
-              if constexpr (LO) {
-                if (UnitVector<TH>::value) normalise_split(p0, q);
-#pragma unroll
-                for (int c = 0; c < C; ++c) two_sum_f(p0[c], q[c], pn[c], ln[c]);
-              } else {
-#pragma unroll
-                for (int c = 0; c < C; ++c) pn[c] = q[c];
-                if (UnitVector<TH>::value) normalise<C>(pn);
-              }
-#pragma unroll
-              for (int c = 0; c < C; ++c) {
-                phi_out[c * P + s] = pn[c];
-                if (LO) lo_out[c * P + s] = ln[c];
-              }
-            }
-          }
-          if (r + 1 < RY) {
-            W.shift();
-            W.enter(setA, (sy0 + r + 3) * T::SX + sx, 4);
-          }
-        }
-      }
-      }
-
-      // ---- partials: the block keeps summing while its next tile belongs to the same
-      // problem and writes a zero partial for this tile; otherwise it reduces and writes
-      // the running sums. The tile that completes the problem's count reduces the
-      // problem's partials in tile order and decides. (A tile whose block still holds
-      // another tile of the problem can never be the last to arrive.)
-      const ProbDesc<R>& d = D;
-      const bool flush = ONE ? tn >= total_tiles : !(tn < total_tiles && tcb[buf ^ 1].p == tc.p);
-      if (!flush) {
-        if (tid == 0) {
-          d.part[lt] = FlowPartial{0.0, 0.0, 0.0, 0.0, 0.0, {0.0, 0.0, 0.0}};
-          __threadfence();
-          atomicAdd(&d.st->ticket, 1u);
-        }
-        continue;
-      }
-      RPair<R> pe{es, ec}, pd{ds, dc};
-      R pm = gmr;
-      tile_reduce<R>(pe, pd, pm, sred);
-      es = ec = ds = dc = gmr = R(0);  // the next run of tiles starts afresh
-      if (tid == 0) {
-        d.part[lt] = FlowPartial{(double)pe.s, (double)pe.c, (double)pd.s, (double)pd.c, (double)pm,
-                                 {0.0, 0.0, 0.0}};
-        __threadfence();
-        const unsigned prev = atomicAdd(&d.st->ticket, 1u);
-        s_last = (prev == (unsigned)d.ntiles - 1);
-      }
-      __syncthreads();
-      if (s_last) {
-        __threadfence();
-        DD acc{0.0, 0.0}, dacc{0.0, 0.0};
-        double mm = 0.0;
-        for (int i = tid; i < d.ntiles; i += NT) {
-          const FlowPartial* q = d.part + i;
-          acc = dd_add(acc, DD{__ldcg(&q->es), __ldcg(&q->ec)});
-          dacc = dd_add(dacc, DD{__ldcg(&q->ds), __ldcg(&q->dc)});
-          mm = nanmax(mm, __ldcg(&q->m));
-        }
-        DD sv2[2] = {acc, dacc};
-        double mv2[1] = {mm};
-        block_reduce<2, 1>(sv2, mv2, dred);
-        if (tid == 0 && PASS == 1) {
-          DevState* st = d.st;
-          const double E = d.area * (sv2[0].s + sv2[0].c);
-          const double dE = d.area * (sv2[1].s + sv2[1].c);
-          const double g = d.area * mv2[0];
-          // Eq. 4, strict: E_h(phi^n) > E_h(phi^{n-1}); no previous field (E_last = +inf): no arrest
-          const int arr = has_prev ? (dE > 0.0 ? 1 : 0) : (E > st->E_last ? 1 : 0);
-          st->E_cur = E;
-          st->dE = has_prev ? dE : 0.0;
-          st->gmax = g;
-          st->arrest = arr;
-          st->arrests += arr;
-          st->E_last = E;
-          st->converged = (g < st->tol) ? 1 : 0;
-          st->nonfinite = (isfinite(E) && isfinite(g) && isfinite(dE)) ? 0 : 1;
-          st->head_step = st->steps;
-          st->ticket = 0;
-        } else if (tid == 0) {
-          // descent: record the evaluated field, count a rise, then take the step
-          // (its new field is already written) unless converged or out of budget
-          DevState* st = d.st;
-          const double E = d.area * (sv2[0].s + sv2[0].c);
-          const double g = d.area * mv2[0];
-          const double El = st->E_last;
-          const int rose = E > El ? 1 : 0;  // E_last = +inf before the first field
-          st->E_cur = E;
-          st->dE = isfinite(El) ? E - El : 0.0;
-          st->gmax = g;
-          st->arrest = rose;
-          st->arrests += rose;
-          st->E_last = E;
-          const int conv = (g < st->tol) ? 1 : 0;
-          const int bad = (isfinite(E) && isfinite(g)) ? 0 : 1;
-          st->converged = conv;
-          st->nonfinite = bad;
-          st->head_step = st->steps;
-          if (!conv && !bad && st->steps < st->step_limit) st->steps += 1;
-          st->ticket = 0;
-        }
-      }
-    } else {
-      // stage 3 at Y_3: k_v3 kept in registers
-      R k3[RY][C];
-      {
-        StageWin<TH, R, T::SXY> W;
-#pragma unroll
-        for (int s = 0; s < 5; ++s) W.enter(setA, (sy0 - 2 + s) * T::SX + sx, s);
-#pragma unroll
-        for (int r = 0; r < RY; ++r) {
-          const int off = (sy0 + r) * T::SX + sx;
-          R v[C], fx[C], fy[C], fxx[C], fyy[C], fxy[C], G[C];
-          W.derivs(setA, off, h, v, fx, fy, fxx, fyy, fxy);
-          force_at<TH, R>(kc, v, fx, fy, fxx, fyy, fxy, G, xs, ypos(r));
-#pragma unroll
-          for (int c = 0; c < C; ++c) k3[r][c] = -G[c];
-          if (r + 1 < RY) {
-            W.shift();
-            W.enter(setA, (sy0 + r + 3) * T::SX + sx, 4);
-          }
-        }
-      }
-      // stage 4 at Y_4, then the RK4 combination
-      {
-        StageWin<TH, R, T::SXY> W;
-#pragma unroll
-        for (int s = 0; s < 5; ++s) W.enter(setB, (sy0 - 2 + s) * T::SX + sx, s);
-        const R w6 = dt * dt / R(6), u6 = dt / R(6);
-        R* __restrict__ phi_out = D.phi[cur ^ 1];
-        R* __restrict__ lo_out = D.lo[cur ^ 1];
-        R* __restrict__ v_out = D.v[cur ^ 1];
-#pragma unroll
-        for (int r = 0; r < RY; ++r) {
-          const int off = (sy0 + r) * T::SX + sx;
-          R v[C], fx[C], fy[C], fxx[C], fyy[C], fxy[C], G[C];
-          W.derivs(setB, off, h, v, fx, fy, fxx, fyy, fxy);
-          force_at<TH, R>(kc, v, fx, fy, fxx, fyy, fxy, G, xs, ypos(r));
-          if (colok && gyb + r >= 2 && gyb + r < ny - 2) {
-            const size_t s = (size_t)(gyb + r) * nx + gx;
-            R p0[C], q[C], vn[C];
-#pragma unroll
-            for (int c = 0; c < C; ++c) {
-              p0[c] = phi[c * P + s];
-              const R v0 = arrest ? R(0) : vel[c * P + s];
-              const R k1 = kv1[c * P + s];
-              const R k2 = arrest ? k1 : kv2[c * P + s];
-              const R k4 = -G[c];
-              // increment of phi; with compensated storage it joins the stored remainder
-              const R inc = dt * v0 + w6 * (k1 + k2 + k3[r][c]);
-              q[c] = LO ? lo[c * P + s] + inc : p0[c] + inc;
-              vn[c] = v0 + u6 * (k1 + R(2) * (k2 + k3[r][c]) + k4);
-            }
-            R pn[C], ln[C];
-            if constexpr (LO) {
-              if (UnitVector<TH>::value) normalise_split(p0, q);
-#pragma unroll
-              for (int c = 0; c < C; ++c) two_sum_f(p0[c], q[c], pn[c], ln[c]);  // hi' = fl(hi + small), lo' = rest
-            } else {
-#pragma unroll
-              for (int c = 0; c < C; ++c) pn[c] = q[c];
-              if (UnitVector<TH>::value) normalise<C>(pn);
-            }
-            if (UnitVector<TH>::value) {
-              const R vp = vn[0] * pn[0] + vn[1] * pn[1] + vn[2] * pn[2];
-#pragma unroll
-              for (int c = 0; c < C; ++c) vn[c] -= vp * pn[c];
-            }
-#pragma unroll
-            for (int c = 0; c < C; ++c) {
-              phi_out[c * P + s] = pn[c];
-              if (LO) lo_out[c * P + s] = ln[c];
-              v_out[c * P + s] = vn[c];
-            }
-          }
-          if (r + 1 < RY) {
-            W.shift();
-            W.enter(setB, (sy0 + r + 3) * T::SX + sx, 4);
-          }
-        }
-      }
-      // The step count selects the ping-pong buffers and gates every tile of this
-      // problem, so it advances only when the problem's last tile has arrived (its
-      // own stores need not be finished: nothing in this launch reads them, and the
-      // next launch starts after this one ends).
-      if (tid == 0) {
-        __threadfence();
-        DevState* st = D.st;
-        const unsigned prev = atomicAdd(&st->ticket, 1u);
-        if (prev == (unsigned)D.ntiles - 1) {
-          st->ticket = 0;
-          st->steps += 1;
-        }
-      }
-    }
-  }
 }
 
 // ------------------------------------------------------------------ control kernels
@@ -881,53 +66,12 @@ __global__ void k_scaled_copy(R* __restrict__ out, const R* __restrict__ in, siz
     out[i] = scale * in[i];
 }
 
-// ------------------------------------------------------------------ launchers
-template <int TH, typename R, int TS>
-static size_t pass_smem(int pass) {
-  return (size_t)(pass == 1 ? 3 : (pass == 2 ? 2 : 1)) * NComp<TH>::C * FlowTile<R, TS>::SXY * sizeof(R);
-}
-
-template <int TH, typename R, bool LO, bool ONE, int TS>
-static void pass_launch(const BatchLaunch& b, int pass, cudaStream_t s) {
-  const ProbDesc<R>* probs = static_cast<const ProbDesc<R>*>(b.probs);
-  const ProbDesc<R> one = ONE ? *static_cast<const ProbDesc<R>*>(b.one) : ProbDesc<R>{};
-  const dim3 blk(BX, BY);
-  if (pass == 1)
-    k_pass<TH, R, 1, LO, ONE, TS><<<b.flow_blocks[0], blk, pass_smem<TH, R, TS>(1), s>>>(one, probs, b.tile_prob,
-                                                                                          b.total_tiles);
-  else if (pass == 2)
-    k_pass<TH, R, 2, LO, ONE, TS><<<b.flow_blocks[1], blk, pass_smem<TH, R, TS>(2), s>>>(one, probs, b.tile_prob,
-                                                                                          b.total_tiles);
-  else
-    k_pass<TH, R, 3, LO, ONE, TS><<<b.flow_blocks[2], blk, pass_smem<TH, R, TS>(3), s>>>(one, probs, b.tile_prob,
-                                                                                          b.total_tiles);
-}
-template <int TH, typename R, bool LO>
-static cudaError_t pass_t(const BatchLaunch& b, int pass, cudaStream_t s) {
-  if (pass < 1 || pass > 3) return cudaErrorInvalidValue;
-  if (b.one) {
-    if (b.ts) pass_launch<TH, R, LO, true, 1>(b, pass, s);
-    else pass_launch<TH, R, LO, true, 0>(b, pass, s);
-  } else {
-    if (b.ts) pass_launch<TH, R, LO, false, 1>(b, pass, s);
-    else pass_launch<TH, R, LO, false, 0>(b, pass, s);
-  }
-  return cudaGetLastError();
-}
-template <int TH>
-static cudaError_t pass_th(const BatchLaunch& b, int pass, cudaStream_t s) {
-  switch (b.prec) {
-    case PREC_F32C: return pass_t<TH, float, true>(b, pass, s);
-    case PREC_F64: return pass_t<TH, double, false>(b, pass, s);
-    default: return pass_t<TH, float, false>(b, pass, s);
-  }
-}
-
 cudaError_t launch_pass(const BatchLaunch& b, int pass, cudaStream_t s) {
-  if (b.theory == TH_AH) return pass_th<TH_AH>(b, pass, s);
-  if (b.theory == TH_CM) return pass_th<TH_CM>(b, pass, s);
-  if (b.theory == TH_BS) return pass_th<TH_BS>(b, pass, s);
-  return pass_th<TH_BEC>(b, pass, s);
+  if (b.theory == TH_AH) return launch_pass_theory<TH_AH>(b, pass, s);
+  if (b.theory == TH_CM) return launch_pass_theory<TH_CM>(b, pass, s);
+  if (b.theory == TH_BS) return launch_pass_theory<TH_BS>(b, pass, s);
+  if (b.theory == TH_SID) return launch_pass_theory<TH_SID>(b, pass, s);
+  return launch_pass_theory<TH_BEC>(b, pass, s);
 }
 
 cudaError_t launch_reset_states(DevState* st, int n, cudaStream_t s) {
@@ -946,7 +90,7 @@ cudaError_t launch_count_active(const DevState* st, int n, int* out, cudaStream_
 }
 
 cudaError_t launch_scaled_copy(const LaunchCtx& c, void* out, const void* in, double scale, cudaStream_t s) {
-  const int C = c.theory == TH_AH ? 4 : (c.theory == TH_BEC ? 2 : 3);
+  const int C = c.theory == TH_AH ? 4 : (c.theory == TH_BEC ? 2 : (c.theory == TH_SID ? 6 : 3));
   const size_t n = (size_t)C * c.plane;
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
@@ -957,48 +101,13 @@ cudaError_t launch_scaled_copy(const LaunchCtx& c, void* out, const void* in, do
   return cudaGetLastError();
 }
 
-// Opt the pass kernels into their dynamic shared memory and report how many blocks
-// of each pass fit on one SM.
-template <int TH, typename R, int PASS, bool LO, bool ONE, int TS>
-static void one_occupancy(int* occ) {
-  cudaFuncSetAttribute(k_pass<TH, R, PASS, LO, ONE, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)pass_smem<TH, R, TS>(PASS));
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_pass<TH, R, PASS, LO, ONE, TS>, NT,
-                                                pass_smem<TH, R, TS>(PASS));
-}
-template <int TH, typename R, bool LO, bool ONE, int TS>
-static void pass_occupancy(int occ[3]) {
-  one_occupancy<TH, R, 1, LO, ONE, TS>(&occ[0]);
-  one_occupancy<TH, R, 2, LO, ONE, TS>(&occ[1]);
-  one_occupancy<TH, R, 3, LO, ONE, TS>(&occ[2]);
-}
-
-template <int TH, bool ONE, int TS>
-static void occupancy_th(int prec, int occ[3]) {
-  switch (prec) {
-    case PREC_F32C: pass_occupancy<TH, float, true, ONE, TS>(occ); break;
-    case PREC_F64: pass_occupancy<TH, double, false, ONE, TS>(occ); break;
-    default: pass_occupancy<TH, float, false, ONE, TS>(occ); break;
-  }
-}
-
-template <int TH>
-static void occupancy_sel(int prec, int ts, bool one, int occ[3]) {
-  if (one) {
-    if (ts) occupancy_th<TH, true, 1>(prec, occ);
-    else occupancy_th<TH, true, 0>(prec, occ);
-  } else {
-    if (ts) occupancy_th<TH, false, 1>(prec, occ);
-    else occupancy_th<TH, false, 0>(prec, occ);
-  }
-}
-
 void flow_occupancy(int theory, int prec, int ts, bool one, int occ[3]) {
   occ[0] = occ[1] = occ[2] = 1;
-  if (theory == TH_AH) occupancy_sel<TH_AH>(prec, ts, one, occ);
-  else if (theory == TH_CM) occupancy_sel<TH_CM>(prec, ts, one, occ);
-  else if (theory == TH_BS) occupancy_sel<TH_BS>(prec, ts, one, occ);
-  else occupancy_sel<TH_BEC>(prec, ts, one, occ);
+  if (theory == TH_AH) occupancy_theory<TH_AH>(prec, ts, one, occ);
+  else if (theory == TH_CM) occupancy_theory<TH_CM>(prec, ts, one, occ);
+  else if (theory == TH_BS) occupancy_theory<TH_BS>(prec, ts, one, occ);
+  else if (theory == TH_SID) occupancy_theory<TH_SID>(prec, ts, one, occ);
+  else occupancy_theory<TH_BEC>(prec, ts, one, occ);
   for (int i = 0; i < 3; ++i)
     if (occ[i] < 1) occ[i] = 1;
 }

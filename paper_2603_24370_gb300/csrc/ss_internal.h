@@ -75,6 +75,13 @@ struct BatchLaunch {
   int ts;              // tile shape: 0 small, 1 large (flow_tile_dims)
 };
 
+// One theory's flow-pass launcher and occupancy query (ss_flow_kernel.cuh), each
+// instantiated in that theory's translation unit.
+template <int TH>
+cudaError_t launch_pass_theory(const BatchLaunch& b, int pass, cudaStream_t s);
+template <int TH>
+void occupancy_theory(int prec, int ts, bool one, int occ[3]);
+
 // Tile shape of the flow kernels for a precision (sites per tile along x, y).
 void flow_tile_dims(int prec, int ts, int* tx, int* ty);
 

@@ -95,6 +95,12 @@ extern "C" int ss_observables_noalloc(int theory, const double* params, int n_pa
     if (type == 0) { k[5] = 1.0; k[7] = -1.0; }
     else if (type == 1) { k[4] = 1.0; k[8] = 1.0; }
     else { k[4] = 1.0; k[8] = -1.0; }
+  } else if (theory == SS_SID) {
+    if (n_params != 7) return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: s+id takes {a1, a2, b1, b2, b3, b4, nu}");
+    for (int i = 0; i < 7; ++i) {
+      if (!std::isfinite(params[i])) return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: parameters must be finite");
+      k[i] = params[i];
+    }
   } else if (theory == SS_BEC) {
     if (n_params != 3) return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: BEC takes {g, Omega, mu}");
     for (int i = 0; i < 3; ++i)
@@ -139,6 +145,7 @@ extern "C" int ss_observables_noalloc(int theory, const double* params, int n_pa
   L.theory = theory == SS_ABELIAN_HIGGS ? TH_AH
              : theory == SS_CHIRAL_MAGNET ? TH_CM
              : theory == SS_BABY_SKYRME   ? TH_BS
+             : theory == SS_SID           ? TH_SID
                                           : TH_BEC;
   L.prec = precision;
   L.nx = nx;

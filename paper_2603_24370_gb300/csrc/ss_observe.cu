@@ -5,13 +5,16 @@
 // Observables are evaluated in FP64 arithmetic from the stored field (FP32 or
 // FP64), with compensated sums and a fixed reduction order:
 //   E_h  = dx dy sum_I e                              (Table 1 / Eq. 5 densities)
-//   flux = dx dy sum_I (d_1 A_2 - d_2 A_1)            (Abelian Higgs)
+//   flux = dx dy sum_I (d_1 A_2 - d_2 A_1)            (Abelian Higgs, s+id)
 //   Q    = (1/4pi) sum over plaquettes of the Berg-Luescher solid angles of the
 //          two triangles (n00, n10, n11), (n00, n11, n01)   (chiral magnet, Baby Skyrme)
-//   Q    = (1/2pi) sum of wrapped arg-psi steps around the boundary of I (Abelian Higgs)
+//   Q    = (1/2pi) sum of wrapped arg-psi steps around the boundary of I (Abelian Higgs;
+//          s+id: arg Delta_s)
 //   max_I |G|, max ||n| - 1|
 //   N    = dx dy sum_I |psi|^2, L = dx dy sum_I Re(psi* L_z psi)   (BEC)
 // A compensated FP32 field is read as value + remainder, exactly, in FP64.
+#include <cmath>
+
 #include "ss_internal.h"
 
 namespace ss {
@@ -94,7 +97,7 @@ __global__ void __launch_bounds__(NT) k_observables(ObsArgs<R> a) {
       double v[C], fx[C], fy[C], fxx[C], fyy[C], fxy[C];
 #pragma unroll
       for (int c = 0; c < C; ++c) {
-        const Deriv<double> d = ((TH == TH_AH && c >= 2) || TH == TH_BS)
+        const Deriv<double> d = ((TH == TH_AH && c >= 2) || TH == TH_BS || (TH == TH_SID && c >= 4))
                                     ? stencil<double, true, true>(sY[c], sx, sy, a.h)
                                     : stencil<double, true, false>(sY[c], sx, sy, a.h);
         v[c] = d.v; fx[c] = d.fx; fy[c] = d.fy; fxx[c] = d.fxx; fyy[c] = d.fyy; fxy[c] = d.fxy;
@@ -104,6 +107,10 @@ __global__ void __launch_bounds__(NT) k_observables(ObsArgs<R> a) {
         force_ah<double>(a.k, v, fx, fy, fxx, fyy, fxy, G);
         neumaier(se, density_ah<double>(a.k, v, fx, fy));
         neumaier(sf, fx[3] - fy[2]);
+      } else if (TH == TH_SID) {
+        force_of<TH, double>(a.k, v, fx, fy, fxx, fyy, fxy, G);
+        neumaier(se, density_at<TH, double>(a.k, v, fx, fy));
+        neumaier(sf, fx[5] - fy[4]);
       } else if (TH == TH_BEC) {
         const double x = (gx - 0.5 * (a.nx - 1)) * a.hx, y = (gy - 0.5 * (a.ny - 1)) * a.hy;
         force_of<TH, double>(a.k, v, fx, fy, fxx, fyy, fxy, G, x, y);
@@ -147,7 +154,7 @@ __global__ void __launch_bounds__(NT) k_observables(ObsArgs<R> a) {
   if (tid == 0) {
     DevState* st = a.st;
     st->obs_energy = a.area * (sv2[0].s + sv2[0].c);
-    st->obs_flux = TH == TH_AH ? a.area * (sv2[1].s + sv2[1].c) : 0.0;
+    st->obs_flux = (TH == TH_AH || TH == TH_SID) ? a.area * (sv2[1].s + sv2[1].c) : 0.0;
     st->obs_atoms = TH == TH_BEC ? a.area * (sv2[1].s + sv2[1].c) : 0.0;
     st->obs_lz = TH == TH_BEC ? a.area * (sv2[2].s + sv2[2].c) : 0.0;
     if (UnitVector<TH>::value) st->obs_charge = (sv2[2].s + sv2[2].c) / (4.0 * 3.14159265358979323846);
@@ -192,16 +199,18 @@ __global__ void __launch_bounds__(NT) k_winding(const R* __restrict__ phi, int n
 // Initial data (Sec. 3.4 "model-specific ansatz"; standard forms, see soliton.h),
 // evaluated in FP64 and rounded once to the storage type, into both field buffers.
 // BEC: psi = sqrt(max(0, mu - r^2/2) / g) prod_k tanh(r_k/s_k)^{|n_k|} exp(i (n_k theta_k + chi_k))
-// (Thomas-Fermi amplitude times vortex factors); cp = {g, mu}.
+// (Thomas-Fermi amplitude times vortex factors); q0 = g, q1 = mu.
+// s+id: the Abelian Higgs vortex product scaled by the uniform minimum, Delta_s = q0 x it,
+// Delta_d = q1 e^{i q2} x it (q2 the relative phase), A as for the Abelian Higgs model.
 template <int TH, typename R>
 __global__ void k_ansatz(R* __restrict__ f0, R* __restrict__ f1, int nx, int ny, size_t plane, double dx, double dy,
-                         const double* __restrict__ sol, int ns, double cg, double cmu) {
+                         const double* __restrict__ sol, int ns, double q0, double q1, double q2) {
   const double PI = 3.14159265358979323846;
   for (size_t s = (size_t)blockIdx.x * blockDim.x + threadIdx.x; s < plane; s += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(s % nx), j = (int)(s / nx);
     const double x = (i - 0.5 * (nx - 1)) * dx, y = (j - 0.5 * (ny - 1)) * dy;
     if (TH == TH_BEC) {
-      double mod = sqrt(fmax(0.0, cmu - 0.5 * (x * x + y * y)) / cg), ph = 0.0;
+      double mod = sqrt(fmax(0.0, q1 - 0.5 * (x * x + y * y)) / q0), ph = 0.0;
       for (int k = 0; k < ns; ++k) {
         const double X = x - sol[5 * k], Y = y - sol[5 * k + 1];
         const double n = sol[5 * k + 2], sz = sol[5 * k + 3], chi = sol[5 * k + 4];
@@ -213,7 +222,7 @@ __global__ void k_ansatz(R* __restrict__ f0, R* __restrict__ f1, int nx, int ny,
       const R v[2] = {(R)(mod * cs), (R)(mod * sn)};
 #pragma unroll
       for (int c = 0; c < 2; ++c) { f0[c * plane + s] = v[c]; f1[c * plane + s] = v[c]; }
-    } else if (TH == TH_AH) {
+    } else if (TH == TH_AH || TH == TH_SID) {
       double mod = 1.0, ph = 0.0, A1 = 0.0, A2 = 0.0;
       for (int k = 0; k < ns; ++k) {
         const double X = x - sol[5 * k], Y = y - sol[5 * k + 1];
@@ -229,9 +238,17 @@ __global__ void k_ansatz(R* __restrict__ f0, R* __restrict__ f1, int nx, int ny,
       }
       double sn, cs;
       sincos(ph, &sn, &cs);
-      const R v[4] = {(R)(mod * cs), (R)(mod * sn), (R)A1, (R)A2};
+      if (TH == TH_AH) {
+        const R v[4] = {(R)(mod * cs), (R)(mod * sn), (R)A1, (R)A2};
 #pragma unroll
-      for (int c = 0; c < 4; ++c) { f0[c * plane + s] = v[c]; f1[c * plane + s] = v[c]; }
+        for (int c = 0; c < 4; ++c) { f0[c * plane + s] = v[c]; f1[c * plane + s] = v[c]; }
+      } else {
+        double sd, cd;
+        sincos(ph + q2, &sd, &cd);
+        const R v[6] = {(R)(q0 * mod * cs), (R)(q0 * mod * sn), (R)(q1 * mod * cd), (R)(q1 * mod * sd), (R)A1, (R)A2};
+#pragma unroll
+        for (int c = 0; c < 6; ++c) { f0[c * plane + s] = v[c]; f1[c * plane + s] = v[c]; }
+      }
     } else {
       double n1 = 0.0, n2 = 0.0, n3 = 1.0;
       for (int k = 0; k < ns; ++k) {
@@ -279,7 +296,7 @@ static cudaError_t obs_t(const LaunchCtx& c, int cur, cudaStream_t s) {
   k_observables<TH, R><<<c.obs_blocks, dim3(BX, BY), 0, s>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  if (TH == TH_AH) {
+  if (TH == TH_AH || TH == TH_SID) {  // winding of the first complex field
     k_winding<R><<<1, dim3(BX, BY), 0, s>>>(a.phi, c.nx, c.ny, c.plane, c.st);
     e = cudaGetLastError();
   }
@@ -291,14 +308,37 @@ cudaError_t launch_observables(const LaunchCtx& c, int cur, cudaStream_t s) {
   if (c.theory == TH_AH) return f ? obs_t<TH_AH, float>(c, cur, s) : obs_t<TH_AH, double>(c, cur, s);
   if (c.theory == TH_CM) return f ? obs_t<TH_CM, float>(c, cur, s) : obs_t<TH_CM, double>(c, cur, s);
   if (c.theory == TH_BS) return f ? obs_t<TH_BS, float>(c, cur, s) : obs_t<TH_BS, double>(c, cur, s);
+  if (c.theory == TH_SID) return f ? obs_t<TH_SID, float>(c, cur, s) : obs_t<TH_SID, double>(c, cur, s);
   return f ? obs_t<TH_BEC, float>(c, cur, s) : obs_t<TH_BEC, double>(c, cur, s);
+}
+
+// Uniform minimum of the s+id potential: the relative phase is pi/2 for b4 > 0 (else 0),
+// which turns b3 into b3 - 2 |b4|; the two-band stationary point if both densities are
+// positive, else the better one-band minimum (or the normal state). Returns sqrt(S),
+// sqrt(D) and the phase.
+static void sid_uniform_minimum(const double* k, double* rs, double* rd, double* phase) {
+  const double a1 = k[0], a2 = k[1], b1 = k[2], b2 = k[3], b3 = k[4] - 2.0 * std::fabs(k[5]);
+  *phase = k[5] > 0.0 ? 1.57079632679489661923 : 0.0;
+  auto V = [&](double S, double D) { return a1 * S + a2 * D + b1 * S * S + b2 * D * D + b3 * S * D; };
+  double bs = 0.0, bd = 0.0, bv = 0.0;
+  auto take = [&](double S, double D) {
+    if (S >= 0.0 && D >= 0.0 && V(S, D) < bv) { bs = S; bd = D; bv = V(S, D); }
+  };
+  const double det = 4.0 * b1 * b2 - b3 * b3;
+  if (det != 0.0) take((-2.0 * b2 * a1 + b3 * a2) / det, (-2.0 * b1 * a2 + b3 * a1) / det);
+  if (b1 > 0.0) take(-a1 / (2.0 * b1), 0.0);
+  if (b2 > 0.0) take(0.0, -a2 / (2.0 * b2));
+  *rs = std::sqrt(bs);
+  *rd = std::sqrt(bd);
 }
 
 template <int TH, typename R>
 static cudaError_t ansatz_t(const LaunchCtx& c, const double* sol, int n, cudaStream_t s) {
   const int blocks = (int)((c.plane + 255) / 256 < 4096 ? (c.plane + 255) / 256 : 4096);
+  double q[3] = {c.coup[0], c.coup[2], 0.0};  // BEC: g, mu
+  if (TH == TH_SID) sid_uniform_minimum(c.coup, &q[0], &q[1], &q[2]);
   k_ansatz<TH, R><<<blocks, 256, 0, s>>>(static_cast<R*>(c.phi[0]), static_cast<R*>(c.phi[1]), c.nx, c.ny, c.plane,
-                                         c.dx, c.dy, sol, n, c.coup[0], c.coup[2]);
+                                         c.dx, c.dy, sol, n, q[0], q[1], q[2]);
   return cudaGetLastError();
 }
 
@@ -307,6 +347,8 @@ cudaError_t launch_ansatz(const LaunchCtx& c, const double* d_sol, int n, cudaSt
   if (c.theory == TH_AH) return f ? ansatz_t<TH_AH, float>(c, d_sol, n, s) : ansatz_t<TH_AH, double>(c, d_sol, n, s);
   if (c.theory == TH_BEC)
     return f ? ansatz_t<TH_BEC, float>(c, d_sol, n, s) : ansatz_t<TH_BEC, double>(c, d_sol, n, s);
+  if (c.theory == TH_SID)
+    return f ? ansatz_t<TH_SID, float>(c, d_sol, n, s) : ansatz_t<TH_SID, double>(c, d_sol, n, s);
   // both unit-vector theories take the compact skyrmion
   return f ? ansatz_t<TH_CM, float>(c, d_sol, n, s) : ansatz_t<TH_CM, double>(c, d_sol, n, s);
 }
@@ -327,6 +369,7 @@ int obs_grid(int theory, int prec, int ntiles) {
   if (theory == TH_AH) occ = f ? obs_occ<TH_AH, float>() : obs_occ<TH_AH, double>();
   else if (theory == TH_CM) occ = f ? obs_occ<TH_CM, float>() : obs_occ<TH_CM, double>();
   else if (theory == TH_BS) occ = f ? obs_occ<TH_BS, float>() : obs_occ<TH_BS, double>();
+  else if (theory == TH_SID) occ = f ? obs_occ<TH_SID, float>() : obs_occ<TH_SID, double>();
   else occ = f ? obs_occ<TH_BEC, float>() : obs_occ<TH_BEC, double>();
   const int g = nsm * occ;
   return ntiles < g ? ntiles : g;

@@ -34,6 +34,7 @@ SS_ABELIAN_HIGGS = 1
 SS_CHIRAL_MAGNET = 2
 SS_BABY_SKYRME = 3
 SS_BEC = 4
+SS_SID = 5
 SS_METHOD_ANF = 0       # arrested Newton flow (default)
 SS_METHOD_GRADIENT = 1  # gradient descent phi <- phi - dtau G
 
@@ -399,14 +400,15 @@ class Solver:
                  stream=None):
         self.theory, self.nx, self.ny, self.dx, self.dy = theory, nx, ny, dx, dy
         self.precision = precision
-        self.C = {SS_ABELIAN_HIGGS: 4, SS_BEC: 2}.get(theory, 3)
+        self.C = {SS_ABELIAN_HIGGS: 4, SS_BEC: 2, SS_SID: 6}.get(theory, 3)
         self.dtype = np.float64 if precision == SS_FP64 else np.float32
         self.ctx = None
         self.ctx = ss_create_grid(nx, ny, dx, dy, precision, stream)
         try:
             ss_set_theory(self.ctx, theory, params)
         except Exception:
-            ss_destroy(self.ctx)
+            ctx, self.ctx = self.ctx, None  # the destructor must not release it again
+            ss_destroy(ctx)
             raise
 
     @property

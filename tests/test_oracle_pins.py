@@ -619,6 +619,7 @@ def test_sid_uniform_ground_state_closed_form():
     b3e = b3 - 2 * b4
     S, D = np.linalg.solve([[2 * b1, b3e], [b3e, 2 * b2]], [-a1, -a2])
     assert S == pytest.approx(1.0) and D == pytest.approx(0.75)
+    assert O.ansatz_sid(SID_PRM, [[0, 0, 0, 1.0, 0]], 8, 8, 0.3, 0.3)[1] == pytest.approx((S, D, math.pi / 2))
     nx, ny, dx, dy = 14, 12, 0.3, 0.2
     f = np.zeros((6, ny, nx))
     f[0] = math.sqrt(S)
