@@ -36,6 +36,11 @@ throughput on 2048^2 (mu = 40, Omega = 0.9, box 24 x 24) in compensated FP32, an
 the vortex-lattice relaxation of the tests (96^2, mu = 10, Omega = 0.85, to
 dx dy max|G| < 1e-4) on the GPU against the FP64 oracle on the host cores.
 
+--workload sid: the s+id two-band superconductor (Table 1; a1 = -1, a2 = -0.6, b1 = 0.5,
+b2 = 0.4, b3 = 0.3, b4 = 0.15, nu = 0.35): flow throughput on 2048^2 (dx 0.3, 64
+vortices) in compensated FP32, and a 256^2 box with 4 vortices relaxed to
+dx dy max|G| < 1e-4 on the GPU against the FP64 oracle on the host cores.
+
 --workload ah-batch: time per solve to dx dy max|G| < 1e-6 on the batched Abelian
 Higgs set (256 problems, sides 64..512, dx = 0.1, lambda ~ U[0.5, 2], N in 1..4):
 one bench step = the whole set relaxed in one batch (compensated FP32), against
@@ -753,6 +758,78 @@ def run_bec(args) -> int:
     return 0
 
 
+def run_sid(args) -> int:
+    """s+id: flow throughput and time to solution (see the module docstring)."""
+    rank, local_rank, world = D.env_rank()
+    if rank != 0:
+        return 0
+    D.pin_visible_device(local_rank, 1)
+    import numpy as np
+    import torch
+    import oracle as O
+    from paper_2603_24370_gb300 import build as B
+    from paper_2603_24370_gb300 import inputs as I
+    from paper_2603_24370_gb300 import soliton as S
+    B.build()
+    O.build()
+    S.load_library()
+    peaks, src = measured_peaks()
+    prm = (-1.0, -0.6, 0.5, 0.4, 0.3, 0.15, 0.35)
+
+    def vortices(n, dx, count, seed):
+        rng = I.SplitMix64(seed)
+        half = 0.5 * (n - 1) * dx
+        pts = I._separated_positions(rng, count, half, half, 6.0, 5.0)
+        return [(x, y, 1.0, 1.0, 0.0) for x, y in pts]
+
+    n, dx = 2048, 0.3
+    with S.Solver(S.SS_SID, prm, n, n, dx, dx, S.SS_FP32) as sv:
+        sv.init_ansatz(vortices(n, dx, 64, 20267))
+        tuned = sv.autotune(4)
+        for _ in range(args.warmup):
+            sv.step(INNER)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            sv.step(INNER)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        ms = S.ss_profile_stages(sv.ctx, 8)
+        o = sv.observables()
+    bytes6 = {1: 4 * 7 * 6, 2: 4 * 8 * 6}  # compensated FP32, C = 6
+    thr = {"site_updates_per_s": interior(n) * INNER * args.steps / sec, "pass_ms": ms, "autotuned": tuned,
+           "hbm_frac_of_measured": [bytes6[k + 1] * interior(n) / (ms[k] * 1e-3) / 1e9 / peaks["hbm_gbs"]
+                                    for k in range(2)],
+           "winding_after": o["charge"], "flux_over_2pi": o["flux"] / (2 * np.pi)}
+    m, dxm = 256, 0.3
+    vort = vortices(m, dxm, 4, 20268)
+    gpu = {}
+    for name, prec in (("fp64", S.SS_FP64), ("fp32c", S.SS_FP32)):
+        with S.Solver(S.SS_SID, prm, m, m, dxm, dxm, prec) as sv:
+            sv.init_ansatz(vort)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = sv.minimise(1e-4, 100000)
+            torch.cuda.synchronize()
+            o = sv.observables()
+            gpu[name] = {"seconds": time.perf_counter() - t0, "steps": r["steps"], "converged": bool(r["converged"]),
+                         "energy": o["energy"], "winding": o["charge"], "flux_over_2pi": o["flux"] / (2 * np.pi)}
+    f, _ = O.ansatz_sid(prm, vort, m, m, dxm, dxm)
+    t0 = time.perf_counter()
+    ref = O.minimise(5, prm, f, dxm, dxm, 1e-4, 100000)
+    osec = time.perf_counter() - t0
+    line = {"metric": "s+id: site-updates/s at 2048^2; time to dx dy max|G| < 1e-4 at 256^2", "unit": "s",
+            "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": "s+id a1=-1 a2=-0.6 b1=0.5 b2=0.4 b3=0.3 b4=0.15 nu=0.35, dx=0.3; 2048^2 with 64 "
+                                   "unit vortices (min-sep 5), 256^2 with 4", "flow_steps_per_bench_step": INNER},
+            "throughput": thr,
+            "time_to_solution": {"gpu": gpu, "oracle": {"seconds": osec, "steps": ref["steps"],
+                                                         "energy": ref["energy"], "converged": ref["converged"],
+                                                         "cores": O.num_threads(), "timed": "in full"}}}
+    print(json.dumps(line))
+    return 0
+
+
 def main() -> int:
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -761,7 +838,8 @@ def main() -> int:
     ap.add_argument("--impl", choices=("native", "reference"), default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grid", type=int, default=N, help="grid side (default: the 4096 workload; smaller for ncu)")
-    ap.add_argument("--workload", choices=("cm4096", "ah-batch", "configs", "methods", "baby-skyrme", "bec"),
+    ap.add_argument("--workload",
+                    choices=("cm4096", "ah-batch", "configs", "methods", "baby-skyrme", "bec", "sid"),
                     default="cm4096")
     ap.add_argument("--tile-shape", choices=("auto", "0", "1"), default="auto",
                     help="flow tile shape: autotuned (default) or fixed (for profiling one shape)")
@@ -784,6 +862,8 @@ def main() -> int:
         return run_baby_skyrme(args)
     if args.workload == "bec":
         return run_bec(args)
+    if args.workload == "sid":
+        return run_sid(args)
     return run_native(args)
 
 
