@@ -9,7 +9,7 @@ appearance, see ``soliton_oracle.cpp``):
 
 * ``derivatives``          -- Eq. 1, Eq. 2 and the composed mixed derivative (Sec. 3.1)
 * ``energy`` / ``energy_density`` -- E_h of Table 1 (Abelian Higgs, Baby Skyrme, BEC, s+id)
-  and Eq. 5 (chiral magnet)
+  and Eq. 5 (chiral magnet, also with the magnetostatic term of Eq. 6: ``demag_*``)
 * ``force``                -- Euler-Lagrange residual G driving Eq. 3
 * ``energy_grad_exact``    -- exact dE_h/dphi, only for pinning ``force``
 * ``anf_step`` / ``minimise`` -- arrested Newton flow, RK4 + Eq. 4 (Sec. 3.2)
@@ -35,6 +35,7 @@ CHIRAL_MAGNET = 2
 BABY_SKYRME = 3
 BEC = 4
 SID = 5
+CM_DEMAG = 6
 HARMONIC_TEST = 99
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -100,6 +101,10 @@ def _load():
             lib.or_observables.restype = None
             lib.or_ansatz.argtypes = [i, _D, i, _D, i, i, d, d]
             lib.or_ansatz_bec.argtypes = [_D, _D, i, _D, i, i, d, d]
+            lib.or_demag_potential.argtypes = [_D, i, i, d, d, _D, _D]
+            lib.or_demag_potential.restype = None
+            lib.or_demag_energy.argtypes = [_D, _D, i, i, d, d]
+            lib.or_demag_energy.restype = d
             lib.or_ansatz_sid.argtypes = [_D, _D, i, _D, i, i, d, d, _D]
             lib.or_ansatz_sid.restype = None
             lib.or_ansatz_bec.restype = None
@@ -229,6 +234,21 @@ def observables(theory: int, params, f, dx: float, dy: float) -> dict:
     _load().or_observables(theory, _p(_params(params)), _p(f), nx, ny, dx, dy, _p(out))
     return {"energy": out[0], "charge": out[1], "flux": out[2], "grad_max": out[3], "grad_max_raw": out[4],
             "norm_dev": out[5], "atoms": out[6], "angular_momentum": out[7]}
+
+
+def demag_potential(f, dx: float, dy: float):
+    """Magnetostatic charge and potential (rho, psi) of a field, Eq. 6 (see the C++)."""
+    f = _f64(f)
+    _, ny, nx = f.shape
+    rho, psi = np.zeros((ny, nx)), np.zeros((ny, nx))
+    _load().or_demag_potential(_p(f), nx, ny, dx, dy, _p(rho), _p(psi))
+    return rho, psi
+
+
+def demag_energy(params, f, dx: float, dy: float) -> float:
+    f = _f64(f)
+    _, ny, nx = f.shape
+    return _load().or_demag_energy(_p(_params(params)), _p(f), nx, ny, dx, dy)
 
 
 def ansatz_bec(params, vortices, nx: int, ny: int, dx: float, dy: float) -> np.ndarray:

@@ -43,6 +43,17 @@
 //     delta_jk and gamma^{sd}_{jk} = gamma^{ds}_{jk} = nu diag(1, -1)_{jk} (the
 //     d_{x^2-y^2} mixed gradient), unit charge D = d - i A, components
 //     (Re, Im Delta_s, Re, Im Delta_d, A_1, A_2). params = {a1, a2, b1, b2, b3, b4, nu}.
+//   * Demagnetisation (Eq. 6, the chiral magnet with demag, theory 6): with
+//     psi = phi / (mu_0 M_s) the Poisson equation reads lap psi = div n (in-plane n),
+//     discretised as L psi = rho on I: rho the Eq. 1 divergence of (n_1, n_2), L the
+//     5-point Laplacian, psi = 0 on the halo (the sites next to I are the Dirichlet
+//     boundary). Energy E_ms = 1/(2 mu_0) int |grad phi|^2 = -mu_d/2 int psi rho with
+//     mu_d = mu_0 M_s^2, discretised as -mu_d/2 dx dy sum_I psi rho, whose exact lattice
+//     gradient is mu_d dx dy (Eq. 1 gradient of psi) because L is symmetric and Eq. 1
+//     antisymmetric: the force is G_cm + mu_d (d_1 psi, d_2 psi, 0), then projected.
+//     Within a flow step psi is solved once, for the step's starting field, and held
+//     through the RK stages; every energy uses the psi of its own field.
+//     params = {J, D, K, h, dmi_type, mu_d}.
 //   * Arrest compares potential energies with a strict '>' (Eq. 4).
 //   * Convergence measure: max over I and components of |dx dy G|.
 #include <cmath>
@@ -58,10 +69,12 @@ namespace {
 const double PI = 3.14159265358979323846;
 
 enum { TH_ABELIAN_HIGGS = 1, TH_CHIRAL_MAGNET = 2, TH_BABY_SKYRME = 3, TH_BEC = 4, TH_SID = 5,
-       TH_HARMONIC_TEST = 99 };
+       TH_CM_DEMAG = 6, TH_HARMONIC_TEST = 99 };
 
 // Theories whose field is a unit 3-vector (normalised after every update).
-bool unit_vector(int theory) { return theory == TH_CHIRAL_MAGNET || theory == TH_BABY_SKYRME; }
+bool unit_vector(int theory) {
+  return theory == TH_CHIRAL_MAGNET || theory == TH_BABY_SKYRME || theory == TH_CM_DEMAG;
+}
 
 struct Grid {
   int nx, ny;
@@ -77,6 +90,7 @@ int ncomp(int theory) {
     case TH_BABY_SKYRME: return 3;     // m_1, m_2, m_3 (Table 1)
     case TH_BEC: return 2;             // Re psi, Im psi (Table 1)
     case TH_SID: return 6;             // Delta_s, Delta_d (Re, Im), A_1, A_2 (Table 1)
+    case TH_CM_DEMAG: return 3;        // n (Eq. 5 with the magnetostatic term)
     case TH_HARMONIC_TEST: return 1;   // scalar test field
     default: return 0;
   }
@@ -276,6 +290,7 @@ double density(int theory, const double* prm, const Site& s) {
   switch (theory) {
     case TH_ABELIAN_HIGGS: return density_ah(prm, s);
     case TH_CHIRAL_MAGNET: return density_cm(prm, s);
+    case TH_CM_DEMAG: return density_cm(prm, s);  // local part; E_ms is added over the lattice
     case TH_BABY_SKYRME: return density_bs(prm, s);
     case TH_BEC: return density_bec(prm, s);
     case TH_SID: return density_sid(prm, s);
@@ -306,8 +321,10 @@ void force_ah(const double* prm, const Site& s, double G[4]) {
 }
 
 // Chiral magnet: delta E / delta n = -J lap n - 2 D sum_i d_i x d_i n - 2 K n_3 e_3 - h e_3,
-// then the tangent projection G <- G - (G . n) n that keeps |n| = 1 (Sec. 3.2).
-void force_cm(const double* prm, const Site& s, double G[3]) {
+// then the tangent projection G <- G - (G . n) n that keeps |n| = 1 (Sec. 3.2). With
+// demagnetisation, mu_d (d_1 psi, d_2 psi, 0) is added before the projection (psi_g:
+// the Eq. 1 gradient of the magnetostatic potential at the site, else NULL).
+void force_cm(const double* prm, const Site& s, double G[3], const double* psi_g = nullptr) {
   const double J = prm[0], D = prm[1], K = prm[2], h = prm[3];
   double dv1[3], dv2[3];
   dmi_vectors((int)prm[4], dv1, dv2);
@@ -318,6 +335,10 @@ void force_cm(const double* prm, const Site& s, double G[3]) {
   cross(dv2, ny_, c2);
   for (int a = 0; a < 3; ++a) G[a] = -J * (s.fxx[a] + s.fyy[a]) - 2.0 * D * (c1[a] + c2[a]);
   G[2] += -2.0 * K * s.v[2] - h;
+  if (psi_g) {
+    G[0] += prm[5] * psi_g[0];
+    G[1] += prm[5] * psi_g[1];
+  }
   const double n[3] = {s.v[0], s.v[1], s.v[2]};
   const double gn = dot3(G, n);
   for (int a = 0; a < 3; ++a) G[a] -= gn * n[a];
@@ -430,7 +451,7 @@ void partials(int theory, const double* prm, const Site& s, double dv[6], double
     dv[1] = A1 * X1 + A2 * X2 - 0.5 * lam * w * p2;
     dv[2] = X1 * p2 - Y1 * p1;
     dv[3] = X2 * p2 - Y2 * p1;
-  } else if (theory == TH_CHIRAL_MAGNET) {
+  } else if (theory == TH_CHIRAL_MAGNET || theory == TH_CM_DEMAG) {  // demag part added over the lattice
     const double J = prm[0], D = prm[1], K = prm[2], h = prm[3];
     double dv1[3], dv2[3];
     dmi_vectors((int)prm[4], dv1, dv2);
@@ -500,6 +521,71 @@ void partials(int theory, const double* prm, const Site& s, double dv[6], double
   }
 }
 
+// ---------------------------------------------------------------- demagnetisation
+// Magnetostatic charge rho = d_1 n_1 + d_2 n_2 (Eq. 1) on I, zero elsewhere.
+void demag_charge(const double* f, const Grid& g, double* rho) {
+  std::memset(rho, 0, sizeof(double) * g.plane());
+  for (int j = 2; j <= g.ny - 3; ++j)
+    for (int i = 2; i <= g.nx - 3; ++i) rho[(size_t)j * g.nx + i] = d1x(f, g, i, j) + d1y(f + g.plane(), g, i, j);
+}
+
+// Solve L psi = rho on I (5-point Laplacian, psi = 0 off I) by the sine transform that
+// diagonalises L: interior index i' = i - 1 = 1..Nx (i' = 0 and Nx + 1 are the zero
+// boundary), L sin(pi k i'/(Nx+1)) sin(pi l j'/(Ny+1)) = lambda_kl (same mode),
+//   lambda_kl = -(2 - 2 cos(pi k/(Nx+1)))/dx^2 - (2 - 2 cos(pi l/(Ny+1)))/dy^2,
+// with the transform written out as plain sums (test sizes only).
+void demag_potential(const double* f, const Grid& g, double* psi) {
+  const int Nx = g.nx - 4, Ny = g.ny - 4;
+  std::vector<double> rho(g.plane());
+  demag_charge(f, g, rho.data());
+  std::vector<double> sx((size_t)Nx * Nx), sy((size_t)Ny * Ny);
+  for (int k = 1; k <= Nx; ++k)
+    for (int i = 1; i <= Nx; ++i) sx[(size_t)(k - 1) * Nx + (i - 1)] = std::sin(PI * k * i / (Nx + 1));
+  for (int l = 1; l <= Ny; ++l)
+    for (int j = 1; j <= Ny; ++j) sy[(size_t)(l - 1) * Ny + (j - 1)] = std::sin(PI * l * j / (Ny + 1));
+  auto at = [&](int ip, int jp) { return (size_t)(jp + 1) * g.nx + (ip + 1); };  // i', j' >= 1
+  std::vector<double> a((size_t)Nx * Ny), b((size_t)Nx * Ny);
+  for (int jp = 1; jp <= Ny; ++jp)  // along x
+    for (int k = 1; k <= Nx; ++k) {
+      double acc = 0.0;
+      for (int ip = 1; ip <= Nx; ++ip) acc += sx[(size_t)(k - 1) * Nx + (ip - 1)] * rho[at(ip, jp)];
+      a[(size_t)(jp - 1) * Nx + (k - 1)] = acc;
+    }
+  for (int l = 1; l <= Ny; ++l)  // along y, then divide by the eigenvalue
+    for (int k = 1; k <= Nx; ++k) {
+      double acc = 0.0;
+      for (int jp = 1; jp <= Ny; ++jp) acc += sy[(size_t)(l - 1) * Ny + (jp - 1)] * a[(size_t)(jp - 1) * Nx + (k - 1)];
+      const double lam = -(2.0 - 2.0 * std::cos(PI * k / (Nx + 1))) / (g.dx * g.dx) -
+                         (2.0 - 2.0 * std::cos(PI * l / (Ny + 1))) / (g.dy * g.dy);
+      b[(size_t)(l - 1) * Nx + (k - 1)] = acc / lam;
+    }
+  const double norm = (2.0 / (Nx + 1)) * (2.0 / (Ny + 1));
+  for (int jp = 1; jp <= Ny; ++jp)  // inverse along y
+    for (int k = 1; k <= Nx; ++k) {
+      double acc = 0.0;
+      for (int l = 1; l <= Ny; ++l) acc += sy[(size_t)(l - 1) * Ny + (jp - 1)] * b[(size_t)(l - 1) * Nx + (k - 1)];
+      a[(size_t)(jp - 1) * Nx + (k - 1)] = acc;
+    }
+  std::memset(psi, 0, sizeof(double) * g.plane());
+  for (int jp = 1; jp <= Ny; ++jp)  // inverse along x
+    for (int ip = 1; ip <= Nx; ++ip) {
+      double acc = 0.0;
+      for (int k = 1; k <= Nx; ++k) acc += sx[(size_t)(k - 1) * Nx + (ip - 1)] * a[(size_t)(jp - 1) * Nx + (k - 1)];
+      psi[at(ip, jp)] = norm * acc;
+    }
+}
+
+// E_ms = -mu_d/2 dx dy sum_I psi rho.
+double demag_energy(const double* prm, const double* f, const Grid& g) {
+  std::vector<double> rho(g.plane()), psi(g.plane());
+  demag_charge(f, g, rho.data());
+  demag_potential(f, g, psi.data());
+  Neumaier acc;
+  for (int j = 2; j <= g.ny - 3; ++j)
+    for (int i = 2; i <= g.nx - 3; ++i) acc.add(psi[(size_t)j * g.nx + i] * rho[(size_t)j * g.nx + i]);
+  return -0.5 * prm[5] * g.dx * g.dy * acc.value();
+}
+
 // ---------------------------------------------------------------- lattice sums
 double energy(int theory, const double* prm, const double* f, const Grid& g) {
   const int C = ncomp(theory);
@@ -510,18 +596,33 @@ double energy(int theory, const double* prm, const double* f, const Grid& g) {
   Neumaier acc;
   for (int j = 2; j <= g.ny - 3; ++j)
     for (int i = 2; i <= g.nx - 3; ++i) acc.add(e[(size_t)j * g.nx + i]);
-  return g.dx * g.dy * acc.value();
+  const double E = g.dx * g.dy * acc.value();
+  return theory == TH_CM_DEMAG ? E + demag_energy(prm, f, g) : E;
 }
 
-// G on I, zero on the halo.
-void force(int theory, const double* prm, const double* f, const Grid& g, double* G) {
+// G on I, zero on the halo. Demagnetisation: with the potential psi_in if given (the
+// step's held potential), else the potential of f itself.
+void force(int theory, const double* prm, const double* f, const Grid& g, double* G, const double* psi_in = nullptr) {
   const int C = ncomp(theory);
   std::memset(G, 0, sizeof(double) * C * g.plane());
+  std::vector<double> psi_own;
+  const double* psi = psi_in;
+  if (theory == TH_CM_DEMAG && !psi) {
+    psi_own.resize(g.plane());
+    demag_potential(f, g, psi_own.data());
+    psi = psi_own.data();
+  }
 #pragma omp parallel for schedule(static)
   for (int j = 2; j <= g.ny - 3; ++j)
     for (int i = 2; i <= g.nx - 3; ++i) {
       double Gs[6];
-      force_site(theory, prm, gather(f, C, g, i, j, true), Gs);
+      const Site st = gather(f, C, g, i, j, true);
+      if (theory == TH_CM_DEMAG) {
+        const double pg[2] = {d1x(psi, g, i, j), d1y(psi, g, i, j)};
+        force_cm(prm, st, Gs, pg);
+      } else {
+        force_site(theory, prm, st, Gs);
+      }
       for (int c = 0; c < C; ++c) G[c * g.plane() + (size_t)j * g.nx + i] = Gs[c];
     }
 }
@@ -607,6 +708,17 @@ void or_force(int theory, const double* prm, const double* f, int nx, int ny, do
   force(theory, prm, f, Grid{nx, ny, dx, dy}, G);
 }
 
+// Demagnetisation: the magnetostatic charge rho and potential psi of a field (both
+// [ny][nx], zero off I), and E_ms alone (prm as for the chiral magnet with demag).
+void or_demag_potential(const double* f, int nx, int ny, double dx, double dy, double* rho, double* psi) {
+  const Grid g{nx, ny, dx, dy};
+  demag_charge(f, g, rho);
+  demag_potential(f, g, psi);
+}
+double or_demag_energy(const double* prm, const double* f, int nx, int ny, double dx, double dy) {
+  return demag_energy(prm, f, Grid{nx, ny, dx, dy});
+}
+
 // Exact gradient dE_h/dphi of the lattice energy (adjoint of Eq. 1), no projection.
 // Used only to pin G; footprint 9x9 instead of G's 5x5.
 void or_energy_grad_exact(int theory, const double* prm, const double* f, int nx, int ny, double dx, double dy,
@@ -630,6 +742,20 @@ void or_energy_grad_exact(int theory, const double* prm, const double* f, int nx
         }
       }
     }
+  if (theory == TH_CM_DEMAG) {
+    // d E_ms / d n = mu_d dx dy (Eq. 1 gradient of psi) at every site, the halo included
+    // (the charges on I see the halo's in-plane values), psi taken as zero off the array
+    std::vector<double> psi(g.plane());
+    demag_potential(f, g, psi.data());
+    auto ps = [&](int i, int j) { return (i < 0 || i >= nx || j < 0 || j >= ny) ? 0.0 : psi[(size_t)j * nx + i]; };
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        const double gx = (-ps(i + 2, j) + 8.0 * ps(i + 1, j) - 8.0 * ps(i - 1, j) + ps(i - 2, j)) / (12.0 * dx);
+        const double gy = (-ps(i, j + 2) + 8.0 * ps(i, j + 1) - 8.0 * ps(i, j - 1) + ps(i, j - 2)) / (12.0 * dy);
+        grad[(size_t)j * nx + i] += A * prm[5] * gx;
+        grad[P + (size_t)j * nx + i] += A * prm[5] * gy;
+      }
+  }
 }
 
 // One arrested-Newton-flow step (Eq. 3, Eq. 4) by classic RK4 on the first-order
@@ -652,9 +778,14 @@ int or_anf_step(int theory, const double* prm, double* f, double* v, int nx, int
   // v and every G vanish on the halo, so every k_phi and k_v does too and the halo
   // stays fixed without special cases.
   std::vector<double> k1p(N), k1v(N), k2p(N), k2v(N), k3p(N), k3v(N), k4p(N), k4v(N), y(N);
+  std::vector<double> psi;  // demagnetisation: the potential of phi^n, held through the stages
+  if (theory == TH_CM_DEMAG) {
+    psi.resize(g.plane());
+    demag_potential(f, g, psi.data());
+  }
   auto kv_at = [&](std::vector<double>& kv) {  // k_v = -G(y)
     if (cm) normalise(y.data(), g);
-    force(theory, prm, y.data(), g, kv.data());
+    force(theory, prm, y.data(), g, kv.data(), psi.empty() ? nullptr : psi.data());
     for (size_t k = 0; k < N; ++k) kv[k] = -kv[k];
   };
   // k1
@@ -729,7 +860,7 @@ int or_gd_step(int theory, const double* prm, double* f, int nx, int ny, double 
   const int C = ncomp(theory);
   const size_t N = (size_t)C * g.plane();
   std::vector<double> G(N);
-  force(theory, prm, f, g, G.data());  // zero on the halo
+  force(theory, prm, f, g, G.data());  // zero on the halo (demagnetisation: psi of phi^n)
   for (size_t k = 0; k < N; ++k) f[k] -= dtau * G[k];
   if (unit_vector(theory)) normalise(f, g);
   const double E_new = energy(theory, prm, f, g);

@@ -43,6 +43,7 @@ CHIRAL_MAGNET = 2
 BABY_SKYRME = 3
 BEC = 4
 SID = 5
+CM_DEMAG = 6
 
 # Couplings of the workloads. Abelian Higgs: (lambda, u). Chiral magnet:
 # (J, D, K, h, dmi_type) with interfacial DMI (type 0).
@@ -188,7 +189,7 @@ def smooth_field(theory: int, nx: int, ny: int, dx: float, dy: float, seed: int,
         return np.stack([env * (1.0 + bumpsum()), env * bumpsum()])
     if theory == SID:
         return np.stack([1.0 + bumpsum(), bumpsum(), 0.5 + bumpsum(), 0.5 + bumpsum(), bumpsum(), bumpsum()])
-    if theory in (CHIRAL_MAGNET, BABY_SKYRME):
+    if theory in (CHIRAL_MAGNET, BABY_SKYRME, CM_DEMAG):
         T = 0.6 + 3.0 * bumpsum()
         P = 5.0 * bumpsum()
         return np.stack([np.sin(T) * np.cos(P), np.sin(T) * np.sin(P), np.cos(T)])

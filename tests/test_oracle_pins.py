@@ -24,6 +24,8 @@ BEC = O.BEC
 BEC_PRM = (1.3, 0.6, 2.0)  # g, Omega, mu
 SID = O.SID
 SID_PRM = (-1.0, -0.6, 0.5, 0.4, 0.3, 0.15, 0.35)  # a1, a2, b1, b2, b3, b4, nu
+CMD = O.CM_DEMAG
+CMD_PRM = (1.0, 0.8, 0.15, 0.5, 0.0, 0.7)  # J, D, K, h, dmi_type, mu_d
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_constants.json")
 AH_PRM = (1.0, 1.0)
 CM_PRM = (1.0, 1.0, 0.1, 0.6, 0.0)
@@ -633,12 +635,70 @@ def test_sid_uniform_ground_state_closed_form():
     assert O.energy(SID, SID_PRM, g, dx, dy) > O.energy(SID, SID_PRM, f, dx, dy) + area * 4 * b4 * S * D * 0.99
 
 
+# ---------------------------------------------------------------- demagnetisation (Eq. 6)
+def test_demag_energy_of_a_single_mode_is_the_discrete_closed_form():
+    """n_1 = a cos(k x') sin(q y'), measured from the zero boundary nodes next to I
+    (x' = (i - 1) dx), with k, q fitting the box: the Eq. 1 divergence is the pure mode
+    -a s1 sin(k x') sin(q y') (s1 the Eq. 1 symbol), the 5-point Laplacian multiplies it by
+    lambda = -(2 - 2 cos k dx)/dx^2 - (2 - 2 cos q dy)/dy^2, so
+    E_ms = -mu_d/2 dx dy sum_I rho^2 / lambda exactly."""
+    nx, ny, dx, dy = 30, 24, 0.3, 0.25
+    X, Y = np.meshgrid((np.arange(nx) - 1) * dx, (np.arange(ny) - 1) * dy)
+    Lx, Ly = (nx - 3) * dx, (ny - 3) * dy
+    a, k, q = 0.4, 2 * math.pi / Lx, math.pi / Ly
+    f = np.zeros((3, ny, nx))
+    f[0] = a * np.cos(k * X) * np.sin(q * Y)
+    s1 = (8 * math.sin(k * dx) - math.sin(2 * k * dx)) / (6 * dx)
+    lam = -(2 - 2 * math.cos(k * dx)) / dx ** 2 - (2 - 2 * math.cos(q * dy)) / dy ** 2
+    rho = -a * s1 * np.sin(k * X) * np.sin(q * Y)
+    sl = (slice(2, ny - 2), slice(2, nx - 2))
+    exp = -0.5 * CMD_PRM[5] * dx * dy * (rho[sl] ** 2).sum() / lam
+    assert O.demag_energy(CMD_PRM, f, dx, dy) == pytest.approx(exp, rel=1e-13)
+    r, psi = O.demag_potential(f, dx, dy)
+    np.testing.assert_allclose(r[sl], rho[sl], rtol=0, atol=1e-14)
+    np.testing.assert_allclose(psi[sl], rho[sl] / lam, rtol=0, atol=1e-14)
+
+
+def test_demag_potential_solves_the_five_point_poisson_problem():
+    """On a general field the sine-transform solution satisfies the 5-point stencil
+    equation L psi = rho on I directly, with psi = 0 on the halo, and E_ms > 0."""
+    nx, ny, dx, dy = 33, 27, 0.3, 0.25
+    f = I.smooth_field(CM, nx, ny, dx, dy, seed=19)
+    rho, psi = O.demag_potential(f, dx, dy)
+    sl = (slice(2, ny - 2), slice(2, nx - 2))
+    L = np.zeros_like(psi)
+    L[1:-1, 1:-1] = ((psi[1:-1, 2:] - 2 * psi[1:-1, 1:-1] + psi[1:-1, :-2]) / dx ** 2 +
+                     (psi[2:, 1:-1] - 2 * psi[1:-1, 1:-1] + psi[:-2, 1:-1]) / dy ** 2)
+    np.testing.assert_allclose(L[sl], rho[sl], rtol=0, atol=1e-12 * np.abs(rho).max())
+    assert not psi[:2].any() and not psi[-2:].any() and not psi[:, :2].any() and not psi[:, -2:].any()
+    assert O.demag_energy(CMD_PRM, f, dx, dy) > 0.0
+    assert O.energy(CMD, CMD_PRM, f, dx, dy) == pytest.approx(
+        O.energy(CM, CMD_PRM[:5], f, dx, dy) + O.demag_energy(CMD_PRM, f, dx, dy), rel=1e-14)
+
+
+def test_demag_spares_bloch_and_charges_neel_skyrmions():
+    """The magnetostatic energy comes from the in-plane divergence: a Bloch skyrmion
+    (helicity pi/2, divergence-free) has none beyond the stencils' O(h^4) remainder,
+    a Neel one (helicity 0, radial in-plane part) a finite amount."""
+    e = {}
+    for n in (61, 121):
+        d = 16.0 / (n - 1)
+        X, Y = grid(n, n, d, d)
+        fr = np.pi * np.exp(-(np.hypot(X, Y) / 2.0) ** 2)
+        for gam in (0.0, np.pi / 2):
+            th = np.arctan2(Y, X) + gam
+            ff = np.stack([np.sin(fr) * np.cos(th), np.sin(fr) * np.sin(th), np.cos(fr)])
+            e[(n, gam)] = O.demag_energy(CMD_PRM, ff, d, d)
+    assert e[(121, 0.0)] == pytest.approx(e[(61, 0.0)], rel=1e-2) and e[(121, 0.0)] > 1.0
+    assert e[(61, np.pi / 2)] < 1e-6 * e[(61, 0.0)] and e[(121, np.pi / 2)] < 1e-2 * e[(61, np.pi / 2)]
+
+
 # ---------------------------------------------------------------- force (Eq. 3's right-hand side)
 def _prm(theory):
-    return {AH: AH_PRM, CM: (1.0, 0.8, 0.15, 0.5, 0.0), BS: BS_PRM, BEC: BEC_PRM, SID: SID_PRM}[theory]
+    return {AH: AH_PRM, CM: (1.0, 0.8, 0.15, 0.5, 0.0), BS: BS_PRM, BEC: BEC_PRM, SID: SID_PRM, CMD: CMD_PRM}[theory]
 
 
-@pytest.mark.parametrize("theory", [AH, CM, BS, BEC, SID])
+@pytest.mark.parametrize("theory", [AH, CM, BS, BEC, SID, CMD])
 def test_exact_gradient_matches_brute_force(theory):
     nx, ny, dx, dy = 12, 11, 0.3, 0.25
     prm = _prm(theory)
@@ -654,7 +714,7 @@ def test_exact_gradient_matches_brute_force(theory):
     np.testing.assert_allclose(grad, fd, rtol=0, atol=1e-7 * np.abs(grad).max())
 
 
-@pytest.mark.parametrize("theory", [AH, CM, BS, BEC, SID])
+@pytest.mark.parametrize("theory", [AH, CM, BS, BEC, SID, CMD])
 def test_force_is_energy_gradient_to_fourth_order(theory):
     """dx dy G and dE_h/dphi (tangent part for the unit-vector theories) are two O(h^4)
     discretisations of the same Euler-Lagrange expression: their gap shrinks ~16x per halving."""
@@ -668,7 +728,7 @@ def test_force_is_energy_gradient_to_fourth_order(theory):
         f = I.smooth_field(theory, n, n, dx, dy, seed=7, amplitude=0.15 if theory == BS else 0.3)
         G = O.force(theory, prm, f, dx, dy)
         gr = O.energy_grad_exact(theory, prm, f, dx, dy) / (dx * dy)
-        if theory in (CM, BS):
+        if theory in (CM, BS, CMD):
             gr = gr - (gr * f).sum(axis=0, keepdims=True) * f
         k = 4 if n == 41 else 8  # same physical margin on both grids
         errs.append(np.abs(G - gr)[:, k:-k, k:-k].max() / np.abs(G).max())
