@@ -62,7 +62,12 @@ extern "C" {
 
 /* ---- theories ---- */
 #define SS_ABELIAN_HIGGS 1 /* Table 1, params {lambda, u}                                */
-#define SS_CHIRAL_MAGNET 2 /* Eq. 5 without demag, params {J, D, K, h, dmi_type}:       */
+#define SS_CHIRAL_MAGNET 2 /* Eq. 5, params {J, D, K, h[, dmi_type[, mu_d]]}:             */
+                           /* mu_d = mu_0 M_s^2 > 0 adds demagnetisation (Eq. 6): the      */
+                           /* potential psi (lap psi = div n, 5-point Laplacian, psi = 0   */
+                           /* on the halo) is solved by a sine transform once per step and */
+                           /* adds -mu_d/2 psi div n to the energy, mu_d grad psi to the   */
+                           /* force (single-grid contexts only);                           */
                            /* dmi_type 0 interfacial (d_i = e_3 x e_i), 1 bulk (d_i = e_i),*/
                            /* 2 D_2d "Heusler" (d_1 = e_1, d_2 = -e_2)                     */
 #define SS_BABY_SKYRME 3   /* Table 1, params {kappa, mu[, nu]}: unit 3-vector m with       */
@@ -164,7 +169,7 @@ int ss_create_grid(ss_ctx** out, int nx, int ny, double dx, double dy, int preci
 /* Select the theory and its couplings (Sec. 3.1 "theory-specific parameters packed
  * into device arrays"; Table 1; Eq. 5). params is a host array of n_params
  * doubles: Abelian Higgs {lambda, u} (u defaults to 1 if n_params == 1); chiral
- * magnet {J, D, K, h, dmi_type} (dmi_type defaults to 0 if n_params == 4); Baby
+ * magnet {J, D, K, h, dmi_type, mu_d} (dmi_type and mu_d default to 0); Baby
  * Skyrme {kappa, mu, nu} (nu defaults to 0 if n_params == 2); BEC {g, Omega, mu}
  * with g > 0 (the BEC's charge observable is 0: see atoms, angular_momentum); s+id
  * {a1, a2, b1, b2, b3, b4, nu} (see SS_SID for the constraints).

@@ -58,9 +58,9 @@ namespace {
 
 // Couplings of Table 1 / Eq. 5 packed as the kernels read them (Couplings in
 // ss_device.cuh). Returns SS_OK or an error code (message set).
-int pack_couplings(int theory, const double* params, int n_params, double k[10], int* C) {
+int pack_couplings(int theory, const double* params, int n_params, double k[NCOUP], int* C) {
   if (!params && n_params > 0) return fail(SS_ERR_ARG, "params is NULL");
-  for (int i = 0; i < 10; ++i) k[i] = 0.0;
+  for (int i = 0; i < NCOUP; ++i) k[i] = 0.0;
   if (theory == SS_ABELIAN_HIGGS) {
     if (n_params < 1 || n_params > 2) return fail(SS_ERR_ARG, "Abelian Higgs takes {lambda[, u]}");
     const double lam = params[0], u = n_params > 1 ? params[1] : 1.0;
@@ -69,7 +69,8 @@ int pack_couplings(int theory, const double* params, int n_params, double k[10],
     k[1] = u * u;
     *C = 4;
   } else if (theory == SS_CHIRAL_MAGNET) {
-    if (n_params < 4 || n_params > 5) return fail(SS_ERR_ARG, "chiral magnet takes {J, D, K, h[, dmi_type]}");
+    if (n_params < 4 || n_params > 6)
+      return fail(SS_ERR_ARG, "chiral magnet takes {J, D, K, h[, dmi_type[, mu_d]]}");
     for (int i = 0; i < n_params; ++i)
       if (!std::isfinite(params[i])) return fail(SS_ERR_ARG, "chiral-magnet parameters must be finite");
     if (!(params[0] > 0.0)) return fail(SS_ERR_ARG, "J must be > 0");
@@ -81,6 +82,10 @@ int pack_couplings(int theory, const double* params, int n_params, double k[10],
     if (type == 0) { k[5] = 1.0; k[7] = -1.0; }      // d_i = e_3 x e_i
     else if (type == 1) { k[4] = 1.0; k[8] = 1.0; }  // d_i = e_i
     else { k[4] = 1.0; k[8] = -1.0; }                // d_1 = e_1, d_2 = -e_2
+    if (n_params > 5) {  // demagnetisation (Eq. 6), mu_d = mu_0 M_s^2 in the energy's units
+      if (!(params[5] >= 0.0)) return fail(SS_ERR_ARG, "mu_d must be >= 0");
+      k[10] = params[5];
+    }
     *C = 3;
   } else if (theory == SS_SID) {
     if (n_params != 7) return fail(SS_ERR_ARG, "s+id takes {a1, a2, b1, b2, b3, b4, nu}");
@@ -116,7 +121,8 @@ int pack_couplings(int theory, const double* params, int n_params, double k[10],
   return SS_OK;
 }
 
-// Kernel theory tag of an SS_* theory code.
+// Kernel theory tag of an SS_* theory code (the chiral magnet with mu_d > 0 runs the
+// demagnetisation kernels: th_of_coup).
 int th_of(int theory) {
   switch (theory) {
     case SS_ABELIAN_HIGGS: return TH_AH;
@@ -126,6 +132,7 @@ int th_of(int theory) {
     default: return TH_BEC;
   }
 }
+int th_of_coup(int theory, const double* k) { return theory == SS_CHIRAL_MAGNET && k[10] > 0.0 ? TH_CMD : th_of(theory); }
 
 int check_grid(int nx, int ny, double dx, double dy) {
   if (nx < 5 || ny < 5) return fail(SS_ERR_ARG, "nx and ny must be >= 5 (halo of width 2 on each side)");
@@ -160,13 +167,14 @@ struct Problem {
   int nx = 0, ny = 0;
   double dx = 0, dy = 0, dt = 0;
   double tau = 0;  // gradient-descent step
-  double coup[10] = {0};
+  double coup[NCOUP] = {0};
   size_t plane = 0;
   int ntx = 0, ntiles = 0, tile0 = 0;
   void* phi[2] = {nullptr, nullptr};
   void* lo[2] = {nullptr, nullptr};
   void* v[2] = {nullptr, nullptr};
   void* kv[2] = {nullptr, nullptr};
+  void* psi[2] = {nullptr, nullptr};  // demagnetisation: the potential of phi[0], phi[1]
 };
 
 template <typename R>
@@ -183,6 +191,7 @@ ProbDesc<R> make_desc(const Problem& p, DevState* st, FlowPartial* part) {
     d.lo[i] = static_cast<R*>(p.lo[i]);
     d.v[i] = static_cast<R*>(p.v[i]);
     d.kv[i] = static_cast<R*>(p.kv[i]);
+    d.psi[i] = static_cast<R*>(p.psi[i]);
   }
   d.dt = (R)p.dt;
   d.tau = (R)p.tau;
@@ -193,7 +202,7 @@ ProbDesc<R> make_desc(const Problem& p, DevState* st, FlowPartial* part) {
   d.h.i12dx2 = (R)(1.0 / (12.0 * p.dx * p.dx));
   d.h.i12dy2 = (R)(1.0 / (12.0 * p.dy * p.dy));
   d.h.i144dxdy = (R)(1.0 / (144.0 * p.dx * p.dy));
-  for (int i = 0; i < 10; ++i) d.k.c[i] = (R)p.coup[i];
+  for (int i = 0; i < NCOUP; ++i) d.k.c[i] = (R)p.coup[i];
   d.area = p.dx * p.dy;
   d.st = st;
   d.part = part;
@@ -223,6 +232,8 @@ struct ss_batch {
   int* d_active = nullptr;
   BatchLaunch BL{};
   int method = METHOD_ANF;      // SS_METHOD_ANF / SS_METHOD_GRADIENT
+  bool demag = false;           // chiral magnet with demagnetisation (single problem)
+  DemagSolver* ds = nullptr;
   cudaGraphExec_t chunk = nullptr;  // K_CHUNK steps of the current method
   DevState* h_st = nullptr;  // pinned [n]
   int* h_active = nullptr;   // pinned [2]
@@ -239,6 +250,7 @@ void batch_free(ss_batch* b) {
   if (!b) return;
   if (b->stream) cudaStreamSynchronize(b->stream);
   if (b->chunk) cudaGraphExecDestroy(b->chunk);
+  if (b->ds) demag_destroy(b->ds);
   if (b->base) cudaFree(b->base);
   if (b->d_sol) cudaFree(b->d_sol);
   if (b->h_st) cudaFreeHost(b->h_st);
@@ -287,7 +299,7 @@ int batch_layout(ss_batch* b, int ts, const int* blocks) {
   b->BL.ts = ts;
   // a batch of one passes its descriptor to the pass kernels by value
   b->BL.one = n == 1 ? static_cast<const void*>(b->one_desc.data()) : nullptr;
-  const int th = th_of(b->theory);
+  const int th = (b->demag ? TH_CMD : th_of(b->theory));
   flow_grid(th, b->prec, ts, total, n == 1, b->BL.flow_blocks);
   if (blocks) {
     if (b->method == METHOD_GD) b->BL.flow_blocks[2] = blocks[0] < total ? blocks[0] : total;
@@ -309,11 +321,12 @@ int batch_alloc(ss_batch* b) {
   const int nbuf = 6 + (b->prec == SS_FP32 ? 2 : 0);
   size_t bytes = 0;
   int total_tiles = 0, obs_need = 1;
-  const int th = th_of(b->theory);
+  const int th = (b->demag ? TH_CMD : th_of(b->theory));
   for (Problem& p : b->probs) {
     p.plane = (size_t)p.nx * p.ny;
     total_tiles += ((p.nx + tx - 1) / tx) * ((p.ny + ty - 1) / ty);
     bytes += nbuf * align256((size_t)b->C * p.plane * b->elem);
+    if (b->demag) bytes += 2 * align256(p.plane * b->elem);
     const int otiles = ((p.nx + TX - 1) / TX) * ((p.ny + TY - 1) / TY);
     const int og = obs_grid(th, b->prec, otiles);
     if (og > obs_need) obs_need = og;
@@ -340,6 +353,11 @@ int batch_alloc(ss_batch* b) {
       *slots[i] = q;
       q += pb;
     }
+    if (b->demag)
+      for (int k = 0; k < 2; ++k) {
+        p.psi[k] = q;
+        q += align256(p.plane * b->elem);
+      }
   }
   b->desc = q;
   q += desc_b;
@@ -364,10 +382,23 @@ int batch_alloc(ss_batch* b) {
   SS_CK(cudaMallocHost(&b->h_st, sizeof(DevState) * n));
   SS_CK(cudaMallocHost(&b->h_active, sizeof(int) * 2));
   for (int i = 0; i < 2; ++i) SS_CK(cudaEventCreateWithFlags(&b->ev[i], cudaEventDisableTiming));
+  if (b->demag) {
+    const Problem& p = b->probs[0];
+    const int dr = demag_create(&b->ds, p.nx, p.ny, p.dx, p.dy, b->prec == SS_FP64 ? PREC_F64 : PREC_F32);
+    if (dr != 0)
+      return fail(dr == -1 ? SS_ERR_NOMEM : SS_ERR_CUDA, "demagnetisation solver: allocation or transform plan failed");
+  }
   SS_CK(launch_reset_states(b->st, n, b->stream));
   SS_CK(cudaStreamSynchronize(b->stream));
   b->fields_set.assign(n, 0);
   return SS_OK;
+}
+
+// Demagnetisation: the potential of the current field (a no-op without demag).
+cudaError_t demag_refresh(ss_batch* b) {
+  if (!b->demag) return cudaSuccess;
+  const Problem& p = b->probs[0];
+  return demag_solve(b->ds, b->st, p.phi, p.lo, p.psi, b->stream);
 }
 
 // Launch view of one problem for the per-problem kernels (ansatz, observables);
@@ -375,7 +406,7 @@ int batch_alloc(ss_batch* b) {
 LaunchCtx problem_ctx(const ss_batch* b, int i, int cur) {
   const Problem& p = b->probs[i];
   LaunchCtx L{};
-  L.theory = th_of(b->theory);
+  L.theory = (b->demag ? TH_CMD : th_of(b->theory));
   L.prec = b->prec;
   L.nx = p.nx;
   L.ny = p.ny;
@@ -389,6 +420,7 @@ LaunchCtx problem_ctx(const ss_batch* b, int i, int cur) {
     L.lo[k] = p.lo[k ^ cur];
     L.v[k] = p.v[k ^ cur];
     L.kv[k] = p.kv[k];
+    L.psi[k] = p.psi[k ^ cur];
   }
   L.st = b->st + i;
   L.opart = b->opart;
@@ -416,6 +448,7 @@ int problem_new_fields(ss_batch* b, int i) {
     if (p.lo[k]) SS_CK(cudaMemsetAsync(p.lo[k], 0, bytes, b->stream));
   }
   SS_CK(launch_reset_states(b->st + i, 1, b->stream));
+  SS_CK(demag_refresh(b));  // the potential of the new field (step count 0: buffer 0)
   b->fields_set[i] = 1;
   return SS_OK;
 }
@@ -455,9 +488,11 @@ int ensure_chunk(ss_batch* b) {
   for (int k = 0; k < K_CHUNK && e == cudaSuccess; ++k) {
     if (b->method == METHOD_GD) {
       e = launch_pass(b->BL, PASS_GD, b->stream);  // evaluate, then step
+      if (e == cudaSuccess) e = demag_refresh(b);  // the potential of the new field
       continue;
     }
     e = launch_pass(b->BL, 2, b->stream);                        // stages 3-4: new fields
+    if (e == cudaSuccess) e = demag_refresh(b);                  // their potential (demagnetisation)
     if (e == cudaSuccess) e = launch_pass(b->BL, 1, b->stream);  // stages 1-2 of the new fields
   }
   cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
@@ -510,8 +545,10 @@ int batch_run(ss_batch* b, double tol, long long max_steps) {
   for (int k = 0; k < rem && !stopped; ++k) {
     if (b->method == METHOD_GD) {
       SS_CK(launch_pass(b->BL, PASS_GD, b->stream));
+      SS_CK(demag_refresh(b));
     } else {
       SS_CK(launch_pass(b->BL, 2, b->stream));
+      SS_CK(demag_refresh(b));
       SS_CK(launch_pass(b->BL, 1, b->stream));
     }
   }
@@ -631,7 +668,7 @@ int ss_create_grid(ss_ctx** out, int nx, int ny, double dx, double dy, int preci
 
 int ss_set_theory(ss_ctx* c, int theory, const double* params, int n_params) {
   if (!c) return fail(SS_ERR_ARG, "null context");
-  double k[10];
+  double k[NCOUP];
   int C = 0;
   int rc = pack_couplings(theory, params, n_params, k, &C);
   if (rc != SS_OK) return rc;
@@ -645,6 +682,7 @@ int ss_set_theory(ss_ctx* c, int theory, const double* params, int n_params) {
   b->prec = c->prec;
   b->C = C;
   b->elem = c->prec == SS_FP64 ? 8 : 4;
+  b->demag = th_of_coup(theory, k) == TH_CMD;
   rc = make_stream(b, c->user_stream);
   if (rc != SS_OK) {
     batch_free(b);
@@ -811,6 +849,7 @@ int ss_profile_stages(ss_ctx* c, int n_steps, float* ms_out) {
     if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
     float m = 0.f;
     if (e == cudaSuccess) e = cudaEventElapsedTime(&m, ev[0], ev[1]);
+    if (e == cudaSuccess) e = demag_refresh(b);
     acc[0] += m;
   }
   if (gd && e == cudaSuccess) e = launch_pass(b->BL, PASS_GD, b->stream);  // evaluates the last field
@@ -818,11 +857,17 @@ int ss_profile_stages(ss_ctx* c, int n_steps, float* ms_out) {
     e = cudaEventRecord(ev[0], b->stream);
     if (e == cudaSuccess) e = launch_pass(b->BL, 2, b->stream);  // stages 3-4 -> new field
     if (e == cudaSuccess) e = cudaEventRecord(ev[1], b->stream);
+    float m1 = 0.f, m2 = 0.f;
+    if (e == cudaSuccess && b->demag) {  // the potential of the new field, outside both intervals
+      e = cudaEventSynchronize(ev[1]);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&m2, ev[0], ev[1]);
+      if (e == cudaSuccess) e = demag_refresh(b);
+      if (e == cudaSuccess) e = cudaEventRecord(ev[1], b->stream);  // pass 1 starts after the solve
+    }
     if (e == cudaSuccess) e = launch_pass(b->BL, 1, b->stream);  // stages 1-2 of the new field
     if (e == cudaSuccess) e = cudaEventRecord(ev[2], b->stream);
     if (e == cudaSuccess) e = cudaEventSynchronize(ev[2]);
-    float m1 = 0.f, m2 = 0.f;
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&m2, ev[0], ev[1]);
+    if (e == cudaSuccess && !b->demag) e = cudaEventElapsedTime(&m2, ev[0], ev[1]);
     if (e == cudaSuccess) e = cudaEventElapsedTime(&m1, ev[1], ev[2]);
     acc[0] += m1;
     acc[1] += m2;
@@ -859,9 +904,11 @@ int ss_batch_create(ss_batch** out, int theory, int precision, const ss_batch_it
   for (int i = 0; i < n; ++i) {
     const ss_batch_item& it = items[i];
     int rc = check_grid(it.nx, it.ny, it.dx, it.dy);
-    double k[10];
+    double k[NCOUP];
     int C = 0;
     if (rc == SS_OK) rc = pack_couplings(theory, it.params, it.n_params, k, &C);
+    if (rc == SS_OK && th_of_coup(theory, k) == TH_CMD)
+      rc = fail(SS_ERR_ARG, "demagnetisation (mu_d > 0) needs a single-grid context (ss_create_grid)");
     if (rc == SS_OK && (!it.solitons || it.n_solitons < 1)) rc = fail(SS_ERR_ARG, "every item needs at least one soliton");
     if (rc != SS_OK) {
       g_err = "item " + std::to_string(i) + ": " + g_err;
@@ -978,7 +1025,7 @@ int batch_autotune(ss_batch* b, int trial_steps, int* choice) {
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const int th = th_of(b->theory);
+  const int th = (b->demag ? TH_CMD : th_of(b->theory));
   cudaEvent_t ev[3];
   for (int i = 0; i < 3; ++i)
     if (cudaEventCreate(&ev[i]) != cudaSuccess) return release(fail(SS_ERR_CUDA, "autotune: event creation failed"));
@@ -1093,6 +1140,7 @@ int batch_set_method(ss_batch* b, int method, double step_factor) {
     for (int k = 0; k < 2; ++k) SS_CK(cudaMemsetAsync(p.v[k], 0, bytes, b->stream));
     SS_CK(launch_reset_states(b->st + i, 1, b->stream));
   }
+  if (b->fields_set[0]) SS_CK(demag_refresh(b));  // step count 0: the potential of buffer 0
   b->method = method;
   const int blocks_keep[2] = {b->BL.flow_blocks[0], b->BL.flow_blocks[1]};
   b->BL.flow_blocks[2] = 0;

@@ -22,7 +22,7 @@ constexpr int HALO = 2;
 constexpr int SX = TX + 2 * HALO, SY = TY + 2 * HALO;
 constexpr int ROWS_PER_THREAD = TY / BY;
 
-enum { TH_AH = 1, TH_CM = 2, TH_BS = 3, TH_BEC = 4, TH_SID = 5 };
+enum { TH_AH = 1, TH_CM = 2, TH_BS = 3, TH_BEC = 4, TH_SID = 5, TH_CMD = 6 };
 
 template <int TH> struct NComp;
 template <> struct NComp<TH_AH> { static constexpr int C = 4; };
@@ -30,9 +30,10 @@ template <> struct NComp<TH_CM> { static constexpr int C = 3; };
 template <> struct NComp<TH_BS> { static constexpr int C = 3; };
 template <> struct NComp<TH_BEC> { static constexpr int C = 2; };
 template <> struct NComp<TH_SID> { static constexpr int C = 6; };
+template <> struct NComp<TH_CMD> { static constexpr int C = 3; };  // chiral magnet with demagnetisation
 
 // Theories whose field is a unit 3-vector (projected onto the sphere).
-template <int TH> struct UnitVector { static constexpr bool value = TH == TH_CM || TH == TH_BS; };
+template <int TH> struct UnitVector { static constexpr bool value = TH == TH_CM || TH == TH_BS || TH == TH_CMD; };
 
 // ------------------------------------------------------------------ flow state
 // One per context, in device memory. Written only by the single last-arriving
@@ -197,9 +198,11 @@ SS_HD Deriv<R> stencil(const R* P, int sx, int sy, const Spacing<R>& h) {
 // Baby Skyrme: c[0] = kappa^2, c[1] = mu^2, c[2] = nu^2.
 // BEC: c[0] = g, c[1] = Omega, c[2] = mu (chemical potential).
 // s+id: c[0..6] = a1, a2, b1, b2, b3, b4, nu.
+// Chiral magnet with demagnetisation: the chiral magnet's c[0..9], c[10] = mu_d.
+constexpr int NCOUP = 12;  // couplings per problem
 template <typename R>
 struct Couplings {
-  R c[10];
+  R c[NCOUP];
 };
 
 // Abelian Higgs (Table 1): e = 1/2 |D psi|^2 + 1/2 B^2 + lambda/8 (u^2 - |psi|^2)^2,
@@ -255,8 +258,8 @@ SS_HD R density_cm(const Couplings<R>& k, const R* n, const R* fx, const R* fy) 
 
 // G = -J lap n - 2 D sum_i d_i x d_i n - 2 K n_3 e_3 - h e_3, then G <- G - (G.n) n.
 template <typename R>
-SS_HD void force_cm(const Couplings<R>& k, const R* n, const R* fx, const R* fy, const R* fxx,
-                                         const R* fyy, R* G) {
+SS_HD void force_cm_raw(const Couplings<R>& k, const R* n, const R* fx, const R* fy, const R* fxx, const R* fyy,
+                        R* G) {
   R c1[3], c2[3];
   const R d1[3] = {k.c[4], k.c[5], k.c[6]}, d2[3] = {k.c[7], k.c[8], k.c[9]};
   cross3(d1, fx, c1);
@@ -265,9 +268,30 @@ SS_HD void force_cm(const Couplings<R>& k, const R* n, const R* fx, const R* fy,
 #pragma unroll
   for (int a = 0; a < 3; ++a) G[a] = -k.c[0] * (fxx[a] + fyy[a]) - twoD * (c1[a] + c2[a]);
   G[2] += -R(2) * k.c[2] * n[2] - k.c[3];
+}
+template <typename R>
+SS_HD void project_tangent(const R* n, R* G) {
   const R gn = G[0] * n[0] + G[1] * n[1] + G[2] * n[2];
 #pragma unroll
   for (int a = 0; a < 3; ++a) G[a] -= gn * n[a];
+}
+template <typename R>
+SS_HD void force_cm(const Couplings<R>& k, const R* n, const R* fx, const R* fy, const R* fxx,
+                                         const R* fyy, R* G) {
+  force_cm_raw<R>(k, n, fx, fy, fxx, fyy, G);
+  project_tangent<R>(n, G);
+}
+
+// Demagnetisation (Eq. 6) with psi = phi / (mu_0 M_s), lap psi = div n: the energy
+// -mu_d/2 int psi rho (rho = d_1 n_1 + d_2 n_2) has the force mu_d (d_1 psi, d_2 psi, 0),
+// added before the projection; psi is computed for the whole lattice (ss_demag.cu).
+template <typename R>
+SS_HD void force_cmd(const Couplings<R>& k, const R* n, const R* fx, const R* fy, const R* fxx, const R* fyy, R psx,
+                     R psy, R* G) {
+  force_cm_raw<R>(k, n, fx, fy, fxx, fyy, G);
+  G[0] += k.c[10] * psx;
+  G[1] += k.c[10] * psy;
+  project_tangent<R>(n, G);
 }
 
 // Baby Skyrme (Table 1): e = 1/2 |d m|^2 + kappa^2/4 sum_{i,j} |d_i m x d_j m|^2 + V(m)
@@ -554,10 +578,15 @@ SS_HD R delta_density_sid(const Couplings<R>& k, const R* a, const R* ax, const 
          R(2) * k.c[5] * ((R(2) * p - dp) * dp - (R(2) * q - dq) * dq);
 }
 
-// Energy density, force and energy difference of theory TH at a site at (x, y)
-// (the position enters only the BEC's trap and rotation terms).
+// Energy density, force and energy difference of theory TH. (x, y) carries the
+// site-dependent extras: the BEC's site position; for the chiral magnet with
+// demagnetisation the potential psi (density), its gradient (d_1 psi, d_2 psi) (force),
+// and (psi, psi - psi_prev) (energy difference, whose magnetostatic part
+// -mu_d/2 (psi - psi') (rho + rho') sums to E_ms(new) - E_ms(old) because the inverse
+// Laplacian is symmetric).
 template <int TH, typename R>
 SS_HD R density_at(const Couplings<R>& k, const R* v, const R* fx, const R* fy, R x = R(0), R y = R(0)) {
+  if (TH == TH_CMD) return density_cm<R>(k, v, fx, fy) - R(0.5) * k.c[10] * x * (fx[0] + fy[1]);
   if (TH == TH_AH) return density_ah<R>(k, v, fx, fy);
   if (TH == TH_CM) return density_cm<R>(k, v, fx, fy);
   if (TH == TH_BS) return density_bs<R>(k, v, fx, fy);
@@ -567,6 +596,9 @@ SS_HD R density_at(const Couplings<R>& k, const R* v, const R* fx, const R* fy, 
 template <int TH, typename R>
 SS_HD R delta_density_at(const Couplings<R>& k, const R* a, const R* ax, const R* ay, const R* d, const R* dx,
                          const R* dy, R x = R(0), R y = R(0)) {
+  if (TH == TH_CMD)
+    return delta_density_cm<R>(k, a, ax, ay, d, dx, dy) -
+           R(0.5) * k.c[10] * y * (R(2) * (ax[0] + ay[1]) - (dx[0] + dy[1]));
   if (TH == TH_AH) return delta_density_ah<R>(k, a, ax, ay, d, dx, dy);
   if (TH == TH_CM) return delta_density_cm<R>(k, a, ax, ay, d, dx, dy);
   if (TH == TH_BS) return delta_density_bs<R>(k, a, ax, ay, d, dx, dy);
@@ -578,6 +610,7 @@ SS_HD void force_of(const Couplings<R>& k, const R* v, const R* fx, const R* fy,
                     const R* fxy, R* G, R x = R(0), R y = R(0)) {
   if (TH == TH_AH) force_ah<R>(k, v, fx, fy, fxx, fyy, fxy, G);
   else if (TH == TH_CM) force_cm<R>(k, v, fx, fy, fxx, fyy, G);
+  else if (TH == TH_CMD) force_cmd<R>(k, v, fx, fy, fxx, fyy, x, y, G);
   else if (TH == TH_BS) force_bs<R>(k, v, fx, fy, fxx, fyy, fxy, G);
   else if (TH == TH_SID) force_sid<R>(k, v, fx, fy, fxx, fyy, fxy, G);
   else force_bec<R>(k, v, fx, fy, fxx, fyy, x, y, G);

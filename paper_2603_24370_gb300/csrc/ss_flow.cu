@@ -2,7 +2,7 @@
 // per-theory dispatch of the pass launches and occupancy queries, the pass grids,
 // and the control kernels over the per-problem flow records. The pass kernels
 // themselves are in ss_flow_kernel.cuh, instantiated per theory in ss_flow_ah.cu,
-// ss_flow_cm.cu, ss_flow_bs.cu, ss_flow_bec.cu and ss_flow_sid.cu.
+// ss_flow_cm.cu, ss_flow_bs.cu, ss_flow_bec.cu, ss_flow_sid.cu and ss_flow_cmd.cu.
 #include "ss_internal.h"
 
 namespace ss {
@@ -71,6 +71,7 @@ cudaError_t launch_pass(const BatchLaunch& b, int pass, cudaStream_t s) {
   if (b.theory == TH_CM) return launch_pass_theory<TH_CM>(b, pass, s);
   if (b.theory == TH_BS) return launch_pass_theory<TH_BS>(b, pass, s);
   if (b.theory == TH_SID) return launch_pass_theory<TH_SID>(b, pass, s);
+  if (b.theory == TH_CMD) return launch_pass_theory<TH_CMD>(b, pass, s);
   return launch_pass_theory<TH_BEC>(b, pass, s);
 }
 
@@ -107,6 +108,7 @@ void flow_occupancy(int theory, int prec, int ts, bool one, int occ[3]) {
   else if (theory == TH_CM) occupancy_theory<TH_CM>(prec, ts, one, occ);
   else if (theory == TH_BS) occupancy_theory<TH_BS>(prec, ts, one, occ);
   else if (theory == TH_SID) occupancy_theory<TH_SID>(prec, ts, one, occ);
+  else if (theory == TH_CMD) occupancy_theory<TH_CMD>(prec, ts, one, occ);
   else occupancy_theory<TH_BEC>(prec, ts, one, occ);
   for (int i = 0; i < 3; ++i)
     if (occ[i] < 1) occ[i] = 1;

@@ -226,8 +226,13 @@ struct StageWin {
   Win<R, NeedsMix<TH, 3>::value> w3;
   Win<R, NeedsMix<TH, 4>::value> w4;
   Win<R, NeedsMix<TH, 5>::value> w5;
+  // chiral magnet with demagnetisation: the magnetostatic potential's tile, walked with
+  // the stage input (pbase must be set before the first enter)
+  Win<R, false> wp;
+  const R* pbase = nullptr;
 
   __device__ __forceinline__ void enter(const R* tiles, int off, int slot) {
+    if (TH == TH_CMD) wp.enter(pbase + off, slot);
     w0.enter(tiles + off, slot);
     w1.enter(tiles + SXY + off, slot);
     if (C > 2) w2.enter(tiles + 2 * SXY + off, slot);
@@ -236,6 +241,7 @@ struct StageWin {
     if (C > 5) w5.enter(tiles + 5 * SXY + off, slot);
   }
   __device__ __forceinline__ void shift() {
+    if (TH == TH_CMD) wp.shift();
     w0.shift();
     w1.shift();
     if (C > 2) w2.shift();
@@ -251,6 +257,11 @@ struct StageWin {
     if (C > 3) w3.template derivs<true>(tiles + 3 * SXY + off, h, v[3], fx[3], fy[3], fxx[3], fyy[3], fxy[3]);
     if (C > 4) w4.template derivs<true>(tiles + 4 * SXY + off, h, v[4], fx[4], fy[4], fxx[4], fyy[4], fxy[4]);
     if (C > 5) w5.template derivs<true>(tiles + 5 * SXY + off, h, v[5], fx[5], fy[5], fxx[5], fyy[5], fxy[5]);
+  }
+  // the potential and its Eq. 1 gradient at the window's centre row
+  __device__ __forceinline__ void psi_at(int off, const Spacing<R>& h, R& p, R& px, R& py) const {
+    R u0, u1, u2;
+    wp.template derivs<false>(pbase + off, h, p, px, py, u0, u1, u2);
   }
 };
 
@@ -400,7 +411,7 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
   constexpr int RY = T::RY;
   constexpr int PS = C * T::SXY;  // values per tile set
   extern __shared__ __align__(16) unsigned char smraw[];
-  R* sm = reinterpret_cast<R*>(smraw);  // pass 1: [Y1 | Y2 | delta], pass 2: [Y3 | Y4], pass 3: [phi]
+  R* sm = reinterpret_cast<R*>(smraw);  // pass 1: [Y1 | Y2 | delta], pass 2: [Y3 | Y4], pass 3: [phi], (+ psi)
   __shared__ TileCtx<R> tcb[2];         // this tile's view and the next one's (read ahead)
   __shared__ R sred[(NT / 32) * 5];
   __shared__ double dred[RedSmem<2, 1>::n];
@@ -409,6 +420,7 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
   R* const setA = sm;           // first stage input of the pass
   R* const setB = sm + PS;      // second stage input
   R* const setD = sm + 2 * PS;  // pass 1: phi^n - phi^{n-1}
+  R* const setP = sm + (PASS == 1 ? 3 : (PASS == 2 ? 2 : 1)) * PS;  // demagnetisation: psi of phi^n
   // passes 1, 3: running sums over this block's consecutive tiles of one problem
   R es = R(0), ec = R(0), ds = R(0), dc = R(0), gmr = R(0);
 
@@ -432,6 +444,8 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
     const R* __restrict__ vel = D.v[cur];
     const R* __restrict__ phi_prev = D.phi[cur ^ 1];
     const R* __restrict__ lo_prev = D.lo[cur ^ 1];
+    const R* __restrict__ psi = D.psi[cur];         // demagnetisation only
+    const R* __restrict__ psi_prev = D.psi[cur ^ 1];
     R* __restrict__ kv1 = D.kv[0];
     R* __restrict__ kv2 = D.kv[1];
     const Spacing<R> h = D.h;
@@ -445,7 +459,7 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
     // of all LU sites are issued before any is used: more bytes in flight per thread)
     constexpr int LU = PASS == 1 ? SS_LU1 : (PASS == 2 ? SS_LU2 : SS_LU3);
     for (int base = tid; base < T::SXY; base += LU * NT) {
-      R pv[LU][C], lv[LU][C], vv[LU][C], k1v[LU][C], k2v[LU][C], pp[LU][C], lp[LU][C];
+      R pv[LU][C], lv[LU][C], vv[LU][C], k1v[LU][C], k2v[LU][C], pp[LU][C], lp[LU][C], pz[LU];
       bool in[LU], inside[LU];
 #pragma unroll
       for (int u = 0; u < LU; ++u) {  // all global loads of the sites first
@@ -455,6 +469,7 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
         in[u] = idx < T::SXY && gx >= 0 && gx < nx && gy >= 0 && gy < ny;
         inside[u] = in[u] && gx >= 2 && gx < nx - 2 && gy >= 2 && gy < ny - 2;
         const size_t s = in[u] ? (size_t)gy * nx + gx : 0;
+        if (TH == TH_CMD) pz[u] = in[u] ? psi[s] : R(0);
 #pragma unroll
         for (int c = 0; c < C; ++c) {
           pv[u][c] = in[u] ? phi[c * P + s] : R(0);
@@ -520,6 +535,7 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
           if (PASS != 3) setB[c * T::SXY + idx] = yb[c];
           if (PASS == 1) setD[c * T::SXY + idx] = has_prev ? yd[c] : R(0);
         }
+        if (TH == TH_CMD) setP[idx] = pz[u];
       }
     }
     __syncthreads();
@@ -538,6 +554,7 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
       // stage 1 at Y_1 = phi: k_v1, e, max|G|, and e(phi^n) - e(phi^{n-1})
       {
         StageWin<TH, R, T::SXY> W;
+        W.pbase = setP;
         DiffWin<TH, R, T::SXY> D;
 #pragma unroll
         for (int s = 0; s < 5; ++s) {
@@ -551,7 +568,10 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
           const bool ok = colok && gyb + r >= 2 && gyb + r < ny - 2;
           R v[C], fx[C], fy[C], fxx[C], fyy[C], fxy[C], G[C];
           W.derivs(setA, off, h, v, fx, fy, fxx, fyy, fxy);
-          force_at<TH, R>(kc, v, fx, fy, fxx, fyy, fxy, G, xs, ypos(r));
+          // site extras: the BEC's position; with demagnetisation psi and its gradient
+          R q0 = xs, q1 = ypos(r), ps = R(0);
+          if (TH == TH_CMD) W.psi_at(off, h, ps, q0, q1);
+          force_at<TH, R>(kc, v, fx, fy, fxx, fyy, fxy, G, q0, q1);
           if (ok) {
             const size_t s = (size_t)(gyb + r) * nx + gx;
 #pragma unroll
@@ -559,7 +579,7 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
               kv1[c * P + s] = -G[c];
               gmr = absmax(gmr, G[c]);
             }
-            const R e = density_at<TH, R>(kc, v, fx, fy, xs, ypos(r));
+            const R e = density_at<TH, R>(kc, v, fx, fy, TH == TH_CMD ? ps : q0, q1);
             const R t1 = es + e;
             ec += (fabs(es) >= fabs(e)) ? (es - t1) + e : (e - t1) + es;
             es = t1;
@@ -568,7 +588,9 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
             R dd[C], dxv[C], dyv[C];
             D.derivs(setD, off, h, dd, dxv, dyv);
             if (ok) {
-              const R de = delta_density_at<TH, R>(kc, v, fx, fy, dd, dxv, dyv, xs, ypos(r));
+              const R de = delta_density_at<TH, R>(
+                  kc, v, fx, fy, dd, dxv, dyv, TH == TH_CMD ? ps : q0,
+                  TH == TH_CMD ? ps - psi_prev[(size_t)(gyb + r) * nx + gx] : q1);
               const R t2 = ds + de;
               dc += (fabs(ds) >= fabs(de)) ? (ds - t2) + de : (de - t2) + ds;
               ds = t2;
@@ -588,6 +610,7 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
       // stage 2 at Y_2 = phi + dt/2 v: k_v2
       {
         StageWin<TH, R, T::SXY> W;
+        W.pbase = setP;
 #pragma unroll
         for (int s = 0; s < 5; ++s) W.enter(setB, (sy0 - 2 + s) * T::SX + sx, s);
 #pragma unroll
@@ -595,7 +618,10 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
           const int off = (sy0 + r) * T::SX + sx;
           R v[C], fx[C], fy[C], fxx[C], fyy[C], fxy[C], G[C];
           W.derivs(setB, off, h, v, fx, fy, fxx, fyy, fxy);
-          force_at<TH, R>(kc, v, fx, fy, fxx, fyy, fxy, G, xs, ypos(r));
+          // site extras: the BEC's position; with demagnetisation psi and its gradient
+          R q0 = xs, q1 = ypos(r), ps = R(0);
+          if (TH == TH_CMD) W.psi_at(off, h, ps, q0, q1);
+          force_at<TH, R>(kc, v, fx, fy, fxx, fyy, fxy, G, q0, q1);
           if (colok && gyb + r >= 2 && gyb + r < ny - 2) {
             const size_t s = (size_t)(gyb + r) * nx + gx;
 #pragma unroll
@@ -611,6 +637,7 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
       // gradient descent at phi: -G into k_v1, e, max|G|, and phi - dtau G
       {
         StageWin<TH, R, T::SXY> W;
+        W.pbase = setP;
 #pragma unroll
         for (int s = 0; s < 5; ++s) W.enter(setA, (sy0 - 2 + s) * T::SX + sx, s);
         const R tau = D.tau;
@@ -621,7 +648,10 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
           const int off = (sy0 + r) * T::SX + sx;
           R v[C], fx[C], fy[C], fxx[C], fyy[C], fxy[C], G[C];
           W.derivs(setA, off, h, v, fx, fy, fxx, fyy, fxy);
-          force_at<TH, R>(kc, v, fx, fy, fxx, fyy, fxy, G, xs, ypos(r));
+          // site extras: the BEC's position; with demagnetisation psi and its gradient
+          R q0 = xs, q1 = ypos(r), ps = R(0);
+          if (TH == TH_CMD) W.psi_at(off, h, ps, q0, q1);
+          force_at<TH, R>(kc, v, fx, fy, fxx, fyy, fxy, G, q0, q1);
           if (colok && gyb + r >= 2 && gyb + r < ny - 2) {
             const size_t s = (size_t)(gyb + r) * nx + gx;
 #pragma unroll
@@ -629,7 +659,7 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
               kv1[c * P + s] = -G[c];
               gmr = absmax(gmr, G[c]);
             }
-            const R e = density_at<TH, R>(kc, v, fx, fy, xs, ypos(r));
+            const R e = density_at<TH, R>(kc, v, fx, fy, TH == TH_CMD ? ps : q0, q1);
             const R t1 = es + e;
             ec += (fabs(es) >= fabs(e)) ? (es - t1) + e : (e - t1) + es;
             es = t1;
@@ -749,6 +779,7 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
       R k3[RY][C];
       {
         StageWin<TH, R, T::SXY> W;
+        W.pbase = setP;
 #pragma unroll
         for (int s = 0; s < 5; ++s) W.enter(setA, (sy0 - 2 + s) * T::SX + sx, s);
 #pragma unroll
@@ -756,7 +787,10 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
           const int off = (sy0 + r) * T::SX + sx;
           R v[C], fx[C], fy[C], fxx[C], fyy[C], fxy[C], G[C];
           W.derivs(setA, off, h, v, fx, fy, fxx, fyy, fxy);
-          force_at<TH, R>(kc, v, fx, fy, fxx, fyy, fxy, G, xs, ypos(r));
+          // site extras: the BEC's position; with demagnetisation psi and its gradient
+          R q0 = xs, q1 = ypos(r), ps = R(0);
+          if (TH == TH_CMD) W.psi_at(off, h, ps, q0, q1);
+          force_at<TH, R>(kc, v, fx, fy, fxx, fyy, fxy, G, q0, q1);
 #pragma unroll
           for (int c = 0; c < C; ++c) k3[r][c] = -G[c];
           if (r + 1 < RY) {
@@ -768,6 +802,7 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
       // stage 4 at Y_4, then the RK4 combination
       {
         StageWin<TH, R, T::SXY> W;
+        W.pbase = setP;
 #pragma unroll
         for (int s = 0; s < 5; ++s) W.enter(setB, (sy0 - 2 + s) * T::SX + sx, s);
         const R w6 = dt * dt / R(6), u6 = dt / R(6);
@@ -779,7 +814,10 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
           const int off = (sy0 + r) * T::SX + sx;
           R v[C], fx[C], fy[C], fxx[C], fyy[C], fxy[C], G[C];
           W.derivs(setB, off, h, v, fx, fy, fxx, fyy, fxy);
-          force_at<TH, R>(kc, v, fx, fy, fxx, fyy, fxy, G, xs, ypos(r));
+          // site extras: the BEC's position; with demagnetisation psi and its gradient
+          R q0 = xs, q1 = ypos(r), ps = R(0);
+          if (TH == TH_CMD) W.psi_at(off, h, ps, q0, q1);
+          force_at<TH, R>(kc, v, fx, fy, fxx, fyy, fxy, G, q0, q1);
           if (colok && gyb + r >= 2 && gyb + r < ny - 2) {
             const size_t s = (size_t)(gyb + r) * nx + gx;
             R p0[C], q[C], vn[C];
@@ -843,7 +881,8 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
 // ------------------------------------------------------------------ launchers
 template <int TH, typename R, int TS>
 static size_t pass_smem(int pass) {
-  return (size_t)(pass == 1 ? 3 : (pass == 2 ? 2 : 1)) * NComp<TH>::C * FlowTile<R, TS>::SXY * sizeof(R);
+  return ((size_t)(pass == 1 ? 3 : (pass == 2 ? 2 : 1)) * NComp<TH>::C + (TH == TH_CMD ? 1 : 0)) *
+         FlowTile<R, TS>::SXY * sizeof(R);
 }
 
 template <int TH, typename R, bool LO, bool ONE, int TS>

@@ -21,11 +21,12 @@ struct LaunchCtx {
   int nx, ny;
   size_t plane;    // nx * ny
   double dx, dy, dt;
-  double coup[10]; // Couplings layout of ss_device.cuh, in FP64
+  double coup[NCOUP]; // Couplings layout of ss_device.cuh, in FP64
   void* phi[2];    // ping-pong field buffers [C][ny][nx] (hi part when compensated)
   void* lo[2];     // compensated FP32: lo parts of phi[2] (else unused)
   void* v[2];      // ping-pong velocity buffers
   void* kv[2];     // RK stage accelerations k_v1, k_v2 (k_v3, k_v4 never leave registers)
+  void* psi[2];    // chiral magnet with demagnetisation: magnetostatic potential planes
   DevState* st;
   FlowPartial* fpart;
   ObsPartial* opart;
@@ -47,6 +48,7 @@ struct ProbDesc {
   R* lo[2];         // compensated FP32: remainder planes (else null)
   R* v[2];          // ping-pong velocities
   R* kv[2];         // k_v1, k_v2
+  R* psi[2];        // chiral magnet with demagnetisation: magnetostatic potential of phi[0], phi[1]
   R dt;
   R tau;            // gradient descent: the step dtau of phi <- phi - dtau G
   R hx, hy;         // dx, dy (site positions of the BEC's trap and rotation terms)
@@ -108,6 +110,16 @@ cudaError_t launch_scaled_copy(const LaunchCtx& c, void* out, const void* in, do
 cudaError_t launch_observables(const LaunchCtx& c, int cur, cudaStream_t s);
 // Ansatz of n solitons (device array of 5 doubles each) into both field buffers.
 cudaError_t launch_ansatz(const LaunchCtx& c, const double* d_sol, int n, cudaStream_t s);
+
+// Magnetostatic potential of one chiral-magnet problem (Eq. 6; ss_demag.cu): the sine
+// transform solver of the 5-point Poisson problem with its transform plans and buffers.
+struct DemagSolver;
+// Returns 0, or -1 (device allocation failed) / -2 (transform plan failed).
+int demag_create(DemagSolver** out, int nx, int ny, double dx, double dy, int prec);
+void demag_destroy(DemagSolver* d);
+// psi[cur] = L^{-1} rho(phi[cur] (+ lo[cur])), cur = st->steps & 1 read on the device.
+cudaError_t demag_solve(DemagSolver* d, const DevState* st, void* const phi[2], void* const lo[2], void* const psi[2],
+                        cudaStream_t s);
 
 // Record the calling thread's error message for ss_last_error().
 void set_last_error(const std::string& msg);

@@ -74,7 +74,7 @@ extern "C" int ss_observables_noalloc(int theory, const double* params, int n_pa
   if (!params && n_params > 0) return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: params is NULL");
 
   // couplings, packed as in ss_set_theory
-  double k[10] = {0};
+  double k[NCOUP] = {0};
   if (theory == SS_ABELIAN_HIGGS) {
     if (n_params < 1 || n_params > 2) return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: Abelian Higgs takes {lambda[, u]}");
     const double u = n_params > 1 ? params[1] : 1.0;
@@ -83,7 +83,9 @@ extern "C" int ss_observables_noalloc(int theory, const double* params, int n_pa
     k[0] = params[0];
     k[1] = u * u;
   } else if (theory == SS_CHIRAL_MAGNET) {
-    if (n_params < 4 || n_params > 5)
+    if (n_params == 6 && params[5] != 0.0)
+      return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: demagnetisation needs a context (a Poisson solve)");
+    if (n_params < 4 || n_params > 6)
       return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: chiral magnet takes {J, D, K, h[, dmi_type]}");
     for (int i = 0; i < n_params; ++i)
       if (!std::isfinite(params[i])) return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: parameters must be finite");

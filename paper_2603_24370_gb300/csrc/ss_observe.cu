@@ -23,6 +23,7 @@ template <typename R>
 struct ObsArgs {
   const R* __restrict__ phi;
   const R* __restrict__ lo;  // compensated FP32: remainder plane added in FP64 (else null)
+  const R* __restrict__ psi; // chiral magnet with demagnetisation: magnetostatic potential (else null)
   int nx, ny;
   size_t plane;
   int ntx, ntiles;
@@ -49,7 +50,8 @@ __device__ __forceinline__ double solid_angle(const double* a, const double* b, 
 template <int TH, typename R>
 __global__ void __launch_bounds__(NT) k_observables(ObsArgs<R> a) {
   constexpr int C = NComp<TH>::C;
-  __shared__ double sY[C][SY * SX];
+  constexpr int CP = C + (TH == TH_CMD ? 1 : 0);  // + the potential plane
+  __shared__ double sY[CP][SY * SX];
   __shared__ double sred[RedSmem<3, 2>::n];
   __shared__ int s_last;
   const int tid = threadIdx.y * BX + threadIdx.x;
@@ -68,6 +70,7 @@ __global__ void __launch_bounds__(NT) k_observables(ObsArgs<R> a) {
 #pragma unroll
       for (int c = 0; c < C; ++c)
         sY[c][idx] = in ? (double)a.phi[c * P + s] + (a.lo ? (double)a.lo[c * P + s] : 0.0) : 0.0;
+      if (TH == TH_CMD) sY[CP - 1][idx] = in ? (double)a.psi[s] : 0.0;
     }
     __syncthreads();
 #pragma unroll
@@ -107,6 +110,10 @@ __global__ void __launch_bounds__(NT) k_observables(ObsArgs<R> a) {
         force_ah<double>(a.k, v, fx, fy, fxx, fyy, fxy, G);
         neumaier(se, density_ah<double>(a.k, v, fx, fy));
         neumaier(sf, fx[3] - fy[2]);
+      } else if (TH == TH_CMD) {  // E_ms density -mu_d/2 psi rho, force with mu_d grad psi
+        const Deriv<double> pd = stencil<double, false, false>(sY[CP - 1], sx, sy, a.h);
+        force_of<TH, double>(a.k, v, fx, fy, fxx, fyy, fxy, G, pd.fx, pd.fy);
+        neumaier(se, density_at<TH, double>(a.k, v, fx, fy, pd.v, 0.0));
       } else if (TH == TH_SID) {
         force_of<TH, double>(a.k, v, fx, fy, fxx, fyy, fxy, G);
         neumaier(se, density_at<TH, double>(a.k, v, fx, fy));
@@ -277,6 +284,7 @@ static cudaError_t obs_t(const LaunchCtx& c, int cur, cudaStream_t s) {
   ObsArgs<R> a{};
   a.phi = static_cast<const R*>(c.phi[cur]);
   a.lo = static_cast<const R*>(c.lo[cur]);
+  a.psi = static_cast<const R*>(c.psi[cur]);
   a.nx = c.nx;
   a.ny = c.ny;
   a.plane = c.plane;
@@ -289,7 +297,7 @@ static cudaError_t obs_t(const LaunchCtx& c, int cur, cudaStream_t s) {
   a.h.i144dxdy = 1.0 / (144.0 * c.dx * c.dy);
   a.hx = c.dx;
   a.hy = c.dy;
-  for (int i = 0; i < 10; ++i) a.k.c[i] = c.coup[i];
+  for (int i = 0; i < NCOUP; ++i) a.k.c[i] = c.coup[i];
   a.area = c.dx * c.dy;
   a.st = c.st;
   a.part = c.opart;
@@ -309,6 +317,7 @@ cudaError_t launch_observables(const LaunchCtx& c, int cur, cudaStream_t s) {
   if (c.theory == TH_CM) return f ? obs_t<TH_CM, float>(c, cur, s) : obs_t<TH_CM, double>(c, cur, s);
   if (c.theory == TH_BS) return f ? obs_t<TH_BS, float>(c, cur, s) : obs_t<TH_BS, double>(c, cur, s);
   if (c.theory == TH_SID) return f ? obs_t<TH_SID, float>(c, cur, s) : obs_t<TH_SID, double>(c, cur, s);
+  if (c.theory == TH_CMD) return f ? obs_t<TH_CMD, float>(c, cur, s) : obs_t<TH_CMD, double>(c, cur, s);
   return f ? obs_t<TH_BEC, float>(c, cur, s) : obs_t<TH_BEC, double>(c, cur, s);
 }
 
@@ -370,6 +379,7 @@ int obs_grid(int theory, int prec, int ntiles) {
   else if (theory == TH_CM) occ = f ? obs_occ<TH_CM, float>() : obs_occ<TH_CM, double>();
   else if (theory == TH_BS) occ = f ? obs_occ<TH_BS, float>() : obs_occ<TH_BS, double>();
   else if (theory == TH_SID) occ = f ? obs_occ<TH_SID, float>() : obs_occ<TH_SID, double>();
+  else if (theory == TH_CMD) occ = f ? obs_occ<TH_CMD, float>() : obs_occ<TH_CMD, double>();
   else occ = f ? obs_occ<TH_BEC, float>() : obs_occ<TH_BEC, double>();
   const int g = nsm * occ;
   return ntiles < g ? ntiles : g;
