@@ -41,6 +41,11 @@ b2 = 0.4, b3 = 0.3, b4 = 0.15, nu = 0.35): flow throughput on 2048^2 (dx 0.3, 64
 vortices) in compensated FP32, and a 256^2 box with 4 vortices relaxed to
 dx dy max|G| < 1e-4 on the GPU against the FP64 oracle on the host cores.
 
+--workload demag: the chiral magnet with demagnetisation (Eq. 6, mu_d = 0.8): per-step
+cost on the 4096^2 workload (passes and the sine-transform Poisson solve) against the
+same workload without it, and time to dx dy max|G| < 1e-6 of the 1024^2 configuration
+(8 skyrmions) with and without it.
+
 --workload ah-batch: time per solve to dx dy max|G| < 1e-6 on the batched Abelian
 Higgs set (256 problems, sides 64..512, dx = 0.1, lambda ~ U[0.5, 2], N in 1..4):
 one bench step = the whole set relaxed in one batch (compensated FP32), against
@@ -830,6 +835,62 @@ def run_sid(args) -> int:
     return 0
 
 
+def run_demag(args) -> int:
+    """Chiral magnet with demagnetisation: step cost and time to solution."""
+    rank, local_rank, world = D.env_rank()
+    if rank != 0:
+        return 0
+    D.pin_visible_device(local_rank, 1)
+    import torch
+    from paper_2603_24370_gb300 import build as B
+    from paper_2603_24370_gb300 import inputs as I
+    from paper_2603_24370_gb300 import soliton as S
+    B.build()
+    S.load_library()
+    mu_d = 0.8
+    out = {}
+    p = I.cm_skyrmions(n=N, count=COUNT, seed=SEED)
+    for name, prm in (("demag", tuple(p.params) + (mu_d,)), ("plain", tuple(p.params))):
+        with S.Solver(S.SS_CHIRAL_MAGNET, prm, N, N, DX, DX, S.SS_FP32) as sv:
+            sv.init_ansatz(p.soliton_array())
+            tuned = sv.autotune(4)
+            for _ in range(args.warmup):
+                sv.step(INNER)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                sv.step(INNER)
+            torch.cuda.synchronize()
+            ms_step = 1e3 * (time.perf_counter() - t0) / (args.steps * INNER)
+            ms = S.ss_profile_stages(sv.ctx, 8)
+        out[name] = {"site_updates_per_s": interior(N) / (ms_step * 1e-3), "ms_per_flow_step": ms_step,
+                     "pass_ms": ms, "autotuned": tuned}
+    out["demag"]["poisson_solve_ms_per_step"] = out["demag"]["ms_per_flow_step"] - sum(out["demag"]["pass_ms"])
+    q = I.cm_skyrmions()
+    tts = {}
+    for name, prec, prm in (("demag_fp32c", S.SS_FP32, tuple(q.params) + (mu_d,)),
+                            ("demag_fp64", S.SS_FP64, tuple(q.params) + (mu_d,)),
+                            ("plain_fp32c", S.SS_FP32, tuple(q.params))):
+        with S.Solver(S.SS_CHIRAL_MAGNET, prm, q.nx, q.ny, q.dx, q.dy, prec) as sv:
+            sv.init_ansatz(q.soliton_array())
+            sv.autotune(4)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = sv.minimise(1e-6, 100000)
+            torch.cuda.synchronize()
+            o = sv.observables()
+            tts[name] = {"seconds": time.perf_counter() - t0, "steps": r["steps"], "converged": bool(r["converged"]),
+                         "energy": o["energy"], "charge": o["charge"]}
+    line = {"metric": "chiral magnet with demagnetisation: ms per flow step at 4096^2; time to 1e-6 at 1024^2",
+            "unit": "ms", "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": f"chiral magnet (J=D=1, K=0.1, h=0.6, interfacial), mu_d={mu_d}, dx=0.2; "
+                                   "4096^2 with 400 skyrmions, 1024^2 with 8; compensated FP32 unless stated",
+                       "flow_steps_per_bench_step": INNER},
+            "step_cost_4096": out, "time_to_solution_1024": tts}
+    print(json.dumps(line))
+    return 0
+
+
 def main() -> int:
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -839,7 +900,7 @@ def main() -> int:
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grid", type=int, default=N, help="grid side (default: the 4096 workload; smaller for ncu)")
     ap.add_argument("--workload",
-                    choices=("cm4096", "ah-batch", "configs", "methods", "baby-skyrme", "bec", "sid"),
+                    choices=("cm4096", "ah-batch", "configs", "methods", "baby-skyrme", "bec", "sid", "demag"),
                     default="cm4096")
     ap.add_argument("--tile-shape", choices=("auto", "0", "1"), default="auto",
                     help="flow tile shape: autotuned (default) or fixed (for profiling one shape)")
@@ -864,6 +925,8 @@ def main() -> int:
         return run_bec(args)
     if args.workload == "sid":
         return run_sid(args)
+    if args.workload == "demag":
+        return run_demag(args)
     return run_native(args)
 
 

@@ -581,9 +581,12 @@ SS_HD R delta_density_sid(const Couplings<R>& k, const R* a, const R* ax, const 
 // Energy density, force and energy difference of theory TH. (x, y) carries the
 // site-dependent extras: the BEC's site position; for the chiral magnet with
 // demagnetisation the potential psi (density), its gradient (d_1 psi, d_2 psi) (force),
-// and (psi, psi - psi_prev) (energy difference, whose magnetostatic part
-// -mu_d/2 (psi - psi') (rho + rho') sums to E_ms(new) - E_ms(old) because the inverse
-// Laplacian is symmetric).
+// and (psi, psi - psi_prev) (energy difference). Its magnetostatic part is written
+// -mu_d/2 (rho - rho') (psi + psi'), which sums to E_ms(new) - E_ms(old) because the
+// inverse Laplacian is symmetric: the small charge difference rho - rho' is formed
+// exactly from the field difference, so the solver's rounding of psi enters relative
+// to the energy change (the difference psi - psi' of two solves would carry it relative
+// to E_ms and decide arrests by noise near convergence).
 template <int TH, typename R>
 SS_HD R density_at(const Couplings<R>& k, const R* v, const R* fx, const R* fy, R x = R(0), R y = R(0)) {
   if (TH == TH_CMD) return density_cm<R>(k, v, fx, fy) - R(0.5) * k.c[10] * x * (fx[0] + fy[1]);
@@ -597,8 +600,7 @@ template <int TH, typename R>
 SS_HD R delta_density_at(const Couplings<R>& k, const R* a, const R* ax, const R* ay, const R* d, const R* dx,
                          const R* dy, R x = R(0), R y = R(0)) {
   if (TH == TH_CMD)
-    return delta_density_cm<R>(k, a, ax, ay, d, dx, dy) -
-           R(0.5) * k.c[10] * y * (R(2) * (ax[0] + ay[1]) - (dx[0] + dy[1]));
+    return delta_density_cm<R>(k, a, ax, ay, d, dx, dy) - R(0.5) * k.c[10] * (dx[0] + dy[1]) * (R(2) * x - y);
   if (TH == TH_AH) return delta_density_ah<R>(k, a, ax, ay, d, dx, dy);
   if (TH == TH_CM) return delta_density_cm<R>(k, a, ax, ay, d, dx, dy);
   if (TH == TH_BS) return delta_density_bs<R>(k, a, ax, ay, d, dx, dy);
