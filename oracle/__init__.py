@@ -109,6 +109,16 @@ def _load():
             lib.or_ansatz_sid.restype = None
             lib.or_ansatz_bec.restype = None
             lib.or_ansatz.restype = None
+            lib.or_bec_multiplier.argtypes = [_D, _D, i, i, d, d]
+            lib.or_bec_multiplier.restype = d
+            lib.or_bec_refresh.argtypes = [_D, d, _D, ctypes.c_void_p, i, i, d, d, _D]
+            lib.or_bec_refresh.restype = i
+            lib.or_anf_step_fixed_n.argtypes = [_D, d, _D, _D, i, i, d, d, d, _D, _D]
+            lib.or_anf_step_fixed_n.restype = i
+            lib.or_minimise_fixed_n.argtypes = [_D, d, _D, _D, i, i, d, d, d, d, ll, _D]
+            lib.or_minimise_fixed_n.restype = i
+            lib.or_gd_minimise_fixed_n.argtypes = [_D, d, _D, i, i, d, d, d, d, ll, _D]
+            lib.or_gd_minimise_fixed_n.restype = i
             _lib = lib
     return _lib
 
@@ -234,6 +244,73 @@ def observables(theory: int, params, f, dx: float, dy: float) -> dict:
     _load().or_observables(theory, _p(_params(params)), _p(f), nx, ny, dx, dy, _p(out))
     return {"energy": out[0], "charge": out[1], "flux": out[2], "grad_max": out[3], "grad_max_raw": out[4],
             "norm_dev": out[5], "atoms": out[6], "angular_momentum": out[7]}
+
+
+def bec_multiplier(params, f, dx: float, dy: float) -> float:
+    """Lagrange multiplier of the atom-number constraint at a BEC field as it stands,
+    sum_I G_0.psi / (2 sum_I |psi|^2) (params {g, Omega[, ...]}; see the C++)."""
+    f = _f64(f)
+    _, ny, nx = f.shape
+    return _load().or_bec_multiplier(_p(_params(params)), _p(f), nx, ny, dx, dy)
+
+
+def bec_refresh(params, atoms: float, f, v, dx: float, dy: float):
+    """Fixed-atom-number refresh of a new BEC field: v tangent to N_h = const, psi scaled
+    on I to N_h = atoms, the multiplier of the scaled field. Returns (f, v, mu); v may
+    be None."""
+    f = _f64(f).copy()
+    v = None if v is None else _f64(v).copy()
+    _, ny, nx = f.shape
+    mu = np.zeros(1)
+    rc = _load().or_bec_refresh(_p(_params(params)), atoms, _p(f), None if v is None else _p(v), nx, ny, dx, dy,
+                                _p(mu))
+    if rc != 0:
+        raise ValueError("bec_refresh: the field has no atoms")
+    return f, v, float(mu[0])
+
+
+def anf_step_fixed_n(params, atoms: float, f, v, dx: float, dy: float, dt: float, E: float, mu: float):
+    """One fixed-atom-number step from a refreshed (f, v) with multiplier mu and energy
+    E (at mu = 0). Returns (f_new, v_new, E_new, mu_new, arrested)."""
+    f = _f64(f).copy()
+    v = _f64(v).copy()
+    _, ny, nx = f.shape
+    e, m = np.array([E]), np.array([mu])
+    a = _load().or_anf_step_fixed_n(_p(_params(params)), atoms, _p(f), _p(v), nx, ny, dx, dy, dt, _p(e), _p(m))
+    if a < 0:
+        raise ValueError("anf_step_fixed_n: the field has no atoms")
+    return f, v, float(e[0]), float(m[0]), bool(a)
+
+
+def minimise_fixed_n(params, atoms: float, f, dx: float, dy: float, tol: float, max_steps: int, v=None,
+                     dt=None) -> dict:
+    """Arrested Newton flow of the BEC at fixed atom number (params {g, Omega[, ...]})."""
+    f = _f64(f).copy()
+    v = np.zeros_like(f) if v is None else _f64(v).copy()
+    _, ny, nx = f.shape
+    dt = time_step(dx, dy) if dt is None else dt
+    out = np.zeros(5)
+    conv = _load().or_minimise_fixed_n(_p(_params(params)), atoms, _p(f), _p(v), nx, ny, dx, dy, dt, tol,
+                                       int(max_steps), _p(out))
+    if conv < 0:
+        raise ValueError("minimise_fixed_n: the field has no atoms")
+    return {"f": f, "v": v, "energy": out[0], "grad_max": out[1], "steps": int(out[2]), "arrests": int(out[3]),
+            "mu": out[4], "converged": bool(conv)}
+
+
+def gd_minimise_fixed_n(params, atoms: float, f, dx: float, dy: float, tol: float, max_steps: int, dtau=None,
+                        step_factor: float = 0.8) -> dict:
+    """Gradient descent of the BEC at fixed atom number."""
+    f = _f64(f).copy()
+    _, ny, nx = f.shape
+    dtau = step_factor * gd_step_limit(dx, dy) if dtau is None else dtau
+    out = np.zeros(5)
+    conv = _load().or_gd_minimise_fixed_n(_p(_params(params)), atoms, _p(f), nx, ny, dx, dy, dtau, tol,
+                                          int(max_steps), _p(out))
+    if conv < 0:
+        raise ValueError("gd_minimise_fixed_n: the field has no atoms")
+    return {"f": f, "energy": out[0], "grad_max": out[1], "steps": int(out[2]), "rises": int(out[3]),
+            "mu": out[4], "converged": bool(conv), "dtau": dtau}
 
 
 def demag_potential(f, dx: float, dy: float):

@@ -758,20 +758,20 @@ void or_energy_grad_exact(int theory, const double* prm, const double* f, int nx
   }
 }
 
-// One arrested-Newton-flow step (Eq. 3, Eq. 4) by classic RK4 on the first-order
-// system (phi, v = phi-dot) (Sec. 3.2):
+}  // extern "C"
+
+namespace {
+
+// The RK4 update of one arrested-Newton-flow step (Eq. 3) by classic RK4 on the
+// first-order system (phi, v = phi-dot) (Sec. 3.2), without the arrest:
 //   k1 = (v,            -G(phi))
 //   k2 = (v + dt/2 k1v, -G(phi + dt/2 k1phi))
 //   k3 = (v + dt/2 k2v, -G(phi + dt/2 k2phi))
 //   k4 = (v + dt   k3v, -G(phi + dt   k3phi))
 //   (phi, v) += dt/6 (k1 + 2 k2 + 2 k3 + k4)
-// then, if E_h(phi^{n+1}) > E_h(phi^n), v^{n+1} <- 0 (Eq. 4).
 // Chiral magnet: every stage input and phi^{n+1} are normalised; v^{n+1} is
 // tangent-projected at phi^{n+1}. Halo sites stay fixed (v = 0 there).
-// *E_io holds E_h(phi^n) on entry and E_h(phi^{n+1}) on exit. Returns 1 if arrested.
-int or_anf_step(int theory, const double* prm, double* f, double* v, int nx, int ny, double dx, double dy, double dt,
-                double* E_io) {
-  const Grid g{nx, ny, dx, dy};
+void rk4_update(int theory, const double* prm, double* f, double* v, const Grid& g, double dt) {
   const int C = ncomp(theory);
   const size_t N = (size_t)C * g.plane();
   const bool cm = unit_vector(theory);
@@ -809,6 +809,21 @@ int or_anf_step(int theory, const double* prm, double* f, double* v, int nx, int
     normalise(f, g);
     tangent(v, f, g);
   }
+}
+
+}  // namespace
+
+extern "C" {
+
+// One arrested-Newton-flow step (Eq. 3, Eq. 4): the RK4 update above, then, if
+// E_h(phi^{n+1}) > E_h(phi^n), v^{n+1} <- 0 (Eq. 4).
+// *E_io holds E_h(phi^n) on entry and E_h(phi^{n+1}) on exit. Returns 1 if arrested.
+int or_anf_step(int theory, const double* prm, double* f, double* v, int nx, int ny, double dx, double dy, double dt,
+                double* E_io) {
+  const Grid g{nx, ny, dx, dy};
+  const int C = ncomp(theory);
+  const size_t N = (size_t)C * g.plane();
+  rk4_update(theory, prm, f, v, g, dt);
   const double E_new = energy(theory, prm, f, g);
   int arrested = 0;
   if (E_new > *E_io) {  // Eq. 4, strict
@@ -896,6 +911,174 @@ int or_gd_minimise(int theory, const double* prm, double* f, int nx, int ny, dou
     ++steps;
   }
   out[0] = E; out[1] = norm; out[2] = (double)steps; out[3] = (double)rises;
+  return converged;
+}
+
+// ---------------------------------------------------------------- BEC at a fixed atom number
+// The BEC section holds the atom number N = int |psi|^2 fixed (its normalisation).
+// Read here as the flow on the constraint surface N_h(psi) = dx dy sum_I |psi|^2 = N0
+// of the lattice functional at zero chemical potential, E_h = dx dy sum_I e(mu = 0):
+//   refresh of a new field (psi, v):
+//     v   <- v - alpha psi on I,  alpha = sum_I v.psi / sum_I |psi|^2  (v tangent to the
+//            constraint surface; psi and the scaled psi point the same way),
+//     psi <- s psi on I,  s = sqrt(N0 / N_h(psi))  (the halo keeps its values),
+//     mu  =  sum_I G_0(psi).psi / (2 sum_I |psi|^2)  for the scaled psi, G_0 the force at
+//            zero chemical potential: the Lagrange multiplier of the constraint, for which
+//            the force G_mu = G_0 - 2 mu psi of the grand-canonical form has no part along
+//            psi (the part the constraint removes);
+//   one step: the BEC flow at chemical potential mu (held through the RK stages, like
+//     the potential of the demagnetising field), then a refresh;
+//   arrest (Eq. 4) and convergence as for every theory, on E_h at mu = 0 and on
+//     dx dy max_I |G_mu| of the refreshed field.
+// Gradient descent takes the same refresh after each Euler step (v absent).
+namespace {
+
+double bec_sum_sq(const double* f, const Grid& g) {  // sum_I |psi|^2
+  const size_t P = g.plane();
+  Neumaier a;
+  for (int j = 2; j <= g.ny - 3; ++j)
+    for (int i = 2; i <= g.nx - 3; ++i) {
+      const size_t k = (size_t)j * g.nx + i;
+      a.add(f[k] * f[k] + f[P + k] * f[P + k]);
+    }
+  return a.value();
+}
+
+// mu = sum_I G_0.psi / (2 sum_I |psi|^2); prm = {g, Omega, ...} (its mu is not used)
+double bec_multiplier(const double* prm, const double* f, const Grid& g) {
+  const double p0[3] = {prm[0], prm[1], 0.0};
+  const size_t P = g.plane();
+  std::vector<double> G(2 * P);
+  force(TH_BEC, p0, f, g, G.data());
+  Neumaier a;
+  for (size_t k = 0; k < P; ++k) a.add(G[k] * f[k] + G[P + k] * f[P + k]);  // G = 0 off I
+  return a.value() / (2.0 * bec_sum_sq(f, g));
+}
+
+// The refresh above; v may be null (gradient descent). Returns 0, or -1 if N_h(psi)
+// is zero or not finite (nothing to scale).
+int bec_refresh(const double* prm, double N0, double* f, double* v, const Grid& g, double* mu) {
+  const size_t P = g.plane();
+  const double S = bec_sum_sq(f, g);
+  if (!(S > 0.0) || !std::isfinite(S)) return -1;
+  if (v) {
+    Neumaier vp;
+    for (int j = 2; j <= g.ny - 3; ++j)
+      for (int i = 2; i <= g.nx - 3; ++i) {
+        const size_t k = (size_t)j * g.nx + i;
+        vp.add(v[k] * f[k] + v[P + k] * f[P + k]);
+      }
+    const double alpha = vp.value() / S;
+    for (int j = 2; j <= g.ny - 3; ++j)
+      for (int i = 2; i <= g.nx - 3; ++i) {
+        const size_t k = (size_t)j * g.nx + i;
+        v[k] -= alpha * f[k];
+        v[P + k] -= alpha * f[P + k];
+      }
+  }
+  const double sc = std::sqrt(N0 / (g.dx * g.dy * S));
+  for (int j = 2; j <= g.ny - 3; ++j)
+    for (int i = 2; i <= g.nx - 3; ++i) {
+      const size_t k = (size_t)j * g.nx + i;
+      f[k] *= sc;
+      f[P + k] *= sc;
+    }
+  *mu = bec_multiplier(prm, f, g);
+  return 0;
+}
+
+}  // namespace
+
+// The multiplier of a field as it stands (no scaling).
+double or_bec_multiplier(const double* prm, const double* f, int nx, int ny, double dx, double dy) {
+  return bec_multiplier(prm, f, Grid{nx, ny, dx, dy});
+}
+
+// The refresh of a new field; v may be NULL. Returns 0 or -1 (see bec_refresh).
+int or_bec_refresh(const double* prm, double N0, double* f, double* v, int nx, int ny, double dx, double dy,
+                   double* mu) {
+  return bec_refresh(prm, N0, f, v, Grid{nx, ny, dx, dy}, mu);
+}
+
+// One step at fixed atom number from a refreshed (psi, v) whose multiplier is *mu_io
+// and energy (mu = 0) *E_io: the RK4 update at chemical potential mu, the refresh,
+// then Eq. 4 on E_h at mu = 0. On exit *mu_io and *E_io belong to the new field.
+// Returns 1 if arrested, 0 if not, -1 if the refresh failed.
+int or_anf_step_fixed_n(const double* prm, double N0, double* f, double* v, int nx, int ny, double dx, double dy,
+                        double dt, double* E_io, double* mu_io) {
+  const Grid g{nx, ny, dx, dy};
+  const double pm[3] = {prm[0], prm[1], *mu_io}, p0[3] = {prm[0], prm[1], 0.0};
+  rk4_update(TH_BEC, pm, f, v, g, dt);
+  if (bec_refresh(prm, N0, f, v, g, mu_io) != 0) return -1;
+  const double E_new = energy(TH_BEC, p0, f, g);
+  int arrested = 0;
+  if (E_new > *E_io) {
+    std::memset(v, 0, sizeof(double) * 2 * g.plane());
+    arrested = 1;
+  }
+  *E_io = E_new;
+  return arrested;
+}
+
+// Arrested Newton flow at fixed atom number N0 from (phi, v), refreshed first, until
+// dx dy max_I |G_mu| < tol or max_steps steps. out = {E (mu = 0), norm, steps,
+// arrests, mu}. Returns 1 if converged, 0 if not, -1 if a refresh failed.
+int or_minimise_fixed_n(const double* prm, double N0, double* f, double* v, int nx, int ny, double dx, double dy,
+                        double dt, double tol, long long max_steps, double* out) {
+  const Grid g{nx, ny, dx, dy};
+  const size_t N = 2 * g.plane();
+  std::vector<double> G(N);
+  double mu = 0.0;
+  if (bec_refresh(prm, N0, f, v, g, &mu) != 0) return -1;
+  const double p0[3] = {prm[0], prm[1], 0.0};
+  double E = energy(TH_BEC, p0, f, g);
+  long long steps = 0, arrests = 0;
+  double norm = 0.0;
+  int converged = 0;
+  for (;;) {
+    const double pm[3] = {prm[0], prm[1], mu};
+    force(TH_BEC, pm, f, g, G.data());
+    norm = dx * dy * max_abs(G.data(), N);
+    if (norm < tol) { converged = 1; break; }
+    if (steps >= max_steps) break;
+    const int a = or_anf_step_fixed_n(prm, N0, f, v, nx, ny, dx, dy, dt, &E, &mu);
+    if (a < 0) return -1;
+    arrests += a;
+    ++steps;
+  }
+  out[0] = E; out[1] = norm; out[2] = (double)steps; out[3] = (double)arrests; out[4] = mu;
+  return converged;
+}
+
+// Gradient descent at fixed atom number: phi <- phi - dtau G_mu(phi), then the refresh
+// (no velocity); rises of E_h (mu = 0) are counted. out as for or_minimise_fixed_n
+// with out[3] = energy rises.
+int or_gd_minimise_fixed_n(const double* prm, double N0, double* f, int nx, int ny, double dx, double dy,
+                           double dtau, double tol, long long max_steps, double* out) {
+  const Grid g{nx, ny, dx, dy};
+  const size_t N = 2 * g.plane();
+  std::vector<double> G(N);
+  double mu = 0.0;
+  if (bec_refresh(prm, N0, f, nullptr, g, &mu) != 0) return -1;
+  const double p0[3] = {prm[0], prm[1], 0.0};
+  double E = energy(TH_BEC, p0, f, g);
+  long long steps = 0, rises = 0;
+  double norm = 0.0;
+  int converged = 0;
+  for (;;) {
+    const double pm[3] = {prm[0], prm[1], mu};
+    force(TH_BEC, pm, f, g, G.data());
+    norm = dx * dy * max_abs(G.data(), N);
+    if (norm < tol) { converged = 1; break; }
+    if (steps >= max_steps) break;
+    for (size_t k = 0; k < N; ++k) f[k] -= dtau * G[k];
+    if (bec_refresh(prm, N0, f, nullptr, g, &mu) != 0) return -1;
+    const double E_new = energy(TH_BEC, p0, f, g);
+    rises += E_new > E ? 1 : 0;
+    E = E_new;
+    ++steps;
+  }
+  out[0] = E; out[1] = norm; out[2] = (double)steps; out[3] = (double)rises; out[4] = mu;
   return converged;
 }
 

@@ -544,6 +544,100 @@ def test_bec_ground_state_is_the_radial_solution_and_near_thomas_fermi():
     assert 12.0 < errs[0] / errs[1] < 20.0
 
 
+# ---------------------------------------------------------------- BEC at a fixed atom number
+def _zero_halo(f):
+    f = f.copy()
+    f[:, :2, :] = 0.0
+    f[:, -2:, :] = 0.0
+    f[:, :, :2] = 0.0
+    f[:, :, -2:] = 0.0
+    return f
+
+
+def test_bec_fixed_n_refresh_scales_projects_and_takes_the_multiplier():
+    """The refresh of a new field: N_h exactly N0; v tangent to the constraint
+    (sum_I v.psi = 0); the halo untouched; the force at the multiplier orthogonal to
+    psi; and, with a zero halo (so every stencil sees s psi), the multiplier of the
+    scaled field in closed form (sum_I G_lin.psi + 2 g s^2 sum_I |psi|^4) / (2 sum_I |psi|^2),
+    G_lin the force at g = 0 and mu = 0 of the unscaled field."""
+    nx, ny, dx, dy = 41, 37, 0.21, 0.19
+    g, Om, N0 = 1.3, 0.4, 7.5
+    f = _zero_halo(I.smooth_field(BEC, nx, ny, dx, dy, seed=71))
+    v = I.smooth_velocity(BEC, nx, ny, dx, dy, seed=72, amplitude=0.3)
+    fr, vr, mu = O.bec_refresh((g, Om), N0, f, v, dx, dy)
+    In = (slice(None), slice(2, -2), slice(2, -2))
+    assert dx * dy * (fr[In] ** 2).sum() == pytest.approx(N0, rel=1e-14)
+    assert abs((vr * fr).sum()) <= 1e-13 * (np.abs(vr) * np.abs(fr)).sum()
+    ring = np.ones((ny, nx), bool)
+    ring[2:-2, 2:-2] = False
+    v[:, 2, 5] = 0.7  # a velocity on the first interior row changes; the halo's does not
+    v[:, 0, 3] = 0.2
+    fr, vr, mu = O.bec_refresh((g, Om), N0, f, v, dx, dy)
+    assert np.array_equal(vr[:, ring], v[:, ring]) and vr[0, 2, 5] != 0.7
+    G = O.force(BEC, (g, Om, mu), fr, dx, dy)
+    assert abs((G * fr).sum()) <= 1e-12 * (np.abs(G) * np.abs(fr)).sum()
+    S = (f[In] ** 2).sum()
+    sc = math.sqrt(N0 / (dx * dy * S))
+    assert np.abs(fr - sc * f).max() <= 1e-15 * sc * np.abs(f).max()
+    A = (O.force(BEC, (0.0, Om, 0.0), f, dx, dy) * f).sum()
+    B = ((f[0] ** 2 + f[1] ** 2) ** 2)[2:-2, 2:-2].sum()
+    assert mu == pytest.approx((A + 2 * g * sc * sc * B) / (2 * S), rel=1e-12)
+    # a field with a non-zero halo keeps it
+    h = I.smooth_field(BEC, nx, ny, dx, dy, seed=73)
+    hr, _, _ = O.bec_refresh((g, Om), N0, h, None, dx, dy)
+    assert np.array_equal(hr[:, ring], h[:, ring])
+    with pytest.raises(ValueError):
+        O.bec_refresh((g, Om), N0, np.zeros_like(f), None, dx, dy)
+
+
+def _bec_gc(g, mu, n, dx):
+    f = O.ansatz_bec((g, 0.0, mu), [], n, n, dx, dx)
+    r = O.minimise(BEC, (g, 0.0, mu), f, dx, dx, tol=1e-9, max_steps=40000)
+    assert r["converged"]
+    return r, O.observables(BEC, (g, 0.0, mu), r["f"], dx, dx)
+
+
+@pytest.mark.parametrize("start", ["thomas_fermi", "smooth"])
+def test_bec_fixed_n_relaxes_to_the_grand_canonical_ground_state(start):
+    """The canonical problem at N = N_h of the grand-canonical ground state at mu (Omega
+    = 0) has that ground state as its solution: the fixed-N flow from another start
+    (a Thomas-Fermi profile at a different mu, or a smooth random complex field; zero
+    halo in both) ends on the same density (the phase is free), with multiplier mu and
+    energy E_gc + mu N; gradient descent at fixed N likewise."""
+    g, mu, n, dx = 1.0, 4.0, 49, 0.2
+    r, o = _bec_gc(g, mu, n, dx)
+    N = o["atoms"]
+    rho = r["f"][0] ** 2 + r["f"][1] ** 2
+    if start == "thomas_fermi":
+        f0 = O.ansatz_bec((g, 0.0, 2.5), [], n, n, dx, dx)
+    else:
+        f0 = _zero_halo(I.smooth_field(BEC, n, n, dx, dx, seed=5))
+    for res in (O.minimise_fixed_n((g, 0.0), N, f0, dx, dx, 1e-9, 40000),
+                O.gd_minimise_fixed_n((g, 0.0), N, f0, dx, dx, 1e-9, 200000)):
+        assert res["converged"]
+        rf = res["f"]
+        assert np.abs(rf[0] ** 2 + rf[1] ** 2 - rho).max() < 1e-7 * rho.max()
+        assert res["mu"] == pytest.approx(mu, abs=1e-7)
+        assert res["energy"] == pytest.approx(o["energy"] + mu * N, rel=1e-10)
+        assert dx * dx * (rf[:, 2:-2, 2:-2] ** 2).sum() == pytest.approx(N, rel=1e-14)
+
+
+def test_bec_fixed_n_multiplier_is_dE_dN():
+    """The multiplier is the chemical potential of the canonical ground state: the
+    central difference of E(N) at N (1 +- 1e-3) against the multiplier at N."""
+    g, n, dx, N = 1.0, 49, 0.2, 40.0
+    f0 = O.ansatz_bec((g, 0.0, math.sqrt(g * N / math.pi)), [], n, n, dx, dx)
+    E = {}
+    for s in (0.999, 1.0, 1.001):
+        res = O.minimise_fixed_n((g, 0.0), N * s, f0, dx, dx, 1e-10, 40000)
+        assert res["converged"]
+        E[s] = res
+    dEdN = (E[1.001]["energy"] - E[0.999]["energy"]) / (0.002 * N)
+    assert dEdN == pytest.approx(E[1.0]["mu"], rel=2e-5)
+    # and the Thomas-Fermi value sqrt(g N / pi) is close (the kinetic term is small)
+    assert E[1.0]["mu"] == pytest.approx(math.sqrt(g * N / math.pi), rel=0.05)
+
+
 # ---------------------------------------------------------------- s+id superconductor (Table 1)
 @pytest.mark.parametrize("nu", [0.0, 0.35])
 def test_sid_reduces_to_abelian_higgs_without_the_d_band(nu):
