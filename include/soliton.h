@@ -8,7 +8,10 @@
  * arrest v <- 0 whenever E_h rises (Sec. 3.2, Eq. 4), with the unit-length
  * projection of magnetisation models in every RK stage (Sec. 3.2) and GPU-resident
  * reductions of the energy and convergence norm (Sec. 3.3). Theories: Abelian
- * Higgs (Table 1) and the chiral magnet without demagnetisation (Sec. 4.2, Eq. 5).
+ * Higgs, Baby Skyrme and the s+id superconductor (Table 1), the chiral magnet
+ * (Sec. 4.2, Eq. 5) with optional demagnetisation (Eq. 6), and the rotating trapped
+ * BEC (Sec. 4.3) in grand-canonical form or at a fixed atom number. Gradient descent
+ * is the alternative minimiser (SS_METHOD_GRADIENT).
  *
  * Conventions shared by every call:
  *  - Every call returns SS_OK (0) or a negative SS_ERR_* code; ss_last_error()
@@ -74,13 +77,20 @@ extern "C" {
                            /* e = |d m|^2/2 + kappa^2/2 |d_1 m x d_2 m|^2 + V(m),            */
                            /* V = mu^2 (1 - m_3) + nu^2/2 m_1^2 (standard potential at nu = 0,*/
                            /* easy-plane at mu = 0); projected like the chiral magnet       */
-#define SS_BEC 4           /* rotating trapped BEC (Table 1), params {g, Omega, mu}, g > 0: */
-                           /* psi = u + i v, dimensionless (hbar = m = omega = 1), in the   */
-                           /* grand-canonical form at chemical potential mu:                */
+#define SS_BEC 4           /* rotating trapped BEC (Table 1), params {g, Omega, mu[, N]},   */
+                           /* g > 0: psi = u + i v, dimensionless (hbar = m = omega = 1),  */
                            /* e = |grad psi|^2/2 + r^2/2 |psi|^2 + g/2 |psi|^4 - mu |psi|^2 */
                            /*     - Omega Re(psi* L_z psi), L_z = -i (x d_y - y d_x),       */
-                           /* (x, y) measured from the grid centre; the atom number N and  */
-                           /* the angular momentum are observables (ss_obs)                 */
+                           /* (x, y) measured from the grid centre. N = 0 (or absent):      */
+                           /* grand-canonical form at chemical potential mu. N > 0: the    */
+                           /* atom number dx dy sum_I |psi|^2 is held at N (mu is ignored): */
+                           /* every new field is scaled to N on I, its velocity made       */
+                           /* tangent to the constraint, and its step takes the force at   */
+                           /* the constraint's multiplier mu = sum G_0.psi / (2 sum |psi|^2)*/
+                           /* (G_0: mu = 0), held through the step; E_h, the arrest test   */
+                           /* and ss_obs.energy are then at mu = 0, and grad_max is the    */
+                           /* constrained residual. Fixed N needs a single-grid context.   */
+                           /* Atom number, angular momentum and mu are observables (ss_obs)*/
 #define SS_SID 5           /* s+id two-band superconductor (Table 1), params               */
                            /* {a1, a2, b1, b2, b3, b4, nu}: Delta_s, Delta_d, A (6 planes:  */
                            /* Re, Im Delta_s, Re, Im Delta_d, A_1, A_2), D = d - i A,       */
@@ -113,7 +123,9 @@ typedef struct ss_ctx ss_ctx;
  *       the Abelian Higgs model. Charge: winding of Delta_s; flux as Abelian Higgs.
  *  BEC: the Thomas-Fermi amplitude sqrt(max(0, mu - r^2/2) / g) times a vortex factor
  *       tanh(r_k/size_k)^|charge_k| exp(i (charge_k theta_k + phase_k)) per entry (an
- *       entry of charge 0 and phase 0 gives the Thomas-Fermi profile alone). */
+ *       entry of charge 0 and phase 0 gives the Thomas-Fermi profile alone). At a fixed
+ *       atom number N, mu = sqrt(g N / pi), the Thomas-Fermi value for N atoms (then
+ *       scaled to N exactly by the refresh of the new field). */
 typedef struct {
   double x, y;
   int charge;
@@ -149,6 +161,8 @@ typedef struct {
   long long steps;     /* steps taken since the fields were last set                    */
   double atoms;        /* BEC: N = dx dy sum_I |psi|^2; else 0                          */
   double angular_momentum; /* BEC: dx dy sum_I Re(psi* L_z psi); else 0                 */
+  double chemical_potential; /* BEC: mu in force (the given one, or the multiplier of    */
+                             /* the current field at a fixed atom number); else 0         */
 } ss_obs;
 
 /* Message for the calling thread's last failed call ("" if none). Owned by the
@@ -345,7 +359,9 @@ int ss_batch_destroy(ss_batch* batch);
  * `fields`, without a context, and calls no cudaMalloc, cudaFree or allocating
  * library routine.
  *
- *  theory, params, n_params: as ss_set_theory.
+ *  theory, params, n_params: as ss_set_theory, except that the two forms that
+ *             need a context's state are rejected: demagnetisation (mu_d > 0) and the
+ *             BEC at a fixed atom number (N > 0).
  *  fields:    device pointer, [C][ny][nx] planes of the given precision (float for
  *             SS_FP32, double for SS_FP64), halo included. Read only.
  *  nx, ny, dx, dy: as ss_create_grid; nx, ny <= 65536 and nx * ny <= 2^31, larger

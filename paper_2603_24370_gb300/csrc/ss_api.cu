@@ -98,13 +98,16 @@ int pack_couplings(int theory, const double* params, int n_params, double k[NCOU
     for (int i = 0; i < 7; ++i) k[i] = params[i];
     *C = 6;
   } else if (theory == SS_BEC) {
-    if (n_params != 3) return fail(SS_ERR_ARG, "BEC takes {g, Omega, mu}");
-    for (int i = 0; i < 3; ++i)
+    if (n_params < 3 || n_params > 4) return fail(SS_ERR_ARG, "BEC takes {g, Omega, mu[, N]}");
+    for (int i = 0; i < n_params; ++i)
       if (!std::isfinite(params[i])) return fail(SS_ERR_ARG, "BEC parameters must be finite");
     if (!(params[0] > 0.0)) return fail(SS_ERR_ARG, "g must be > 0 (the functional is unbounded below otherwise)");
+    const double atoms = n_params > 3 ? params[3] : 0.0;
+    if (atoms < 0.0) return fail(SS_ERR_ARG, "the atom number N must be >= 0 (0: grand-canonical form)");
     k[0] = params[0];  // g
     k[1] = params[1];  // Omega
-    k[2] = params[2];  // mu
+    k[2] = atoms > 0.0 ? 0.0 : params[2];  // mu (fixed N: the energy at mu = 0; the multiplier is held per step)
+    k[4] = atoms;      // fixed atom number N0 (0: none); host-side only
     *C = 2;
   } else if (theory == SS_BABY_SKYRME) {
     if (n_params < 2 || n_params > 3) return fail(SS_ERR_ARG, "Baby Skyrme takes {kappa, mu[, nu]}");
@@ -156,7 +159,10 @@ double descent_step(double dx, double dy, double factor, int theory = 0, int nx 
   if (theory == SS_BEC && coup) {
     const double hx = 0.5 * (nx - 1) * dx, hy = 0.5 * (ny - 1) * dy;
     const double r2 = hx * hx + hy * hy;
-    lam += r2 + 4.0 * std::fabs(coup[2]) + 2.0 * std::fabs(coup[1]) * std::sqrt(r2) * 1.3722 / (dx < dy ? dx : dy);
+    // at a fixed atom number the chemical potential is not known in advance: its
+    // Thomas-Fermi value sqrt(g N / pi) (harmonic trap, 2D) stands in for |mu|
+    const double mu = coup[4] > 0.0 ? std::sqrt(coup[0] * coup[4] / 3.14159265358979323846) : std::fabs(coup[2]);
+    lam += r2 + 4.0 * mu + 2.0 * std::fabs(coup[1]) * std::sqrt(r2) * 1.3722 / (dx < dy ? dx : dy);
   }
   return factor * 2.0 / lam;
 }
@@ -233,6 +239,7 @@ struct ss_batch {
   BatchLaunch BL{};
   int method = METHOD_ANF;      // SS_METHOD_ANF / SS_METHOD_GRADIENT
   bool demag = false;           // chiral magnet with demagnetisation (single problem)
+  bool fixed_n = false;         // BEC at a fixed atom number (single problem)
   DemagSolver* ds = nullptr;
   cudaGraphExec_t chunk = nullptr;  // K_CHUNK steps of the current method
   DevState* h_st = nullptr;  // pinned [n]
@@ -394,12 +401,32 @@ int batch_alloc(ss_batch* b) {
   return SS_OK;
 }
 
-// Demagnetisation: the potential of the current field (a no-op without demag).
-cudaError_t demag_refresh(ss_batch* b) {
-  if (!b->demag) return cudaSuccess;
+// What a new field needs before its step: the demagnetising potential, or the BEC's
+// fixed-atom-number refresh (a no-op for every other problem).
+cudaError_t field_refresh(ss_batch* b) {
   const Problem& p = b->probs[0];
-  return demag_solve(b->ds, b->st, p.phi, p.lo, p.psi, b->stream);
+  if (b->demag) return demag_solve(b->ds, b->st, p.phi, p.lo, p.psi, b->stream);
+  if (!b->fixed_n) return cudaSuccess;
+  FixedNLaunch L{};
+  L.prec = b->prec;
+  for (int k = 0; k < 2; ++k) {
+    L.phi[k] = p.phi[k];
+    L.lo[k] = p.lo[k];
+    L.v[k] = p.v[k];
+  }
+  L.nx = p.nx;
+  L.ny = p.ny;
+  L.dx = p.dx;
+  L.dy = p.dy;
+  L.g = p.coup[0];
+  L.omega = p.coup[1];
+  L.atoms = p.coup[4];
+  L.st = b->st;
+  L.part = b->opart;
+  L.blocks = b->obs_cap;
+  return launch_fixed_n_refresh(L, b->stream);
 }
+bool has_refresh(const ss_batch* b) { return b->demag || b->fixed_n; }
 
 // Launch view of one problem for the per-problem kernels (ansatz, observables);
 // phi[0] of the view is the problem's current field (parity cur).
@@ -439,8 +466,9 @@ int read_states(ss_batch* b) {
 
 int cur_of(const ss_batch* b, int i) { return (int)(b->h_st[i].steps & 1); }
 
-// New fields for problem i (already in phi[0], phi[1]): zero v and lo, reset its record.
-int problem_new_fields(ss_batch* b, int i) {
+// New fields for problem i (already in phi[0], phi[1]): zero v and lo, reset its record,
+// and (refresh) the potential or atom-number refresh of the new field.
+int problem_new_fields(ss_batch* b, int i, bool refresh = true) {
   const Problem& p = b->probs[i];
   const size_t bytes = (size_t)b->C * p.plane * b->elem;
   for (int k = 0; k < 2; ++k) {
@@ -448,7 +476,7 @@ int problem_new_fields(ss_batch* b, int i) {
     if (p.lo[k]) SS_CK(cudaMemsetAsync(p.lo[k], 0, bytes, b->stream));
   }
   SS_CK(launch_reset_states(b->st + i, 1, b->stream));
-  SS_CK(demag_refresh(b));  // the potential of the new field (step count 0: buffer 0)
+  if (refresh) SS_CK(field_refresh(b));  // the new field's potential or atom-number refresh (step count 0: buffer 0)
   b->fields_set[i] = 1;
   return SS_OK;
 }
@@ -488,11 +516,11 @@ int ensure_chunk(ss_batch* b) {
   for (int k = 0; k < K_CHUNK && e == cudaSuccess; ++k) {
     if (b->method == METHOD_GD) {
       e = launch_pass(b->BL, PASS_GD, b->stream);  // evaluate, then step
-      if (e == cudaSuccess) e = demag_refresh(b);  // the potential of the new field
+      if (e == cudaSuccess) e = field_refresh(b);  // refresh of the new field
       continue;
     }
     e = launch_pass(b->BL, 2, b->stream);                        // stages 3-4: new fields
-    if (e == cudaSuccess) e = demag_refresh(b);                  // their potential (demagnetisation)
+    if (e == cudaSuccess) e = field_refresh(b);                  // their refresh (potential, atom number)
     if (e == cudaSuccess) e = launch_pass(b->BL, 1, b->stream);  // stages 1-2 of the new fields
   }
   cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
@@ -545,10 +573,10 @@ int batch_run(ss_batch* b, double tol, long long max_steps) {
   for (int k = 0; k < rem && !stopped; ++k) {
     if (b->method == METHOD_GD) {
       SS_CK(launch_pass(b->BL, PASS_GD, b->stream));
-      SS_CK(demag_refresh(b));
+      SS_CK(field_refresh(b));
     } else {
       SS_CK(launch_pass(b->BL, 2, b->stream));
-      SS_CK(demag_refresh(b));
+      SS_CK(field_refresh(b));
       SS_CK(launch_pass(b->BL, 1, b->stream));
     }
   }
@@ -576,7 +604,9 @@ int copy_planes(ss_batch* b, int i, void* dst, const void* src, int is_device) {
 int problem_observables(ss_batch* b, int i, ss_obs* out) {
   int rc = read_states(b);
   if (rc != SS_OK) return rc;
-  SS_CK(launch_observables(problem_ctx(b, i, cur_of(b, i)), 0, b->stream));
+  LaunchCtx L = problem_ctx(b, i, cur_of(b, i));
+  if (b->fixed_n) L.coup[3] = b->h_st[i].mu_held;  // the residual of the constrained problem
+  SS_CK(launch_observables(L, 0, b->stream));
   rc = read_states(b);
   if (rc != SS_OK) return rc;
   const DevState& h = b->h_st[i];
@@ -589,6 +619,7 @@ int problem_observables(ss_batch* b, int i, ss_obs* out) {
   out->steps = h.steps;
   out->atoms = h.obs_atoms;
   out->angular_momentum = h.obs_lz;
+  out->chemical_potential = b->theory != SS_BEC ? 0.0 : (b->fixed_n ? h.mu_held : b->probs[i].coup[2]);
   return SS_OK;
 }
 
@@ -683,6 +714,7 @@ int ss_set_theory(ss_ctx* c, int theory, const double* params, int n_params) {
   b->C = C;
   b->elem = c->prec == SS_FP64 ? 8 : 4;
   b->demag = th_of_coup(theory, k) == TH_CMD;
+  b->fixed_n = theory == SS_BEC && k[4] > 0.0;
   rc = make_stream(b, c->user_stream);
   if (rc != SS_OK) {
     batch_free(b);
@@ -849,7 +881,7 @@ int ss_profile_stages(ss_ctx* c, int n_steps, float* ms_out) {
     if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
     float m = 0.f;
     if (e == cudaSuccess) e = cudaEventElapsedTime(&m, ev[0], ev[1]);
-    if (e == cudaSuccess) e = demag_refresh(b);
+    if (e == cudaSuccess) e = field_refresh(b);
     acc[0] += m;
   }
   if (gd && e == cudaSuccess) e = launch_pass(b->BL, PASS_GD, b->stream);  // evaluates the last field
@@ -858,16 +890,16 @@ int ss_profile_stages(ss_ctx* c, int n_steps, float* ms_out) {
     if (e == cudaSuccess) e = launch_pass(b->BL, 2, b->stream);  // stages 3-4 -> new field
     if (e == cudaSuccess) e = cudaEventRecord(ev[1], b->stream);
     float m1 = 0.f, m2 = 0.f;
-    if (e == cudaSuccess && b->demag) {  // the potential of the new field, outside both intervals
+    if (e == cudaSuccess && has_refresh(b)) {  // the new field's refresh, outside both intervals
       e = cudaEventSynchronize(ev[1]);
       if (e == cudaSuccess) e = cudaEventElapsedTime(&m2, ev[0], ev[1]);
-      if (e == cudaSuccess) e = demag_refresh(b);
+      if (e == cudaSuccess) e = field_refresh(b);
       if (e == cudaSuccess) e = cudaEventRecord(ev[1], b->stream);  // pass 1 starts after the solve
     }
     if (e == cudaSuccess) e = launch_pass(b->BL, 1, b->stream);  // stages 1-2 of the new field
     if (e == cudaSuccess) e = cudaEventRecord(ev[2], b->stream);
     if (e == cudaSuccess) e = cudaEventSynchronize(ev[2]);
-    if (e == cudaSuccess && !b->demag) e = cudaEventElapsedTime(&m2, ev[0], ev[1]);
+    if (e == cudaSuccess && !has_refresh(b)) e = cudaEventElapsedTime(&m2, ev[0], ev[1]);
     if (e == cudaSuccess) e = cudaEventElapsedTime(&m1, ev[1], ev[2]);
     acc[0] += m1;
     acc[1] += m2;
@@ -909,6 +941,8 @@ int ss_batch_create(ss_batch** out, int theory, int precision, const ss_batch_it
     if (rc == SS_OK) rc = pack_couplings(theory, it.params, it.n_params, k, &C);
     if (rc == SS_OK && th_of_coup(theory, k) == TH_CMD)
       rc = fail(SS_ERR_ARG, "demagnetisation (mu_d > 0) needs a single-grid context (ss_create_grid)");
+    if (rc == SS_OK && theory == SS_BEC && k[4] > 0.0)
+      rc = fail(SS_ERR_ARG, "a fixed atom number (N > 0) needs a single-grid context (ss_create_grid)");
     if (rc == SS_OK && (!it.solitons || it.n_solitons < 1)) rc = fail(SS_ERR_ARG, "every item needs at least one soliton");
     if (rc != SS_OK) {
       g_err = "item " + std::to_string(i) + ": " + g_err;
@@ -1013,13 +1047,14 @@ int batch_autotune(ss_batch* b, int trial_steps, int* choice) {
     for (int i = 0; i < n; ++i) {
       const Problem& p = b->probs[i];
       const size_t bytes = (size_t)b->C * p.plane * b->elem;
-      int r = problem_new_fields(b, i);
+      int r = problem_new_fields(b, i, false);  // the refresh must see the restored field
       if (r != SS_OK) return r;
       for (int k = 0; k < 2; ++k) {
         SS_CK(cudaMemcpyAsync(p.phi[k], snap + off[i], bytes, cudaMemcpyDeviceToDevice, b->stream));
         if (lo) SS_CK(cudaMemcpyAsync(p.lo[k], snap + off[i] + bytes, bytes, cudaMemcpyDeviceToDevice, b->stream));
       }
     }
+    SS_CK(field_refresh(b));
     return SS_OK;
   };
   int dev = 0, nsm = 0;
@@ -1140,7 +1175,7 @@ int batch_set_method(ss_batch* b, int method, double step_factor) {
     for (int k = 0; k < 2; ++k) SS_CK(cudaMemsetAsync(p.v[k], 0, bytes, b->stream));
     SS_CK(launch_reset_states(b->st + i, 1, b->stream));
   }
-  if (b->fields_set[0]) SS_CK(demag_refresh(b));  // step count 0: the potential of buffer 0
+  if (b->fields_set[0]) SS_CK(field_refresh(b));  // step count 0: refresh of buffer 0
   b->method = method;
   const int blocks_keep[2] = {b->BL.flow_blocks[0], b->BL.flow_blocks[1]};
   b->BL.flow_blocks[2] = 0;

@@ -58,6 +58,12 @@ struct DevState {
   // observables (FP64 evaluation)
   double obs_energy, obs_charge, obs_flux, obs_gmax_raw, obs_normdev;
   double obs_atoms, obs_lz;  // BEC: dx dy sum_I |psi|^2 and dx dy sum_I Re(psi* L_z psi)
+  // BEC at a fixed atom number (ss_fixedn.cu)
+  double mu_held;             // multiplier of the current field, held through its step's stages
+  double fn_scale, fn_alpha;  // refresh in progress: psi <- s psi, v <- v - alpha psi
+  long long fn_step;          // `steps` of the last refreshed field (-1: none)
+  int fn_pending;             // 1 from the refresh's first kernel to its last
+  unsigned int fn_ticket;     // arrival counter of the refresh kernels
 };
 
 struct FlowPartial {  // per-block part of the flow reduction (64 B)
@@ -196,7 +202,9 @@ SS_HD Deriv<R> stencil(const R* P, int sx, int sy, const Spacing<R>& h) {
 // Couplings in the working type. Abelian Higgs: c[0] = lambda, c[1] = u^2.
 // Chiral magnet: c[0] = J, c[1] = D, c[2] = K, c[3] = h, c[4..6] = d_1, c[7..9] = d_2.
 // Baby Skyrme: c[0] = kappa^2, c[1] = mu^2, c[2] = nu^2.
-// BEC: c[0] = g, c[1] = Omega, c[2] = mu (chemical potential).
+// BEC: c[0] = g, c[1] = Omega, c[2] = mu (chemical potential), c[3] = the held
+// multiplier of the fixed-atom-number form (force only; set per tile from the flow
+// record, 0 in the grand-canonical form).
 // s+id: c[0..6] = a1, a2, b1, b2, b3, b4, nu.
 // Chiral magnet with demagnetisation: the chiral magnet's c[0..9], c[10] = mu_d.
 constexpr int NCOUP = 12;  // couplings per problem
@@ -342,11 +350,12 @@ SS_HD R density_bec(const Couplings<R>& k, const R* v, const R* fx, const R* fy,
 }
 
 // G_u = -lap u + (r^2 + 2 g |psi|^2 - 2 mu) u - 2 Omega D v,
-// G_v = -lap v + (r^2 + 2 g |psi|^2 - 2 mu) v + 2 Omega D u.
+// G_v = -lap v + (r^2 + 2 g |psi|^2 - 2 mu) v + 2 Omega D u,
+// with mu = c[2] + c[3] (the held multiplier at a fixed atom number).
 template <typename R>
 SS_HD void force_bec(const Couplings<R>& k, const R* v, const R* fx, const R* fy, const R* fxx, const R* fyy, R x,
                      R y, R* G) {
-  const R w = (x * x + y * y) + R(2) * k.c[0] * (v[0] * v[0] + v[1] * v[1]) - R(2) * k.c[2];
+  const R w = (x * x + y * y) + R(2) * k.c[0] * (v[0] * v[0] + v[1] * v[1]) - R(2) * (k.c[2] + k.c[3]);
   const R Du = x * fy[0] - y * fx[0], Dv = x * fy[1] - y * fx[1];
   G[0] = -(fxx[0] + fyy[0]) + w * v[0] - R(2) * k.c[1] * Dv;
   G[1] = -(fxx[1] + fyy[1]) + w * v[1] + R(2) * k.c[1] * Du;

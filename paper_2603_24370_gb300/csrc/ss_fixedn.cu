@@ -1,0 +1,280 @@
+// ss_fixedn.cu -- the rotating BEC at a fixed atom number N = int |psi|^2 (the BEC
+// section: N is conserved and fixed by the normalisation of psi).
+//
+// The flow runs on the constraint surface N_h(psi) = dx dy sum_I |psi|^2 = N0 of the
+// lattice functional at zero chemical potential. Every new field (psi, v) is
+// refreshed before its step:
+//   v   <- v - alpha psi on I,  alpha = sum_I v.psi / sum_I |psi|^2  (tangent to the surface;
+//                                psi and the scaled psi point the same way),
+//   psi <- s psi on I,          s = sqrt(N0 / N_h(psi))              (the halo keeps its values),
+//   mu  =  sum_I G_0(psi).psi / (2 sum_I |psi|^2) of the scaled psi  (the Lagrange multiplier),
+// and the step's RK stages take the force G_0 - 2 mu psi of the grand-canonical form at
+// that mu (held through the step, like the demagnetising potential), which has no
+// component along psi; the energy, its change and the arrest test (Eq. 4) are those
+// of mu = 0. The previous field in the other ping-pong buffer is a refreshed field
+// too, so Eq. 4 compares two fields of the same atom number.
+//
+// Three launches per refresh, every block skipping unless the problem holds a field
+// not refreshed yet (its step count moved since the last refresh) and is running:
+//   k_fn_sums   sum_I |psi|^2 and sum_I v.psi (FP64, compensated, fixed order); the
+//               last block derives s and alpha (a field without atoms stops the flow
+//               as non-finite);
+//   k_fn_mu     sum_I G_0(psi').psi' and sum_I |psi'|^2 over the scaled field psi' as
+//               the flow will see it (the working type's rounding of s psi on I, psi on
+//               the halo), staged per tile from the unscaled planes; the last block
+//               stores mu;
+//   k_fn_apply  psi <- s psi (re-split into value and remainder when compensated),
+//               v <- v - alpha psi on I; the last block marks the field refreshed.
+#include <cuda_runtime.h>
+
+#include "ss_internal.h"
+
+namespace ss {
+namespace {
+
+template <typename R>
+struct FnArgs {
+  R* phi[2];
+  R* lo[2];  // compensated FP32: remainder planes (else null)
+  R* v[2];
+  int nx, ny;
+  size_t plane;
+  int ntx, ntiles;  // tiles of the staged kernel
+  Spacing<R> h;
+  R hx, hy;
+  Couplings<R> k0;  // g, Omega; mu = 0
+  double n0;        // the atom number held
+  double area;      // dx dy
+  DevState* st;
+  ObsPartial* part;
+};
+
+// The last block to arrive (thread 0's view is broadcast through s_last).
+__device__ __forceinline__ bool fn_arrive(DevState* st, int tid, int* s_last) {
+  if (tid == 0) {
+    __threadfence();
+    const unsigned prev = atomicAdd(&st->fn_ticket, 1u);
+    *s_last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  const bool last = *s_last != 0;
+  if (last) __threadfence();
+  return last;
+}
+
+// Block partials -> the fixed-order total of two compensated sums (last block).
+__device__ __forceinline__ void fn_total(const ObsPartial* part, DD& a, DD& b, double* sred) {
+  DD sa{0.0, 0.0}, sb{0.0, 0.0};
+  const int tid = threadIdx.y * BX + threadIdx.x;
+  for (int i = tid; i < (int)gridDim.x; i += NT) {
+    sa = dd_add(sa, DD{__ldcg(&part[i].es), __ldcg(&part[i].ec)});
+    sb = dd_add(sb, DD{__ldcg(&part[i].fs), __ldcg(&part[i].fc)});
+  }
+  DD sv[2] = {sa, sb};
+  double mv[1] = {0.0};
+  block_reduce<2, 1>(sv, mv, sred);
+  a = sv[0];
+  b = sv[1];
+}
+
+template <typename R>
+__global__ void __launch_bounds__(NT) k_fn_sums(FnArgs<R> a) {
+  __shared__ double sred[RedSmem<2, 1>::n];
+  __shared__ int s_last;
+  DevState* st = a.st;
+  if (st->nonfinite || st->fn_step == st->steps) return;  // uniform: nothing changes them before the last block
+  const int cur = (int)(st->steps & 1);
+  const R* __restrict__ f = a.phi[cur];
+  const R* __restrict__ lo = a.lo[cur];
+  const R* __restrict__ v = a.v[cur];
+  const int tid = threadIdx.y * BX + threadIdx.x;
+  const int iw = a.nx - 2 * HALO;
+  const size_t n = (size_t)iw * (a.ny - 2 * HALO);
+  DD sn{0.0, 0.0}, sv{0.0, 0.0};
+  for (size_t t = (size_t)blockIdx.x * NT + tid; t < n; t += (size_t)gridDim.x * NT) {
+    const size_t s = (t / iw + HALO) * a.nx + (t % iw + HALO);
+    double nn = 0.0, vp = 0.0;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const double x = (double)f[c * a.plane + s] + (lo ? (double)lo[c * a.plane + s] : 0.0);
+      nn += x * x;
+      vp += (double)v[c * a.plane + s] * x;
+    }
+    neumaier(sn, nn);
+    neumaier(sv, vp);
+  }
+  DD sums[2] = {sn, sv};
+  double mv[1] = {0.0};
+  block_reduce<2, 1>(sums, mv, sred);
+  if (tid == 0) {
+    ObsPartial* p = a.part + blockIdx.x;
+    p->es = sums[0].s; p->ec = sums[0].c;
+    p->fs = sums[1].s; p->fc = sums[1].c;
+  }
+  if (!fn_arrive(st, tid, &s_last)) return;
+  DD tn, tv;
+  fn_total(a.part, tn, tv, sred);
+  if (tid == 0) {
+    const double S = tn.s + tn.c;
+    st->fn_ticket = 0;
+    if (!(S > 0.0) || !isfinite(S) || !isfinite(tv.s + tv.c)) {
+      st->nonfinite = 1;  // no atoms to scale: the flow stops
+      return;
+    }
+    st->fn_scale = sqrt(a.n0 / (a.area * S));
+    st->fn_alpha = (tv.s + tv.c) / S;
+    st->fn_pending = 1;
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(NT) k_fn_mu(FnArgs<R> a) {
+  constexpr int RPT = TY / BY;  // rows per thread
+  __shared__ R sY[2][SY * SX];
+  __shared__ double sred[RedSmem<2, 1>::n];
+  __shared__ int s_last;
+  DevState* st = a.st;
+  if (!st->fn_pending) return;
+  const int cur = (int)(st->steps & 1);
+  const R* __restrict__ f = a.phi[cur];
+  const R* __restrict__ lo = a.lo[cur];
+  const double sc = st->fn_scale;
+  const int tid = threadIdx.y * BX + threadIdx.x;
+  DD sg{0.0, 0.0}, sn{0.0, 0.0};
+  for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+    const int x0 = (t % a.ntx) * TX, y0 = (t / a.ntx) * TY;
+    __syncthreads();
+    for (int idx = tid; idx < SX * SY; idx += NT) {
+      const int lx = idx % SX, ly = idx / SX;
+      const int gx = x0 + lx - HALO, gy = y0 + ly - HALO;
+      const bool in = gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny;
+      const bool inside = gx >= HALO && gx < a.nx - HALO && gy >= HALO && gy < a.ny - HALO;
+      const size_t s = (size_t)gy * a.nx + gx;
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        R y = R(0);
+        if (in) {
+          const double x = (double)f[c * a.plane + s] + (lo ? (double)lo[c * a.plane + s] : 0.0);
+          y = inside ? R(sc * x) : f[c * a.plane + s];  // what the flow will read after k_fn_apply
+        }
+        sY[c][idx] = y;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      const int lx = threadIdx.x, ly = threadIdx.y + r * BY;
+      const int gx = x0 + lx, gy = y0 + ly;
+      if (gx < HALO || gx >= a.nx - HALO || gy < HALO || gy >= a.ny - HALO) continue;
+      const int sx = lx + HALO, sy = ly + HALO;
+      R v[2], fx[2], fy[2], fxx[2], fyy[2], G[2];
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const Deriv<R> d = stencil<R, true, false>(sY[c], sx, sy, a.h);
+        v[c] = d.v; fx[c] = d.fx; fy[c] = d.fy; fxx[c] = d.fxx; fyy[c] = d.fyy;
+      }
+      const R x = R(gx - 0.5 * (a.nx - 1)) * a.hx, y = R(gy - 0.5 * (a.ny - 1)) * a.hy;
+      force_bec<R>(a.k0, v, fx, fy, fxx, fyy, x, y, G);
+      neumaier(sg, (double)G[0] * (double)v[0] + (double)G[1] * (double)v[1]);
+      neumaier(sn, (double)v[0] * (double)v[0] + (double)v[1] * (double)v[1]);
+    }
+  }
+  DD sums[2] = {sg, sn};
+  double mv[1] = {0.0};
+  block_reduce<2, 1>(sums, mv, sred);
+  if (tid == 0) {
+    ObsPartial* p = a.part + blockIdx.x;
+    p->es = sums[0].s; p->ec = sums[0].c;
+    p->fs = sums[1].s; p->fc = sums[1].c;
+  }
+  if (!fn_arrive(st, tid, &s_last)) return;
+  DD tg, tn;
+  fn_total(a.part, tg, tn, sred);
+  if (tid == 0) {
+    st->fn_ticket = 0;
+    st->mu_held = (tg.s + tg.c) / (2.0 * (tn.s + tn.c));
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(NT) k_fn_apply(FnArgs<R> a) {
+  __shared__ int s_last;
+  DevState* st = a.st;
+  if (!st->fn_pending) return;
+  const int cur = (int)(st->steps & 1);
+  R* __restrict__ f = a.phi[cur];
+  R* __restrict__ lo = a.lo[cur];
+  R* __restrict__ v = a.v[cur];
+  const double sc = st->fn_scale, al = st->fn_alpha;
+  const int tid = threadIdx.y * BX + threadIdx.x;
+  const int iw = a.nx - 2 * HALO;
+  const size_t n = (size_t)iw * (a.ny - 2 * HALO);
+  for (size_t t = (size_t)blockIdx.x * NT + tid; t < n; t += (size_t)gridDim.x * NT) {
+    const size_t s = (t / iw + HALO) * a.nx + (t % iw + HALO);
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const size_t k = c * a.plane + s;
+      const double x = (double)f[k] + (lo ? (double)lo[k] : 0.0);
+      v[k] = R((double)v[k] - al * x);
+      const double y = sc * x;
+      const R hi = R(y);
+      f[k] = hi;
+      if (lo) lo[k] = R(y - (double)hi);
+    }
+  }
+  if (!fn_arrive(st, tid, &s_last)) return;
+  if (tid == 0) {
+    st->fn_ticket = 0;
+    st->fn_pending = 0;
+    st->fn_step = st->steps;
+  }
+}
+
+template <typename R>
+cudaError_t fixed_n_t(const FixedNLaunch& L, cudaStream_t s) {
+  FnArgs<R> a{};
+  for (int k = 0; k < 2; ++k) {
+    a.phi[k] = static_cast<R*>(L.phi[k]);
+    a.lo[k] = static_cast<R*>(L.lo[k]);
+    a.v[k] = static_cast<R*>(L.v[k]);
+  }
+  a.nx = L.nx;
+  a.ny = L.ny;
+  a.plane = (size_t)L.nx * L.ny;
+  a.ntx = (L.nx + TX - 1) / TX;
+  a.ntiles = a.ntx * ((L.ny + TY - 1) / TY);
+  a.h.i12dx = R(1.0 / (12.0 * L.dx));
+  a.h.i12dy = R(1.0 / (12.0 * L.dy));
+  a.h.i12dx2 = R(1.0 / (12.0 * L.dx * L.dx));
+  a.h.i12dy2 = R(1.0 / (12.0 * L.dy * L.dy));
+  a.h.i144dxdy = R(1.0 / (144.0 * L.dx * L.dy));
+  a.hx = R(L.dx);
+  a.hy = R(L.dy);
+  a.k0.c[0] = R(L.g);
+  a.k0.c[1] = R(L.omega);
+  a.n0 = L.atoms;
+  a.area = L.dx * L.dy;
+  a.st = L.st;
+  a.part = L.part;
+  const size_t n = (size_t)(L.nx - 2 * HALO) * (L.ny - 2 * HALO);
+  int g1 = (int)((n + NT - 1) / NT);
+  if (g1 > L.blocks) g1 = L.blocks;
+  int g2 = a.ntiles < L.blocks ? a.ntiles : L.blocks;
+  const dim3 blk(BX, BY);
+  k_fn_sums<R><<<g1, blk, 0, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_fn_mu<R><<<g2, blk, 0, s>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_fn_apply<R><<<g1, blk, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_fixed_n_refresh(const FixedNLaunch& L, cudaStream_t s) {
+  return L.prec == PREC_F64 ? fixed_n_t<double>(L, s) : fixed_n_t<float>(L, s);
+}
+
+}  // namespace ss

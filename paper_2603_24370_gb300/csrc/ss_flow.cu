@@ -30,6 +30,12 @@ __global__ void k_reset_states(DevState* st, int n) {
     s->nonfinite = 0;
     s->ticket = 0;
     s->obs_ticket = 0;
+    s->mu_held = 0.0;
+    s->fn_scale = 1.0;
+    s->fn_alpha = 0.0;
+    s->fn_step = -1;
+    s->fn_pending = 0;
+    s->fn_ticket = 0;
   }
 }
 

@@ -449,7 +449,8 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
     R* __restrict__ kv1 = D.kv[0];
     R* __restrict__ kv2 = D.kv[1];
     const Spacing<R> h = D.h;
-    const Couplings<R> kc = D.k;
+    Couplings<R> kc = D.k;
+    if (TH == TH_BEC) kc.c[3] = R(D.st->mu_held);  // fixed atom number: the field's multiplier
     const R dt = D.dt, hdt = R(0.5) * dt;
     const R c3 = R(0.25) * dt * dt, c4 = R(0.5) * dt * dt;
     const int lt = t - D.tile0;  // tile index within the problem

@@ -121,6 +121,20 @@ void demag_destroy(DemagSolver* d);
 cudaError_t demag_solve(DemagSolver* d, const DevState* st, void* const phi[2], void* const lo[2], void* const psi[2],
                         cudaStream_t s);
 
+// The rotating BEC at a fixed atom number (ss_fixedn.cu): the refresh of a new field
+// (scale to the atom number, velocity tangent to the constraint, the multiplier
+// st->mu_held), three launches that skip unless the current field is new.
+struct FixedNLaunch {
+  int prec;                          // PREC_*
+  void* phi[2]; void* lo[2]; void* v[2];
+  int nx, ny;
+  double dx, dy, g, omega, atoms;
+  DevState* st;
+  ObsPartial* part;                  // >= blocks entries
+  int blocks;                        // grid cap
+};
+cudaError_t launch_fixed_n_refresh(const FixedNLaunch& L, cudaStream_t s);
+
 // Record the calling thread's error message for ss_last_error().
 void set_last_error(const std::string& msg);
 

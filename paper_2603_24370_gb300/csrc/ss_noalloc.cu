@@ -104,8 +104,11 @@ extern "C" int ss_observables_noalloc(int theory, const double* params, int n_pa
       k[i] = params[i];
     }
   } else if (theory == SS_BEC) {
-    if (n_params != 3) return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: BEC takes {g, Omega, mu}");
-    for (int i = 0; i < 3; ++i)
+    if (n_params == 4 && params[3] != 0.0)
+      return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: a fixed atom number needs a context (its multiplier)");
+    if (n_params < 3 || n_params > 4)
+      return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: BEC takes {g, Omega, mu[, N = 0]}");
+    for (int i = 0; i < n_params; ++i)
       if (!std::isfinite(params[i])) return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: parameters must be finite");
     if (!(params[0] > 0.0)) return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: g must be > 0");
     k[0] = params[0];

@@ -344,7 +344,8 @@ static void sid_uniform_minimum(const double* k, double* rs, double* rd, double*
 template <int TH, typename R>
 static cudaError_t ansatz_t(const LaunchCtx& c, const double* sol, int n, cudaStream_t s) {
   const int blocks = (int)((c.plane + 255) / 256 < 4096 ? (c.plane + 255) / 256 : 4096);
-  double q[3] = {c.coup[0], c.coup[2], 0.0};  // BEC: g, mu
+  // BEC: g and mu; at a fixed atom number N the Thomas-Fermi mu of N atoms, sqrt(g N / pi)
+  double q[3] = {c.coup[0], c.coup[4] > 0.0 ? std::sqrt(c.coup[0] * c.coup[4] / 3.14159265358979323846) : c.coup[2], 0.0};
   if (TH == TH_SID) sid_uniform_minimum(c.coup, &q[0], &q[1], &q[2]);
   k_ansatz<TH, R><<<blocks, 256, 0, s>>>(static_cast<R*>(c.phi[0]), static_cast<R*>(c.phi[1]), c.nx, c.ny, c.plane,
                                          c.dx, c.dy, sol, n, q[0], q[1], q[2]);

@@ -76,7 +76,8 @@ class ss_batch_item(ctypes.Structure):
 class ss_obs(ctypes.Structure):
     _fields_ = [("energy", ctypes.c_double), ("charge", ctypes.c_double), ("flux", ctypes.c_double),
                 ("grad_max", ctypes.c_double), ("grad_max_raw", ctypes.c_double), ("norm_dev", ctypes.c_double),
-                ("steps", ctypes.c_longlong), ("atoms", ctypes.c_double), ("angular_momentum", ctypes.c_double)]
+                ("steps", ctypes.c_longlong), ("atoms", ctypes.c_double), ("angular_momentum", ctypes.c_double),
+                ("chemical_potential", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
