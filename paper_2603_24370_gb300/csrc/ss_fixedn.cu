@@ -77,6 +77,65 @@ __device__ __forceinline__ void fn_total(const ObsPartial* part, DD& a, DD& b, d
   b = sv[1];
 }
 
+// Per-thread sums of products in the working type's extended precision: FP32 as a
+// float-float pair (the product's rounding error recovered by FMA, the running sum by
+// TwoSum), FP64 as a plain double. A thread sums tens of terms before the FP64 block
+// reduction, so both keep ~1e-13 relative, which the arrest test needs of the atom
+// number, while the per-site work stays off the FP64 units (a small fraction of the
+// FP32 rate on this GPU).
+struct AccF {
+  float h = 0.f, l = 0.f;
+  __device__ __forceinline__ void add(float p, float e) {  // p + e, |e| << |p|
+    const float t = h + p, bp = t - h;
+    l += ((h - (t - bp)) + (p - bp)) + e;
+    h = t;
+  }
+  __device__ __forceinline__ void add_prod(float a, float b) {
+    const float p = a * b;
+    add(p, fmaf(a, b, -p));
+  }
+  __device__ __forceinline__ void add_small(float x) { l += x; }
+  __device__ __forceinline__ double value() const { return (double)h + (double)l; }
+};
+struct AccD {
+  double s = 0.0;
+  __device__ __forceinline__ void add_prod(double a, double b) { s = fma(a, b, s); }
+  __device__ __forceinline__ void add_small(double x) { s += x; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <typename R>
+struct AccOf { using T = AccF; };
+template <>
+struct AccOf<double> { using T = AccD; };
+
+// The scale factor in the working type: FP32 as a float pair (s = sh + sl).
+struct ScaleF {
+  float h, l;
+  __device__ explicit ScaleF(double s) : h((float)s), l((float)(s - (double)(float)s)) {}
+};
+// y = s (hi + lo) as value + remainder: the product's rounding error recovered by FMA
+// and the small cross terms added in FP32, then a fast TwoSum (|p| >= |e|), so the
+// value is the FP32 rounding of s (hi + lo) to within the remainder's ~1e-14. Both
+// the multiplier's staging and the in-place scaling call this, so they agree bitwise.
+__device__ __forceinline__ void scale_split(const ScaleF& s, float hi, float lo, float& yh, float& yl) {
+  const float p = s.h * hi;
+  const float e = fmaf(s.h, hi, -p) + fmaf(s.h, lo, s.l * hi);
+  yh = p + e;
+  yl = e - (yh - p);
+}
+struct ScaleD {
+  double v;
+  __device__ explicit ScaleD(double s) : v(s) {}
+};
+__device__ __forceinline__ void scale_split(const ScaleD& s, double hi, double lo, double& yh, double& yl) {
+  yh = s.v * (hi + lo);
+  yl = 0.0;
+}
+template <typename R>
+struct ScaleOf { using T = ScaleF; };
+template <>
+struct ScaleOf<double> { using T = ScaleD; };
+
 template <typename R>
 __global__ void __launch_bounds__(NT) k_fn_sums(FnArgs<R> a) {
   __shared__ double sred[RedSmem<2, 1>::n];
@@ -88,22 +147,20 @@ __global__ void __launch_bounds__(NT) k_fn_sums(FnArgs<R> a) {
   const R* __restrict__ lo = a.lo[cur];
   const R* __restrict__ v = a.v[cur];
   const int tid = threadIdx.y * BX + threadIdx.x;
-  const int iw = a.nx - 2 * HALO;
-  const size_t n = (size_t)iw * (a.ny - 2 * HALO);
-  DD sn{0.0, 0.0}, sv{0.0, 0.0};
-  for (size_t t = (size_t)blockIdx.x * NT + tid; t < n; t += (size_t)gridDim.x * NT) {
-    const size_t s = (t / iw + HALO) * a.nx + (t % iw + HALO);
-    double nn = 0.0, vp = 0.0;
+  typename AccOf<R>::T an, av;
+  // a block per interior row at a time, its threads along the row (no index division)
+  for (int j = HALO + blockIdx.x; j < a.ny - HALO; j += gridDim.x)
+    for (int i = HALO + tid; i < a.nx - HALO; i += NT) {
+      const size_t s = (size_t)j * a.nx + i;
 #pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      const double x = (double)f[c * a.plane + s] + (lo ? (double)lo[c * a.plane + s] : 0.0);
-      nn += x * x;
-      vp += (double)v[c * a.plane + s] * x;
+      for (int c = 0; c < 2; ++c) {
+        const R hi = f[c * a.plane + s], l = lo ? lo[c * a.plane + s] : R(0);
+        an.add_prod(hi, hi);             // (hi + lo)^2 = hi^2 + 2 hi lo + (lo^2: below the sum's precision)
+        an.add_small(R(2) * hi * l);
+        av.add_prod(v[c * a.plane + s], hi);  // v.psi: the velocity's own precision suffices
+      }
     }
-    neumaier(sn, nn);
-    neumaier(sv, vp);
-  }
-  DD sums[2] = {sn, sv};
+  DD sums[2] = {DD{an.value(), 0.0}, DD{av.value(), 0.0}};
   double mv[1] = {0.0};
   block_reduce<2, 1>(sums, mv, sred);
   if (tid == 0) {
@@ -138,9 +195,9 @@ __global__ void __launch_bounds__(NT) k_fn_mu(FnArgs<R> a) {
   const int cur = (int)(st->steps & 1);
   const R* __restrict__ f = a.phi[cur];
   const R* __restrict__ lo = a.lo[cur];
-  const double sc = st->fn_scale;
+  const typename ScaleOf<R>::T sc(st->fn_scale);
   const int tid = threadIdx.y * BX + threadIdx.x;
-  DD sg{0.0, 0.0}, sn{0.0, 0.0};
+  typename AccOf<R>::T ag, an;
   for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
     const int x0 = (t % a.ntx) * TX, y0 = (t / a.ntx) * TY;
     __syncthreads();
@@ -154,8 +211,11 @@ __global__ void __launch_bounds__(NT) k_fn_mu(FnArgs<R> a) {
       for (int c = 0; c < 2; ++c) {
         R y = R(0);
         if (in) {
-          const double x = (double)f[c * a.plane + s] + (lo ? (double)lo[c * a.plane + s] : 0.0);
-          y = inside ? R(sc * x) : f[c * a.plane + s];  // what the flow will read after k_fn_apply
+          y = f[c * a.plane + s];
+          if (inside) {  // what the flow will read after k_fn_apply
+            R yl;
+            scale_split(sc, y, lo ? lo[c * a.plane + s] : R(0), y, yl);
+          }
         }
         sY[c][idx] = y;
       }
@@ -173,13 +233,15 @@ __global__ void __launch_bounds__(NT) k_fn_mu(FnArgs<R> a) {
         const Deriv<R> d = stencil<R, true, false>(sY[c], sx, sy, a.h);
         v[c] = d.v; fx[c] = d.fx; fy[c] = d.fy; fxx[c] = d.fxx; fyy[c] = d.fyy;
       }
-      const R x = R(gx - 0.5 * (a.nx - 1)) * a.hx, y = R(gy - 0.5 * (a.ny - 1)) * a.hy;
+      const R x = (R(gx) - R(0.5) * R(a.nx - 1)) * a.hx, y = (R(gy) - R(0.5) * R(a.ny - 1)) * a.hy;
       force_bec<R>(a.k0, v, fx, fy, fxx, fyy, x, y, G);
-      neumaier(sg, (double)G[0] * (double)v[0] + (double)G[1] * (double)v[1]);
-      neumaier(sn, (double)v[0] * (double)v[0] + (double)v[1] * (double)v[1]);
+      ag.add_prod(G[0], v[0]);
+      ag.add_prod(G[1], v[1]);
+      an.add_prod(v[0], v[0]);
+      an.add_prod(v[1], v[1]);
     }
   }
-  DD sums[2] = {sg, sn};
+  DD sums[2] = {DD{ag.value(), 0.0}, DD{an.value(), 0.0}};
   double mv[1] = {0.0};
   block_reduce<2, 1>(sums, mv, sred);
   if (tid == 0) {
@@ -205,23 +267,23 @@ __global__ void __launch_bounds__(NT) k_fn_apply(FnArgs<R> a) {
   R* __restrict__ f = a.phi[cur];
   R* __restrict__ lo = a.lo[cur];
   R* __restrict__ v = a.v[cur];
-  const double sc = st->fn_scale, al = st->fn_alpha;
+  const typename ScaleOf<R>::T sc(st->fn_scale);
+  const R al = R(st->fn_alpha);
   const int tid = threadIdx.y * BX + threadIdx.x;
-  const int iw = a.nx - 2 * HALO;
-  const size_t n = (size_t)iw * (a.ny - 2 * HALO);
-  for (size_t t = (size_t)blockIdx.x * NT + tid; t < n; t += (size_t)gridDim.x * NT) {
-    const size_t s = (t / iw + HALO) * a.nx + (t % iw + HALO);
+  for (int j = HALO + blockIdx.x; j < a.ny - HALO; j += gridDim.x)
+    for (int i = HALO + tid; i < a.nx - HALO; i += NT) {
+      const size_t s = (size_t)j * a.nx + i;
 #pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      const size_t k = c * a.plane + s;
-      const double x = (double)f[k] + (lo ? (double)lo[k] : 0.0);
-      v[k] = R((double)v[k] - al * x);
-      const double y = sc * x;
-      const R hi = R(y);
-      f[k] = hi;
-      if (lo) lo[k] = R(y - (double)hi);
+      for (int c = 0; c < 2; ++c) {
+        const size_t k = c * a.plane + s;
+        const R hi = f[k], l = lo ? lo[k] : R(0);
+        v[k] = v[k] - al * hi;  // alpha psi: the velocity's own precision suffices
+        R yh, yl;
+        scale_split(sc, hi, l, yh, yl);
+        f[k] = yh;
+        if (lo) lo[k] = yl;
+      }
     }
-  }
   if (!fn_arrive(st, tid, &s_last)) return;
   if (tid == 0) {
     st->fn_ticket = 0;
@@ -256,8 +318,7 @@ cudaError_t fixed_n_t(const FixedNLaunch& L, cudaStream_t s) {
   a.area = L.dx * L.dy;
   a.st = L.st;
   a.part = L.part;
-  const size_t n = (size_t)(L.nx - 2 * HALO) * (L.ny - 2 * HALO);
-  int g1 = (int)((n + NT - 1) / NT);
+  int g1 = L.ny - 2 * HALO;  // interior rows
   if (g1 > L.blocks) g1 = L.blocks;
   int g2 = a.ntiles < L.blocks ? a.ntiles : L.blocks;
   const dim3 blk(BX, BY);
