@@ -150,6 +150,63 @@ __device__ __forceinline__ void block_reduce(DD (&s)[K], double (&m)[L], double*
   __syncthreads();
 }
 
+// ------------------------------------------------------------------ FP32 compensated sums
+// FP32 pairs keep reductions of FP32 kernels on the FP32 units: this GPU's FP64 rate
+// is a small fraction of its FP32 rate, and an FP64 block reduction would stall the
+// SM for microseconds.
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bp = s - a;
+  e = (a - (s - bp)) + (b - bp);
+}
+
+// Block reduction in the working type: two compensated sums, one max.
+template <typename R>
+struct RPair {
+  R s, c;
+};
+__device__ __forceinline__ RPair<float> pair_add(RPair<float> x, RPair<float> y) {
+  float s, e;
+  two_sum_f(x.s, y.s, s, e);
+  return RPair<float>{s, x.c + y.c + e};
+}
+__device__ __forceinline__ RPair<double> pair_add(RPair<double> x, RPair<double> y) {
+  double s, e;
+  two_sum(x.s, y.s, s, e);
+  return RPair<double>{s, x.c + y.c + e};
+}
+template <typename R>
+__device__ __forceinline__ R rmax(R a, R b) {
+  return (b > a || b != b) ? b : a;  // propagates NaN
+}
+// Block-wide: thread 0 ends with the block's two pairs and maximum. sm holds
+// (NT / 32) * 5 values of R. Fixed shape: bitwise reproducible.
+template <typename R>
+__device__ __forceinline__ void tile_reduce(RPair<R>& a, RPair<R>& b, R& m, R* sm) {
+  constexpr int W = NT / 32;
+  const int lane = threadIdx.x & 31, wid = (threadIdx.y * BX + threadIdx.x) >> 5;
+  for (int off = 16; off > 0; off >>= 1) {
+    a = pair_add(a, RPair<R>{__shfl_down_sync(0xffffffffu, a.s, off), __shfl_down_sync(0xffffffffu, a.c, off)});
+    b = pair_add(b, RPair<R>{__shfl_down_sync(0xffffffffu, b.s, off), __shfl_down_sync(0xffffffffu, b.c, off)});
+    m = rmax(m, __shfl_down_sync(0xffffffffu, m, off));
+  }
+  if (lane == 0) {
+    sm[wid] = a.s; sm[W + wid] = a.c; sm[2 * W + wid] = b.s; sm[3 * W + wid] = b.c; sm[4 * W + wid] = m;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    a = lane < W ? RPair<R>{sm[lane], sm[W + lane]} : RPair<R>{R(0), R(0)};
+    b = lane < W ? RPair<R>{sm[2 * W + lane], sm[3 * W + lane]} : RPair<R>{R(0), R(0)};
+    m = lane < W ? sm[4 * W + lane] : R(0);
+    for (int off = 16; off > 0; off >>= 1) {
+      a = pair_add(a, RPair<R>{__shfl_down_sync(0xffffffffu, a.s, off), __shfl_down_sync(0xffffffffu, a.c, off)});
+      b = pair_add(b, RPair<R>{__shfl_down_sync(0xffffffffu, b.s, off), __shfl_down_sync(0xffffffffu, b.c, off)});
+      m = rmax(m, __shfl_down_sync(0xffffffffu, m, off));
+    }
+  }
+  __syncthreads();
+}
+
 // ------------------------------------------------------------------ stencils
 // Spacing factors of Eq. 1 / Eq. 2, precomputed per context in the working type.
 template <typename R>

@@ -62,19 +62,35 @@ __device__ __forceinline__ bool fn_arrive(DevState* st, int tid, int* s_last) {
   return last;
 }
 
-// Block partials -> the fixed-order total of two compensated sums (last block).
-__device__ __forceinline__ void fn_total(const ObsPartial* part, DD& a, DD& b, double* sred) {
-  DD sa{0.0, 0.0}, sb{0.0, 0.0};
+// Block sums of two per-thread pairs (thread 0 ends with them), in the working type:
+// FP32 pairs for the FP32 kernels (this GPU's FP64 units would stall the SM for
+// microseconds on an FP64 tree), FP64 pairs for FP64. sm holds (NT / 32) * 5 values.
+template <typename R>
+__device__ __forceinline__ void pair_block_sum(RPair<R>& a, RPair<R>& b, R* sm) {
+  R m = R(0);
+  tile_reduce<R>(a, b, m, sm);
+}
+
+// Block partials -> the fixed-order totals of two sums (last block); the partials hold
+// the working type's pairs exactly.
+template <typename R>
+__device__ __forceinline__ void fn_total(const ObsPartial* part, double& ta, double& tb, R* sm) {
+  RPair<R> sa{R(0), R(0)}, sb{R(0), R(0)};
   const int tid = threadIdx.y * BX + threadIdx.x;
   for (int i = tid; i < (int)gridDim.x; i += NT) {
-    sa = dd_add(sa, DD{__ldcg(&part[i].es), __ldcg(&part[i].ec)});
-    sb = dd_add(sb, DD{__ldcg(&part[i].fs), __ldcg(&part[i].fc)});
+    sa = pair_add(sa, RPair<R>{R(__ldcg(&part[i].es)), R(__ldcg(&part[i].ec))});
+    sb = pair_add(sb, RPair<R>{R(__ldcg(&part[i].fs)), R(__ldcg(&part[i].fc))});
   }
-  DD sv[2] = {sa, sb};
-  double mv[1] = {0.0};
-  block_reduce<2, 1>(sv, mv, sred);
-  a = sv[0];
-  b = sv[1];
+  pair_block_sum<R>(sa, sb, sm);
+  ta = (double)sa.s + (double)sa.c;
+  tb = (double)sb.s + (double)sb.c;
+}
+
+// Thread 0 writes the block's pairs as its partial.
+template <typename R>
+__device__ __forceinline__ void fn_partial(ObsPartial* p, const RPair<R>& a, const RPair<R>& b) {
+  p->es = (double)a.s; p->ec = (double)a.c;
+  p->fs = (double)b.s; p->fc = (double)b.c;
 }
 
 // Per-thread sums of products in the working type's extended precision: FP32 as a
@@ -95,13 +111,13 @@ struct AccF {
     add(p, fmaf(a, b, -p));
   }
   __device__ __forceinline__ void add_small(float x) { l += x; }
-  __device__ __forceinline__ double value() const { return (double)h + (double)l; }
+  __device__ __forceinline__ RPair<float> pair() const { return RPair<float>{h, l}; }
 };
 struct AccD {
   double s = 0.0;
   __device__ __forceinline__ void add_prod(double a, double b) { s = fma(a, b, s); }
   __device__ __forceinline__ void add_small(double x) { s += x; }
-  __device__ __forceinline__ double value() const { return s; }
+  __device__ __forceinline__ RPair<double> pair() const { return RPair<double>{s, 0.0}; }
 };
 template <typename R>
 struct AccOf { using T = AccF; };
@@ -138,7 +154,7 @@ struct ScaleOf<double> { using T = ScaleD; };
 
 template <typename R>
 __global__ void __launch_bounds__(NT) k_fn_sums(FnArgs<R> a) {
-  __shared__ double sred[RedSmem<2, 1>::n];
+  __shared__ R sred[(NT / 32) * 5];
   __shared__ int s_last;
   DevState* st = a.st;
   if (st->nonfinite || st->fn_step == st->steps) return;  // uniform: nothing changes them before the last block
@@ -160,26 +176,20 @@ __global__ void __launch_bounds__(NT) k_fn_sums(FnArgs<R> a) {
         av.add_prod(v[c * a.plane + s], hi);  // v.psi: the velocity's own precision suffices
       }
     }
-  DD sums[2] = {DD{an.value(), 0.0}, DD{av.value(), 0.0}};
-  double mv[1] = {0.0};
-  block_reduce<2, 1>(sums, mv, sred);
-  if (tid == 0) {
-    ObsPartial* p = a.part + blockIdx.x;
-    p->es = sums[0].s; p->ec = sums[0].c;
-    p->fs = sums[1].s; p->fc = sums[1].c;
-  }
+  RPair<R> pn = an.pair(), pv = av.pair();
+  pair_block_sum<R>(pn, pv, sred);
+  if (tid == 0) fn_partial<R>(a.part + blockIdx.x, pn, pv);
   if (!fn_arrive(st, tid, &s_last)) return;
-  DD tn, tv;
-  fn_total(a.part, tn, tv, sred);
+  double S, V;
+  fn_total<R>(a.part, S, V, sred);
   if (tid == 0) {
-    const double S = tn.s + tn.c;
     st->fn_ticket = 0;
-    if (!(S > 0.0) || !isfinite(S) || !isfinite(tv.s + tv.c)) {
+    if (!(S > 0.0) || !isfinite(S) || !isfinite(V)) {
       st->nonfinite = 1;  // no atoms to scale: the flow stops
       return;
     }
     st->fn_scale = sqrt(a.n0 / (a.area * S));
-    st->fn_alpha = (tv.s + tv.c) / S;
+    st->fn_alpha = V / S;
     st->fn_pending = 1;
   }
 }
@@ -188,7 +198,7 @@ template <typename R>
 __global__ void __launch_bounds__(NT) k_fn_mu(FnArgs<R> a) {
   constexpr int RPT = TY / BY;  // rows per thread
   __shared__ R sY[2][SY * SX];
-  __shared__ double sred[RedSmem<2, 1>::n];
+  __shared__ R sred[(NT / 32) * 5];
   __shared__ int s_last;
   DevState* st = a.st;
   if (!st->fn_pending) return;
@@ -241,20 +251,15 @@ __global__ void __launch_bounds__(NT) k_fn_mu(FnArgs<R> a) {
       an.add_prod(v[1], v[1]);
     }
   }
-  DD sums[2] = {DD{ag.value(), 0.0}, DD{an.value(), 0.0}};
-  double mv[1] = {0.0};
-  block_reduce<2, 1>(sums, mv, sred);
-  if (tid == 0) {
-    ObsPartial* p = a.part + blockIdx.x;
-    p->es = sums[0].s; p->ec = sums[0].c;
-    p->fs = sums[1].s; p->fc = sums[1].c;
-  }
+  RPair<R> pg = ag.pair(), pn = an.pair();
+  pair_block_sum<R>(pg, pn, sred);
+  if (tid == 0) fn_partial<R>(a.part + blockIdx.x, pg, pn);
   if (!fn_arrive(st, tid, &s_last)) return;
-  DD tg, tn;
-  fn_total(a.part, tg, tn, sred);
+  double tg, tn;
+  fn_total<R>(a.part, tg, tn, sred);
   if (tid == 0) {
     st->fn_ticket = 0;
-    st->mu_held = (tg.s + tg.c) / (2.0 * (tn.s + tn.c));
+    st->mu_held = tg / (2.0 * tn);
   }
 }
 

@@ -118,12 +118,6 @@ __device__ __forceinline__ void normalise(R* y) {
   for (int c = 0; c < C; ++c) y[c] *= s;
 }
 
-__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float bp = s - a;
-  e = (a - (s - bp)) + (b - bp);
-}
-
 // Split-form projection onto the unit sphere: given hi (FP32) and a small part t,
 // return t' with hi + t' = (hi + t) / |hi + t| to about eps^2. With
 // eta = |hi + t|^2 - 1 = (|hi|^2 - 1) + 2 hi.t + |t|^2, where |hi|^2 - 1 is formed
@@ -294,25 +288,6 @@ __device__ __forceinline__ void force_at(const Couplings<R>& k, const R* v, cons
   force_of<TH, R>(k, v, fx, fy, fxx, fyy, fxy, G, x, y);
 }
 
-// ---- per-tile block reduction in the working type: two compensated sums, one max
-template <typename R>
-struct RPair {
-  R s, c;
-};
-__device__ __forceinline__ RPair<float> pair_add(RPair<float> x, RPair<float> y) {
-  float s, e;
-  two_sum_f(x.s, y.s, s, e);
-  return RPair<float>{s, x.c + y.c + e};
-}
-__device__ __forceinline__ RPair<double> pair_add(RPair<double> x, RPair<double> y) {
-  double s, e;
-  two_sum(x.s, y.s, s, e);
-  return RPair<double>{s, x.c + y.c + e};
-}
-template <typename R>
-__device__ __forceinline__ R rmax(R a, R b) {
-  return (b > a || b != b) ? b : a;  // propagates NaN
-}
 // Running maximum of |g| for a >= 0: on non-negative values the IEEE bit patterns
 // order as unsigned integers, with every NaN above +Inf, so one integer max keeps
 // the maximum and propagates NaN (as rmax does).
@@ -323,34 +298,6 @@ __device__ __forceinline__ double absmax(double a, double g) {
   return __longlong_as_double((long long)max((unsigned long long)__double_as_longlong(a),
                                              (unsigned long long)__double_as_longlong(fabs(g))));
 }
-// Block-wide: thread 0 ends with the block's two pairs and maximum. sm holds
-// (NT / 32) * 5 values of R. Fixed shape: bitwise reproducible.
-template <typename R>
-__device__ __forceinline__ void tile_reduce(RPair<R>& a, RPair<R>& b, R& m, R* sm) {
-  constexpr int W = NT / 32;
-  const int lane = threadIdx.x & 31, wid = (threadIdx.y * BX + threadIdx.x) >> 5;
-  for (int off = 16; off > 0; off >>= 1) {
-    a = pair_add(a, RPair<R>{__shfl_down_sync(0xffffffffu, a.s, off), __shfl_down_sync(0xffffffffu, a.c, off)});
-    b = pair_add(b, RPair<R>{__shfl_down_sync(0xffffffffu, b.s, off), __shfl_down_sync(0xffffffffu, b.c, off)});
-    m = rmax(m, __shfl_down_sync(0xffffffffu, m, off));
-  }
-  if (lane == 0) {
-    sm[wid] = a.s; sm[W + wid] = a.c; sm[2 * W + wid] = b.s; sm[3 * W + wid] = b.c; sm[4 * W + wid] = m;
-  }
-  __syncthreads();
-  if (wid == 0) {
-    a = lane < W ? RPair<R>{sm[lane], sm[W + lane]} : RPair<R>{R(0), R(0)};
-    b = lane < W ? RPair<R>{sm[2 * W + lane], sm[3 * W + lane]} : RPair<R>{R(0), R(0)};
-    m = lane < W ? sm[4 * W + lane] : R(0);
-    for (int off = 16; off > 0; off >>= 1) {
-      a = pair_add(a, RPair<R>{__shfl_down_sync(0xffffffffu, a.s, off), __shfl_down_sync(0xffffffffu, a.c, off)});
-      b = pair_add(b, RPair<R>{__shfl_down_sync(0xffffffffu, b.s, off), __shfl_down_sync(0xffffffffu, b.c, off)});
-      m = rmax(m, __shfl_down_sync(0xffffffffu, m, off));
-    }
-  }
-  __syncthreads();
-}
-
 // Per-tile view of the problem, staged in shared memory by thread 0.
 template <typename R>
 struct TileCtx {
@@ -724,22 +671,43 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
       __syncthreads();
       if (s_last) {
         __threadfence();
-        DD acc{0.0, 0.0}, dacc{0.0, 0.0};
-        double mm = 0.0;
-        for (int i = tid; i < d.ntiles; i += NT) {
-          const FlowPartial* q = d.part + i;
-          acc = dd_add(acc, DD{__ldcg(&q->es), __ldcg(&q->ec)});
-          dacc = dd_add(dacc, DD{__ldcg(&q->ds), __ldcg(&q->dc)});
-          mm = nanmax(mm, __ldcg(&q->m));
+        double tot[2], mtot;  // the problem's sum of e, sum of e(new) - e(previous), max |G|
+        if constexpr (sizeof(R) == 4) {
+          // the partials hold FP32 pairs exactly: total them as FP32 pairs (this GPU's
+          // FP64 units would hold the problem's last block for microseconds)
+          RPair<R> acc{R(0), R(0)}, dacc{R(0), R(0)};
+          R mm = R(0);
+          for (int i = tid; i < d.ntiles; i += NT) {
+            const FlowPartial* q = d.part + i;
+            acc = pair_add(acc, RPair<R>{R(__ldcg(&q->es)), R(__ldcg(&q->ec))});
+            dacc = pair_add(dacc, RPair<R>{R(__ldcg(&q->ds)), R(__ldcg(&q->dc))});
+            mm = rmax(mm, R(__ldcg(&q->m)));
+          }
+          tile_reduce<R>(acc, dacc, mm, sred);
+          tot[0] = (double)acc.s + (double)acc.c;
+          tot[1] = (double)dacc.s + (double)dacc.c;
+          mtot = (double)mm;
+        } else {
+          DD acc{0.0, 0.0}, dacc{0.0, 0.0};
+          double mm = 0.0;
+          for (int i = tid; i < d.ntiles; i += NT) {
+            const FlowPartial* q = d.part + i;
+            acc = dd_add(acc, DD{__ldcg(&q->es), __ldcg(&q->ec)});
+            dacc = dd_add(dacc, DD{__ldcg(&q->ds), __ldcg(&q->dc)});
+            mm = nanmax(mm, __ldcg(&q->m));
+          }
+          DD sv2[2] = {acc, dacc};
+          double mv2[1] = {mm};
+          block_reduce<2, 1>(sv2, mv2, dred);
+          tot[0] = sv2[0].s + sv2[0].c;
+          tot[1] = sv2[1].s + sv2[1].c;
+          mtot = mv2[0];
         }
-        DD sv2[2] = {acc, dacc};
-        double mv2[1] = {mm};
-        block_reduce<2, 1>(sv2, mv2, dred);
         if (tid == 0 && PASS == 1) {
           DevState* st = d.st;
-          const double E = d.area * (sv2[0].s + sv2[0].c);
-          const double dE = d.area * (sv2[1].s + sv2[1].c);
-          const double g = d.area * mv2[0];
+          const double E = d.area * tot[0];
+          const double dE = d.area * tot[1];
+          const double g = d.area * mtot;
           // Eq. 4, strict: E_h(phi^n) > E_h(phi^{n-1}); no previous field (E_last = +inf): no arrest
           const int arr = has_prev ? (dE > 0.0 ? 1 : 0) : (E > st->E_last ? 1 : 0);
           st->E_cur = E;
@@ -756,8 +724,8 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
           // descent: record the evaluated field, count a rise, then take the step
           // (its new field is already written) unless converged or out of budget
           DevState* st = d.st;
-          const double E = d.area * (sv2[0].s + sv2[0].c);
-          const double g = d.area * mv2[0];
+          const double E = d.area * tot[0];
+          const double g = d.area * mtot;
           const double El = st->E_last;
           const int rose = E > El ? 1 : 0;  // E_last = +inf before the first field
           st->E_cur = E;
