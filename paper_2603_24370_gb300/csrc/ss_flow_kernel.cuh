@@ -26,10 +26,10 @@
 // since the previous field, dE = sum_I [e(phi^n) - e(phi^{n-1})], in the
 // cancellation-free form of ss_device.cuh (phi^{n-1} is still intact in the other
 // ping-pong buffer): a compensated pair per thread, summed over a block's run of
-// consecutive tiles of one problem and reduced into the partial of the run's last
-// tile; the last tile of the problem to arrive (arrival counter) sums the problem's
-// partials in tile order (bitwise reproducible) and decides on the device, with no
-// host round trip:
+// consecutive tiles of one problem and reduced into a partial (one per run; a single
+// problem has one run per block); the last arrival (arrival counter) sums the
+// problem's partials in a fixed order (bitwise reproducible for a given grid) and
+// decides on the device, with no host round trip:
 //   arrest    = dE > 0, i.e. E_h(phi^n) > E_h(phi^{n-1})   (Eq. 4)
 //   converged = dx dy max|G| < tol
 // Pass 1 computes k_v2 with v before the arrest is known. That is exact either way:
@@ -643,30 +643,34 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
       }
 
       // ---- partials: the block keeps summing while its next tile belongs to the same
-      // problem and writes a zero partial for this tile; otherwise it reduces and writes
-      // the running sums. The tile that completes the problem's count reduces the
-      // problem's partials in tile order and decides. (A tile whose block still holds
-      // another tile of the problem can never be the last to arrive.)
+      // problem; otherwise it reduces and writes the running sums. Batches: a problem's
+      // tiles are spread over blocks, so every tile counts (a zero partial for a tile
+      // whose run goes on) and the partials are indexed by tile. A single problem: every
+      // block with tiles flushes exactly once, at its last tile, into its own slot, and
+      // the blocks are counted (no per-tile fence or counter). The arrival that
+      // completes the count reduces the problem's partials in slot order and decides.
+      // (A block that still holds another tile of the problem can never be the last.)
       const ProbDesc<R>& d = D;
       const bool flush = ONE ? tn >= total_tiles : !(tn < total_tiles && tcb[buf ^ 1].p == tc.p);
       if (!flush) {
-        if (tid == 0) {
+        if (!ONE && tid == 0) {
           d.part[lt] = FlowPartial{0.0, 0.0, 0.0, 0.0, 0.0, {0.0, 0.0, 0.0}};
           __threadfence();
           atomicAdd(&d.st->ticket, 1u);
         }
         continue;
       }
+      const int nslots = ONE ? min((int)gridDim.x, d.ntiles) : d.ntiles;
       RPair<R> pe{es, ec}, pd{ds, dc};
       R pm = gmr;
       tile_reduce<R>(pe, pd, pm, sred);
       es = ec = ds = dc = gmr = R(0);  // the next run of tiles starts afresh
       if (tid == 0) {
-        d.part[lt] = FlowPartial{(double)pe.s, (double)pe.c, (double)pd.s, (double)pd.c, (double)pm,
-                                 {0.0, 0.0, 0.0}};
+        d.part[ONE ? (int)blockIdx.x : lt] = FlowPartial{(double)pe.s, (double)pe.c, (double)pd.s, (double)pd.c,
+                                                         (double)pm, {0.0, 0.0, 0.0}};
         __threadfence();
         const unsigned prev = atomicAdd(&d.st->ticket, 1u);
-        s_last = (prev == (unsigned)d.ntiles - 1);
+        s_last = (prev == (unsigned)nslots - 1);
       }
       __syncthreads();
       if (s_last) {
@@ -677,7 +681,7 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
           // FP64 units would hold the problem's last block for microseconds)
           RPair<R> acc{R(0), R(0)}, dacc{R(0), R(0)};
           R mm = R(0);
-          for (int i = tid; i < d.ntiles; i += NT) {
+          for (int i = tid; i < nslots; i += NT) {
             const FlowPartial* q = d.part + i;
             acc = pair_add(acc, RPair<R>{R(__ldcg(&q->es)), R(__ldcg(&q->ec))});
             dacc = pair_add(dacc, RPair<R>{R(__ldcg(&q->ds)), R(__ldcg(&q->dc))});
@@ -690,7 +694,7 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
         } else {
           DD acc{0.0, 0.0}, dacc{0.0, 0.0};
           double mm = 0.0;
-          for (int i = tid; i < d.ntiles; i += NT) {
+          for (int i = tid; i < nslots; i += NT) {
             const FlowPartial* q = d.part + i;
             acc = dd_add(acc, DD{__ldcg(&q->es), __ldcg(&q->ec)});
             dacc = dd_add(dacc, DD{__ldcg(&q->ds), __ldcg(&q->dc)});
