@@ -64,26 +64,25 @@ __global__ void k_rho_ext(const R* __restrict__ phi0, const R* __restrict__ phi1
   const int cur = (int)(st->steps & 1);
   const R* __restrict__ f = cur ? phi1 : phi0;
   const R* __restrict__ lo = cur ? lo1 : lo0;
-  const size_t total = (size_t)Ny * (Nx + 2);
-  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-    const int jp = (int)(t / (Nx + 2));  // row 0 .. Ny-1  (j' - 1)
-    const int ip = (int)(t % (Nx + 2));  // 0 .. Nx+1      (i')
-    R* row = ext + (size_t)jp * Mx;
-    if (ip == 0 || ip == Nx + 1) {
-      row[ip] = R(0);
-      continue;
+  // rows over blocks, the row's points over threads (no index division)
+  for (int jp = blockIdx.x; jp < Ny; jp += gridDim.x)  // row 0 .. Ny-1  (j' - 1)
+    for (int ip = threadIdx.x; ip < Nx + 2; ip += blockDim.x) {  // 0 .. Nx+1  (i')
+      R* row = ext + (size_t)jp * Mx;
+      if (ip == 0 || ip == Nx + 1) {
+        row[ip] = R(0);
+        continue;
+      }
+      const int i = ip + 1, j = jp + 2;  // full-array site
+      const size_t s = (size_t)j * nx + i;
+      auto d1 = [&](const R* p, size_t c, ptrdiff_t st1, R sc) {
+        const R* q = p + c * plane + s;
+        return (R(8) * (q[st1] - q[-st1]) - (q[2 * st1] - q[-2 * st1])) * sc;
+      };
+      R rho = d1(f, 0, 1, i12dx) + d1(f, 1, (ptrdiff_t)nx, i12dy);
+      if (lo) rho += d1(lo, 0, 1, i12dx) + d1(lo, 1, (ptrdiff_t)nx, i12dy);
+      row[ip] = rho;
+      row[Mx - ip] = -rho;
     }
-    const int i = ip + 1, j = jp + 2;  // full-array site
-    const size_t s = (size_t)j * nx + i;
-    auto d1 = [&](const R* p, size_t c, ptrdiff_t st1, R sc) {
-      const R* q = p + c * plane + s;
-      return (R(8) * (q[st1] - q[-st1]) - (q[2 * st1] - q[-2 * st1])) * sc;
-    };
-    R rho = d1(f, 0, 1, i12dx) + d1(f, 1, (ptrdiff_t)nx, i12dy);
-    if (lo) rho += d1(lo, 0, 1, i12dx) + d1(lo, 1, (ptrdiff_t)nx, i12dy);
-    row[ip] = rho;
-    row[Mx - ip] = -rho;
-  }
 }
 
 // -Im/2 of a row transform, written transposed as odd extensions of the columns:
@@ -112,22 +111,29 @@ __global__ void k_im_transpose_ext(const Cx* __restrict__ in, int rows, int H, i
   }
 }
 
+// a / b: FP32 by the fast reciprocal (2 ulp; b is a sum of two negative eigenvalues,
+// far from the range where it loses accuracy), FP64 exactly.
+__device__ __forceinline__ float div_eig(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double div_eig(double a, double b) { return a / b; }
+
 // In place along the same rows: b = -Im/2 / (lam_x[row] + lam_y[l]) written back as
 // the odd extension of the row (for the inverse transform along y).
 template <typename R, typename Cx>
 __global__ void k_scale_ext(const Cx* __restrict__ in, int rows, int H, int L, const R* __restrict__ lamx,
                             const R* __restrict__ lamy, R* __restrict__ out, int Mo) {
-  const size_t total = (size_t)rows * (L + 2);
-  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-    const int r = (int)(t / (L + 2)), l = (int)(t % (L + 2));
+  for (int r = blockIdx.x; r < rows; r += gridDim.x) {
+    const R lx = lamx[r];
     R* o = out + (size_t)r * Mo;
-    if (l == 0 || l == L + 1) {
-      o[l] = R(0);
-      continue;
+    const Cx* q = in + (size_t)r * H;
+    for (int l = threadIdx.x; l < L + 2; l += blockDim.x) {
+      if (l == 0 || l == L + 1) {
+        o[l] = R(0);
+        continue;
+      }
+      const R v = div_eig(-R(0.5) * q[l].y, lx + lamy[l - 1]);
+      o[l] = v;
+      o[Mo - l] = -v;
     }
-    const R v = -R(0.5) * in[(size_t)r * H + l].y / (lamx[r] + lamy[l - 1]);
-    o[l] = v;
-    o[Mo - l] = -v;
   }
 }
 
@@ -137,11 +143,9 @@ template <typename R, typename Cx>
 __global__ void k_scatter_psi(const Cx* __restrict__ in, int H, int Nx, int Ny, int nx, R norm, const DevState* st,
                               R* __restrict__ psi0, R* __restrict__ psi1) {
   R* __restrict__ psi = (st->steps & 1) ? psi1 : psi0;
-  const size_t total = (size_t)Nx * Ny;
-  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-    const int jp = (int)(t / Nx), ip = (int)(t % Nx);  // 0-based interior indices
-    psi[(size_t)(jp + 2) * nx + (ip + 2)] = norm * (-R(0.5) * in[(size_t)jp * H + (ip + 1)].y);
-  }
+  for (int jp = blockIdx.x; jp < Ny; jp += gridDim.x)  // 0-based interior indices
+    for (int ip = threadIdx.x; ip < Nx; ip += blockDim.x)
+      psi[(size_t)(jp + 2) * nx + (ip + 2)] = norm * (-R(0.5) * in[(size_t)jp * H + (ip + 1)].y);
 }
 
 // ---- host side
