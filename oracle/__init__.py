@@ -102,6 +102,10 @@ def _load():
             lib.or_ansatz.argtypes = [i, _D, i, _D, i, i, d, d]
             lib.or_ansatz_bec.argtypes = [_D, _D, i, _D, i, i, d, d]
             lib.or_demag_potential.argtypes = [_D, i, i, d, d, _D, _D]
+            lib.or_demag_box.argtypes = [i, ctypes.POINTER(ctypes.c_int)]
+            lib.or_demag_box.restype = None
+            lib.or_demag_box_potential.argtypes = [_D, i, i, d, d, _D]
+            lib.or_demag_box_potential.restype = None
             lib.or_demag_potential.restype = None
             lib.or_demag_energy.argtypes = [_D, _D, i, i, d, d]
             lib.or_demag_energy.restype = d
@@ -320,6 +324,24 @@ def demag_potential(f, dx: float, dy: float):
     rho, psi = np.zeros((ny, nx)), np.zeros((ny, nx))
     _load().or_demag_potential(_p(f), nx, ny, dx, dy, _p(rho), _p(psi))
     return rho, psi
+
+
+def demag_box(N: int):
+    """The Dirichlet box of an axis with N interior sites: (N', sites added below I)."""
+    out = (ctypes.c_int * 2)()
+    _load().or_demag_box(int(N), out)
+    return out[0], out[1]
+
+
+def demag_box_potential(f, dx: float, dy: float) -> np.ndarray:
+    """psi on the whole Dirichlet box, [Ny' + 2][Nx' + 2] with its zero outer nodes."""
+    f = _f64(f)
+    _, ny, nx = f.shape
+    Nx, _ = demag_box(nx - 4)
+    Ny, _ = demag_box(ny - 4)
+    box = np.zeros((Ny + 2, Nx + 2))
+    _load().or_demag_box_potential(_p(f), nx, ny, dx, dy, _p(box))
+    return box
 
 
 def demag_energy(params, f, dx: float, dy: float) -> float:

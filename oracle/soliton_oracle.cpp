@@ -45,9 +45,14 @@
 //     (Re, Im Delta_s, Re, Im Delta_d, A_1, A_2). params = {a1, a2, b1, b2, b3, b4, nu}.
 //   * Demagnetisation (Eq. 6, the chiral magnet with demag, theory 6): with
 //     psi = phi / (mu_0 M_s) the Poisson equation reads lap psi = div n (in-plane n),
-//     discretised as L psi = rho on I: rho the Eq. 1 divergence of (n_1, n_2), L the
-//     5-point Laplacian, psi = 0 on the halo (the sites next to I are the Dirichlet
-//     boundary). Energy E_ms = 1/(2 mu_0) int |grad phi|^2 = -mu_d/2 int psi rho with
+//     discretised as L psi = rho on a Dirichlet box B containing I: rho the Eq. 1
+//     divergence of (n_1, n_2) on I and zero on the rest of B, L the 5-point Laplacian,
+//     psi = 0 on the nodes just outside B (standing in for the far field). Along each
+//     axis B has the N' >= N sites with N' + 1 the first size free of prime factors
+//     above 7, floor((N' - N) / 2) of the extra sites below I and the rest above, so
+//     the sine transform has an FFT-friendly length (B = I when N + 1 already is).
+//     Only psi on I enters: the stored potential is psi on I and zero on the halo.
+//     Energy E_ms = 1/(2 mu_0) int |grad phi|^2 = -mu_d/2 int psi rho with
 //     mu_d = mu_0 M_s^2, discretised as -mu_d/2 dx dy sum_I psi rho, whose exact lattice
 //     gradient is mu_d dx dy (Eq. 1 gradient of psi) because L is symmetric and Eq. 1
 //     antisymmetric: the force is G_cm + mu_d (d_1 psi, d_2 psi, 0), then projected.
@@ -529,26 +534,49 @@ void demag_charge(const double* f, const Grid& g, double* rho) {
     for (int i = 2; i <= g.nx - 3; ++i) rho[(size_t)j * g.nx + i] = d1x(f, g, i, j) + d1y(f + g.plane(), g, i, j);
 }
 
-// Solve L psi = rho on I (5-point Laplacian, psi = 0 off I) by the sine transform that
-// diagonalises L: interior index i' = i - 1 = 1..Nx (i' = 0 and Nx + 1 are the zero
-// boundary), L sin(pi k i'/(Nx+1)) sin(pi l j'/(Ny+1)) = lambda_kl (same mode),
+// The Dirichlet box along one axis of N interior sites: its size N' (the smallest
+// N' >= N whose N' + 1 has no prime factor above 7) and the sites it adds below I.
+void demag_box(int N, int* Np, int* below) {
+  auto smooth = [](int m) {
+    for (int q : {2, 3, 5, 7})
+      while (m % q == 0) m /= q;
+    return m == 1;
+  };
+  int n = N;
+  while (!smooth(n + 1)) ++n;
+  *Np = n;
+  *below = (n - N) / 2;
+}
+
+// Solve L psi = rho on the Dirichlet box (5-point Laplacian, psi = 0 on the nodes
+// just outside it) by the sine transform that diagonalises L: box index
+// i' = i - 1 + bx = 1..Nx (i' = 0 and Nx + 1 the zero nodes; bx the sites below I),
+// L sin(pi k i'/(Nx+1)) sin(pi l j'/(Ny+1)) = lambda_kl (same mode),
 //   lambda_kl = -(2 - 2 cos(pi k/(Nx+1)))/dx^2 - (2 - 2 cos(pi l/(Ny+1)))/dy^2,
-// with the transform written out as plain sums (test sizes only).
-void demag_potential(const double* f, const Grid& g, double* psi) {
-  const int Nx = g.nx - 4, Ny = g.ny - 4;
-  std::vector<double> rho(g.plane());
-  demag_charge(f, g, rho.data());
+// with the transform written out as plain sums (test sizes only). box receives psi at
+// box nodes [0, Ny + 1] x [0, Nx + 1] (zero on the outer ones); psi (if not null) the
+// array plane, psi on I and zero on the halo.
+void demag_box_potential(const double* f, const Grid& g, std::vector<double>& box, int& Nx, int& Ny, int& bx,
+                         int& by) {
+  demag_box(g.nx - 4, &Nx, &bx);
+  demag_box(g.ny - 4, &Ny, &by);
+  std::vector<double> rho_a(g.plane());
+  demag_charge(f, g, rho_a.data());
+  // rho on the box: the array's charge on I, zero on the padding
+  std::vector<double> rho((size_t)(Nx + 2) * (Ny + 2), 0.0);
+  auto bat = [&](int ip, int jp) { return (size_t)jp * (Nx + 2) + ip; };
+  for (int j = 2; j <= g.ny - 3; ++j)
+    for (int i = 2; i <= g.nx - 3; ++i) rho[bat(i - 1 + bx, j - 1 + by)] = rho_a[(size_t)j * g.nx + i];
   std::vector<double> sx((size_t)Nx * Nx), sy((size_t)Ny * Ny);
   for (int k = 1; k <= Nx; ++k)
     for (int i = 1; i <= Nx; ++i) sx[(size_t)(k - 1) * Nx + (i - 1)] = std::sin(PI * k * i / (Nx + 1));
   for (int l = 1; l <= Ny; ++l)
     for (int j = 1; j <= Ny; ++j) sy[(size_t)(l - 1) * Ny + (j - 1)] = std::sin(PI * l * j / (Ny + 1));
-  auto at = [&](int ip, int jp) { return (size_t)(jp + 1) * g.nx + (ip + 1); };  // i', j' >= 1
   std::vector<double> a((size_t)Nx * Ny), b((size_t)Nx * Ny);
   for (int jp = 1; jp <= Ny; ++jp)  // along x
     for (int k = 1; k <= Nx; ++k) {
       double acc = 0.0;
-      for (int ip = 1; ip <= Nx; ++ip) acc += sx[(size_t)(k - 1) * Nx + (ip - 1)] * rho[at(ip, jp)];
+      for (int ip = 1; ip <= Nx; ++ip) acc += sx[(size_t)(k - 1) * Nx + (ip - 1)] * rho[bat(ip, jp)];
       a[(size_t)(jp - 1) * Nx + (k - 1)] = acc;
     }
   for (int l = 1; l <= Ny; ++l)  // along y, then divide by the eigenvalue
@@ -566,13 +594,23 @@ void demag_potential(const double* f, const Grid& g, double* psi) {
       for (int l = 1; l <= Ny; ++l) acc += sy[(size_t)(l - 1) * Ny + (jp - 1)] * b[(size_t)(l - 1) * Nx + (k - 1)];
       a[(size_t)(jp - 1) * Nx + (k - 1)] = acc;
     }
-  std::memset(psi, 0, sizeof(double) * g.plane());
+  box.assign((size_t)(Nx + 2) * (Ny + 2), 0.0);
   for (int jp = 1; jp <= Ny; ++jp)  // inverse along x
     for (int ip = 1; ip <= Nx; ++ip) {
       double acc = 0.0;
       for (int k = 1; k <= Nx; ++k) acc += sx[(size_t)(k - 1) * Nx + (ip - 1)] * a[(size_t)(jp - 1) * Nx + (k - 1)];
-      psi[at(ip, jp)] = norm * acc;
+      box[bat(ip, jp)] = norm * acc;
     }
+}
+
+// psi on I (zero on the halo): the box solution at I's sites.
+void demag_potential(const double* f, const Grid& g, double* psi) {
+  std::vector<double> box;
+  int Nx, Ny, bx, by;
+  demag_box_potential(f, g, box, Nx, Ny, bx, by);
+  std::memset(psi, 0, sizeof(double) * g.plane());
+  for (int j = 2; j <= g.ny - 3; ++j)
+    for (int i = 2; i <= g.nx - 3; ++i) psi[(size_t)j * g.nx + i] = box[(size_t)(j - 1 + by) * (Nx + 2) + (i - 1 + bx)];
 }
 
 // E_ms = -mu_d/2 dx dy sum_I psi rho.
@@ -714,6 +752,16 @@ void or_demag_potential(const double* f, int nx, int ny, double dx, double dy, d
   const Grid g{nx, ny, dx, dy};
   demag_charge(f, g, rho);
   demag_potential(f, g, psi);
+}
+// The Dirichlet box of an axis with N interior sites: out = {N', sites below I}.
+void or_demag_box(int N, int* out) { demag_box(N, &out[0], &out[1]); }
+// psi on the whole box [Ny' + 2][Nx' + 2] (the zero nodes included); box must hold
+// (Nx' + 2)(Ny' + 2) doubles, sizes from or_demag_box.
+void or_demag_box_potential(const double* f, int nx, int ny, double dx, double dy, double* box) {
+  std::vector<double> b;
+  int Nx, Ny, bx, by;
+  demag_box_potential(f, Grid{nx, ny, dx, dy}, b, Nx, Ny, bx, by);
+  std::memcpy(box, b.data(), sizeof(double) * b.size());
 }
 double or_demag_energy(const double* prm, const double* f, int nx, int ny, double dx, double dy) {
   return demag_energy(prm, f, Grid{nx, ny, dx, dy});

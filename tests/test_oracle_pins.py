@@ -770,6 +770,62 @@ def test_demag_potential_solves_the_five_point_poisson_problem():
         O.energy(CM, CMD_PRM[:5], f, dx, dy) + O.demag_energy(CMD_PRM, f, dx, dy), rel=1e-14)
 
 
+def test_demag_box_is_the_smallest_fft_friendly_one():
+    """The Dirichlet box along an axis of N sites: N' + 1 has no prime factor above 7,
+    no smaller N' >= N has that property, and floor((N' - N) / 2) sites go below I."""
+    def smooth(m):
+        for q in (2, 3, 5, 7):
+            while m % q == 0:
+                m //= q
+        return m == 1
+    for N in list(range(1, 300)) + [1020, 2044, 4092, 8188]:
+        Np, below = O.demag_box(N)
+        assert Np >= N and smooth(Np + 1) and not any(smooth(m + 1) for m in range(N, Np))
+        assert below == (Np - N) // 2
+    assert O.demag_box(4092) == (4095, 1)  # 4093 is prime: the box adds 3 sites
+
+
+def test_demag_padded_box_solves_the_five_point_poisson_problem():
+    """A grid whose interior needs padding (60 and 36 sites: 61 and 37 are prime): the
+    box potential satisfies L psi = rho on every box site, with rho the charge on I and
+    zero on the padding, vanishes on the box's outer nodes, and the stored potential is
+    the box solution on I and zero on the halo."""
+    nx, ny, dx, dy = 64, 40, 0.3, 0.25
+    (Nx, bx), (Ny, by) = O.demag_box(nx - 4), O.demag_box(ny - 4)
+    assert (Nx, bx, Ny, by) == (62, 1, 39, 1)
+    f = I.smooth_field(CM, nx, ny, dx, dy, seed=23)
+    rho, psi = O.demag_potential(f, dx, dy)
+    box = O.demag_box_potential(f, dx, dy)
+    assert box.shape == (Ny + 2, Nx + 2)
+    assert not box[0].any() and not box[-1].any() and not box[:, 0].any() and not box[:, -1].any()
+    rb = np.zeros_like(box)
+    rb[1 + by:1 + by + ny - 4, 1 + bx:1 + bx + nx - 4] = rho[2:-2, 2:-2]
+    L = ((box[1:-1, 2:] - 2 * box[1:-1, 1:-1] + box[1:-1, :-2]) / dx ** 2 +
+         (box[2:, 1:-1] - 2 * box[1:-1, 1:-1] + box[:-2, 1:-1]) / dy ** 2)
+    np.testing.assert_allclose(L, rb[1:-1, 1:-1], rtol=0, atol=1e-12 * np.abs(rho).max())
+    assert np.array_equal(psi[2:-2, 2:-2], box[1 + by:1 + by + ny - 4, 1 + bx:1 + bx + nx - 4])
+    assert not psi[:2].any() and not psi[-2:].any() and not psi[:, :2].any() and not psi[:, -2:].any()
+    assert np.abs(box[1:-1, 1:-1]).max() > 0 and abs(box[1 + by, 1]) > 0  # the padding carries potential
+
+
+def test_demag_gradient_is_exact_on_a_padded_box():
+    """Brute-force lattice gradient of the full energy with demagnetisation where the
+    Dirichlet box is larger than I (both axes padded): the force uses psi on I only,
+    which is the exact gradient of -mu_d/2 dx dy sum_I psi rho for any box."""
+    nx, ny, dx, dy = 14, 40, 0.3, 0.25
+    assert O.demag_box(nx - 4) == (11, 0) and O.demag_box(ny - 4) == (39, 1)  # padded above; below and above
+    f = I.smooth_field(CMD, nx, ny, dx, dy, seed=29, amplitude=0.5)
+    grad = O.energy_grad_exact(CMD, CMD_PRM, f, dx, dy)
+    eps = 1e-6
+    fd = np.zeros_like(f)
+    for idx in np.ndindex(f.shape):
+        fp, fm = f.copy(), f.copy()
+        fp[idx] += eps
+        fm[idx] -= eps
+        fd[idx] = (O.energy(CMD, CMD_PRM, fp, dx, dy) - O.energy(CMD, CMD_PRM, fm, dx, dy)) / (2 * eps)
+    np.testing.assert_allclose(grad, fd, rtol=0, atol=1e-7 * np.abs(grad).max())
+
+
 def test_demag_spares_bloch_and_charges_neel_skyrmions():
     """The magnetostatic energy comes from the in-plane divergence: a Bloch skyrmion
     (helicity pi/2, divergence-free) has none beyond the stencils' O(h^4) remainder,
