@@ -67,10 +67,13 @@ extern "C" {
 #define SS_ABELIAN_HIGGS 1 /* Table 1, params {lambda, u}                                */
 #define SS_CHIRAL_MAGNET 2 /* Eq. 5, params {J, D, K, h[, dmi_type[, mu_d]]}:             */
                            /* mu_d = mu_0 M_s^2 > 0 adds demagnetisation (Eq. 6): the      */
-                           /* potential psi (lap psi = div n, 5-point Laplacian, psi = 0   */
-                           /* on the halo) is solved by a sine transform once per step and */
-                           /* adds -mu_d/2 psi div n to the energy, mu_d grad psi to the   */
-                           /* force (single-grid contexts only);                           */
+                           /* potential psi (lap psi = div n on a Dirichlet box holding the*/
+                           /* interior, 5-point Laplacian, psi = 0 just outside the box;   */
+                           /* the box is the interior widened by at most a few sites to an */
+                           /* FFT-friendly size, and psi is kept on the interior only) is  */
+                           /* solved by a sine transform once per step and adds            */
+                           /* -mu_d/2 psi div n to the energy, mu_d grad psi to the force  */
+                           /* (single-grid contexts only);                                 */
                            /* dmi_type 0 interfacial (d_i = e_3 x e_i), 1 bulk (d_i = e_i),*/
                            /* 2 D_2d "Heusler" (d_1 = e_1, d_2 = -e_2)                     */
 #define SS_BABY_SKYRME 3   /* Table 1, params {kappa, mu[, nu]}: unit 3-vector m with       */

@@ -1,10 +1,14 @@
 // ss_demag.cu -- magnetostatic potential of the chiral magnet (arxiv 2603.24370, Eq. 6).
 //
 // With psi = phi / (mu_0 M_s) the Poisson equation of Eq. 6 reads lap psi = div n (the
-// in-plane components). On the lattice: L psi = rho on the interior I, rho the Eq. 1
-// divergence of (n_1, n_2), L the 5-point Laplacian with psi = 0 on the halo (the sites
-// next to I are the Dirichlet boundary). L is diagonalised by the 2D sine transform
-// (DST-I) over I's Nx x Ny sites: mode (k, l) has the eigenvalue
+// in-plane components). On the lattice: L psi = rho on a Dirichlet box B containing the
+// interior I, rho the Eq. 1 divergence of (n_1, n_2) on I and zero on the rest of B, L
+// the 5-point Laplacian with psi = 0 on the nodes just outside B (standing in for the
+// far field). Along each axis B has the first size N' >= N with N' + 1 free of prime
+// factors above 7, floor((N' - N) / 2) sites below I and the rest above; only psi on I
+// is kept (the plane's halo stays zero), and the flow's force, the Eq. 1 gradient of
+// that plane, is the exact gradient of the energy for any such box. L is diagonalised
+// by the 2D sine transform (DST-I) over B's Nx x Ny sites: mode (k, l) has the eigenvalue
 //   lambda_kl = -(2 - 2 cos(pi k / (Nx + 1))) / dx^2 - (2 - 2 cos(pi l / (Ny + 1))) / dy^2,
 // and DST-I is its own inverse up to 2 / (N + 1) per direction.
 //
@@ -42,12 +46,15 @@ struct FftOf<double> {
 };
 
 struct DemagSolver {
-  int nx = 0, ny = 0, Nx = 0, Ny = 0, Mx = 0, My = 0, Hx = 0, Hy = 0;
+  int nx = 0, ny = 0;
+  int Nx = 0, Ny = 0;  // Dirichlet box sites per axis (>= the interior's nx - 4, ny - 4)
+  int bx = 0, by = 0;  // box sites below I along x, y
+  int Mx = 0, My = 0, Hx = 0, Hy = 0;
   int prec = 0;  // PREC_*: FP64 transforms for FP64 fields, FP32 otherwise
   double dx = 0, dy = 0;
   cufftHandle px = 0, py = 0;
   bool have_px = false, have_py = false;
-  void* ext_x = nullptr;  // R [Ny][Mx]
+  void* ext_x = nullptr;  // R [Ny][Mx] (box rows)
   void* cx = nullptr;     // complex [Ny][Hx]
   void* ext_y = nullptr;  // R [Nx][My]
   void* cy = nullptr;     // complex [Nx][Hy]
@@ -56,11 +63,12 @@ struct DemagSolver {
 
 // ---- kernels (R the transform type; F the field storage type, equal except that
 // compensated FP32 adds the remainder plane)
-// rho on I into the x-extension rows, with the two zero points of every row.
+// rho into the x-extension rows of the box (zero on the box's padding), with the two
+// zero points of every row.
 template <typename R>
 __global__ void k_rho_ext(const R* __restrict__ phi0, const R* __restrict__ phi1, const R* __restrict__ lo0,
-                          const R* __restrict__ lo1, const DevState* st, int nx, size_t plane, int Nx, int Ny,
-                          int Mx, R i12dx, R i12dy, R* __restrict__ ext) {
+                          const R* __restrict__ lo1, const DevState* st, int nx, int ny, size_t plane, int Nx, int Ny,
+                          int bx, int by, int Mx, R i12dx, R i12dy, R* __restrict__ ext) {
   const int cur = (int)(st->steps & 1);
   const R* __restrict__ f = cur ? phi1 : phi0;
   const R* __restrict__ lo = cur ? lo1 : lo0;
@@ -68,11 +76,12 @@ __global__ void k_rho_ext(const R* __restrict__ phi0, const R* __restrict__ phi1
   for (int jp = blockIdx.x; jp < Ny; jp += gridDim.x)  // row 0 .. Ny-1  (j' - 1)
     for (int ip = threadIdx.x; ip < Nx + 2; ip += blockDim.x) {  // 0 .. Nx+1  (i')
       R* row = ext + (size_t)jp * Mx;
-      if (ip == 0 || ip == Nx + 1) {
+      const int i = ip + 1 - bx, j = jp + 2 - by;  // full-array site of box node (ip, jp + 1)
+      if (ip == 0 || ip == Nx + 1 || i < 2 || i > nx - 3 || j < 2 || j > ny - 3) {  // zero node, padding
         row[ip] = R(0);
+        if (ip != 0) row[Mx - ip] = R(0);
         continue;
       }
-      const int i = ip + 1, j = jp + 2;  // full-array site
       const size_t s = (size_t)j * nx + i;
       auto d1 = [&](const R* p, size_t c, ptrdiff_t st1, R sc) {
         const R* q = p + c * plane + s;
@@ -137,15 +146,15 @@ __global__ void k_scale_ext(const Cx* __restrict__ in, int rows, int H, int L, c
   }
 }
 
-// psi = norm x (-Im/2) of the final row transform, into the interior of the plane of
-// the current parity (the halo stays zero).
+// psi = norm x (-Im/2) of the final row transform at I's box nodes, into the interior
+// of the plane of the current parity (the halo stays zero).
 template <typename R, typename Cx>
-__global__ void k_scatter_psi(const Cx* __restrict__ in, int H, int Nx, int Ny, int nx, R norm, const DevState* st,
-                              R* __restrict__ psi0, R* __restrict__ psi1) {
+__global__ void k_scatter_psi(const Cx* __restrict__ in, int H, int nx, int ny, int bx, int by, R norm,
+                              const DevState* st, R* __restrict__ psi0, R* __restrict__ psi1) {
   R* __restrict__ psi = (st->steps & 1) ? psi1 : psi0;
-  for (int jp = blockIdx.x; jp < Ny; jp += gridDim.x)  // 0-based interior indices
-    for (int ip = threadIdx.x; ip < Nx; ip += blockDim.x)
-      psi[(size_t)(jp + 2) * nx + (ip + 2)] = norm * (-R(0.5) * in[(size_t)jp * H + (ip + 1)].y);
+  for (int jp = blockIdx.x; jp < ny - 4; jp += gridDim.x)  // 0-based interior indices
+    for (int ip = threadIdx.x; ip < nx - 4; ip += blockDim.x)
+      psi[(size_t)(jp + 2) * nx + (ip + 2)] = norm * (-R(0.5) * in[(size_t)(jp + by) * H + (ip + 1 + bx)].y);
 }
 
 // ---- host side
@@ -165,9 +174,9 @@ cudaError_t solve_t(DemagSolver* d, const DevState* st, void* const phi[2], void
   Cx* cy = static_cast<Cx*>(d->cy);
   const R* lam = static_cast<const R*>(d->lam);
   k_rho_ext<R><<<grid, 256, 0, s>>>(static_cast<const R*>(phi[0]), static_cast<const R*>(phi[1]),
-                                    static_cast<const R*>(lo[0]), static_cast<const R*>(lo[1]), st, d->nx,
-                                    (size_t)d->nx * d->ny, d->Nx, d->Ny, d->Mx, (R)(1.0 / (12.0 * d->dx)),
-                                    (R)(1.0 / (12.0 * d->dy)), ext_x);
+                                    static_cast<const R*>(lo[0]), static_cast<const R*>(lo[1]), st, d->nx, d->ny,
+                                    (size_t)d->nx * d->ny, d->Nx, d->Ny, d->bx, d->by, d->Mx,
+                                    (R)(1.0 / (12.0 * d->dx)), (R)(1.0 / (12.0 * d->dy)), ext_x);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   cufftSetStream(d->px, s);
@@ -183,8 +192,8 @@ cudaError_t solve_t(DemagSolver* d, const DevState* st, void* const phi[2], void
                                                                                         d->Mx);
   if (FftOf<R>::exec(d->px, ext_x, cx) != CUFFT_SUCCESS) return cudaErrorLaunchFailure;  // back along x
   const R norm = (R)((2.0 / (d->Nx + 1)) * (2.0 / (d->Ny + 1)));
-  k_scatter_psi<R, Cx><<<grid, 256, 0, s>>>(cx, d->Hx, d->Nx, d->Ny, d->nx, norm, st, static_cast<R*>(psi[0]),
-                                            static_cast<R*>(psi[1]));
+  k_scatter_psi<R, Cx><<<grid, 256, 0, s>>>(cx, d->Hx, d->nx, d->ny, d->bx, d->by, norm, st,
+                                            static_cast<R*>(psi[0]), static_cast<R*>(psi[1]));
   return cudaGetLastError();
 }
 
@@ -216,14 +225,32 @@ int create_t(DemagSolver* d) {
 
 }  // namespace
 
+namespace {
+// The Dirichlet box along an axis of N interior sites: the smallest N' >= N whose
+// N' + 1 has no prime factor above 7 (the transform length 2 (N' + 1) then factors
+// into small primes; 2 (N + 1) with a large prime factor, as 2 (4092 + 1) = 2 x 4093,
+// is several times slower), and floor((N' - N) / 2) of the extra sites below I.
+void box_of(int N, int* Np, int* below) {
+  int n = N;
+  for (;; ++n) {
+    int m = n + 1;
+    for (int q = 2; q <= 7; ++q)
+      while (m % q == 0) m /= q;
+    if (m == 1) break;
+  }
+  *Np = n;
+  *below = (n - N) / 2;
+}
+}  // namespace
+
 int demag_create(DemagSolver** out, int nx, int ny, double dx, double dy, int prec) {
   *out = nullptr;
   DemagSolver* d = new (std::nothrow) DemagSolver();
   if (!d) return -1;
   d->nx = nx;
   d->ny = ny;
-  d->Nx = nx - 4;
-  d->Ny = ny - 4;
+  box_of(nx - 4, &d->Nx, &d->bx);
+  box_of(ny - 4, &d->Ny, &d->by);
   d->Mx = 2 * (d->Nx + 1);
   d->My = 2 * (d->Ny + 1);
   d->Hx = d->Mx / 2 + 1;
