@@ -70,12 +70,13 @@
 // occupy registers or whose working type is wider, would spill and keep their
 // natural allocation).
 // Defaults measured best at 4096^2: pass 1 gains 4% from 3 blocks / SM with two
-// sites in flight, pass 2 2% from 5, the descent pass 8% from 6.
+// sites in flight, pass 2 6% from three sites in flight at 4 blocks / SM (against two
+// at 5), the descent pass 8% from 6.
 #ifndef SS_LU1
 #define SS_LU1 2
 #endif
 #ifndef SS_LU2
-#define SS_LU2 2
+#define SS_LU2 3
 #endif
 #ifndef SS_LU3
 #define SS_LU3 4
@@ -84,7 +85,7 @@
 #define SS_MINB1 3
 #endif
 #ifndef SS_MINB2
-#define SS_MINB2 5
+#define SS_MINB2 4
 #endif
 #ifndef SS_MINB3
 #define SS_MINB3 6
