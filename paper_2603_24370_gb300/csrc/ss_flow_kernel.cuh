@@ -71,7 +71,8 @@
 // natural allocation).
 // Defaults measured best at 4096^2: pass 1 gains 4% from 3 blocks / SM with two
 // sites in flight, pass 2 6% from three sites in flight at 4 blocks / SM (against two
-// at 5), the descent pass 8% from 6.
+// at 5), the descent pass 4% from three sites in flight at 5 blocks / SM (against four
+// at 6).
 #ifndef SS_LU1
 #define SS_LU1 2
 #endif
@@ -79,7 +80,7 @@
 #define SS_LU2 3
 #endif
 #ifndef SS_LU3
-#define SS_LU3 4
+#define SS_LU3 3
 #endif
 #ifndef SS_MINB1
 #define SS_MINB1 3
@@ -88,7 +89,7 @@
 #define SS_MINB2 4
 #endif
 #ifndef SS_MINB3
-#define SS_MINB3 6
+#define SS_MINB3 5
 #endif
 
 
