@@ -1,8 +1,21 @@
 // ss_flow_ah.cu -- the flow pass kernels of the Abelian Higgs, instantiated in a
 // translation unit of their own (see ss_flow_kernel.cuh).
+//
+// Launch shape of the FP32 kernels, single problems and batches alike: without a
+// bound they hold 146 / 128 / 114 registers (passes 1 / 2 / 3), one or two blocks per
+// SM. Bounds of 2 / 3 / 3 blocks per SM with one staged site in flight for pass 2 (no
+// spills in passes 1 and 2) were the best of a sweep on a 64-problem batch of the
+// batched set: 0.515 -> 0.404 ms per step.
+#define SS_MINB_THEORY 1  // TH_AH
+#define SS_MINB_BATCH 1
+#define SS_MINB1 2
+#define SS_MINB2 3
+#define SS_MINB3 3
+#define SS_LU2 1
 #include "ss_flow_kernel.cuh"
 
 namespace ss {
+static_assert(SS_MINB_THEORY == TH_AH, "the launch bounds above are the Abelian Higgs kernels'");
 template cudaError_t launch_pass_theory<TH_AH>(const BatchLaunch& b, int pass, cudaStream_t s);
 template void occupancy_theory<TH_AH>(int prec, int ts, bool one, int occ[3]);
 }  // namespace ss

@@ -91,6 +91,16 @@
 #ifndef SS_MINB3
 #define SS_MINB3 5
 #endif
+// The kernels those bounds apply to: the FP32 kernels of theory SS_MINB_THEORY (a TH_*
+// value; default the chiral magnet), single-problem launches, and batched launches too
+// when SS_MINB_BATCH is 1. A theory's translation unit may set all of these before
+// including this header.
+#ifndef SS_MINB_THEORY
+#define SS_MINB_THEORY 2
+#endif
+#ifndef SS_MINB_BATCH
+#define SS_MINB_BATCH 0
+#endif
 
 
 namespace ss {
@@ -348,7 +358,9 @@ __device__ __forceinline__ void load_tile_ctx(TileCtx<R>& tc, const ProbDesc<R>&
 // couplings are read as constant operands instead of occupying registers.
 template <int TH, typename R, int PASS, bool ONE>
 constexpr int pass_min_blocks() {
-  return (TH == TH_CM && sizeof(R) == 4 && ONE) ? (PASS == 1 ? SS_MINB1 : (PASS == 2 ? SS_MINB2 : SS_MINB3)) : 1;
+  return (TH == SS_MINB_THEORY && sizeof(R) == 4 && (ONE || SS_MINB_BATCH))
+             ? (PASS == 1 ? SS_MINB1 : (PASS == 2 ? SS_MINB2 : SS_MINB3))
+             : 1;
 }
 
 template <int TH, typename R, int PASS, bool LO, bool ONE, int TS>

@@ -148,6 +148,11 @@ def test_skyrmion_relaxes_like_the_oracle(S):
 
 @pytest.mark.parametrize("prec", [1, 2])
 def test_batch_problems_evolve_exactly_as_alone(S, prec):
+    """Every problem of a batch follows the trajectory it follows alone: bitwise in FP64.
+    In FP32 the single-problem kernels of this theory carry a register bound (3 blocks
+    per SM) that the batched ones cannot take without spilling, so the two are compiled
+    apart and may contract a product into an FMA differently: the fields agree to the
+    FP32 trajectory tolerance, the step and arrest counts exactly."""
     rng = I.SplitMix64(41)
     probs = []
     for k in range(4):
@@ -164,7 +169,10 @@ def test_batch_problems_evolve_exactly_as_alone(S, prec):
                 s.init_ansatz(p.solitons)
                 st1 = s.step(17)
                 ref = s.fields()
-            assert np.array_equal(got, ref), k
+            if prec == 2:
+                assert np.array_equal(got, ref), k
+            else:
+                assert np.abs(got.astype(np.float64) - ref).max() <= 2e-5, k
             assert st[k]["steps"] == 17 and st[k]["arrests"] == st1["arrests"]
     finally:
         S.ss_batch_destroy(b)
