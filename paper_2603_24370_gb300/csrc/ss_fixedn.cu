@@ -16,7 +16,7 @@
 //
 // Three launches per refresh, every block skipping unless the problem holds a field
 // not refreshed yet (its step count moved since the last refresh) and is running:
-//   k_fn_sums   sum_I |psi|^2 and sum_I v.psi (FP64, compensated, fixed order); the
+//   k_fn_sums   sum_I |psi|^2 and sum_I v.psi (compensated pairs, fixed order); the
 //               last block derives s and alpha (a field without atoms stops the flow
 //               as non-finite);
 //   k_fn_mu     sum_I G_0(psi').psi' and sum_I |psi'|^2 over the scaled field psi' as
@@ -95,8 +95,8 @@ __device__ __forceinline__ void fn_partial(ObsPartial* p, const RPair<R>& a, con
 
 // Per-thread sums of products in the working type's extended precision: FP32 as a
 // float-float pair (the product's rounding error recovered by FMA, the running sum by
-// TwoSum), FP64 as a plain double. A thread sums tens of terms before the FP64 block
-// reduction, so both keep ~1e-13 relative, which the arrest test needs of the atom
+// TwoSum), FP64 as a plain double. A thread sums tens of terms before the block tree
+// of pairs, so both keep ~1e-13 relative, which the arrest test needs of the atom
 // number, while the per-site work stays off the FP64 units (a small fraction of the
 // FP32 rate on this GPU).
 struct AccF {
