@@ -577,6 +577,22 @@ def run_configs(args) -> int:
     return 0
 
 
+def launch_shape(sv, args) -> dict:
+    """Autotune a context's tile shape and pass grids, or fix the tile shape with its
+    default grids (--tile-shape, for profiling one launch configuration)."""
+    if args.tile_shape == "auto":
+        return sv.autotune(4)
+    sv.set_launch(int(args.tile_shape))
+    return {"tile_shape": int(args.tile_shape), "blocks": None, "set_by_hand": True}
+
+
+def throughput_only(metric: str, thr: dict) -> int:
+    """--no-solve: the workload's throughput record alone (for profiling captures)."""
+    print(json.dumps({"metric": metric, "unit": "site-updates/s", "n_gpus": 1, "data": "synthetic",
+                      "throughput": thr}))
+    return 0
+
+
 def run_methods(args) -> int:
     """Arrested Newton flow vs gradient descent, to dx dy max|G| < 1e-6 or a cap."""
     rank, local_rank, world = D.env_rank()
@@ -644,7 +660,7 @@ def run_baby_skyrme(args) -> int:
     p = I.bs_skyrmions(n=n)
     with S.Solver(S.SS_BABY_SKYRME, p.params, n, n, p.dx, p.dy, S.SS_FP32) as sv:
         sv.init_ansatz(p.soliton_array())
-        tuned = sv.autotune(4)
+        tuned = launch_shape(sv, args)
         for _ in range(args.warmup):
             sv.step(INNER)
         torch.cuda.synchronize()
@@ -659,6 +675,8 @@ def run_baby_skyrme(args) -> int:
            "hbm_frac_of_measured": [PASS_BYTES[k + 1] * interior(n) / (ms[k] * 1e-3) / 1e9 / peaks["hbm_gbs"]
                                     for k in range(2)],
            "charge_after": o["charge"], "skyrmions": len(p.solitons)}
+    if args.no_solve:
+        return throughput_only("Baby Skyrme: site-updates/s at 2048^2", thr)
 
     q = I.bs_skyrmions(n=256, count=4, seed=20266)
     sol = q.soliton_array()
@@ -715,7 +733,7 @@ def run_bec(args) -> int:
     ring = [[3.0 * math.cos(a), 3.0 * math.sin(a), 1, 0.3, 0.0] for a in np.linspace(0, 2 * math.pi, 9)[:-1]]
     with S.Solver(S.SS_BEC, prm, n, n, dx, dx, S.SS_FP32) as sv:
         sv.init_ansatz(ring)
-        tuned = sv.autotune(4)
+        tuned = launch_shape(sv, args)
         for _ in range(args.warmup):
             sv.step(INNER)
         torch.cuda.synchronize()
@@ -749,6 +767,8 @@ def run_bec(args) -> int:
                                     for k in range(2)],
            "atoms": o["atoms"], "angular_momentum_per_atom": o["angular_momentum"] / o["atoms"],
            "fixed_atom_number": fixed}
+    if args.no_solve:
+        return throughput_only("BEC: site-updates/s at 2048^2", thr)
     n2, dx2 = 96, 0.15
     prm2 = (1.0, 0.85, 10.0)
     vort = [[1.2 * math.cos(a), 1.2 * math.sin(a), 1, 0.4, 0.0] for a in np.linspace(0, 2 * math.pi, 6)[:-1]]
@@ -831,7 +851,7 @@ def run_sid(args) -> int:
     n, dx = 2048, 0.3
     with S.Solver(S.SS_SID, prm, n, n, dx, dx, S.SS_FP32) as sv:
         sv.init_ansatz(vortices(n, dx, 64, 20267))
-        tuned = sv.autotune(4)
+        tuned = launch_shape(sv, args)
         for _ in range(args.warmup):
             sv.step(INNER)
         torch.cuda.synchronize()
@@ -847,6 +867,8 @@ def run_sid(args) -> int:
            "hbm_frac_of_measured": [bytes6[k + 1] * interior(n) / (ms[k] * 1e-3) / 1e9 / peaks["hbm_gbs"]
                                     for k in range(2)],
            "winding_after": o["charge"], "flux_over_2pi": o["flux"] / (2 * np.pi)}
+    if args.no_solve:
+        return throughput_only("s+id: site-updates/s at 2048^2", thr)
     m, dxm = 256, 0.3
     vort = vortices(m, dxm, 4, 20268)
     gpu = {}
@@ -944,9 +966,12 @@ def main() -> int:
                     choices=("cm4096", "ah-batch", "configs", "methods", "baby-skyrme", "bec", "sid", "demag"),
                     default="cm4096")
     ap.add_argument("--tile-shape", choices=("auto", "0", "1"), default="auto",
-                    help="flow tile shape: autotuned (default) or fixed (for profiling one shape)")
+                    help="flow tile shape: autotuned (default) or fixed with default grids (for profiling "
+                         "one shape; the default run and the baby-skyrme, bec and sid workloads)")
     ap.add_argument("--fp64-per-side", type=int, default=2, help="ah-batch: FP64 problems timed per side")
-    ap.add_argument("--no-solve", action="store_true", help="skip the time-per-solve record of the default run")
+    ap.add_argument("--no-solve", action="store_true",
+                    help="skip the time-per-solve record of the default run, and the time-to-solution runs of "
+                         "the baby-skyrme, bec and sid workloads")
     ap.add_argument("--method", choices=("anf", "gradient"), default="anf",
                     help="minimiser timed by the default workload (gradient: one descent kernel per step)")
     args = ap.parse_args()
