@@ -199,12 +199,14 @@ def test_chiral_magnet_1024_fp32_relaxes_with_exact_charge(S):
 
 @pytest.mark.parametrize("prec", [1, 2])
 def test_sampled_one_step_parity_at_4096(S, prec):
-    """The 4096^2 chiral-magnet workload (400 skyrmions): one flow step on the GPU vs
+    """The 4096^2 chiral-magnet workload (400 skyrmions): one flow step on the GPU, in
+    the launch configuration the benchmark times (autotuned tile shape and grids), vs
     the oracle's step of 41x41 patches around sampled sites (a step reaches 8 sites
     out, so the central 11x11 of each patch is exact)."""
     p = I.cm_skyrmions(n=4096, count=400, seed=20264)
     with S.Solver(CM, p.params, p.nx, p.ny, p.dx, p.dy, prec) as s:
         s.init_ansatz(p.soliton_array())
+        s.autotune(4)  # as bench.py does; the field is restored at rest
         f0 = s.fields().astype(np.float64)
         q = s.observables()["charge"]
         s.step(1)
