@@ -309,7 +309,12 @@ def run_native(args) -> int:
                 "pass_ms": stage_ms,
                 "step_bytes_per_site_update": GD_BYTES if gd else sum(PASS_BYTES.values()),
                 "step_frac": ((GD_BYTES if gd else sum(PASS_BYTES.values())) * interior(n)
-                              / (sum(stage_ms) * 1e-3) / 1e9) / peaks["hbm_gbs"]}
+                              / (sum(stage_ms) * 1e-3) / 1e9) / peaks["hbm_gbs"],
+                # the method's own minimum per site-update, reachable only by a single-pass
+                # (temporally blocked) step: phi and v in and out (descent: phi in and out)
+                "min_bytes_per_site_update": (2 if gd else 4) * 4 * C,
+                "effective_frac": ((2 if gd else 4) * 4 * C * interior(n)
+                                   / (sum(stage_ms) * 1e-3) / 1e9) / peaks["hbm_gbs"]}
 
     # end to end through the C-ABI with host buffers: field in from pinned memory,
     # 32 flow steps, field out to pinned memory, every bench step
