@@ -287,6 +287,9 @@ typedef struct {
 
 /* Create a batch of n >= 1 problems of `theory` in `precision`, each initialised
  * from its ansatz, at rest. cuda_stream as for ss_create_grid.
+ * Two forms need a single-grid context and are rejected here (SS_ERR_ARG): the chiral
+ * magnet with demagnetisation (mu_d > 0; its Poisson solve is per grid) and the BEC at a
+ * fixed atom number (N > 0; its refresh reduces over one grid).
  * Errors: SS_ERR_ARG (message names the item), SS_ERR_NOMEM, SS_ERR_CUDA. */
 int ss_batch_create(ss_batch** out, int theory, int precision, const ss_batch_item* items, int n, void* cuda_stream);
 
