@@ -20,6 +20,9 @@ pytestmark = pytest.mark.gpu
 CMD = 6
 PRM = (1.0, 1.0, 0.1, 0.6, 0.0, 0.8)  # J, D, K, h, dmi_type, mu_d
 GRID = (71, 45, 0.2, 0.23)
+# Dirichlet boxes: GRID pads x only (67 -> 69 sites, one below I); GRID_PAD pads both
+# axes with a site below I (60 -> 62, 36 -> 39)
+GRID_PAD = (64, 40, 0.21, 0.2)
 
 
 @pytest.fixture(scope="module")
@@ -37,9 +40,10 @@ def dtype_of(prec):
     return np.float64 if prec == 2 else np.float32
 
 
+@pytest.mark.parametrize("grid", [GRID, GRID_PAD])
 @pytest.mark.parametrize("prec", [1, 2, 3])
-def test_force_and_energy_match_oracle(S, prec):
-    nx, ny, dx, dy = GRID
+def test_force_and_energy_match_oracle(S, prec, grid):
+    nx, ny, dx, dy = grid
     f = I.smooth_field(CMD, nx, ny, dx, dy, seed=181).astype(dtype_of(prec))
     with S.Solver(S.SS_CHIRAL_MAGNET, PRM, nx, ny, dx, dy, prec) as s:
         s.set_fields(f)
@@ -58,10 +62,11 @@ def test_force_and_energy_match_oracle(S, prec):
     assert np.abs(G.astype(np.float64) - G0).max() > 1e-3 * scale
 
 
+@pytest.mark.parametrize("grid", [GRID, GRID_PAD])
 @pytest.mark.parametrize("prec", [1, 2, 3])
-def test_trajectory_matches_oracle(S, prec):
+def test_trajectory_matches_oracle(S, prec, grid):
     """30 flow steps, the potential solved once per step for the step's starting field."""
-    nx, ny, dx, dy = GRID
+    nx, ny, dx, dy = grid
     n = 30
     f = I.smooth_field(CMD, nx, ny, dx, dy, seed=282).astype(dtype_of(prec))
     with S.Solver(S.SS_CHIRAL_MAGNET, PRM, nx, ny, dx, dy, prec) as s:
