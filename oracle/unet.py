@@ -4,8 +4,9 @@ Only the tests, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU legs may impo
 this module; the library never does. It restates, in plain numpy (float64), what the
 network computes: 3x3 convolutions with zero padding written as a sum over the nine
 taps, ReLU, 2x2 average pooling, nearest-neighbour x2 upsampling, channel
-concatenation, the mean-squared loss over the interior sites, and the exact
-backward pass of all of it. Nothing here is blocked, fused or reordered.
+concatenation, the mean-squared loss over the interior sites, the exact backward
+pass of all of it, and the Adam update that trains it (Kingma & Ba 2015,
+Algorithm 1). Nothing here is blocked, fused or reordered.
 
 The paper has no learned component (it starts every relaxation from a
 model-specific ansatz, Sec. 4.1); the architecture is the 4-level U-Net with
@@ -20,7 +21,7 @@ format keeps the upper 16 bits of an IEEE float32).
 
 Pins: tests/test_unet_oracle.py (direct-sum definition, scipy correlation,
 adjointness of every linear layer, central-difference gradients, torch's bfloat16
-conversion).
+conversion, Adam's closed-form first steps).
 """
 from __future__ import annotations
 
@@ -181,16 +182,23 @@ def mse(out: np.ndarray, target: np.ndarray, C: int):
     return float(np.sum(diff * diff) / count), d
 
 
-def backward(theta: np.ndarray, cache: dict, gout: np.ndarray, widths=WIDTHS, bf16: bool = True) -> np.ndarray:
-    """Gradient of the loss with respect to the flat parameter vector, given d loss / d output."""
+def backward(theta: np.ndarray, cache: dict, gout: np.ndarray, widths=WIDTHS, bf16: bool = True,
+             magnitudes: bool = False):
+    """Gradient of the loss with respect to the flat parameter vector, given d loss / d output.
+    With magnitudes=True, also the flat vector of the sums of the absolute values of
+    the terms that make up each gradient entry (the same contractions on |x| and |g|):
+    the scale against which an accumulation in another order or precision is judged."""
     r = round_bf16 if bf16 else (lambda a: a)
     c, P = cache, cache["P"]
     c1, c2, c3, c4 = widths
     grads = [None] * 15
+    mags = [None] * 15
 
     def back(i, x, y, gy, need_gx=True):
         g = gy * (y > 0) if y is not None else gy
         grads[i] = (conv3x3_grad_weight(x, r(g)), g.sum(axis=(0, 1, 2)))
+        if magnitudes:
+            mags[i] = (conv3x3_grad_weight(np.abs(x), np.abs(r(g))), np.abs(g).sum(axis=(0, 1, 2)))
         return conv3x3_grad_input(r(g), P[i][0]) if need_gx else None
 
     g = back(14, c["d1"], None, gout)
@@ -208,7 +216,10 @@ def backward(theta: np.ndarray, cache: dict, gout: np.ndarray, widths=WIDTHS, bf
     gp1 = back(2, c["p1"], c["e2a"], g)
     g = back(1, c["e1a"], c["e1"], gcat1[..., c2:] + avgpool2_backward(gp1))
     back(0, c["in"], c["e1a"], g, need_gx=False)
-    return np.concatenate([np.concatenate([gw.ravel(), gb]) for gw, gb in grads])
+    flat = np.concatenate([np.concatenate([gw.ravel(), gb]) for gw, gb in grads])
+    if magnitudes:
+        return flat, np.concatenate([np.concatenate([mw.ravel(), mb]) for mw, mb in mags])
+    return flat
 
 
 def loss_and_grad(theta, x, target, C, widths=WIDTHS, bf16=True):
@@ -227,3 +238,16 @@ def pack_input(fields: np.ndarray, couplings, cin=CIN) -> np.ndarray:
         for k in range(cp.shape[1]):
             x[..., C + k] = cp[:, k][:, None, None]
     return x
+
+
+# ---------------------------------------------------------------- optimiser
+def adam_step(theta, m, v, g, t: int, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):
+    """Update t (counted from 1) of Adam (Kingma & Ba 2015, Algorithm 1), in float64:
+    the first and second moment estimates, their bias corrections 1 - beta^t, and the
+    parameter step lr * m_hat / (sqrt(v_hat) + eps). Returns new (theta, m, v)."""
+    theta, m, v, g = (np.asarray(a, dtype=np.float64) for a in (theta, m, v, g))
+    m_new = beta1 * m + (1.0 - beta1) * g
+    v_new = beta2 * v + (1.0 - beta2) * g * g
+    m_hat = m_new / (1.0 - beta1 ** t)
+    v_hat = v_new / (1.0 - beta2 ** t)
+    return theta - lr * m_hat / (np.sqrt(v_hat) + eps), m_new, v_new

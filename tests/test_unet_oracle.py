@@ -89,3 +89,37 @@ def test_bf16_rounding_ties_to_even_and_matches_torch():
     v = rng.normal(size=10000) * np.exp(rng.uniform(-20, 20, size=10000))
     ref = torch.tensor(v, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
     assert np.array_equal(U.round_bf16(v), ref)
+
+
+def test_adam_first_update_is_the_normalised_gradient():
+    """Bias correction makes update 1 exactly -lr g / (|g| + eps): m_hat = g and
+    v_hat = g^2 after one step from zero moments."""
+    g = np.array([3.0, -0.5, 1e-9, -2e-8, 0.0, 7e4])
+    theta = rng.normal(size=g.size)
+    lr, eps = 1e-3, 1e-8
+    t1, m1, v1 = U.adam_step(theta, np.zeros_like(g), np.zeros_like(g), g, 1, lr)
+    assert np.allclose(t1, theta - lr * g / (np.abs(g) + eps), rtol=0, atol=1e-15)
+    assert np.allclose(m1, 0.1 * g, rtol=1e-15) and np.allclose(v1, 0.001 * g * g, rtol=1e-15)
+
+
+def test_adam_constant_gradient_keeps_the_step_size():
+    """With a constant gradient the corrected moments stay g and g^2 at every update
+    (sum_k (1 - b) b^k over t terms = 1 - b^t), so each step is lr g / (|g| + eps)."""
+    g = np.array([0.25, -4.0])
+    theta, m, v = np.zeros(2), np.zeros(2), np.zeros(2)
+    for t in range(1, 8):
+        theta, m, v = U.adam_step(theta, m, v, g, t, 0.01)
+    assert np.allclose(theta, -7 * 0.01 * g / (np.abs(g) + 1e-8), rtol=1e-12)
+
+
+def test_adam_two_updates_worked_by_hand():
+    """g = +1 then -1: m_2 = 0.9 * 0.1 - 0.1 = -0.01, m_hat = -0.01 / 0.19 = -1/19;
+    v_2 = 0.999 * 0.001 + 0.001 = 0.001999 = 1 - 0.999^2, v_hat = 1. So
+    theta_2 = theta_0 - lr / (1 + eps) + lr / (19 (1 + eps)).
+    g = +1 then 0: m_hat = 0.09 / 0.19 = 9/19, v_hat = 0.000999 / 0.001999 = 999/1999."""
+    lr, eps = 0.05, 1e-8
+    th, m, v = U.adam_step(np.zeros(2), np.zeros(2), np.zeros(2), np.array([1.0, 1.0]), 1, lr)
+    th, m, v = U.adam_step(th, m, v, np.array([-1.0, 0.0]), 2, lr)
+    assert th[0] == pytest.approx(-lr / (1 + eps) + lr / (19 * (1 + eps)), rel=1e-13)
+    assert th[1] == pytest.approx(-lr / (1 + eps) - lr * (9 / 19) / (np.sqrt(999 / 1999) + eps), rel=1e-13)
+    assert m[0] == pytest.approx(-0.01, rel=1e-13) and v[0] == pytest.approx(0.001999, rel=1e-13)
