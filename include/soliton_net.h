@@ -78,6 +78,18 @@ int ss_net_gradients(ss_net* net, const float* ansatz, const double* couplings, 
  * stream and completes before the next call on it. */
 int ss_net_train_step(ss_net* net, const float* ansatz, const double* couplings, const float* relaxed, int batch,
                       float lr, double* loss_out);
+/* One Adam update (the same as ss_net_train_step's) from a caller-supplied gradient
+ * `grad` (device, ss_net_num_params floats, read only), e.g. gradients accumulated
+ * over several batches or summed across ranks. Adam (Kingma & Ba 2015, Algorithm 1)
+ * in FP32: m <- 0.9 m + 0.1 g, v <- 0.999 v + 0.001 g^2, theta <- theta - lr
+ * (m / (1 - 0.9^t)) / (sqrt(v / (1 - 0.999^t)) + 1e-8), t the update count from 1.
+ * The paper has no learned part; this call serves the network's training. Enqueued
+ * on the network's stream; returns after the update has completed. Errors:
+ * SS_ERR_ARG (NULL, lr not positive and finite), SS_ERR_CUDA. */
+int ss_net_apply_gradients(ss_net* net, const float* grad, float lr);
+/* Copy the Adam moments m and v (host arrays of ss_net_num_params floats; either may
+ * be NULL) and the number of updates taken (may be NULL). Synchronises the stream. */
+int ss_net_get_optimizer_state(ss_net* net, float* m_host, float* v_host, long long* steps);
 /* Initial fields (device, FP32 SoA [batch][C][size][size]) = ansatz + correction on
  * the interior, the ansatz itself on the halo (the Dirichlet values stay exact);
  * chiral magnet: renormalised to unit length. `ansatz` (device) in the same layout. */

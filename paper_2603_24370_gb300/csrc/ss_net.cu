@@ -165,12 +165,16 @@ __global__ void k_pack_weights(const float* __restrict__ theta, const LayerTable
   }
 }
 
+// Adam (Kingma & Ba 2015, Algorithm 1) over the flat parameter vector. omb1, omb2 are
+// 1 - beta1, 1 - beta2 and c1, c2 the bias corrections 1 - beta1^t, 1 - beta2^t of
+// update t, each formed in FP64 and rounded once (1.f - 0.999f would be 1.3e-5 off).
 __global__ void k_adam(float* __restrict__ theta, const float* __restrict__ g, float* __restrict__ m,
-                       float* __restrict__ v, long long n, float lr, float b1, float b2, float eps, float c1, float c2) {
+                       float* __restrict__ v, long long n, float lr, float b1, float b2, float omb1, float omb2,
+                       float eps, float c1, float c2) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const float gi = g[i];
-    const float mi = b1 * m[i] + (1.f - b1) * gi;
-    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    const float mi = b1 * m[i] + omb1 * gi;
+    const float vi = b2 * v[i] + omb2 * (gi * gi);
     m[i] = mi;
     v[i] = vi;
     theta[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
@@ -595,18 +599,42 @@ extern "C" int ss_net_gradients(ss_net* n, const float* ansatz, const double* co
   return SS_OK;
 }
 
+// One Adam update of the parameters from the gradient `g` (device, nparam floats),
+// then the BF16 weight copies are re-packed.
+static int adam_update(ss_net* n, const float* g, float lr) {
+  n->t += 1;
+  const double b1 = 0.9, b2 = 0.999;
+  const float c1 = (float)(1.0 - std::pow(b1, (double)n->t)), c2 = (float)(1.0 - std::pow(b2, (double)n->t));
+  k_adam<<<grid_of((size_t)n->nparam), 256, 0, n->stream>>>(n->theta, g, n->m, n->v, n->nparam, lr, (float)b1,
+                                                            (float)b2, (float)(1.0 - b1), (float)(1.0 - b2), 1e-8f,
+                                                            c1, c2);
+  NET_CK(cudaGetLastError());
+  return pack_weights(n);
+}
+
 extern "C" int ss_net_train_step(ss_net* n, const float* ansatz, const double* couplings, const float* relaxed,
                                  int batch, float lr, double* loss_out) {
   if (!(lr > 0.f) || !std::isfinite(lr)) return nfail(SS_ERR_ARG, "lr must be positive and finite");
   int rc = ss_net_gradients(n, ansatz, couplings, relaxed, batch, nullptr, loss_out);
   if (rc) return rc;
-  n->t += 1;
-  const float b1 = 0.9f, b2 = 0.999f;
-  const float c1 = 1.f - (float)std::pow(0.9, (double)n->t), c2 = 1.f - (float)std::pow(0.999, (double)n->t);
-  k_adam<<<grid_of((size_t)n->nparam), 256, 0, n->stream>>>(n->theta, n->grad, n->m, n->v, n->nparam, lr, b1, b2,
-                                                            1e-8f, c1, c2);
-  NET_CK(cudaGetLastError());
-  return pack_weights(n);
+  return adam_update(n, n->grad, lr);
+}
+
+extern "C" int ss_net_apply_gradients(ss_net* n, const float* grad, float lr) {
+  if (!n || !grad) return nfail(SS_ERR_ARG, "NULL argument");
+  if (!(lr > 0.f) || !std::isfinite(lr)) return nfail(SS_ERR_ARG, "lr must be positive and finite");
+  int rc = adam_update(n, grad, lr);
+  if (rc) return rc;
+  return check_err(n);
+}
+
+extern "C" int ss_net_get_optimizer_state(ss_net* n, float* m_host, float* v_host, long long* steps) {
+  if (!n) return nfail(SS_ERR_ARG, "NULL argument");
+  if (m_host) NET_CK(cudaMemcpyAsync(m_host, n->m, sizeof(float) * n->nparam, cudaMemcpyDeviceToHost, n->stream));
+  if (v_host) NET_CK(cudaMemcpyAsync(v_host, n->v, sizeof(float) * n->nparam, cudaMemcpyDeviceToHost, n->stream));
+  NET_CK(cudaStreamSynchronize(n->stream));
+  if (steps) *steps = n->t;
+  return SS_OK;
 }
 
 extern "C" int ss_net_predict(ss_net* n, const float* ansatz, const double* couplings, int batch, float* init) {

@@ -144,6 +144,8 @@ def load_library(path: str | None = None):
             "ss_net_gradients": ([vp, vp, pd, vp, i, vp, pd], i),
             "ss_net_train_step": ([vp, vp, pd, vp, i, ctypes.c_float, pd], i),
             "ss_net_predict": ([vp, vp, pd, i, vp], i),
+            "ss_net_apply_gradients": ([vp, vp, ctypes.c_float], i),
+            "ss_net_get_optimizer_state": ([vp, vp, vp, ctypes.POINTER(ll)], i),
             "ss_conv3x3": ([vp, i, i, i, i, vp, i, vp, i, vp, vp], i),
             "ss_conv3x3_wgrad": ([vp, vp, i, i, i, i, i, vp, vp], i),
             "ss_wait_selftest": ([i, vp], i),
@@ -578,6 +580,21 @@ def ss_net_train_step(net, ansatz, couplings, relaxed, batch: int, lr: float) ->
     _net_check(load_library().ss_net_train_step(net, _dev(ansatz), keep[1] if keep else None, _dev(relaxed), batch,
                                                 lr, ctypes.byref(loss)))
     return loss.value
+
+
+def ss_net_apply_gradients(net, grad, lr: float) -> None:
+    _net_check(load_library().ss_net_apply_gradients(net, _dev(grad), lr))
+
+
+def ss_net_get_optimizer_state(net):
+    """(m, v, updates taken) of the network's Adam state, m and v as host float32 arrays."""
+    n = ss_net_num_params(net)
+    m = np.empty(n, dtype=np.float32)
+    v = np.empty(n, dtype=np.float32)
+    t = ctypes.c_longlong()
+    _net_check(load_library().ss_net_get_optimizer_state(net, ctypes.c_void_p(m.ctypes.data),
+                                                         ctypes.c_void_p(v.ctypes.data), ctypes.byref(t)))
+    return m, v, int(t.value)
 
 
 def ss_net_predict(net, ansatz, couplings, batch: int, init) -> None:
