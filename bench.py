@@ -4,7 +4,8 @@
 
 Workload: chiral magnet (J = D = 1, h = 0.6, K = 0.1, interfacial DMI) on a
 4096 x 4096 grid (dx = 0.2, halo included), compensated FP32 fields (value +
-remainder planes) with FP64 reductions, 400 compact skyrmions at seeded positions
+remainder planes; the flow's sums in float-float pairs totalled in FP64), 400 compact
+skyrmions at seeded positions
 (minimum separation 8). Its arrays (8 x 201 MB) are far larger than the 129 MB L2,
 so every timed step streams HBM.
 
@@ -75,8 +76,12 @@ COUNT = 400
 SEED = 20264
 CROP = 512          # oracle sample (CPU baseline / reference arm)
 C = 3
+# planes per component of the method's minimum traffic in compensated FP32: phi
+# (value, remainder) and v read and written; descent: phi read and written
+MIN_PLANES = {False: 6, True: 4}
 WORKLOAD = ("chiral magnet 4096x4096 (halo incl.), dx=0.2, J=D=1, h=0.6, K=0.1, interfacial DMI, "
-            "400 skyrmions min-sep 8, compensated FP32 fields + FP64 reductions, ANF-RK4 (2 fused kernels/step)")
+            "400 skyrmions min-sep 8, compensated FP32 fields (value + remainder planes), float-float flow sums "
+            "totalled in FP64, ANF-RK4 (2 fused kernels/step)")
 
 
 def interior(n: int) -> int:
@@ -310,10 +315,13 @@ def run_native(args) -> int:
                 "step_bytes_per_site_update": GD_BYTES if gd else sum(PASS_BYTES.values()),
                 "step_frac": ((GD_BYTES if gd else sum(PASS_BYTES.values())) * interior(n)
                               / (sum(stage_ms) * 1e-3) / 1e9) / peaks["hbm_gbs"],
-                # the method's own minimum per site-update, reachable only by a single-pass
-                # (temporally blocked) step: phi and v in and out (descent: phi in and out)
-                "min_bytes_per_site_update": (2 if gd else 4) * 4 * C,
-                "effective_frac": ((2 if gd else 4) * 4 * C * interior(n)
+                # the method's own minimum per site-update at the run's storage precision,
+                # reachable only by a single-pass (temporally blocked) step: phi (value and
+                # remainder planes) and v in and out; descent: phi in and out
+                "min_bytes_per_site_update": MIN_PLANES[gd] * 4 * C,
+                "min_bytes_basis": ("compensated FP32: phi value + remainder in and out" if gd else
+                                    "compensated FP32: phi value + remainder and v, in and out"),
+                "effective_frac": (MIN_PLANES[gd] * 4 * C * interior(n)
                                    / (sum(stage_ms) * 1e-3) / 1e9) / peaks["hbm_gbs"]}
 
     # end to end through the C-ABI with host buffers: field in from pinned memory,
@@ -379,7 +387,7 @@ BATCH_TOL = 1e-6
 BATCH_CAP = 40000
 BATCH_WORKLOAD = ("256 Abelian Higgs relaxations in one batch, sides U{64,128,256,512} (halo incl.), dx=0.1, "
                   "lambda U[0.5,2], N U{1..4} unit vortices uniform in the central half, compensated FP32 "
-                  "fields + FP64 reductions, to dx dy max|G| < 1e-6")
+                  "fields (float-float flow sums totalled in FP64), to dx dy max|G| < 1e-6")
 
 
 def solve_summary(S, I, np, count: int = 64, fp64_per_side: int = 1) -> dict:

@@ -689,22 +689,29 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
       __syncthreads();
       if (s_last) {
         __threadfence();
-        double tot[2], mtot;  // the problem's sum of e, sum of e(new) - e(previous), max |G|
+        double tot[2] = {0.0, 0.0}, mtot = 0.0;  // the problem's sum of e, sum of e(new) - e(previous), max |G|
         if constexpr (sizeof(R) == 4) {
-          // the partials hold FP32 pairs exactly: total them as FP32 pairs (this GPU's
-          // FP64 units would hold the problem's last block for microseconds)
-          RPair<R> acc{R(0), R(0)}, dacc{R(0), R(0)};
-          R mm = R(0);
-          for (int i = tid; i < nslots; i += NT) {
-            const FlowPartial* q = d.part + i;
-            acc = pair_add(acc, RPair<R>{R(__ldcg(&q->es)), R(__ldcg(&q->ec))});
-            dacc = pair_add(dacc, RPair<R>{R(__ldcg(&q->ds)), R(__ldcg(&q->dc))});
-            mm = rmax(mm, R(__ldcg(&q->m)));
+          // The partials hold float-float pairs exactly. One warp totals them in FP64
+          // pairs (Neumaier per lane, then a fixed warp tree): a few hundred slots, so
+          // this GPU's slow FP64 pipe is busy for well under a microsecond.
+          if (tid < 32) {
+            DD acc{0.0, 0.0}, dacc{0.0, 0.0};
+            R mm = R(0);
+            for (int i = tid; i < nslots; i += 32) {
+              const FlowPartial* q = d.part + i;
+              neumaier(acc, __ldcg(&q->es));
+              neumaier(acc, __ldcg(&q->ec));
+              neumaier(dacc, __ldcg(&q->ds));
+              neumaier(dacc, __ldcg(&q->dc));
+              mm = rmax(mm, R(__ldcg(&q->m)));
+            }
+            acc = warp_sum(acc);
+            dacc = warp_sum(dacc);
+            for (int off = 16; off > 0; off >>= 1) mm = rmax(mm, __shfl_down_sync(0xffffffffu, mm, off));
+            tot[0] = acc.s + acc.c;
+            tot[1] = dacc.s + dacc.c;
+            mtot = (double)mm;
           }
-          tile_reduce<R>(acc, dacc, mm, sred);
-          tot[0] = (double)acc.s + (double)acc.c;
-          tot[1] = (double)dacc.s + (double)dacc.c;
-          mtot = (double)mm;
         } else {
           DD acc{0.0, 0.0}, dacc{0.0, 0.0};
           double mm = 0.0;
