@@ -57,8 +57,9 @@ extern "C" {
 /* ---- precisions ---- */
 #define SS_FP32 1       /* compensated FP32: each field component is stored as two   */
                         /* FP32 planes (value + rounding remainder) so that small    */
-                        /* flow increments accumulate; stencils and forces in FP32,  */
-                        /* reductions in FP64 (compensated)                          */
+                        /* flow increments accumulate; stencils and forces in FP32;  */
+                        /* the flow's sums in float-float pairs (TwoSum) totalled in */
+                        /* FP64; observables in FP64 (compensated)                   */
 #define SS_FP64 2       /* all-FP64 reference form                                    */
 #define SS_FP32_PLAIN 3 /* one FP32 plane per component: fastest, but field rounding  */
                         /* limits the attainable dx dy max|G| to about 1e-5           */
@@ -243,9 +244,13 @@ int ss_step(ss_ctx* ctx, int n_steps, ss_status* out);
 
 /* Run the flow until dx dy max_I |G| < tol (checked before every step) or
  * max_steps steps have been taken in this call. Steps run in CUDA-graph chunks;
- * the host polls one small status record per chunk. Returns SS_OK if converged,
- * SS_ERR_NOT_CONVERGED if max_steps was reached, SS_ERR_NONFINITE, or another error.
- * out (may be NULL) receives the final status in every case. */
+ * the host polls one small status record per chunk. With FP32 fields the flow's
+ * own residual is FP32 arithmetic, so the verdict is the FP64 evaluation of the
+ * stored field (value + remainder, as ss_observables): while that is not below
+ * tol, the flow continues under a working threshold tightened by 0.7 each time,
+ * within the same max_steps. Returns SS_OK if converged, SS_ERR_NOT_CONVERGED if
+ * max_steps was reached, SS_ERR_NONFINITE, or another error. out (may be NULL)
+ * receives the final status in every case (its grad_max is the flow's own). */
 int ss_minimise(ss_ctx* ctx, double tol, long long max_steps, ss_status* out);
 
 /* Observables of the current field (Sec. 2: "GPU-resident evaluation of
@@ -365,11 +370,12 @@ int ss_batch_destroy(ss_batch* batch);
  * `fields`, without a context, and calls no cudaMalloc, cudaFree or allocating
  * library routine.
  *
- *  theory, params, n_params: as ss_set_theory, except that the two forms that
- *             need a context's state are rejected: demagnetisation (mu_d > 0) and the
- *             BEC at a fixed atom number (N > 0).
+ *  theory, params, n_params: as ss_set_theory (validated by the same rules), except
+ *             that the two forms that need a context's state are rejected:
+ *             demagnetisation (mu_d > 0) and the BEC at a fixed atom number (N > 0).
  *  fields:    device pointer, [C][ny][nx] planes of the given precision (float for
- *             SS_FP32, double for SS_FP64), halo included. Read only.
+ *             SS_FP32 and SS_FP32_PLAIN, double for SS_FP64), halo included. Read
+ *             only. For SS_FP32 this is the value plane alone (no remainder).
  *  nx, ny, dx, dy: as ss_create_grid; nx, ny <= 65536 and nx * ny <= 2^31, larger
  *             grids are rejected with SS_ERR_ARG.
  *  out:       device pointer to 6 doubles, written with {energy, charge, flux,
@@ -384,9 +390,10 @@ int ss_batch_destroy(ss_batch* batch);
  * it and it keeps the last call's contents: each call clears the counter it needs
  * zeroed, but calls whose GPU work overlaps (different streams or host threads
  * without ordering between them) race on it and must be serialized by the caller.
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture.
+ * Every call looks up the array's device address (cudaGetSymbolAddress) on the
+ * caller's current device, so no address outlives a device reset. The first call
+ * on a device also loads the library's device code there: make that first call
+ * before any stream capture.
  *
  * Errors: SS_ERR_ARG (NULL pointers, sizes, spacings, theory, params), SS_ERR_CUDA. */
 int ss_observables_noalloc(int theory, const double* params, int n_params, const void* fields, int nx, int ny,

@@ -138,6 +138,11 @@ cudaError_t launch_fixed_n_refresh(const FixedNLaunch& L, cudaStream_t s);
 // Record the calling thread's error message for ss_last_error().
 void set_last_error(const std::string& msg);
 
+// Validate the parameters of an SS_* theory (ss_set_theory's rules) and pack them as
+// the kernels' couplings; *C = components per site. Returns SS_OK or SS_ERR_ARG
+// (message set). ss_api.cu.
+int pack_couplings(int theory, const double* params, int n_params, double k[NCOUP], int* C);
+
 // Grid of each flow pass 1, 2, 3 (its occupancy x SMs, capped by the tile count).
 void flow_grid(int theory, int prec, int ts, int total_tiles, bool one, int blocks[3]);
 // Blocks of each pass 1, 2, 3 that fit on one SM.

@@ -14,7 +14,6 @@
 
 #include <cmath>
 #include <cstring>
-#include <mutex>
 #include <string>
 
 #include "soliton.h"
@@ -29,7 +28,6 @@ namespace {
 constexpr int NOALLOC_MAX_BLOCKS = 2048;
 constexpr size_t NOALLOC_RECORD_BYTES = (sizeof(DevState) + 255) & ~size_t(255);
 constexpr size_t NOALLOC_BYTES = NOALLOC_RECORD_BYTES + sizeof(ObsPartial) * NOALLOC_MAX_BLOCKS;
-constexpr int NOALLOC_MAX_DEVICES = 64;
 
 }  // namespace
 
@@ -38,9 +36,6 @@ constexpr int NOALLOC_MAX_DEVICES = 64;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 
 namespace {
-
-std::mutex g_noalloc_mu;
-void* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {nullptr};
 
 // Copy the result record into the caller's output (grad_max = dx dy * max|G|).
 __global__ void k_noalloc_out(const DevState* st, double area, double* out) {
@@ -69,82 +64,26 @@ extern "C" int ss_observables_noalloc(int theory, const double* params, int n_pa
                         "ss_observables_noalloc: grid larger than the supported maximum (nx, ny <= 65536, nx*ny <= 2^31)");
   if (!(dx > 0.0) || !(dy > 0.0) || !std::isfinite(dx) || !std::isfinite(dy))
     return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: dx and dy must be positive and finite");
-  if (precision != SS_FP32 && precision != SS_FP64)
-    return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: precision must be SS_FP32 or SS_FP64");
-  if (!params && n_params > 0) return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: params is NULL");
+  if (precision != SS_FP32 && precision != SS_FP64 && precision != SS_FP32_PLAIN)
+    return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: precision must be SS_FP32, SS_FP32_PLAIN or SS_FP64");
 
-  // couplings, packed as in ss_set_theory
-  double k[NCOUP] = {0};
-  if (theory == SS_ABELIAN_HIGGS) {
-    if (n_params < 1 || n_params > 2) return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: Abelian Higgs takes {lambda[, u]}");
-    const double u = n_params > 1 ? params[1] : 1.0;
-    if (!std::isfinite(params[0]) || !std::isfinite(u) || params[0] < 0.0)
-      return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: lambda must be finite and >= 0");
-    k[0] = params[0];
-    k[1] = u * u;
-  } else if (theory == SS_CHIRAL_MAGNET) {
-    if (n_params == 6 && params[5] != 0.0)
-      return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: demagnetisation needs a context (a Poisson solve)");
-    if (n_params < 4 || n_params > 6)
-      return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: chiral magnet takes {J, D, K, h[, dmi_type]}");
-    for (int i = 0; i < n_params; ++i)
-      if (!std::isfinite(params[i])) return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: parameters must be finite");
-    if (!(params[0] > 0.0)) return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: J must be > 0");
-    const int type = n_params > 4 ? (int)params[4] : 0;
-    if (type < 0 || type > 2 || (n_params > 4 && params[4] != (double)type))
-      return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: dmi_type must be 0, 1 or 2");
-    for (int i = 0; i < 4; ++i) k[i] = params[i];
-    if (type == 0) { k[5] = 1.0; k[7] = -1.0; }
-    else if (type == 1) { k[4] = 1.0; k[8] = 1.0; }
-    else { k[4] = 1.0; k[8] = -1.0; }
-  } else if (theory == SS_SID) {
-    if (n_params != 7) return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: s+id takes {a1, a2, b1, b2, b3, b4, nu}");
-    for (int i = 0; i < 7; ++i) {
-      if (!std::isfinite(params[i])) return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: parameters must be finite");
-      k[i] = params[i];
-    }
-  } else if (theory == SS_BEC) {
-    if (n_params == 4 && params[3] != 0.0)
-      return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: a fixed atom number needs a context (its multiplier)");
-    if (n_params < 3 || n_params > 4)
-      return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: BEC takes {g, Omega, mu[, N = 0]}");
-    for (int i = 0; i < n_params; ++i)
-      if (!std::isfinite(params[i])) return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: parameters must be finite");
-    if (!(params[0] > 0.0)) return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: g must be > 0");
-    k[0] = params[0];
-    k[1] = params[1];
-    k[2] = params[2];
-  } else if (theory == SS_BABY_SKYRME) {
-    if (n_params < 2 || n_params > 3)
-      return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: Baby Skyrme takes {kappa, mu[, nu]}");
-    for (int i = 0; i < n_params; ++i)
-      if (!std::isfinite(params[i])) return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: parameters must be finite");
-    const double nu = n_params > 2 ? params[2] : 0.0;
-    k[0] = params[0] * params[0];
-    k[1] = params[1] * params[1];
-    k[2] = nu * nu;
-  } else {
-    return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: unknown theory");
-  }
+  // couplings, validated and packed by the same routine as ss_set_theory's
+  double k[NCOUP];
+  int C = 0;
+  const int rc = pack_couplings(theory, params, n_params, k, &C);
+  if (rc != SS_OK) return rc;
+  if (theory == SS_CHIRAL_MAGNET && k[10] > 0.0)
+    return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: demagnetisation needs a context (a Poisson solve)");
+  if (theory == SS_BEC && k[4] > 0.0)
+    return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: a fixed atom number needs a context (its multiplier)");
 
-  // set-up, once per device, with that device current: the device address of the
-  // scratch (the array's name is only a host-side stand-in)
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return noalloc_fail(SS_ERR_CUDA, std::string("ss_observables_noalloc: ") + cudaGetErrorString(e));
-  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return noalloc_fail(SS_ERR_ARG, "ss_observables_noalloc: device index too large");
+  // set-up, on every call, with the caller's device current: the device address of
+  // the scratch (the array's name is only a host-side stand-in). Looking it up each
+  // time keeps no address that a device reset could leave stale.
   void* base = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-      void* ptr = nullptr;
-      e = cudaGetSymbolAddress((void**)&ptr, g_noalloc_scratch);
-      if (e != cudaSuccess)
-        return noalloc_fail(SS_ERR_CUDA, std::string("ss_observables_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-      g_noalloc_ptr[dev] = ptr;
-    }
-    base = g_noalloc_ptr[dev];
-  }
+  cudaError_t e = cudaGetSymbolAddress(&base, g_noalloc_scratch);
+  if (e != cudaSuccess)
+    return noalloc_fail(SS_ERR_CUDA, std::string("ss_observables_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
 
   LaunchCtx L{};
   L.theory = theory == SS_ABELIAN_HIGGS ? TH_AH

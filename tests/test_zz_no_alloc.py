@@ -66,6 +66,29 @@ def test_noalloc_matches_ss_observables_on_two_calls_in_a_row(S):
             assert got[k] == pytest.approx(ref[k], rel=1e-12, abs=1e-12), (theory, k)
 
 
+def test_noalloc_plain_fp32_and_the_rules_of_ss_set_theory(S):
+    """A single-plane FP32 field passes its own precision code; parameter sets that
+    ss_set_theory rejects, and the two forms that need a context, are rejected."""
+    f = I.smooth_field(1, 61, 40, 0.2, 0.2, seed=903).astype(np.float32)
+    for _ in range(2):
+        got = noalloc(S, S.SS_ABELIAN_HIGGS, AH_PRM, f, 0.2, 0.2, S.SS_FP32_PLAIN)
+        ref = reference(S, S.SS_ABELIAN_HIGGS, AH_PRM, f, 0.2, 0.2, S.SS_FP32_PLAIN)
+        for k in KEYS:
+            assert got[k] == pytest.approx(ref[k], rel=1e-12, abs=1e-12), k
+    dev = torch.zeros((6, 16, 16), dtype=torch.float32, device="cuda")
+    out = torch.zeros(6, dtype=torch.float64, device="cuda")
+    bad = [
+        (S.SS_SID, (-1.0, -1.0, 1.0, 1.0, 3.0, 0.0, 0.1)),   # quartic unbounded below
+        (S.SS_SID, (-1.0, -1.0, 1.0, 1.0, 0.5, 0.0, 1.5)),   # |nu| >= 1
+        (S.SS_CHIRAL_MAGNET, (1.0, 1.0, 0.1, 0.6, 0.0, 0.5)),  # demagnetisation
+        (S.SS_BEC, (1.0, 0.5, 10.0, 100.0)),                  # fixed atom number
+    ]
+    for theory, params in bad:
+        with pytest.raises(S.SolitonError) as ei:
+            S.ss_observables_noalloc(theory, params, dev, 16, 16, 0.2, 0.2, S.SS_FP32, out)
+        assert ei.value.code == S.SS_ERR_ARG, (theory, params)
+
+
 def test_noalloc_rejects_grids_beyond_the_maximum(S):
     dummy = ctypes.c_void_p(1)  # never dereferenced: the size check comes first
     p = np.array(AH_PRM)
