@@ -143,7 +143,10 @@ typedef struct {
  * summed in the working precision, so with FP32 fields the count also picks up
  * rounding noise once the per-step decrease falls below it (near convergence). */
 typedef struct {
-  double energy;      /* E_h of the current field (FP64 accumulation)                  */
+  double energy;      /* E_h of the current field as the flow sums it. FP32 kernels   */
+                      /* sum it on the first field, every 16th step and the last     */
+                      /* field of a run; in between it is the previous E_h plus the  */
+                      /* exact change (energy_change). ss_observables: FP64.         */
   double grad_max;    /* dx dy max_I |G| of the current field: the convergence measure */
   long long steps;    /* steps taken since the fields were last set                    */
   long long arrests;  /* arrests (Eq. 4) since the fields were last set                */
@@ -247,8 +250,8 @@ int ss_step(ss_ctx* ctx, int n_steps, ss_status* out);
  * the host polls one small status record per chunk. With FP32 fields the flow's
  * own residual is FP32 arithmetic, so the verdict is the FP64 evaluation of the
  * stored field (value + remainder, as ss_observables): while that is not below
- * tol, the flow continues under a working threshold tightened by 0.7 each time,
- * within the same max_steps. Returns SS_OK if converged, SS_ERR_NOT_CONVERGED if
+ * tol, the flow takes further rounds of steps (1/64 of the steps taken so far, 8 to
+ * 512 per round) within the same max_steps, and is judged again. Returns SS_OK if converged, SS_ERR_NOT_CONVERGED if
  * max_steps was reached, SS_ERR_NONFINITE, or another error. out (may be NULL)
  * receives the final status in every case (its grad_max is the flow's own). */
 int ss_minimise(ss_ctx* ctx, double tol, long long max_steps, ss_status* out);

@@ -191,6 +191,7 @@ ProbDesc<R> make_desc(const Problem& p, DevState* st, FlowPartial* part) {
   d.ntx = p.ntx;
   d.ntiles = p.ntiles;
   d.tile0 = p.tile0;
+  d.vec = (sizeof(R) == 4 && p.nx % 4 == 0) ? 1 : 0;
   d.plane = (long long)p.plane;
   for (int i = 0; i < 2; ++i) {
     d.phi[i] = static_cast<R*>(p.phi[i]);
@@ -540,9 +541,16 @@ int ensure_chunk(ss_batch* b) {
 // chunk is a row of launches whose tiles all skip.
 // Under gradient descent each pass evaluates a field and then steps, so a run takes
 // max_steps + 1 passes, the last one evaluating the final field.
+int batch_steps(ss_batch* b, long long max_steps);
+
 int batch_run(ss_batch* b, double tol, long long max_steps) {
+  SS_CK(launch_set_run_all(b->st, b->n(), tol, max_steps, b->stream));
+  return batch_steps(b, max_steps);
+}
+
+// The run loop of batch_run, for run parameters already set in the flow records.
+int batch_steps(ss_batch* b, long long max_steps) {
   const int n = b->n();
-  SS_CK(launch_set_run_all(b->st, n, tol, max_steps, b->stream));
   long long passes = max_steps;
   if (b->method == METHOD_GD) passes += 1;
   else SS_CK(launch_pass(b->BL, 1, b->stream));  // heads of the current fields (skipped where done)
@@ -579,6 +587,77 @@ int batch_run(ss_batch* b, double tol, long long max_steps) {
       SS_CK(field_refresh(b));
       SS_CK(launch_pass(b->BL, 1, b->stream));
     }
+  }
+  return read_states(b);
+}
+
+int problem_observables(ss_batch* b, int i, ss_obs* out);
+
+// The convergence verdict after a run under threshold tol that started at step
+// start[i] of problem i and may take max_steps steps. FP64: the flow's own test. FP32
+// fields: the flow judged its residual in FP32 arithmetic, whose rounding noise near
+// 1e-6 is a sizeable fraction of it, so the verdict is the FP64 evaluation of the
+// stored field (value + remainder, as the observables): a problem the flow stopped as
+// converged whose FP64 residual is not below tol takes further rounds of steps (1/64
+// of the steps it took so far, 8 to 512) within its budget, and is judged again.
+// conv[i] receives the verdict; the flow records are read back (h_st) on return.
+int batch_verify(ss_batch* b, double tol, long long max_steps, const std::vector<long long>& start,
+                 std::vector<char>& conv) {
+  const int n = b->n();
+  conv.assign(n, 0);
+  int rc = read_states(b);
+  if (rc != SS_OK) return rc;
+  std::vector<char> pending(n, 0);
+  for (int i = 0; i < n; ++i) {
+    conv[i] = b->h_st[i].converged && !b->h_st[i].nonfinite;
+    pending[i] = b->prec != SS_FP64 && conv[i];
+  }
+  if (b->prec == SS_FP64) return SS_OK;
+  std::vector<double> g64(n, 0.0);
+  for (;;) {
+    for (int i = 0; i < n; ++i) {  // (each evaluation re-reads the flow records)
+      if (!pending[i]) continue;
+      ss_obs o{};
+      rc = problem_observables(b, i, &o);
+      if (rc != SS_OK) return rc;
+      g64[i] = o.grad_max;
+    }
+    bool more = false;
+    long long kmax = 0;
+    for (int i = 0; i < n; ++i) {
+      DevState& h = b->h_st[i];
+      if (!pending[i]) {
+        if (!conv[i] && !h.nonfinite) h.step_limit = h.steps;  // stays stopped
+        continue;
+      }
+      if (g64[i] < tol) {
+        conv[i] = 1;
+        pending[i] = 0;
+        h.converged = 1;
+        continue;
+      }
+      conv[i] = 0;
+      h.converged = 0;
+      const long long used = h.steps - start[i];
+      if (h.nonfinite || used >= max_steps) {
+        pending[i] = 0;
+        h.step_limit = h.steps;  // stopped: budget spent
+        continue;
+      }
+      long long k = used / 64;
+      k = k < 8 ? 8 : (k > 512 ? 512 : k);
+      if (k > max_steps - used) k = max_steps - used;
+      h.tol = -1.0;
+      h.step_limit = h.steps + k;
+      if (k > kmax) kmax = k;
+      more = true;
+    }
+    SS_CK(cudaMemcpyAsync(b->st, b->h_st, sizeof(DevState) * n, cudaMemcpyHostToDevice, b->stream));
+    if (!more) break;
+    rc = batch_steps(b, kmax);
+    if (rc != SS_OK) return rc;
+    rc = read_states(b);
+    if (rc != SS_OK) return rc;
   }
   return read_states(b);
 }
@@ -853,35 +932,14 @@ int ss_minimise(ss_ctx* c, double tol, long long max_steps, ss_status* out) {
   rc = batch_run(b, tol, max_steps);
   if (rc != SS_OK) return rc;
   const DevState& h = b->h_st[0];
-  // FP32 fields: the flow judged its residual in FP32 arithmetic, whose rounding noise
-  // is of the order of the tolerances in use. The verdict is the FP64 evaluation of
-  // the stored field (value + remainder); while it is not below tol, the flow goes on
-  // under a tightened working threshold, within the same step budget.
-  if (b->prec != SS_FP64 && h.converged && !h.nonfinite) {
-    double work_tol = tol;
-    bool verified = false;
-    for (int k = 0; k < 64 && h.converged && !h.nonfinite; ++k) {
-      ss_obs o{};
-      rc = problem_observables(b, 0, &o);
-      if (rc != SS_OK) return rc;
-      if (o.grad_max < tol) {
-        verified = true;
-        break;
-      }
-      const long long used = h.steps - start;
-      work_tol *= 0.7;
-      rc = batch_run(b, work_tol, max_steps > used ? max_steps - used : 0);
-      if (rc != SS_OK) return rc;
-    }
-    if (!verified && h.converged && !h.nonfinite) {
-      fill_status(h, out);
-      if (out) out->converged = 0;
-      return fail(SS_ERR_NOT_CONVERGED, "the FP64 residual of the FP32 field stayed above the tolerance");
-    }
-  }
+  std::vector<long long> first(1, start);
+  std::vector<char> conv;
+  rc = batch_verify(b, tol, max_steps, first, conv);
+  if (rc != SS_OK) return rc;
   fill_status(h, out);
+  if (out) out->converged = conv[0];
   if (h.nonfinite) return fail(SS_ERR_NONFINITE, "energy or force became non-finite; the flow stopped");
-  if (!h.converged) return fail(SS_ERR_NOT_CONVERGED, "max_steps reached before the tolerance");
+  if (!conv[0]) return fail(SS_ERR_NOT_CONVERGED, "max_steps reached before the tolerance");
   return SS_OK;
 }
 
@@ -1016,7 +1074,14 @@ int ss_batch_minimise(ss_batch* b, double tol, long long max_steps, ss_status* p
   if (!b) return fail(SS_ERR_ARG, "null batch");
   if (max_steps < 0) return fail(SS_ERR_ARG, "max_steps must be >= 0");
   if (!(tol >= 0.0)) return fail(SS_ERR_ARG, "tol must be >= 0");
-  int rc = batch_run(b, tol, max_steps);
+  int rc = read_states(b);
+  if (rc != SS_OK) return rc;
+  std::vector<long long> start(b->n());
+  for (int i = 0; i < b->n(); ++i) start[i] = b->h_st[i].steps;
+  rc = batch_run(b, tol, max_steps);
+  if (rc != SS_OK) return rc;
+  std::vector<char> conv;
+  rc = batch_verify(b, tol, max_steps, start, conv);
   if (rc != SS_OK) return rc;
   return batch_finish(b, per_item, true);
 }

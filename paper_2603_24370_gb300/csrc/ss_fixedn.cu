@@ -71,38 +71,20 @@ __device__ __forceinline__ void pair_block_sum(RPair<R>& a, RPair<R>& b, R* sm) 
   tile_reduce<R>(a, b, m, sm);
 }
 
-// Block partials -> the fixed-order totals of two sums (last block; thread 0 ends with
-// them). FP32 kernels: the partials hold float-float pairs exactly and one warp totals
-// them in FP64 pairs (a partial per block, so the slow FP64 pipe is busy for well
-// under a microsecond); FP64 kernels: a block tree of FP64 pairs.
+// Block partials -> the fixed-order totals of two sums (last block); the partials hold
+// the working type's pairs exactly, and are totalled as such (FP32: float-float pairs,
+// ~2^-47 relative; an FP64 tree would hold this GPU's slow FP64 pipe for tens of us).
 template <typename R>
 __device__ __forceinline__ void fn_total(const ObsPartial* part, double& ta, double& tb, R* sm) {
+  RPair<R> sa{R(0), R(0)}, sb{R(0), R(0)};
   const int tid = threadIdx.y * BX + threadIdx.x;
-  if constexpr (sizeof(R) == 4) {
-    ta = tb = 0.0;
-    if (tid < 32) {
-      DD sa{0.0, 0.0}, sb{0.0, 0.0};
-      for (int i = tid; i < (int)gridDim.x; i += 32) {
-        neumaier(sa, __ldcg(&part[i].es));
-        neumaier(sa, __ldcg(&part[i].ec));
-        neumaier(sb, __ldcg(&part[i].fs));
-        neumaier(sb, __ldcg(&part[i].fc));
-      }
-      sa = warp_sum(sa);
-      sb = warp_sum(sb);
-      ta = sa.s + sa.c;
-      tb = sb.s + sb.c;
-    }
-  } else {
-    RPair<R> sa{R(0), R(0)}, sb{R(0), R(0)};
-    for (int i = tid; i < (int)gridDim.x; i += NT) {
-      sa = pair_add(sa, RPair<R>{R(__ldcg(&part[i].es)), R(__ldcg(&part[i].ec))});
-      sb = pair_add(sb, RPair<R>{R(__ldcg(&part[i].fs)), R(__ldcg(&part[i].fc))});
-    }
-    pair_block_sum<R>(sa, sb, sm);
-    ta = (double)sa.s + (double)sa.c;
-    tb = (double)sb.s + (double)sb.c;
+  for (int i = tid; i < (int)gridDim.x; i += NT) {
+    sa = pair_add(sa, RPair<R>{R(__ldcg(&part[i].es)), R(__ldcg(&part[i].ec))});
+    sb = pair_add(sb, RPair<R>{R(__ldcg(&part[i].fs)), R(__ldcg(&part[i].fc))});
   }
+  pair_block_sum<R>(sa, sb, sm);
+  ta = (double)sa.s + (double)sa.c;
+  tb = (double)sb.s + (double)sb.c;
 }
 
 // Thread 0 writes the block's pairs as its partial.

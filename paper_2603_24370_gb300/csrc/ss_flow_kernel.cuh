@@ -76,6 +76,11 @@
 #ifndef SS_LU1
 #define SS_LU1 2
 #endif
+// FP32 pass 1 sums E_h itself every SS_E_EVERY steps (a power of two), and on the first
+// and last field of a run.
+#ifndef SS_E_EVERY
+#define SS_E_EVERY 16
+#endif
 #ifndef SS_LU2
 #define SS_LU2 3
 #endif
@@ -84,6 +89,23 @@
 #endif
 #ifndef SS_MINB1
 #define SS_MINB1 3
+#endif
+// Width (2 or 4 sites) of the vector units that stage interior tiles of FP32 grids
+// whose rows start on 16-byte boundaries: compensated storage, plain FP32.
+#ifndef SS_VW_LO
+#define SS_VW_LO 2
+#endif
+#ifndef SS_VW_PLAIN
+#define SS_VW_PLAIN 4
+#endif
+#ifndef SS_VW1_LO
+#define SS_VW1_LO SS_VW_LO
+#endif
+#ifndef SS_VW2_LO
+#define SS_VW2_LO SS_VW_LO
+#endif
+#ifndef SS_VW3_LO
+#define SS_VW3_LO SS_VW_LO
 #endif
 #ifndef SS_MINB2
 #define SS_MINB2 4
@@ -107,12 +129,18 @@ namespace ss {
 
 // Tile shape: TS = 0 (small) or 1 (large) selects the rows each thread walks,
 // FP32 2 or 4 (tiles of 32 x 16 or 32 x 32 sites), FP64 1 or 2 (32 x 8 or 32 x 16).
+// Shared rows: FP32 tiles keep 4 columns on each side (the stencils use 2), so that
+// every row starts on a 16-byte boundary and the tile can be staged in float4 units;
+// OX is the shared column of the tile's first site.
 template <typename R, int TS>
 struct FlowTile {
   static constexpr int RY = (sizeof(R) == 4 ? 2 : 1) << TS;  // rows per thread
   static constexpr int TX = 32, TY = BY * RY;
-  static constexpr int SX = TX + 4, SY = TY + 4, SXY = SX * SY;
+  static constexpr int OX = sizeof(R) == 4 ? 4 : 2;
+  static constexpr int SX = TX + 2 * OX, SY = TY + 4, SXY = SX * SY;
+  static constexpr int SW = TX + 4;  // staged sites per row (the tile and its halo)
 };
+
 
 
 // 1 / |n| for the unit-length projection: FP32 uses the hardware reciprocal square
@@ -159,6 +187,74 @@ __device__ __forceinline__ void normalise_split(const float* hi, float* t) {
 #pragma unroll
   for (int c = 0; c < 3; ++c) t[c] = t[c] + rho * (hi[c] + t[c]);
 }
+
+// Stage inputs of one site from its stored values: pass 1 Y_1 = phi, Y_2 = phi + dt/2 v
+// and delta = phi^n - phi^{n-1}; pass 2 Y_3, Y_4; pass 3 phi. With compensated storage
+// the small parts are formed first and added to the value once; unit vectors are
+// normalised (split form) at sites of the interior.
+template <int TH, typename R, int PASS, bool LO>
+__device__ __forceinline__ void stage_site(const R* pv, const R* lv, const R* vv, const R* k1v, const R* k2v,
+                                           const R* pp, const R* lp, bool inside, R hdt, R dt, R c3, R c4, R* ya,
+                                           R* yb, R* yd) {
+  constexpr int C = NComp<TH>::C;
+  if (PASS == 1) {
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      // delta = phi^n - phi^{n-1} (differences of neighbouring values: exact per part)
+      yd[c] = LO ? (pv[c] - pp[c]) + (lv[c] - lp[c]) : pv[c] - pp[c];
+      ya[c] = LO ? lv[c] : pv[c];
+      yb[c] = (LO ? lv[c] : pv[c]) + hdt * vv[c];
+    }
+    if (UnitVector<TH>::value && inside) {
+      if constexpr (LO) normalise_split(pv, yb);
+      else normalise<C>(yb);
+    }
+  } else if (PASS == 2) {
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const R base3 = hdt * vv[c] + c3 * k1v[c];
+      const R base4 = dt * vv[c] + c4 * k2v[c];
+      ya[c] = (LO ? lv[c] : pv[c]) + base3;
+      yb[c] = (LO ? lv[c] : pv[c]) + base4;
+    }
+    if (UnitVector<TH>::value && inside) {
+      if constexpr (LO) {
+        normalise_split(pv, ya);
+        normalise_split(pv, yb);
+      } else {
+        normalise<C>(ya);
+        normalise<C>(yb);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < C; ++c) ya[c] = LO ? lv[c] : pv[c];
+  }
+  if (LO) {  // stage inputs: value + small part, rounded once
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      ya[c] = pv[c] + ya[c];
+      if (PASS != 3) yb[c] = pv[c] + yb[c];
+    }
+  }
+}
+
+// Vector units of VW = 2 or 4 consecutive FP32 sites (8- or 16-byte loads and stores).
+template <int VW> struct VecOf;
+template <> struct VecOf<2> { using T = float2; };
+template <> struct VecOf<4> { using T = float4; };
+template <int VW>
+__device__ __forceinline__ typename VecOf<VW>::T ldv(const float* p) {
+  return *reinterpret_cast<const typename VecOf<VW>::T*>(p);
+}
+template <int VW>
+__device__ __forceinline__ void stv(float* p, const typename VecOf<VW>::T& v) {
+  *reinterpret_cast<typename VecOf<VW>::T*>(p) = v;
+}
+template <typename V>
+__device__ __forceinline__ float& vat(V& v, int j) { return (&v.x)[j]; }
+template <int VW>
+__device__ __forceinline__ typename VecOf<VW>::T vzero() { return typename VecOf<VW>::T{}; }
 
 // Sliding 5-row window over one component plane of the shared tile, for one
 // column. MIX keeps the x-stencil of all five rows for the mixed derivative.
@@ -319,6 +415,7 @@ struct TileCtx {
   int cur;       // ping-pong parity of the current field
   int arrest;    // pass 2: the current velocity counts as zero
   int has_prev;  // pass 1: the other buffer holds the previous field
+  int want_e;    // pass 1: sum E_h itself (else E_h = previous E_h + the exact change)
   int adv;       // pass 3: the step budget allows a new field
 };
 
@@ -350,6 +447,11 @@ __device__ __forceinline__ void load_tile_ctx(TileCtx<R>& tc, const ProbDesc<R>&
   tc.cur = (int)(steps & 1);
   tc.arrest = (PASS == 2) && (st->arrest != 0);
   tc.has_prev = (PASS == 1) && (steps > 0);
+  // FP32 pass 1 sums E_h itself on the first field, every SS_E_EVERY-th step and on
+  // the last field of a run; in between E_h = E_h(previous) + dE, the cancellation-free
+  // change it sums anyway for Eq. 4 (drift over SS_E_EVERY steps: a few roundings of dE)
+  tc.want_e = PASS != 1 || sizeof(R) == 8 || steps == 0 || (steps & (SS_E_EVERY - 1)) == 0 ||
+              steps >= st->step_limit;
   tc.adv = (PASS == 3) && (steps < st->step_limit);
 }
 
@@ -397,6 +499,7 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
     const int cur = tc.cur;
     const bool arrest = tc.arrest != 0;
     const bool has_prev = tc.has_prev != 0;
+    const bool want_e = tc.want_e != 0;
     const bool adv = tc.adv != 0;
     const int nx = D.nx, ny = D.ny;
     const size_t P = (size_t)D.plane;
@@ -417,18 +520,81 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
     const int lt = t - D.tile0;  // tile index within the problem
     const int x0 = (lt % D.ntx) * T::TX, y0 = (lt / D.ntx) * T::TY;
 
-    // ---- stage inputs over the tile and its halo, LU sites per iteration (the loads
-    // of all LU sites are issued before any is used: more bytes in flight per thread)
+    // ---- stage inputs over the tile and its halo
     constexpr int LU = PASS == 1 ? SS_LU1 : (PASS == 2 ? SS_LU2 : SS_LU3);
-    for (int base = tid; base < T::SXY; base += LU * NT) {
+    bool vec = false;  // float4 staging: every loaded site in bounds, every used site in I
+    if constexpr (sizeof(R) == 4) vec = D.vec && x0 >= 4 && x0 + T::TX + 4 <= nx && y0 >= 4 && y0 + T::TY + 4 <= ny;
+    if constexpr (sizeof(R) == 4) {
+      if (vec) {
+        // units of VW consecutive sites of one shared row (shared columns VW u ..,
+        // sites x0 - 4 + VW u ..): one VW-wide load per stored plane, one VW-wide store
+        // per staged plane; the outermost two columns of each side are staged but unused.
+        // Compensated storage loads twice the planes: narrower units keep them in registers.
+        constexpr int VW = LO ? (PASS == 1 ? SS_VW1_LO : (PASS == 2 ? SS_VW2_LO : SS_VW3_LO)) : SS_VW_PLAIN;
+        using V = typename VecOf<VW>::T;
+        constexpr int UW = T::SX / VW, NU = UW * T::SY;
+        for (int u = tid; u < NU; u += NT) {
+          const int ly = u / UW, ux = u - ly * UW;
+          const size_t s = (size_t)(y0 - 2 + ly) * nx + (size_t)(x0 - 4 + VW * ux);
+          const int so = ly * T::SX + VW * ux;
+          const V z = vzero<VW>();
+          V P4[C], L4[C], V4[C], A4[C], B4[C], Z4 = z;
+#pragma unroll
+          for (int c = 0; c < C; ++c) {
+            P4[c] = ldv<VW>(phi + c * P + s);
+            L4[c] = LO ? ldv<VW>(lo + c * P + s) : z;
+            V4[c] = (PASS != 3 && !arrest) ? ldv<VW>(vel + c * P + s) : z;
+            if (PASS == 1) {  // the previous field (A: value, B: remainder)
+              A4[c] = has_prev ? ldv<VW>(phi_prev + c * P + s) : P4[c];
+              B4[c] = (LO && has_prev) ? ldv<VW>(lo_prev + c * P + s) : L4[c];
+            } else if (PASS == 2) {  // k_v1, k_v2
+              A4[c] = ldv<VW>(kv1 + c * P + s);
+              B4[c] = arrest ? A4[c] : ldv<VW>(kv2 + c * P + s);
+            }
+          }
+          if (TH == TH_CMD) Z4 = ldv<VW>(psi + s);
+          V OA[C], OB[C], OD[C];
+#pragma unroll
+          for (int j = 0; j < VW; ++j) {
+            R pv[C], lv[C], vv[C], aa[C], bb[C], ya[C], yb[C], yd[C];
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+              pv[c] = vat(P4[c], j);
+              lv[c] = vat(L4[c], j);
+              vv[c] = vat(V4[c], j);
+              aa[c] = vat(A4[c], j);
+              bb[c] = vat(B4[c], j);
+            }
+            stage_site<TH, R, PASS, LO>(pv, lv, vv, aa, bb, aa, bb, true, hdt, dt, c3, c4, ya, yb, yd);
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+              vat(OA[c], j) = ya[c];
+              if (PASS != 3) vat(OB[c], j) = yb[c];
+              if (PASS == 1) vat(OD[c], j) = yd[c];
+            }
+          }
+#pragma unroll
+          for (int c = 0; c < C; ++c) {
+            stv<VW>(setA + c * T::SXY + so, OA[c]);
+            if (PASS != 3) stv<VW>(setB + c * T::SXY + so, OB[c]);
+            if (PASS == 1) stv<VW>(setD + c * T::SXY + so, OD[c]);
+          }
+          if (TH == TH_CMD) stv<VW>(setP + so, Z4);
+        }
+      }
+    }
+    // scalar staging (grid edges, rows not 16-byte aligned, FP64): LU sites per
+    // iteration, the loads of all LU sites issued before any is used
+    constexpr int SWY = T::SW * T::SY;
+    for (int base = tid; !vec && base < SWY; base += LU * NT) {
       R pv[LU][C], lv[LU][C], vv[LU][C], k1v[LU][C], k2v[LU][C], pp[LU][C], lp[LU][C], pz[LU];
       bool in[LU], inside[LU];
 #pragma unroll
       for (int u = 0; u < LU; ++u) {  // all global loads of the sites first
         const int idx = base + u * NT;
-        const int ly = idx / T::SX, lx = idx - ly * T::SX;
+        const int ly = idx / T::SW, lx = idx - ly * T::SW;
         const int gx = x0 + lx - 2, gy = y0 + ly - 2;
-        in[u] = idx < T::SXY && gx >= 0 && gx < nx && gy >= 0 && gy < ny;
+        in[u] = idx < SWY && gx >= 0 && gx < nx && gy >= 0 && gy < ny;
         inside[u] = in[u] && gx >= 2 && gx < nx - 2 && gy >= 2 && gy < ny - 2;
         const size_t s = in[u] ? (size_t)gy * nx + gx : 0;
         if (TH == TH_CMD) pz[u] = in[u] ? psi[s] : R(0);
@@ -449,61 +615,25 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
 #pragma unroll
       for (int u = 0; u < LU; ++u) {
         const int idx = base + u * NT;
-        if (idx >= T::SXY) break;
+        if (idx >= SWY) break;
+        const int ly = idx / T::SW, lx = idx - ly * T::SW;
+        const int sh = ly * T::SX + lx + (T::OX - 2);  // shared index of the site
         R ya[C], yb[C], yd[C];
-        if (PASS == 1) {
-#pragma unroll
-          for (int c = 0; c < C; ++c) {
-            // delta = phi^n - phi^{n-1} (differences of neighbouring values: exact per part)
-            yd[c] = LO ? (pv[u][c] - pp[u][c]) + (lv[u][c] - lp[u][c]) : pv[u][c] - pp[u][c];
-            ya[c] = LO ? lv[u][c] : pv[u][c];
-            yb[c] = (LO ? lv[u][c] : pv[u][c]) + hdt * vv[u][c];
-          }
-          if (UnitVector<TH>::value && inside[u]) {
-            if constexpr (LO) normalise_split(pv[u], yb);
-            else normalise<C>(yb);
-          }
-        } else if (PASS == 2) {
-#pragma unroll
-          for (int c = 0; c < C; ++c) {
-            const R base3 = hdt * vv[u][c] + c3 * k1v[u][c];
-            const R base4 = dt * vv[u][c] + c4 * k2v[u][c];
-            ya[c] = (LO ? lv[u][c] : pv[u][c]) + base3;
-            yb[c] = (LO ? lv[u][c] : pv[u][c]) + base4;
-          }
-          if (UnitVector<TH>::value && inside[u]) {
-            if constexpr (LO) {
-              normalise_split(pv[u], ya);
-              normalise_split(pv[u], yb);
-            } else {
-              normalise<C>(ya);
-              normalise<C>(yb);
-            }
-          }
-        } else {
-#pragma unroll
-          for (int c = 0; c < C; ++c) ya[c] = LO ? lv[u][c] : pv[u][c];
-        }
-        if (LO) {  // stage inputs: value + small part, rounded once
-#pragma unroll
-          for (int c = 0; c < C; ++c) {
-            ya[c] = pv[u][c] + ya[c];
-            if (PASS != 3) yb[c] = pv[u][c] + yb[c];
-          }
-        }
+        stage_site<TH, R, PASS, LO>(pv[u], lv[u], vv[u], k1v[u], k2v[u], pp[u], lp[u], inside[u], hdt, dt, c3, c4,
+                                    ya, yb, yd);
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-          setA[c * T::SXY + idx] = ya[c];
-          if (PASS != 3) setB[c * T::SXY + idx] = yb[c];
-          if (PASS == 1) setD[c * T::SXY + idx] = has_prev ? yd[c] : R(0);
+          setA[c * T::SXY + sh] = ya[c];
+          if (PASS != 3) setB[c * T::SXY + sh] = yb[c];
+          if (PASS == 1) setD[c * T::SXY + sh] = has_prev ? yd[c] : R(0);
         }
-        if (TH == TH_CMD) setP[idx] = pz[u];
+        if (TH == TH_CMD) setP[sh] = pz[u];
       }
     }
     __syncthreads();
 
     // ---- column walk: RY rows of column threadIdx.x
-    const int sx = threadIdx.x + 2, sy0 = threadIdx.y * RY + 2;
+    const int sx = threadIdx.x + T::OX, sy0 = threadIdx.y * RY + 2;
     const int gx = x0 + threadIdx.x, gyb = y0 + threadIdx.y * RY;
     const bool colok = gx >= 2 && gx < nx - 2;
     // site position, origin at the grid centre (only the BEC's trap and rotation use it)
@@ -541,10 +671,12 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
               kv1[c * P + s] = -G[c];
               gmr = absmax(gmr, G[c]);
             }
-            const R e = density_at<TH, R>(kc, v, fx, fy, TH == TH_CMD ? ps : q0, q1);
-            const R t1 = es + e;
-            ec += (fabs(es) >= fabs(e)) ? (es - t1) + e : (e - t1) + es;
-            es = t1;
+            if (want_e) {
+              const R e = density_at<TH, R>(kc, v, fx, fy, TH == TH_CMD ? ps : q0, q1);
+              const R t1 = es + e;
+              ec += (fabs(es) >= fabs(e)) ? (es - t1) + e : (e - t1) + es;
+              es = t1;
+            }
           }
           if (has_prev) {
             R dd[C], dxv[C], dyv[C];
@@ -691,27 +823,22 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
         __threadfence();
         double tot[2] = {0.0, 0.0}, mtot = 0.0;  // the problem's sum of e, sum of e(new) - e(previous), max |G|
         if constexpr (sizeof(R) == 4) {
-          // The partials hold float-float pairs exactly. One warp totals them in FP64
-          // pairs (Neumaier per lane, then a fixed warp tree): a few hundred slots, so
-          // this GPU's slow FP64 pipe is busy for well under a microsecond.
-          if (tid < 32) {
-            DD acc{0.0, 0.0}, dacc{0.0, 0.0};
-            R mm = R(0);
-            for (int i = tid; i < nslots; i += 32) {
-              const FlowPartial* q = d.part + i;
-              neumaier(acc, __ldcg(&q->es));
-              neumaier(acc, __ldcg(&q->ec));
-              neumaier(dacc, __ldcg(&q->ds));
-              neumaier(dacc, __ldcg(&q->dc));
-              mm = rmax(mm, R(__ldcg(&q->m)));
-            }
-            acc = warp_sum(acc);
-            dacc = warp_sum(dacc);
-            for (int off = 16; off > 0; off >>= 1) mm = rmax(mm, __shfl_down_sync(0xffffffffu, mm, off));
-            tot[0] = acc.s + acc.c;
-            tot[1] = dacc.s + dacc.c;
-            mtot = (double)mm;
+          // The partials hold float-float pairs exactly; the block totals them as
+          // float-float pairs (TwoSum tree, ~2^-47 relative: far below the FP32
+          // per-site rounding). An FP64 total costs this GPU 25-40 us per launch: its
+          // FP64 pipe runs at a small fraction of the FP32 rate.
+          RPair<R> acc{R(0), R(0)}, dacc{R(0), R(0)};
+          R mm = R(0);
+          for (int i = tid; i < nslots; i += NT) {
+            const FlowPartial* q = d.part + i;
+            acc = pair_add(acc, RPair<R>{R(__ldcg(&q->es)), R(__ldcg(&q->ec))});
+            dacc = pair_add(dacc, RPair<R>{R(__ldcg(&q->ds)), R(__ldcg(&q->dc))});
+            mm = rmax(mm, R(__ldcg(&q->m)));
           }
+          tile_reduce<R>(acc, dacc, mm, sred);
+          tot[0] = (double)acc.s + (double)acc.c;
+          tot[1] = (double)dacc.s + (double)dacc.c;
+          mtot = (double)mm;
         } else {
           DD acc{0.0, 0.0}, dacc{0.0, 0.0};
           double mm = 0.0;
@@ -730,8 +857,8 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
         }
         if (tid == 0 && PASS == 1) {
           DevState* st = d.st;
-          const double E = d.area * tot[0];
           const double dE = d.area * tot[1];
+          const double E = want_e ? d.area * tot[0] : st->E_last + dE;
           const double g = d.area * mtot;
           // Eq. 4, strict: E_h(phi^n) > E_h(phi^{n-1}); no previous field (E_last = +inf): no arrest
           const int arr = has_prev ? (dE > 0.0 ? 1 : 0) : (E > st->E_last ? 1 : 0);

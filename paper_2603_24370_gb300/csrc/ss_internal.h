@@ -42,7 +42,8 @@ template <typename R>
 struct ProbDesc {
   int nx, ny;
   int ntx, ntiles;  // tiles along x, tiles in total
-  int tile0, pad;   // index of the problem's first tile in the batch
+  int tile0;        // index of the problem's first tile in the batch
+  int vec;          // FP32 rows start on 16-byte boundaries (nx % 4 == 0; every plane is 256-byte aligned)
   long long plane;  // nx * ny
   R* phi[2];        // ping-pong field buffers [C][ny][nx] (value part when compensated)
   R* lo[2];         // compensated FP32: remainder planes (else null)
