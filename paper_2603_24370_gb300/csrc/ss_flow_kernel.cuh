@@ -62,6 +62,7 @@
 // component. Blocks stride over the batch's tiles; the grid is occupancy x SMs.
 #pragma once
 #include "ss_internal.h"
+#include "ss_pack.cuh"
 
 // Launch-shape knobs of the three passes: sites staged per iteration of the tile
 // loading loop (their loads are all issued before any is used), and the resident
@@ -256,6 +257,17 @@ __device__ __forceinline__ float& vat(V& v, int j) { return (&v.x)[j]; }
 template <int VW>
 __device__ __forceinline__ typename VecOf<VW>::T vzero() { return typename VecOf<VW>::T{}; }
 
+// Spacing factors and couplings broadcast to both lanes of a packed stage pair.
+__device__ __forceinline__ Spacing<F2> bcast(const Spacing<float>& h) {
+  return Spacing<F2>{F2(h.i12dx), F2(h.i12dy), F2(h.i12dx2), F2(h.i12dy2), F2(h.i144dxdy)};
+}
+__device__ __forceinline__ Couplings<F2> bcast(const Couplings<float>& k) {
+  Couplings<F2> o;
+#pragma unroll
+  for (int i = 0; i < NCOUP; ++i) o.c[i] = F2(k.c[i]);
+  return o;
+}
+
 // Sliding 5-row window over one component plane of the shared tile, for one
 // column. MIX keeps the x-stencil of all five rows for the mixed derivative.
 template <typename R, bool MIX>
@@ -318,7 +330,7 @@ struct NeedsMix {
   static constexpr bool value = TH == TH_BS || (TH == TH_AH && c >= 2) || (TH == TH_SID && c >= 4);
 };
 
-template <int TH, typename R, int SXY_>
+template <int TH, typename R, int SXY_, typename RP = R>
 struct StageWin {
   static constexpr int C = NComp<TH>::C;
   static constexpr int SXY = SXY_;
@@ -330,8 +342,8 @@ struct StageWin {
   Win<R, NeedsMix<TH, 5>::value> w5;
   // chiral magnet with demagnetisation: the magnetostatic potential's tile, walked with
   // the stage input (pbase must be set before the first enter)
-  Win<R, false> wp;
-  const R* pbase = nullptr;
+  Win<RP, false> wp;
+  const RP* pbase = nullptr;
 
   __device__ __forceinline__ void enter(const R* tiles, int off, int slot) {
     if (TH == TH_CMD) wp.enter(pbase + off, slot);
@@ -361,8 +373,8 @@ struct StageWin {
     if (C > 5) w5.template derivs<true>(tiles + 5 * SXY + off, h, v[5], fx[5], fy[5], fxx[5], fyy[5], fxy[5]);
   }
   // the potential and its Eq. 1 gradient at the window's centre row
-  __device__ __forceinline__ void psi_at(int off, const Spacing<R>& h, R& p, R& px, R& py) const {
-    R u0, u1, u2;
+  __device__ __forceinline__ void psi_at(int off, const Spacing<RP>& h, RP& p, RP& px, RP& py) const {
+    RP u0, u1, u2;
     wp.template derivs<false>(pbase + off, h, p, px, py, u0, u1, u2);
   }
 };
@@ -394,6 +406,51 @@ template <int TH, typename R>
 __device__ __forceinline__ void force_at(const Couplings<R>& k, const R* v, const R* fx, const R* fy, const R* fxx,
                                          const R* fyy, const R* fxy, R* G, R x = R(0), R y = R(0)) {
   force_of<TH, R>(k, v, fx, fy, fxx, fyy, fxy, G, x, y);
+}
+
+// The RK4 combination at interior site s: phi' = phi + dt v + dt^2/6 (k1 + k2 + k3),
+// the increment joining the stored remainder with compensated storage, and
+// v' = v + dt/6 (k1 + 2 k2 + 2 k3 + k4); unit vectors are normalised (split form) and
+// v' tangent-projected. Under a pending arrest v counts as zero and k2 as k1.
+template <int TH, typename R, bool LO>
+__device__ __forceinline__ void combine_site(const R* __restrict__ phi, const R* __restrict__ lo,
+                                             const R* __restrict__ vel, const R* __restrict__ kv1,
+                                             const R* __restrict__ kv2, R* __restrict__ phi_out,
+                                             R* __restrict__ lo_out, R* __restrict__ v_out, size_t P, size_t s,
+                                             bool arrest, R dt, R w6, R u6, const R* k3, const R* k4) {
+  constexpr int C = NComp<TH>::C;
+  R p0[C], q[C], vn[C];
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    p0[c] = phi[c * P + s];
+    const R v0 = arrest ? R(0) : vel[c * P + s];
+    const R k1 = kv1[c * P + s];
+    const R k2 = arrest ? k1 : kv2[c * P + s];
+    const R inc = dt * v0 + w6 * (k1 + k2 + k3[c]);
+    q[c] = LO ? lo[c * P + s] + inc : p0[c] + inc;
+    vn[c] = v0 + u6 * (k1 + R(2) * (k2 + k3[c]) + k4[c]);
+  }
+  R pn[C], ln[C];
+  if constexpr (LO) {
+    if (UnitVector<TH>::value) normalise_split(p0, q);
+#pragma unroll
+    for (int c = 0; c < C; ++c) two_sum_f(p0[c], q[c], pn[c], ln[c]);  // hi' = fl(hi + small), lo' = rest
+  } else {
+#pragma unroll
+    for (int c = 0; c < C; ++c) pn[c] = q[c];
+    if (UnitVector<TH>::value) normalise<C>(pn);
+  }
+  if (UnitVector<TH>::value) {
+    const R vp = vn[0] * pn[0] + vn[1] * pn[1] + vn[2] * pn[2];
+#pragma unroll
+    for (int c = 0; c < C; ++c) vn[c] -= vp * pn[c];
+  }
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    phi_out[c * P + s] = pn[c];
+    if (LO) lo_out[c * P + s] = ln[c];
+    v_out[c * P + s] = vn[c];
+  }
 }
 
 // Running maximum of |g| for a >= 0: on non-negative values the IEEE bit patterns
@@ -472,6 +529,9 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
   using T = FlowTile<R, TS>;
   constexpr int C = NComp<TH>::C;
   constexpr int RY = T::RY;
+  // FP32 flow passes evaluate their two stage inputs as packed pairs (ss_pack.cuh):
+  // shared [C][SXY] planes of (Y_a, Y_b), one walk for both stages
+  constexpr bool PK = sizeof(R) == 4 && PASS != 3;
   constexpr int PS = C * T::SXY;  // values per tile set
   extern __shared__ __align__(16) unsigned char smraw[];
   R* sm = reinterpret_cast<R*>(smraw);  // pass 1: [Y1 | Y2 | delta], pass 2: [Y3 | Y4], pass 3: [phi], (+ psi)
@@ -575,8 +635,15 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
           }
 #pragma unroll
           for (int c = 0; c < C; ++c) {
-            stv<VW>(setA + c * T::SXY + so, OA[c]);
-            if (PASS != 3) stv<VW>(setB + c * T::SXY + so, OB[c]);
+            if constexpr (PK) {  // interleaved (Y_a, Y_b) pairs
+              float* ab = setA + 2 * (c * T::SXY + so);
+#pragma unroll
+              for (int j = 0; j < VW; j += 2)
+                stv<4>(ab + 2 * j, make_float4(vat(OA[c], j), vat(OB[c], j), vat(OA[c], j + 1), vat(OB[c], j + 1)));
+            } else {
+              stv<VW>(setA + c * T::SXY + so, OA[c]);
+              if (PASS != 3) stv<VW>(setB + c * T::SXY + so, OB[c]);
+            }
             if (PASS == 1) stv<VW>(setD + c * T::SXY + so, OD[c]);
           }
           if (TH == TH_CMD) stv<VW>(setP + so, Z4);
@@ -623,8 +690,13 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
                                     ya, yb, yd);
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-          setA[c * T::SXY + sh] = ya[c];
-          if (PASS != 3) setB[c * T::SXY + sh] = yb[c];
+          if constexpr (PK) {
+            setA[2 * (c * T::SXY + sh)] = ya[c];
+            setA[2 * (c * T::SXY + sh) + 1] = yb[c];
+          } else {
+            setA[c * T::SXY + sh] = ya[c];
+            if (PASS != 3) setB[c * T::SXY + sh] = yb[c];
+          }
           if (PASS == 1) setD[c * T::SXY + sh] = has_prev ? yd[c] : R(0);
         }
         if (TH == TH_CMD) setP[sh] = pz[u];
@@ -643,6 +715,76 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
 
     if (PASS != 2) {
       if (PASS == 1) {
+      if constexpr (PK) {
+        // stages 1 and 2 in one walk over the pairs (Y_1, Y_2): k_v1, k_v2; at Y_1
+        // also e, max|G| and e(phi^n) - e(phi^{n-1})
+        const F2* ab = reinterpret_cast<const F2*>(setA);
+        const Spacing<F2> h2 = bcast(h);
+        const Couplings<F2> k2c = bcast(kc);
+        StageWin<TH, F2, T::SXY, R> W;
+        W.pbase = setP;
+        DiffWin<TH, R, T::SXY> Dw;
+#pragma unroll
+        for (int s = 0; s < 5; ++s) {
+          const int off = (sy0 - 2 + s) * T::SX + sx;
+          W.enter(ab, off, s);
+          if (has_prev) Dw.enter(setD, off, s);
+        }
+#pragma unroll
+        for (int r = 0; r < RY; ++r) {
+          const int off = (sy0 + r) * T::SX + sx;
+          const bool ok = colok && gyb + r >= 2 && gyb + r < ny - 2;
+          F2 v[C], fx[C], fy[C], fxx[C], fyy[C], fxy[C], G[C];
+          W.derivs(ab, off, h2, v, fx, fy, fxx, fyy, fxy);
+          // site extras: the BEC's position; with demagnetisation psi and its gradient
+          R q0 = xs, q1 = ypos(r), ps = R(0);
+          if (TH == TH_CMD) W.psi_at(off, h, ps, q0, q1);
+          force_at<TH, F2>(k2c, v, fx, fy, fxx, fyy, fxy, G, F2(q0), F2(q1));
+          R va[C], fxa[C], fya[C];  // stage 1: the field and its first derivatives
+#pragma unroll
+          for (int c = 0; c < C; ++c) {
+            va[c] = v[c].v.x;
+            fxa[c] = fx[c].v.x;
+            fya[c] = fy[c].v.x;
+          }
+          if (ok) {
+            const size_t s = (size_t)(gyb + r) * nx + gx;
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+              kv1[c * P + s] = -G[c].v.x;
+              kv2[c * P + s] = -G[c].v.y;
+              gmr = absmax(gmr, G[c].v.x);
+            }
+            if (want_e) {
+              const R e = density_at<TH, R>(kc, va, fxa, fya, TH == TH_CMD ? ps : q0, q1);
+              const R t1 = es + e;
+              ec += (fabs(es) >= fabs(e)) ? (es - t1) + e : (e - t1) + es;
+              es = t1;
+            }
+          }
+          if (has_prev) {
+            R dd[C], dxv[C], dyv[C];
+            Dw.derivs(setD, off, h, dd, dxv, dyv);
+            if (ok) {
+              const R de = delta_density_at<TH, R>(
+                  kc, va, fxa, fya, dd, dxv, dyv, TH == TH_CMD ? ps : q0,
+                  TH == TH_CMD ? ps - psi_prev[(size_t)(gyb + r) * nx + gx] : q1);
+              const R t2 = ds + de;
+              dc += (fabs(ds) >= fabs(de)) ? (ds - t2) + de : (de - t2) + ds;
+              ds = t2;
+            }
+          }
+          if (r + 1 < RY) {
+            const int noff = (sy0 + r + 3) * T::SX + sx;
+            W.shift();
+            W.enter(ab, noff, 4);
+            if (has_prev) {
+              Dw.shift();
+              Dw.enter(setD, noff, 4);
+            }
+          }
+        }
+      } else {
       // stage 1 at Y_1 = phi: k_v1, e, max|G|, and e(phi^n) - e(phi^{n-1})
       {
         StageWin<TH, R, T::SXY> W;
@@ -726,6 +868,7 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
             W.enter(setB, (sy0 + r + 3) * T::SX + sx, 4);
           }
         }
+      }
       }
       } else {
       // gradient descent at phi: -G into k_v1, e, max|G|, and phi - dtau G
@@ -896,6 +1039,45 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
         }
       }
     } else {
+      if constexpr (PK) {
+        // stages 3 and 4 in one walk over the pairs (Y_3, Y_4), then the RK4
+        // combination at each site
+        const F2* ab = reinterpret_cast<const F2*>(setA);
+        const Spacing<F2> h2 = bcast(h);
+        const Couplings<F2> k2c = bcast(kc);
+        StageWin<TH, F2, T::SXY, R> W;
+        W.pbase = setP;
+#pragma unroll
+        for (int s = 0; s < 5; ++s) W.enter(ab, (sy0 - 2 + s) * T::SX + sx, s);
+        const R w6 = dt * dt / R(6), u6 = dt / R(6);
+        R* __restrict__ phi_out = D.phi[cur ^ 1];
+        R* __restrict__ lo_out = D.lo[cur ^ 1];
+        R* __restrict__ v_out = D.v[cur ^ 1];
+#pragma unroll
+        for (int r = 0; r < RY; ++r) {
+          const int off = (sy0 + r) * T::SX + sx;
+          F2 v[C], fx[C], fy[C], fxx[C], fyy[C], fxy[C], G[C];
+          W.derivs(ab, off, h2, v, fx, fy, fxx, fyy, fxy);
+          // site extras: the BEC's position; with demagnetisation psi and its gradient
+          R q0 = xs, q1 = ypos(r), ps = R(0);
+          if (TH == TH_CMD) W.psi_at(off, h, ps, q0, q1);
+          force_at<TH, F2>(k2c, v, fx, fy, fxx, fyy, fxy, G, F2(q0), F2(q1));
+          if (colok && gyb + r >= 2 && gyb + r < ny - 2) {
+            R k3[C], k4[C];
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+              k3[c] = -G[c].v.x;
+              k4[c] = -G[c].v.y;
+            }
+            combine_site<TH, R, LO>(phi, lo, vel, kv1, kv2, phi_out, lo_out, v_out, P, (size_t)(gyb + r) * nx + gx,
+                                    arrest, dt, w6, u6, k3, k4);
+          }
+          if (r + 1 < RY) {
+            W.shift();
+            W.enter(ab, (sy0 + r + 3) * T::SX + sx, 4);
+          }
+        }
+      } else {
       // stage 3 at Y_3: k_v3 kept in registers
       R k3[RY][C];
       {
@@ -940,47 +1122,18 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
           if (TH == TH_CMD) W.psi_at(off, h, ps, q0, q1);
           force_at<TH, R>(kc, v, fx, fy, fxx, fyy, fxy, G, q0, q1);
           if (colok && gyb + r >= 2 && gyb + r < ny - 2) {
-            const size_t s = (size_t)(gyb + r) * nx + gx;
-            R p0[C], q[C], vn[C];
+            R k4[C];
 #pragma unroll
-            for (int c = 0; c < C; ++c) {
-              p0[c] = phi[c * P + s];
-              const R v0 = arrest ? R(0) : vel[c * P + s];
-              const R k1 = kv1[c * P + s];
-              const R k2 = arrest ? k1 : kv2[c * P + s];
-              const R k4 = -G[c];
-              // increment of phi; with compensated storage it joins the stored remainder
-              const R inc = dt * v0 + w6 * (k1 + k2 + k3[r][c]);
-              q[c] = LO ? lo[c * P + s] + inc : p0[c] + inc;
-              vn[c] = v0 + u6 * (k1 + R(2) * (k2 + k3[r][c]) + k4);
-            }
-            R pn[C], ln[C];
-            if constexpr (LO) {
-              if (UnitVector<TH>::value) normalise_split(p0, q);
-#pragma unroll
-              for (int c = 0; c < C; ++c) two_sum_f(p0[c], q[c], pn[c], ln[c]);  // hi' = fl(hi + small), lo' = rest
-            } else {
-#pragma unroll
-              for (int c = 0; c < C; ++c) pn[c] = q[c];
-              if (UnitVector<TH>::value) normalise<C>(pn);
-            }
-            if (UnitVector<TH>::value) {
-              const R vp = vn[0] * pn[0] + vn[1] * pn[1] + vn[2] * pn[2];
-#pragma unroll
-              for (int c = 0; c < C; ++c) vn[c] -= vp * pn[c];
-            }
-#pragma unroll
-            for (int c = 0; c < C; ++c) {
-              phi_out[c * P + s] = pn[c];
-              if (LO) lo_out[c * P + s] = ln[c];
-              v_out[c * P + s] = vn[c];
-            }
+            for (int c = 0; c < C; ++c) k4[c] = -G[c];
+            combine_site<TH, R, LO>(phi, lo, vel, kv1, kv2, phi_out, lo_out, v_out, P, (size_t)(gyb + r) * nx + gx,
+                                    arrest, dt, w6, u6, k3[r], k4);
           }
           if (r + 1 < RY) {
             W.shift();
             W.enter(setB, (sy0 + r + 3) * T::SX + sx, 4);
           }
         }
+      }
       }
       // The step count selects the ping-pong buffers and gates every tile of this
       // problem, so it advances only when the problem's last tile has arrived (its
