@@ -75,10 +75,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if errors:
         raise RuntimeError("nvcc failed:\n" + "\n".join(errors))
     tmp = LIB + ".tmp"
-    cuda_lib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(cc))), "lib64")
-    # cuFFT (the demagnetisation's sine transforms), found at run time next to the toolkit
-    link = ["-L" + cuda_lib, "-lcufft", "-Xlinker", "-rpath=" + cuda_lib]
-    subprocess.run([cc, *ARCH, "-shared", "-Xcompiler", "-fPIC", *objs, *link, "-o", tmp], check=True)
+    subprocess.run([cc, *ARCH, "-shared", "-Xcompiler", "-fPIC", *objs, "-o", tmp], check=True)
     os.replace(tmp, LIB)
     with open(STAMP, "w") as fh:
         fh.write(platform.machine())

@@ -12,16 +12,22 @@
 //   lambda_kl = -(2 - 2 cos(pi k / (Nx + 1))) / dx^2 - (2 - 2 cos(pi l / (Ny + 1))) / dy^2,
 // and DST-I is its own inverse up to 2 / (N + 1) per direction.
 //
-// A DST-I of length N is the imaginary part of a real FFT of the odd extension
-// (0, s_1 .. s_N, 0, -s_N .. -s_1) of length M = 2 (N + 1): X_k = -2 i DST_k. The solve
-// is four batched real FFTs (cuFFT, a plain library transform): along x for every row,
-// along y for every column (after a tiled transpose), the division by lambda, and the
-// same two transforms back. The kernels around them build the extensions, take the
-// imaginary parts, transpose in 32 x 32 shared-memory tiles and scatter psi into the
-// field-sized plane of the current ping-pong parity (read on the device from the flow
-// record, so the solve can sit inside a captured step graph).
-#include <cufft.h>
-
+// The transforms are this file's own. A DST-I of length N is -Im/2 of the DFT of the
+// odd extension y = (0, s_1 .. s_N, 0, -s_N .. -s_1) of length 2L, L = N + 1; that real
+// DFT is one complex DFT of length L of z_n = y_2n + i y_2n+1, unpacked as
+//   Y_k = E_k + e^{-i pi k / L} O_k,  E_k = (Z_k + conj Z_{L-k}) / 2,  O_k = (Z_k - conj Z_{L-k}) / 2i.
+// The complex DFT is a Stockham autosort FFT (radix 8, 4, 2, 3, 5, 7 stages, L being
+// 7-smooth) held in shared memory: one thread block transforms one line, reading it
+// once from global memory and writing it once. The solve is three line kernels and two
+// tiled transposes:
+//   rows:    rho (formed from the field on the fly) -> DST along x           -> T1 [Ny][Nx]
+//   T1 -> T2 [Nx][Ny] (transpose)
+//   columns: DST along y, division by lambda, DST along y again (in place)    -> T2
+//   T2 -> T1 (transpose)
+//   rows:    DST along x, the normalisation, psi on I into the current plane
+// Twiddles are tabulated once in FP64 and rounded to the working type. The field's
+// ping-pong parity is read on the device from the flow record, so the solve can sit
+// inside a captured step graph.
 #include <cmath>
 #include <new>
 #include <vector>
@@ -30,206 +36,444 @@
 
 namespace ss {
 
+namespace {
+
+constexpr int DST_THREADS = 256;
+constexpr int TW_FINE = 64;  // twiddles as coarse x fine factors: e^{-2 pi i t / L} = C[t / 64] F[t % 64]
+constexpr int DST_MAX_STAGES = 24;
+
 template <typename R>
-struct FftOf;
-template <>
-struct FftOf<float> {
-  using C = cufftComplex;
-  static constexpr cufftType type = CUFFT_R2C;
-  static cufftResult exec(cufftHandle p, float* in, C* out) { return cufftExecR2C(p, in, out); }
+struct Cx {
+  R x, y;
 };
-template <>
-struct FftOf<double> {
-  using C = cufftDoubleComplex;
-  static constexpr cufftType type = CUFFT_D2Z;
-  static cufftResult exec(cufftHandle p, double* in, C* out) { return cufftExecD2Z(p, in, out); }
+template <typename R>
+__device__ __forceinline__ Cx<R> cmul(Cx<R> a, Cx<R> b) {
+  return Cx<R>{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <typename R>
+__device__ __forceinline__ Cx<R> cadd(Cx<R> a, Cx<R> b) { return Cx<R>{a.x + b.x, a.y + b.y}; }
+template <typename R>
+__device__ __forceinline__ Cx<R> csub(Cx<R> a, Cx<R> b) { return Cx<R>{a.x - b.x, a.y - b.y}; }
+
+// One line transform: radices of its Stockham stages, and its tables.
+template <typename R>
+struct LinePlan {
+  int L;                            // complex DFT length (= N + 1)
+  int nst;                          // stages
+  int rad[DST_MAX_STAGES];          // radix of each stage (product = L)
+  unsigned magic[DST_MAX_STAGES];   // ceil(2^32 / Ns) of each stage (0 when Ns = 1)
+  int ncoarse;                      // ceil(L / 64)
+  const Cx<R>* tw;                  // global: C[h] = e^{-2 pi i 64 h / L} (ncoarse), then F[l] = e^{-2 pi i l / L} (64)
+  const Cx<R>* pw;                  // pw[k] = e^{-i pi k / L}, k <= L
 };
+
+// The twiddle table of a line, staged in shared memory once per block.
+template <typename R>
+struct Tw {
+  const Cx<R>* c;
+  const Cx<R>* f;
+  __device__ __forceinline__ Cx<R> operator[](int t) const { return cmul(c[t / TW_FINE], f[t % TW_FINE]); }
+};
+
+// j / Ns for the butterfly indices j < L <= 2^14 of a stage: with m = ceil(2^32 / Ns),
+// floor(j m / 2^32) = floor(j / Ns) exactly because j Ns < 2^32.
+__device__ __forceinline__ int div_ns(int j, int Ns, unsigned m) { return Ns == 1 ? j : (int)__umulhi((unsigned)j, m); }
+
+// One Stockham stage of radix RAD (Ns = product of the earlier radices): butterfly j
+// reads src[j + r L / RAD], twiddles r by e^{-2 pi i r (j mod Ns) / (Ns RAD)}, takes
+// the RAD-point DFT and writes dst[(j / Ns) Ns RAD + j mod Ns + k Ns].
+template <int RAD, typename R>
+__device__ __forceinline__ void stockham_stage(const Cx<R>* __restrict__ src, Cx<R>* __restrict__ dst, int L, int Ns,
+                                               unsigned magic, const Tw<R>& tw) {
+  const int nb = L / RAD;
+  const int step = L / (Ns * RAD);
+  constexpr int UNR = RAD <= 4 ? 2 : 1;  // two butterflies in flight where registers allow
+#pragma unroll UNR
+  for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+    const int jd = div_ns(j, Ns, magic);
+    const int jm = j - jd * Ns;
+    Cx<R> v[RAD];
+#pragma unroll
+    for (int r = 0; r < RAD; ++r) v[r] = src[j + r * nb];
+    if (RAD == 8) {  // w^1, w^2, w^4 from the table, the other powers as their products
+      const int t1 = jm * step;
+      const Cx<R> w1 = tw[t1], w2 = tw[2 * t1], w4 = tw[4 * t1];
+      const Cx<R> w3 = cmul(w1, w2);
+      v[1] = cmul(v[1], w1);
+      v[2] = cmul(v[2], w2);
+      v[3] = cmul(v[3], w3);
+      v[4] = cmul(v[4], w4);
+      v[5] = cmul(v[5], cmul(w1, w4));
+      v[6] = cmul(v[6], cmul(w2, w4));
+      v[7] = cmul(v[7], cmul(w3, w4));
+    } else {
+#pragma unroll
+      for (int r = 1; r < RAD; ++r) v[r] = cmul(v[r], tw[jm * r * step]);
+    }
+    Cx<R> o[RAD];
+    if (RAD == 8) {  // three radix-2 levels; W8 = (1 - i) / sqrt 2, W8^3 = (-1 - i) / sqrt 2
+      const R h = R(0.70710678118654752440);
+      auto mi = [](Cx<R> z) { return Cx<R>{z.y, -z.x}; };  // z * (-i)
+      const Cx<R> a0 = cadd(v[0], v[4]), a1 = csub(v[0], v[4]), a2 = cadd(v[2], v[6]), a3 = mi(csub(v[2], v[6]));
+      const Cx<R> a4 = cadd(v[1], v[5]), a5 = csub(v[1], v[5]), a6 = cadd(v[3], v[7]), a7 = mi(csub(v[3], v[7]));
+      const Cx<R> b0 = cadd(a0, a2), b2 = csub(a0, a2), b1 = cadd(a1, a3), b3 = csub(a1, a3);
+      const Cx<R> b4 = cadd(a4, a6), b6 = mi(csub(a4, a6)), b5 = cadd(a5, a7), b7 = csub(a5, a7);
+      const Cx<R> t5{h * (b5.x + b5.y), h * (b5.y - b5.x)};     // W8 b5
+      const Cx<R> t7{h * (b7.y - b7.x), -h * (b7.x + b7.y)};    // W8^3 b7
+      o[0] = cadd(b0, b4);
+      o[4] = csub(b0, b4);
+      o[2] = cadd(b2, b6);
+      o[6] = csub(b2, b6);
+      o[1] = cadd(b1, t5);
+      o[5] = csub(b1, t5);
+      o[3] = cadd(b3, t7);
+      o[7] = csub(b3, t7);
+    } else if (RAD == 2) {
+      o[0] = cadd(v[0], v[1]);
+      o[1] = csub(v[0], v[1]);
+    } else if (RAD == 4) {
+      const Cx<R> a = cadd(v[0], v[2]), b = csub(v[0], v[2]), c = cadd(v[1], v[3]), d = csub(v[1], v[3]);
+      o[0] = cadd(a, c);
+      o[2] = csub(a, c);
+      o[1] = Cx<R>{b.x + d.y, b.y - d.x};  // b - i d
+      o[3] = Cx<R>{b.x - d.y, b.y + d.x};  // b + i d
+    } else {  // 3, 5, 7: the direct DFT with the table's roots of unity
+#pragma unroll
+      for (int k = 0; k < RAD; ++k) {
+        Cx<R> acc = v[0];
+#pragma unroll
+        for (int r = 1; r < RAD; ++r) acc = cadd(acc, cmul(v[r], tw[((r * k) % RAD) * (L / RAD)]));
+        o[k] = acc;
+      }
+    }
+    const int idx = jd * Ns * RAD + jm;
+#pragma unroll
+    for (int k = 0; k < RAD; ++k) dst[idx + k * Ns] = o[k];
+  }
+}
+
+// Copy a line's coarse and fine twiddle factors into shared memory at t (the block's
+// first use of them follows a barrier).
+template <typename R>
+__device__ __forceinline__ Tw<R> stage_twiddles(Cx<R>* t, const LinePlan<R>& p) {
+  for (int i = threadIdx.x; i < p.ncoarse + TW_FINE; i += blockDim.x) t[i] = p.tw[i];
+  __syncthreads();
+  return Tw<R>{t, t + p.ncoarse};
+}
+
+// DFT of the L complex values in a (scratch b): returns the buffer holding the result.
+template <typename R>
+__device__ Cx<R>* line_fft(Cx<R>* a, Cx<R>* b, const LinePlan<R>& p, const Tw<R>& tw) {
+  int Ns = 1;
+  for (int s = 0; s < p.nst; ++s) {
+    const int rad = p.rad[s];
+    const unsigned m = p.magic[s];
+    if (rad == 8) stockham_stage<8, R>(a, b, p.L, Ns, m, tw);
+    else if (rad == 4) stockham_stage<4, R>(a, b, p.L, Ns, m, tw);
+    else if (rad == 2) stockham_stage<2, R>(a, b, p.L, Ns, m, tw);
+    else if (rad == 3) stockham_stage<3, R>(a, b, p.L, Ns, m, tw);
+    else if (rad == 5) stockham_stage<5, R>(a, b, p.L, Ns, m, tw);
+    else stockham_stage<7, R>(a, b, p.L, Ns, m, tw);
+    __syncthreads();
+    Ns *= rad;
+    Cx<R>* t = a;
+    a = b;
+    b = t;
+  }
+  return a;
+}
+
+// z_n = y_2n + i y_2n+1 of the odd extension of s_1 .. s_N (s(m) gives s_m, 1 <= m <= N):
+// the N values are gathered once into tmp (L values of scratch, not z), then paired.
+template <int UNR, typename R, typename S>
+__device__ __forceinline__ void line_pack(Cx<R>* z, R* tmp, int L, S s) {
+#pragma unroll UNR
+  for (int m = 1 + threadIdx.x; m < L; m += blockDim.x) tmp[m] = s(m);  // UNR loads in flight per thread
+  __syncthreads();
+  auto y = [&](int m) -> R {
+    if (m == 0 || m == L) return R(0);
+    return m < L ? tmp[m] : -tmp[2 * L - m];
+  };
+  for (int n = threadIdx.x; n < L; n += blockDim.x) z[n] = Cx<R>{y(2 * n), y(2 * n + 1)};
+}
+
+// DST_k = -Im(Y_k) / 2, k = 1 .. N, from the DFT Z of the packed extension.
+template <typename R>
+__device__ __forceinline__ R line_dst_at(const Cx<R>* Z, int L, const Cx<R>* __restrict__ pw, int k) {
+  const Cx<R> zk = Z[k], zc = Z[L - k];
+  const Cx<R> E{R(0.5) * (zk.x + zc.x), R(0.5) * (zk.y - zc.y)};
+  const Cx<R> O{R(0.5) * (zk.y + zc.y), -R(0.5) * (zk.x - zc.x)};  // (Z_k - conj Z_{L-k}) / 2i
+  const Cx<R> w = pw[k];
+  const R imY = E.y + (w.x * O.y + w.y * O.x);
+  return -R(0.5) * imY;
+}
+
+// rho at box node (m, jp + 1) of an x line (m = 1 .. Nx): the Eq. 1 divergence of the
+// in-plane field on I, zero on the box's padding.
+template <typename R>
+struct RhoRow {
+  const R* f;
+  const R* lo;
+  int nx, ny, bx, by, jp;
+  size_t plane;
+  R i12dx, i12dy;
+  __device__ __forceinline__ R operator()(int m) const {
+    const int i = m + 1 - bx, j = jp + 2 - by;
+    if (i < 2 || i > nx - 3 || j < 2 || j > ny - 3) return R(0);
+    const size_t s = (size_t)j * nx + i;
+    auto d1 = [&](const R* p, size_t c, ptrdiff_t st1, R sc) {
+      const R* q = p + c * plane + s;
+      return (R(8) * (q[st1] - q[-st1]) - (q[2 * st1] - q[-2 * st1])) * sc;
+    };
+    R rho = d1(f, 0, 1, i12dx) + d1(f, 1, (ptrdiff_t)nx, i12dy);
+    if (lo) rho += d1(lo, 0, 1, i12dx) + d1(lo, 1, (ptrdiff_t)nx, i12dy);
+    return rho;
+  }
+};
+
+// Rows of the box along x: rho, its DST, into T1[Ny][Nx].
+template <typename R>
+__global__ void __launch_bounds__(DST_THREADS, sizeof(R) == 4 ? 3 : 1) k_dst_rho_rows(const R* __restrict__ phi0, const R* __restrict__ phi1,
+                                                              const R* __restrict__ lo0, const R* __restrict__ lo1,
+                                                              const DevState* st, int nx, int ny, size_t plane, int Nx,
+                                                              int Ny, int bx, int by, R i12dx, R i12dy,
+                                                              const LinePlan<R> p, R* __restrict__ T1) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  Cx<R>* a = reinterpret_cast<Cx<R>*>(dsm);
+  Cx<R>* b = a + p.L;
+  const Tw<R> tw = stage_twiddles(b + p.L, p);
+  const int cur = (int)(st->steps & 1);
+  RhoRow<R> rr{cur ? phi1 : phi0, cur ? lo1 : lo0, nx, ny, bx, by, 0, plane, i12dx, i12dy};
+  for (int jp = blockIdx.x; jp < Ny; jp += gridDim.x) {
+    rr.jp = jp;
+    line_pack<2>(a, reinterpret_cast<R*>(b), p.L, rr);
+    __syncthreads();
+    const Cx<R>* Z = line_fft(a, b, p, tw);
+    R* out = T1 + (size_t)jp * Nx;
+#pragma unroll 4
+    for (int k = 1 + threadIdx.x; k <= Nx; k += blockDim.x) out[k - 1] = line_dst_at(Z, p.L, p.pw, k);
+    __syncthreads();
+  }
+}
+
+// Columns of the box (rows of T2[Nx][Ny]): DST along y, division by lambda_x + lambda_y,
+// DST along y again, in place.
+template <typename R>
+__global__ void __launch_bounds__(DST_THREADS, sizeof(R) == 4 ? 3 : 1) k_dst_solve_cols(R* __restrict__ T2, int Nx, int Ny,
+                                                                const R* __restrict__ lamx, const R* __restrict__ lamy,
+                                                                const LinePlan<R> p) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  Cx<R>* a = reinterpret_cast<Cx<R>*>(dsm);
+  Cx<R>* b = a + p.L;
+  const Tw<R> tw = stage_twiddles(b + p.L, p);
+  for (int r = blockIdx.x; r < Nx; r += gridDim.x) {
+    R* line = T2 + (size_t)r * Ny;
+    const R lx = lamx[r];
+    line_pack<8>(a, reinterpret_cast<R*>(b), p.L, [&](int m) { return line[m - 1]; });
+    __syncthreads();
+    const Cx<R>* Z = line_fft(a, b, p, tw);
+    // the divided coefficients, in the other buffer (as reals, index l = 1 .. Ny)
+    Cx<R>* c = (Z == a) ? b : a;
+    R* cr = reinterpret_cast<R*>(c);
+#pragma unroll 4
+    for (int l = 1 + threadIdx.x; l <= Ny; l += blockDim.x) cr[l] = line_dst_at(Z, p.L, p.pw, l) / (lx + lamy[l - 1]);
+    __syncthreads();
+    // the second transform's input: its gather is in place (each thread copies its own
+    // entries), its pairs go to Z's buffer, free now
+    Cx<R>* z2 = const_cast<Cx<R>*>(Z);
+    line_pack<4>(z2, cr, p.L, [&](int m) { return cr[m]; });
+    __syncthreads();
+    const Cx<R>* Z2 = line_fft(z2, c, p, tw);
+#pragma unroll 4
+    for (int l = 1 + threadIdx.x; l <= Ny; l += blockDim.x) line[l - 1] = line_dst_at(Z2, p.L, p.pw, l);
+    __syncthreads();
+  }
+}
+
+// Rows along x again: DST, the normalisation, and psi on I into the plane of the current
+// parity (its halo stays zero).
+template <typename R>
+__global__ void __launch_bounds__(DST_THREADS, sizeof(R) == 4 ? 3 : 1) k_dst_psi_rows(const R* __restrict__ T1, int nx, int ny, int Nx, int Ny,
+                                                              int bx, int by, R norm, const LinePlan<R> p,
+                                                              const DevState* st, R* __restrict__ psi0,
+                                                              R* __restrict__ psi1) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  Cx<R>* a = reinterpret_cast<Cx<R>*>(dsm);
+  Cx<R>* b = a + p.L;
+  const Tw<R> tw = stage_twiddles(b + p.L, p);
+  R* __restrict__ psi = (st->steps & 1) ? psi1 : psi0;
+  for (int jp = blockIdx.x; jp < Ny; jp += gridDim.x) {
+    const int j = jp + 2 - by;  // full-array row of box row jp
+    if (j < 2 || j > ny - 3) continue;  // uniform over the block
+    const R* line = T1 + (size_t)jp * Nx;
+    line_pack<8>(a, reinterpret_cast<R*>(b), p.L, [&](int m) { return line[m - 1]; });
+    __syncthreads();
+    const Cx<R>* Z = line_fft(a, b, p, tw);
+#pragma unroll 4
+    for (int i = 2 + threadIdx.x; i <= nx - 3; i += blockDim.x) {
+      const int m = i - 1 + bx;  // box column of site i
+      psi[(size_t)j * nx + i] = norm * line_dst_at(Z, p.L, p.pw, m);
+    }
+    __syncthreads();
+  }
+}
+
+// out[c][r] = in[r][c] for an rows x cols array, through 32 x 32 shared tiles.
+template <typename R>
+__global__ void k_transpose(const R* __restrict__ in, int rows, int cols, R* __restrict__ out) {
+  __shared__ R tile[32][33];
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) {
+    const int r = r0 + dy, c = c0 + threadIdx.x;
+    if (r < rows && c < cols) tile[dy][threadIdx.x] = in[(size_t)r * cols + c];
+  }
+  __syncthreads();
+  for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) {
+    const int c = c0 + dy, r = r0 + threadIdx.x;
+    if (c < cols && r < rows) out[(size_t)c * rows + r] = tile[threadIdx.x][dy];
+  }
+}
+
+// Radices of a 7-smooth length, eights and fours first; 0 if L has another prime factor or needs
+// too many stages.
+int plan_radices(int L, int* rad) {
+  int n = 0, m = L;
+  while (m % 8 == 0 && n < DST_MAX_STAGES) { rad[n++] = 8; m /= 8; }
+  while (m % 4 == 0 && n < DST_MAX_STAGES) { rad[n++] = 4; m /= 4; }
+  const int ps[4] = {2, 3, 5, 7};
+  for (int q : ps)
+    while (m % q == 0 && n < DST_MAX_STAGES) { rad[n++] = q; m /= q; }
+  return m == 1 ? n : 0;
+}
+
+}  // namespace
 
 struct DemagSolver {
   int nx = 0, ny = 0;
   int Nx = 0, Ny = 0;  // Dirichlet box sites per axis (>= the interior's nx - 4, ny - 4)
   int bx = 0, by = 0;  // box sites below I along x, y
-  int Mx = 0, My = 0, Hx = 0, Hy = 0;
-  int prec = 0;  // PREC_*: FP64 transforms for FP64 fields, FP32 otherwise
+  int prec = 0;        // PREC_*: FP64 transforms for FP64 fields, FP32 otherwise
   double dx = 0, dy = 0;
-  cufftHandle px = 0, py = 0;
-  bool have_px = false, have_py = false;
-  void* ext_x = nullptr;  // R [Ny][Mx] (box rows)
-  void* cx = nullptr;     // complex [Ny][Hx]
-  void* ext_y = nullptr;  // R [Nx][My]
-  void* cy = nullptr;     // complex [Nx][Hy]
-  void* lam = nullptr;    // R [Nx + Ny]: the x and y parts of lambda
+  void* T1 = nullptr;   // R [Ny][Nx]
+  void* T2 = nullptr;   // R [Nx][Ny]
+  void* tab = nullptr;  // twiddles of both axes, then lambda_x, lambda_y
+  int radx[DST_MAX_STAGES] = {0}, rady[DST_MAX_STAGES] = {0};
+  int nstx = 0, nsty = 0;
+  size_t off_twx = 0, off_pwx = 0, off_twy = 0, off_pwy = 0, off_lam = 0;  // element offsets into tab
+  int occ = 1;  // resident blocks per SM of the line kernels
 };
 
-// ---- kernels (R the transform type; F the field storage type, equal except that
-// compensated FP32 adds the remainder plane)
-// rho into the x-extension rows of the box (zero on the box's padding), with the two
-// zero points of every row.
-template <typename R>
-__global__ void k_rho_ext(const R* __restrict__ phi0, const R* __restrict__ phi1, const R* __restrict__ lo0,
-                          const R* __restrict__ lo1, const DevState* st, int nx, int ny, size_t plane, int Nx, int Ny,
-                          int bx, int by, int Mx, R i12dx, R i12dy, R* __restrict__ ext) {
-  const int cur = (int)(st->steps & 1);
-  const R* __restrict__ f = cur ? phi1 : phi0;
-  const R* __restrict__ lo = cur ? lo1 : lo0;
-  // rows over blocks, the row's points over threads (no index division)
-  for (int jp = blockIdx.x; jp < Ny; jp += gridDim.x)  // row 0 .. Ny-1  (j' - 1)
-    for (int ip = threadIdx.x; ip < Nx + 2; ip += blockDim.x) {  // 0 .. Nx+1  (i')
-      R* row = ext + (size_t)jp * Mx;
-      const int i = ip + 1 - bx, j = jp + 2 - by;  // full-array site of box node (ip, jp + 1)
-      if (ip == 0 || ip == Nx + 1 || i < 2 || i > nx - 3 || j < 2 || j > ny - 3) {  // zero node, padding
-        row[ip] = R(0);
-        if (ip != 0) row[Mx - ip] = R(0);
-        continue;
-      }
-      const size_t s = (size_t)j * nx + i;
-      auto d1 = [&](const R* p, size_t c, ptrdiff_t st1, R sc) {
-        const R* q = p + c * plane + s;
-        return (R(8) * (q[st1] - q[-st1]) - (q[2 * st1] - q[-2 * st1])) * sc;
-      };
-      R rho = d1(f, 0, 1, i12dx) + d1(f, 1, (ptrdiff_t)nx, i12dy);
-      if (lo) rho += d1(lo, 0, 1, i12dx) + d1(lo, 1, (ptrdiff_t)nx, i12dy);
-      row[ip] = rho;
-      row[Mx - ip] = -rho;
-    }
-}
-
-// -Im/2 of a row transform, written transposed as odd extensions of the columns:
-// in [rows][H] (complex, k = 1..K used), out [K][Mo] with out[k-1][r+1] = value and
-// out[k-1][Mo - r - 1] = -value, zeros at 0 and rows + 1. Optionally divided by
-// (lam_in[k-1] + lam_out[r]) (not here) -- plain transposition via 32 x 32 tiles.
-template <typename R, typename Cx>
-__global__ void k_im_transpose_ext(const Cx* __restrict__ in, int rows, int H, int K, R* __restrict__ out, int Mo) {
-  __shared__ R tile[32][33];
-  const int k0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
-  for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) {
-    const int r = r0 + dy, k = k0 + threadIdx.x;
-    tile[dy][threadIdx.x] = (r < rows && k < K) ? -R(0.5) * in[(size_t)r * H + (k + 1)].y : R(0);
-  }
-  __syncthreads();
-  for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) {
-    const int k = k0 + dy, r = r0 + threadIdx.x;
-    if (k < K && r < rows) {
-      const R v = tile[threadIdx.x][dy];
-      R* o = out + (size_t)k * Mo;
-      o[r + 1] = v;
-      o[Mo - r - 1] = -v;
-      if (r == 0) o[0] = R(0);
-      if (r == rows - 1) o[rows + 1] = R(0);
-    }
-  }
-}
-
-// a / b: FP32 by the fast reciprocal (2 ulp; b is a sum of two negative eigenvalues,
-// far from the range where it loses accuracy), FP64 exactly.
-__device__ __forceinline__ float div_eig(float a, float b) { return __fdividef(a, b); }
-__device__ __forceinline__ double div_eig(double a, double b) { return a / b; }
-
-// In place along the same rows: b = -Im/2 / (lam_x[row] + lam_y[l]) written back as
-// the odd extension of the row (for the inverse transform along y).
-template <typename R, typename Cx>
-__global__ void k_scale_ext(const Cx* __restrict__ in, int rows, int H, int L, const R* __restrict__ lamx,
-                            const R* __restrict__ lamy, R* __restrict__ out, int Mo) {
-  for (int r = blockIdx.x; r < rows; r += gridDim.x) {
-    const R lx = lamx[r];
-    R* o = out + (size_t)r * Mo;
-    const Cx* q = in + (size_t)r * H;
-    for (int l = threadIdx.x; l < L + 2; l += blockDim.x) {
-      if (l == 0 || l == L + 1) {
-        o[l] = R(0);
-        continue;
-      }
-      const R v = div_eig(-R(0.5) * q[l].y, lx + lamy[l - 1]);
-      o[l] = v;
-      o[Mo - l] = -v;
-    }
-  }
-}
-
-// psi = norm x (-Im/2) of the final row transform at I's box nodes, into the interior
-// of the plane of the current parity (the halo stays zero).
-template <typename R, typename Cx>
-__global__ void k_scatter_psi(const Cx* __restrict__ in, int H, int nx, int ny, int bx, int by, R norm,
-                              const DevState* st, R* __restrict__ psi0, R* __restrict__ psi1) {
-  R* __restrict__ psi = (st->steps & 1) ? psi1 : psi0;
-  for (int jp = blockIdx.x; jp < ny - 4; jp += gridDim.x)  // 0-based interior indices
-    for (int ip = threadIdx.x; ip < nx - 4; ip += blockDim.x)
-      psi[(size_t)(jp + 2) * nx + (ip + 2)] = norm * (-R(0.5) * in[(size_t)(jp + by) * H + (ip + 1 + bx)].y);
-}
-
-// ---- host side
 namespace {
+
+template <typename R>
+size_t line_smem(int L) { return sizeof(Cx<R>) * (2 * (size_t)L + (L + TW_FINE - 1) / TW_FINE + TW_FINE); }
+
+template <typename R>
+LinePlan<R> plan_of(const DemagSolver* d, int axis) {
+  LinePlan<R> p{};
+  const Cx<R>* t = static_cast<const Cx<R>*>(d->tab);
+  p.L = (axis == 0 ? d->Nx : d->Ny) + 1;
+  p.nst = axis == 0 ? d->nstx : d->nsty;
+  long long Ns = 1;
+  for (int s = 0; s < p.nst; ++s) {
+    p.rad[s] = axis == 0 ? d->radx[s] : d->rady[s];
+    p.magic[s] = Ns == 1 ? 0u : (unsigned)(((1ULL << 32) + (unsigned long long)Ns - 1) / (unsigned long long)Ns);
+    Ns *= p.rad[s];
+  }
+  p.ncoarse = (p.L + TW_FINE - 1) / TW_FINE;
+  p.tw = t + (axis == 0 ? d->off_twx : d->off_twy);
+  p.pw = t + (axis == 0 ? d->off_pwx : d->off_pwy);
+  return p;
+}
 
 template <typename R>
 cudaError_t solve_t(DemagSolver* d, const DevState* st, void* const phi[2], void* const lo[2], void* const psi[2],
                     cudaStream_t s) {
-  using Cx = typename FftOf<R>::C;
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const int grid = nsm * 8;
-  R* ext_x = static_cast<R*>(d->ext_x);
-  R* ext_y = static_cast<R*>(d->ext_y);
-  Cx* cx = static_cast<Cx*>(d->cx);
-  Cx* cy = static_cast<Cx*>(d->cy);
-  const R* lam = static_cast<const R*>(d->lam);
-  k_rho_ext<R><<<grid, 256, 0, s>>>(static_cast<const R*>(phi[0]), static_cast<const R*>(phi[1]),
-                                    static_cast<const R*>(lo[0]), static_cast<const R*>(lo[1]), st, d->nx, d->ny,
-                                    (size_t)d->nx * d->ny, d->Nx, d->Ny, d->bx, d->by, d->Mx,
-                                    (R)(1.0 / (12.0 * d->dx)), (R)(1.0 / (12.0 * d->dy)), ext_x);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  cufftSetStream(d->px, s);
-  cufftSetStream(d->py, s);
-  if (FftOf<R>::exec(d->px, ext_x, cx) != CUFFT_SUCCESS) return cudaErrorLaunchFailure;  // along x, every row
+  const LinePlan<R> px = plan_of<R>(d, 0), py = plan_of<R>(d, 1);
+  R* T1 = static_cast<R*>(d->T1);
+  R* T2 = static_cast<R*>(d->T2);
+  const R* lam = reinterpret_cast<const R*>(static_cast<const Cx<R>*>(d->tab) + d->off_lam);
+  // one wave of resident blocks striding over the lines
+  const int gx = d->Ny < d->occ * nsm ? d->Ny : d->occ * nsm, gy = d->Nx < d->occ * nsm ? d->Nx : d->occ * nsm;
+  k_dst_rho_rows<R><<<gx, DST_THREADS, line_smem<R>(px.L), s>>>(
+      static_cast<const R*>(phi[0]), static_cast<const R*>(phi[1]), static_cast<const R*>(lo[0]),
+      static_cast<const R*>(lo[1]), st, d->nx, d->ny, (size_t)d->nx * d->ny, d->Nx, d->Ny, d->bx, d->by,
+      (R)(1.0 / (12.0 * d->dx)), (R)(1.0 / (12.0 * d->dy)), px, T1);
   const dim3 tb(32, 8);
-  k_im_transpose_ext<R, Cx><<<dim3((d->Nx + 31) / 32, (d->Ny + 31) / 32), tb, 0, s>>>(cx, d->Ny, d->Hx, d->Nx, ext_y,
-                                                                                        d->My);
-  if (FftOf<R>::exec(d->py, ext_y, cy) != CUFFT_SUCCESS) return cudaErrorLaunchFailure;  // along y, every column
-  k_scale_ext<R, Cx><<<grid, 256, 0, s>>>(cy, d->Nx, d->Hy, d->Ny, lam, lam + d->Nx, ext_y, d->My);
-  if (FftOf<R>::exec(d->py, ext_y, cy) != CUFFT_SUCCESS) return cudaErrorLaunchFailure;  // back along y
-  k_im_transpose_ext<R, Cx><<<dim3((d->Ny + 31) / 32, (d->Nx + 31) / 32), tb, 0, s>>>(cy, d->Nx, d->Hy, d->Ny, ext_x,
-                                                                                        d->Mx);
-  if (FftOf<R>::exec(d->px, ext_x, cx) != CUFFT_SUCCESS) return cudaErrorLaunchFailure;  // back along x
+  k_transpose<R><<<dim3((d->Nx + 31) / 32, (d->Ny + 31) / 32), tb, 0, s>>>(T1, d->Ny, d->Nx, T2);
+  k_dst_solve_cols<R><<<gy, DST_THREADS, line_smem<R>(py.L), s>>>(T2, d->Nx, d->Ny, lam, lam + d->Nx, py);
+  k_transpose<R><<<dim3((d->Ny + 31) / 32, (d->Nx + 31) / 32), tb, 0, s>>>(T2, d->Nx, d->Ny, T1);
   const R norm = (R)((2.0 / (d->Nx + 1)) * (2.0 / (d->Ny + 1)));
-  k_scatter_psi<R, Cx><<<grid, 256, 0, s>>>(cx, d->Hx, d->nx, d->ny, d->bx, d->by, norm, st,
-                                            static_cast<R*>(psi[0]), static_cast<R*>(psi[1]));
+  k_dst_psi_rows<R><<<gx, DST_THREADS, line_smem<R>(px.L), s>>>(T1, d->nx, d->ny, d->Nx, d->Ny, d->bx, d->by, norm,
+                                                                 px, st, static_cast<R*>(psi[0]),
+                                                                 static_cast<R*>(psi[1]));
   return cudaGetLastError();
 }
 
 template <typename R>
 int create_t(DemagSolver* d) {
-  using Cx = typename FftOf<R>::C;
-  const size_t ex = sizeof(R) * (size_t)d->Ny * d->Mx, cxb = sizeof(Cx) * (size_t)d->Ny * d->Hx;
-  const size_t ey = sizeof(R) * (size_t)d->Nx * d->My, cyb = sizeof(Cx) * (size_t)d->Nx * d->Hy;
-  if (cudaMalloc(&d->ext_x, ex) != cudaSuccess || cudaMalloc(&d->cx, cxb) != cudaSuccess ||
-      cudaMalloc(&d->ext_y, ey) != cudaSuccess || cudaMalloc(&d->cy, cyb) != cudaSuccess ||
-      cudaMalloc(&d->lam, sizeof(R) * (size_t)(d->Nx + d->Ny)) != cudaSuccess)
-    return -1;
-  std::vector<R> lam((size_t)d->Nx + d->Ny);
+  const int Lx = d->Nx + 1, Ly = d->Ny + 1;
+  d->nstx = plan_radices(Lx, d->radx);
+  d->nsty = plan_radices(Ly, d->rady);
+  if (!d->nstx || !d->nsty) return -2;
+  int dev = 0;
+  size_t max_smem = 0;
+  {
+    int v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    max_smem = (size_t)v;
+  }
+  const size_t need = line_smem<R>(Lx > Ly ? Lx : Ly);
+  if (need > max_smem || Lx > (1 << 14) || Ly > (1 << 14)) return -2;  // one line per block, exact index division
+  if (cudaFuncSetAttribute(k_dst_rho_rows<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need) != cudaSuccess ||
+      cudaFuncSetAttribute(k_dst_solve_cols<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(k_dst_psi_rows<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need) != cudaSuccess)
+    return -2;
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_dst_solve_cols<R>, DST_THREADS, need) != cudaSuccess)
+    return -2;
+  d->occ = occ < 1 ? 1 : occ;
+  // tables: twiddle factors x (coarse, fine), pw_x [Lx + 1], the same for y, then lambda_x [Nx],
+  // lambda_y [Ny] as R
+  d->off_twx = 0;
+  d->off_pwx = d->off_twx + (Lx + TW_FINE - 1) / TW_FINE + TW_FINE;
+  d->off_twy = d->off_pwx + Lx + 1;
+  d->off_pwy = d->off_twy + (Ly + TW_FINE - 1) / TW_FINE + TW_FINE;
+  d->off_lam = d->off_pwy + Ly + 1;
+  const size_t ncx = d->off_lam + (d->Nx + d->Ny + 1) / 2 + 1;  // lambdas packed two per complex slot
+  std::vector<Cx<R>> t(ncx, Cx<R>{R(0), R(0)});
   const double pi = 3.14159265358979323846;
-  for (int k = 1; k <= d->Nx; ++k) lam[k - 1] = (R)(-(2.0 - 2.0 * std::cos(pi * k / (d->Nx + 1))) / (d->dx * d->dx));
-  for (int l = 1; l <= d->Ny; ++l)
-    lam[d->Nx + l - 1] = (R)(-(2.0 - 2.0 * std::cos(pi * l / (d->Ny + 1))) / (d->dy * d->dy));
-  if (cudaMemcpy(d->lam, lam.data(), sizeof(R) * lam.size(), cudaMemcpyHostToDevice) != cudaSuccess) return -1;
-  int n = d->Mx;
-  if (cufftPlanMany(&d->px, 1, &n, nullptr, 1, d->Mx, nullptr, 1, d->Hx, FftOf<R>::type, d->Ny) != CUFFT_SUCCESS)
-    return -2;
-  d->have_px = true;
-  n = d->My;
-  if (cufftPlanMany(&d->py, 1, &n, nullptr, 1, d->My, nullptr, 1, d->Hy, FftOf<R>::type, d->Nx) != CUFFT_SUCCESS)
-    return -2;
-  d->have_py = true;
+  auto fill = [&](size_t tw0, size_t pw0, int L) {
+    const int nc = (L + TW_FINE - 1) / TW_FINE;
+    for (int h = 0; h < nc; ++h)
+      t[tw0 + h] = Cx<R>{(R)std::cos(2.0 * pi * TW_FINE * h / L), (R)(-std::sin(2.0 * pi * TW_FINE * h / L))};
+    for (int l = 0; l < TW_FINE; ++l)
+      t[tw0 + nc + l] = Cx<R>{(R)std::cos(2.0 * pi * l / L), (R)(-std::sin(2.0 * pi * l / L))};
+    for (int k = 0; k <= L; ++k) t[pw0 + k] = Cx<R>{(R)std::cos(pi * k / L), (R)(-std::sin(pi * k / L))};
+  };
+  fill(d->off_twx, d->off_pwx, Lx);
+  fill(d->off_twy, d->off_pwy, Ly);
+  R* lam = reinterpret_cast<R*>(t.data() + d->off_lam);
+  for (int k = 1; k <= d->Nx; ++k) lam[k - 1] = (R)(-(2.0 - 2.0 * std::cos(pi * k / Lx)) / (d->dx * d->dx));
+  for (int l = 1; l <= d->Ny; ++l) lam[d->Nx + l - 1] = (R)(-(2.0 - 2.0 * std::cos(pi * l / Ly)) / (d->dy * d->dy));
+  const size_t tb = sizeof(R) * (size_t)d->Nx * d->Ny;
+  if (cudaMalloc(&d->T1, tb) != cudaSuccess || cudaMalloc(&d->T2, tb) != cudaSuccess ||
+      cudaMalloc(&d->tab, sizeof(Cx<R>) * t.size()) != cudaSuccess)
+    return -1;
+  if (cudaMemcpy(d->tab, t.data(), sizeof(Cx<R>) * t.size(), cudaMemcpyHostToDevice) != cudaSuccess) return -1;
   return 0;
 }
 
-}  // namespace
-
-namespace {
 // The Dirichlet box along an axis of N interior sites: the smallest N' >= N whose
-// N' + 1 has no prime factor above 7 (the transform length 2 (N' + 1) then factors
-// into small primes; 2 (N + 1) with a large prime factor, as 2 (4092 + 1) = 2 x 4093,
-// is several times slower), and floor((N' - N) / 2) of the extra sites below I.
+// N' + 1 has no prime factor above 7 (the line transform of length N' + 1 then runs
+// in stages of radix 4, 2, 3, 5, 7; a length with a large prime factor, as
+// 4092 + 1 = 4093, has no such factoring), and floor((N' - N) / 2) of the extra sites
+// below I.
 void box_of(int N, int* Np, int* below) {
   int n = N;
   for (;; ++n) {
@@ -241,6 +485,7 @@ void box_of(int N, int* Np, int* below) {
   *Np = n;
   *below = (n - N) / 2;
 }
+
 }  // namespace
 
 int demag_create(DemagSolver** out, int nx, int ny, double dx, double dy, int prec) {
@@ -251,10 +496,6 @@ int demag_create(DemagSolver** out, int nx, int ny, double dx, double dy, int pr
   d->ny = ny;
   box_of(nx - 4, &d->Nx, &d->bx);
   box_of(ny - 4, &d->Ny, &d->by);
-  d->Mx = 2 * (d->Nx + 1);
-  d->My = 2 * (d->Ny + 1);
-  d->Hx = d->Mx / 2 + 1;
-  d->Hy = d->My / 2 + 1;
   d->dx = dx;
   d->dy = dy;
   d->prec = prec;
@@ -269,13 +510,9 @@ int demag_create(DemagSolver** out, int nx, int ny, double dx, double dy, int pr
 
 void demag_destroy(DemagSolver* d) {
   if (!d) return;
-  if (d->have_px) cufftDestroy(d->px);
-  if (d->have_py) cufftDestroy(d->py);
-  cudaFree(d->ext_x);
-  cudaFree(d->cx);
-  cudaFree(d->ext_y);
-  cudaFree(d->cy);
-  cudaFree(d->lam);
+  cudaFree(d->T1);
+  cudaFree(d->T2);
+  cudaFree(d->tab);
   delete d;
 }
 
