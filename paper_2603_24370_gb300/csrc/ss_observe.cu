@@ -278,6 +278,86 @@ __global__ void k_ansatz(R* __restrict__ f0, R* __restrict__ f1, int nx, int ny,
   }
 }
 
+// The compact skyrmions of the unit-vector theories (the last branch of k_ansatz) with
+// the work proportional to the sites each soliton covers: a block takes a tile of
+// 32 x 8 sites, first lists, in ascending order, the solitons whose disc reaches the
+// tile's bounding box (widened by 1e-9 of the spacing), then each site scans only
+// that list, with the same FP64 arithmetic and first-match rule as k_ansatz. A tile
+// reached by more than ANS_CAP discs scans them all.
+constexpr int ANS_CAP = 512;
+template <typename R>
+__global__ void __launch_bounds__(256) k_ansatz_compact(R* __restrict__ f0, R* __restrict__ f1, int nx, int ny,
+                                                        size_t plane, double dx, double dy,
+                                                        const double* __restrict__ sol, int ns) {
+  const double PI = 3.14159265358979323846;
+  __shared__ int list[ANS_CAP];
+  __shared__ int wcnt[8];
+  __shared__ int cnt;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int ntx = (nx + 31) / 32, nty = (ny + 7) / 8;
+  for (int t = blockIdx.x; t < ntx * nty; t += gridDim.x) {
+    const int i0 = (t % ntx) * 32, j0 = (t / ntx) * 8;
+    const double ex = 1e-9 * dx, ey = 1e-9 * dy;
+    const double xlo = (i0 - 0.5 * (nx - 1)) * dx - ex, xhi = (min(i0 + 31, nx - 1) - 0.5 * (nx - 1)) * dx + ex;
+    const double ylo = (j0 - 0.5 * (ny - 1)) * dy - ey, yhi = (min(j0 + 7, ny - 1) - 0.5 * (ny - 1)) * dy + ey;
+    if (tid == 0) cnt = 0;
+    __syncthreads();
+    for (int base = 0; base < ns; base += 256) {
+      const int k = base + tid;
+      bool hit = false;
+      if (k < ns) {
+        const double cx = sol[5 * k], cy = sol[5 * k + 1], R0 = sol[5 * k + 3];
+        const double ddx = fmax(fmax(xlo - cx, cx - xhi), 0.0), ddy = fmax(fmax(ylo - cy, cy - yhi), 0.0);
+        hit = ddx * ddx + ddy * ddy < R0 * R0;
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, hit);
+      if (lane == 0) wcnt[w] = __popc(m);
+      __syncthreads();
+      int before = cnt;
+      for (int q = 0; q < w; ++q) before += wcnt[q];
+      const int pos = before + __popc(m & ((1u << lane) - 1u));
+      if (hit && pos < ANS_CAP) list[pos] = k;
+      __syncthreads();
+      if (tid == 0) {
+        int tot = 0;
+        for (int q = 0; q < 8; ++q) tot += wcnt[q];
+        cnt += tot;
+      }
+      __syncthreads();
+    }
+    const int nl = cnt;
+    const int i = i0 + lane, j = j0 + w;
+    if (i < nx && j < ny) {
+      const size_t s = (size_t)j * nx + i;
+      const double x = (i - 0.5 * (nx - 1)) * dx, y = (j - 0.5 * (ny - 1)) * dy;
+      double n1 = 0.0, n2 = 0.0, n3 = 1.0;
+      const bool all = nl > ANS_CAP;
+      const int nk = all ? ns : nl;
+      for (int q = 0; q < nk; ++q) {
+        const int k = all ? q : list[q];
+        const double X = x - sol[5 * k], Y = y - sol[5 * k + 1];
+        const double R0 = sol[5 * k + 3];
+        const double r2 = X * X + Y * Y;
+        if (r2 < R0 * R0) {
+          const double r = sqrt(r2);
+          const double fr = PI * (1.0 - r / R0), th = sol[5 * k + 2] * atan2(Y, X) + sol[5 * k + 4];
+          n1 = sin(fr) * cos(th);
+          n2 = sin(fr) * sin(th);
+          n3 = cos(fr);
+          break;
+        }
+      }
+      const R v[3] = {(R)n1, (R)n2, (R)n3};
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        f0[c * plane + s] = v[c];
+        f1[c * plane + s] = v[c];
+      }
+    }
+    __syncthreads();  // the list is rebuilt for the next tile
+  }
+}
+
 // ------------------------------------------------------------------ launchers
 template <int TH, typename R>
 static cudaError_t obs_t(const LaunchCtx& c, int cur, cudaStream_t s) {
@@ -347,6 +427,16 @@ static cudaError_t ansatz_t(const LaunchCtx& c, const double* sol, int n, cudaSt
   // BEC: g and mu; at a fixed atom number N the Thomas-Fermi mu of N atoms, sqrt(g N / pi)
   double q[3] = {c.coup[0], c.coup[4] > 0.0 ? std::sqrt(c.coup[0] * c.coup[4] / 3.14159265358979323846) : c.coup[2], 0.0};
   if (TH == TH_SID) sid_uniform_minimum(c.coup, &q[0], &q[1], &q[2]);
+  if (TH == TH_CM) {  // compact skyrmions: each site scans only the discs near its tile
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const long long tiles = (long long)((c.nx + 31) / 32) * ((c.ny + 7) / 8);
+    const int g = (int)(tiles < 8LL * nsm ? tiles : 8LL * nsm);
+    k_ansatz_compact<R><<<g, 256, 0, s>>>(static_cast<R*>(c.phi[0]), static_cast<R*>(c.phi[1]), c.nx, c.ny, c.plane,
+                                          c.dx, c.dy, sol, n);
+    return cudaGetLastError();
+  }
   k_ansatz<TH, R><<<blocks, 256, 0, s>>>(static_cast<R*>(c.phi[0]), static_cast<R*>(c.phi[1]), c.nx, c.ny, c.plane,
                                          c.dx, c.dy, sol, n, q[0], q[1], q[2]);
   return cudaGetLastError();
