@@ -1,5 +1,13 @@
 // ss_flow_cm.cu -- the flow pass kernels of the chiral magnet, instantiated in a
 // translation unit of their own (see ss_flow_kernel.cuh).
+//
+// Launch shape: the header's defaults (3 / 4 / 5 blocks per SM for passes 1 / 2 / 3)
+// except pass 2, which loads each site's stored values for the RK4 combination
+// before its stage forces and runs at 3 blocks per SM for the registers that takes:
+// on the 4096^2 workload, in one call, pass 2 0.454 -> 0.442 ms (the step 0.894 ->
+// 0.869 ms); at 4 blocks per SM the early loads spill.
+#define SS_PF2 1
+#define SS_MINB2 3
 #include "ss_flow_kernel.cuh"
 
 namespace ss {

@@ -82,6 +82,11 @@
 #ifndef SS_E_EVERY
 #define SS_E_EVERY 16
 #endif
+// FP32 pass 2 loads a site's stored values for the RK4 combination before computing
+// the site's stage forces (1) or after them (0).
+#ifndef SS_PF2
+#define SS_PF2 0
+#endif
 #ifndef SS_LU2
 #define SS_LU2 3
 #endif
@@ -412,22 +417,37 @@ __device__ __forceinline__ void force_at(const Couplings<R>& k, const R* v, cons
 // the increment joining the stored remainder with compensated storage, and
 // v' = v + dt/6 (k1 + 2 k2 + 2 k3 + k4); unit vectors are normalised (split form) and
 // v' tangent-projected. Under a pending arrest v counts as zero and k2 as k1.
+// The stored values the combination needs at site s (loaded before the stage forces
+// are computed, so that their latency overlaps that work).
+template <int TH, typename R>
+struct SiteVals {
+  R p0[NComp<TH>::C], l0[NComp<TH>::C], v0[NComp<TH>::C], k1[NComp<TH>::C], k2[NComp<TH>::C];
+};
 template <int TH, typename R, bool LO>
-__device__ __forceinline__ void combine_site(const R* __restrict__ phi, const R* __restrict__ lo,
-                                             const R* __restrict__ vel, const R* __restrict__ kv1,
-                                             const R* __restrict__ kv2, R* __restrict__ phi_out,
-                                             R* __restrict__ lo_out, R* __restrict__ v_out, size_t P, size_t s,
-                                             bool arrest, R dt, R w6, R u6, const R* k3, const R* k4) {
+__device__ __forceinline__ void load_site(SiteVals<TH, R>& sv, const R* __restrict__ phi, const R* __restrict__ lo,
+                                          const R* __restrict__ vel, const R* __restrict__ kv1,
+                                          const R* __restrict__ kv2, size_t P, size_t s, bool arrest) {
+#pragma unroll
+  for (int c = 0; c < NComp<TH>::C; ++c) {
+    sv.p0[c] = phi[c * P + s];
+    sv.l0[c] = LO ? lo[c * P + s] : R(0);
+    sv.v0[c] = arrest ? R(0) : vel[c * P + s];
+    sv.k1[c] = kv1[c * P + s];
+    sv.k2[c] = arrest ? sv.k1[c] : kv2[c * P + s];
+  }
+}
+template <int TH, typename R, bool LO>
+__device__ __forceinline__ void combine_loaded(const SiteVals<TH, R>& sv, R* __restrict__ phi_out,
+                                               R* __restrict__ lo_out, R* __restrict__ v_out, size_t P, size_t s,
+                                               R dt, R w6, R u6, const R* k3, const R* k4) {
   constexpr int C = NComp<TH>::C;
   R p0[C], q[C], vn[C];
 #pragma unroll
   for (int c = 0; c < C; ++c) {
-    p0[c] = phi[c * P + s];
-    const R v0 = arrest ? R(0) : vel[c * P + s];
-    const R k1 = kv1[c * P + s];
-    const R k2 = arrest ? k1 : kv2[c * P + s];
+    p0[c] = sv.p0[c];
+    const R v0 = sv.v0[c], k1 = sv.k1[c], k2 = sv.k2[c];
     const R inc = dt * v0 + w6 * (k1 + k2 + k3[c]);
-    q[c] = LO ? lo[c * P + s] + inc : p0[c] + inc;
+    q[c] = LO ? sv.l0[c] + inc : p0[c] + inc;
     vn[c] = v0 + u6 * (k1 + R(2) * (k2 + k3[c]) + k4[c]);
   }
   R pn[C], ln[C];
@@ -451,6 +471,16 @@ __device__ __forceinline__ void combine_site(const R* __restrict__ phi, const R*
     if (LO) lo_out[c * P + s] = ln[c];
     v_out[c * P + s] = vn[c];
   }
+}
+template <int TH, typename R, bool LO>
+__device__ __forceinline__ void combine_site(const R* __restrict__ phi, const R* __restrict__ lo,
+                                             const R* __restrict__ vel, const R* __restrict__ kv1,
+                                             const R* __restrict__ kv2, R* __restrict__ phi_out,
+                                             R* __restrict__ lo_out, R* __restrict__ v_out, size_t P, size_t s,
+                                             bool arrest, R dt, R w6, R u6, const R* k3, const R* k4) {
+  SiteVals<TH, R> sv;
+  load_site<TH, R, LO>(sv, phi, lo, vel, kv1, kv2, P, s, arrest);
+  combine_loaded<TH, R, LO>(sv, phi_out, lo_out, v_out, P, s, dt, w6, u6, k3, k4);
 }
 
 // Running maximum of |g| for a >= 0: on non-negative values the IEEE bit patterns
@@ -1056,21 +1086,25 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
 #pragma unroll
         for (int r = 0; r < RY; ++r) {
           const int off = (sy0 + r) * T::SX + sx;
+          const bool ok = colok && gyb + r >= 2 && gyb + r < ny - 2;
+          const size_t s = (size_t)(gyb + r) * nx + gx;
+          SiteVals<TH, R> sv;
+          if (SS_PF2 && ok) load_site<TH, R, LO>(sv, phi, lo, vel, kv1, kv2, P, s, arrest);
           F2 v[C], fx[C], fy[C], fxx[C], fyy[C], fxy[C], G[C];
           W.derivs(ab, off, h2, v, fx, fy, fxx, fyy, fxy);
           // site extras: the BEC's position; with demagnetisation psi and its gradient
           R q0 = xs, q1 = ypos(r), ps = R(0);
           if (TH == TH_CMD) W.psi_at(off, h, ps, q0, q1);
           force_at<TH, F2>(k2c, v, fx, fy, fxx, fyy, fxy, G, F2(q0), F2(q1));
-          if (colok && gyb + r >= 2 && gyb + r < ny - 2) {
+          if (ok) {
             R k3[C], k4[C];
 #pragma unroll
             for (int c = 0; c < C; ++c) {
               k3[c] = -G[c].v.x;
               k4[c] = -G[c].v.y;
             }
-            combine_site<TH, R, LO>(phi, lo, vel, kv1, kv2, phi_out, lo_out, v_out, P, (size_t)(gyb + r) * nx + gx,
-                                    arrest, dt, w6, u6, k3, k4);
+            if (!SS_PF2) load_site<TH, R, LO>(sv, phi, lo, vel, kv1, kv2, P, s, arrest);
+            combine_loaded<TH, R, LO>(sv, phi_out, lo_out, v_out, P, s, dt, w6, u6, k3, k4);
           }
           if (r + 1 < RY) {
             W.shift();
