@@ -1,8 +1,9 @@
 """Chiral magnet with demagnetisation (Eq. 6) on the CUDA path vs the FP64 oracle.
 
 The GPU solves the 5-point Poisson problem of the magnetostatic potential with a
-sine transform built on batched real FFTs; the oracle with the transform written out
-as plain sums. Tolerances as in test_gpu_parity.py (FP64 1e-11 of the force scale,
+sine transform built on its own shared-memory FFTs (the test grids' boxes take
+lengths 40, 42, 63, 70: radix 8, 5, 2, 3, 7 stages); the oracle with the transform
+written out as plain sums. Tolerances as in test_gpu_parity.py (FP64 1e-11 of the force scale,
 1e-10 of the field after tens of steps; FP32 3e-5 and 2e-5), with the potential
 solved in the working precision.
 """
@@ -23,6 +24,10 @@ GRID = (71, 45, 0.2, 0.23)
 # Dirichlet boxes: GRID pads x only (67 -> 69 sites, one below I); GRID_PAD pads both
 # axes with a site below I (60 -> 62, 36 -> 39)
 GRID_PAD = (64, 40, 0.21, 0.2)
+# boxes whose transform lengths take radix 8 x 4 (35 -> Lx = 32) and 8 x 8 (67 -> Lx = 64)
+# along x, 5 x 7 along y (36 -> Ly = 35)
+GRID_R4 = (35, 36, 0.2, 0.22)
+GRID_R8 = (67, 36, 0.19, 0.2)
 
 
 @pytest.fixture(scope="module")
@@ -40,7 +45,7 @@ def dtype_of(prec):
     return np.float64 if prec == 2 else np.float32
 
 
-@pytest.mark.parametrize("grid", [GRID, GRID_PAD])
+@pytest.mark.parametrize("grid", [GRID, GRID_PAD, GRID_R4, GRID_R8])
 @pytest.mark.parametrize("prec", [1, 2, 3])
 def test_force_and_energy_match_oracle(S, prec, grid):
     nx, ny, dx, dy = grid
