@@ -108,7 +108,7 @@ def measured_peaks() -> tuple[dict, str]:
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for fn in ("ss_flow_kernel.cuh", "ss_flow.cu", "ss_device.cuh", "ss_flow_cm.cu"):
+    for fn in ("ss_flow_kernel.cuh", "ss_flow.cu", "ss_device.cuh", "ss_flow_cm.cu", "ss_pack.cuh"):
         with open(os.path.join(ROOT, "paper_2603_24370_gb300", "csrc", fn), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

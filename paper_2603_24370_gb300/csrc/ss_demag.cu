@@ -87,7 +87,7 @@ __device__ __forceinline__ void stockham_stage(const Cx<R>* __restrict__ src, Cx
                                                unsigned magic, const Tw<R>& tw) {
   const int nb = L / RAD;
   const int step = L / (Ns * RAD);
-  constexpr int UNR = RAD <= 4 ? 2 : 1;  // two butterflies in flight where registers allow
+  constexpr int UNR = (RAD <= 4 || RAD == 8) ? 2 : 1;  // two butterflies in flight where registers allow
 #pragma unroll UNR
   for (int j = threadIdx.x; j < nb; j += blockDim.x) {
     const int jd = div_ns(j, Ns, magic);
