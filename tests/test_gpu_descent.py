@@ -108,10 +108,13 @@ def test_descent_minimise_reaches_the_oracles_minimum(S, theory):
         # in FP32 near convergence the per-step decrease is below the sum's rounding
         if prec == 2:
             assert st["arrests"] == 0
-        # FP32: the residual's rounding noise near 1e-6 moves the stopping step by
-        # (noise / residual) / (dtau lambda_min) steps: a few % of the total
+        # FP32: the residual's rounding noise near 1e-6 moves the step where the flow's
+        # own FP32 residual first passes by (noise / residual) / (dtau lambda_min)
+        # steps (a few % of the total); the FP64 verdict on the stored field then adds
+        # rounds of max(8, steps / 64) steps until the field passes in FP64 as well
         slack = 1 if prec == 2 else max(5, ref["steps"] // 20)
-        assert abs(st["steps"] - ref["steps"]) <= slack, (prec, st["steps"], ref["steps"])
+        over = 0 if prec == 2 else 2 * max(8, ref["steps"] // 64)
+        assert -slack <= st["steps"] - ref["steps"] <= slack + over, (prec, st["steps"], ref["steps"])
         # the working-precision energy, and the FP64 energy of the field reached (FP32:
         # stopping up to `slack` steps off moves E by that many per-step decreases,
         # ~1e-8 of E here)
