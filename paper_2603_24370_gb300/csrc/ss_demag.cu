@@ -197,15 +197,21 @@ __device__ __forceinline__ void line_pack(Cx<R>* z, R* tmp, int L, S s) {
   for (int n = threadIdx.x; n < L; n += blockDim.x) z[n] = Cx<R>{y(2 * n), y(2 * n + 1)};
 }
 
-// DST_k = -Im(Y_k) / 2, k = 1 .. N, from the DFT Z of the packed extension.
-template <typename R>
-__device__ __forceinline__ R line_dst_at(const Cx<R>* Z, int L, const Cx<R>* __restrict__ pw, int k) {
-  const Cx<R> zk = Z[k], zc = Z[L - k];
-  const Cx<R> E{R(0.5) * (zk.x + zc.x), R(0.5) * (zk.y - zc.y)};
-  const Cx<R> O{R(0.5) * (zk.y + zc.y), -R(0.5) * (zk.x - zc.x)};  // (Z_k - conj Z_{L-k}) / 2i
-  const Cx<R> w = pw[k];
-  const R imY = E.y + (w.x * O.y + w.y * O.x);
-  return -R(0.5) * imY;
+// Every DST_k, k = 1 .. L - 1, to out(k, value), two at a time: k and L - k share the
+// loads of Z_k, Z_{L-k} and the factor w_k = e^{-i pi k / L}, since E_{L-k} = conj E_k,
+// O_{L-k} = conj O_k and w_{L-k} = -conj w_k give Im Y_{L-k} = -(Im E_k - Im(w_k O_k)).
+template <int UNR, typename R, typename F>
+__device__ __forceinline__ void line_dst_all(const Cx<R>* Z, int L, const Cx<R>* __restrict__ pw, F out) {
+#pragma unroll UNR
+  for (int k = 1 + threadIdx.x; 2 * k <= L; k += blockDim.x) {
+    const Cx<R> zk = Z[k], zc = Z[L - k];
+    const R Ey = R(0.5) * (zk.y - zc.y);
+    const Cx<R> O{R(0.5) * (zk.y + zc.y), -R(0.5) * (zk.x - zc.x)};
+    const Cx<R> w = pw[k];
+    const R wo = w.x * O.y + w.y * O.x;  // Im(w_k O_k)
+    out(k, -R(0.5) * (Ey + wo));
+    if (2 * k != L) out(L - k, R(0.5) * (Ey - wo));
+  }
 }
 
 // rho at box node (m, jp + 1) of an x line (m = 1 .. Nx): the Eq. 1 divergence of the
@@ -250,8 +256,7 @@ __global__ void __launch_bounds__(DST_THREADS, sizeof(R) == 4 ? 3 : 1) k_dst_rho
     __syncthreads();
     const Cx<R>* Z = line_fft(a, b, p, tw);
     R* out = T1 + (size_t)jp * Nx;
-#pragma unroll 4
-    for (int k = 1 + threadIdx.x; k <= Nx; k += blockDim.x) out[k - 1] = line_dst_at(Z, p.L, p.pw, k);
+    line_dst_all<2>(Z, p.L, p.pw, [&](int k, R v) { out[k - 1] = v; });
     __syncthreads();
   }
 }
@@ -275,8 +280,7 @@ __global__ void __launch_bounds__(DST_THREADS, sizeof(R) == 4 ? 3 : 1) k_dst_sol
     // the divided coefficients, in the other buffer (as reals, index l = 1 .. Ny)
     Cx<R>* c = (Z == a) ? b : a;
     R* cr = reinterpret_cast<R*>(c);
-#pragma unroll 4
-    for (int l = 1 + threadIdx.x; l <= Ny; l += blockDim.x) cr[l] = line_dst_at(Z, p.L, p.pw, l) / (lx + lamy[l - 1]);
+    line_dst_all<2>(Z, p.L, p.pw, [&](int l, R v) { cr[l] = v / (lx + lamy[l - 1]); });
     __syncthreads();
     // the second transform's input: its gather is in place (each thread copies its own
     // entries), its pairs go to Z's buffer, free now
@@ -284,8 +288,7 @@ __global__ void __launch_bounds__(DST_THREADS, sizeof(R) == 4 ? 3 : 1) k_dst_sol
     line_pack<4>(z2, cr, p.L, [&](int m) { return cr[m]; });
     __syncthreads();
     const Cx<R>* Z2 = line_fft(z2, c, p, tw);
-#pragma unroll 4
-    for (int l = 1 + threadIdx.x; l <= Ny; l += blockDim.x) line[l - 1] = line_dst_at(Z2, p.L, p.pw, l);
+    line_dst_all<2>(Z2, p.L, p.pw, [&](int l, R v) { line[l - 1] = v; });
     __syncthreads();
   }
 }
@@ -309,11 +312,10 @@ __global__ void __launch_bounds__(DST_THREADS, sizeof(R) == 4 ? 3 : 1) k_dst_psi
     line_pack<8>(a, reinterpret_cast<R*>(b), p.L, [&](int m) { return line[m - 1]; });
     __syncthreads();
     const Cx<R>* Z = line_fft(a, b, p, tw);
-#pragma unroll 4
-    for (int i = 2 + threadIdx.x; i <= nx - 3; i += blockDim.x) {
-      const int m = i - 1 + bx;  // box column of site i
-      psi[(size_t)j * nx + i] = norm * line_dst_at(Z, p.L, p.pw, m);
-    }
+    line_dst_all<2>(Z, p.L, p.pw, [&](int m, R v) {
+      const int i = m + 1 - bx;  // the site of box column m
+      if (i >= 2 && i <= nx - 3) psi[(size_t)j * nx + i] = norm * v;
+    });
     __syncthreads();
   }
 }

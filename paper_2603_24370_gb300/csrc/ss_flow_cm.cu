@@ -6,8 +6,12 @@
 // before its stage forces and runs at 3 blocks per SM for the registers that takes:
 // on the 4096^2 workload, in one call, pass 2 0.454 -> 0.442 ms (the step 0.894 ->
 // 0.869 ms); at 4 blocks per SM the early loads spill.
+//
+// The descent pass unrolls its vector staging loop by three (0.264 -> 0.253 ms at
+// 4096^2; passes 1 and 2 measured no gain from it).
 #define SS_PF2 1
 #define SS_MINB2 3
+#define SS_VUNR3 3
 #include "ss_flow_kernel.cuh"
 
 namespace ss {

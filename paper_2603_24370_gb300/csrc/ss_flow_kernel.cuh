@@ -82,6 +82,17 @@
 #ifndef SS_E_EVERY
 #define SS_E_EVERY 16
 #endif
+// Vector staging units a thread's loop takes in one unrolled step in passes 1 / 2 / 3
+// (their loads may be issued together).
+#ifndef SS_VUNR1
+#define SS_VUNR1 1
+#endif
+#ifndef SS_VUNR2
+#define SS_VUNR2 1
+#endif
+#ifndef SS_VUNR3
+#define SS_VUNR3 1
+#endif
 // FP32 pass 2 loads a site's stored values for the RK4 combination before computing
 // the site's stage forces (1) or after them (0).
 #ifndef SS_PF2
@@ -623,6 +634,8 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
         constexpr int VW = LO ? (PASS == 1 ? SS_VW1_LO : (PASS == 2 ? SS_VW2_LO : SS_VW3_LO)) : SS_VW_PLAIN;
         using V = typename VecOf<VW>::T;
         constexpr int UW = T::SX / VW, NU = UW * T::SY;
+        constexpr int VUNR = PASS == 1 ? SS_VUNR1 : (PASS == 2 ? SS_VUNR2 : SS_VUNR3);
+#pragma unroll VUNR
         for (int u = tid; u < NU; u += NT) {
           const int ly = u / UW, ux = u - ly * UW;
           const size_t s = (size_t)(y0 - 2 + ly) * nx + (size_t)(x0 - 4 + VW * ux);
