@@ -517,6 +517,37 @@ struct TileCtx {
   int adv;       // pass 3: the step budget allows a new field
 };
 
+// Whether a pass skips the tiles of a problem: it has stopped, or (pass 1) its head is
+// already evaluated, or (pass 2) its step budget is spent, or (descent) both.
+template <int PASS>
+__device__ __forceinline__ int tile_skip(const DevState* st) {
+  const long long steps = st->steps;
+  int skip = (st->converged | st->nonfinite) != 0;
+  if (PASS == 1) skip |= (st->head_step == steps);
+  else if (PASS == 2) skip |= (steps >= st->step_limit);
+  else skip |= (st->head_step == steps && steps >= st->step_limit);  // evaluated, budget spent
+  return skip;
+}
+
+// Batches: the first tile at or after `start` (stepping by `stride`) whose problem the
+// pass does not skip, or `total`. Warp 0 tests 32 candidates per round (one ballot),
+// so a block runs past the tiles of stopped problems without a block barrier per tile.
+// A problem's record changes only when its last tile of the launch arrives, and every
+// candidate is a tile this block has not processed yet, so the test is stable.
+template <typename R, int PASS>
+__device__ __forceinline__ int next_running(const ProbDesc<R>* __restrict__ probs, const int* __restrict__ tile_prob,
+                                            int start, int stride, int total) {
+  const int lane = threadIdx.x & 31;
+  for (long long base = start; base < total; base += 32LL * stride) {
+    const long long c = base + (long long)lane * stride;
+    bool run = false;
+    if (c < total) run = !tile_skip<PASS>(probs[tile_prob[c]].st);
+    const unsigned m = __ballot_sync(0xffffffffu, run);
+    if (m) return (int)(base + (long long)(__ffs(m) - 1) * stride);
+  }
+  return total;
+}
+
 // Thread 0 stages the view of tile t. A problem's record changes only when its last
 // tile of a launch arrives, so while any of its tiles is still unprocessed (as tile
 // t is here) the view stays valid: it may be read ahead of use. A launch over a
@@ -537,11 +568,7 @@ __device__ __forceinline__ void load_tile_ctx(TileCtx<R>& tc, const ProbDesc<R>&
     st = tc.d.st;
   }
   const long long steps = st->steps;
-  int skip = (st->converged | st->nonfinite) != 0;
-  if (PASS == 1) skip |= (st->head_step == steps);
-  else if (PASS == 2) skip |= (steps >= st->step_limit);
-  else skip |= (st->head_step == steps && steps >= st->step_limit);  // evaluated, budget spent
-  tc.skip = skip;
+  tc.skip = tile_skip<PASS>(st);
   tc.cur = (int)(steps & 1);
   tc.arrest = (PASS == 2) && (st->arrest != 0);
   tc.has_prev = (PASS == 1) && (steps > 0);
@@ -588,14 +615,42 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
   // passes 1, 3: running sums over this block's consecutive tiles of one problem
   R es = R(0), ec = R(0), ds = R(0), dc = R(0), gmr = R(0);
 
-  if (tid == 0 && (int)blockIdx.x < total_tiles) load_tile_ctx<R, PASS, ONE>(tcb[0], one, probs, tile_prob, blockIdx.x);
+  // The block's tiles: blockIdx.x, + gridDim.x, ... For a batch, warp 0 finds the next
+  // tile of a running problem (s_next, one slot per buffer) while the block works on
+  // the current one, so stopped problems cost no per-tile barrier.
+  __shared__ int s_next[2];
+  int t = blockIdx.x;
+  if constexpr (ONE) {
+    if (tid == 0 && t < total_tiles) load_tile_ctx<R, PASS, ONE>(tcb[0], one, probs, tile_prob, t);
+  } else {
+    if (tid < 32) {
+      const int t0 = next_running<R, PASS>(probs, tile_prob, blockIdx.x, gridDim.x, total_tiles);
+      if (tid == 0) {
+        s_next[0] = t0;
+        if (t0 < total_tiles) load_tile_ctx<R, PASS, ONE>(tcb[0], one, probs, tile_prob, t0);
+      }
+    }
+    __syncthreads();
+    t = s_next[0];
+  }
   int buf = 0;
-  for (int t = blockIdx.x; t < total_tiles; t += gridDim.x, buf ^= 1) {
+  for (; t < total_tiles; t = ONE ? t + (int)gridDim.x : s_next[buf ^ 1], buf ^= 1) {
     __syncthreads();  // tcb[buf] is staged; the previous tile's shared reads are finished
-    const int tn = t + gridDim.x;
-    if (tid == 0 && tn < total_tiles) load_tile_ctx<R, PASS, ONE>(tcb[buf ^ 1], one, probs, tile_prob, tn);
+    if constexpr (ONE) {
+      const int tn1 = t + gridDim.x;
+      if (tid == 0 && tn1 < total_tiles) load_tile_ctx<R, PASS, ONE>(tcb[buf ^ 1], one, probs, tile_prob, tn1);
+    } else if (tid < 32) {
+      const int tn1 = next_running<R, PASS>(probs, tile_prob, t + gridDim.x, gridDim.x, total_tiles);
+      if (tid == 0) {
+        s_next[buf ^ 1] = tn1;
+        if (tn1 < total_tiles) load_tile_ctx<R, PASS, ONE>(tcb[buf ^ 1], one, probs, tile_prob, tn1);
+      }
+    }
     const TileCtx<R>& tc = tcb[buf];
-    if (tc.skip) continue;  // uniform over the block
+    if (tc.skip) {  // uniform over the block (batches: only if a record changed after the search)
+      if (!ONE) __syncthreads();  // s_next[buf ^ 1] is read by the loop step
+      continue;
+    }
     const ProbDesc<R>& D = ONE ? one : tc.d;
     const int cur = tc.cur;
     const bool arrest = tc.arrest != 0;
@@ -983,6 +1038,7 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
       // completes the count reduces the problem's partials in slot order and decides.
       // (A block that still holds another tile of the problem can never be the last.)
       const ProbDesc<R>& d = D;
+      const int tn = ONE ? t + (int)gridDim.x : s_next[buf ^ 1];  // written before the staging barrier
       const bool flush = ONE ? tn >= total_tiles : !(tn < total_tiles && tcb[buf ^ 1].p == tc.p);
       if (!flush) {
         if (!ONE && tid == 0) {
