@@ -140,6 +140,16 @@
 #ifndef SS_MINB_BATCH
 #define SS_MINB_BATCH 0
 #endif
+// Batched launches may take bounds of their own (default: the single-problem ones).
+#ifndef SS_MINB1B
+#define SS_MINB1B SS_MINB1
+#endif
+#ifndef SS_MINB2B
+#define SS_MINB2B SS_MINB2
+#endif
+#ifndef SS_MINB3B
+#define SS_MINB3B SS_MINB3
+#endif
 
 
 namespace ss {
@@ -586,7 +596,8 @@ __device__ __forceinline__ void load_tile_ctx(TileCtx<R>& tc, const ProbDesc<R>&
 template <int TH, typename R, int PASS, bool ONE>
 constexpr int pass_min_blocks() {
   return (TH == SS_MINB_THEORY && sizeof(R) == 4 && (ONE || SS_MINB_BATCH))
-             ? (PASS == 1 ? SS_MINB1 : (PASS == 2 ? SS_MINB2 : SS_MINB3))
+             ? (ONE ? (PASS == 1 ? SS_MINB1 : (PASS == 2 ? SS_MINB2 : SS_MINB3))
+                    : (PASS == 1 ? SS_MINB1B : (PASS == 2 ? SS_MINB2B : SS_MINB3B)))
              : 1;
 }
 
