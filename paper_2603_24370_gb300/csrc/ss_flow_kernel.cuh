@@ -93,6 +93,21 @@
 #ifndef SS_VUNR3
 #define SS_VUNR3 1
 #endif
+// Vector staging of passes 1 / 2 / 3 leaves out the units no stencil reads (1) or
+// stages whole shared rows (0). At 4096^2 (chiral magnet, compensated; one GPU, both
+// builds) leaving them out took pass 2 from 0.441 to 0.436 ms and the descent pass from
+// 0.254 to 0.251 ms, and slowed pass 1 from 0.424 to 0.433 ms. (Forming pass 2's two
+// stage inputs of a staged site as one packed pair measured 1% slower than the two
+// scalar evaluations.)
+#ifndef SS_VSKIP1
+#define SS_VSKIP1 0
+#endif
+#ifndef SS_VSKIP2
+#define SS_VSKIP2 1
+#endif
+#ifndef SS_VSKIP3
+#define SS_VSKIP3 1
+#endif
 // FP32 pass 2 loads a site's stored values for the RK4 combination before computing
 // the site's stage forces (1) or after them (0).
 #ifndef SS_PF2
@@ -695,15 +710,20 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
       if (vec) {
         // units of VW consecutive sites of one shared row (shared columns VW u ..,
         // sites x0 - 4 + VW u ..): one VW-wide load per stored plane, one VW-wide store
-        // per staged plane; the outermost two columns of each side are staged but unused.
-        // Compensated storage loads twice the planes: narrower units keep them in registers.
+        // per staged plane. The stencils read shared columns OX - 2 .. OX + TX + 1; with
+        // SS_VSKIPn units wholly outside them (the outermost two columns of each side,
+        // with 2-site units) are not staged. Compensated storage loads twice the planes:
+        // narrower units keep them in registers.
         constexpr int VW = LO ? (PASS == 1 ? SS_VW1_LO : (PASS == 2 ? SS_VW2_LO : SS_VW3_LO)) : SS_VW_PLAIN;
         using V = typename VecOf<VW>::T;
-        constexpr int UW = T::SX / VW, NU = UW * T::SY;
+        constexpr bool VSKIP = PASS == 1 ? SS_VSKIP1 : (PASS == 2 ? SS_VSKIP2 : SS_VSKIP3);
+        constexpr int U0 = VSKIP ? (T::OX - 2) / VW : 0;  // first and last unit staged
+        constexpr int U1 = VSKIP ? (T::OX + T::TX + 1) / VW : T::SX / VW - 1;
+        constexpr int UW = U1 - U0 + 1, NU = UW * T::SY;
         constexpr int VUNR = PASS == 1 ? SS_VUNR1 : (PASS == 2 ? SS_VUNR2 : SS_VUNR3);
 #pragma unroll VUNR
         for (int u = tid; u < NU; u += NT) {
-          const int ly = u / UW, ux = u - ly * UW;
+          const int ly = u / UW, ux = U0 + (u - ly * UW);
           const size_t s = (size_t)(y0 - 2 + ly) * nx + (size_t)(x0 - 4 + VW * ux);
           const int so = ly * T::SX + VW * ux;
           const V z = vzero<VW>();
