@@ -100,7 +100,20 @@ struct PConvArgs {
   int tiles;
   int resident;  // 1: all weight groups in shared memory, loaded once
   int wbytes;    // BN * K * 2
+  int halo;      // 1: halo staging (rows of at least 128 pixels, resident weights)
 };
+
+// Halo staging. For rows of at least 128 pixels a tile is 128 pixels of one image row.
+// Per pair of 8-channel groups, two TMA boxes of {8 channels, 130 pixels, 3 rows}
+// (the tile's pixels, one more on each side, the rows above and below; zero outside
+// the image) hold every input the tile's nine taps read. In a box, pixel x of row r
+// sits at r * HROW + x * 16 bytes, so the A operand of tap (dy, dx) is the box read
+// from byte dy * HROW + dx * 16 on: 128 rows at a 16-byte pitch, the K-major
+// no-swizzle layout with the K-adjacent group in the pair's other box (LBO = HSLOT).
+// Against one box per tap and group this moves a third of the bytes from L2.
+constexpr int HROW = 130 * 16;   // one row of a halo box
+constexpr int HBOX = 3 * HROW;   // box bytes: 6240
+constexpr int HSLOT = 49 * 128;  // a box's slot, 128-byte aligned: 6272
 
 template <int BN>
 __global__ void __launch_bounds__(192) k_conv3x3_p(const __grid_constant__ CUtensorMap mx,
@@ -111,7 +124,8 @@ __global__ void __launch_bounds__(192) k_conv3x3_p(const __grid_constant__ CUten
   constexpr int A_BYTES = GPS * BM * 16;
   constexpr int TCOLS = ptcols(BN);
   const bool resident = pa.resident != 0;
-  const int stage = A_BYTES + (resident ? 0 : GPS * BN * 16);
+  const bool halo = pa.halo != 0;  // implies resident
+  const int stage = halo ? 2 * HSLOT : A_BYTES + (resident ? 0 : GPS * BN * 16);
   unsigned char* wsm = smem + P_STAGES * stage;  // resident weights: group g at g * BN * 16
   __shared__ __align__(8) uint64_t full[P_STAGES], empty[P_STAGES], tfull[2], tempty[2], wbar;
   __shared__ uint32_t tmem_base;
@@ -125,7 +139,7 @@ __global__ void __launch_bounds__(192) k_conv3x3_p(const __grid_constant__ CUten
   const int tpi = (H / rows) * tpr;
   const int cg = a.Cin >> 3;
   const int G = 9 * cg;
-  const int nkb = (G + GPS - 1) / GPS;
+  const int nkb = halo ? cg / 2 : (G + GPS - 1) / GPS;  // ring entries per tile
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < P_STAGES; ++s) {
@@ -167,6 +181,12 @@ __global__ void __launch_bounds__(192) k_conv3x3_p(const __grid_constant__ CUten
             break;
           }
           unsigned char* sa = smem + s * stage;
+          if (halo) {  // channel groups 2 kb and 2 kb + 1, every tap
+            mbar_arrive_expect_tx(&full[s], (uint32_t)(2 * HBOX));
+            tma_load_4d(sa, &mx, &full[s], 16 * kb, x0 - 1, y0 - 1, n);
+            tma_load_4d(sa + HSLOT, &mx, &full[s], 16 * kb + 8, x0 - 1, y0 - 1, n);
+            continue;
+          }
           unsigned char* sb = sa + A_BYTES;
           const int g0 = kb * GPS, ng = min(GPS, G - g0);
           mbar_arrive_expect_tx(&full[s], (uint32_t)(ng * (BM + (resident ? 0 : BN)) * 16));
@@ -213,6 +233,15 @@ __global__ void __launch_bounds__(192) k_conv3x3_p(const __grid_constant__ CUten
           }
           fence_after_sync();
           const uint32_t sa = smem_u32(smem + s * stage), sb = sa + A_BYTES;
+          if (halo) {
+            for (int tap = 0; tap < 9; ++tap) {
+              const uint64_t ad = sdesc(sa + (uint32_t)((tap / 3) * HROW + (tap % 3) * 16), HSLOT, 128);
+              const uint64_t bd = sdesc(wbase + (uint32_t)((tap * cg + 2 * kb) * (BN * 16)), BN * 16, 128);
+              mma_bf16(acc, ad, bd, idesc, (kb > 0 || tap > 0) ? 1u : 0u);
+            }
+            mma_commit(&empty[s]);
+            continue;
+          }
           const int g0 = kb * GPS, ng = min(GPS, G - g0);
           for (int j = 0; j < ng; j += 2) {
             const uint64_t ad = sdesc(sa + j * (BM * 16), BM * 16, 128);
@@ -540,6 +569,174 @@ __global__ void __launch_bounds__(128) k_wgrad_sw(const __grid_constant__ CUtens
   }
 }
 
+// ---------------------------------------------------------------- weight gradient, tap rows
+// For rows of at least 64 pixels and 9 Cin <= 512: the M rows of the contraction are
+// the (tap, input channel) pairs, N the output channels, K 64 pixels of one image row
+// per K-block. The nine shifted input boxes of a K-block ({64 pixels, Cin channels}
+// each, 128-byte swizzle) are stacked, so rows 128 g .. 128 g + 127 of the stack are
+// the A operand of accumulator g; the last accumulator runs past the stack into bytes
+// whose products land in TMEM rows that are never read (the allocation is padded so
+// those reads stay inside it). The output-gradient box ({64 pixels, Cout channels}) is
+// B. Against one 128-row tile of output channels per tap (k_wgrad_sw) this issues
+// ceil(9 Cin / 128) instead of nine MMAs per K step and loads no zero rows.
+struct WgRowArgs {
+  int N, H, W, Cout, Cin;
+  int kb_per_cta, total_kb;
+  int stages, groups, stage_bytes, tcols;
+  float* dw;
+  int* err;
+};
+
+template <int BN>
+__global__ void __launch_bounds__(128) k_wgrad_rows(const __grid_constant__ CUtensorMap mdy,
+                                                    const __grid_constant__ CUtensorMap mx0,
+                                                    const __grid_constant__ CUtensorMap mx1,
+                                                    const __grid_constant__ CUtensorMap mx2, const WgRowArgs a) {
+  extern __shared__ unsigned char smraw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+  constexpr int MAXS = 4;
+  __shared__ __align__(8) uint64_t full[MAXS], empty[MAXS], accum;
+  __shared__ uint32_t tmem_base;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int S = a.stages, G = a.groups, STAGE = a.stage_bytes;
+  const int Cin = a.Cin, XB = Cin * 128;  // one tap's box
+  const int A_BYTES = 9 * XB;             // a multiple of 1 KB (Cin % 16 == 0)
+  const int kb0 = blockIdx.x * a.kb_per_cta;
+  const int kb1 = min(kb0 + a.kb_per_cta, a.total_kb);
+  const int nkb = kb1 > kb0 ? kb1 - kb0 : 0;
+  const int HW = a.H * a.W;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < MAXS; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(&accum, 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(&tmem_base, (uint32_t)a.tcols);
+    tmem_relinquish();
+  }
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = tmem_base;
+
+  if (warp == 0 && lane == 0) {  // ---- producer
+    int issued = 0;
+    for (int i = 0; i < nkb; ++i) {
+      const int s = i % S;
+      if (!mbar_wait(&empty[s], (uint32_t)(((i / S) & 1) ^ 1), WAIT_NS)) {
+        record_fail(a.err, 41);
+        break;
+      }
+      unsigned char* sa = smem + s * STAGE;
+      const int p0 = (kb0 + i) * 64;
+      const int n = p0 / HW, rem = p0 - n * HW;
+      const int y = rem / a.W, x = rem - y * a.W;
+      mbar_arrive_expect_tx(&full[s], (uint32_t)(A_BYTES + BN * 128));
+#pragma unroll 1
+      for (int tap = 0; tap < 9; ++tap) {
+        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+        const CUtensorMap* mx = dx < 0 ? &mx0 : (dx == 0 ? &mx1 : &mx2);
+        tma_load_4d(sa + tap * XB, mx, &full[s], x, y + dy, n, 0);
+      }
+      tma_load_4d(sa + A_BYTES, &mdy, &full[s], x, y, n, 0);
+      issued = i + 1;
+    }
+    for (int s = 0; s < S && s < issued; ++s) {
+      const int last = s + S * ((issued - 1 - s) / S);
+      mbar_wait(&full[s], (uint32_t)((last / S) & 1), WAIT_NS);
+    }
+  } else if (warp == 1 && lane == 0) {  // ---- MMA issuer
+    constexpr uint32_t idesc = idesc_bf16(BM, BN);
+    for (int i = 0; i < nkb; ++i) {
+      const int s = i % S;
+      if (!mbar_wait(&full[s], (uint32_t)((i / S) & 1), WAIT_NS)) {
+        record_fail(a.err, 42);
+        break;
+      }
+      fence_after_sync();
+      const uint32_t sa = smem_u32(smem + s * STAGE), sb = sa + (uint32_t)A_BYTES;
+      for (int g = 0; g < G; ++g) {
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+          mma_bf16(tmem + (uint32_t)(g * BN), sdesc_sw128(sa + (uint32_t)(g * BM * 128 + kk * 32)),
+                   sdesc_sw128(sb + kk * 32), idesc, (i > 0 || kk > 0) ? 1u : 0u);
+      }
+      mma_commit(&empty[s]);
+    }
+    mma_commit(&accum);
+  }
+  __syncwarp();
+
+  bool ok = nkb > 0 ? mbar_wait(&accum, 0, WAIT_NS) : false;
+  ok = __all_sync(0xffffffffu, ok);
+  fence_after_sync();
+  if (!ok) {
+    if (lane == 0 && nkb > 0) record_fail(a.err, 43);
+  } else {
+    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+    for (int g = 0; g < G; ++g) {
+      const int r = g * BM + warp * 32 + lane;  // stack row: (tap, input channel)
+      const int tap = r / Cin, ci = r - tap * Cin;
+#pragma unroll 1
+      for (int c = 0; c < BN; c += 16) {
+        float v[16];
+        tmem_ld16(trow + (uint32_t)(g * BN + c), v);
+        if (r < 9 * Cin) {  // a warp's lanes: consecutive input channels of one entry row
+          float* d = a.dw + (size_t)tap * Cin + ci;
+#pragma unroll
+          for (int q = 0; q < 16; ++q) atomicAdd(d + (size_t)(c + q) * 9 * Cin, v[q]);
+        }
+      }
+    }
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    fence_after_sync();
+    tmem_dealloc(tmem, (uint32_t)a.tcols);
+  }
+}
+
+template <int BN>
+cudaError_t wgrad_rows_launch(const CUtensorMap& mdy, const CUtensorMap* mx, WgRowArgs a, cudaStream_t s) {
+  const int A_BYTES = 9 * a.Cin * 128;
+  a.groups = (9 * a.Cin + BM - 1) / BM;
+  a.stage_bytes = A_BYTES + BN * 128;  // a multiple of 1 KB
+  int cols = a.groups * BN;
+  a.tcols = cols <= 32 ? 32 : cols <= 64 ? 64 : cols <= 128 ? 128 : cols <= 256 ? 256 : 512;
+  int stages = (100 * 1024) / a.stage_bytes;
+  stages = stages < 2 ? 2 : (stages > 4 ? 4 : stages);
+  a.stages = stages;
+  // the last accumulator's A rows run up to groups x 16 KB past the last stage's start
+  const int over = a.groups * BM * 128 - a.stage_bytes;
+  const size_t smem = (size_t)stages * a.stage_bytes + (over > 0 ? over : 0) + 1024;
+  static int max_smem_set = 0;
+  if ((int)smem > max_smem_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_wgrad_rows<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    max_smem_set = (int)smem;
+  }
+  int dev = 0, nsm = 0, sm_smem = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  int per_sm = sm_smem / (int)(smem + 1024);
+  if (per_sm > 512 / a.tcols) per_sm = 512 / a.tcols;
+  if (per_sm > 2) per_sm = 2;
+  if (per_sm < 1) per_sm = 1;
+  int splits = nsm * per_sm;
+  a.kb_per_cta = (a.total_kb + splits - 1) / splits;
+  if (a.kb_per_cta < 4) a.kb_per_cta = 4;
+  splits = (a.total_kb + a.kb_per_cta - 1) / a.kb_per_cta;
+  k_wgrad_rows<BN><<<splits, 128, smem, s>>>(mdy, mx[0], mx[1], mx[2], a);
+  return cudaGetLastError();
+}
+
 template <int BN, int TPC>
 cudaError_t wgrad_sw_launch(const CUtensorMap& mdy, const CUtensorMap* mx, WgSwArgs a, cudaStream_t s) {
   constexpr int STAGE = BM * 128 + TPC * BN * 128;
@@ -596,12 +793,13 @@ cudaError_t make_map(CUtensorMap* m, const void* base, int r, const cuuint64_t* 
 }
 
 template <int BN>
-cudaError_t conv_launch_p(const CUtensorMap& mx, const CUtensorMap& mw, const ConvArgs& a, int tiles, int K,
-                          cudaStream_t s) {
-  PConvArgs pa{a, tiles, 0, BN * K * 2};
+cudaError_t conv_launch_p(const CUtensorMap& mx, const CUtensorMap* mxh, const CUtensorMap& mw, const ConvArgs& a,
+                          int tiles, int K, cudaStream_t s) {
+  PConvArgs pa{a, tiles, 0, BN * K * 2, 0};
   pa.resident = pa.wbytes <= W_RESIDENT_MAX ? 1 : 0;
-  const size_t smem = (size_t)P_STAGES * (GPS * BM * 16 + (pa.resident ? 0 : GPS * BN * 16)) +
-                      (pa.resident ? (size_t)pa.wbytes : 0) + 1024;
+  pa.halo = (mxh != nullptr && pa.resident) ? 1 : 0;
+  const size_t stage = pa.halo ? (size_t)2 * HSLOT : (size_t)GPS * BM * 16 + (pa.resident ? 0 : GPS * BN * 16);
+  const size_t smem = (size_t)P_STAGES * stage + (pa.resident ? (size_t)pa.wbytes : 0) + 1024;
   static int max_smem_set = 0;  // per instantiation, under g_attr_mu
   if ((int)smem > max_smem_set) {
     cudaError_t e = cudaFuncSetAttribute(k_conv3x3_p<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -620,7 +818,7 @@ cudaError_t conv_launch_p(const CUtensorMap& mx, const CUtensorMap& mw, const Co
   if (per_sm > 2048 / 192) per_sm = 2048 / 192;
   if (per_sm < 1) per_sm = 1;
   const int grid = tiles < nsm * per_sm ? tiles : nsm * per_sm;
-  k_conv3x3_p<BN><<<grid, 192, smem, s>>>(mx, mw, pa);
+  k_conv3x3_p<BN><<<grid, 192, smem, s>>>(pa.halo ? *mxh : mx, mw, pa);
   return cudaGetLastError();
 }
 
@@ -659,6 +857,13 @@ cudaError_t conv3x3_tc(const Act& x, const void* w, int Cout, int mode, const fl
   const cuuint32_t xbox[4] = {8, (cuuint32_t)Wt, (cuuint32_t)(128 / Wt), 1};
   cudaError_t e = make_map(&mx, xb, 4, xd, xs, xbox);
   if (e != cudaSuccess) return e;
+  CUtensorMap mxh;  // halo boxes (rows of at least 128 pixels)
+  const bool halo = W % 128 == 0;
+  if (halo) {
+    const cuuint32_t hbox[4] = {8, 130, 3, 1};
+    e = make_map(&mxh, xb, 4, xd, xs, hbox);
+    if (e != cudaSuccess) return e;
+  }
   const int K = 9 * x.C;
   const cuuint64_t wd[2] = {(cuuint64_t)K, (cuuint64_t)Cout};
   const cuuint64_t ws[1] = {(cuuint64_t)K * 2};
@@ -670,7 +875,7 @@ cudaError_t conv3x3_tc(const Act& x, const void* w, int Cout, int mode, const fl
     const cuuint32_t wbox[2] = {8, (cuuint32_t)BNV};        \
     e = make_map(&mw, w, 2, wd, ws, wbox);                  \
     if (e != cudaSuccess) return e;                         \
-    return conv_launch_p<BNV>(mx, mw, a, tiles, K, s);      \
+    return conv_launch_p<BNV>(mx, halo ? &mxh : nullptr, mw, a, tiles, K, s); \
   }
   switch (Cout) {
     SS_CONV_CASE(16)
@@ -695,6 +900,25 @@ cudaError_t wgrad3x3_tc(const void* dyT, const void* xT, int N, int H, int W, in
   const cuuint64_t st[3] = {(cuuint64_t)W * 2, (cuuint64_t)W * H * 2, (cuuint64_t)P * 2};
   const cuuint64_t xd[4] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)N, (cuuint64_t)Cin};
   cudaError_t e;
+  if (W % 64 == 0 && Cin % 16 == 0 && Cin <= 48 && (Cout == 16 || Cout == 32 || Cout == 48 || Cout == 96)) {
+    // (tap, input channel) rows: 64-pixel K-blocks in 128-byte-swizzled boxes
+    WgRowArgs a{N, H, W, Cout, Cin, 0, (int)(P / 64), 0, 0, 0, 0, dw, err};
+    const cuuint32_t xbox[4] = {64, 1, 1, (cuuint32_t)Cin};
+    for (int d = 0; d < 3; ++d) {
+      e = make_map(&mx[d], static_cast<const char*>(xT) + (size_t)d * Cin * P * 2, 4, xd, st, xbox, true);
+      if (e != cudaSuccess) return e;
+    }
+    const cuuint32_t dbox[4] = {64, 1, 1, (cuuint32_t)Cout};
+    e = make_map(&mdy, dyT, 4, dd, st, dbox, true);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(g_attr_mu);
+    switch (Cout) {
+      case 16: return wgrad_rows_launch<16>(mdy, mx, a, s);
+      case 32: return wgrad_rows_launch<32>(mdy, mx, a, s);
+      case 48: return wgrad_rows_launch<48>(mdy, mx, a, s);
+      default: return wgrad_rows_launch<96>(mdy, mx, a, s);
+    }
+  }
   if (W % 64 == 0) {  // 64-pixel K-blocks in 128-byte-swizzled boxes
     const cuuint32_t dbox[4] = {64, 1, 1, 128};
     e = make_map(&mdy, dyT, 4, dd, st, dbox, true);

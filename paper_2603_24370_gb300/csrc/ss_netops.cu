@@ -208,39 +208,64 @@ __global__ void k_shifted_transpose_rows(const Act x, __nv_bfloat16* __restrict_
 }
 
 // dy (FP32 NHWC) -> masked gradient: BF16 NHWC (dyb) and channel-major (dyT), and the
-// bias gradient. A block takes 128 pixels at a time, stages the BF16 values as
-// [C][128] in shared memory for the channel-major writes, and sums each channel's
-// FP32 values there (one atomic per channel per block at the end).
-constexpr int RG_TP = 128;
+// bias gradient. A block takes 128 pixels at a time: four channels per thread in NHWC
+// order (16-byte loads of dy, 8-byte loads of the mask and stores of dyb), staged in
+// shared memory as [128][C + 1] FP32 (the odd pitch keeps the channel-major reads free
+// of bank conflicts), then written channel-major. A warp's 32 channel-major values
+// share one channel, so they are summed by shuffles into one shared atomic; one
+// global atomic per channel per block at the end.
+constexpr int RG_TP = 128;  // pixels per tile, a multiple of 32
 __global__ void k_relu_grad_tiles(const float* __restrict__ dy, const Act yact, int has_mask, size_t P, int C,
                                   __nv_bfloat16* __restrict__ dyb, __nv_bfloat16* __restrict__ dyT,
                                   float* __restrict__ dbias) {
   extern __shared__ unsigned char rg_smem[];
-  float* g = reinterpret_cast<float*>(rg_smem);                       // [RG_TP][C] FP32
-  float* csum = g + RG_TP * C;                                        // [C]
+  const int GS = C + 1;
+  float* g = reinterpret_cast<float*>(rg_smem);  // [RG_TP][GS] FP32
+  float* csum = g + RG_TP * GS;                  // [C]
   for (int c = threadIdx.x; c < C; c += blockDim.x) csum[c] = 0.f;
+  const int C4 = C / 4;
   const size_t ntiles = (P + RG_TP - 1) / RG_TP;
   for (size_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const size_t pix0 = tile * RG_TP;
     const int np = (int)((P - pix0) < (size_t)RG_TP ? (P - pix0) : (size_t)RG_TP);
     __syncthreads();
-    for (int i = threadIdx.x; i < np * C; i += blockDim.x) {  // NHWC order: coalesced
-      const int pp = i / C, c = i - pp * C;
+    for (int i = threadIdx.x; i < np * C4; i += blockDim.x) {  // NHWC order: coalesced
+      const int pp = i / C4, c = (i - pp * C4) * 4;
       const size_t e = (pix0 + pp) * C + c;
-      float v = dy[e];
-      if (has_mask && !(__bfloat162float(act_ptr(yact, pix0 + pp)[c]) > 0.f)) v = 0.f;
-      g[pp * C + c] = v;
-      dyb[e] = __float2bfloat16(v);
+      float4 v = *reinterpret_cast<const float4*>(dy + e);
+      if (has_mask) {
+        const uint2 m = *reinterpret_cast<const uint2*>(act_ptr(yact, pix0 + pp) + c);
+        const float2 m01 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&m.x));
+        const float2 m23 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&m.y));
+        if (!(m01.x > 0.f)) v.x = 0.f;
+        if (!(m01.y > 0.f)) v.y = 0.f;
+        if (!(m23.x > 0.f)) v.z = 0.f;
+        if (!(m23.y > 0.f)) v.w = 0.f;
+      }
+      float* gr = g + pp * GS + c;
+      gr[0] = v.x;
+      gr[1] = v.y;
+      gr[2] = v.z;
+      gr[3] = v.w;
+      __nv_bfloat162 b01 = __floats2bfloat162_rn(v.x, v.y), b23 = __floats2bfloat162_rn(v.z, v.w);
+      uint2 o;
+      o.x = *reinterpret_cast<uint32_t*>(&b01);
+      o.y = *reinterpret_cast<uint32_t*>(&b23);
+      *reinterpret_cast<uint2*>(dyb + e) = o;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < C * np; i += blockDim.x) {  // channel-major: coalesced
       const int c = i / np, pp = i - c * np;
-      dyT[(size_t)c * P + pix0 + pp] = __float2bfloat16(g[pp * C + c]);
-    }
-    for (int c = threadIdx.x; c < C; c += blockDim.x) {  // per-channel sums of this tile
-      float acc = 0.f;
-      for (int pp = 0; pp < np; ++pp) acc += g[pp * C + c];
-      csum[c] += acc;
+      const float v = g[pp * GS + c];
+      dyT[(size_t)c * P + pix0 + pp] = __float2bfloat16(v);
+      if (np == RG_TP) {  // the warp's lanes hold 32 pixels of channel c
+        float w = v;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+        if ((threadIdx.x & 31) == 0) atomicAdd(&csum[c], w);
+      } else {
+        atomicAdd(&csum[c], v);
+      }
     }
   }
   __syncthreads();
@@ -270,8 +295,8 @@ cudaError_t relu_grad(const float* dy, const Act* y_act, int N, int H, int W, in
   const size_t P = (size_t)N * H * W;
   Act y{};
   if (y_act) y = *y_act;
-  const size_t smem = (size_t)(RG_TP + 1) * C * sizeof(float);
-  if (smem <= 48 * 1024) {
+  const size_t smem = ((size_t)RG_TP * (C + 1) + C) * sizeof(float);
+  if (smem <= 48 * 1024 && C % 4 == 0) {
     const size_t ntiles = (P + RG_TP - 1) / RG_TP;
     int blocks = grid_for(ntiles * 256);
     if ((size_t)blocks > ntiles) blocks = (int)ntiles;

@@ -60,6 +60,8 @@ CONV_CASES = [  # (N, H, W, Cin, Cout)
     (2, 8, 64, 32, 48),
     (1, 4, 128, 48, 80),
     (1, 2, 256, 16, 96),
+    (2, 3, 128, 32, 16),
+    (1, 3, 384, 16, 48),
     (2, 16, 16, 144, 48),
     (1, 8, 32, 80, 144),
 ]
@@ -93,7 +95,9 @@ def test_conv_forward_matches_oracle(S, case, mode):
                                   (2, 16, 16, 144, 48), (2, 32, 32, 80, 32), (1, 8, 32, 96, 16),
                                   # rows of >= 64 pixels: 64-pixel swizzled K-blocks, all taps per CTA
                                   (2, 3, 128, 16, 16), (1, 4, 64, 80, 32), (1, 2, 64, 144, 48),
-                                  (2, 2, 64, 96, 96), (1, 6, 256, 16, 48)])
+                                  (2, 2, 64, 96, 96), (1, 6, 256, 16, 48),
+                                  # (tap, input channel) rows for 9 Cin <= 512
+                                  (2, 4, 64, 16, 16), (1, 2, 128, 48, 16), (1, 3, 64, 32, 96)])
 def test_conv_weight_gradient_matches_oracle(S, case):
     N, H, W, Cin, Cout = case
     rng = np.random.default_rng(sum(case))
