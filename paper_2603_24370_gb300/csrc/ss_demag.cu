@@ -16,7 +16,7 @@
 // odd extension y = (0, s_1 .. s_N, 0, -s_N .. -s_1) of length 2L, L = N + 1; that real
 // DFT is one complex DFT of length L of z_n = y_2n + i y_2n+1, unpacked as
 //   Y_k = E_k + e^{-i pi k / L} O_k,  E_k = (Z_k + conj Z_{L-k}) / 2,  O_k = (Z_k - conj Z_{L-k}) / 2i.
-// The complex DFT is a Stockham autosort FFT (radix 8, 4, 2, 3, 5, 7 stages, L being
+// The complex DFT is a Stockham autosort FFT (radix 16, 8, 4, 2, 3, 5, 7 stages, L being
 // 7-smooth) held in shared memory: one thread block transforms one line, reading it
 // once from global memory and writing it once. The solve is three line kernels and two
 // tiled transposes:
@@ -39,6 +39,16 @@ namespace ss {
 namespace {
 
 constexpr int DST_THREADS = 256;
+// Radix-16 Stockham stages where the length allows (1) or radix 8 at most (0), and padded
+// shared line buffers (1) or dense ones (0). The Poisson solve at 4096^2 (FP32, one GPU,
+// all four builds): dense radix 8 0.778 ms, dense radix 16 0.817 ms, padded radix 8 0.724
+// ms, padded radix 16 0.648 ms.
+#ifndef SS_DST_R16
+#define SS_DST_R16 1
+#endif
+#ifndef SS_DST_PAD
+#define SS_DST_PAD 1
+#endif
 constexpr int TW_FINE = 64;  // twiddles as coarse x fine factors: e^{-2 pi i t / L} = C[t / 64] F[t % 64]
 constexpr int DST_MAX_STAGES = 24;
 
@@ -75,6 +85,12 @@ struct Tw {
   __device__ __forceinline__ Cx<R> operator[](int t) const { return cmul(c[t / TW_FINE], f[t % TW_FINE]); }
 };
 
+// Shared line buffers hold element i at pz(i): one unused slot after every 16, so that a
+// first stage's writes (each thread's RAD outputs at consecutive positions) and the
+// strided accesses of later stages fall on different banks.
+__host__ __device__ __forceinline__ int pz(int i) { return SS_DST_PAD ? i + (i >> 4) : i; }
+__host__ __device__ __forceinline__ int pad_len(int L) { return SS_DST_PAD ? L + (L >> 4) + 1 : L; }
+
 // j / Ns for the butterfly indices j < L <= 2^14 of a stage: with m = ceil(2^32 / Ns),
 // floor(j m / 2^32) = floor(j / Ns) exactly because j Ns < 2^32.
 __device__ __forceinline__ int div_ns(int j, int Ns, unsigned m) { return Ns == 1 ? j : (int)__umulhi((unsigned)j, m); }
@@ -88,14 +104,24 @@ __device__ __forceinline__ void stockham_stage(const Cx<R>* __restrict__ src, Cx
   const int nb = L / RAD;
   const int step = L / (Ns * RAD);
   constexpr int UNR = (RAD <= 4 || RAD == 8) ? 2 : 1;  // two butterflies in flight where registers allow
+  // radix-16 internal twiddles W16^1 and W16^3: (cos pi/8, -sin pi/8) and (sin pi/8, -cos pi/8)
+  const R c8 = R(0.92387953251128675613), s8 = R(0.38268343236508977173), h = R(0.70710678118654752440);
 #pragma unroll UNR
   for (int j = threadIdx.x; j < nb; j += blockDim.x) {
     const int jd = div_ns(j, Ns, magic);
     const int jm = j - jd * Ns;
     Cx<R> v[RAD];
 #pragma unroll
-    for (int r = 0; r < RAD; ++r) v[r] = src[j + r * nb];
-    if (RAD == 8) {  // w^1, w^2, w^4 from the table, the other powers as their products
+    for (int r = 0; r < RAD; ++r) v[r] = src[pz(j + r * nb)];
+    if (RAD == 16) {  // w^1, w^2, w^4, w^8 from the table, the other powers as their products
+      const int t1 = jm * step;
+      const Cx<R> w1 = tw[t1], w2 = tw[2 * t1], w4 = tw[4 * t1], w8 = tw[8 * t1];
+      const Cx<R> w3 = cmul(w1, w2), w5 = cmul(w1, w4), w6 = cmul(w2, w4), w7 = cmul(w3, w4);
+      const Cx<R> w[16] = {Cx<R>{R(1), R(0)}, w1, w2, w3, w4, w5, w6, w7, w8, cmul(w1, w8), cmul(w2, w8),
+                           cmul(w3, w8), cmul(w4, w8), cmul(w5, w8), cmul(w6, w8), cmul(w7, w8)};
+#pragma unroll
+      for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], w[r]);
+    } else if (RAD == 8) {  // w^1, w^2, w^4 from the table, the other powers as their products
       const int t1 = jm * step;
       const Cx<R> w1 = tw[t1], w2 = tw[2 * t1], w4 = tw[4 * t1];
       const Cx<R> w3 = cmul(w1, w2);
@@ -111,8 +137,38 @@ __device__ __forceinline__ void stockham_stage(const Cx<R>* __restrict__ src, Cx
       for (int r = 1; r < RAD; ++r) v[r] = cmul(v[r], tw[jm * r * step]);
     }
     Cx<R> o[RAD];
-    if (RAD == 8) {  // three radix-2 levels; W8 = (1 - i) / sqrt 2, W8^3 = (-1 - i) / sqrt 2
-      const R h = R(0.70710678118654752440);
+    if (RAD == 16) {  // 4 x 4: n = n2 + 4 n1, k = k1 + 4 k2
+      // 4-point DFTs over n1, then the factors W16^(n2 k1), then 4-point DFTs over n2
+      Cx<R> A[4][4];
+#pragma unroll
+      for (int n2 = 0; n2 < 4; ++n2) {
+        const Cx<R> a = cadd(v[n2], v[n2 + 8]), b = csub(v[n2], v[n2 + 8]);
+        const Cx<R> c = cadd(v[n2 + 4], v[n2 + 12]), d = csub(v[n2 + 4], v[n2 + 12]);
+        A[n2][0] = cadd(a, c);
+        A[n2][2] = csub(a, c);
+        A[n2][1] = Cx<R>{b.x + d.y, b.y - d.x};  // b - i d
+        A[n2][3] = Cx<R>{b.x - d.y, b.y + d.x};  // b + i d
+      }
+      auto mulw = [](Cx<R> z, R wr, R wi) { return Cx<R>{z.x * wr - z.y * wi, z.x * wi + z.y * wr}; };
+      A[1][1] = mulw(A[1][1], c8, -s8);                          // W16^1
+      A[1][2] = mulw(A[1][2], h, -h);                            // W16^2
+      A[1][3] = mulw(A[1][3], s8, -c8);                          // W16^3
+      A[2][1] = mulw(A[2][1], h, -h);                            // W16^2
+      A[2][2] = Cx<R>{A[2][2].y, -A[2][2].x};                    // W16^4 = -i
+      A[2][3] = mulw(A[2][3], -h, -h);                           // W16^6
+      A[3][1] = mulw(A[3][1], s8, -c8);                          // W16^3
+      A[3][2] = mulw(A[3][2], -h, -h);                           // W16^6
+      A[3][3] = mulw(A[3][3], -c8, s8);                          // W16^9
+#pragma unroll
+      for (int k1 = 0; k1 < 4; ++k1) {
+        const Cx<R> a = cadd(A[0][k1], A[2][k1]), b = csub(A[0][k1], A[2][k1]);
+        const Cx<R> c = cadd(A[1][k1], A[3][k1]), d = csub(A[1][k1], A[3][k1]);
+        o[k1] = cadd(a, c);
+        o[k1 + 8] = csub(a, c);
+        o[k1 + 4] = Cx<R>{b.x + d.y, b.y - d.x};   // b - i d
+        o[k1 + 12] = Cx<R>{b.x - d.y, b.y + d.x};  // b + i d
+      }
+    } else if (RAD == 8) {  // three radix-2 levels; W8 = (1 - i) / sqrt 2, W8^3 = (-1 - i) / sqrt 2
       auto mi = [](Cx<R> z) { return Cx<R>{z.y, -z.x}; };  // z * (-i)
       const Cx<R> a0 = cadd(v[0], v[4]), a1 = csub(v[0], v[4]), a2 = cadd(v[2], v[6]), a3 = mi(csub(v[2], v[6]));
       const Cx<R> a4 = cadd(v[1], v[5]), a5 = csub(v[1], v[5]), a6 = cadd(v[3], v[7]), a7 = mi(csub(v[3], v[7]));
@@ -148,7 +204,7 @@ __device__ __forceinline__ void stockham_stage(const Cx<R>* __restrict__ src, Cx
     }
     const int idx = jd * Ns * RAD + jm;
 #pragma unroll
-    for (int k = 0; k < RAD; ++k) dst[idx + k * Ns] = o[k];
+    for (int k = 0; k < RAD; ++k) dst[pz(idx + k * Ns)] = o[k];
   }
 }
 
@@ -168,7 +224,8 @@ __device__ Cx<R>* line_fft(Cx<R>* a, Cx<R>* b, const LinePlan<R>& p, const Tw<R>
   for (int s = 0; s < p.nst; ++s) {
     const int rad = p.rad[s];
     const unsigned m = p.magic[s];
-    if (rad == 8) stockham_stage<8, R>(a, b, p.L, Ns, m, tw);
+    if (rad == 16) stockham_stage<16, R>(a, b, p.L, Ns, m, tw);
+    else if (rad == 8) stockham_stage<8, R>(a, b, p.L, Ns, m, tw);
     else if (rad == 4) stockham_stage<4, R>(a, b, p.L, Ns, m, tw);
     else if (rad == 2) stockham_stage<2, R>(a, b, p.L, Ns, m, tw);
     else if (rad == 3) stockham_stage<3, R>(a, b, p.L, Ns, m, tw);
@@ -194,7 +251,7 @@ __device__ __forceinline__ void line_pack(Cx<R>* z, R* tmp, int L, S s) {
     if (m == 0 || m == L) return R(0);
     return m < L ? tmp[m] : -tmp[2 * L - m];
   };
-  for (int n = threadIdx.x; n < L; n += blockDim.x) z[n] = Cx<R>{y(2 * n), y(2 * n + 1)};
+  for (int n = threadIdx.x; n < L; n += blockDim.x) z[pz(n)] = Cx<R>{y(2 * n), y(2 * n + 1)};
 }
 
 // Every DST_k, k = 1 .. L - 1, to out(k, value), two at a time: k and L - k share the
@@ -204,7 +261,7 @@ template <int UNR, typename R, typename F>
 __device__ __forceinline__ void line_dst_all(const Cx<R>* Z, int L, const Cx<R>* __restrict__ pw, F out) {
 #pragma unroll UNR
   for (int k = 1 + threadIdx.x; 2 * k <= L; k += blockDim.x) {
-    const Cx<R> zk = Z[k], zc = Z[L - k];
+    const Cx<R> zk = Z[pz(k)], zc = Z[pz(L - k)];
     const R Ey = R(0.5) * (zk.y - zc.y);
     const Cx<R> O{R(0.5) * (zk.y + zc.y), -R(0.5) * (zk.x - zc.x)};
     const Cx<R> w = pw[k];
@@ -246,8 +303,8 @@ __global__ void __launch_bounds__(DST_THREADS, sizeof(R) == 4 ? 3 : 1) k_dst_rho
                                                               const LinePlan<R> p, R* __restrict__ T1) {
   extern __shared__ __align__(16) unsigned char dsm[];
   Cx<R>* a = reinterpret_cast<Cx<R>*>(dsm);
-  Cx<R>* b = a + p.L;
-  const Tw<R> tw = stage_twiddles(b + p.L, p);
+  Cx<R>* b = a + pad_len(p.L);
+  const Tw<R> tw = stage_twiddles(b + pad_len(p.L), p);
   const int cur = (int)(st->steps & 1);
   RhoRow<R> rr{cur ? phi1 : phi0, cur ? lo1 : lo0, nx, ny, bx, by, 0, plane, i12dx, i12dy};
   for (int jp = blockIdx.x; jp < Ny; jp += gridDim.x) {
@@ -269,8 +326,8 @@ __global__ void __launch_bounds__(DST_THREADS, sizeof(R) == 4 ? 3 : 1) k_dst_sol
                                                                 const LinePlan<R> p) {
   extern __shared__ __align__(16) unsigned char dsm[];
   Cx<R>* a = reinterpret_cast<Cx<R>*>(dsm);
-  Cx<R>* b = a + p.L;
-  const Tw<R> tw = stage_twiddles(b + p.L, p);
+  Cx<R>* b = a + pad_len(p.L);
+  const Tw<R> tw = stage_twiddles(b + pad_len(p.L), p);
   for (int r = blockIdx.x; r < Nx; r += gridDim.x) {
     R* line = T2 + (size_t)r * Ny;
     const R lx = lamx[r];
@@ -302,8 +359,8 @@ __global__ void __launch_bounds__(DST_THREADS, sizeof(R) == 4 ? 3 : 1) k_dst_psi
                                                               R* __restrict__ psi1) {
   extern __shared__ __align__(16) unsigned char dsm[];
   Cx<R>* a = reinterpret_cast<Cx<R>*>(dsm);
-  Cx<R>* b = a + p.L;
-  const Tw<R> tw = stage_twiddles(b + p.L, p);
+  Cx<R>* b = a + pad_len(p.L);
+  const Tw<R> tw = stage_twiddles(b + pad_len(p.L), p);
   R* __restrict__ psi = (st->steps & 1) ? psi1 : psi0;
   for (int jp = blockIdx.x; jp < Ny; jp += gridDim.x) {
     const int j = jp + 2 - by;  // full-array row of box row jp
@@ -336,10 +393,11 @@ __global__ void k_transpose(const R* __restrict__ in, int rows, int cols, R* __r
   }
 }
 
-// Radices of a 7-smooth length, eights and fours first; 0 if L has another prime factor or needs
-// too many stages.
+// Radices of a 7-smooth length, sixteens, eights and fours first; 0 if L has another prime
+// factor or needs too many stages.
 int plan_radices(int L, int* rad) {
   int n = 0, m = L;
+  while (m % 16 == 0 && SS_DST_R16 && n < DST_MAX_STAGES) { rad[n++] = 16; m /= 16; }
   while (m % 8 == 0 && n < DST_MAX_STAGES) { rad[n++] = 8; m /= 8; }
   while (m % 4 == 0 && n < DST_MAX_STAGES) { rad[n++] = 4; m /= 4; }
   const int ps[4] = {2, 3, 5, 7};
@@ -368,7 +426,7 @@ struct DemagSolver {
 namespace {
 
 template <typename R>
-size_t line_smem(int L) { return sizeof(Cx<R>) * (2 * (size_t)L + (L + TW_FINE - 1) / TW_FINE + TW_FINE); }
+size_t line_smem(int L) { return sizeof(Cx<R>) * (2 * (size_t)pad_len(L) + (L + TW_FINE - 1) / TW_FINE + TW_FINE); }
 
 template <typename R>
 LinePlan<R> plan_of(const DemagSolver* d, int axis) {
