@@ -5,9 +5,12 @@
 // / 108 registers (passes 1 / 2 / 3), one or two blocks per SM; bounds of 3 blocks per
 // SM for all three passes with two staged sites in flight for pass 2 were the best of a
 // sweep on the chiral magnet with demagnetisation workload of the benchmark: 0.622 +
-// 0.596 -> 0.547 + 0.552 ms at 4096^2.
+// 0.596 -> 0.547 + 0.552 ms at 4096^2. With the packed stage pairs pass 1 spilled at 3
+// blocks per SM; at 2, staging only the units its stencils read, it measured 0.522 ms
+// against 0.556 ms (one GPU, both builds).
 #define SS_MINB_THEORY 6  // TH_CMD
-#define SS_MINB1 3
+#define SS_MINB1 2
+#define SS_VSKIP1 1
 #define SS_MINB2 3
 #define SS_MINB3 3
 #define SS_LU2 2
