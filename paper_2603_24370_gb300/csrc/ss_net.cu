@@ -91,16 +91,29 @@ __global__ void k_mse(const float* __restrict__ out, const float* __restrict__ a
     const size_t b = i / P, q = i - b * P;
     const int y = (int)(q / S), x = (int)(q % S);
     const bool inside = x >= 2 && x < S - 2 && y >= 2 && y < S - 2;
+    // the pixel's 16 output channels as four 16-byte loads and stores
+    const float4* o4 = reinterpret_cast<const float4*>(out + i * COUT_LAST);
+    float4* g4 = reinterpret_cast<float4*>(dout + i * COUT_LAST);
 #pragma unroll
-    for (int c = 0; c < COUT_LAST; ++c) {
-      float g = 0.f;
-      if (inside && c < C) {
-        const size_t f = (b * C + c) * P + q;
-        const float d = out[i * COUT_LAST + c] - (relaxed[f] - ansatz[f]);
-        acc += (double)d * d;
-        g = (float)(2.0 * inv) * d;
+    for (int v = 0; v < COUT_LAST / 4; ++v) {
+      float4 gv = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (inside && 4 * v < C) {
+        const float4 ov = o4[v];
+        const float on[4] = {ov.x, ov.y, ov.z, ov.w};
+        float gg[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int c = 4 * v + k;
+          if (c < C) {
+            const size_t f = (b * C + c) * P + q;
+            const float d = on[k] - (relaxed[f] - ansatz[f]);
+            acc += (double)d * d;
+            gg[k] = (float)(2.0 * inv) * d;
+          }
+        }
+        gv = make_float4(gg[0], gg[1], gg[2], gg[3]);
       }
-      dout[i * COUT_LAST + c] = g;
+      g4[v] = gv;
     }
   }
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);

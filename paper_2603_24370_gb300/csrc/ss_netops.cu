@@ -112,17 +112,26 @@ __global__ void k_avgpool2(const Act x, const Act out) {
   }
 }
 
+// Four channels per thread (C % 4 == 0): 16-byte loads and stores.
 __global__ void k_avgpool2_backward(const float* __restrict__ dout, int N, int Ho, int Wo, int C,
                                     float* __restrict__ dx) {
-  const size_t total = (size_t)N * (2 * Ho) * (2 * Wo) * C;
+  const int C4 = C / 4;
+  const size_t total = (size_t)N * (2 * Ho) * (2 * Wo) * C4;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-    const size_t pix = i / C;
-    const int c = (int)(i - pix * C);
+    const size_t pix = i / C4;
+    const int c = (int)(i - pix * C4) * 4;
     const int xx = (int)(pix % (2 * Wo));
     const size_t t = pix / (2 * Wo);
     const int yy = (int)(t % (2 * Ho));
     const int n = (int)(t / (2 * Ho));
-    dx[i] += 0.25f * dout[(((size_t)n * Ho + yy / 2) * Wo + xx / 2) * C + c];
+    const float4 g = *reinterpret_cast<const float4*>(dout + (((size_t)n * Ho + yy / 2) * Wo + xx / 2) * C + c);
+    float4* d = reinterpret_cast<float4*>(dx + pix * C + c);
+    float4 v = *d;
+    v.x += 0.25f * g.x;
+    v.y += 0.25f * g.y;
+    v.z += 0.25f * g.z;
+    v.w += 0.25f * g.w;
+    *d = v;
   }
 }
 
@@ -142,32 +151,47 @@ __global__ void k_upsample2(const Act x, const Act out) {
   }
 }
 
+// Four channels per thread (C, cs and off multiples of 4): 16-byte loads and stores.
 __global__ void k_upsample2_backward(const float* __restrict__ dup, int cs, int off, int N, int H, int W, int C,
                                      float* __restrict__ dx) {
-  const size_t total = (size_t)N * H * W * C;
+  const int C4 = C / 4;
+  const size_t total = (size_t)N * H * W * C4;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-    const size_t pix = i / C;
-    const int c = (int)(i - pix * C);
+    const size_t pix = i / C4;
+    const int c = (int)(i - pix * C4) * 4;
     const int xx = (int)(pix % W);
     const size_t t = pix / W;
     const int yy = (int)(t % H);
     const int n = (int)(t / H);
-    float s = 0.f;
+    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const size_t pu = ((size_t)n * (2 * H) + 2 * yy + (q >> 1)) * (2 * W) + 2 * xx + (q & 1);
-      s += dup[pu * cs + off + c];
+      const float4 u = *reinterpret_cast<const float4*>(dup + pu * cs + off + c);
+      s.x += u.x;
+      s.y += u.y;
+      s.z += u.z;
+      s.w += u.w;
     }
-    dx[i] = s;
+    *reinterpret_cast<float4*>(dx + pix * C + c) = s;
   }
 }
 
+// Four channels per thread (C, cs and off multiples of 4).
 __global__ void k_add_slice(const float* __restrict__ src, int cs, int off, size_t P, int C, float* __restrict__ dst) {
-  const size_t total = P * C;
+  const int C4 = C / 4;
+  const size_t total = P * C4;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-    const size_t pix = i / C;
-    const int c = (int)(i - pix * C);
-    dst[i] += src[pix * cs + off + c];
+    const size_t pix = i / C4;
+    const int c = (int)(i - pix * C4) * 4;
+    const float4 u = *reinterpret_cast<const float4*>(src + pix * cs + off + c);
+    float4* d = reinterpret_cast<float4*>(dst + pix * C + c);
+    float4 v = *d;
+    v.x += u.x;
+    v.y += u.y;
+    v.z += u.z;
+    v.w += u.w;
+    *d = v;
   }
 }
 
@@ -317,8 +341,11 @@ cudaError_t avgpool2(const Act& x, const Act& out, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+bool f4_ok(const float* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
 cudaError_t avgpool2_backward(const float* dout, int N, int Ho, int Wo, int C, float* dx, cudaStream_t s) {
-  const size_t n = (size_t)N * 4 * Ho * Wo * C;
+  if (C % 4 || !f4_ok(dout) || !f4_ok(dx)) return cudaErrorInvalidValue;
+  const size_t n = (size_t)N * 4 * Ho * Wo * (C / 4);
   k_avgpool2_backward<<<grid_for(n), 256, 0, s>>>(dout, N, Ho, Wo, C, dx);
   return cudaGetLastError();
 }
@@ -332,14 +359,16 @@ cudaError_t upsample2(const Act& x, const Act& out, cudaStream_t s) {
 
 cudaError_t upsample2_backward(const float* dup, int cs, int off, int N, int H, int W, int C, float* dx,
                                cudaStream_t s) {
-  const size_t n = (size_t)N * H * W * C;
+  if (C % 4 || cs % 4 || off % 4 || !f4_ok(dup) || !f4_ok(dx)) return cudaErrorInvalidValue;
+  const size_t n = (size_t)N * H * W * (C / 4);
   k_upsample2_backward<<<grid_for(n), 256, 0, s>>>(dup, cs, off, N, H, W, C, dx);
   return cudaGetLastError();
 }
 
 cudaError_t add_slice(const float* src, int cs, int off, int N, int H, int W, int C, float* dst, cudaStream_t s) {
+  if (C % 4 || cs % 4 || off % 4 || !f4_ok(src) || !f4_ok(dst)) return cudaErrorInvalidValue;
   const size_t P = (size_t)N * H * W;
-  k_add_slice<<<grid_for(P * C), 256, 0, s>>>(src, cs, off, P, C, dst);
+  k_add_slice<<<grid_for(P * (C / 4)), 256, 0, s>>>(src, cs, off, P, C, dst);
   return cudaGetLastError();
 }
 
