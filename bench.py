@@ -4,7 +4,7 @@
 
 Workload: chiral magnet (J = D = 1, h = 0.6, K = 0.1, interfacial DMI) on a
 4096 x 4096 grid (dx = 0.2, halo included), compensated FP32 fields (value +
-remainder planes; the flow's sums in float-float pairs totalled in FP64), 400 compact
+remainder planes; the flow's sums in float-float pairs, E and dE kept in FP64), 400 compact
 skyrmions at seeded positions
 (minimum separation 8). Its arrays (8 x 201 MB) are far larger than the 129 MB L2,
 so every timed step streams HBM.
@@ -81,7 +81,7 @@ C = 3
 MIN_PLANES = {False: 6, True: 4}
 WORKLOAD = ("chiral magnet 4096x4096 (halo incl.), dx=0.2, J=D=1, h=0.6, K=0.1, interfacial DMI, "
             "400 skyrmions min-sep 8, compensated FP32 fields (value + remainder planes), float-float flow sums "
-            "totalled in FP64, ANF-RK4 (2 fused kernels/step)")
+            "(E and dE kept in FP64), ANF-RK4 (2 fused kernels/step)")
 
 
 def interior(n: int) -> int:
@@ -297,7 +297,7 @@ def run_native(args) -> int:
     value = units / job_sec
 
     # per-kernel durations (CUDA events around each launch on the context stream)
-    stage_ms = S.ss_profile_stages(s.ctx, 8)
+    stage_ms = S.ss_profile_stages(s.ctx, 24)  # mean launch durations over 24 flow steps
     dominant = max(range(2), key=lambda i: stage_ms[i]) + 1
     peaks, src = measured_peaks()
     kname = f"k_pass<CM, float, {dominant}>"
@@ -387,7 +387,7 @@ BATCH_TOL = 1e-6
 BATCH_CAP = 40000
 BATCH_WORKLOAD = ("256 Abelian Higgs relaxations in one batch, sides U{64,128,256,512} (halo incl.), dx=0.1, "
                   "lambda U[0.5,2], N U{1..4} unit vortices uniform in the central half, compensated FP32 "
-                  "fields (float-float flow sums totalled in FP64), to dx dy max|G| < 1e-6")
+                  "fields (float-float flow sums, E and dE kept in FP64), to dx dy max|G| < 1e-6")
 
 
 def solve_summary(S, I, np, count: int = 64, fp64_per_side: int = 4) -> dict:

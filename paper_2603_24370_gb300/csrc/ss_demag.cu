@@ -42,7 +42,9 @@ constexpr int DST_THREADS = 256;
 // Radix-16 Stockham stages where the length allows (1) or radix 8 at most (0), and padded
 // shared line buffers (1) or dense ones (0). The Poisson solve at 4096^2 (FP32, one GPU,
 // all four builds): dense radix 8 0.778 ms, dense radix 16 0.817 ms, padded radix 8 0.724
-// ms, padded radix 16 0.648 ms.
+// ms, padded radix 16 0.648 ms (0.659 ms with the radix-16 twiddles one product deep,
+// the kept form: on a fixed 4096^2 field its FP32 demagnetisation energy is 3.1e-7 from
+// the FP64 solve's, against 3.4e-7 with radix 8 and 3.6e-7 with products three deep).
 #ifndef SS_DST_R16
 #define SS_DST_R16 1
 #endif
@@ -113,12 +115,13 @@ __device__ __forceinline__ void stockham_stage(const Cx<R>* __restrict__ src, Cx
     Cx<R> v[RAD];
 #pragma unroll
     for (int r = 0; r < RAD; ++r) v[r] = src[pz(j + r * nb)];
-    if (RAD == 16) {  // w^1, w^2, w^4, w^8 from the table, the other powers as their products
+    if (RAD == 16) {  // w^1, w^2, w^3, w^4, w^8, w^12 from the table, every other power one product of two
       const int t1 = jm * step;
-      const Cx<R> w1 = tw[t1], w2 = tw[2 * t1], w4 = tw[4 * t1], w8 = tw[8 * t1];
-      const Cx<R> w3 = cmul(w1, w2), w5 = cmul(w1, w4), w6 = cmul(w2, w4), w7 = cmul(w3, w4);
-      const Cx<R> w[16] = {Cx<R>{R(1), R(0)}, w1, w2, w3, w4, w5, w6, w7, w8, cmul(w1, w8), cmul(w2, w8),
-                           cmul(w3, w8), cmul(w4, w8), cmul(w5, w8), cmul(w6, w8), cmul(w7, w8)};
+      const Cx<R> w1 = tw[t1], w2 = tw[2 * t1], w3 = tw[3 * t1], w4 = tw[4 * t1], w8 = tw[8 * t1],
+                  w12 = tw[12 * t1];
+      const Cx<R> w[16] = {Cx<R>{R(1), R(0)}, w1, w2, w3, w4, cmul(w1, w4), cmul(w2, w4), cmul(w3, w4),
+                           w8, cmul(w1, w8), cmul(w2, w8), cmul(w3, w8), w12, cmul(w1, w12), cmul(w2, w12),
+                           cmul(w3, w12)};
 #pragma unroll
       for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], w[r]);
     } else if (RAD == 8) {  // w^1, w^2, w^4 from the table, the other powers as their products

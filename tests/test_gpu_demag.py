@@ -24,10 +24,12 @@ GRID = (71, 45, 0.2, 0.23)
 # Dirichlet boxes: GRID pads x only (67 -> 69 sites, one below I); GRID_PAD pads both
 # axes with a site below I (60 -> 62, 36 -> 39)
 GRID_PAD = (64, 40, 0.21, 0.2)
-# boxes whose transform lengths take radix 8 x 4 (35 -> Lx = 32) and 8 x 8 (67 -> Lx = 64)
-# along x, 5 x 7 along y (36 -> Ly = 35)
+# boxes whose transform lengths take radix 16 x 2 (35 -> Lx = 32) and 16 x 4 (67 -> Lx = 64)
+# along x, 5 x 7 along y (36 -> Ly = 35); and 16 x 16 x 2 along x, 16 x 16 along y
+# (515 -> Lx = 512, 259 -> Ly = 256)
 GRID_R4 = (35, 36, 0.2, 0.22)
 GRID_R8 = (67, 36, 0.19, 0.2)
+GRID_R16 = (515, 259, 0.2, 0.2)
 
 
 @pytest.fixture(scope="module")
@@ -45,7 +47,7 @@ def dtype_of(prec):
     return np.float64 if prec == 2 else np.float32
 
 
-@pytest.mark.parametrize("grid", [GRID, GRID_PAD, GRID_R4, GRID_R8])
+@pytest.mark.parametrize("grid", [GRID, GRID_PAD, GRID_R4, GRID_R8, GRID_R16])
 @pytest.mark.parametrize("prec", [1, 2, 3])
 def test_force_and_energy_match_oracle(S, prec, grid):
     nx, ny, dx, dy = grid
@@ -146,3 +148,28 @@ def test_demag_is_single_context_only(S):
         S.ss_batch_create(S.SS_CHIRAL_MAGNET, 2, probs)
     with pytest.raises(S.SolitonError):
         S.Solver(S.SS_CHIRAL_MAGNET, (1.0, 1.0, 0.1, 0.6, 0.0, -1.0), 32, 32, 0.2, 0.2, 2)
+
+
+def test_fp32_poisson_solve_at_1024_matches_the_fp64_solve(S):
+    """The 1024^2 workload field (8 skyrmions, after 20 FP32 flow steps; the box takes
+    radix 16 x 16 x 4 transforms): the FP32 solve's demagnetisation energy equals the
+    FP64 solve's (oracle-pinned above) to 1e-6 of that energy. The rest of the energy
+    is evaluated from the same field values in both contexts."""
+    from paper_2603_24370_gb300 import inputs as I
+    q = I.cm_skyrmions()
+    prm = tuple(q.params) + (0.8,)
+    with S.Solver(S.SS_CHIRAL_MAGNET, prm, q.nx, q.ny, q.dx, q.dy, S.SS_FP32) as s32:
+        s32.init_ansatz(q.soliton_array())
+        s32.step(20)
+        f = s32.fields()
+        s32.set_fields(f)  # no remainder: both contexts hold the same values
+        e32 = s32.observables()["energy"]
+    with S.Solver(S.SS_CHIRAL_MAGNET, prm, q.nx, q.ny, q.dx, q.dy, S.SS_FP64) as s64:
+        s64.set_fields(f.astype(np.float64))
+        e64 = s64.observables()["energy"]
+    with S.Solver(S.SS_CHIRAL_MAGNET, tuple(q.params), q.nx, q.ny, q.dx, q.dy, S.SS_FP64) as s0:
+        s0.set_fields(f.astype(np.float64))
+        e0 = s0.observables()["energy"]
+    demag = e64 - e0
+    assert demag > 1.0
+    assert abs(e32 - e64) <= 1e-6 * demag
