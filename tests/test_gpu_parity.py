@@ -108,6 +108,30 @@ def test_trajectory_matches_oracle(S, theory, prec):
 
 
 @pytest.mark.parametrize("theory", [AH, CM])
+def test_fp32_pair_reductions_match_fp64_sums_of_the_stored_fields(S, theory):
+    """The compensated-FP32 flow totals E_h and the arrest test's energy change in
+    float-float pairs: after 20 and 21 steps, both equal the oracle's FP64 sums over
+    the exactly stored fields (value + remainder), E to 1e-6 of sum |e| and the change
+    to 1e-4 of itself; the arrest decision (change > 0) agrees."""
+    nx, ny, dx, dy = GRIDS[theory]
+    f = I.smooth_field(theory, nx, ny, dx, dy, seed=207).astype(np.float32)
+    with S.Solver(theory, prm(theory), nx, ny, dx, dy, 1) as s:
+        s.set_fields(f)
+        s.step(20)
+        fa = s.exact_fields()
+        st = s.step(1)
+        fb = s.exact_fields()
+    Ea = O.energy(theory, prm(theory), fa, dx, dy)
+    Eb = O.energy(theory, prm(theory), fb, dx, dy)
+    esc = np.abs(O.energy_density(theory, prm(theory), fb, dx, dy)).sum() * dx * dy
+    assert abs(st["energy"] - Eb) <= 1e-6 * esc
+    dE = Eb - Ea
+    assert abs(dE) > 1e-9 * esc  # a change the test can resolve
+    assert abs(st["energy_change"] - dE) <= 1e-4 * abs(dE) + 1e-12 * esc
+    assert (st["energy_change"] > 0) == (dE > 0)
+
+
+@pytest.mark.parametrize("theory", [AH, CM])
 @pytest.mark.parametrize("prec", [1, 2])
 def test_ansatz_matches_oracle(S, theory, prec):
     nx, ny, dx, dy = 101, 66, 0.15, 0.2
