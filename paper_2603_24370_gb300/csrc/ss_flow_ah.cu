@@ -7,12 +7,12 @@
 // 64-problem batch of the batched set: 0.515 -> 0.404 ms per step. Batched pass 2,
 // whose tile search and per-tile descriptor hold more registers, spilled 600 B at 3
 // blocks per SM; at 2 it spills 52 B and the 256-problem set relaxes in 8.5 s instead
-// of 9.8 s.
+// of 9.8 s. The single-problem pass 2, packed stage pairs and all, spilled 148 B at 3;
+// at 2 blocks per SM it takes 0.155 ms instead of 0.169 ms at 2048^2 (one GPU).
 #define SS_MINB_THEORY 1  // TH_AH
 #define SS_MINB_BATCH 1
 #define SS_MINB1 2
-#define SS_MINB2 3
-#define SS_MINB2B 2
+#define SS_MINB2 2
 #define SS_MINB3 3
 #define SS_LU2 1
 #include "ss_flow_kernel.cuh"

@@ -5,10 +5,12 @@
 // / 125 registers (passes 1 / 2 / 3), one or two blocks per SM; bounds of 3 blocks per
 // SM for all three passes with one staged site in flight for passes 1 and 2 were the
 // best of a sweep on the Baby Skyrme workload of the benchmark: 0.190 + 0.186 -> 0.154
-// + 0.168 ms at 2048^2.
+// + 0.168 ms at 2048^2. With the packed stage pairs passes 1 and 2 spilled 644 / 292 B
+// at 3 blocks per SM (0.180 + 0.148 ms); at 2 they spill 32 / 0 B: 0.137 + 0.145 ms
+// (one GPU, both builds).
 #define SS_MINB_THEORY 3  // TH_BS
-#define SS_MINB1 3
-#define SS_MINB2 3
+#define SS_MINB1 2
+#define SS_MINB2 2
 #define SS_MINB3 3
 #define SS_LU1 1
 #define SS_LU2 1
