@@ -241,7 +241,11 @@ struct ss_net {
   float* out = nullptr;  // FP32 [B][S][S][16]
   float *g_out, *g_d1, *g_d1a, *g_cat1, *g_d2, *g_d2a, *g_cat2, *g_d3, *g_d3a, *g_cat3, *g_b, *g_b1, *g_p3, *g_e3,
       *g_e3a, *g_p2, *g_e2, *g_e2a, *g_p1, *g_e1, *g_e1a;
-  void *dyb = nullptr, *dyT = nullptr, *xT = nullptr;
+  void *dyb = nullptr, *dyT = nullptr, *xT = nullptr, *xT1 = nullptr;
+  // backward: the weight gradients' shifted channel-major input copies are made on a
+  // second stream, one layer ahead, into two alternating buffers (xT, xT1)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_start = nullptr, ev_x[2] = {nullptr, nullptr}, ev_w[2] = {nullptr, nullptr};
   double* h_loss = nullptr;  // pinned
   int* h_err = nullptr;      // pinned
 };
@@ -307,17 +311,24 @@ int forward(ss_net* n, int B) {
   return SS_OK;
 }
 
-// Backward through conv L: gradient gy (FP32 NHWC, cout channels) of its output y
-// (mask: y's BF16 values, or none for the linear last layer), input x. Writes the
-// weight and bias gradients and, if gx is given, the input gradient (FP32 NHWC).
-int conv_backward(ss_net* n, int L, const Act& x, const Act* y, const float* gy, float* gx, int B) {
+// Backward through conv L, the k-th of the backward pass: gradient gy (FP32 NHWC, cout
+// channels) of its output y (mask: y's BF16 values, or none for the linear last layer),
+// input x. Writes the weight and bias gradients and, if gx is given, the input gradient
+// (FP32 NHWC). The shifted copies of x go to buffer k % 2 on the side stream, after the
+// weight gradient of layer k - 2 has read that buffer.
+int conv_backward(ss_net* n, int k, int L, const Act& x, const Act* y, const float* gy, float* gx, int B) {
   const LayerView& lv = n->T.l[L];
   const Act xi = batch(x, B);
   Act yb;
   if (y) yb = batch(*y, B);
+  void* xT = (k & 1) ? n->xT1 : n->xT;
+  if (k >= 2) NET_CK(cudaStreamWaitEvent(n->side, n->ev_w[k & 1], 0));
+  NET_CK(shifted_transpose(xi, xT, n->side));
+  NET_CK(cudaEventRecord(n->ev_x[k & 1], n->side));
   NET_CK(relu_grad(gy, y ? &yb : nullptr, B, xi.H, xi.W, lv.cout, n->dyb, n->dyT, n->grad + lv.boff, n->stream));
-  NET_CK(shifted_transpose(xi, n->xT, n->stream));
-  NET_CK(wgrad3x3_tc(n->dyT, n->xT, B, xi.H, xi.W, lv.cout, lv.cin, n->grad + lv.woff, n->err, n->stream));
+  NET_CK(cudaStreamWaitEvent(n->stream, n->ev_x[k & 1], 0));
+  NET_CK(wgrad3x3_tc(n->dyT, xT, B, xi.H, xi.W, lv.cout, lv.cin, n->grad + lv.woff, n->err, n->stream));
+  NET_CK(cudaEventRecord(n->ev_w[k & 1], n->stream));
   if (gx) {
     Act dy{n->dyb, B, xi.H, xi.W, lv.cout, lv.cout, 0};
     Act gxa{gx, B, xi.H, xi.W, lv.cin, lv.cin, 0};
@@ -331,35 +342,39 @@ int backward(ss_net* n, int B) {
   const cudaStream_t s = n->stream;
   int rc;
   NET_CK(cudaMemsetAsync(n->grad, 0, sizeof(float) * n->nparam, s));
+  // the forward activations are complete: the side stream may start copying them
+  NET_CK(cudaEventRecord(n->ev_start, s));
+  NET_CK(cudaStreamWaitEvent(n->side, n->ev_start, 0));
+  int k = 0;
   const Act e1 = view(n->cat1, B, 32, 16), e2 = view(n->cat2, B, 48, 32), e3 = view(n->cat3, B, 96, 48);
-  if ((rc = conv_backward(n, 14, n->d1, nullptr, n->g_out, n->g_d1, B))) return rc;
-  if ((rc = conv_backward(n, 13, n->d1a, &n->d1, n->g_d1, n->g_d1a, B))) return rc;
-  if ((rc = conv_backward(n, 12, n->cat1, &n->d1a, n->g_d1a, n->g_cat1, B))) return rc;
+  if ((rc = conv_backward(n, k++, 14, n->d1, nullptr, n->g_out, n->g_d1, B))) return rc;
+  if ((rc = conv_backward(n, k++, 13, n->d1a, &n->d1, n->g_d1, n->g_d1a, B))) return rc;
+  if ((rc = conv_backward(n, k++, 12, n->cat1, &n->d1a, n->g_d1a, n->g_cat1, B))) return rc;
   NET_CK(upsample2_backward(n->g_cat1, 48, 0, B, S / 2, S / 2, 32, n->g_d2, s));
-  if ((rc = conv_backward(n, 11, n->d2a, &n->d2, n->g_d2, n->g_d2a, B))) return rc;
-  if ((rc = conv_backward(n, 10, n->cat2, &n->d2a, n->g_d2a, n->g_cat2, B))) return rc;
+  if ((rc = conv_backward(n, k++, 11, n->d2a, &n->d2, n->g_d2, n->g_d2a, B))) return rc;
+  if ((rc = conv_backward(n, k++, 10, n->cat2, &n->d2a, n->g_d2a, n->g_cat2, B))) return rc;
   NET_CK(upsample2_backward(n->g_cat2, 80, 0, B, S / 4, S / 4, 48, n->g_d3, s));
-  if ((rc = conv_backward(n, 9, n->d3a, &n->d3, n->g_d3, n->g_d3a, B))) return rc;
-  if ((rc = conv_backward(n, 8, n->cat3, &n->d3a, n->g_d3a, n->g_cat3, B))) return rc;
+  if ((rc = conv_backward(n, k++, 9, n->d3a, &n->d3, n->g_d3, n->g_d3a, B))) return rc;
+  if ((rc = conv_backward(n, k++, 8, n->cat3, &n->d3a, n->g_d3a, n->g_cat3, B))) return rc;
   NET_CK(upsample2_backward(n->g_cat3, 144, 0, B, S / 8, S / 8, 96, n->g_b, s));
-  if ((rc = conv_backward(n, 7, n->b1, &n->bb, n->g_b, n->g_b1, B))) return rc;
-  if ((rc = conv_backward(n, 6, n->p3, &n->b1, n->g_b1, n->g_p3, B))) return rc;
+  if ((rc = conv_backward(n, k++, 7, n->b1, &n->bb, n->g_b, n->g_b1, B))) return rc;
+  if ((rc = conv_backward(n, k++, 6, n->p3, &n->b1, n->g_b1, n->g_p3, B))) return rc;
   // level 2 encoder output: concatenation slice + pooling path
   NET_CK(cudaMemsetAsync(n->g_e3, 0, sizeof(float) * (size_t)B * (S / 4) * (S / 4) * 48, s));
   NET_CK(add_slice(n->g_cat3, 144, 96, B, S / 4, S / 4, 48, n->g_e3, s));
   NET_CK(avgpool2_backward(n->g_p3, B, S / 8, S / 8, 48, n->g_e3, s));
-  if ((rc = conv_backward(n, 5, n->e3a, &e3, n->g_e3, n->g_e3a, B))) return rc;
-  if ((rc = conv_backward(n, 4, n->p2, &n->e3a, n->g_e3a, n->g_p2, B))) return rc;
+  if ((rc = conv_backward(n, k++, 5, n->e3a, &e3, n->g_e3, n->g_e3a, B))) return rc;
+  if ((rc = conv_backward(n, k++, 4, n->p2, &n->e3a, n->g_e3a, n->g_p2, B))) return rc;
   NET_CK(cudaMemsetAsync(n->g_e2, 0, sizeof(float) * (size_t)B * (S / 2) * (S / 2) * 32, s));
   NET_CK(add_slice(n->g_cat2, 80, 48, B, S / 2, S / 2, 32, n->g_e2, s));
   NET_CK(avgpool2_backward(n->g_p2, B, S / 4, S / 4, 32, n->g_e2, s));
-  if ((rc = conv_backward(n, 3, n->e2a, &e2, n->g_e2, n->g_e2a, B))) return rc;
-  if ((rc = conv_backward(n, 2, n->p1, &n->e2a, n->g_e2a, n->g_p1, B))) return rc;
+  if ((rc = conv_backward(n, k++, 3, n->e2a, &e2, n->g_e2, n->g_e2a, B))) return rc;
+  if ((rc = conv_backward(n, k++, 2, n->p1, &n->e2a, n->g_e2a, n->g_p1, B))) return rc;
   NET_CK(cudaMemsetAsync(n->g_e1, 0, sizeof(float) * (size_t)B * S * S * 16, s));
   NET_CK(add_slice(n->g_cat1, 48, 32, B, S, S, 16, n->g_e1, s));
   NET_CK(avgpool2_backward(n->g_p1, B, S / 2, S / 2, 16, n->g_e1, s));
-  if ((rc = conv_backward(n, 1, n->e1a, &e1, n->g_e1, n->g_e1a, B))) return rc;
-  if ((rc = conv_backward(n, 0, n->in0, &n->e1a, n->g_e1a, nullptr, B))) return rc;
+  if ((rc = conv_backward(n, k++, 1, n->e1a, &e1, n->g_e1, n->g_e1a, B))) return rc;
+  if ((rc = conv_backward(n, k++, 0, n->in0, &n->e1a, n->g_e1a, nullptr, B))) return rc;
   return SS_OK;
 }
 
@@ -393,6 +408,12 @@ void net_free(ss_net* n) {
   if (n->base) cudaFree(n->base);
   if (n->h_loss) cudaFreeHost(n->h_loss);
   if (n->h_err) cudaFreeHost(n->h_err);
+  if (n->side) {
+    cudaStreamSynchronize(n->side);
+    cudaStreamDestroy(n->side);
+  }
+  for (cudaEvent_t e : {n->ev_start, n->ev_x[0], n->ev_x[1], n->ev_w[0], n->ev_w[1]})
+    if (e) cudaEventDestroy(e);
   if (n->own_stream && n->stream) cudaStreamDestroy(n->stream);
   delete n;
 }
@@ -423,6 +444,15 @@ extern "C" int ss_net_create(ss_net** out, int theory, int size, int max_batch, 
       return nfail(SS_ERR_CUDA, "stream creation failed");
     }
     n->own_stream = true;
+  }
+  if (cudaStreamCreateWithFlags(&n->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&n->ev_start, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&n->ev_x[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&n->ev_x[1], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&n->ev_w[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&n->ev_w[1], cudaEventDisableTiming) != cudaSuccess) {
+    net_free(n);
+    return nfail(SS_ERR_CUDA, "stream or event creation failed");
   }
   // parameter layout: per layer W [cout][9][cin] then b [cout]
   long long off = 0, wo = 0;
@@ -483,6 +513,7 @@ extern "C" int ss_net_create(ss_net** out, int theory, int size, int max_batch, 
   add(&n->dyb, sizeof(__nv_bfloat16) * P0 * 16);
   add(&n->dyT, sizeof(__nv_bfloat16) * P0 * 16);
   add(&n->xT, sizeof(__nv_bfloat16) * P0 * 3 * 48);
+  add(&n->xT1, sizeof(__nv_bfloat16) * P0 * 3 * 48);
   size_t total = 0;
   for (auto& e : plan) total += e.second;
   if (cudaMalloc(&n->base, total) != cudaSuccess) {
