@@ -579,6 +579,11 @@ __global__ void __launch_bounds__(128) k_wgrad_sw(const __grid_constant__ CUtens
 // those reads stay inside it). The output-gradient box ({64 pixels, Cout channels}) is
 // B. Against one 128-row tile of output channels per tap (k_wgrad_sw) this issues
 // ceil(9 Cin / 128) instead of nine MMAs per K step and loads no zero rows.
+// The nine shifted input boxes of a K-block as three boxes of three rows each, one per
+// column shift (1), or one box per tap (0).
+#ifndef SS_WG_ROWS3
+#define SS_WG_ROWS3 1
+#endif
 struct WgRowArgs {
   int N, H, W, Cout, Cin;
   int kb_per_cta, total_kb;
@@ -636,11 +641,17 @@ __global__ void __launch_bounds__(128) k_wgrad_rows(const __grid_constant__ CUte
       const int n = p0 / HW, rem = p0 - n * HW;
       const int y = rem / a.W, x = rem - y * a.W;
       mbar_arrive_expect_tx(&full[s], (uint32_t)(A_BYTES + BN * 128));
+      if (SS_WG_ROWS3) {  // per column shift one box of rows y - 1 .. y + 1: stack row (dx, ci, dy)
+        tma_load_4d(sa, &mx0, &full[s], x, y - 1, n, 0);
+        tma_load_4d(sa + 3 * XB, &mx1, &full[s], x, y - 1, n, 0);
+        tma_load_4d(sa + 6 * XB, &mx2, &full[s], x, y - 1, n, 0);
+      } else {  // one box per tap: stack row (tap, ci)
 #pragma unroll 1
-      for (int tap = 0; tap < 9; ++tap) {
-        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
-        const CUtensorMap* mx = dx < 0 ? &mx0 : (dx == 0 ? &mx1 : &mx2);
-        tma_load_4d(sa + tap * XB, mx, &full[s], x, y + dy, n, 0);
+        for (int tap = 0; tap < 9; ++tap) {
+          const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+          const CUtensorMap* mx = dx < 0 ? &mx0 : (dx == 0 ? &mx1 : &mx2);
+          tma_load_4d(sa + tap * XB, mx, &full[s], x, y + dy, n, 0);
+        }
       }
       tma_load_4d(sa + A_BYTES, &mdy, &full[s], x, y, n, 0);
       issued = i + 1;
@@ -680,13 +691,21 @@ __global__ void __launch_bounds__(128) k_wgrad_rows(const __grid_constant__ CUte
     const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
 #pragma unroll 1
     for (int g = 0; g < G; ++g) {
-      const int r = g * BM + warp * 32 + lane;  // stack row: (tap, input channel)
-      const int tap = r / Cin, ci = r - tap * Cin;
+      const int r = g * BM + warp * 32 + lane;  // stack row
+      int tap, ci;
+      if (SS_WG_ROWS3) {  // (column shift, input channel, row shift)
+        const int dxi = r / (3 * Cin), rem = r - dxi * 3 * Cin;
+        ci = rem / 3;
+        tap = (rem - 3 * ci) * 3 + dxi;
+      } else {  // (tap, input channel)
+        tap = r / Cin;
+        ci = r - tap * Cin;
+      }
 #pragma unroll 1
       for (int c = 0; c < BN; c += 16) {
         float v[16];
         tmem_ld16(trow + (uint32_t)(g * BN + c), v);
-        if (r < 9 * Cin) {  // a warp's lanes: consecutive input channels of one entry row
+        if (r < 9 * Cin) {
           float* d = a.dw + (size_t)tap * Cin + ci;
 #pragma unroll
           for (int q = 0; q < 16; ++q) atomicAdd(d + (size_t)(c + q) * 9 * Cin, v[q]);
@@ -903,7 +922,7 @@ cudaError_t wgrad3x3_tc(const void* dyT, const void* xT, int N, int H, int W, in
   if (W % 64 == 0 && Cin % 16 == 0 && Cin <= 48 && (Cout == 16 || Cout == 32 || Cout == 48 || Cout == 96)) {
     // (tap, input channel) rows: 64-pixel K-blocks in 128-byte-swizzled boxes
     WgRowArgs a{N, H, W, Cout, Cin, 0, (int)(P / 64), 0, 0, 0, 0, dw, err};
-    const cuuint32_t xbox[4] = {64, 1, 1, (cuuint32_t)Cin};
+    const cuuint32_t xbox[4] = {64, SS_WG_ROWS3 ? 3u : 1u, 1, (cuuint32_t)Cin};
     for (int d = 0; d < 3; ++d) {
       e = make_map(&mx[d], static_cast<const char*>(xT) + (size_t)d * Cin * P * 2, 4, xd, st, xbox, true);
       if (e != cudaSuccess) return e;
