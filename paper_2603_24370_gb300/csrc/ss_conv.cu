@@ -100,7 +100,8 @@ struct PConvArgs {
   int tiles;
   int resident;  // 1: all weight groups in shared memory, loaded once
   int wbytes;    // BN * K * 2
-  int halo;      // 1: halo staging (rows of at least 128 pixels, resident weights)
+  int halo;      // 1: halo staging (rows of at least 128 pixels), 2: row-halo staging
+                 // (narrower rows); both with resident weights
 };
 
 // Halo staging. For rows of at least 128 pixels a tile is 128 pixels of one image row.
@@ -111,9 +112,20 @@ struct PConvArgs {
 // from byte dy * HROW + dx * 16 on: 128 rows at a 16-byte pitch, the K-major
 // no-swizzle layout with the K-adjacent group in the pair's other box (LBO = HSLOT).
 // Against one box per tap and group this moves a third of the bytes from L2.
+#ifndef SS_CONV_RHALO
+#define SS_CONV_RHALO 1
+#endif
 constexpr int HROW = 130 * 16;   // one row of a halo box
 constexpr int HBOX = 3 * HROW;   // box bytes: 6240
 constexpr int HSLOT = 49 * 128;  // a box's slot, 128-byte aligned: 6272
+
+// Row-halo staging, for rows narrower than 128 pixels (a tile is 128 / W whole image
+// rows). A shift along x would carry a tile row's last pixel into the next row, so
+// each column shift dx gets its own box {8 channels, W pixels, rows + 2} starting at
+// x = dx - 1 (zero outside the image), and the row shift dy is the start offset
+// dy * W * 16 bytes inside it: 128 rows at a 16-byte pitch again. Per pair of channel
+// groups six boxes, [group][dx], hold the nine taps (LBO = three boxes).
+__host__ __device__ inline int rbox_bytes(int W) { return ((128 / W + 2) * W * 16 + 127) & ~127; }
 
 template <int BN>
 __global__ void __launch_bounds__(192) k_conv3x3_p(const __grid_constant__ CUtensorMap mx,
@@ -124,8 +136,9 @@ __global__ void __launch_bounds__(192) k_conv3x3_p(const __grid_constant__ CUten
   constexpr int A_BYTES = GPS * BM * 16;
   constexpr int TCOLS = ptcols(BN);
   const bool resident = pa.resident != 0;
-  const bool halo = pa.halo != 0;  // implies resident
-  const int stage = halo ? 2 * HSLOT : A_BYTES + (resident ? 0 : GPS * BN * 16);
+  const bool halo = pa.halo == 1, rhalo = pa.halo == 2;  // both imply resident
+  const int RB = rhalo ? rbox_bytes(a.W) : 0;
+  const int stage = halo ? 2 * HSLOT : rhalo ? 6 * RB : A_BYTES + (resident ? 0 : GPS * BN * 16);
   unsigned char* wsm = smem + P_STAGES * stage;  // resident weights: group g at g * BN * 16
   __shared__ __align__(8) uint64_t full[P_STAGES], empty[P_STAGES], tfull[2], tempty[2], wbar;
   __shared__ uint32_t tmem_base;
@@ -139,7 +152,7 @@ __global__ void __launch_bounds__(192) k_conv3x3_p(const __grid_constant__ CUten
   const int tpi = (H / rows) * tpr;
   const int cg = a.Cin >> 3;
   const int G = 9 * cg;
-  const int nkb = halo ? cg / 2 : (G + GPS - 1) / GPS;  // ring entries per tile
+  const int nkb = (halo || rhalo) ? cg / 2 : (G + GPS - 1) / GPS;  // ring entries per tile
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < P_STAGES; ++s) {
@@ -185,6 +198,13 @@ __global__ void __launch_bounds__(192) k_conv3x3_p(const __grid_constant__ CUten
             mbar_arrive_expect_tx(&full[s], (uint32_t)(2 * HBOX));
             tma_load_4d(sa, &mx, &full[s], 16 * kb, x0 - 1, y0 - 1, n);
             tma_load_4d(sa + HSLOT, &mx, &full[s], 16 * kb + 8, x0 - 1, y0 - 1, n);
+            continue;
+          }
+          if (rhalo) {  // channel groups 2 kb and 2 kb + 1, one box per column shift
+            mbar_arrive_expect_tx(&full[s], (uint32_t)(6 * (rows + 2) * Wt * 16));
+            for (int gi = 0; gi < 2; ++gi)
+              for (int dxi = 0; dxi < 3; ++dxi)
+                tma_load_4d(sa + (gi * 3 + dxi) * RB, &mx, &full[s], 16 * kb + 8 * gi, x0 + dxi - 1, y0 - 1, n);
             continue;
           }
           unsigned char* sb = sa + A_BYTES;
@@ -233,6 +253,16 @@ __global__ void __launch_bounds__(192) k_conv3x3_p(const __grid_constant__ CUten
           }
           fence_after_sync();
           const uint32_t sa = smem_u32(smem + s * stage), sb = sa + A_BYTES;
+          if (rhalo) {
+            for (int tap = 0; tap < 9; ++tap) {
+              const uint64_t ad =
+                  sdesc(sa + (uint32_t)((tap % 3) * RB + (tap / 3) * Wt * 16), (uint32_t)(3 * RB), 128);
+              const uint64_t bd = sdesc(wbase + (uint32_t)((tap * cg + 2 * kb) * (BN * 16)), BN * 16, 128);
+              mma_bf16(acc, ad, bd, idesc, (kb > 0 || tap > 0) ? 1u : 0u);
+            }
+            mma_commit(&empty[s]);
+            continue;
+          }
           if (halo) {
             for (int tap = 0; tap < 9; ++tap) {
               const uint64_t ad = sdesc(sa + (uint32_t)((tap / 3) * HROW + (tap % 3) * 16), HSLOT, 128);
@@ -816,8 +846,10 @@ cudaError_t conv_launch_p(const CUtensorMap& mx, const CUtensorMap* mxh, const C
                           int tiles, int K, cudaStream_t s) {
   PConvArgs pa{a, tiles, 0, BN * K * 2, 0};
   pa.resident = pa.wbytes <= W_RESIDENT_MAX ? 1 : 0;
-  pa.halo = (mxh != nullptr && pa.resident) ? 1 : 0;
-  const size_t stage = pa.halo ? (size_t)2 * HSLOT : (size_t)GPS * BM * 16 + (pa.resident ? 0 : GPS * BN * 16);
+  pa.halo = (mxh != nullptr && pa.resident) ? (a.W % 128 == 0 ? 1 : 2) : 0;
+  const size_t stage = pa.halo == 1   ? (size_t)2 * HSLOT
+                       : pa.halo == 2 ? (size_t)6 * rbox_bytes(a.W)
+                                      : (size_t)GPS * BM * 16 + (pa.resident ? 0 : GPS * BN * 16);
   const size_t smem = (size_t)P_STAGES * stage + (pa.resident ? (size_t)pa.wbytes : 0) + 1024;
   static int max_smem_set = 0;  // per instantiation, under g_attr_mu
   if ((int)smem > max_smem_set) {
@@ -876,11 +908,15 @@ cudaError_t conv3x3_tc(const Act& x, const void* w, int Cout, int mode, const fl
   const cuuint32_t xbox[4] = {8, (cuuint32_t)Wt, (cuuint32_t)(128 / Wt), 1};
   cudaError_t e = make_map(&mx, xb, 4, xd, xs, xbox);
   if (e != cudaSuccess) return e;
-  CUtensorMap mxh;  // halo boxes (rows of at least 128 pixels)
-  const bool halo = W % 128 == 0;
-  if (halo) {
+  CUtensorMap mxh;  // halo boxes (rows of at least 128 pixels) or row-halo boxes (narrower rows)
+  const bool halo = W % 128 == 0 || SS_CONV_RHALO;
+  if (W % 128 == 0) {
     const cuuint32_t hbox[4] = {8, 130, 3, 1};
     e = make_map(&mxh, xb, 4, xd, xs, hbox);
+    if (e != cudaSuccess) return e;
+  } else if (halo) {
+    const cuuint32_t rbox[4] = {8, (cuuint32_t)W, (cuuint32_t)(128 / W + 2), 1};
+    e = make_map(&mxh, xb, 4, xd, xs, rbox);
     if (e != cudaSuccess) return e;
   }
   const int K = 9 * x.C;

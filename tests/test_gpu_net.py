@@ -64,6 +64,8 @@ CONV_CASES = [  # (N, H, W, Cin, Cout)
     (1, 3, 384, 16, 48),
     (2, 16, 16, 144, 48),
     (1, 8, 32, 80, 144),
+    (1, 16, 8, 16, 16),
+    (2, 4, 64, 48, 48),
 ]
 
 
