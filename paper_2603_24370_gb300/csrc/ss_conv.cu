@@ -59,6 +59,12 @@ struct ConvArgs {
   void* out;
   int out_cs, out_coff;
   int* err;
+  // CONV_GRAD_RELU
+  const __nv_bfloat16* mask;
+  int mask_cs, mask_off;
+  __nv_bfloat16* dyT;
+  float* dbias;
+  long long P;
 };
 
 struct WgradArgs {
@@ -143,7 +149,9 @@ __global__ void __launch_bounds__(192) k_conv3x3_p(const __grid_constant__ CUten
   __shared__ __align__(8) uint64_t full[P_STAGES], empty[P_STAGES], tfull[2], tempty[2], wbar;
   __shared__ uint32_t tmem_base;
   __shared__ int s_fail;
+  __shared__ float sbias[BN];  // CONV_GRAD_RELU: this CTA's per-channel sums
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int c = threadIdx.x; c < BN; c += blockDim.x) sbias[c] = 0.f;
 
   const int W = a.W, H = a.H;
   const int Wt = W < BM ? W : BM;
@@ -311,6 +319,34 @@ __global__ void __launch_bounds__(192) k_conv3x3_p(const __grid_constant__ CUten
         float v[16];
         tmem_ld16(trow + (uint32_t)c, v);
         if (c >= a.Cout) continue;
+        if (a.mode == CONV_GRAD_RELU) {
+          // the previous layer's ReLU: its BF16 output at this pixel masks the gradient
+          const uint4* mk = reinterpret_cast<const uint4*>(a.mask + pix * a.mask_cs + a.mask_off + c);
+          const uint4 mq[2] = {mk[0], mk[1]};
+          const __nv_bfloat16* mb = reinterpret_cast<const __nv_bfloat16*>(mq);
+          uint32_t w[8];
+#pragma unroll
+          for (int i = 0; i < 16; ++i)
+            if (!(__bfloat162float(mb[i]) > 0.f)) v[i] = 0.f;
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            __nv_bfloat162 b2 = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+            w[i] = *reinterpret_cast<uint32_t*>(&b2);
+          }
+          uint4* o4 = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(a.out) + pix * a.out_cs + a.out_coff + c);
+          o4[0] = make_uint4(w[0], w[1], w[2], w[3]);
+          o4[1] = make_uint4(w[4], w[5], w[6], w[7]);
+          const __nv_bfloat16* wb = reinterpret_cast<const __nv_bfloat16*>(w);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {  // channel-major: a warp's 32 pixels are consecutive
+            a.dyT[(size_t)(c + i) * a.P + pix] = wb[i];
+            float sum = v[i];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+            if (lane == 0) atomicAdd(&sbias[c + i], sum);
+          }
+          continue;
+        }
         if (a.mode == CONV_BF16_BIAS_RELU) {
           __nv_bfloat16* o = static_cast<__nv_bfloat16*>(a.out) + pix * a.out_cs + a.out_coff + c;
           uint32_t w[8];
@@ -346,6 +382,8 @@ __global__ void __launch_bounds__(192) k_conv3x3_p(const __grid_constant__ CUten
   }
   fence_before_sync();
   __syncthreads();
+  if (a.mode == CONV_GRAD_RELU)
+    for (int c = threadIdx.x; c < a.Cout; c += blockDim.x) atomicAdd(a.dbias + c, sbias[c]);
   if (warp == 0) {
     fence_after_sync();
     tmem_dealloc(tmem, TCOLS);
@@ -891,7 +929,7 @@ std::mutex g_attr_mu;
 }  // namespace
 
 cudaError_t conv3x3_tc(const Act& x, const void* w, int Cout, int mode, const float* bias, const Act& out, int* err,
-                       cudaStream_t s) {
+                       cudaStream_t s, const GradRelu* gr) {
   const int W = x.W, H = x.H;
   if (x.C % 16 || x.off % 8 || x.cs % 8 || (W < 128 ? (128 % W || W % 8) : W % 128) || (H * W) % 128 ||
       out.N != x.N || out.H != H || out.W != W || out.off % 8 || out.cs % 8 || out.C != Cout)
@@ -922,7 +960,19 @@ cudaError_t conv3x3_tc(const Act& x, const void* w, int Cout, int mode, const fl
   const int K = 9 * x.C;
   const cuuint64_t wd[2] = {(cuuint64_t)K, (cuuint64_t)Cout};
   const cuuint64_t ws[1] = {(cuuint64_t)K * 2};
-  ConvArgs a{x.N, H, W, x.C, Cout, mode, bias, static_cast<char*>(out.p), out.cs, out.off, err};
+  ConvArgs a{x.N, H, W, x.C, Cout, mode, bias, static_cast<char*>(out.p), out.cs, out.off, err,
+             nullptr, 0, 0, nullptr, nullptr, (long long)x.N * H * W};
+  if (mode == CONV_GRAD_RELU) {
+    const Act& m = gr ? gr->mask : out;
+    if (!gr || !gr->dyT || !gr->dbias || !m.p || m.N != x.N || m.H != H || m.W != W || m.C != Cout || m.cs % 8 ||
+        m.off % 8 || (reinterpret_cast<uintptr_t>(m.p) & 15))
+      return cudaErrorInvalidValue;
+    a.mask = static_cast<const __nv_bfloat16*>(m.p);
+    a.mask_cs = m.cs;
+    a.mask_off = m.off;
+    a.dyT = static_cast<__nv_bfloat16*>(gr->dyT);
+    a.dbias = gr->dbias;
+  }
   const int tiles = x.N * H * W / 128;
   std::lock_guard<std::mutex> lock(g_attr_mu);
 #define SS_CONV_CASE(BNV)                                   \

@@ -242,6 +242,7 @@ struct ss_net {
   float *g_out, *g_d1, *g_d1a, *g_cat1, *g_d2, *g_d2a, *g_cat2, *g_d3, *g_d3a, *g_cat3, *g_b, *g_b1, *g_p3, *g_e3,
       *g_e3a, *g_p2, *g_e2, *g_e2a, *g_p1, *g_e1, *g_e1a;
   void *dyb = nullptr, *dyT = nullptr, *xT = nullptr, *xT1 = nullptr;
+  void *dyb1 = nullptr, *dyT1 = nullptr;  // the masked output gradients, alternating by layer
   // backward: the weight gradients' shifted channel-major input copies are made on a
   // second stream, one layer ahead, into two alternating buffers (xT, xT1)
   cudaStream_t side = nullptr;
@@ -315,22 +316,38 @@ int forward(ss_net* n, int B) {
 // channels) of its output y (mask: y's BF16 values, or none for the linear last layer),
 // input x. Writes the weight and bias gradients and, if gx is given, the input gradient
 // (FP32 NHWC). The shifted copies of x go to buffer k % 2 on the side stream, after the
-// weight gradient of layer k - 2 has read that buffer.
-int conv_backward(ss_net* n, int k, int L, const Act& x, const Act* y, const float* gy, float* gx, int B) {
+// weight gradient of layer k - 2 has read that buffer. The masked output gradient
+// (BF16 NHWC and channel-major) alternates between two buffer pairs by k.
+// fused_in: the previous call already left it in pair k % 2 (and added the bias
+// gradient). fuse_out: x is the ReLU output of conv L - 1, the next call: the input
+// gradient is formed through that ReLU straight into pair (k + 1) % 2, with conv L - 1's
+// bias gradient, and gx is not written.
+int conv_backward(ss_net* n, int k, int L, const Act& x, const Act* y, const float* gy, float* gx, int B,
+                  bool fused_in = false, bool fuse_out = false) {
   const LayerView& lv = n->T.l[L];
   const Act xi = batch(x, B);
   Act yb;
   if (y) yb = batch(*y, B);
   void* xT = (k & 1) ? n->xT1 : n->xT;
+  void* dyb = (k & 1) ? n->dyb1 : n->dyb;
+  void* dyT = (k & 1) ? n->dyT1 : n->dyT;
   if (k >= 2) NET_CK(cudaStreamWaitEvent(n->side, n->ev_w[k & 1], 0));
   NET_CK(shifted_transpose(xi, xT, n->side));
   NET_CK(cudaEventRecord(n->ev_x[k & 1], n->side));
-  NET_CK(relu_grad(gy, y ? &yb : nullptr, B, xi.H, xi.W, lv.cout, n->dyb, n->dyT, n->grad + lv.boff, n->stream));
+  if (!fused_in)
+    NET_CK(relu_grad(gy, y ? &yb : nullptr, B, xi.H, xi.W, lv.cout, dyb, dyT, n->grad + lv.boff, n->stream));
   NET_CK(cudaStreamWaitEvent(n->stream, n->ev_x[k & 1], 0));
-  NET_CK(wgrad3x3_tc(n->dyT, xT, B, xi.H, xi.W, lv.cout, lv.cin, n->grad + lv.woff, n->err, n->stream));
+  NET_CK(wgrad3x3_tc(dyT, xT, B, xi.H, xi.W, lv.cout, lv.cin, n->grad + lv.woff, n->err, n->stream));
   NET_CK(cudaEventRecord(n->ev_w[k & 1], n->stream));
-  if (gx) {
-    Act dy{n->dyb, B, xi.H, xi.W, lv.cout, lv.cout, 0};
+  Act dy{dyb, B, xi.H, xi.W, lv.cout, lv.cout, 0};
+  if (fuse_out) {
+    GradRelu g;
+    g.mask = xi;
+    g.dyT = (k & 1) ? n->dyT : n->dyT1;
+    g.dbias = n->grad + n->T.l[L - 1].boff;
+    Act o{(k & 1) ? n->dyb : n->dyb1, B, xi.H, xi.W, lv.cin, lv.cin, 0};
+    NET_CK(conv3x3_tc(dy, n->wbf + lv.wto, lv.cin, CONV_GRAD_RELU, nullptr, o, n->err, n->stream, &g));
+  } else if (gx) {
     Act gxa{gx, B, xi.H, xi.W, lv.cin, lv.cin, 0};
     NET_CK(conv3x3_tc(dy, n->wbf + lv.wto, lv.cin, CONV_F32, nullptr, gxa, n->err, n->stream));
   }
@@ -347,34 +364,34 @@ int backward(ss_net* n, int B) {
   NET_CK(cudaStreamWaitEvent(n->side, n->ev_start, 0));
   int k = 0;
   const Act e1 = view(n->cat1, B, 32, 16), e2 = view(n->cat2, B, 48, 32), e3 = view(n->cat3, B, 96, 48);
-  if ((rc = conv_backward(n, k++, 14, n->d1, nullptr, n->g_out, n->g_d1, B))) return rc;
-  if ((rc = conv_backward(n, k++, 13, n->d1a, &n->d1, n->g_d1, n->g_d1a, B))) return rc;
-  if ((rc = conv_backward(n, k++, 12, n->cat1, &n->d1a, n->g_d1a, n->g_cat1, B))) return rc;
+  if ((rc = conv_backward(n, k++, 14, n->d1, nullptr, n->g_out, n->g_d1, B, false, true))) return rc;
+  if ((rc = conv_backward(n, k++, 13, n->d1a, &n->d1, n->g_d1, n->g_d1a, B, true, true))) return rc;
+  if ((rc = conv_backward(n, k++, 12, n->cat1, &n->d1a, n->g_d1a, n->g_cat1, B, true, false))) return rc;
   NET_CK(upsample2_backward(n->g_cat1, 48, 0, B, S / 2, S / 2, 32, n->g_d2, s));
-  if ((rc = conv_backward(n, k++, 11, n->d2a, &n->d2, n->g_d2, n->g_d2a, B))) return rc;
-  if ((rc = conv_backward(n, k++, 10, n->cat2, &n->d2a, n->g_d2a, n->g_cat2, B))) return rc;
+  if ((rc = conv_backward(n, k++, 11, n->d2a, &n->d2, n->g_d2, n->g_d2a, B, false, true))) return rc;
+  if ((rc = conv_backward(n, k++, 10, n->cat2, &n->d2a, n->g_d2a, n->g_cat2, B, true, false))) return rc;
   NET_CK(upsample2_backward(n->g_cat2, 80, 0, B, S / 4, S / 4, 48, n->g_d3, s));
-  if ((rc = conv_backward(n, k++, 9, n->d3a, &n->d3, n->g_d3, n->g_d3a, B))) return rc;
-  if ((rc = conv_backward(n, k++, 8, n->cat3, &n->d3a, n->g_d3a, n->g_cat3, B))) return rc;
+  if ((rc = conv_backward(n, k++, 9, n->d3a, &n->d3, n->g_d3, n->g_d3a, B, false, true))) return rc;
+  if ((rc = conv_backward(n, k++, 8, n->cat3, &n->d3a, n->g_d3a, n->g_cat3, B, true, false))) return rc;
   NET_CK(upsample2_backward(n->g_cat3, 144, 0, B, S / 8, S / 8, 96, n->g_b, s));
-  if ((rc = conv_backward(n, k++, 7, n->b1, &n->bb, n->g_b, n->g_b1, B))) return rc;
-  if ((rc = conv_backward(n, k++, 6, n->p3, &n->b1, n->g_b1, n->g_p3, B))) return rc;
+  if ((rc = conv_backward(n, k++, 7, n->b1, &n->bb, n->g_b, n->g_b1, B, false, true))) return rc;
+  if ((rc = conv_backward(n, k++, 6, n->p3, &n->b1, n->g_b1, n->g_p3, B, true, false))) return rc;
   // level 2 encoder output: concatenation slice + pooling path
   NET_CK(cudaMemsetAsync(n->g_e3, 0, sizeof(float) * (size_t)B * (S / 4) * (S / 4) * 48, s));
   NET_CK(add_slice(n->g_cat3, 144, 96, B, S / 4, S / 4, 48, n->g_e3, s));
   NET_CK(avgpool2_backward(n->g_p3, B, S / 8, S / 8, 48, n->g_e3, s));
-  if ((rc = conv_backward(n, k++, 5, n->e3a, &e3, n->g_e3, n->g_e3a, B))) return rc;
-  if ((rc = conv_backward(n, k++, 4, n->p2, &n->e3a, n->g_e3a, n->g_p2, B))) return rc;
+  if ((rc = conv_backward(n, k++, 5, n->e3a, &e3, n->g_e3, n->g_e3a, B, false, true))) return rc;
+  if ((rc = conv_backward(n, k++, 4, n->p2, &n->e3a, n->g_e3a, n->g_p2, B, true, false))) return rc;
   NET_CK(cudaMemsetAsync(n->g_e2, 0, sizeof(float) * (size_t)B * (S / 2) * (S / 2) * 32, s));
   NET_CK(add_slice(n->g_cat2, 80, 48, B, S / 2, S / 2, 32, n->g_e2, s));
   NET_CK(avgpool2_backward(n->g_p2, B, S / 4, S / 4, 32, n->g_e2, s));
-  if ((rc = conv_backward(n, k++, 3, n->e2a, &e2, n->g_e2, n->g_e2a, B))) return rc;
-  if ((rc = conv_backward(n, k++, 2, n->p1, &n->e2a, n->g_e2a, n->g_p1, B))) return rc;
+  if ((rc = conv_backward(n, k++, 3, n->e2a, &e2, n->g_e2, n->g_e2a, B, false, true))) return rc;
+  if ((rc = conv_backward(n, k++, 2, n->p1, &n->e2a, n->g_e2a, n->g_p1, B, true, false))) return rc;
   NET_CK(cudaMemsetAsync(n->g_e1, 0, sizeof(float) * (size_t)B * S * S * 16, s));
   NET_CK(add_slice(n->g_cat1, 48, 32, B, S, S, 16, n->g_e1, s));
   NET_CK(avgpool2_backward(n->g_p1, B, S / 2, S / 2, 16, n->g_e1, s));
-  if ((rc = conv_backward(n, k++, 1, n->e1a, &e1, n->g_e1, n->g_e1a, B))) return rc;
-  if ((rc = conv_backward(n, k++, 0, n->in0, &n->e1a, n->g_e1a, nullptr, B))) return rc;
+  if ((rc = conv_backward(n, k++, 1, n->e1a, &e1, n->g_e1, n->g_e1a, B, false, true))) return rc;
+  if ((rc = conv_backward(n, k++, 0, n->in0, &n->e1a, n->g_e1a, nullptr, B, true, false))) return rc;
   return SS_OK;
 }
 
@@ -512,6 +529,8 @@ extern "C" int ss_net_create(ss_net** out, int theory, int size, int max_batch, 
   }
   add(&n->dyb, sizeof(__nv_bfloat16) * P0 * 16);
   add(&n->dyT, sizeof(__nv_bfloat16) * P0 * 16);
+  add(&n->dyb1, sizeof(__nv_bfloat16) * P0 * 16);
+  add(&n->dyT1, sizeof(__nv_bfloat16) * P0 * 16);
   add(&n->xT, sizeof(__nv_bfloat16) * P0 * 3 * 48);
   add(&n->xT1, sizeof(__nv_bfloat16) * P0 * 3 * 48);
   size_t total = 0;

@@ -26,6 +26,17 @@ enum ConvMode {
   CONV_BF16_BIAS_RELU = 0,  // out (bf16) = relu(acc + bias)
   CONV_F32_BIAS = 1,        // out (fp32) = acc + bias
   CONV_F32 = 2,             // out (fp32) = acc          (input gradients)
+  CONV_GRAD_RELU = 3,       // input gradient through the previous layer's ReLU (GradRelu)
+};
+
+// CONV_GRAD_RELU: g = acc * (mask > 0) (mask: that layer's BF16 output, the view read
+// as this convolution's output shape) goes out as BF16 NHWC (out), BF16 channel-major
+// dyT [Cout][N][H][W], and its sum over pixels is added to dbias [Cout]: what
+// relu_grad makes of the FP32 input gradient, without writing it.
+struct GradRelu {
+  Act mask;
+  void* dyT = nullptr;
+  float* dbias = nullptr;
 };
 
 // out[n, y, x, co] = epilogue( sum_{tap, ci} x[n, y + dy, x + dx, ci] * w[co, tap, ci] )
@@ -33,7 +44,7 @@ enum ConvMode {
 // 96, 144; Cin a multiple of 16; H * W a multiple of 128 with W a multiple of 32 (W < 128)
 // or of 128. `err` (device int) is set non-zero when a wait in the kernel gives up.
 cudaError_t conv3x3_tc(const Act& x, const void* w, int Cout, int mode, const float* bias, const Act& out, int* err,
-                       cudaStream_t s);
+                       cudaStream_t s, const GradRelu* gr = nullptr);
 
 // dw[co, tap, ci] += sum_{n, y, x} dyT[co, n, y, x] * xT[dx][ci, n, y + dy, x]
 // dyT: BF16 [Cout][N][H][W]; xT: BF16 [3][Cin][N][H][W], copy dx + 1 holding the
