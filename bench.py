@@ -47,6 +47,10 @@ cost on the 4096^2 workload (passes and the sine-transform Poisson solve) agains
 same workload without it, and time to dx dy max|G| < 1e-6 of the 1024^2 configuration
 (8 skyrmions) with and without it.
 
+--workload unet: the learned initialiser's training step (ss_net_train_step) and forward
+pass at 256^2, batch 16, Abelian Higgs channels, on seeded synthetic fields: ms per call
+after warm-up (CUDA-synchronised wall clock over --steps calls).
+
 --workload ah-batch: time per solve to dx dy max|G| < 1e-6 on the batched Abelian
 Higgs set (256 problems, sides 64..512, dx = 0.1, lambda ~ U[0.5, 2], N in 1..4):
 one bench step = the whole set relaxed in one batch (compensated FP32), against
@@ -1017,6 +1021,49 @@ def run_demag(args) -> int:
     return 0
 
 
+def run_unet(args) -> int:
+    """U-Net training step and forward pass at 256^2, batch 16 (see the module docstring)."""
+    rank, local_rank, world = D.env_rank()
+    if rank != 0:
+        return 0
+    D.pin_visible_device(local_rank, 1)
+    import numpy as np
+    import torch
+    from paper_2603_24370_gb300 import build as B
+    from paper_2603_24370_gb300 import soliton as S
+    B.build()
+    S.load_library()
+    nb, side, C = 16, 256, 4
+    g = torch.Generator(device="cuda").manual_seed(1)
+    ansatz = torch.randn((nb, C, side, side), generator=g, device="cuda") * 0.5
+    relaxed = ansatz + 0.05 * torch.randn((nb, C, side, side), generator=g, device="cuda")
+    cp = np.linspace(0.5, 1.5, nb)
+    out = torch.empty((nb, side, side, 16), device="cuda")
+    net = S.ss_net_create(S.SS_ABELIAN_HIGGS, side, nb, seed=3)
+    try:
+        for _ in range(max(args.warmup, 3)):
+            S.ss_net_train_step(net, ansatz, cp, relaxed, nb, 1e-4)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            loss = S.ss_net_train_step(net, ansatz, cp, relaxed, nb, 1e-4)
+        torch.cuda.synchronize()
+        train_ms = 1e3 * (time.perf_counter() - t0) / args.steps
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            S.ss_net_forward(net, ansatz, cp, nb, out)
+        torch.cuda.synchronize()
+        fwd_ms = 1e3 * (time.perf_counter() - t0) / args.steps
+    finally:
+        S.ss_net_destroy(net)
+    print(json.dumps({"metric": "U-Net training step and forward pass, 256^2, batch 16", "unit": "ms",
+                      "higher_is_better": False, "n_gpus": 1, "data": "synthetic", "dtype": "bf16 (fp32 accumulate)",
+                      "steps": args.steps, "warmup": max(args.warmup, 3),
+                      "config": {"workload": "4-level U-Net (16/32/48/96 channels), Abelian Higgs input, 256^2 x 16"},
+                      "train_step_ms": train_ms, "forward_ms": fwd_ms, "loss": loss}))
+    return 0
+
+
 def main() -> int:
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -1026,7 +1073,7 @@ def main() -> int:
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grid", type=int, default=N, help="grid side (default: the 4096 workload; smaller for ncu)")
     ap.add_argument("--workload",
-                    choices=("cm4096", "ah-batch", "configs", "methods", "baby-skyrme", "bec", "sid", "demag"),
+                    choices=("cm4096", "ah-batch", "configs", "methods", "baby-skyrme", "bec", "sid", "demag", "unet"),
                     default="cm4096")
     ap.add_argument("--tile-shape", choices=("auto", "0", "1"), default="auto",
                     help="flow tile shape: autotuned (default) or fixed with default grids (for profiling "
@@ -1056,6 +1103,8 @@ def main() -> int:
         return run_sid(args)
     if args.workload == "demag":
         return run_demag(args)
+    if args.workload == "unet":
+        return run_unet(args)
     return run_native(args)
 
 
