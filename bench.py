@@ -55,6 +55,7 @@ after warm-up (CUDA-synchronised wall clock over --steps calls).
 Higgs set (256 problems, sides 64..512, dx = 0.1, lambda ~ U[0.5, 2], N in 1..4):
 one bench step = the whole set relaxed in one batch (compensated FP32), against
 the all-FP64 flow run one problem at a time on a seeded subsample of every side.
+The line also carries the set's flow throughput while every problem runs.
 """
 from __future__ import annotations
 
@@ -513,6 +514,33 @@ def run_solve(args) -> int:
     conv = sum(1 for r in recs if r["converged"])
     probs = allp
 
+    # flow throughput of the whole set while every problem runs (the first steps from the
+    # ansatz), against the measured HBM bandwidth for the passes' algorithmic bytes
+    thr = None
+    if rank == 0:
+        peaks, _ = measured_peaks()
+        b = S.ss_batch_create(S.SS_ABELIAN_HIGGS, S.SS_FP32, allp)
+        try:
+            S.ss_batch_autotune(b, 4)
+            for _ in range(3):
+                S.ss_batch_step(b, INNER)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            nthr = 4
+            for _ in range(nthr):
+                _, sts = S.ss_batch_step(b, INNER)
+            torch.cuda.synchronize()
+            ms_step = 1e3 * (time.perf_counter() - t1) / (nthr * INNER)
+        finally:
+            S.ss_batch_destroy(b)
+        sites = sum(p.interior_sites for p in allp)
+        bps = 60 * 4  # compensated FP32, C = 4: pass 1 28 C, pass 2 32 C bytes per site
+        thr = {"site_updates_per_s": sites / (ms_step * 1e-3), "ms_per_flow_step": ms_step,
+               "interior_sites": sites, "bytes_per_site_update": bps,
+               "step_hbm_frac_of_measured": sites * bps / (ms_step * 1e-3) / 1e9 / peaks["hbm_gbs"],
+               "running_after": sum(1 for x in sts if not x["converged"]),
+               "timed": f"{nthr} x {INNER} flow steps after 3 x {INNER}, from the ansatz"}
+
     # all-FP64 flow, one problem at a time, on a seeded subsample of every side;
     # the set's mean is the size-weighted mean of the per-side means
     plain = None
@@ -550,6 +578,7 @@ def run_solve(args) -> int:
                        "parallelism": (f"work list sharded over {world} ranks by interior sites, "
                                        f"{[len(p) for p in parts]} problems") if world > 1 else "single"},
             "converged": conv, "verdict": "FP64 residual of the stored field (value + remainder)",
+            "throughput_all_running": thr,
             "mean_flow_steps": float(np.mean(steps_all)), "max_flow_steps": int(max(steps_all)),
             "converged_by_side": {str(side): sum(1 for p, r in zip(allp, recs) if p.nx == side and r["converged"])
                                   for side in sorted({p.nx for p in allp})},

@@ -573,6 +573,22 @@ __device__ __forceinline__ int next_running(const ProbDesc<R>* __restrict__ prob
   return total;
 }
 
+// The per-tile flags of the view, from the problem's record.
+template <typename R, int PASS>
+__device__ __forceinline__ void set_tile_flags(TileCtx<R>& tc, const DevState* st) {
+  const long long steps = st->steps;
+  tc.skip = tile_skip<PASS>(st);
+  tc.cur = (int)(steps & 1);
+  tc.arrest = (PASS == 2) && (st->arrest != 0);
+  tc.has_prev = (PASS == 1) && (steps > 0);
+  // FP32 pass 1 sums E_h itself on the first field, every SS_E_EVERY-th step and on
+  // the last field of a run; in between E_h = E_h(previous) + dE, the cancellation-free
+  // change it sums anyway for Eq. 4 (drift over SS_E_EVERY steps: a few roundings of dE)
+  tc.want_e = PASS != 1 || sizeof(R) == 8 || steps == 0 || (steps & (SS_E_EVERY - 1)) == 0 ||
+              steps >= st->step_limit;
+  tc.adv = (PASS == 3) && (steps < st->step_limit);
+}
+
 // Thread 0 stages the view of tile t. A problem's record changes only when its last
 // tile of a launch arrives, so while any of its tiles is still unprocessed (as tile
 // t is here) the view stays valid: it may be read ahead of use. A launch over a
@@ -592,17 +608,24 @@ __device__ __forceinline__ void load_tile_ctx(TileCtx<R>& tc, const ProbDesc<R>&
     tc.p = p;
     st = tc.d.st;
   }
-  const long long steps = st->steps;
-  tc.skip = tile_skip<PASS>(st);
-  tc.cur = (int)(steps & 1);
-  tc.arrest = (PASS == 2) && (st->arrest != 0);
-  tc.has_prev = (PASS == 1) && (steps > 0);
-  // FP32 pass 1 sums E_h itself on the first field, every SS_E_EVERY-th step and on
-  // the last field of a run; in between E_h = E_h(previous) + dE, the cancellation-free
-  // change it sums anyway for Eq. 4 (drift over SS_E_EVERY steps: a few roundings of dE)
-  tc.want_e = PASS != 1 || sizeof(R) == 8 || steps == 0 || (steps & (SS_E_EVERY - 1)) == 0 ||
-              steps >= st->step_limit;
-  tc.adv = (PASS == 3) && (steps < st->step_limit);
+  set_tile_flags<R, PASS>(tc, st);
+}
+
+// The same for a batch by the 32 lanes of warp 0 (t is uniform over the warp): the
+// descriptor copied in 8-byte words in parallel, the record's flags by lane 0.
+template <typename R, int PASS>
+__device__ __forceinline__ void load_tile_ctx_warp(TileCtx<R>& tc, const ProbDesc<R>* __restrict__ probs,
+                                                   const int* __restrict__ tile_prob, int t) {
+  static_assert(sizeof(ProbDesc<R>) % 8 == 0, "the descriptor is copied in 8-byte words");
+  const int lane = threadIdx.x & 31;
+  const int p = tile_prob[t];
+  const unsigned long long* src = reinterpret_cast<const unsigned long long*>(probs + p);
+  unsigned long long* dst = reinterpret_cast<unsigned long long*>(&tc.d);
+  for (int i = lane; i < (int)(sizeof(ProbDesc<R>) / 8); i += 32) dst[i] = src[i];
+  if (lane == 0) {
+    tc.p = p;
+    set_tile_flags<R, PASS>(tc, probs[p].st);
+  }
 }
 
 // One flow pass over every tile of a batch. ONE: the batch has a single problem,
@@ -640,6 +663,7 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
   R* const setP = sm + (PASS == 1 ? 3 : (PASS == 2 ? 2 : 1)) * PS;  // demagnetisation: psi of phi^n
   // passes 1, 3: running sums over this block's consecutive tiles of one problem
   R es = R(0), ec = R(0), ds = R(0), dc = R(0), gmr = R(0);
+  int run_lt0 = -1;  // local index of the first tile of the block's current run
 
   // The block's tiles: blockIdx.x, + gridDim.x, ... For a batch, warp 0 finds the next
   // tile of a running problem (s_next, one slot per buffer) while the block works on
@@ -651,10 +675,8 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
   } else {
     if (tid < 32) {
       const int t0 = next_running<R, PASS>(probs, tile_prob, blockIdx.x, gridDim.x, total_tiles);
-      if (tid == 0) {
-        s_next[0] = t0;
-        if (t0 < total_tiles) load_tile_ctx<R, PASS, ONE>(tcb[0], one, probs, tile_prob, t0);
-      }
+      if (tid == 0) s_next[0] = t0;
+      if (t0 < total_tiles) load_tile_ctx_warp<R, PASS>(tcb[0], probs, tile_prob, t0);
     }
     __syncthreads();
     t = s_next[0];
@@ -667,10 +689,8 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
       if (tid == 0 && tn1 < total_tiles) load_tile_ctx<R, PASS, ONE>(tcb[buf ^ 1], one, probs, tile_prob, tn1);
     } else if (tid < 32) {
       const int tn1 = next_running<R, PASS>(probs, tile_prob, t + gridDim.x, gridDim.x, total_tiles);
-      if (tid == 0) {
-        s_next[buf ^ 1] = tn1;
-        if (tn1 < total_tiles) load_tile_ctx<R, PASS, ONE>(tcb[buf ^ 1], one, probs, tile_prob, tn1);
-      }
+      if (tid == 0) s_next[buf ^ 1] = tn1;
+      if (tn1 < total_tiles) load_tile_ctx_warp<R, PASS>(tcb[buf ^ 1], probs, tile_prob, tn1);
     }
     const TileCtx<R>& tc = tcb[buf];
     if (tc.skip) {  // uniform over the block (batches: only if a record changed after the search)
@@ -1061,32 +1081,29 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
       }
 
       // ---- partials: the block keeps summing while its next tile belongs to the same
-      // problem; otherwise it reduces and writes the running sums. Batches: a problem's
-      // tiles are spread over blocks, so every tile counts (a zero partial for a tile
-      // whose run goes on) and the partials are indexed by tile. A single problem: every
-      // block with tiles flushes exactly once, at its last tile, into its own slot, and
-      // the blocks are counted (no per-tile fence or counter). The arrival that
+      // problem; otherwise it reduces and writes the running sums into the slot of its
+      // run, and the runs are counted (no per-tile fence or counter). A problem's tiles
+      // are one contiguous index range and a block walks its tiles in increasing order,
+      // so each block's tiles of a problem form one run: a problem has min(grid, tiles)
+      // runs, and the first tile of block b's run has local index (b - tile0) mod grid,
+      // below that count (a single problem: the block index). The arrival that
       // completes the count reduces the problem's partials in slot order and decides.
       // (A block that still holds another tile of the problem can never be the last.)
       const ProbDesc<R>& d = D;
+      if (run_lt0 < 0) run_lt0 = lt;
       const int tn = ONE ? t + (int)gridDim.x : s_next[buf ^ 1];  // written before the staging barrier
       const bool flush = ONE ? tn >= total_tiles : !(tn < total_tiles && tcb[buf ^ 1].p == tc.p);
-      if (!flush) {
-        if (!ONE && tid == 0) {
-          d.part[lt] = FlowPartial{0.0, 0.0, 0.0, 0.0, 0.0, {0.0, 0.0, 0.0}};
-          __threadfence();
-          atomicAdd(&d.st->ticket, 1u);
-        }
-        continue;
-      }
-      const int nslots = ONE ? min((int)gridDim.x, d.ntiles) : d.ntiles;
+      if (!flush) continue;
+      const int slot = ONE ? (int)blockIdx.x : run_lt0;
+      run_lt0 = -1;
+      const int nslots = min((int)gridDim.x, d.ntiles);
       RPair<R> pe{es, ec}, pd{ds, dc};
       R pm = gmr;
       tile_reduce<R>(pe, pd, pm, sred);
       es = ec = ds = dc = gmr = R(0);  // the next run of tiles starts afresh
       if (tid == 0) {
-        d.part[ONE ? (int)blockIdx.x : lt] = FlowPartial{(double)pe.s, (double)pe.c, (double)pd.s, (double)pd.c,
-                                                         (double)pm, {0.0, 0.0, 0.0}};
+        d.part[slot] = FlowPartial{(double)pe.s, (double)pe.c, (double)pd.s, (double)pd.c, (double)pm,
+                                   {0.0, 0.0, 0.0}};
         __threadfence();
         const unsigned prev = atomicAdd(&d.st->ticket, 1u);
         s_last = (prev == (unsigned)nslots - 1);
@@ -1270,14 +1287,17 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
       }
       }
       // The step count selects the ping-pong buffers and gates every tile of this
-      // problem, so it advances only when the problem's last tile has arrived (its
-      // own stores need not be finished: nothing in this launch reads them, and the
-      // next launch starts after this one ends).
-      if (tid == 0) {
+      // problem, so it advances only when the problem's last run of tiles has arrived
+      // (runs as in pass 1: a block's tiles of a problem are consecutive, one arrival
+      // per run; its own stores need not be finished: nothing in this launch reads
+      // them, and the next launch starts after this one ends).
+      const int tn = ONE ? t + (int)gridDim.x : s_next[buf ^ 1];
+      const bool run_ends = ONE ? tn >= total_tiles : !(tn < total_tiles && tcb[buf ^ 1].p == tc.p);
+      if (run_ends && tid == 0) {
         __threadfence();
         DevState* st = D.st;
         const unsigned prev = atomicAdd(&st->ticket, 1u);
-        if (prev == (unsigned)D.ntiles - 1) {
+        if (prev == (unsigned)min((int)gridDim.x, D.ntiles) - 1) {
           st->ticket = 0;
           st->steps += 1;
         }
