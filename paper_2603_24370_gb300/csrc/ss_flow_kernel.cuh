@@ -688,9 +688,20 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
       const int tn1 = t + gridDim.x;
       if (tid == 0 && tn1 < total_tiles) load_tile_ctx<R, PASS, ONE>(tcb[buf ^ 1], one, probs, tile_prob, tn1);
     } else if (tid < 32) {
-      const int tn1 = next_running<R, PASS>(probs, tile_prob, t + gridDim.x, gridDim.x, total_tiles);
+      // the common case: the block's next tile belongs to the same running problem, whose
+      // view is this tile's (its record cannot change before that tile has run)
+      const int cand = t + (int)gridDim.x;
+      const bool same = cand < total_tiles && !tcb[buf].skip && tile_prob[cand] == tcb[buf].p;
+      const int tn1 = same ? cand : next_running<R, PASS>(probs, tile_prob, cand, gridDim.x, total_tiles);
       if (tid == 0) s_next[buf ^ 1] = tn1;
-      if (tn1 < total_tiles) load_tile_ctx_warp<R, PASS>(tcb[buf ^ 1], probs, tile_prob, tn1);
+      if (same) {
+        static_assert(sizeof(TileCtx<R>) % 8 == 0, "the view is copied in 8-byte words");
+        const unsigned long long* src = reinterpret_cast<const unsigned long long*>(&tcb[buf]);
+        unsigned long long* dst = reinterpret_cast<unsigned long long*>(&tcb[buf ^ 1]);
+        for (int i = tid; i < (int)(sizeof(TileCtx<R>) / 8); i += 32) dst[i] = src[i];
+      } else if (tn1 < total_tiles) {
+        load_tile_ctx_warp<R, PASS>(tcb[buf ^ 1], probs, tile_prob, tn1);
+      }
     }
     const TileCtx<R>& tc = tcb[buf];
     if (tc.skip) {  // uniform over the block (batches: only if a record changed after the search)
