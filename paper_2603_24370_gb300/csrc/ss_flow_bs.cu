@@ -14,6 +14,10 @@
 #define SS_MINB3 3
 #define SS_LU1 1
 #define SS_LU2 1
+// Pass 1 stages the tiles at the grid's edge through the scalar path: with the masked
+// vector loop beside the plain one it ran 0.139 -> 0.143 ms at 2048^2 (pass 2 gained
+// 0.141 -> 0.139 ms from it).
+#define SS_VEDGE1 0
 #include "ss_flow_kernel.cuh"
 
 namespace ss {

@@ -9,6 +9,11 @@
 //
 // The descent pass unrolls its vector staging loop by three (0.264 -> 0.253 ms at
 // 4096^2; passes 1 and 2 measured no gain from it).
+//
+// Pass 2 stages the tiles at the grid's edge through the scalar path: beside the
+// masked vector loop its single-problem kernel spills (0 -> 56 bytes), and with
+// that loop it ran 1.7% slower at 4096^2 (0.4286 -> 0.4360 ms).
+#define SS_VEDGE2 0
 #define SS_PF2 1
 #define SS_MINB2 3
 #define SS_VUNR3 3

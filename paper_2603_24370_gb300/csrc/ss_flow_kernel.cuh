@@ -122,8 +122,21 @@
 #ifndef SS_MINB1
 #define SS_MINB1 3
 #endif
-// Width (2 or 4 sites) of the vector units that stage interior tiles of FP32 grids
-// whose rows start on 16-byte boundaries: compensated storage, plain FP32.
+// Vector staging of tiles at the grid's edge, per pass (0: those take the scalar path).
+#ifndef SS_VEDGE
+#define SS_VEDGE 1
+#endif
+#ifndef SS_VEDGE1
+#define SS_VEDGE1 SS_VEDGE
+#endif
+#ifndef SS_VEDGE2
+#define SS_VEDGE2 SS_VEDGE
+#endif
+#ifndef SS_VEDGE3
+#define SS_VEDGE3 SS_VEDGE
+#endif
+// Width (2 or 4 sites) of the vector units that stage tiles of FP32 grids whose rows
+// start on 16-byte boundaries: compensated storage, plain FP32.
 #ifndef SS_VW_LO
 #define SS_VW_LO 2
 #endif
@@ -639,6 +652,11 @@ constexpr int pass_min_blocks() {
              : 1;
 }
 
+template <bool B>
+struct BoolC {
+  static constexpr bool value = B;
+};
+
 template <int TH, typename R, int PASS, bool LO, bool ONE, int TS>
 __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
     k_pass(const __grid_constant__ ProbDesc<R> one, const ProbDesc<R>* __restrict__ probs,
@@ -737,21 +755,26 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
     constexpr int LU = PASS == 1 ? SS_LU1 : (PASS == 2 ? SS_LU2 : SS_LU3);
     bool vec = false;  // float4 staging: every loaded site in bounds, every used site in I
     if constexpr (sizeof(R) == 4) vec = D.vec && x0 >= 4 && x0 + T::TX + 4 <= nx && y0 >= 4 && y0 + T::TY + 4 <= ny;
+    // the same units on tiles at the grid's edge (FP32 rows of whole 16-byte units): each
+    // unit is wholly in or out of the grid (x0 - 4 and nx are multiples of it)
+    constexpr bool VEDGE = PASS == 1 ? SS_VEDGE1 : (PASS == 2 ? SS_VEDGE2 : SS_VEDGE3);
+    bool vedge = false;
+    if constexpr (sizeof(R) == 4 && VEDGE) vedge = D.vec && !vec;
     if constexpr (sizeof(R) == 4) {
+      // units of VW consecutive sites of one shared row (shared columns VW u ..,
+      // sites x0 - 4 + VW u ..): one VW-wide load per stored plane, one VW-wide store
+      // per staged plane. The stencils read shared columns OX - 2 .. OX + TX + 1; with
+      // SS_VSKIPn units wholly outside them (the outermost two columns of each side,
+      // with 2-site units) are not staged. Compensated storage loads twice the planes:
+      // narrower units keep them in registers.
+      constexpr int VW = LO ? (PASS == 1 ? SS_VW1_LO : (PASS == 2 ? SS_VW2_LO : SS_VW3_LO)) : SS_VW_PLAIN;
+      using V = typename VecOf<VW>::T;
+      constexpr bool VSKIP = PASS == 1 ? SS_VSKIP1 : (PASS == 2 ? SS_VSKIP2 : SS_VSKIP3);
+      constexpr int U0 = VSKIP ? (T::OX - 2) / VW : 0;  // first and last unit staged
+      constexpr int U1 = VSKIP ? (T::OX + T::TX + 1) / VW : T::SX / VW - 1;
+      constexpr int UW = U1 - U0 + 1, NU = UW * T::SY;
+      constexpr int VUNR = PASS == 1 ? SS_VUNR1 : (PASS == 2 ? SS_VUNR2 : SS_VUNR3);
       if (vec) {
-        // units of VW consecutive sites of one shared row (shared columns VW u ..,
-        // sites x0 - 4 + VW u ..): one VW-wide load per stored plane, one VW-wide store
-        // per staged plane. The stencils read shared columns OX - 2 .. OX + TX + 1; with
-        // SS_VSKIPn units wholly outside them (the outermost two columns of each side,
-        // with 2-site units) are not staged. Compensated storage loads twice the planes:
-        // narrower units keep them in registers.
-        constexpr int VW = LO ? (PASS == 1 ? SS_VW1_LO : (PASS == 2 ? SS_VW2_LO : SS_VW3_LO)) : SS_VW_PLAIN;
-        using V = typename VecOf<VW>::T;
-        constexpr bool VSKIP = PASS == 1 ? SS_VSKIP1 : (PASS == 2 ? SS_VSKIP2 : SS_VSKIP3);
-        constexpr int U0 = VSKIP ? (T::OX - 2) / VW : 0;  // first and last unit staged
-        constexpr int U1 = VSKIP ? (T::OX + T::TX + 1) / VW : T::SX / VW - 1;
-        constexpr int UW = U1 - U0 + 1, NU = UW * T::SY;
-        constexpr int VUNR = PASS == 1 ? SS_VUNR1 : (PASS == 2 ? SS_VUNR2 : SS_VUNR3);
 #pragma unroll VUNR
         for (int u = tid; u < NU; u += NT) {
           const int ly = u / UW, ux = U0 + (u - ly * UW);
@@ -809,11 +832,77 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
           if (TH == TH_CMD) stv<VW>(setP + so, Z4);
         }
       }
+      if constexpr (VEDGE) {
+        if (vedge) {  // the loop above with each unit masked to the grid, each site to I
+#pragma unroll 1
+          for (int u = tid; u < NU; u += NT) {
+            const int ly = u / UW, ux = U0 + (u - ly * UW);
+            const int gy = y0 - 2 + ly, gx = x0 - 4 + VW * ux;  // the unit's first site
+            const bool uin = (gy >= 0 && gy < ny && gx >= 0 && gx < nx);
+            const size_t s = uin ? (size_t)gy * nx + (size_t)gx : 0;
+            const int so = ly * T::SX + VW * ux;
+            const V z = vzero<VW>();
+            V P4[C], L4[C], V4[C], A4[C], B4[C], Z4 = z;
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+              P4[c] = uin ? ldv<VW>(phi + c * P + s) : z;
+              L4[c] = (LO && uin) ? ldv<VW>(lo + c * P + s) : z;
+              V4[c] = (PASS != 3 && !arrest && uin) ? ldv<VW>(vel + c * P + s) : z;
+              if (PASS == 1) {  // the previous field (A: value, B: remainder)
+                A4[c] = (has_prev && uin) ? ldv<VW>(phi_prev + c * P + s) : P4[c];
+                B4[c] = (LO && has_prev && uin) ? ldv<VW>(lo_prev + c * P + s) : L4[c];
+              } else if (PASS == 2) {  // k_v1, k_v2
+                A4[c] = uin ? ldv<VW>(kv1 + c * P + s) : z;
+                B4[c] = arrest ? A4[c] : (uin ? ldv<VW>(kv2 + c * P + s) : z);
+              }
+            }
+            if (TH == TH_CMD) Z4 = uin ? ldv<VW>(psi + s) : z;
+            const bool row_in = (gy >= 2 && gy < ny - 2);
+            V OA[C], OB[C], OD[C];
+#pragma unroll
+            for (int j = 0; j < VW; ++j) {
+              // site in I: velocities and stage slopes are zero outside it, and the
+              // unit-vector constraint is applied only inside it
+              const bool ins = (uin && row_in && gx + j >= 2 && gx + j < nx - 2);
+              R pv[C], lv[C], vv[C], aa[C], bb[C], ya[C], yb[C], yd[C];
+#pragma unroll
+              for (int c = 0; c < C; ++c) {
+                pv[c] = vat(P4[c], j);
+                lv[c] = vat(L4[c], j);
+                vv[c] = ins ? vat(V4[c], j) : R(0);
+                aa[c] = (PASS != 2 || ins) ? vat(A4[c], j) : R(0);
+                bb[c] = (PASS != 2 || ins) ? vat(B4[c], j) : R(0);
+              }
+              stage_site<TH, R, PASS, LO>(pv, lv, vv, aa, bb, aa, bb, ins, hdt, dt, c3, c4, ya, yb, yd);
+#pragma unroll
+              for (int c = 0; c < C; ++c) {
+                vat(OA[c], j) = ya[c];
+                if (PASS != 3) vat(OB[c], j) = yb[c];
+                if (PASS == 1) vat(OD[c], j) = yd[c];
+              }
+            }
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+              if constexpr (PK) {  // interleaved (Y_a, Y_b) pairs
+                float* ab = setA + 2 * (c * T::SXY + so);
+#pragma unroll
+                for (int j = 0; j < VW; j += 2)
+                  stv<4>(ab + 2 * j, make_float4(vat(OA[c], j), vat(OB[c], j), vat(OA[c], j + 1), vat(OB[c], j + 1)));
+              } else {
+                stv<VW>(setA + c * T::SXY + so, OA[c]);
+                if (PASS != 3) stv<VW>(setB + c * T::SXY + so, OB[c]);
+              }
+              if (PASS == 1) stv<VW>(setD + c * T::SXY + so, OD[c]);
+            }
+            if (TH == TH_CMD) stv<VW>(setP + so, Z4);
+          }
+        }
+      }
     }
-    // scalar staging (grid edges, rows not 16-byte aligned, FP64): LU sites per
-    // iteration, the loads of all LU sites issued before any is used
+    // scalar staging (rows not 16-byte aligned, FP64; grid edges when SS_VEDGEn is 0): LU
+    // sites per iteration, the loads of all LU sites issued before any is used
     constexpr int SWY = T::SW * T::SY;
-    for (int base = tid; !vec && base < SWY; base += LU * NT) {
+    for (int base = tid; !vec && !vedge && base < SWY; base += LU * NT) {
       R pv[LU][C], lv[LU][C], vv[LU][C], k1v[LU][C], k2v[LU][C], pp[LU][C], lp[LU][C], pz[LU];
       bool in[LU], inside[LU];
 #pragma unroll

@@ -12,6 +12,9 @@
 #define SS_MINB3 2
 #define SS_LU1 1
 #define SS_LU2 1
+// Tiles at the grid's edge take the scalar staging: with the masked vector loop beside
+// the plain one passes 1 and 2 ran 0.280 + 0.221 -> 0.297 + 0.226 ms at 2048^2.
+#define SS_VEDGE 0
 #include "ss_flow_kernel.cuh"
 
 namespace ss {

@@ -20,6 +20,8 @@ AH, CM = 1, 2
 AH_PRM = (1.0, 1.0)
 CM_PRM = (1.0, 1.0, 0.1, 0.6, 0.0)
 GRIDS = {AH: (77, 45, 0.2, 0.17), CM: (83, 38, 0.2, 0.23)}  # ragged tiles, unequal spacings
+# nx % 4 == 0: FP32 rows of whole 16-byte units, vector-staged at the grid's edges too
+UNIT_GRIDS = {AH: (76, 45, 0.2, 0.17), CM: (20, 9, 0.2, 0.23)}
 
 
 @pytest.fixture(scope="module")
@@ -54,8 +56,9 @@ def oracle_descent(theory, f, dx, dy, n, factor=0.8):
 
 @pytest.mark.parametrize("theory", [AH, CM])
 @pytest.mark.parametrize("prec", [1, 2, 3])
-def test_descent_trajectory_matches_oracle(S, theory, prec):
-    nx, ny, dx, dy = GRIDS[theory]
+@pytest.mark.parametrize("units", [False, True])
+def test_descent_trajectory_matches_oracle(S, theory, prec, units):
+    nx, ny, dx, dy = (UNIT_GRIDS if units else GRIDS)[theory]
     n = 40
     f = I.smooth_field(theory, nx, ny, dx, dy, seed=505).astype(dtype_of(prec))
     with S.Solver(theory, prm(theory), nx, ny, dx, dy, prec) as s:
@@ -69,7 +72,12 @@ def test_descent_trajectory_matches_oracle(S, theory, prec):
     fo, Eo, rises = oracle_descent(theory, f, dx, dy, n)
     tol = 1e-10 if prec == 2 else 2e-5
     assert np.abs(fg - fo).max() <= tol * max(1.0, np.abs(fo).max())
-    assert st["steps"] == n and st["arrests"] == rises == 0 and not st["arrested"]
+    assert st["steps"] == n and st["arrests"] == rises
+    # on the 20 x 9 chiral-magnet grid the fixed step raises the energy on a few steps
+    # (in the oracle as in the kernels); elsewhere it never does
+    assert rises == 0 or (theory, units) == (CM, True)
+    if rises == 0:
+        assert not st["arrested"]
     assert not vg.any()  # first-order flow: no velocity
     # the status describes the final field (the run ends with its evaluation)
     assert st["energy"] == pytest.approx(Eo, rel=1e-12 if prec == 2 else 1e-5)

@@ -50,12 +50,22 @@ def dtype_of(prec):
 
 # grids spanning several 32x16 tiles with ragged edges, unequal spacings
 GRIDS = {AH: (77, 45, 0.2, 0.17), CM: (83, 38, 0.2, 0.23)}
+# FP32 rows of whole 16-byte units (nx % 4 == 0) take the vector staging at the grid's
+# edges too: several tiles with a ragged last row of tiles, and grids narrower than
+# one tile (every unit right of the grid outside it)
+UNIT_GRIDS = {"units": {AH: (76, 45, 0.2, 0.17), CM: (84, 38, 0.2, 0.23)},
+              "narrow": {AH: (12, 41, 0.2, 0.17), CM: (20, 9, 0.2, 0.23)}}
+
+
+def grid_of(theory, kind):
+    return GRIDS[theory] if kind == "ragged" else UNIT_GRIDS[kind][theory]
 
 
 @pytest.mark.parametrize("theory", [AH, CM])
 @pytest.mark.parametrize("prec", [1, 2, 3])
-def test_force_and_energy_match_oracle(S, theory, prec):
-    nx, ny, dx, dy = GRIDS[theory]
+@pytest.mark.parametrize("kind", ["ragged", "units", "narrow"])
+def test_force_and_energy_match_oracle(S, theory, prec, kind):
+    nx, ny, dx, dy = grid_of(theory, kind)
     f = I.smooth_field(theory, nx, ny, dx, dy, seed=101).astype(dtype_of(prec))
     with S.Solver(theory, prm(theory), nx, ny, dx, dy, prec) as s:
         s.set_fields(f)
@@ -74,10 +84,11 @@ def test_force_and_energy_match_oracle(S, theory, prec):
 
 @pytest.mark.parametrize("theory", [AH, CM])
 @pytest.mark.parametrize("prec", [1, 2, 3])
-def test_trajectory_matches_oracle(S, theory, prec):
+@pytest.mark.parametrize("kind", ["ragged", "units", "narrow"])
+def test_trajectory_matches_oracle(S, theory, prec, kind):
     """30 flow steps from a smooth field at rest: fields, velocity, energy and the
     arrest count against the oracle's RK4 + Eq. 4 step by step."""
-    nx, ny, dx, dy = GRIDS[theory]
+    nx, ny, dx, dy = grid_of(theory, kind)
     n = 30
     f = I.smooth_field(theory, nx, ny, dx, dy, seed=202).astype(dtype_of(prec))
     with S.Solver(theory, prm(theory), nx, ny, dx, dy, prec) as s:
