@@ -14,7 +14,10 @@ One bench step = one call ss_step(ctx, 32): 32 flow steps, each two fused kernel
 the arrest decision; pass 2: RK stages 3-4 and the RK4 combination), enqueued as
 one CUDA graph. value = interior site-updates per second.
 e2e: the same calls with the field copied in from pinned host memory and out
-again every bench step (ss_set_fields / ss_step / ss_get_fields on host buffers).
+again every bench step (ss_set_fields / ss_step / ss_get_fields on host buffers),
+from two host threads that each drive one solver context on its own stream, so one
+context's copies overlap the other's flow; "serial" in the e2e object is one context
+driven from one thread, its copies between its flows.
 --impl reference: the FP64 CPU oracle on the host cores, same metric, each step one
 oracle flow step on a 512 x 512 crop of the same workload.
 
@@ -332,20 +335,51 @@ def run_native(args) -> int:
     # end to end through the C-ABI with host buffers: field in from pinned memory,
     # 32 flow steps, field out to pinned memory, every bench step
     host_in = torch.from_numpy(np.ascontiguousarray(f_init)).pin_memory()
-    host_out = torch.empty(host_in.shape, dtype=torch.float32).pin_memory()
-    e2e_steps = max(3, args.steps // 4)
+    host_out = [torch.empty(host_in.shape, dtype=torch.float32).pin_memory() for _ in range(2)]
+    e2e_steps = 2 * max(2, (args.steps + 7) // 8)  # bench steps, split over the two threads
+
+    def drive(sv, out, k, err):
+        try:
+            for _ in range(k):
+                sv.set_fields(host_in)
+                sv.step(INNER)
+                S.ss_get_fields(sv.ctx, out)
+        except Exception as exc:  # re-raised by the timing thread
+            err.append(exc)
+
+    # one context, one host thread: each step's copies sit between its flows
     s.set_fields(host_in)
     s.step(INNER)
     D.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        s.set_fields(host_in)
-        s.step(INNER)
-        S.ss_get_fields(s.ctx, host_out)
+    err = []
+    drive(s, host_out[0], e2e_steps, err)
     torch.cuda.synchronize()
-    e2e_sec = time.perf_counter() - t0
-    e_units, e_sec = D.aggregate(interior(n) * INNER * e2e_steps, e2e_sec)
+    if err:
+        raise err[0]
+    serial_units, serial_sec = D.aggregate(interior(n) * INNER * e2e_steps, time.perf_counter() - t0)
+    # two contexts, two host threads: one context's copies overlap the other's flow
+    s2 = S.Solver(S.SS_CHIRAL_MAGNET, p.params, n, n, DX, DX, S.SS_FP32, stream=torch.cuda.Stream())
+    s2.set_fields(host_in)
+    if gd:
+        s2.set_method(S.SS_METHOD_GRADIENT)
+    s2.set_launch(tuned["tile_shape"], tuned.get("blocks"))  # the first context's launch shape
+    s2.step(INNER)  # its graphs are captured here, before the threads start
+    D.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    err = []
+    th = [threading.Thread(target=drive, args=(sv, host_out[i], e2e_steps // 2, err)) for i, sv in enumerate((s, s2))]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    torch.cuda.synchronize()
+    if err:
+        raise err[0]
+    e_units, e_sec = D.aggregate(interior(n) * INNER * e2e_steps, time.perf_counter() - t0)
+    s2.close()
     nbytes = C * n * n * 4
 
     cpu = None
@@ -374,7 +408,10 @@ def run_native(args) -> int:
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": e_units / e_sec, "unit": "site-updates/s", "h2d_bytes_per_step": nbytes,
-                    "d2h_bytes_per_step": nbytes},
+                    "d2h_bytes_per_step": nbytes, "steps": e2e_steps,
+                    "overlap": "two solver contexts on two streams, driven from two host threads",
+                    "serial": {"value": serial_units / serial_sec, "steps": e2e_steps,
+                               "overlap": "none: one context, one host thread"}},
             "gpu_launches": launches_per_call * args.steps,
             "clocks": clk,
             "final_energy": st["energy"], "final_grad_max": st["grad_max"],

@@ -35,6 +35,10 @@
  *    NULL the context creates its own blocking stream (ordered with the legacy
  *    default stream; CUDA graphs cannot be captured on the legacy stream itself).
  *    Calls return after their GPU work has completed.
+ *  - Contexts are independent: different contexts may be driven at the same time
+ *    from different host threads (each on its own stream), so that one context's
+ *    host copies overlap another's flow. One context must not be used by two
+ *    threads at once.
  *  - The library is built for sm_103a only; it has no CPU fallback.
  */
 #ifndef SOLITON_H

@@ -268,3 +268,56 @@ def test_chiral_magnet_batch_matches_the_oracle_fp64(S):
             assert st[k]["arrests"] == arrests
     finally:
         S.ss_batch_destroy(b)
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_contexts_driven_from_two_threads_evolve_exactly_as_alone(S, prec):
+    """Two solver contexts on their own streams, each driven from its own host thread
+    (field in from pinned host memory, flow, field out: the overlapped end-to-end leg
+    of the benchmark), end every round on the fields and status each reaches when run
+    alone."""
+    import threading
+    cases = [(S.SS_CHIRAL_MAGNET, (1.0, 1.0, 0.1, 0.6, 0.0), 96, 84, 0.2, [[0.0, 0.0, -1, 2.0, 0.0]]),
+             (S.SS_ABELIAN_HIGGS, (1.0, 1.0), 77, 64, 0.2, [[0.5, -0.3, 1, 1.0, 0.0], [-1.0, 0.8, 2, 1.0, 0.0]])]
+    dt = np.float64 if prec == 2 else np.float32
+    starts, refs = [], []
+    for th, prm, nx, ny, dx, sol in cases:
+        with S.Solver(th, prm, nx, ny, dx, dx, prec) as s:
+            s.init_ansatz(sol)
+            f0 = s.fields()
+            s.set_fields(f0)  # the state the threads start from (no remainder part)
+            st = s.step(40)
+            refs.append((s.fields(), st["arrests"], st["energy"]))
+        starts.append(f0)
+    solvers = [S.Solver(th, prm, nx, ny, dx, dx, prec, stream=torch.cuda.Stream())
+               for th, prm, nx, ny, dx, sol in cases]
+    host_in = [torch.from_numpy(f).pin_memory() for f in starts]
+    host_out = [torch.empty(f.shape, dtype=torch.float64 if prec == 2 else torch.float32).pin_memory()
+                for f in starts]
+    got, err = [[], []], []
+
+    def drive(i):
+        try:
+            for _ in range(4):
+                solvers[i].set_fields(host_in[i])
+                st = solvers[i].step(40)
+                S.ss_get_fields(solvers[i].ctx, host_out[i])
+                got[i].append((host_out[i].numpy().copy(), st["arrests"], st["energy"]))
+        except Exception as exc:
+            err.append(exc)
+
+    try:
+        threads = [threading.Thread(target=drive, args=(i,)) for i in range(2)]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+        assert not err, err
+        for i in range(2):
+            assert len(got[i]) == 4
+            for f, arrests, energy in got[i]:
+                assert f.dtype == dt and np.array_equal(f, refs[i][0]), i
+                assert arrests == refs[i][1] and energy == refs[i][2]
+    finally:
+        for s in solvers:
+            s.close()
