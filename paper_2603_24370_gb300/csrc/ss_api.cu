@@ -305,6 +305,7 @@ int batch_layout(ss_batch* b, int ts, const int* blocks) {
   SS_CK(cudaMemcpy(b->tile_prob, tp.data(), sizeof(int) * tp.size(), cudaMemcpyHostToDevice));
   b->BL.total_tiles = total;
   b->BL.ts = ts;
+  b->BL.nprob = n;
   // a batch of one passes its descriptor to the pass kernels by value
   b->BL.one = n == 1 ? static_cast<const void*>(b->one_desc.data()) : nullptr;
   const int th = (b->demag ? TH_CMD : th_of(b->theory));

@@ -1204,10 +1204,13 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
       if (tid == 0) {
         d.part[slot] = FlowPartial{(double)pe.s, (double)pe.c, (double)pd.s, (double)pd.c, (double)pm,
                                    {0.0, 0.0, 0.0}};
-        __threadfence();
-        const unsigned prev = atomicAdd(&d.st->ticket, 1u);
-        s_last = (prev == (unsigned)nslots - 1);
+        if constexpr (ONE) {
+          __threadfence();
+          const unsigned prev = atomicAdd(&d.st->ticket, 1u);
+          s_last = (prev == (unsigned)nslots - 1);
+        }
       }
+      if constexpr (!ONE) continue;  // a batch's partials are totalled by k_decide after the launch
       __syncthreads();
       if (s_last) {
         __threadfence();
@@ -1406,6 +1409,96 @@ __global__ void __launch_bounds__(NT, pass_min_blocks<TH, R, PASS, ONE>())
   }
 }
 
+// Batched passes 1 and 3 only leave each run's partial sums in its slot. This kernel,
+// one block per problem, totals a problem's slots in slot order and decides as the
+// single-problem path's last arrival does: Eq. 4 for pass 1, the descent step's record
+// for pass 3. Inside the pass kernel the block that completed a problem's count did
+// that work, so a block that fell behind completed one count after another (57 of
+// the 256 decisions of the 256-problem set in one block, a fifth of the launch).
+template <typename R, int PASS>
+__global__ void __launch_bounds__(NT) k_decide(const ProbDesc<R>* __restrict__ probs, int nprob, int grid) {
+  __shared__ R sred[(NT / 32) * 5];
+  __shared__ double dred[RedSmem<2, 1>::n];
+  const int p = blockIdx.x;
+  if (p >= nprob) return;
+  const ProbDesc<R>& d = probs[p];
+  DevState* st = d.st;
+  if (tile_skip<PASS>(st)) return;  // the pass did not run this problem (its flags as the pass saw them)
+  const int tid = threadIdx.y * BX + threadIdx.x;
+  const long long steps = st->steps;
+  const bool has_prev = PASS == 1 && steps > 0;
+  const bool want_e = PASS != 1 || sizeof(R) == 8 || steps == 0 || (steps & (SS_E_EVERY - 1)) == 0 ||
+                      steps >= st->step_limit;
+  const int nslots = min(grid, d.ntiles);
+  double tot[2] = {0.0, 0.0}, mtot = 0.0;
+  if constexpr (sizeof(R) == 4) {
+    RPair<R> acc{R(0), R(0)}, dacc{R(0), R(0)};
+    R mm = R(0);
+    for (int i = tid; i < nslots; i += NT) {
+      const FlowPartial* q = d.part + i;
+      acc = pair_add(acc, RPair<R>{R(q->es), R(q->ec)});
+      dacc = pair_add(dacc, RPair<R>{R(q->ds), R(q->dc)});
+      mm = rmax(mm, R(q->m));
+    }
+    tile_reduce<R>(acc, dacc, mm, sred);
+    tot[0] = (double)acc.s + (double)acc.c;
+    tot[1] = (double)dacc.s + (double)dacc.c;
+    mtot = (double)mm;
+  } else {
+    DD acc{0.0, 0.0}, dacc{0.0, 0.0};
+    double mm = 0.0;
+    for (int i = tid; i < nslots; i += NT) {
+      const FlowPartial* q = d.part + i;
+      acc = dd_add(acc, DD{q->es, q->ec});
+      dacc = dd_add(dacc, DD{q->ds, q->dc});
+      mm = nanmax(mm, q->m);
+    }
+    DD sv2[2] = {acc, dacc};
+    double mv2[1] = {mm};
+    block_reduce<2, 1>(sv2, mv2, dred);
+    tot[0] = sv2[0].s + sv2[0].c;
+    tot[1] = sv2[1].s + sv2[1].c;
+    mtot = mv2[0];
+  }
+  if (tid != 0) return;
+  if (PASS == 1) {
+    const double dE = d.area * tot[1];
+    const double E = want_e ? d.area * tot[0] : st->E_last + dE;
+    const double g = d.area * mtot;
+    // Eq. 4, strict: E_h(phi^n) > E_h(phi^{n-1}); no previous field (E_last = +inf): no arrest
+    const int arr = has_prev ? (dE > 0.0 ? 1 : 0) : (E > st->E_last ? 1 : 0);
+    st->E_cur = E;
+    st->dE = has_prev ? dE : 0.0;
+    st->gmax = g;
+    st->arrest = arr;
+    st->arrests += arr;
+    st->E_last = E;
+    st->converged = (g < st->tol) ? 1 : 0;
+    st->nonfinite = (isfinite(E) && isfinite(g) && isfinite(dE)) ? 0 : 1;
+    st->head_step = st->steps;
+  } else {
+    // descent: record the evaluated field, count a rise, then take the step (its new
+    // field is already written) unless converged or out of budget
+    const double E = d.area * tot[0];
+    const double g = d.area * mtot;
+    const double El = st->E_last;
+    const int rose = E > El ? 1 : 0;  // E_last = +inf before the first field
+    st->E_cur = E;
+    st->dE = isfinite(El) ? E - El : 0.0;
+    st->gmax = g;
+    st->arrest = rose;
+    st->arrests += rose;
+    st->E_last = E;
+    const int conv = (g < st->tol) ? 1 : 0;
+    const int bad = (isfinite(E) && isfinite(g)) ? 0 : 1;
+    st->converged = conv;
+    st->nonfinite = bad;
+    st->head_step = st->steps;
+    if (!conv && !bad && st->steps < st->step_limit) st->steps += 1;
+  }
+  st->ticket = 0;
+}
+
 // ------------------------------------------------------------------ launchers
 template <int TH, typename R, int TS>
 static size_t pass_smem(int pass) {
@@ -1427,6 +1520,10 @@ static void pass_launch(const BatchLaunch& b, int pass, cudaStream_t s) {
   else
     k_pass<TH, R, 3, LO, ONE, TS><<<b.flow_blocks[2], blk, pass_smem<TH, R, TS>(3), s>>>(one, probs, b.tile_prob,
                                                                                           b.total_tiles);
+  if constexpr (!ONE) {  // a batch's decisions, one block per problem
+    if (pass == 1) k_decide<R, 1><<<b.nprob, blk, 0, s>>>(probs, b.nprob, b.flow_blocks[0]);
+    else if (pass == 3) k_decide<R, 3><<<b.nprob, blk, 0, s>>>(probs, b.nprob, b.flow_blocks[2]);
+  }
 }
 template <int TH, typename R, bool LO>
 static cudaError_t pass_t(const BatchLaunch& b, int pass, cudaStream_t s) {

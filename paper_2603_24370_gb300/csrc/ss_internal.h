@@ -76,6 +76,7 @@ struct BatchLaunch {
   int flow_blocks[3];  // grid of pass 1 / pass 2 / the descent pass
   const void* one;     // host copy of the ProbDesc<R> of a single-problem batch, else NULL
   int ts;              // tile shape: 0 small, 1 large (flow_tile_dims)
+  int nprob;           // problems of the batch
 };
 
 // One theory's flow-pass launcher and occupancy query (ss_flow_kernel.cuh), each
